@@ -1,0 +1,375 @@
+"""Benchmark of the space-time BEM hot path on GB300 (prints one JSON line).
+
+Workload (square256): unit-square boundary with N_x = 256 uniform segments,
+N_t = 256 uniform steps on T = 1, alpha = 1, Dirichlet datum
+g = U*(x - y*, t) with y* = (1.5, 1.5), u_0 = 0 (synthetic, seeded geometry).
+
+One step = the whole hot path on one GPU, inputs (the mesh) resident:
+  assembly of V_h, K_h, D_h (FP64, 3 x 256 x 256 x 256 Toeplitz entries),
+  right-hand side f = 1/2 M_h g + K_h g, lumped mass,
+  right-preconditioned GMRES to a relative residual of 1e-8.
+value = distinct Toeplitz entries assembled per second of whole-step time.
+Component figures (assembly entries/s, Toeplitz-apply GB/s and GFLOP/s, GMRES
+time) are reported beside it.  Between timed steps a 256 MB buffer is written
+to flush L2 (outside the step's CUDA events).
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded random sample of the same entries (the oracle has no GPU code).
+Multi-GPU (torchrun, N > 1): every rank runs its own copy of the workload
+(independent problems, no collective on the data path; weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "assembly entries/s; Toeplitz matvec GB/s; GMRES time to 1e-8 res, mixed vs FP64"
+UNIT = "entries/s"
+WORKLOAD = "square256"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# FP64 pipe: 1.25 TFLOP/s nominal dense FP64 for GB300 (recipe table).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def _oracle_sample(n_entries, seed, rng_lags=None):
+    """Time the oracle on a bounded random sample of (op, lag, i, j) entries."""
+    import workloads as W
+    from oracle import assembly as OA
+    from oracle.geometry import BoundaryMesh
+    p = W.config(WORKLOAD)
+    om = BoundaryMesh(p.vertices, p.T, p.n_t, p.alpha)
+    rng = np.random.default_rng(seed)
+    per_op = n_entries // 3
+    t0 = time.perf_counter()
+    done = 0
+    for op, fn in (("V", OA.V_entries), ("K", OA.K_entries), ("D", OA.D_entries)):
+        lags = rng.integers(0, p.n_t, size=per_op)
+        I = rng.integers(0, p.n_x, size=per_op)
+        J = rng.integers(0, p.n_x, size=per_op)
+        for d in np.unique(lags):
+            sel = lags == d
+            fn(om, int(d), I[sel], J[sel])
+            done += int(sel.sum())
+    return done, time.perf_counter() - t0
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_entries = 96
+    for _ in range(args.warmup):
+        _oracle_sample(24, 1000)
+    times, counts = [], []
+    for k in range(args.steps):
+        c, t = _oracle_sample(n_entries, 2000 + k)
+        counts.append(c)
+        times.append(t)
+    value = sum(counts) / sum(times)
+    sample = ("%d random (op, lag, i, j) entries of %s per step, uniform over the 3 operators, lags "
+              "and index pairs; single numpy process" % (n_entries, WORKLOAD))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_x": 256, "n_t": 256, "alpha": 1.0,
+                                        "T": 1.0, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    from paper_1811_05224_gb300 import capi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = P.Context(local, stream)
+    lib = capi.load()
+    p = W.config(WORKLOAD)
+    mesh = P.Mesh(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    nt, nx = p.n_t, p.n_x
+    V = ctx.empty((nt, nx, nx))
+    K = ctx.empty((nt, nx, nx))
+    D = ctx.empty((nt, nx, nx))
+    awork = P.api.apply_workspace(ctx, nt, nx, 1)
+    swork = P.api.solve_workspace(ctx, nt, nx, 200)
+    w = ctx.empty((nt, nx))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    infos = []
+
+    def step(m, events=None):
+        e = [ev() for _ in range(5)] if events is None else events
+        e[0].record(stream)
+        P.assemble(ctx, m, "V", out=V)
+        P.assemble(ctx, m, "K", out=K)
+        P.assemble(ctx, m, "D", out=D)
+        e[1].record(stream)
+        g, f = P.rhs(ctx, m, K, p.y_star, work=awork)
+        L = P.lumped_mass(ctx, m)
+        e[2].record(stream)
+        _, info = P.solve(ctx, V, f, D, L, tol=1e-8, max_iter=500, restart=200, work=swork, out=w)
+        e[3].record(stream)
+        infos.append(info)
+        return e
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step(mesh)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = lib.stbem_launch_count()
+    step_events = []
+    barrier()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        step_events.append(step(mesh))
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = lib.stbem_launch_count() - n0
+    ck = clocks.stop()
+    ms = [e[0].elapsed_time(e[3]) for e in step_events]
+    ms_asm = [e[0].elapsed_time(e[1]) for e in step_events]
+    ms_solve = [e[2].elapsed_time(e[3]) for e in step_events]
+    ms_step = sum(ms) / len(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    entries = 3 * nt * nx * nx
+    value = world * entries / (ms_step * 1e-3)
+    asm_rate = entries / (statistics.mean(ms_asm) * 1e-3)
+
+    # Toeplitz apply (V, FP64): kernel time with CUDA events on the launch stream
+    x = torch.randn(nt, nx, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        P.apply(ctx, V, x, work=awork, out=y)
+    reps = 10
+    a0, a1 = ev(), ev()
+    flush.zero_()
+    a0.record(stream)
+    for _ in range(reps):
+        P.apply(ctx, V, x, work=awork, out=y)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_apply = a0.elapsed_time(a1) / reps
+    apply_flops = 2.0 * nx * nx * nt * (nt + 1) / 2
+    apply_bytes = nt * nx * nx * 8 + 2 * nt * nx * 8
+    # per-operator assembly time (separate events, same kernels)
+    op_ms = {}
+    for op, buf in (("V", V), ("K", K), ("D", D)):
+        b0, b1 = ev(), ev()
+        b0.record(stream)
+        P.assemble(ctx, mesh, op, out=buf)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        op_ms[op] = b0.elapsed_time(b1)
+
+    # end to end through the public API with host buffers: vertices in, w out
+    verts = np.ascontiguousarray(p.vertices)
+    w_host = torch.empty((nt, nx), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        m2 = P.Mesh(ctx, verts, p.T, p.n_t, p.alpha)
+        step(m2)
+        w_host.copy_(w, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        m2.close()
+    e2e_val = world * entries / (statistics.mean(e2e_ms) * 1e-3)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return 0
+    # oracle CPU baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        c, t = _oracle_sample(96, 12345)
+        cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "96 random (op, lag, i, j) entries of square256, single numpy process"}
+    # dominant kernel by time: D assembly (FP64 ALU); report the FP64 product
+    # roofline for the Toeplitz apply kernel as well
+    dominant = max(op_ms, key=op_ms.get)
+    flops_entry = _assembly_flops_per_entry(dominant, nt)
+    asm_tflops = flops_entry * nt * nx * nx / (op_ms[dominant] * 1e-3) / 1e12
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_x": nx, "n_t": nt, "alpha": p.alpha, "T": p.T,
+                   "y_star": list(p.y_star), "precision": "fp64 assembly + fp64 GMRES",
+                   "l2": "256 MB buffer written between steps"},
+        "components": {
+            "assembly_entries_per_s": asm_rate,
+            "assembly_ms": {k: round(v, 3) for k, v in op_ms.items()},
+            "dense_equivalent_entries_per_s": asm_rate * (nt + 1) / 2,
+            "apply_f64_ms": ms_apply, "apply_f64_gbs": apply_bytes / (ms_apply * 1e-3) / 1e9,
+            "apply_f64_gflops": apply_flops / (ms_apply * 1e-3) / 1e9,
+            "gmres_ms": statistics.mean(ms_solve), "gmres_iterations": last["iterations"],
+            "gmres_rel_residual": last["rel_residual"],
+        },
+        "roofline": {"kernel": "assemble %s lags>=2 (k_lag2)" % dominant, "bound": "alu",
+                     "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "note": "FP64 peak: nominal 1.25 TFLOP/s (recipe table); algorithmic FP64 "
+                             "flops counted per entry from the discretisation rule"},
+        "apply_roofline": {"bound": "alu", "achieved": apply_flops / (ms_apply * 1e-3) / 1e12,
+                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": apply_flops / (ms_apply * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(verts.nbytes),
+                "d2h_bytes_per_step": int(nt * nx * 8)},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+    return 0
+
+
+def _assembly_flops_per_entry(op, nt):
+    """FP64 flops per distinct entry of the lags >= 2 kernel, from the rule.
+
+    Per time-kernel evaluation in the Peano branch (the one the large-lag
+    entries take): one division c/s, one exp, two multiplies and one add for
+    the kernel, one FMA into the sum; exp is counted as 20 FP64 flops and a
+    division as 10 (their polynomial and Newton-iteration costs).  Per entry:
+    (space points) x (Peano nodes of the two intervals) evaluations, summed
+    over lags 2..nt-1 and divided by the lag count.  D has 16 half-segment
+    pairs per entry and two kernels per evaluation sharing the exp."""
+    def space_order(d):       # Gauss points per piece at lag d >= 2
+        return 4 if d >= 32 else (6 if d >= 8 else 8)
+
+    def peano_order(k):       # Gauss nodes on time interval k
+        return 6 if k >= 32 else (8 if k >= 2 else 16)
+
+    per_eval = 20 + 10 + 5 + 2
+    tot = 0.0
+    for d in range(2, nt):
+        n = space_order(d)
+        nodes = peano_order(d - 1) + peano_order(d)
+        ev = n * n * nodes
+        if op == "K":
+            ev *= 2
+        if op == "D":
+            ev *= 16
+            per_d = per_eval + 8
+        else:
+            per_d = per_eval
+        tot += ev * per_d
+    return tot / max(nt - 2, 1) * (nt - 2) / nt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

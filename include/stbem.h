@@ -1,0 +1,159 @@
+/*
+ * stbem.h -- C ABI of the GB300 space-time boundary element library for the
+ * 2D heat equation  alpha d_t u - Laplace u = 0  (paper: Section 1, eq. (1)).
+ *
+ * The library covers the data-parallel hot path of the preconditioned
+ * space-time Galerkin BEM: assembly of the single layer V_h, double layer K_h
+ * and hypersingular D_h matrices on a polygon x uniform time grid
+ * (Section 1 eq. (4); Section 2 Theorem), their block-lower-triangular,
+ * block-Toeplitz-in-time products (Section 3), the right-hand side
+ * (1/2 M_h + K_h) g of eq. (4), and right-preconditioned GMRES with the
+ * operator preconditioner C_V^{-1} = M_h^{-1} D_h M_h^{-T} (Section 2, with
+ * the lumped mass of Section 4).
+ *
+ * Conventions (every call):
+ *  - Return value: 0 (STBEM_OK) or a negative STBEM_ERR_* code.  No exception
+ *    or abort crosses the ABI; stbem_last_error() returns a message for the
+ *    last failing call on that context.
+ *  - Ownership: every array argument named dev_* is a DEVICE pointer owned by
+ *    the caller (e.g. a torch tensor); host_* arrays are host pointers, read
+ *    during the call only.  The library allocates only its opaque handles
+ *    (a context and meshes, which keep a few KB of geometry on the device).
+ *  - Streams: all device work is enqueued on the stream given to
+ *    stbem_create() and is asynchronous unless a call says otherwise.
+ *  - Layouts: time-major unknowns.  A Toeplitz operator is stored as lag
+ *    blocks A[d][i][j], d = 0..n_t-1, row-major, d slowest; it represents the
+ *    block matrix whose block (m, n) is A[m-n] for m >= n and 0 otherwise.
+ *    Vectors are x[n][j] (n_t x n_cols), batches x[b][n][j].
+ *  - Index conventions (geometry): vertices x_0..x_{N-1} counter-clockwise,
+ *    segment i = [x_i, x_{i+1 mod N}], outward normal (t_y, -t_x).
+ */
+#ifndef STBEM_H
+#define STBEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define STBEM_OK 0
+#define STBEM_ERR_ARG (-1)       /* invalid argument (size, pointer, mesh)   */
+#define STBEM_ERR_CUDA (-2)      /* a CUDA runtime call failed               */
+#define STBEM_ERR_NOMEM (-3)     /* caller workspace too small               */
+#define STBEM_ERR_NOCONV (-4)    /* iteration cap reached before tolerance   */
+#define STBEM_ERR_BREAKDOWN (-5) /* GMRES breakdown (zero Krylov vector)     */
+#define STBEM_ERR_NAN (-6)       /* NaN or Inf met in a residual             */
+
+/* operators */
+#define STBEM_OP_V 0 /* single layer  <V phi0_k, phi0_l>,   N_x x N_x blocks */
+#define STBEM_OP_K 1 /* double layer  <K phi10_p, phi0_i>,  N_x x N_x blocks */
+#define STBEM_OP_D 2 /* hypersingular <D psi_k, psi_l>,     N_x x N_x blocks */
+
+/* precisions of stored operators */
+#define STBEM_F64 0
+#define STBEM_F32 1
+
+typedef struct stbem_ctx stbem_ctx;
+typedef struct stbem_mesh stbem_mesh;
+
+/* Create a context on CUDA device `device`; `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Uploads the quadrature tables of the
+ * discretisation rule to the device.  Errors: STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_create(stbem_ctx** out, int device, void* stream);
+void stbem_destroy(stbem_ctx* ctx);
+/* Message of the last failing call on ctx (never NULL). */
+const char* stbem_last_error(const stbem_ctx* ctx);
+/* Library version string. */
+const char* stbem_version(void);
+/* Number of CUDA kernels this library has launched in the process (all
+ * contexts); a diagnostic counter with no counterpart in the paper. */
+unsigned long long stbem_launch_count(void);
+
+/* Boundary mesh Gamma_h x I_h (Section 1: tensor-product decomposition of
+ * Sigma).  host_xy: 2*n_x doubles (x_0, y_0, x_1, y_1, ...), a closed
+ * polygon in counter-clockwise order; n_t uniform steps of length T/n_t; alpha
+ * the heat capacity constant.  Errors: STBEM_ERR_ARG if n_x < 3, n_t < 1,
+ * T <= 0, alpha <= 0, a segment has zero length or the vertices are clockwise. */
+int stbem_mesh_create(stbem_ctx* ctx, const double* host_xy, int n_x, double T,
+                      int n_t, double alpha, stbem_mesh** out);
+void stbem_mesh_destroy(stbem_mesh* mesh);
+
+/* Bytes of a stored operator: n_t * n_x * n_x * sizeof(element). */
+int stbem_op_bytes(const stbem_mesh* mesh, int op, int prec, size_t* bytes);
+
+/* Assemble the lag blocks of op (STBEM_OP_V / K / D) into dev_out
+ * (n_t x n_x x n_x, precision prec).  Entries follow the Galerkin
+ * definitions of Section 1 eq. (4) (V, K) and the integrated-by-parts form of
+ * the hypersingular operator (Section 2, citing Costabel Thm 6.1) on the dual
+ * space Y_h (Section 2), integrated by the discretisation rule documented in
+ * the repository (Gauss-Legendre in space, graded/Duffy rules for coincident
+ * and touching pieces at lags 0-1, closed-form or Peano time integrals).
+ * STBEM_F32 stores the FP64-computed entries rounded to float.
+ * Errors: STBEM_ERR_ARG (bad op/prec/NULL), STBEM_ERR_CUDA. */
+int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec,
+                   void* dev_out);
+
+/* Block-Toeplitz product (Section 3 block structure).
+ *   transpose = 0:  y[b][m][i] = sum_{d=0}^{m} sum_j A[d][i][j] x[b][m-d][j]
+ *   transpose = 1:  y[b][n][j] = sum_{d=0}^{n_t-1-n} sum_i A[d][i][j] x[b][n+d][i]
+ * A has n_t lag blocks of n_x x n_x in precision prec (F64 or F32); x and y
+ * are FP64, n_rhs x n_t x n_x, and must not overlap.  Accumulation is in the
+ * precision of A (FP64 for F64, FP32 for F32).  dev_work must hold
+ * stbem_apply_workspace_bytes() bytes (partial sums over lag chunks, so the
+ * result is deterministic).  Errors: STBEM_ERR_ARG, STBEM_ERR_NOMEM. */
+int stbem_apply_workspace_bytes(int n_t, int n_x, int n_rhs, int prec, size_t* bytes);
+int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
+                const void* dev_A, int n_rhs, const double* dev_x, double* dev_y,
+                void* dev_work, size_t work_bytes);
+
+/* Right-hand side of eq. (4) for u_0 = 0 and the Dirichlet datum
+ * g = U*(x - y*, t) (y* outside the domain):
+ *   dev_g[n][p] = time average of g at vertex p over tau_n,
+ *   dev_f       = 1/2 M_h g + K_h g   (M_h of Section 1, K_h given as dev_K).
+ * dev_K: the assembled K (FP64); dev_g, dev_f: n_t x n_x doubles; dev_work as
+ * for stbem_apply with prec F64, n_rhs = 1. */
+int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* mesh, const double* dev_K,
+              double y_star_x, double y_star_y, double* dev_g, double* dev_f,
+              void* dev_work, size_t work_bytes);
+
+/* Lumped dual mass (Section 4): dev_L[l] = ht (h_{l-1} + 2 h_l + h_{l+1}) / 4,
+ * the row sums of M_h[l,k] = <phi0_k, psi_l> (Section 2). n_x doubles. */
+int stbem_lumped_mass(stbem_ctx* ctx, const stbem_mesh* mesh, double* dev_L);
+
+/* GMRES options and result. */
+typedef struct stbem_solve_opts {
+  double tol;       /* stop at ||f - V w|| / ||f|| <= tol (paper: 1e-8)     */
+  int max_iter;     /* total iteration cap                                 */
+  int restart;      /* Krylov dimension before restart                     */
+  int precondition; /* 1: right preconditioning by C_V^{-1} (needs D, L)   */
+} stbem_solve_opts;
+
+typedef struct stbem_solve_info {
+  int iterations;     /* GMRES iterations performed                       */
+  int status;         /* STBEM_OK, STBEM_ERR_NOCONV, _BREAKDOWN or _NAN   */
+  double rel_residual;/* final true relative residual ||f - V w|| / ||f|| */
+} stbem_solve_info;
+
+/* Workspace for stbem_solve: Krylov basis (restart+1 vectors), preconditioned
+ * basis, temporaries and product partial sums. */
+int stbem_solve_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes);
+
+/* Solve V_h w = f (eq. (4)) by right-preconditioned GMRES (Section 2),
+ * x0 = 0, classical Gram-Schmidt with reorthogonalisation in FP64, Givens
+ * rotations; the residual tested is the true residual, recomputed at every
+ * restart and at the end.  dev_V, dev_D: assembled operators (prec vprec, both
+ * the same precision; dev_D and dev_L may be NULL when opts->precondition is
+ * 0); dev_L: lumped dual mass (n_x doubles); dev_f, dev_w: n_t x n_x doubles.
+ * Blocks the host (reads a residual each iteration).  Returns STBEM_OK,
+ * STBEM_ERR_NOCONV, _BREAKDOWN or _NAN (also stored in info->status). */
+int stbem_solve(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void* dev_V,
+                const void* dev_D, const double* dev_L, const double* dev_f,
+                double* dev_w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                void* dev_work, size_t work_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STBEM_H */

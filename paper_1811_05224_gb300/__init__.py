@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) space-time BEM for the 2D heat equation.
+
+The hot path of the preconditioned space-time Galerkin BEM (arXiv:1811.05224):
+assembly of V_h, K_h, D_h and block-Toeplitz products inside preconditioned
+GMRES, in hand-written CUDA behind the C ABI of include/stbem.h.
+"""
+from .api import Context, Mesh, apply, assemble, lumped_mass, rhs, solve  # noqa: F401
+
+__all__ = ["Context", "Mesh", "assemble", "apply", "rhs", "lumped_mass", "solve"]

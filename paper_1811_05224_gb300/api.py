@@ -1,0 +1,156 @@
+"""Torch-facing wrappers of the C ABI (argument marshalling only).
+
+PyTorch provides device memory (outputs and workspaces are torch tensors) and
+the CUDA stream; every computation runs in libstbem's kernels.  Nothing here
+falls back to the CPU: without a CUDA device or the built library the calls
+raise.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+
+OPS = {"V": capi.OP_V, "K": capi.OP_K, "D": capi.OP_D}
+PRECS = {"f64": capi.F64, "f32": capi.F32}
+DTYPES = {capi.F64: torch.float64, capi.F32: torch.float32}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Context:
+    """A library context on one CUDA device, bound to a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("stbem needs a CUDA device (no CPU fallback)")
+        self.lib = capi.load()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        code = self.lib.stbem_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
+        if code != capi.STBEM_OK:
+            raise capi.StbemError(code, "stbem_create failed on device %d" % device)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stbem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, code):
+        return capi.check(self.h, code)
+
+    def empty(self, shape, dtype=torch.float64):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+
+class Mesh:
+    """Polygon boundary mesh x uniform time grid (vertices counter-clockwise)."""
+
+    def __init__(self, ctx: Context, vertices, T: float, n_t: int, alpha: float):
+        xy = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
+        self.ctx = ctx
+        self.n_x = xy.size // 2
+        self.n_t = int(n_t)
+        self.T = float(T)
+        self.alpha = float(alpha)
+        self.vertices = xy.reshape(-1, 2).copy()
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.stbem_mesh_create(ctx.h, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            self.n_x, self.T, self.n_t, self.alpha, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.stbem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def assemble(ctx: Context, mesh: Mesh, op: str, prec: str = "f64", out=None):
+    """Lag blocks A[d][i][j] of op in {'V','K','D'} (n_t x n_x x n_x)."""
+    p = PRECS[prec]
+    if out is None:
+        out = ctx.empty((mesh.n_t, mesh.n_x, mesh.n_x), DTYPES[p])
+    ctx.check(ctx.lib.stbem_assemble(ctx.h, mesh.h, OPS[op], p, _ptr(out)))
+    return out
+
+
+def apply_workspace(ctx: Context, n_t: int, n_x: int, n_rhs: int = 1, prec: str = "f64"):
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_apply_workspace_bytes(n_t, n_x, n_rhs, PRECS[prec], ctypes.byref(nb)))
+    return torch.empty(max(nb.value, 8), dtype=torch.uint8, device=ctx.device)
+
+
+def apply(ctx: Context, A, x, transpose: bool = False, work=None, out=None):
+    """Block-Toeplitz product with the lag blocks A (x: [n_rhs,] n_t x n_x, FP64)."""
+    prec = capi.F64 if A.dtype == torch.float64 else capi.F32
+    n_t, n_x = A.shape[0], A.shape[1]
+    xb = x if x.dim() == 3 else x.unsqueeze(0)
+    n_rhs = xb.shape[0]
+    if out is None:
+        out = torch.empty_like(xb)
+    if work is None:
+        work = apply_workspace(ctx, n_t, n_x, n_rhs, "f64" if prec == capi.F64 else "f32")
+    ctx.check(ctx.lib.stbem_apply(ctx.h, prec, int(transpose), n_t, n_x, _ptr(A), n_rhs, _ptr(xb),
+                                  _ptr(out), _ptr(work), work.numel()))
+    return out if x.dim() == 3 else out[0]
+
+
+def rhs(ctx: Context, mesh: Mesh, K, y_star, work=None):
+    """(g, f): vertex time averages of g = U*(x - y*, t) and f = 1/2 M_h g + K_h g."""
+    g = ctx.empty((mesh.n_t, mesh.n_x))
+    f = ctx.empty((mesh.n_t, mesh.n_x))
+    if work is None:
+        work = apply_workspace(ctx, mesh.n_t, mesh.n_x, 1)
+    ctx.check(ctx.lib.stbem_rhs(ctx.h, mesh.h, _ptr(K), float(y_star[0]), float(y_star[1]), _ptr(g),
+                                _ptr(f), _ptr(work), work.numel()))
+    return g, f
+
+
+def lumped_mass(ctx: Context, mesh: Mesh):
+    L = ctx.empty((mesh.n_x,))
+    ctx.check(ctx.lib.stbem_lumped_mass(ctx.h, mesh.h, _ptr(L)))
+    return L
+
+
+def solve_workspace(ctx: Context, n_t: int, n_x: int, restart: int):
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_solve_workspace_bytes(n_t, n_x, restart, ctypes.byref(nb)))
+    return torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+
+
+def solve(ctx: Context, V, f, D=None, L=None, tol: float = 1e-8, max_iter: int = 500,
+          restart: int = 200, work=None, out=None, raise_on_fail: bool = True):
+    """Right-preconditioned GMRES for V_h w = f; returns (w, info dict)."""
+    n_t, n_x = V.shape[0], V.shape[1]
+    prec = capi.F64 if V.dtype == torch.float64 else capi.F32
+    if D is not None and D.dtype != V.dtype:
+        raise ValueError("V and D must share a precision")
+    opts = capi.SolveOpts(tol, max_iter, restart, int(D is not None))
+    info = capi.SolveInfo()
+    if out is None:
+        out = ctx.empty((n_t, n_x))
+    if work is None:
+        work = solve_workspace(ctx, n_t, n_x, restart)
+    code = ctx.lib.stbem_solve(ctx.h, n_t, n_x, prec, _ptr(V), _ptr(D), _ptr(L), _ptr(f), _ptr(out),
+                               ctypes.byref(opts), ctypes.byref(info), _ptr(work), work.numel())
+    res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
+    if code != capi.STBEM_OK and raise_on_fail:
+        ctx.check(code)
+    return out, res

@@ -1,0 +1,93 @@
+"""ctypes binding of libstbem (include/stbem.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch is the memory
+manager); their ``data_ptr()`` is passed through.  There is no CPU fallback:
+``load()`` raises if the shared library is missing or cannot be opened.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libstbem.so")
+
+STBEM_OK = 0
+STBEM_ERR_ARG = -1
+STBEM_ERR_CUDA = -2
+STBEM_ERR_NOMEM = -3
+STBEM_ERR_NOCONV = -4
+STBEM_ERR_BREAKDOWN = -5
+STBEM_ERR_NAN = -6
+OP_V, OP_K, OP_D = 0, 1, 2
+F64, F32 = 0, 1
+
+ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOMEM", -4: "ERR_NOCONV",
+             -5: "ERR_BREAKDOWN", -6: "ERR_NAN"}
+
+EXPORTS = [
+    "stbem_version", "stbem_launch_count", "stbem_create", "stbem_destroy", "stbem_last_error", "stbem_mesh_create",
+    "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_apply_workspace_bytes",
+    "stbem_apply", "stbem_rhs", "stbem_lumped_mass", "stbem_solve_workspace_bytes", "stbem_solve",
+]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
+                ("precondition", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+class StbemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Open libstbem.so (built by ``paper_1811_05224_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libstbem.so not found at %s: run paper_1811_05224_gb300.build.build() "
+                           "(the CUDA library is required; there is no CPU fallback)" % path)
+    L = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER
+    L.stbem_version.restype = ctypes.c_char_p
+    L.stbem_launch_count.restype = ctypes.c_ulonglong
+    L.stbem_create.argtypes = [P(vp), i, vp]
+    L.stbem_destroy.argtypes = [vp]
+    L.stbem_destroy.restype = None
+    L.stbem_last_error.argtypes = [vp]
+    L.stbem_last_error.restype = ctypes.c_char_p
+    L.stbem_mesh_create.argtypes = [vp, P(d), i, d, i, d, P(vp)]
+    L.stbem_mesh_destroy.argtypes = [vp]
+    L.stbem_mesh_destroy.restype = None
+    L.stbem_op_bytes.argtypes = [vp, i, i, P(sz)]
+    L.stbem_assemble.argtypes = [vp, vp, i, i, vp]
+    L.stbem_apply_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_apply.argtypes = [vp, i, i, i, i, vp, i, vp, vp, vp, sz]
+    L.stbem_rhs.argtypes = [vp, vp, vp, d, d, vp, vp, vp, sz]
+    L.stbem_lumped_mass.argtypes = [vp, vp, vp]
+    L.stbem_solve_workspace_bytes.argtypes = [i, i, i, P(sz)]
+    L.stbem_solve.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
+    for name in EXPORTS:
+        if name not in ("stbem_version", "stbem_launch_count", "stbem_destroy", "stbem_mesh_destroy", "stbem_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def check(ctx, code):
+    if code != STBEM_OK:
+        msg = load().stbem_last_error(ctx).decode() if ctx else ""
+        raise StbemError(code, msg)
+    return code

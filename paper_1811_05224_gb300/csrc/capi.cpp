@@ -1,0 +1,439 @@
+// C ABI of the library (declared in include/stbem.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "assemble.h"
+#include "stbem.h"
+#include "toeplitz.h"
+#include "vec.h"
+
+struct stbem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+struct stbem_mesh {
+  int device = 0;
+  int N = 0, n_t = 0;
+  double T = 0, ht = 0, alpha = 0;
+  std::vector<double> h;     // segment lengths (host copy)
+  double* dbuf = nullptr;    // device geometry
+  int* ibuf = nullptr;
+  stbem::DevMesh dev{};
+};
+
+namespace {
+
+int fail(stbem_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(stbem_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, STBEM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, call, where)                      \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+size_t elt_size(int prec) { return prec == STBEM_F64 ? 8 : 4; }
+
+}  // namespace
+
+extern "C" {
+
+const char* stbem_version(void) { return "stbem 0.1 (sm_103a)"; }
+
+unsigned long long stbem_launch_count(void) { return stbem::launch_count(); }
+
+int stbem_create(stbem_ctx** out, int device, void* stream) {
+  if (!out) return STBEM_ERR_ARG;
+  *out = nullptr;
+  stbem_ctx* ctx = new stbem_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return STBEM_ERR_CUDA;
+  }
+  stbem::RuleTables t;
+  stbem::build_rule_tables(&t);
+  e = stbem::upload_rule_tables(t, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return STBEM_ERR_CUDA;
+  }
+  *out = ctx;
+  return STBEM_OK;
+}
+
+void stbem_destroy(stbem_ctx* ctx) { delete ctx; }
+
+const char* stbem_last_error(const stbem_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n_t, double alpha,
+                      stbem_mesh** out) {
+  if (!ctx || !out) return STBEM_ERR_ARG;
+  *out = nullptr;
+  if (!xy) return fail(ctx, STBEM_ERR_ARG, "mesh: NULL vertex array");
+  if (n_x < 3) return fail(ctx, STBEM_ERR_ARG, "mesh: need n_x >= 3 (got %d)", n_x);
+  if (n_t < 1) return fail(ctx, STBEM_ERR_ARG, "mesh: need n_t >= 1 (got %d)", n_t);
+  if (!(T > 0) || !std::isfinite(T)) return fail(ctx, STBEM_ERR_ARG, "mesh: need T > 0");
+  if (!(alpha > 0) || !std::isfinite(alpha)) return fail(ctx, STBEM_ERR_ARG, "mesh: need alpha > 0");
+  const int N = n_x;
+  std::vector<double> ax(N), ay(N), bx(N), by(N), h(N), nx(N), ny(N);
+  double area2 = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const int k = (i + 1) % N;
+    ax[i] = xy[2 * i];
+    ay[i] = xy[2 * i + 1];
+    bx[i] = xy[2 * k];
+    by[i] = xy[2 * k + 1];
+    if (!std::isfinite(ax[i]) || !std::isfinite(ay[i])) return fail(ctx, STBEM_ERR_ARG, "mesh: non-finite vertex %d", i);
+    const double ex = bx[i] - ax[i], ey = by[i] - ay[i];
+    h[i] = std::sqrt(ex * ex + ey * ey);
+    if (!(h[i] > 0)) return fail(ctx, STBEM_ERR_ARG, "mesh: zero-length segment %d", i);
+    const double tx = ex / h[i], ty = ey / h[i];
+    nx[i] = ty;
+    ny[i] = -tx;
+    area2 += ax[i] * by[i] - bx[i] * ay[i];
+  }
+  if (!(area2 > 0)) return fail(ctx, STBEM_ERR_ARG, "mesh: vertices must be counter-clockwise");
+  const int M2 = 2 * N;
+  std::vector<double> hx0(M2), hy0(M2), hx1(M2), hy1(M2), hl(M2), hnx(M2), hny(M2);
+  for (int i = 0; i < N; ++i) {
+    const double mx = 0.5 * (ax[i] + bx[i]), my = 0.5 * (ay[i] + by[i]);
+    hx0[2 * i] = ax[i]; hy0[2 * i] = ay[i]; hx1[2 * i] = mx; hy1[2 * i] = my;
+    hx0[2 * i + 1] = mx; hy0[2 * i + 1] = my; hx1[2 * i + 1] = bx[i]; hy1[2 * i + 1] = by[i];
+    hl[2 * i] = hl[2 * i + 1] = 0.5 * h[i];
+    hnx[2 * i] = hnx[2 * i + 1] = nx[i];
+    hny[2 * i] = hny[2 * i + 1] = ny[i];
+  }
+  std::vector<int> dp(4 * N);
+  std::vector<double> dv0(4 * N), dv1(4 * N), dc(4 * N);
+  for (int l = 0; l < N; ++l) {
+    const double hm = h[(l - 1 + N) % N], h0 = h[l], hp = h[(l + 1) % N];
+    const double al = hm / (hm + h0), bl = hp / (h0 + hp);
+    const double up = 2.0 / (hm + h0), dn = -2.0 / (h0 + hp);
+    const int p[4] = {(2 * l - 1 + M2) % M2, (2 * l) % M2, (2 * l + 1) % M2, (2 * l + 2) % M2};
+    const double v0[4] = {0.0, al, 1.0, bl}, v1[4] = {al, 1.0, bl, 0.0}, c[4] = {up, up, dn, dn};
+    for (int k = 0; k < 4; ++k) {
+      dp[4 * l + k] = p[k];
+      dv0[4 * l + k] = v0[k];
+      dv1[4 * l + k] = v1[k];
+      dc[4 * l + k] = c[k];
+    }
+  }
+  // pack: seg 7N | half 7*2N | dual 3*4N | vertices 2N
+  std::vector<double> host;
+  host.reserve(7 * N + 14 * N + 12 * N + 2 * N);
+  for (auto* v : {&ax, &ay, &bx, &by, &h, &nx, &ny}) host.insert(host.end(), v->begin(), v->end());
+  for (auto* v : {&hx0, &hy0, &hx1, &hy1, &hl, &hnx, &hny}) host.insert(host.end(), v->begin(), v->end());
+  for (auto* v : {&dv0, &dv1, &dc}) host.insert(host.end(), v->begin(), v->end());
+  host.insert(host.end(), ax.begin(), ax.end());
+  host.insert(host.end(), ay.begin(), ay.end());
+
+  stbem_mesh* m = new stbem_mesh();
+  m->device = ctx->device;
+  m->N = N;
+  m->n_t = n_t;
+  m->T = T;
+  m->ht = T / n_t;
+  m->alpha = alpha;
+  m->h = h;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&m->dbuf, host.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->ibuf, dp.size() * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->dbuf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->ibuf, dp.data(), dp.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    if (m->dbuf) cudaFree(m->dbuf);
+    if (m->ibuf) cudaFree(m->ibuf);
+    delete m;
+    return cuda_fail(ctx, e, "mesh upload");
+  }
+  const double* b = m->dbuf;
+  stbem::DevMesh& D = m->dev;
+  D.N = N; D.n_t = n_t; D.ht = m->ht; D.alpha = alpha;
+  D.sx0 = b; D.sy0 = b + N; D.sx1 = b + 2 * N; D.sy1 = b + 3 * N; D.slen = b + 4 * N; D.snx = b + 5 * N; D.sny = b + 6 * N;
+  b += 7 * N;
+  D.hx0 = b; D.hy0 = b + M2; D.hx1 = b + 2 * M2; D.hy1 = b + 3 * M2; D.hlen = b + 4 * M2; D.hnx = b + 5 * M2; D.hny = b + 6 * M2;
+  b += 7 * M2;
+  D.dv0 = b; D.dv1 = b + 4 * N; D.dcurl = b + 8 * N;
+  b += 12 * N;
+  D.vx = b; D.vy = b + N;
+  D.dpiece = m->ibuf;
+  *out = m;
+  return STBEM_OK;
+}
+
+void stbem_mesh_destroy(stbem_mesh* m) {
+  if (!m) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(m->device);
+  if (m->dbuf) cudaFree(m->dbuf);
+  if (m->ibuf) cudaFree(m->ibuf);
+  cudaSetDevice(prev);
+  delete m;
+}
+
+int stbem_op_bytes(const stbem_mesh* m, int op, int prec, size_t* bytes) {
+  if (!m || !bytes || op < 0 || op > 2 || (prec != STBEM_F64 && prec != STBEM_F32)) return STBEM_ERR_ARG;
+  *bytes = (size_t)m->n_t * m->N * m->N * elt_size(prec);
+  return STBEM_OK;
+}
+
+int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, void* out) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !out) return fail(ctx, STBEM_ERR_ARG, "assemble: NULL mesh or output");
+  if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown operator %d", op);
+  if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown precision %d", prec);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble: set device");
+  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, out, ctx->stream), "assemble: launch");
+  return STBEM_OK;
+}
+
+int stbem_apply_workspace_bytes(int n_t, int n_x, int n_rhs, int prec, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || (prec != STBEM_F64 && prec != STBEM_F32)) return STBEM_ERR_ARG;
+  *bytes = stbem::apply_workspace_bytes(n_t, n_x, n_rhs);
+  return STBEM_OK;
+}
+
+int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x, const void* A, int n_rhs,
+                const double* x, double* y, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A || !x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "apply: NULL pointer");
+  if (n_t < 1 || n_x < 1 || n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "apply: bad sizes");
+  if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "apply: bad precision");
+  if ((const void*)x == (const void*)y) return fail(ctx, STBEM_ERR_ARG, "apply: x and y overlap");
+  const size_t need = stbem::apply_workspace_bytes(n_t, n_x, n_rhs);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "apply: workspace %zu < %zu bytes", work_bytes, need);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply: set device");
+  CUDA_TRY(ctx, stbem::apply_launch(prec, transpose != 0, n_t, n_x, A, n_rhs, x, y, work, ctx->stream), "apply");
+  return STBEM_OK;
+}
+
+int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, double* g,
+              double* f, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !K || !g || !f || !work) return fail(ctx, STBEM_ERR_ARG, "rhs: NULL pointer");
+  const size_t need = stbem::apply_workspace_bytes(m->n_t, m->N, 1);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "rhs: workspace %zu < %zu bytes", work_bytes, need);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "rhs: set device");
+  CUDA_TRY(ctx, stbem::rhs_g_launch(m->dev, ysx, ysy, g, ctx->stream), "rhs: g");
+  CUDA_TRY(ctx, stbem::apply_launch(STBEM_F64, false, m->n_t, m->N, K, 1, g, f, work, ctx->stream), "rhs: K g");
+  CUDA_TRY(ctx, stbem::half_mass_add_launch(m->dev, g, f, ctx->stream), "rhs: mass");
+  return STBEM_OK;
+}
+
+int stbem_lumped_mass(stbem_ctx* ctx, const stbem_mesh* m, double* L) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !L) return fail(ctx, STBEM_ERR_ARG, "lumped: NULL pointer");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "lumped: set device");
+  CUDA_TRY(ctx, stbem::lumped_mass_launch(m->dev, L, ctx->stream), "lumped");
+  return STBEM_OK;
+}
+
+// ---------------------------------------------------------------- GMRES ------
+namespace {
+
+struct SolveWork {
+  double *Q, *z, *v, *r, *u, *h;
+  void* apply;
+  size_t apply_bytes;
+};
+
+size_t solve_bytes(int nt, int nx, int restart) {
+  const size_t N = (size_t)nt * nx;
+  const size_t hn = (size_t)(restart + 2) * 65;
+  return ((size_t)(restart + 1) * N + 4 * N + hn) * sizeof(double) + stbem::apply_workspace_bytes(nt, nx, 1);
+}
+
+bool carve(void* base, size_t bytes, int nt, int nx, int restart, SolveWork* w) {
+  const size_t N = (size_t)nt * nx;
+  double* p = static_cast<double*>(base);
+  w->Q = p; p += (size_t)(restart + 1) * N;
+  w->z = p; p += N;
+  w->v = p; p += N;
+  w->r = p; p += N;
+  w->u = p; p += N;
+  w->h = p; p += (size_t)(restart + 2) * 65;
+  w->apply = p;
+  w->apply_bytes = stbem::apply_workspace_bytes(nt, nx, 1);
+  return (size_t)((char*)p - (char*)base) + w->apply_bytes <= bytes;
+}
+
+}  // namespace
+
+int stbem_solve_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || restart < 1) return STBEM_ERR_ARG;
+  *bytes = solve_bytes(n_t, n_x, restart);
+  return STBEM_OK;
+}
+
+int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const void* D, const double* L,
+                const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!V || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve: NULL pointer");
+  if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve: bad sizes");
+  if (vprec != STBEM_F64 && vprec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "solve: bad precision");
+  const int restart = opts->restart, maxit = opts->max_iter;
+  if (restart < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "solve: bad options");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!D || !L)) return fail(ctx, STBEM_ERR_ARG, "solve: preconditioner needs D and L");
+  SolveWork W;
+  if (!carve(work, work_bytes, nt, nx, restart, &W))
+    return fail(ctx, STBEM_ERR_NOMEM, "solve: workspace %zu < %zu bytes", work_bytes, solve_bytes(nt, nx, restart));
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve: set device");
+  cudaStream_t s = ctx->stream;
+  const size_t N = (size_t)nt * nx;
+  info->iterations = 0;
+  info->status = STBEM_OK;
+  info->rel_residual = 0.0;
+
+  auto applyV = [&](const double* x, double* y) {
+    return stbem::apply_launch(vprec, false, nt, nx, V, 1, x, y, W.apply, s);
+  };
+  // right preconditioner: y = L^{-1} D L^{-1} x (or y = x)
+  auto applyP = [&](const double* x, double* y) -> cudaError_t {
+    if (!prec) return cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = stbem::diag_div_launch(x, L, W.u, nt, nx, s);
+    if (e != cudaSuccess) return e;
+    e = stbem::apply_launch(vprec, false, nt, nx, D, 1, W.u, y, W.apply, s);
+    if (e != cudaSuccess) return e;
+    return stbem::diag_div_launch(y, L, y, nt, nx, s);
+  };
+  auto norm = [&](const double* x, double* out) -> cudaError_t {
+    cudaError_t e = stbem::dots_launch(x, 1, x, N, W.h, s);
+    if (e != cudaSuccess) return e;
+    double v;
+    e = cudaMemcpyAsync(&v, W.h, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *out = std::sqrt(v);
+    return e;
+  };
+
+  double nf;
+  CUDA_TRY(ctx, norm(f, &nf), "solve: norm f");
+  CUDA_TRY(ctx, cudaMemsetAsync(w, 0, N * sizeof(double), s), "solve: zero w");
+  if (!std::isfinite(nf)) {
+    info->status = STBEM_ERR_NAN;
+    return fail(ctx, STBEM_ERR_NAN, "solve: right-hand side is not finite");
+  }
+  if (nf == 0.0) return STBEM_OK;
+
+  std::vector<double> H((size_t)(restart + 1) * restart, 0.0), cs(restart), sn(restart), g(restart + 1);
+  std::vector<double> hcol(restart + 2), h2(restart + 2);
+  int iters = 0;
+  double relres = 1.0;
+  int status = STBEM_OK;
+  bool first = true;
+  while (true) {
+    // true residual r = f - V w
+    if (first) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(W.r, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "solve: r");
+    } else {
+      CUDA_TRY(ctx, applyV(w, W.v), "solve: V w");
+      CUDA_TRY(ctx, stbem::sub_launch(f, W.v, W.r, N, s), "solve: f - V w");
+    }
+    first = false;
+    double beta;
+    CUDA_TRY(ctx, norm(W.r, &beta), "solve: norm r");
+    if (!std::isfinite(beta)) { status = STBEM_ERR_NAN; break; }
+    relres = beta / nf;
+    if (relres <= opts->tol) break;
+    if (iters >= maxit) { status = STBEM_ERR_NOCONV; break; }
+    CUDA_TRY(ctx, stbem::scale_launch(W.r, 1.0 / beta, W.Q, N, s), "solve: q0");
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k_done = 0;
+    bool stop_cycle = false;
+    for (int k = 0; k < restart; ++k) {
+      double* qk = W.Q + (size_t)k * N;
+      double* qk1 = W.Q + (size_t)(k + 1) * N;
+      CUDA_TRY(ctx, applyP(qk, W.z), "solve: precondition");
+      CUDA_TRY(ctx, applyV(W.z, W.v), "solve: V z");
+      // classical Gram-Schmidt, twice
+      CUDA_TRY(ctx, stbem::dots_launch(W.Q, k + 1, W.v, N, W.h, s), "solve: dots");
+      CUDA_TRY(ctx, stbem::sub_combination_launch(W.Q, k + 1, W.h, W.v, N, s), "solve: orth");
+      CUDA_TRY(ctx, cudaMemcpyAsync(hcol.data(), W.h, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s), "solve: h");
+      CUDA_TRY(ctx, stbem::dots_launch(W.Q, k + 1, W.v, N, W.h, s), "solve: dots2");
+      CUDA_TRY(ctx, stbem::sub_combination_launch(W.Q, k + 1, W.h, W.v, N, s), "solve: orth2");
+      CUDA_TRY(ctx, cudaMemcpyAsync(h2.data(), W.h, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s), "solve: h2");
+      double hk1;
+      CUDA_TRY(ctx, norm(W.v, &hk1), "solve: norm v");
+      for (int t = 0; t <= k; ++t) hcol[t] += h2[t];
+      bool bad = !std::isfinite(hk1);
+      for (int t = 0; t <= k; ++t) bad = bad || !std::isfinite(hcol[t]);
+      if (bad) { status = STBEM_ERR_NAN; stop_cycle = true; break; }
+      if (hk1 > 0.0) CUDA_TRY(ctx, stbem::scale_launch(W.v, 1.0 / hk1, qk1, N, s), "solve: q");
+      // Givens rotations on column k
+      for (int t = 0; t < k; ++t) {
+        const double a = cs[t] * hcol[t] + sn[t] * hcol[t + 1];
+        hcol[t + 1] = -sn[t] * hcol[t] + cs[t] * hcol[t + 1];
+        hcol[t] = a;
+      }
+      const double den = std::hypot(hcol[k], hk1);
+      cs[k] = hcol[k] / den;
+      sn[k] = hk1 / den;
+      hcol[k] = den;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      for (int t = 0; t <= k; ++t) H[(size_t)t * restart + k] = hcol[t];
+      ++iters;
+      k_done = k + 1;
+      const double est = std::fabs(g[k + 1]) / nf;
+      if (est <= opts->tol || iters >= maxit || hk1 == 0.0) break;
+    }
+    if (status != STBEM_OK) break;
+    // y = H^{-1} g (upper triangular), w += P(Q y)
+    std::vector<double> y(k_done, 0.0);
+    for (int t = k_done - 1; t >= 0; --t) {
+      double acc = g[t];
+      for (int u = t + 1; u < k_done; ++u) acc -= H[(size_t)t * restart + u] * y[u];
+      y[t] = acc / H[(size_t)t * restart + t];
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(W.h, y.data(), k_done * sizeof(double), cudaMemcpyHostToDevice, s), "solve: y");
+    CUDA_TRY(ctx, stbem::combination_launch(W.Q, k_done, W.h, W.r, N, s), "solve: Qy");
+    CUDA_TRY(ctx, applyP(W.r, W.z), "solve: P Qy");
+    CUDA_TRY(ctx, stbem::axpy_launch(1.0, W.z, w, N, s), "solve: update");
+    CUDA_TRY(ctx, cudaStreamSynchronize(s), "solve: sync");
+    (void)stop_cycle;
+  }
+  info->iterations = iters;
+  info->rel_residual = relres;
+  info->status = status;
+  if (status != STBEM_OK)
+    return fail(ctx, status, "solve: %s after %d iterations (relres %.3e)",
+                status == STBEM_ERR_NAN ? "NaN" : "no convergence", iters, relres);
+  return STBEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Block-lower-triangular block-Toeplitz products (Section 3 block structure,
+// uniform time grid => block (m, n) = A^(m-n)).
+//
+//   y[b][m][i] = sum_{d=0}^{m} sum_j A[d][i][j] x[b][m-d][j]              (forward)
+//   y[b][n][j] = sum_{d=0}^{nt-1-n} sum_i A[d][i][j] x[b][n+d][i]          (transpose)
+//
+// The transpose runs backward in time; with reversed time m' = nt-1-n it has
+// the forward structure with A^(d) transposed, which is how it is computed.
+//
+// Work split: a CTA owns an output tile (TM time steps x TI rows) of one
+// right-hand side and one chunk of lags; the (lag, column) reduction runs
+// through shared-memory tiles of A^(d) and of the shifted x.  Lag chunks write
+// partial tiles to the caller's workspace and a second kernel sums them in
+// chunk order, so results do not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include "assemble.h"
+#include "toeplitz.h"
+
+namespace stbem {
+
+constexpr int TI = 64, TM = 32, TJ = 16, kApplyThreads = 256;
+
+struct ApplyPlan {
+  int MT, IT, CH, DC;
+};
+
+static ApplyPlan make_plan(int nt, int nx) {
+  ApplyPlan p;
+  p.MT = (nt + TM - 1) / TM;
+  p.IT = (nx + TI - 1) / TI;
+  // aim at ~4 waves of 152 SMs of (tile, chunk) units
+  const long long target = 4 * 152;
+  long long per_chunk = (long long)p.IT * ((p.MT + 1) / 2);
+  if (per_chunk < 1) per_chunk = 1;
+  int ch = (int)((target + per_chunk - 1) / per_chunk);
+  if (ch < 1) ch = 1;
+  if (ch > nt) ch = nt;
+  p.DC = (nt + ch - 1) / ch;
+  p.CH = (nt + p.DC - 1) / p.DC;
+  return p;
+}
+
+size_t apply_workspace_bytes(int nt, int nx, int n_rhs) {
+  const ApplyPlan p = make_plan(nt, nx);
+  return (size_t)n_rhs * p.MT * p.CH * TM * (size_t)nx * sizeof(double);
+}
+
+template <typename TA, typename TC, bool TRANS>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
+        const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ TC As[TJ][TI + 1];
+  __shared__ TC Xs[TJ][TM + 1];
+  const int it = blockIdx.x, ch = blockIdx.y;
+  const int b = blockIdx.z / MT, mt = blockIdx.z % MT;
+  const int m0 = mt * TM, i0 = it * TI;
+  const int mmax = min(m0 + TM, nt) - 1;        // largest m in the tile
+  const int d0 = ch * DC;
+  if (d0 > mmax) return;
+  const int d1 = min(d0 + DC, mmax + 1);
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;        // rows tx*4.., time ty*2..
+  const double* xb = x + (size_t)b * nt * nx;
+  TC acc[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = (TC)0;
+
+  for (int d = d0; d < d1; ++d) {
+    const TA* Ad = A + (size_t)d * nx * nx;
+    for (int j0 = 0; j0 < nx; j0 += TJ) {
+      // A tile: element (row i0+ii, column j0+jj)
+#pragma unroll
+      for (int q = 0; q < (TI * TJ) / kApplyThreads; ++q) {
+        const int e = tid + q * kApplyThreads;
+        int ii, jj;
+        if (!TRANS) { jj = e % TJ; ii = e / TJ; } else { ii = e % TI; jj = e / TI; }
+        const int gi = i0 + ii, gj = j0 + jj;
+        TC v = (TC)0;
+        if (gi < nx && gj < nx) v = (TC)(!TRANS ? Ad[(size_t)gi * nx + gj] : Ad[(size_t)gj * nx + gi]);
+        As[jj][ii] = v;
+      }
+      // x tile: element (column j0+jj, time m0+mm) = x[m - d][j]
+#pragma unroll
+      for (int q = 0; q < (TM * TJ) / kApplyThreads; ++q) {
+        const int e = tid + q * kApplyThreads;
+        const int jj = e % TJ, mm = e / TJ;
+        const int m = m0 + mm, gj = j0 + jj;
+        TC v = (TC)0;
+        if (m <= mmax && m - d >= 0 && gj < nx) {
+          const int src = TRANS ? (nt - 1 - (m - d)) : (m - d);
+          v = (TC)xb[(size_t)src * nx + gj];
+        }
+        Xs[jj][mm] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) {
+        TC av[4], xv[2];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) av[c] = As[jj][tx * 4 + c];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) xv[a] = Xs[jj][ty * 2 + a];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[c], xv[a], acc[a][c]);
+      }
+      __syncthreads();
+    }
+  }
+  // partial tile -> part[b][mt][ch][mm][i]
+  double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TM) * nx;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int mm = ty * 2 + a;
+    if (m0 + mm > mmax) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gi = i0 + tx * 4 + c;
+      if (gi < nx) pt[(size_t)mm * nx + gi] = (double)acc[a][c];
+    }
+  }
+}
+
+template <bool TRANS>
+__global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC,
+                               const double* __restrict__ part, double* __restrict__ y) {
+  const size_t total = (size_t)n_rhs * nt * nx;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nx);
+    const int m = (int)((e / nx) % nt);       // time index in the computed order
+    const int b = (int)(e / ((size_t)nx * nt));
+    const int mt = m / TM, mm = m % TM;
+    const int mmax = min(mt * TM + TM, nt) - 1;
+    const int nch = min(CH, mmax / DC + 1);
+    const double* pt = part + ((((size_t)b * MT + mt) * CH) * TM + mm) * nx + i;
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += pt[(size_t)c * TM * nx];
+    const int mo = TRANS ? (nt - 1 - m) : m;
+    y[((size_t)b * nt + mo) * nx + i] = s;
+  }
+}
+
+template <typename TA, typename TC>
+static cudaError_t launch(bool trans, int nt, int nx, const TA* A, int n_rhs, const double* x,
+                          double* y, double* part, cudaStream_t s) {
+  const ApplyPlan p = make_plan(nt, nx);
+  dim3 grid(p.IT, p.CH, n_rhs * p.MT);
+  if (trans)
+    k_apply<TA, TC, true><<<grid, kApplyThreads, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, A, x, part);
+  else
+    k_apply<TA, TC, false><<<grid, kApplyThreads, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, A, x, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launches(2);
+  const size_t total = (size_t)n_rhs * nt * nx;
+  const int threads = 256;
+  const int blocks = (int)((total + threads - 1) / threads < 152 * 16 ? (total + threads - 1) / threads : 152 * 16);
+  if (trans)
+    k_apply_reduce<true><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
+  else
+    k_apply_reduce<false><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
+  return cudaGetLastError();
+}
+
+cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
+                         const double* x, double* y, void* work, cudaStream_t s) {
+  double* part = static_cast<double*>(work);
+  if (prec == STBEM_F64)
+    return launch<double, double>(trans, nt, nx, static_cast<const double*>(A), n_rhs, x, y, part, s);
+  return launch<float, float>(trans, nt, nx, static_cast<const float*>(A), n_rhs, x, y, part, s);
+}
+
+}  // namespace stbem

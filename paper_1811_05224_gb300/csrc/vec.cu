@@ -1,0 +1,174 @@
+// Vector kernels: right-hand side data, mass matrices and the FP64 building
+// blocks of GMRES (dot products, linear combinations, diagonal scaling).
+#include <cuda_runtime.h>
+
+#include "special.cuh"
+#include "vec.h"
+
+#include <atomic>
+
+namespace stbem {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches += n; }
+unsigned long long launch_count() { return g_launches.load(); }
+
+// g[n][p] = (1/ht) int_{tau_n} U*(x_p - y*, t) dt
+//         = alpha/(4 pi) [E1(a_p/t_{n+1}) - E1(a_p/t_n)] / ht,  a_p = alpha |x_p - y*|^2 / 4
+__global__ void k_rhs_g(DevMesh M, double ysx, double ysy, double* __restrict__ g) {
+  const int total = M.n_t * M.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int p = e % M.N, n = e / M.N;
+    const double dx = M.vx[p] - ysx, dy = M.vy[p] - ysy;
+    const double a = M.alpha * (dx * dx + dy * dy) / 4.0;
+    const double t1 = (double)(n + 1) * M.ht, t0 = (double)n * M.ht;
+    const double E1 = e1_only(a / t1);
+    const double E0 = n > 0 ? e1_only(a / t0) : 0.0;
+    g[e] = (E1 - E0) * M.alpha / (4.0 * kPi) / M.ht;
+  }
+}
+
+// f[m][i] += (1/2) M_h g: M_h[(i,m),(p,m)] = ht h_i / 2 for p in {i, i+1}
+__global__ void k_half_mass_add(DevMesh M, const double* __restrict__ g, double* __restrict__ f) {
+  const int total = M.n_t * M.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e % M.N, m = e / M.N;
+    const int ip = (i + 1) % M.N;
+    const double hm = 0.5 * M.ht * 0.5 * M.slen[i] * (g[e] + g[(size_t)m * M.N + ip]);
+    f[e] = hm + f[e];
+  }
+}
+
+// L_l = ht (h_{l-1} + 2 h_l + h_{l+1}) / 4  (row sums of <phi0_k, psi_l>)
+__global__ void k_lumped(DevMesh M, double* __restrict__ L) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= M.N) return;
+  const int N = M.N;
+  L[l] = M.ht * (M.slen[(l - 1 + N) % N] + 2.0 * M.slen[l] + M.slen[(l + 1) % N]) / 4.0;
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 64;
+
+// Stage 1: per (vector k, block) partial sums; stage 2: sum partials in order.
+__global__ void k_dots_partial(const double* __restrict__ Q, const double* __restrict__ v,
+                               size_t n, double* __restrict__ part) {
+  __shared__ double red[kRedThreads];
+  const int k = blockIdx.y;
+  const double* q = Q + (size_t)k * n;
+  double s = 0.0;
+  for (size_t e = (size_t)blockIdx.x * kRedThreads + threadIdx.x; e < n; e += (size_t)kRedBlocks * kRedThreads)
+    s = fma(q[e], v[e], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)k * kRedBlocks + blockIdx.x] = red[0];
+}
+
+__global__ void k_dots_final(const double* __restrict__ part, int k, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < kRedBlocks; ++b) s += part[(size_t)t * kRedBlocks + b];
+  out[t] = s;
+}
+
+// out holds k results followed by k * kRedBlocks scratch partials.
+cudaError_t dots_launch(const double* Q, int k, const double* v, size_t n, double* out, cudaStream_t s) {
+  double* part = out + k;
+  k_dots_partial<<<dim3(kRedBlocks, k), kRedThreads, 0, s>>>(Q, v, n, part);
+  k_dots_final<<<(k + 127) / 128, 128, 0, s>>>(part, k, out);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+__global__ void k_sub_comb(const double* __restrict__ Q, int k, const double* __restrict__ h,
+                           double* __restrict__ v, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double s = v[e];
+    for (int t = 0; t < k; ++t) s -= h[t] * Q[(size_t)t * n + e];
+    v[e] = s;
+  }
+}
+__global__ void k_comb(const double* __restrict__ Q, int k, const double* __restrict__ h,
+                       double* __restrict__ y, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < k; ++t) s += h[t] * Q[(size_t)t * n + e];
+    y[e] = s;
+  }
+}
+__global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = a * x[e];
+}
+__global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = fma(a, x[e], y[e]);
+}
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = a[e] - b[e];
+}
+__global__ void k_diag_div(const double* __restrict__ x, const double* __restrict__ L,
+                           double* __restrict__ y, int nt, int nx) {
+  const size_t n = (size_t)nt * nx;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = x[e] / L[e % nx];
+}
+
+static int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
+}
+
+cudaError_t rhs_g_launch(const DevMesh& M, double ysx, double ysy, double* g, cudaStream_t s) {
+  k_rhs_g<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, ysx, ysy, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t half_mass_add_launch(const DevMesh& M, const double* g, double* f, cudaStream_t s) {
+  k_half_mass_add<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, g, f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t lumped_mass_launch(const DevMesh& M, double* L, cudaStream_t s) {
+  k_lumped<<<(M.N + 127) / 128, 128, 0, s>>>(M, L);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t sub_combination_launch(const double* Q, int k, const double* h, double* v, size_t n, cudaStream_t s) {
+  k_sub_comb<<<grid_for(n), 256, 0, s>>>(Q, k, h, v, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t combination_launch(const double* Q, int k, const double* h, double* y, size_t n, cudaStream_t s) {
+  k_comb<<<grid_for(n), 256, 0, s>>>(Q, k, h, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t scale_launch(const double* x, double a, double* y, size_t n, cudaStream_t s) {
+  k_scale<<<grid_for(n), 256, 0, s>>>(x, a, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t axpy_launch(double a, const double* x, double* y, size_t n, cudaStream_t s) {
+  k_axpy<<<grid_for(n), 256, 0, s>>>(a, x, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t sub_launch(const double* a, const double* b, double* y, size_t n, cudaStream_t s) {
+  k_sub<<<grid_for(n), 256, 0, s>>>(a, b, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t diag_div_launch(const double* x, const double* L, double* y, int nt, int nx, cudaStream_t s) {
+  k_diag_div<<<grid_for((size_t)nt * nx), 256, 0, s>>>(x, L, y, nt, nx);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace stbem

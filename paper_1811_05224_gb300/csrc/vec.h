@@ -1,0 +1,21 @@
+#pragma once
+#include <cuda_runtime.h>
+
+#include "assemble.h"
+
+namespace stbem {
+cudaError_t rhs_g_launch(const DevMesh& M, double ysx, double ysy, double* g, cudaStream_t s);
+cudaError_t half_mass_add_launch(const DevMesh& M, const double* g, double* f, cudaStream_t s);
+cudaError_t lumped_mass_launch(const DevMesh& M, double* L, cudaStream_t s);
+// out[k] = <Q[k], v>, k = 0..k-1 (deterministic block reductions)
+cudaError_t dots_launch(const double* Q, int k, const double* v, size_t n, double* out, cudaStream_t s);
+// v -= sum_k h[k] Q[k]
+cudaError_t sub_combination_launch(const double* Q, int k, const double* h, double* v, size_t n, cudaStream_t s);
+// y = sum_k h[k] Q[k]
+cudaError_t combination_launch(const double* Q, int k, const double* h, double* y, size_t n, cudaStream_t s);
+cudaError_t scale_launch(const double* x, double a, double* y, size_t n, cudaStream_t s);
+cudaError_t axpy_launch(double a, const double* x, double* y, size_t n, cudaStream_t s);       // y += a x
+cudaError_t sub_launch(const double* a, const double* b, double* y, size_t n, cudaStream_t s);  // y = a - b
+// y[m][i] = x[m][i] / L[i]
+cudaError_t diag_div_launch(const double* x, const double* L, double* y, int nt, int nx, cudaStream_t s);
+}  // namespace stbem

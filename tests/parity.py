@@ -1,0 +1,52 @@
+"""Shared comparison helpers for GPU-vs-oracle parity tests."""
+import numpy as np
+
+
+def lag_rel_err(A, B, floor=1e-6):
+    """max over entries of |A - B| / max(|B|, floor * max|B^(d)|), per lag block.
+
+    The floor keeps entries that underflow or sit at a zero of the kernel from
+    dominating: far pairs at small lags are e^{-z}-small (z up to ~700)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    out = []
+    for d in range(B.shape[0]):
+        den = np.maximum(np.abs(B[d]), floor * np.abs(B[d]).max())
+        den = np.where(den > 0, den, 1.0)
+        out.append((np.abs(A[d] - B[d]) / den).max())
+    return np.array(out)
+
+
+def k_structural_zeros(om, tol=1e-12):
+    """(i, p) of K whose trial support (segments p-1, p, minus i itself) is
+    collinear with the test segment i: there q = (x - y) . n_y vanishes
+    identically, so both sides compute rounding noise (|K| ~ eps max|K|)."""
+    N = om.N
+    cr = lambda a, b: a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0]   # noqa: E731
+    mask = np.zeros((N, N), dtype=bool)
+    for i in range(N):
+        for p in range(N):
+            js = [j for j in (p, (p - 1) % N) if j != i]
+            mask[i, p] = all(abs(cr(om.t[i], om.t[j])) < tol and
+                             abs(cr(om.t[i], om.a[j] - om.a[i])) < tol * om.h[i] for j in js)
+    return mask
+
+
+def k_rel_err(A, B, om, floor=1e-6, zero_tol=1e-14):
+    """lag_rel_err for K with the structural zeros compared in absolute terms
+    (|value| <= zero_tol * max|K^(d)| on both sides)."""
+    mask = k_structural_zeros(om)
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    out = []
+    for d in range(B.shape[0]):
+        scale = np.abs(B[d]).max()
+        if mask.any():
+            assert np.abs(A[d][mask]).max() <= zero_tol * scale
+            assert np.abs(B[d][mask]).max() <= zero_tol * scale
+        den = np.maximum(np.abs(B[d]), floor * scale)
+        den = np.where(den > 0, den, 1.0)
+        e = np.abs(A[d] - B[d]) / den
+        e[mask] = 0.0
+        out.append(e.max())
+    return np.array(out)

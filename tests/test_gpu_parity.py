@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 entries relative error <= 1e-12 per entry (floored at 1e-6 of
+the lag block's largest entry); FP32 storage equals the FP64 result rounded to
+float (<= 1 ulp).  Products: FP64 within 1e-13 of the norm of |A||x|, FP32
+within 1e-5.  Solves: w_h within 1e-7 of the exact forward substitution.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import assembly as OA
+from oracle import rhs as OR
+from oracle import solve as OS
+from oracle.geometry import BoundaryMesh
+from tests.parity import k_rel_err, lag_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1811_05224_gb300 as P
+    return P.Context(0)
+
+
+def _pair(ctx, X, T, nt, al):
+    import paper_1811_05224_gb300 as P
+    return P.Mesh(ctx, X, T, nt, al), BoundaryMesh(X, T, nt, al)
+
+
+SMALL = {
+    "square32": (W.unit_square(8), 1.0, 32, 1.0),
+    "lshape24": (W.l_shape(24, seed=3), 1.0, 19, 0.5),
+    "star24": (W.star(8, 3, seed=5), 1.3, 13, 1.7),
+    "triangle": (np.array([[0.0, 0.0], [1.0, 0.2], [0.3, 0.9]]), 0.5, 5, 1.0),
+    "square_nt1": (W.unit_square(3), 1.0, 1, 2.0),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("op", ["V", "K", "D"])
+def test_assembly_matches_oracle(ctx, name, op):
+    import paper_1811_05224_gb300 as P
+    m, om = _pair(ctx, *SMALL[name])
+    A = P.assemble(ctx, m, op, "f64").cpu().numpy()
+    B = OA.assemble(op, om)
+    err = k_rel_err(A, B, om) if op == "K" else lag_rel_err(A, B)
+    assert err.max() <= 1e-12, (name, op, err.max(), int(err.argmax()))
+    A32 = P.assemble(ctx, m, op, "f32").cpu().numpy()
+    assert np.array_equal(A32, A.astype(np.float32))
+
+
+def test_assembly_sampled_full_size(ctx):
+    """square256 (N_x = N_t = 256), full operators on the GPU; sampled entries
+    of every pair class and lag regime against the oracle one by one."""
+    import paper_1811_05224_gb300 as P
+    p = W.config("square256")
+    m, om = _pair(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    rng = np.random.default_rng(7)
+    lags = [0, 1, 2, 3, 7, 8, 31, 32, 33, 100, 255]
+    fixed = [(0, 0), (0, 1), (1, 0), (0, 2), (63, 64), (64, 62), (0, 255), (255, 0), (5, 200), (128, 129)]
+    for op in "VKD":
+        A = P.assemble(ctx, m, op, "f64")
+        for d in lags:
+            pairs = fixed + [tuple(x) for x in rng.integers(0, 256, size=(6, 2))]
+            I = np.array([a for a, _ in pairs])
+            J = np.array([b for _, b in pairs])
+            got = A[d, torch.as_tensor(I), torch.as_tensor(J)].cpu().numpy()
+            fn = {"V": OA.V_entries, "K": OA.K_entries, "D": OA.D_entries}[op]
+            ref = fn(om, d, I, J)
+            scale = float(A[d].abs().max())
+            err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-6 * scale)
+            assert err.max() <= 1e-12, (op, d, pairs[int(err.argmax())], err.max())
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_apply_matches_oracle(ctx, prec, tol):
+    import paper_1811_05224_gb300 as P
+    rng = np.random.default_rng(3)
+    for nt, nx, nb in [(37, 45, 3), (1, 7, 1), (70, 64, 2), (5, 130, 1)]:
+        A = rng.standard_normal((nt, nx, nx))
+        x = rng.standard_normal((nb, nt, nx))
+        dt = torch.float64 if prec == "f64" else torch.float32
+        Ad = torch.as_tensor(A).to(dt).cuda()
+        Aeff = Ad.double().cpu().numpy()
+        xd = torch.as_tensor(x).cuda()
+        for tr in (False, True):
+            y = P.apply(ctx, Ad, xd, transpose=tr).cpu().numpy()
+            for b in range(nb):
+                ref = OS.toeplitz_apply(Aeff, x[b], transpose=tr)
+                mag = OS.toeplitz_apply(np.abs(Aeff), np.abs(x[b]), transpose=tr)
+                assert np.all(np.abs(y[b] - ref) <= tol * mag + 1e-300), (nt, nx, tr)
+
+
+def test_rhs_matches_oracle(ctx):
+    import paper_1811_05224_gb300 as P
+    for X, T, nt, al, ys in [(W.unit_square(8), 1.0, 32, 1.0, (1.5, 1.5)),
+                             (W.l_shape(24, seed=3), 0.7, 19, 0.5, (-0.4, 1.3))]:
+        m, om = _pair(ctx, X, T, nt, al)
+        K = P.assemble(ctx, m, "K")
+        g, f = P.rhs(ctx, m, K, ys)
+        g_ref = OR.g_vec(om, ys)
+        f_ref = OR.f_vec(om, OA.assemble("K", om), g_ref)
+        assert np.abs(g.cpu().numpy() - g_ref).max() <= 1e-13 * np.abs(g_ref).max()
+        assert np.abs(f.cpu().numpy() - f_ref).max() <= 1e-12 * np.abs(f_ref).max()
+        L = P.lumped_mass(ctx, m).cpu().numpy()
+        assert np.allclose(L, OA.lumped_dual_mass(om), rtol=1e-15, atol=0)
+
+
+def test_solve_matches_forward_substitution(ctx):
+    import paper_1811_05224_gb300 as P
+    p = W.config("square32")
+    m, om = _pair(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    V, K, D = (P.assemble(ctx, m, o) for o in "VKD")
+    L = P.lumped_mass(ctx, m)
+    g, f = P.rhs(ctx, m, K, p.y_star)
+    Vo = OA.assemble("V", om)
+    fo = f.cpu().numpy()
+    w_ref = OS.forward_substitution(Vo, fo)
+    Do = OA.assemble("D", om)
+    Lo = OA.lumped_dual_mass(om)
+    for use_prec in (True, False):
+        w, info = P.solve(ctx, V, f, D if use_prec else None, L if use_prec else None, tol=1e-8)
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+        wn = w.cpu().numpy()
+        assert np.linalg.norm(wn - w_ref) <= 1e-6 * np.linalg.norm(w_ref)
+        Pm = (lambda v: OS.toeplitz_apply(Do, v / Lo) / Lo) if use_prec else None
+        _, it_ref, _ = OS.gmres(lambda v: OS.toeplitz_apply(Vo, v), fo, Pm, tol=1e-8)
+        assert abs(info["iterations"] - it_ref) <= 1, (info["iterations"], it_ref)
+
+
+def test_solve_full_size_converges_to_exact_datum(ctx):
+    """square256: preconditioned GMRES to 1e-8; w_h against the exact Neumann
+    datum (projection), which the finer meshes approach at order > 1."""
+    import paper_1811_05224_gb300 as P
+    p = W.config("square256")
+    m, om = _pair(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    V, K, D = (P.assemble(ctx, m, o) for o in "VKD")
+    L = P.lumped_mass(ctx, m)
+    g, f = P.rhs(ctx, m, K, p.y_star)
+    w, info = P.solve(ctx, V, f, D, L, tol=1e-8)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+    assert info["iterations"] <= 40
+    err = OR.l2_rel_error(om, w.cpu().numpy(), OR.w_projection(om, p.y_star))
+    assert err < 3e-3, err
+
+
+def test_error_codes(ctx):
+    import paper_1811_05224_gb300 as P
+    from paper_1811_05224_gb300 import capi
+    sq = W.unit_square(2)
+    for args in [(sq[:2], 1.0, 4, 1.0), (sq, 0.0, 4, 1.0), (sq, 1.0, 0, 1.0), (sq, 1.0, 4, -1.0),
+                 (sq[::-1], 1.0, 4, 1.0), (np.vstack([sq, sq[-1:]]), 1.0, 4, 1.0)]:
+        with pytest.raises(capi.StbemError) as e:
+            P.Mesh(ctx, *args)
+        assert e.value.code == capi.STBEM_ERR_ARG
+    m = P.Mesh(ctx, sq, 1.0, 4, 1.0)
+    A = P.assemble(ctx, m, "V")
+    x = torch.zeros(4, 8, dtype=torch.float64, device="cuda")
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.StbemError) as e:
+        P.apply(ctx, A, x, work=small)
+    assert e.value.code == capi.STBEM_ERR_NOMEM
+    with pytest.raises(capi.StbemError) as e:
+        P.apply(ctx, A, x, out=x)
+    assert e.value.code == capi.STBEM_ERR_ARG
+    nan_f = torch.full((4, 8), float("nan"), dtype=torch.float64, device="cuda")
+    w, info = P.solve(ctx, A, nan_f, raise_on_fail=False)
+    assert info["status"] == capi.STBEM_ERR_NAN
