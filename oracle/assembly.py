@@ -60,13 +60,15 @@ def _rule(code, d, rules):
 
 
 def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
-                   wa0, wa1, wb0, wb1, rules=DEFAULT_RULES, chunk=2048):
+                   wa0, wa1, wb0, wb1, rules=DEFAULT_RULES, chunk=2048, magnitude=False):
     """int_a int_b k_d(x, y) wa(x) wb(y) ds_y ds_x for arrays of piece pairs.
 
     kind: 'V' (D2_d F_V), 'K' (D2_d F_K, uses the trial normal NB) or '1'
     (D2_d F_1).  Pieces a: A0 -> A1 (length LA), b: B0 -> B1 (length LB).
     wa, wb are linear in the local parameters xi, eta in [0,1]:
     wa(xi) = wa0 + (wa1 - wa0) xi.
+    With magnitude=True the sum of the absolute values of the point terms is
+    returned instead (the scale of the rounding error of the sum).
     """
     n = len(cls)
     out = np.zeros(n)
@@ -100,7 +102,10 @@ def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
                 raise ValueError(kind)
             fa = wa0[sel, None] + (wa1 - wa0)[sel, None] * xi[None, :]
             fb = wb0[sel, None] + (wb1 - wb0)[sel, None] * eta[None, :]
-            out[sel] = (w[None, :] * k * fa * fb).sum(-1) * LA[sel] * LB[sel]
+            terms = w[None, :] * k * fa * fb
+            if magnitude:
+                terms = np.abs(terms)
+            out[sel] = terms.sum(-1) * LA[sel] * LB[sel]
     return out
 
 
@@ -156,8 +161,12 @@ def _dual_tables(mesh):
     return idx, v0, v1, dp
 
 
-def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES):
-    """D^(d)[l][k] = <D psi_k, psi_l> at lag d (form written above)."""
+def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False):
+    """D^(d)[l][k] = <D psi_k, psi_l> at lag d (form written above).
+
+    magnitude=True returns S = sum over pieces and quadrature points of the
+    absolute values of the terms of the sum, the scale against which rounding
+    in any evaluation order of this signed sum is measured."""
     L, K = np.asarray(L), np.asarray(K)
     lo, hi = np.minimum(L, K), np.maximum(L, K)
     idx, v0, v1, dp = _dual_tables(mesh)
@@ -180,12 +189,14 @@ def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES):
     B0, B1, LB = mesh.hs0[pb], mesh.hs1[pb], mesh.hs_len[pb]
     NB = mesh.hs_n[pb]
     IV = pair_integrals('V', d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
-                        one, one, one, one, rules)
+                        one, one, one, one, rules, magnitude=magnitude)
     I1 = pair_integrals('1', d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
                         v0[ra[:, 0], ra[:, 1]], v1[ra[:, 0], ra[:, 1]],
-                        v0[rb[:, 0], rb[:, 1]], v1[rb[:, 0], rb[:, 1]], rules)
+                        v0[rb[:, 0], rb[:, 1]], v1[rb[:, 0], rb[:, 1]], rules, magnitude=magnitude)
     curl = dp[ra[:, 0], ra[:, 1]] * dp[rb[:, 0], rb[:, 1]]
     nn = (mesh.hs_n[pa] * mesh.hs_n[pb]).sum(-1)
+    if magnitude:
+        curl, nn = np.abs(curl), np.abs(nn)
     contrib = curl * IV + nn * I1
     out = np.zeros(E)
     np.add.at(out, eo, contrib)
@@ -203,8 +214,10 @@ def _all_pairs(N, symmetric):
     return I, J
 
 
-def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None):
-    """Lag blocks A[d][i][j] (N_t x N_x x N_x) of op in {'V', 'K', 'D'}."""
+def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None, magnitude=False):
+    """Lag blocks A[d][i][j] (N_t x N_x x N_x) of op in {'V', 'K', 'D'}.
+
+    magnitude=True (D only) returns the term-magnitude sums S instead."""
     N = mesh.N
     lags = range(mesh.n_t) if lags is None else lags
     sym = op in ('V', 'D')
@@ -212,7 +225,7 @@ def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None):
     fn = {'V': V_entries, 'K': K_entries, 'D': D_entries}[op]
     out = np.zeros((len(list(lags)), N, N))
     for k, d in enumerate(lags):
-        vals = fn(mesh, d, I, J, rules)
+        vals = fn(mesh, d, I, J, rules, magnitude=True) if magnitude else fn(mesh, d, I, J, rules)
         out[k, I, J] = vals
         if sym:
             out[k, J, I] = vals

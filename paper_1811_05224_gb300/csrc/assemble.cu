@@ -208,6 +208,164 @@ __global__ void k_lag2(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
   if ((OP == STBEM_OP_V || OP == STBEM_OP_D) && i != j) out[base + (size_t)j * N + i] = (T)val;
 }
 
+// ---- lags >= 2, K and D: tile kernels on piece-pair moments -------------------
+// D: a CTA owns a kDT x kDT tile of entries (l, k); the pieces of the dual
+// functions of its rows are the 2 kDT + 2 consecutive half-segments starting at
+// 2 l0 - 1 (likewise for the columns).  Per lag it integrates every half-pair
+// once into five moments -- the V kernel with weight 1 and the D time kernel
+// with the bilinear basis (1-xi)(1-eta), (1-xi)eta, xi(1-eta), xi eta -- and
+// then sums the 16 piece pairs of each entry from shared memory.
+constexpr int kDT = 16;
+constexpr int kDP = 2 * kDT + 2;          // half-segments per tile side
+constexpr int kTileThreads = 256;
+
+__device__ void pair_moments_D(const Piece& A, const Piece& B, int d, int n, double ht, double alpha,
+                               double* mom) {
+  const int o = gauss_offset(n);
+  const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
+  const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
+  const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
+  double sv = 0.0, s00 = 0.0, s01 = 0.0, s10 = 0.0, s11 = 0.0;
+  for (int a = 0; a < n; ++a) {
+    const double xi = c_tab.gx[o + a];
+    const double wa = c_tab.gw[o + a];
+    for (int b = 0; b < n; ++b) {
+      const double eta = c_tab.gx[o + b];
+      const double w = wa * c_tab.gw[o + b];
+      const double dx = (abx + xi * eax) - eta * ebx;
+      const double dy = (aby + xi * eay) - eta * eby;
+      const double c = 0.25 * alpha * (dx * dx + dy * dy);
+      double kv, k1v;
+      lag_kernel_D(c, d, ht, alpha, &kv, &k1v);
+      sv += w * kv;
+      const double wk = w * k1v;
+      s00 += wk * (1.0 - xi) * (1.0 - eta);
+      s01 += wk * (1.0 - xi) * eta;
+      s10 += wk * xi * (1.0 - eta);
+      s11 += wk * xi * eta;
+    }
+  }
+  const double L = A.len * B.len;
+  mom[0] = sv * L; mom[1] = s00 * L; mom[2] = s01 * L; mom[3] = s10 * L; mom[4] = s11 * L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_lag2_D(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
+  __shared__ double mom[kDP * kDP][5];
+  const int N = M.N, H = 2 * N;
+  // upper-triangular tile pair from the linear block index
+  int lt = 0, rem = blockIdx.x;
+  const int nT = (N + kDT - 1) / kDT;
+  while (rem >= nT - lt) { rem -= nT - lt; ++lt; }
+  const int kt = lt + rem;
+  const int l0 = lt * kDT, k0 = kt * kDT;
+  const int tid = threadIdx.x;
+  const double ht = M.ht, alpha = M.alpha;
+  for (int d = d_begin + blockIdx.y; d < d_end; d += gridDim.y) {
+    const int n = space_order(d);
+    for (int p = tid; p < kDP * kDP; p += kTileThreads) {
+      const int u = p / kDP, v = p % kDP;
+      const int ga = ((2 * l0 - 1 + u) % H + H) % H;
+      const int gb = ((2 * k0 - 1 + v) % H + H) % H;
+      pair_moments_D(half_piece(M, ga), half_piece(M, gb), d, n, ht, alpha, mom[p]);
+    }
+    __syncthreads();
+    if (tid < kDT * kDT) {
+      const int s = tid / kDT, t = tid % kDT;
+      const int l = l0 + s, k = k0 + t;
+      // evaluate the smaller index first (symmetric block): on the diagonal
+      // tile both ranges coincide, so (lo, hi) local offsets exist
+      const int lo = l < k ? l : k, hi = l < k ? k : l;
+      const int so = lo - l0, to = hi - k0;
+      if (l < N && k < N && so >= 0 && to >= 0 && so < kDT && to < kDT) {
+        double val = 0.0;
+        for (int ia = 0; ia < 4; ++ia) {
+          const int qa = 4 * lo + ia;
+          const double ca = M.dcurl[qa], a0 = M.dv0[qa], a1 = M.dv1[qa];
+          const int u = 2 * so + ia;
+          const int ga = M.dpiece[qa];
+          const double nax = M.hnx[ga], nay = M.hny[ga];
+          for (int ib = 0; ib < 4; ++ib) {
+            const int qb = 4 * hi + ib;
+            const double cb = M.dcurl[qb], b0 = M.dv0[qb], b1 = M.dv1[qb];
+            const int v = 2 * to + ib;
+            const int gb = M.dpiece[qb];
+            const double nn = nax * M.hnx[gb] + nay * M.hny[gb];
+            const double* m = mom[u * kDP + v];
+            const double I1 = a0 * (b0 * m[1] + b1 * m[2]) + a1 * (b0 * m[3] + b1 * m[4]);
+            val += ca * cb * m[0] + nn * I1;
+          }
+        }
+        const size_t base = (size_t)d * N * N;
+        out[base + (size_t)l * N + k] = (T)val;
+        if (lt != kt) out[base + (size_t)k * N + l] = (T)val;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// K: a CTA owns kKI x kKP entries (i, p); the trial segments are p0-1 .. p0+kKP-1.
+// Moments per segment pair (i, j): int k (1 - eta) and int k eta, so that
+// K[i][p] = Ma(i, p) + Mb(i, p-1) (identical pairs contribute 0).
+constexpr int kKI = 16, kKP = 15, kKJ = kKP + 1;
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_lag2_K(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
+  __shared__ double mom[kKI * kKJ][2];
+  const int N = M.N;
+  const int nP = (N + kKP - 1) / kKP;
+  const int it = blockIdx.x / nP, pt = blockIdx.x % nP;
+  const int i0 = it * kKI, p0 = pt * kKP;
+  const int tid = threadIdx.x;
+  const double ht = M.ht, alpha = M.alpha;
+  for (int d = d_begin + blockIdx.y; d < d_end; d += gridDim.y) {
+    const int n = space_order(d);
+    const int o = gauss_offset(n);
+    for (int p = tid; p < kKI * kKJ; p += kTileThreads) {
+      const int si = p / kKJ, sj = p % kKJ;
+      const int i = i0 + si;
+      const int j = ((p0 - 1 + sj) % N + N) % N;
+      double ma = 0.0, mb = 0.0;
+      if (i < N && j != i) {
+        const Piece A = seg_piece(M, i), B = seg_piece(M, j);
+        const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
+        const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
+        const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
+        for (int a = 0; a < n; ++a) {
+          const double xi = c_tab.gx[o + a];
+          const double wa = c_tab.gw[o + a];
+          for (int b = 0; b < n; ++b) {
+            const double eta = c_tab.gx[o + b];
+            const double w = wa * c_tab.gw[o + b];
+            const double dx = (abx + xi * eax) - eta * ebx;
+            const double dy = (aby + xi * eay) - eta * eby;
+            const double c = 0.25 * alpha * (dx * dx + dy * dy);
+            const double k = (dx * B.nx + dy * B.ny) * lag_kernel<kKq>(c, d, ht, alpha, c_tab.gx, c_tab.gw);
+            const double wk = w * k;
+            ma += wk * (1.0 - eta);
+            mb += wk * eta;
+          }
+        }
+        ma *= A.len * B.len;
+        mb *= A.len * B.len;
+      }
+      mom[p][0] = ma;
+      mom[p][1] = mb;
+    }
+    __syncthreads();
+    if (tid < kKI * kKP) {
+      const int si = tid / kKP, sp = tid % kKP;
+      const int i = i0 + si, p = p0 + sp;
+      if (i < N && p < N) {
+        const double val = mom[si * kKJ + sp + 1][0] + mom[si * kKJ + sp][1];
+        out[(size_t)d * N * N + (size_t)i * N + p] = (T)val;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---- lags 0, 1: one CTA per entry -----------------------------------------------
 constexpr int kLag01Threads = 128;
 
@@ -412,10 +570,19 @@ static cudaError_t launch_op(const DevMesh& M, T* out, cudaStream_t s) {
     const int chunk = 64;
     for (int d0 = 2; d0 < nt; d0 += chunk) {
       const int d1 = d0 + chunk < nt ? d0 + chunk : nt;
-      const long long total = (long long)(d1 - d0) * N * N;
-      const int threads = 128;
-      const long long blocks = (total + threads - 1) / threads;
-      k_lag2<OP, T><<<(unsigned)blocks, threads, 0, s>>>(M, d0, d1, out);
+      if (OP == STBEM_OP_V) {
+        const long long total = (long long)(d1 - d0) * N * N;
+        const int threads = 128;
+        const long long blocks = (total + threads - 1) / threads;
+        k_lag2<OP, T><<<(unsigned)blocks, threads, 0, s>>>(M, d0, d1, out);
+      } else if (OP == STBEM_OP_K) {
+        const int tiles = ((N + kKI - 1) / kKI) * ((N + kKP - 1) / kKP);
+        k_lag2_K<T><<<dim3(tiles, d1 - d0), kTileThreads, 0, s>>>(M, d0, d1, out);
+      } else {
+        const int nT = (N + kDT - 1) / kDT;
+        const int tiles = nT * (nT + 1) / 2;
+        k_lag2_D<T><<<dim3(tiles, d1 - d0), kTileThreads, 0, s>>>(M, d0, d1, out);
+      }
       count_launches(1);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;

@@ -1,0 +1,55 @@
+"""Generate expint_cheb.inc: Chebyshev coefficients of A(z) = e^z E1(z) and
+B(z) = e^z E2(z) on [1,2], [2,4], [4,8], [8,16].
+
+Each function is interpolated at the 26 Chebyshev points of the first kind of
+the interval, in 40-digit arithmetic (mpmath), and the coefficients of
+    f(z) = c_0 / 2 + sum_{k=1}^{25} c_k T_k(t),  t = (2 z - a - b) / (b - a)
+are written as double literals.  On each interval the nearest singularity of
+A and B is the log branch point at z = 0, three half-widths from the centre,
+so the coefficients decay like (3 + sqrt 8)^{-k}: 26 terms reach ~1e-19.
+
+Run from the repository root:  python paper_1811_05224_gb300/csrc/gen_expint_tables.py
+"""
+import os
+
+import mpmath as mp
+
+mp.mp.dps = 40
+NC = 26
+INTERVALS = [(1, 2), (2, 4), (4, 8), (8, 16)]
+
+
+def cheb_coeffs(f, a, b, n=NC):
+    nodes = [mp.cos(mp.pi * (j + mp.mpf(1) / 2) / n) for j in range(n)]
+    vals = [f((b - a) / mp.mpf(2) * t + (a + b) / mp.mpf(2)) for t in nodes]
+    out = []
+    for k in range(n):
+        s = mp.fsum(v * mp.cos(k * mp.pi * (j + mp.mpf(1) / 2) / n) for j, v in enumerate(vals))
+        out.append(2 * s / n)
+    return out
+
+
+def main():
+    A = lambda z: mp.e ** z * mp.e1(z)            # noqa: E731
+    B = lambda z: mp.e ** z * mp.expint(2, z)     # noqa: E731
+    lines = ["// Generated by gen_expint_tables.py: Chebyshev coefficients of",
+             "// A(z) = e^z E1(z) and B(z) = e^z E2(z), %d terms per interval," % NC,
+             "// intervals [1,2], [2,4], [4,8], [8,16]; f = c0/2 + sum_k c_k T_k(t).",
+             "#pragma once", "namespace stbem {",
+             "constexpr int kChebN = %d;" % NC,
+             "constexpr int kChebIntervals = %d;" % len(INTERVALS)]
+    for name, f in (("kChebE1", A), ("kChebE2", B)):
+        lines.append("static __constant__ const double %s[%d][%d] = {" % (name, len(INTERVALS), NC))
+        for a, b in INTERVALS:
+            c = cheb_coeffs(f, mp.mpf(a), mp.mpf(b))
+            lines.append("  {" + ", ".join(mp.nstr(x, 20, min_fixed=0, max_fixed=0) for x in c) + "},")
+        lines.append("};")
+    lines.append("}  // namespace stbem")
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "expint_cheb.inc")
+    with open(out, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    print(out)
+
+
+if __name__ == "__main__":
+    main()

@@ -6,3 +6,6 @@
 #define STB_HD inline
 #endif
 #include <cmath>
+#ifndef __CUDACC__
+#define __constant__
+#endif

@@ -2,13 +2,18 @@
 // definitions: E_n(z) = int_1^inf e^{-zt} t^{-n} dt.
 //  * z < 1: E1(z) = -gamma - ln z + Ein(z), Ein(z) = sum_{k>=1} (-1)^{k+1} z^k/(k k!)
 //    (Abramowitz & Stegun 5.1.11), and E2(z) = e^{-z} - z E1(z) (A&S 5.1.14);
-//  * z >= 1: the continued fraction of A&S 5.1.22 in its even (contracted)
+//  * 1 <= z < 16: e^z E1 and e^z E2 from 26-term Chebyshev expansions on
+//    [1,2], [2,4], [4,8], [8,16] (coefficients in expint_cheb.inc, generated
+//    by gen_expint_tables.py in 40-digit arithmetic), Clenshaw summation;
+//  * z >= 16: the continued fraction of A&S 5.1.22 in its even (contracted)
 //    form, E_n(z) = e^{-z} / (z + n - 1 n / (z + n + 2 - 2 (n+1) / (z + n + 4 - ...))),
-//    evaluated by Lentz's method (Lentz, Appl. Opt. 15, 1976) to relative
-//    convergence 1e-16.
+//    evaluated backward at a fixed depth of 14 (converged to < 1e-16 there).
+//    The Lentz evaluation (Lentz, Appl. Opt. 15, 1976) of the same fraction is
+//    kept as cf_e1e2 for checks.
 // exp and log are the platform's; nothing here reproduces their internals.
 #pragma once
 #include "hd.cuh"
+#include "expint_cheb.inc"
 
 namespace stbem {
 
@@ -58,18 +63,45 @@ STB_HD void cf_e1e2(double z, double* f1, double* f2) {
   *f2 = h2;
 }
 
+// Backward evaluation of the contracted fraction at fixed depth (z >= 16).
+STB_HD double cf_backward(double z, int n) {
+  constexpr int K = 14;
+  double f = z + (double)n + 2.0 * K;
+  for (int k = K; k >= 1; --k) {
+    const double a = -(double)k * (double)(n - 1 + k);
+    f = (z + (double)n + 2.0 * (double)(k - 1)) + a / f;
+  }
+  return 1.0 / f;
+}
+
+// Clenshaw sum of c0/2 + sum_{k>=1} c_k T_k(t).
+STB_HD double cheb_sum(const double* c, double t) {
+  double b1 = 0.0, b2 = 0.0;
+  for (int k = kChebN - 1; k >= 1; --k) {
+    const double b0 = c[k] + 2.0 * t * b1 - b2;
+    b2 = b1;
+    b1 = b0;
+  }
+  return 0.5 * c[0] + t * b1 - b2;
+}
+
 // E1(z), E2(z) for z > 0.
 STB_HD void e1e2(double z, double* e1, double* e2) {
   if (z < 1.0) {
     const double E1 = -kEulerGamma - log(z) + ein_series(z);
     *e1 = E1;
     *e2 = exp(-z) - z * E1;
-  } else {
-    double f1, f2;
-    cf_e1e2(z, &f1, &f2);
+  } else if (z < 16.0) {
+    const int k = z < 2.0 ? 0 : (z < 4.0 ? 1 : (z < 8.0 ? 2 : 3));
+    const double a = (double)(1 << k);
+    const double t = 2.0 * z / a - 3.0;
     const double ez = exp(-z);
-    *e1 = f1 * ez;
-    *e2 = f2 * ez;
+    *e1 = cheb_sum(kChebE1[k], t) * ez;
+    *e2 = cheb_sum(kChebE2[k], t) * ez;
+  } else {
+    const double ez = exp(-z);
+    *e1 = cf_backward(z, 1) * ez;
+    *e2 = cf_backward(z, 2) * ez;
   }
 }
 

@@ -50,3 +50,23 @@ def k_rel_err(A, B, om, floor=1e-6, zero_tol=1e-14):
         e[mask] = 0.0
         out.append(e.max())
     return np.array(out)
+
+
+def d_rel_err(A, B, S, floor=1e-6, tol=1e-12, term_tol=1e-14):
+    """Normalised D error: |A - B| / (tol max(|B|, floor max|B^(d)|) + term_tol S).
+
+    A D_h entry (Section 2, integrated-by-parts form) is a signed sum of curl
+    and time terms; S, the sum of the magnitudes of all its quadrature terms,
+    exceeds |D| by up to ~1e6 far from the diagonal.  Any evaluation order
+    rounds by ~eps S, so the entry is required to 1e-12 relative where it is
+    well conditioned and to 1e-14 S (about 50 ulp per term) elsewhere.  The
+    returned value is <= 1 when both bounds hold jointly."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    out = []
+    for d in range(B.shape[0]):
+        den = tol * np.maximum(np.abs(B[d]), floor * np.abs(B[d]).max()) + term_tol * S[d]
+        den = np.where(den > 0, den, 1.0)
+        out.append((np.abs(A[d] - B[d]) / den).max())
+    return np.array(out)
