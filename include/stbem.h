@@ -108,6 +108,26 @@ int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
                 const void* dev_A, int n_rhs, const double* dev_x, double* dev_y,
                 void* dev_work, size_t work_bytes);
 
+/* Allocation-free block-Toeplitz product.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate device memory at all -- for
+ * example code embedded in a host framework that owns every device buffer
+ * through its own pool and forbids raw allocations, or a C caller without an
+ * allocator -- and so cannot provide the workspace stbem_apply needs.  Same
+ * arguments and result as stbem_apply, minus the workspace: the lag-chunk
+ * partial sums go to a fixed scratch array inside the library's device image
+ * (32 MiB; every GPU that loads the library holds it until the process exits).
+ * The first call on a device looks up that array's device address; make that
+ * first call before any stream capture.  Calls share the one array: two calls
+ * that overlap on the GPU (other streams, other threads, other contexts on the
+ * same device) race on it and must be serialised by the caller.  Each call
+ * writes every scratch entry it later reads, so nothing has to start at zero
+ * and the previous call's leftovers are never read.  Allocates nothing (no
+ * cudaMalloc, no allocating library call).  Errors: STBEM_ERR_ARG;
+ * STBEM_ERR_NOMEM if the product needs more scratch than the fixed array
+ * holds (stbem_apply_workspace_bytes() > 32 MiB); STBEM_ERR_CUDA. */
+int stbem_apply_noalloc(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
+                        const void* dev_A, int n_rhs, const double* dev_x, double* dev_y);
+
 /* Right-hand side of eq. (4) for u_0 = 0 and the Dirichlet datum
  * g = U*(x - y*, t) (y* outside the domain):
  *   dev_g[n][p] = time average of g at vertex p over tau_n,

@@ -239,6 +239,26 @@ int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x, const
   return STBEM_OK;
 }
 
+int stbem_apply_noalloc(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x, const void* A,
+                        int n_rhs, const double* x, double* y) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A || !x || !y) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: NULL pointer");
+  if (n_t < 1 || n_x < 1 || n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: bad sizes");
+  if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: bad precision");
+  if ((const void*)x == (const void*)y) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: x and y overlap");
+  const size_t need = stbem::apply_workspace_bytes(n_t, n_x, n_rhs);
+  if (need > stbem::kNoAllocScratchBytes)
+    return fail(ctx, STBEM_ERR_NOMEM,
+                "apply_noalloc: this product needs %zu bytes of scratch but the fixed scratch holds %zu; "
+                "use stbem_apply with a caller workspace", need, stbem::kNoAllocScratchBytes);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_noalloc: set device");
+  void* scratch = nullptr;
+  CUDA_TRY(ctx, stbem::noalloc_scratch_ptr(ctx->device, &scratch), "apply_noalloc: scratch address");
+  CUDA_TRY(ctx, stbem::apply_launch(prec, transpose != 0, n_t, n_x, A, n_rhs, x, y, scratch, ctx->stream),
+           "apply_noalloc");
+  return STBEM_OK;
+}
+
 int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, double* g,
               double* f, void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;

@@ -14,6 +14,8 @@
 // chunk order, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "assemble.h"
 #include "toeplitz.h"
 
@@ -165,6 +167,30 @@ static cudaError_t launch(bool trans, int nt, int nx, const TA* A, int n_rhs, co
   else
     k_apply_reduce<false><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
   return cudaGetLastError();
+}
+
+// ---- allocation-free variant --------------------------------------------------
+// Scratch for callers that cannot allocate device memory: a fixed array in the
+// library's own device image.  Every GPU that loads this library keeps these
+// kNoAllocScratchBytes until the process exits.  Host code must not use the
+// symbol as a pointer; its device address is looked up once per device.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+cudaError_t noalloc_scratch_ptr(int device, void** ptr) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    // the caller has made `device` current; resolve the symbol on it once
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = p;
+  }
+  *ptr = g_noalloc_ptr[device];
+  return cudaSuccess;
 }
 
 cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
