@@ -96,8 +96,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n_x": 256, "n_t": 256, "alpha": 1.0,
-                                        "T": 1.0, "l2": "n/a (CPU)"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -281,7 +280,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         c, t = _oracle_sample(96, 12345)
         cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "96 random (op, lag, i, j) entries of square256, single numpy process"}
+               "sample": "96 random (op, lag, i, j) entries of %s, single numpy process" % WORKLOAD}
     # dominant kernel by time: D assembly (FP64 ALU); report the FP64 product
     # roofline for the Toeplitz apply kernel as well
     dominant = max(op_ms, key=op_ms.get)
@@ -365,7 +364,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named workload (default square256; smaller ones are for profiling)")
     args = ap.parse_args()
+    globals()["WORKLOAD"] = args.workload
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -146,13 +146,14 @@ def ragged_squares(n_problems: int = 64, seed: int = 41, k_range=(16, 128),
     return [(int(4 * k), int(nt)) for k, nt in zip(ks, nts)]
 
 
-CONFIG_NAMES = ("square32", "square256", "lshape1024", "square512", "star256")
+CONFIG_NAMES = ("square32", "square64", "square256", "lshape1024", "square512", "star256")
 
 
 def config(name: str) -> Problem:
     """Named workloads (sizes of the measured configurations).
 
     * ``square32``   unit square, N_x = 32 (8 per side), N_t = 32, T = 1, alpha = 1
+    * ``square64``   unit square, N_x = 64, N_t = 64 (small profiling case)
     * ``square256``  unit square, N_x = 256, N_t = 256, T = 1, alpha = 1
     * ``lshape1024`` L-shape, N_x = 1024 (seeded lengths, seed 3), N_t = 1024, alpha = 0.5
     * ``square512``  unit square, N_x = 512, N_t = 512, alpha = 1
@@ -161,6 +162,8 @@ def config(name: str) -> Problem:
     """
     if name == "square32":
         return Problem(name, unit_square(8), 1.0, 32, 1.0)
+    if name == "square64":
+        return Problem(name, unit_square(16), 1.0, 64, 1.0)
     if name == "square256":
         return Problem(name, unit_square(64), 1.0, 256, 1.0)
     if name == "lshape1024":
