@@ -90,7 +90,11 @@ int stbem_op_bytes(const stbem_mesh* mesh, int op, int prec, size_t* bytes);
  * space Y_h (Section 2), integrated by the discretisation rule documented in
  * the repository (Gauss-Legendre in space, graded/Duffy rules for coincident
  * and touching pieces at lags 0-1, closed-form or Peano time integrals).
- * STBEM_F32 stores the FP64-computed entries rounded to float.
+ * STBEM_F32 is the mixed-precision assembly: FP32 arithmetic and storage,
+ * except that identical pieces and pieces sharing a vertex at lags 0 and 1
+ * (where the small-argument E1 terms cancel) are integrated in FP64; entries
+ * carry about 1e-6 relative error (D_h entries far from the diagonal, which
+ * are small differences of larger terms, carry about 1e-6 of their terms).
  * Errors: STBEM_ERR_ARG (bad op/prec/NULL), STBEM_ERR_CUDA. */
 int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec,
                    void* dev_out);
@@ -172,6 +176,26 @@ int stbem_solve(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void* dev_V,
                 const void* dev_D, const double* dev_L, const double* dev_f,
                 double* dev_w, const stbem_solve_opts* opts, stbem_solve_info* info,
                 void* dev_work, size_t work_bytes);
+
+/* Mixed-precision solve of V_h w = f (eq. (4)): FP64 iterative refinement,
+ * r = f - V_h w with the FP64 operator dev_V64, around right-preconditioned
+ * GMRES (Section 2 preconditioner) on the FP32 operators dev_V32 and dev_D32
+ * (FP32 products, FP64 Krylov vectors and orthogonalisation).  Each inner
+ * solve reduces its residual by inner_tol (0 < inner_tol < 1, e.g. 1e-4);
+ * refinement stops when the FP64 residual ||f - V64 w|| / ||f|| <= opts->tol.
+ * opts->max_iter caps the inner iterations in total; info->iterations reports
+ * them.  Workspace: stbem_solve_mixed_workspace_bytes().  Errors as
+ * stbem_solve. */
+int stbem_solve_mixed_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes);
+int stbem_solve_mixed(stbem_ctx* ctx, int n_t, int n_x, const double* dev_V64, const float* dev_V32,
+                      const float* dev_D32, const double* dev_L, const double* dev_f, double* dev_w,
+                      const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info,
+                      void* dev_work, size_t work_bytes);
+
+/* dev_dst[i] = (float)dev_src[i], i < n (rounds an FP64 operator to FP32 for
+ * the inner solves of stbem_solve_mixed; a utility with no counterpart in the
+ * paper).  Errors: STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_round_f32(stbem_ctx* ctx, size_t n, const double* dev_src, float* dev_dst);
 
 #ifdef __cplusplus
 }

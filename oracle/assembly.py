@@ -124,9 +124,12 @@ def V_entries(mesh: BoundaryMesh, d, I, J, rules=DEFAULT_RULES):
 
 # --- K_h ----------------------------------------------------------------------
 
-def K_entries(mesh: BoundaryMesh, d, I, P, rules=DEFAULT_RULES):
+def K_entries(mesh: BoundaryMesh, d, I, P, rules=DEFAULT_RULES, magnitude=False):
     """K^(d)[i][p] = sum_{j in {p-1, p}} int_{gamma_i} int_{gamma_j}
     D2_d F_K(x, y) phi_p(y) ds_y ds_x, phi_p the P1 hat at vertex p.
+
+    magnitude=True returns the sum of the absolute values of the quadrature
+    terms instead (q changes sign inside some pairs near re-entrant corners).
 
     On gamma_p the hat falls 1 -> 0, on gamma_{p-1} it rises 0 -> 1.  The
     identical pair (i == j) contributes exactly 0: x - y is tangential there,
@@ -142,7 +145,7 @@ def K_entries(mesh: BoundaryMesh, d, I, P, rules=DEFAULT_RULES):
         one = np.ones(ii.shape)
         val = pair_integrals('K', d, mesh, mesh.a[ii], mesh.b[ii], mesh.h[ii],
                              mesh.a[jj], mesh.b[jj], mesh.h[jj], mesh.n[jj], cls,
-                             one, one, w0 * one, w1 * one, rules)
+                             one, one, w0 * one, w1 * one, rules, magnitude=magnitude)
         total[keep] += val
     return total
 
@@ -217,7 +220,7 @@ def _all_pairs(N, symmetric):
 def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None, magnitude=False):
     """Lag blocks A[d][i][j] (N_t x N_x x N_x) of op in {'V', 'K', 'D'}.
 
-    magnitude=True (D only) returns the term-magnitude sums S instead."""
+    magnitude=True (K and D) returns the term-magnitude sums S instead."""
     N = mesh.N
     lags = range(mesh.n_t) if lags is None else lags
     sym = op in ('V', 'D')

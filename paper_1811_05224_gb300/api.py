@@ -154,3 +154,31 @@ def solve(ctx: Context, V, f, D=None, L=None, tol: float = 1e-8, max_iter: int =
     if code != capi.STBEM_OK and raise_on_fail:
         ctx.check(code)
     return out, res
+
+
+def round_f32(ctx: Context, A):
+    """FP32 copy of an FP64 operator (rounded by a library kernel)."""
+    out = torch.empty(A.shape, dtype=torch.float32, device=A.device)
+    ctx.check(ctx.lib.stbem_round_f32(ctx.h, A.numel(), _ptr(A), _ptr(out)))
+    return out
+
+
+def solve_mixed(ctx: Context, V64, V32, f, D32=None, L=None, tol: float = 1e-8, inner_tol: float = 1e-4,
+                max_iter: int = 500, restart: int = 200, work=None, out=None, raise_on_fail: bool = True):
+    """FP64 iterative refinement around preconditioned GMRES on FP32 operators."""
+    n_t, n_x = V64.shape[0], V64.shape[1]
+    opts = capi.SolveOpts(tol, max_iter, restart, int(D32 is not None))
+    info = capi.SolveInfo()
+    if out is None:
+        out = ctx.empty((n_t, n_x))
+    if work is None:
+        nb = ctypes.c_size_t()
+        ctx.check(ctx.lib.stbem_solve_mixed_workspace_bytes(n_t, n_x, restart, ctypes.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+    code = ctx.lib.stbem_solve_mixed(ctx.h, n_t, n_x, _ptr(V64), _ptr(V32), _ptr(D32), _ptr(L), _ptr(f),
+                                     _ptr(out), ctypes.byref(opts), float(inner_tol), ctypes.byref(info),
+                                     _ptr(work), work.numel())
+    res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
+    if code != capi.STBEM_OK and raise_on_fail:
+        ctx.check(code)
+    return out, res

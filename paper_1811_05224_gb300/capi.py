@@ -28,6 +28,7 @@ EXPORTS = [
     "stbem_version", "stbem_launch_count", "stbem_create", "stbem_destroy", "stbem_last_error", "stbem_mesh_create",
     "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_apply_workspace_bytes",
     "stbem_apply", "stbem_apply_noalloc", "stbem_rhs", "stbem_lumped_mass", "stbem_solve_workspace_bytes", "stbem_solve",
+    "stbem_solve_mixed_workspace_bytes", "stbem_solve_mixed", "stbem_round_f32",
 ]
 
 
@@ -80,6 +81,9 @@ def load(path: str = LIB_PATH):
     L.stbem_lumped_mass.argtypes = [vp, vp, vp]
     L.stbem_solve_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
+    L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
+    L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
+    L.stbem_round_f32.argtypes = [vp, sz, vp, vp]
     for name in EXPORTS:
         if name not in ("stbem_version", "stbem_launch_count", "stbem_destroy", "stbem_mesh_destroy", "stbem_last_error"):
             getattr(L, name).restype = ctypes.c_int

@@ -1,4 +1,4 @@
-// Assembly of the block-Toeplitz lag blocks of V_h, K_h and D_h (FP64).
+// Assembly of the block-Toeplitz lag blocks of V_h, K_h and D_h.
 //
 // Entries (Section 1 eq. (4); Section 2 Theorem and dual space Y_h):
 //   V^(d)[i][j] = int_{g_i} int_{g_j} D2_d F_V
@@ -9,14 +9,23 @@
 // (D in the integrated-by-parts form of the hypersingular operator, Section 2
 // citing Costabel 1990 Thm 6.1; a, b half-segments on which psi is linear).
 //
-// Two kernels per operator:
-//   * lags d >= 2: one thread per entry; tensor Gauss-Legendre of order
-//     space_order(d) on every piece pair; time by closed form or Peano form.
-//   * lags 0 and 1: one CTA per entry; pair classes select the regular, near,
-//     identical (graded diagonal) or shared-vertex (Duffy, graded) rule; the
-//     rule's points are strided over the threads and reduced in a fixed tree.
-// V^(d) and D^(d) are symmetric: the entry with the smaller index first is
-// evaluated and written to both triangles.
+// One tile kernel per operator.  A CTA owns a tile of entries at one lag and
+// first integrates every piece pair the tile needs into moments in shared
+// memory, then sums the moments of each entry:
+//   V: 16 x 16 entries = the segment pairs themselves (symmetric tiles only);
+//   K: 16 x 15 entries from 16 x 16 segment pairs, moments int k (1 - eta)
+//      and int k eta, so K[i][p] = Ma(i, p) + Mb(i, p-1);
+//   D: 16 x 16 entries from 34 x 34 half-segment pairs, moments int k_V and
+//      int k_1 times (1-xi)(1-eta), (1-xi)eta, xi(1-eta), xi eta.
+// Phase 1 gives each thread whole pairs (tensor Gauss-Legendre) in the compute
+// precision R; at lags 0 and 1 identical pieces and pieces sharing a vertex are
+// deferred to phase 2, where one warp integrates one pair with the graded /
+// Duffy rules in FP64 (the small-z E1 terms cancel there) and reduces with
+// shuffles.  V^(d) and D^(d) are symmetric: the entry with the smaller index
+// first is evaluated and written to both triangles.
+//
+// Precisions: R = double, T = double (STBEM_F64); R = float, T = float
+// (STBEM_F32: FP32 arithmetic everywhere except the deferred FP64 pairs).
 #include <cuda_runtime.h>
 
 #include "assemble.h"
@@ -26,6 +35,20 @@
 namespace stbem {
 
 __constant__ RuleTables c_tab;
+__constant__ float c_gxf[kGaussTotal];
+__constant__ float c_gwf[kGaussTotal];
+
+template <typename R> __device__ __forceinline__ R gxr(int i);
+template <> __device__ __forceinline__ double gxr<double>(int i) { return c_tab.gx[i]; }
+template <> __device__ __forceinline__ float gxr<float>(int i) { return c_gxf[i]; }
+template <typename R> __device__ __forceinline__ R gwr(int i);
+template <> __device__ __forceinline__ double gwr<double>(int i) { return c_tab.gw[i]; }
+template <> __device__ __forceinline__ float gwr<float>(int i) { return c_gwf[i]; }
+
+__device__ __forceinline__ double exp_neg(double x) { return exp_neg_fast(x); }
+__device__ __forceinline__ float exp_neg(float x) { return exp_neg_f(x); }
+__device__ __forceinline__ void e12(double z, double* a, double* b) { e1e2(z, a, b); }
+__device__ __forceinline__ void e12(float z, float* a, float* b) { e1e2_f(z, a, b); }
 
 // ---- piece access -----------------------------------------------------------
 struct Piece {
@@ -45,330 +68,7 @@ __device__ __forceinline__ Piece half_piece(const DevMesh& M, int i) {
   return p;
 }
 
-// ---- fused time kernels for D (share E1/E2 and exp between F_V and F_1) ------
-__device__ __forceinline__ void lag_kernel_D(double c, int d, double ht, double alpha,
-                                             double* outv, double* out1) {
-  const double* gx = c_tab.gx;
-  const double* gw = c_tab.gw;
-  if (d == 0) {
-    double a, b;
-    e1e2(c / ht, &a, &b);
-    *outv = ht / kFourPi * (a - b);
-    *out1 = alpha / kFourPi * a;
-    return;
-  }
-  if (d == 1) {
-    const double z = c / ht;
-    if (z < 1.0) {
-      *outv = lag1_series<kV>(z, ht, alpha);
-      *out1 = lag1_series<k1>(z, ht, alpha);
-      return;
-    }
-    double a2, b2, a1, b1;
-    e1e2(c / (2.0 * ht), &a2, &b2);
-    e1e2(c / ht, &a1, &b1);
-    *outv = (2.0 * ht) / kFourPi * (a2 - b2) - 2.0 * (ht / kFourPi * (a1 - b1));
-    *out1 = alpha / kFourPi * a2 - 2.0 * (alpha / kFourPi * a1);
-    return;
-  }
-  const double zd = c / ((double)d * ht);
-  if (zd > 0.5 * (double)d) {
-    const double s3 = (double)(d + 1) * ht, s2 = (double)d * ht, s1 = (double)(d - 1) * ht;
-    double a3, b3, a2, b2, a1, b1;
-    e1e2(c / s3, &a3, &b3);
-    e1e2(c / s2, &a2, &b2);
-    e1e2(c / s1, &a1, &b1);
-    *outv = (s3 / kFourPi * (a3 - b3) - 2.0 * (s2 / kFourPi * (a2 - b2))) + s1 / kFourPi * (a1 - b1);
-    *out1 = (alpha / kFourPi * a3 - 2.0 * (alpha / kFourPi * a2)) + alpha / kFourPi * a1;
-    return;
-  }
-  const int nl = peano_order(d - 1), nr = peano_order(d);
-  const int ol = gauss_offset(nl), orr = gauss_offset(nr);
-  double lv = 0.0, rv = 0.0, l1 = 0.0, r1 = 0.0;
-  for (int g = 0; g < nl; ++g) {
-    const double t = gx[ol + g];
-    const double s = ((double)(d - 1) + t) * ht;
-    const double e = exp(-c / s);
-    const double wt = gw[ol + g] * t;
-    lv += wt * (e / (kFourPi * s));
-    l1 += wt * (alpha / kFourPi * e * (c / (s * s * s) - 1.0 / (s * s)));
-  }
-  for (int g = 0; g < nr; ++g) {
-    const double t = gx[orr + g];
-    const double s = ((double)d + t) * ht;
-    const double e = exp(-c / s);
-    const double wt = gw[orr + g] * (1.0 - t);
-    rv += wt * (e / (kFourPi * s));
-    r1 += wt * (alpha / kFourPi * e * (c / (s * s * s) - 1.0 / (s * s)));
-  }
-  *outv = ht * ht * (lv + rv);
-  *out1 = ht * ht * (l1 + r1);
-}
-
-// ---- tensor rule on a piece pair (lags >= 2) -----------------------------------
-// Returns int_a int_b k(x,y) fa(xi) fb(eta) for kernel K (V or K/q*q).
-template <int K>
-__device__ double tensor_pair(const Piece& A, const Piece& B, double fa0, double fa1,
-                              double fb0, double fb1, int d, int n, double ht, double alpha) {
-  const int o = gauss_offset(n);
-  const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
-  const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
-  const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
-  double acc = 0.0;
-  for (int a = 0; a < n; ++a) {
-    const double xi = c_tab.gx[o + a];
-    const double wa = c_tab.gw[o + a];
-    const double fa = fa0 + (fa1 - fa0) * xi;
-    for (int b = 0; b < n; ++b) {
-      const double eta = c_tab.gx[o + b];
-      const double w = wa * c_tab.gw[o + b];
-      const double dx = (abx + xi * eax) - eta * ebx;
-      const double dy = (aby + xi * eay) - eta * eby;
-      const double r2 = dx * dx + dy * dy;
-      const double c = 0.25 * alpha * r2;
-      double k = lag_kernel<K>(c, d, ht, alpha, c_tab.gx, c_tab.gw);
-      if (K == kKq) k = (dx * B.nx + dy * B.ny) * k;
-      const double fb = fb0 + (fb1 - fb0) * eta;
-      acc += w * k * fa * fb;
-    }
-  }
-  return acc * A.len * B.len;
-}
-
-// Fused V-kernel and F_1-kernel integrals on a half-segment pair (D operator).
-__device__ void tensor_pair_D(const Piece& A, const Piece& B, double fa0, double fa1,
-                              double fb0, double fb1, int d, int n, double ht, double alpha,
-                              double* IV, double* I1) {
-  const int o = gauss_offset(n);
-  const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
-  const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
-  const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
-  double accv = 0.0, acc1 = 0.0;
-  for (int a = 0; a < n; ++a) {
-    const double xi = c_tab.gx[o + a];
-    const double wa = c_tab.gw[o + a];
-    const double fa = fa0 + (fa1 - fa0) * xi;
-    for (int b = 0; b < n; ++b) {
-      const double eta = c_tab.gx[o + b];
-      const double w = wa * c_tab.gw[o + b];
-      const double dx = (abx + xi * eax) - eta * ebx;
-      const double dy = (aby + xi * eay) - eta * eby;
-      const double c = 0.25 * alpha * (dx * dx + dy * dy);
-      double kv, k1v;
-      lag_kernel_D(c, d, ht, alpha, &kv, &k1v);
-      const double fb = fb0 + (fb1 - fb0) * eta;
-      accv += w * kv * 1.0 * 1.0;
-      acc1 += w * k1v * fa * fb;
-    }
-  }
-  *IV = accv * A.len * B.len;
-  *I1 = acc1 * A.len * B.len;
-}
-
-// ---- lags >= 2: one thread per entry ------------------------------------------
-template <int OP, typename T>
-__global__ void k_lag2(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
-  const int N = M.N;
-  const long long total = (long long)(d_end - d_begin) * N * N;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= total) return;
-  const int j = (int)(tid % N);
-  const int i = (int)((tid / N) % N);
-  const int d = d_begin + (int)(tid / ((long long)N * N));
-  const double ht = M.ht, alpha = M.alpha;
-  const int n = space_order(d);
-  double val = 0.0;
-  if (OP == STBEM_OP_V) {
-    if (i > j) return;
-    val = tensor_pair<kV>(seg_piece(M, i), seg_piece(M, j), 1.0, 1.0, 1.0, 1.0, d, n, ht, alpha);
-  } else if (OP == STBEM_OP_K) {
-    const Piece A = seg_piece(M, i);
-    const int jp = j, jm = (j - 1 + N) % N;
-    if (jp != i) val += tensor_pair<kKq>(A, seg_piece(M, jp), 1.0, 1.0, 1.0, 0.0, d, n, ht, alpha);
-    if (jm != i) val += tensor_pair<kKq>(A, seg_piece(M, jm), 1.0, 1.0, 0.0, 1.0, d, n, ht, alpha);
-  } else {
-    if (i > j) return;
-    for (int ia = 0; ia < 4; ++ia) {
-      const int pa = M.dpiece[4 * i + ia];
-      const double a0 = M.dv0[4 * i + ia], a1 = M.dv1[4 * i + ia], ca = M.dcurl[4 * i + ia];
-      const Piece A = half_piece(M, pa);
-      for (int ib = 0; ib < 4; ++ib) {
-        const int pb = M.dpiece[4 * j + ib];
-        const double b0 = M.dv0[4 * j + ib], b1 = M.dv1[4 * j + ib], cb = M.dcurl[4 * j + ib];
-        const Piece B = half_piece(M, pb);
-        double IV, I1;
-        tensor_pair_D(A, B, a0, a1, b0, b1, d, n, ht, alpha, &IV, &I1);
-        const double nn = A.nx * B.nx + A.ny * B.ny;
-        val += ca * cb * IV + nn * I1;
-      }
-    }
-  }
-  const size_t base = (size_t)d * N * N;
-  out[base + (size_t)i * N + j] = (T)val;
-  if ((OP == STBEM_OP_V || OP == STBEM_OP_D) && i != j) out[base + (size_t)j * N + i] = (T)val;
-}
-
-// ---- lags >= 2, K and D: tile kernels on piece-pair moments -------------------
-// D: a CTA owns a kDT x kDT tile of entries (l, k); the pieces of the dual
-// functions of its rows are the 2 kDT + 2 consecutive half-segments starting at
-// 2 l0 - 1 (likewise for the columns).  Per lag it integrates every half-pair
-// once into five moments -- the V kernel with weight 1 and the D time kernel
-// with the bilinear basis (1-xi)(1-eta), (1-xi)eta, xi(1-eta), xi eta -- and
-// then sums the 16 piece pairs of each entry from shared memory.
-constexpr int kDT = 16;
-constexpr int kDP = 2 * kDT + 2;          // half-segments per tile side
-constexpr int kTileThreads = 256;
-
-__device__ void pair_moments_D(const Piece& A, const Piece& B, int d, int n, double ht, double alpha,
-                               double* mom) {
-  const int o = gauss_offset(n);
-  const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
-  const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
-  const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
-  double sv = 0.0, s00 = 0.0, s01 = 0.0, s10 = 0.0, s11 = 0.0;
-  for (int a = 0; a < n; ++a) {
-    const double xi = c_tab.gx[o + a];
-    const double wa = c_tab.gw[o + a];
-    for (int b = 0; b < n; ++b) {
-      const double eta = c_tab.gx[o + b];
-      const double w = wa * c_tab.gw[o + b];
-      const double dx = (abx + xi * eax) - eta * ebx;
-      const double dy = (aby + xi * eay) - eta * eby;
-      const double c = 0.25 * alpha * (dx * dx + dy * dy);
-      double kv, k1v;
-      lag_kernel_D(c, d, ht, alpha, &kv, &k1v);
-      sv += w * kv;
-      const double wk = w * k1v;
-      s00 += wk * (1.0 - xi) * (1.0 - eta);
-      s01 += wk * (1.0 - xi) * eta;
-      s10 += wk * xi * (1.0 - eta);
-      s11 += wk * xi * eta;
-    }
-  }
-  const double L = A.len * B.len;
-  mom[0] = sv * L; mom[1] = s00 * L; mom[2] = s01 * L; mom[3] = s10 * L; mom[4] = s11 * L;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kTileThreads) k_lag2_D(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
-  __shared__ double mom[kDP * kDP][5];
-  const int N = M.N, H = 2 * N;
-  // upper-triangular tile pair from the linear block index
-  int lt = 0, rem = blockIdx.x;
-  const int nT = (N + kDT - 1) / kDT;
-  while (rem >= nT - lt) { rem -= nT - lt; ++lt; }
-  const int kt = lt + rem;
-  const int l0 = lt * kDT, k0 = kt * kDT;
-  const int tid = threadIdx.x;
-  const double ht = M.ht, alpha = M.alpha;
-  for (int d = d_begin + blockIdx.y; d < d_end; d += gridDim.y) {
-    const int n = space_order(d);
-    for (int p = tid; p < kDP * kDP; p += kTileThreads) {
-      const int u = p / kDP, v = p % kDP;
-      const int ga = ((2 * l0 - 1 + u) % H + H) % H;
-      const int gb = ((2 * k0 - 1 + v) % H + H) % H;
-      pair_moments_D(half_piece(M, ga), half_piece(M, gb), d, n, ht, alpha, mom[p]);
-    }
-    __syncthreads();
-    if (tid < kDT * kDT) {
-      const int s = tid / kDT, t = tid % kDT;
-      const int l = l0 + s, k = k0 + t;
-      // evaluate the smaller index first (symmetric block): on the diagonal
-      // tile both ranges coincide, so (lo, hi) local offsets exist
-      const int lo = l < k ? l : k, hi = l < k ? k : l;
-      const int so = lo - l0, to = hi - k0;
-      if (l < N && k < N && so >= 0 && to >= 0 && so < kDT && to < kDT) {
-        double val = 0.0;
-        for (int ia = 0; ia < 4; ++ia) {
-          const int qa = 4 * lo + ia;
-          const double ca = M.dcurl[qa], a0 = M.dv0[qa], a1 = M.dv1[qa];
-          const int u = 2 * so + ia;
-          const int ga = M.dpiece[qa];
-          const double nax = M.hnx[ga], nay = M.hny[ga];
-          for (int ib = 0; ib < 4; ++ib) {
-            const int qb = 4 * hi + ib;
-            const double cb = M.dcurl[qb], b0 = M.dv0[qb], b1 = M.dv1[qb];
-            const int v = 2 * to + ib;
-            const int gb = M.dpiece[qb];
-            const double nn = nax * M.hnx[gb] + nay * M.hny[gb];
-            const double* m = mom[u * kDP + v];
-            const double I1 = a0 * (b0 * m[1] + b1 * m[2]) + a1 * (b0 * m[3] + b1 * m[4]);
-            val += ca * cb * m[0] + nn * I1;
-          }
-        }
-        const size_t base = (size_t)d * N * N;
-        out[base + (size_t)l * N + k] = (T)val;
-        if (lt != kt) out[base + (size_t)k * N + l] = (T)val;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// K: a CTA owns kKI x kKP entries (i, p); the trial segments are p0-1 .. p0+kKP-1.
-// Moments per segment pair (i, j): int k (1 - eta) and int k eta, so that
-// K[i][p] = Ma(i, p) + Mb(i, p-1) (identical pairs contribute 0).
-constexpr int kKI = 16, kKP = 15, kKJ = kKP + 1;
-
-template <typename T>
-__global__ void __launch_bounds__(kTileThreads) k_lag2_K(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
-  __shared__ double mom[kKI * kKJ][2];
-  const int N = M.N;
-  const int nP = (N + kKP - 1) / kKP;
-  const int it = blockIdx.x / nP, pt = blockIdx.x % nP;
-  const int i0 = it * kKI, p0 = pt * kKP;
-  const int tid = threadIdx.x;
-  const double ht = M.ht, alpha = M.alpha;
-  for (int d = d_begin + blockIdx.y; d < d_end; d += gridDim.y) {
-    const int n = space_order(d);
-    const int o = gauss_offset(n);
-    for (int p = tid; p < kKI * kKJ; p += kTileThreads) {
-      const int si = p / kKJ, sj = p % kKJ;
-      const int i = i0 + si;
-      const int j = ((p0 - 1 + sj) % N + N) % N;
-      double ma = 0.0, mb = 0.0;
-      if (i < N && j != i) {
-        const Piece A = seg_piece(M, i), B = seg_piece(M, j);
-        const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
-        const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
-        const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
-        for (int a = 0; a < n; ++a) {
-          const double xi = c_tab.gx[o + a];
-          const double wa = c_tab.gw[o + a];
-          for (int b = 0; b < n; ++b) {
-            const double eta = c_tab.gx[o + b];
-            const double w = wa * c_tab.gw[o + b];
-            const double dx = (abx + xi * eax) - eta * ebx;
-            const double dy = (aby + xi * eay) - eta * eby;
-            const double c = 0.25 * alpha * (dx * dx + dy * dy);
-            const double k = (dx * B.nx + dy * B.ny) * lag_kernel<kKq>(c, d, ht, alpha, c_tab.gx, c_tab.gw);
-            const double wk = w * k;
-            ma += wk * (1.0 - eta);
-            mb += wk * eta;
-          }
-        }
-        ma *= A.len * B.len;
-        mb *= A.len * B.len;
-      }
-      mom[p][0] = ma;
-      mom[p][1] = mb;
-    }
-    __syncthreads();
-    if (tid < kKI * kKP) {
-      const int si = tid / kKP, sp = tid % kKP;
-      const int i = i0 + si, p = p0 + sp;
-      if (i < N && p < N) {
-        const double val = mom[si * kKJ + sp + 1][0] + mom[si * kKJ + sp][1];
-        out[(size_t)d * N * N + (size_t)i * N + p] = (T)val;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// ---- lags 0, 1: one CTA per entry -----------------------------------------------
-constexpr int kLag01Threads = 128;
-
+// ---- pair classes (lags 0 and 1) ----------------------------------------------
 __device__ double point_seg_dist(double px, double py, double sx0, double sy0, double sx1, double sy1) {
   const double ex = sx1 - sx0, ey = sy1 - sy0;
   const double L2 = ex * ex + ey * ey;
@@ -378,13 +78,13 @@ __device__ double point_seg_dist(double px, double py, double sx0, double sy0, d
   return sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy));
 }
 
-// Pair class on a closed ring of R pieces (piece k ends where k+1 starts).
-__device__ int pair_class(int R, int ia, int ib, const Piece& A, const Piece& B) {
-  const int diff = ((ib - ia) % R + R) % R;
+// Pair class on a closed ring of Rl pieces (piece k ends where k+1 starts).
+__device__ int pair_class(int Rl, int ia, int ib, const Piece& A, const Piece& B) {
+  const int diff = ((ib - ia) % Rl + Rl) % Rl;
   if (diff == 0) return kIdentical;
   if (diff == 1) return kAdjNext;
-  if (diff == R - 1) return kAdjPrev;
-  const int rd = diff < R - diff ? diff : R - diff;
+  if (diff == Rl - 1) return kAdjPrev;
+  const int rd = diff < Rl - diff ? diff : Rl - diff;
   if (rd == 2) return kNear;
   double g = point_seg_dist(A.x0, A.y0, B.x0, B.y0, B.x1, B.y1);
   g = fmin(g, point_seg_dist(A.x1, A.y1, B.x0, B.y0, B.x1, B.y1));
@@ -393,36 +93,21 @@ __device__ int pair_class(int R, int ia, int ib, const Piece& A, const Piece& B)
   return g < kNearGapRatio * fmax(A.len, B.len) ? kNear : kRegular;
 }
 
-__device__ __forceinline__ int class_points(int cls) {
-  if (cls == kRegular) return kRegular01 * kRegular01;
-  if (cls == kNear) return kNear01 * kNear01;
-  if (cls == kIdentical) return 2 * kGradedN * kSingularInner;
-  return 2 * kGradedN * kDuffyAngular;
+__device__ __forceinline__ int singular_points(int cls) {
+  return cls == kIdentical ? 2 * kGradedN * kSingularInner : 2 * kGradedN * kDuffyAngular;
 }
 
-// Point `p` of the class rule: local parameters (xi, eta), weight, and x - y.
-__device__ __forceinline__ void class_point(int cls, int p, const Piece& A, const Piece& B,
-                                            const double* grx, const double* grw,
-                                            double* xi, double* eta, double* w, double* dx, double* dy) {
+// Point p of the identical / shared-vertex rule: (xi, eta), weight, x - y.
+__device__ __forceinline__ void singular_point(int cls, int p, const Piece& A, const Piece& B,
+                                               double* xi, double* eta, double* w, double* dx, double* dy) {
   const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
   const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
-  if (cls == kRegular || cls == kNear) {
-    const int n = cls == kRegular ? kRegular01 : kNear01;
-    const int o = gauss_offset(n);
-    const int a = p / n, b = p % n;
-    *xi = c_tab.gx[o + a];
-    *eta = c_tab.gx[o + b];
-    *w = c_tab.gw[o + a] * c_tab.gw[o + b];
-    *dx = ((A.x0 - B.x0) + *xi * eax) - *eta * ebx;
-    *dy = ((A.y0 - B.y0) + *xi * eay) - *eta * eby;
-    return;
-  }
   if (cls == kIdentical) {
     const int per = kGradedN * kSingularInner;
     const int tri = p / per, rem = p % per;
     const int iu = rem / kSingularInner, it = rem % kSingularInner;
     const int o4 = gauss_offset(kSingularInner);
-    const double U = grx[iu], WU = grw[iu];
+    const double U = c_tab.grx[iu], WU = c_tab.grw[iu];
     const double TA = c_tab.gx[o4 + it], WT = c_tab.gw[o4 + it];
     const double lo = (1.0 - U) * TA;
     *w = WU * WT * (1.0 - U);
@@ -437,11 +122,11 @@ __device__ __forceinline__ void class_point(int cls, int p, const Piece& A, cons
   const int tri = p / per, rem = p % per;
   const int ir = rem / kDuffyAngular, it = rem % kDuffyAngular;
   const int o16 = gauss_offset(kDuffyAngular);
-  const double R = grx[ir], WR = grw[ir];
+  const double Rr = c_tab.grx[ir], WR = c_tab.grw[ir];
   const double T = c_tab.gx[o16 + it], WT = c_tab.gw[o16 + it];
-  *w = WR * WT * R;
-  const double xp = tri == 0 ? R : R * T;
-  const double ep = tri == 0 ? R * T : R;
+  *w = WR * WT * Rr;
+  const double xp = tri == 0 ? Rr : Rr * T;
+  const double ep = tri == 0 ? Rr * T : Rr;
   if (cls == kAdjNext) {   // end of A == start of B
     *xi = 1.0 - xp;
     *eta = ep;
@@ -455,138 +140,536 @@ __device__ __forceinline__ void class_point(int cls, int p, const Piece& A, cons
   }
 }
 
-__device__ double block_sum(double v, double* red) {
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = kLag01Threads / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
+// ---- FP64 lag-0/1 kernels for D (share E1/E2 between F_V and F_1) ----------------
+__device__ __forceinline__ void lag01_D64(double c, int d, double ht, double alpha, double* outv, double* out1) {
+  if (d == 0) {
+    double a, b;
+    e1e2(c / ht, &a, &b);
+    *outv = ht / kFourPi * (a - b);
+    *out1 = alpha / kFourPi * a;
+    return;
   }
-  const double r = red[0];
-  __syncthreads();
-  return r;
+  const double z = c / ht;
+  if (z < 1.0) {
+    *outv = lag1_series<kV>(z, ht, alpha);
+    *out1 = lag1_series<k1>(z, ht, alpha);
+    return;
+  }
+  double a2, b2, a1, b1;
+  e1e2(c / (2.0 * ht), &a2, &b2);
+  e1e2(c / ht, &a1, &b1);
+  *outv = (2.0 * ht) / kFourPi * (a2 - b2) - 2.0 * (ht / kFourPi * (a1 - b1));
+  *out1 = alpha / kFourPi * a2 - 2.0 * (alpha / kFourPi * a1);
 }
 
-// Integral of the lag-0/1 kernel(s) over one piece pair with class rules.
+// ---- FP32 lag-0/1 kernels (regular and near pairs of the mixed precision) --------
 template <int K>
-__device__ void class_pair(const Piece& A, const Piece& B, int cls, double fa0, double fa1,
-                           double fb0, double fb1, int d, double ht, double alpha,
-                           const double* grx, const double* grw, double* red,
-                           double* out0, double* out1) {
-  const int np = class_points(cls);
-  double s0 = 0.0, s1 = 0.0;
-  for (int p = threadIdx.x; p < np; p += kLag01Threads) {
-    double xi, eta, w, dx, dy;
-    class_point(cls, p, A, B, grx, grw, &xi, &eta, &w, &dx, &dy);
-    const double c = 0.25 * alpha * (dx * dx + dy * dy);
-    const double fa = fa0 + (fa1 - fa0) * xi;
-    const double fb = fb0 + (fb1 - fb0) * eta;
-    if (K == k1) {   // D: both kernels
-      double kv, k1v;
-      lag_kernel_D(c, d, ht, alpha, &kv, &k1v);
-      s0 += w * kv * 1.0 * 1.0;
-      s1 += w * k1v * fa * fb;
-    } else {
-      double k = lag_kernel<K>(c, d, ht, alpha, c_tab.gx, c_tab.gw);
-      if (K == kKq) k = (dx * B.nx + dy * B.ny) * k;
-      s0 += w * k * fa * fb;
-    }
+__device__ __forceinline__ float lag01_f(float c, int d, float ht, float alpha) {
+  const float four_pi = (float)kFourPi;
+  const float z = c * (1.0f / ht);
+  if (d == 0) {
+    float a, b;
+    e1e2_f(z, &a, &b);
+    if (K == kV) return ht / four_pi * (a - b);
+    if (K == kKq) return alpha / (2.0f * four_pi * z) * b;
+    return alpha / four_pi * a;
   }
-  *out0 = block_sum(s0, red) * A.len * B.len;
-  if (K == k1) *out1 = block_sum(s1, red) * A.len * B.len;
+  if (z < 1.0f) {
+    const float eh = ein_series_f(0.5f * z), ef = ein_series_f(z);
+    const float g = (float)kEulerGamma, l2z = logf(2.0f * z);
+    const float em = exp_neg_f(0.5f * z) * expm1f(-0.5f * z);
+    if (K == kV) return ht / (2.0f * (float)kPi) * (0.69314718f + eh - ef + 0.5f * z * (g + l2z + eh - 2.0f * ef) + em);
+    if (K == kKq) return alpha / four_pi * (-em / z - 0.5f * (g + l2z) - 0.5f * eh + ef);
+    return alpha / four_pi * (g + l2z + eh - 2.0f * ef);
+  }
+  float a2, b2, a1, b1;
+  e1e2_f(0.5f * z, &a2, &b2);
+  e1e2_f(z, &a1, &b1);
+  if (K == kV) return (2.0f * ht) / four_pi * (a2 - b2) - 2.0f * (ht / four_pi * (a1 - b1));
+  if (K == kKq) return alpha / (four_pi * z) * (b2 - b1);   // 2 ht alpha / (8 pi c)
+  return alpha / four_pi * a2 - 2.0f * (alpha / four_pi * a1);
 }
 
-template <int OP, typename T>
-__global__ void __launch_bounds__(kLag01Threads) k_lag01(DevMesh M, T* __restrict__ out) {
-  __shared__ double grx[kGradedN], grw[kGradedN];
-  __shared__ double red[kLag01Threads];
-  const int N = M.N;
-  const int e = blockIdx.x;
-  const int i = e / N, j = e % N;
-  const int d = blockIdx.y;
-  if ((OP == STBEM_OP_V || OP == STBEM_OP_D) && i > j) return;
-  for (int t = threadIdx.x; t < kGradedN; t += kLag01Threads) {
-    grx[t] = c_tab.grx[t];
-    grw[t] = c_tab.grw[t];
-  }
-  __syncthreads();
-  const double ht = M.ht, alpha = M.alpha;
-  double val = 0.0, dummy;
-  if (OP == STBEM_OP_V) {
-    const Piece A = seg_piece(M, i), B = seg_piece(M, j);
-    const int cls = pair_class(N, i, j, A, B);
-    class_pair<kV>(A, B, cls, 1.0, 1.0, 1.0, 1.0, d, ht, alpha, grx, grw, red, &val, &dummy);
-  } else if (OP == STBEM_OP_K) {
-    const Piece A = seg_piece(M, i);
-    const int js[2] = {j, (j - 1 + N) % N};
-    const double w0[2] = {1.0, 0.0}, w1[2] = {0.0, 1.0};
-    for (int t = 0; t < 2; ++t) {
-      if (js[t] == i) continue;
-      const Piece B = seg_piece(M, js[t]);
-      const int cls = pair_class(N, i, js[t], A, B);
-      double v;
-      class_pair<kKq>(A, B, cls, 1.0, 1.0, w0[t], w1[t], d, ht, alpha, grx, grw, red, &v, &dummy);
-      val += v;
-    }
+// precision-generic lag-0/1 evaluation
+template <typename R, int K>
+__device__ __forceinline__ R lag01(R c, int d, double ht, double alpha) {
+  if constexpr (sizeof(R) == 8) return lag_kernel<K>(c, d, ht, alpha, c_tab.gx, c_tab.gw);
+  else return lag01_f<K>(c, d, (float)ht, (float)alpha);
+}
+template <typename R>
+__device__ __forceinline__ void lag01D(R c, int d, double ht, double alpha, R* kv, R* k1v) {
+  if constexpr (sizeof(R) == 8) {
+    lag01_D64(c, d, ht, alpha, kv, k1v);
   } else {
-    for (int ia = 0; ia < 4; ++ia) {
-      const int pa = M.dpiece[4 * i + ia];
-      const double a0 = M.dv0[4 * i + ia], a1 = M.dv1[4 * i + ia], ca = M.dcurl[4 * i + ia];
-      const Piece A = half_piece(M, pa);
-      for (int ib = 0; ib < 4; ++ib) {
-        const int pb = M.dpiece[4 * j + ib];
-        const double b0 = M.dv0[4 * j + ib], b1 = M.dv1[4 * j + ib], cb = M.dcurl[4 * j + ib];
-        const Piece B = half_piece(M, pb);
-        const int cls = pair_class(2 * N, pa, pb, A, B);
-        double IV, I1;
-        class_pair<k1>(A, B, cls, a0, a1, b0, b1, d, ht, alpha, grx, grw, red, &IV, &I1);
-        const double nn = A.nx * B.nx + A.ny * B.ny;
-        val += ca * cb * IV + nn * I1;
+    *kv = lag01_f<kV>(c, d, (float)ht, (float)alpha);
+    *k1v = lag01_f<k1>(c, d, (float)ht, (float)alpha);
+  }
+}
+
+// ---- per-lag time-node tables (lags >= 2) ----------------------------------------
+// For one lag d every Peano node s_g and its weight are shared by all points
+// and pairs, so they are tabulated once per CTA with sigma = 1/s folded into
+// the weights; a node then costs one exp and a few multiply-adds:
+//   Peano V  = sum_g wv_g e_g,           wv = ht^2 wt sigma / (4 pi)
+//   Peano K/q= sum_g wk_g e_g,           wk = ht^2 wt alpha sigma^2 / (8 pi)
+//   Peano D1 = sum_g e_g (w3_g c - w2_g), w3 = ht^2 wt alpha sigma^3/(4 pi), w2 = .. sigma^2
+// with e_g = exp(-c sigma_g), wt = Gauss weight x hat (tau on the left interval,
+// 1 - tau on the right).  The closed form uses the node reciprocals 1/s too.
+// Tables are computed in FP64 and stored in the compute precision R.
+constexpr int kMaxNodes = 32;
+template <typename R>
+struct LagNodes {
+  int n;                      // total nodes (left + right interval)
+  R inv_dht;                  // 1 / (d ht): the closed/Peano switch
+  R s[3], inv_s[3];           // (d+1) ht, d ht, (d-1) ht and reciprocals
+  R sig[kMaxNodes], wv[kMaxNodes], wk[kMaxNodes], w3[kMaxNodes], w2[kMaxNodes];
+};
+
+template <typename R>
+__device__ void build_lag_nodes(LagNodes<R>& L, int d, double ht, double alpha) {
+  const int nl = peano_order(d - 1), nr = peano_order(d);
+  const int ol = gauss_offset(nl), orr = gauss_offset(nr);
+  for (int g = threadIdx.x; g < nl + nr; g += blockDim.x) {
+    double t, wt, s;
+    if (g < nl) {
+      t = c_tab.gx[ol + g];
+      wt = c_tab.gw[ol + g] * t;
+      s = ((double)(d - 1) + t) * ht;
+    } else {
+      t = c_tab.gx[orr + g - nl];
+      wt = c_tab.gw[orr + g - nl] * (1.0 - t);
+      s = ((double)d + t) * ht;
+    }
+    const double sig = 1.0 / s;
+    const double base = ht * ht * wt;
+    L.sig[g] = (R)sig;
+    L.wv[g] = (R)(base * sig / kFourPi);
+    L.wk[g] = (R)(base * alpha * sig * sig / (2.0 * kFourPi));
+    L.w3[g] = (R)(base * alpha * sig * sig * sig / kFourPi);
+    L.w2[g] = (R)(base * alpha * sig * sig / kFourPi);
+  }
+  if (threadIdx.x == 0) {
+    L.n = nl + nr;
+    L.inv_dht = (R)(1.0 / ((double)d * ht));
+    const double s3[3] = {(double)(d + 1) * ht, (double)d * ht, (double)(d - 1) * ht};
+    for (int k = 0; k < 3; ++k) {
+      L.s[k] = (R)s3[k];
+      L.inv_s[k] = (R)(1.0 / s3[k]);
+    }
+  }
+}
+
+// D2_d F_V (K = kV) or D2_d F_K / q (K = kKq) at lag d >= 2 from the tables.
+template <typename R, int K>
+__device__ __forceinline__ R lag2_kernel(R c, int d, R alpha, const LagNodes<R>& L) {
+  const R four_pi = (R)kFourPi;
+  if (c * L.inv_dht > (R)0.5 * (R)d) {
+    R f[3];
+    for (int k = 0; k < 3; ++k) {
+      R a, b;
+      e12(c * L.inv_s[k], &a, &b);
+      f[k] = K == kV ? L.s[k] / four_pi * (a - b) : alpha / ((R)2 * four_pi * c) * L.s[k] * b;
+    }
+    return (f[0] - (R)2 * f[1]) + f[2];
+  }
+  R acc = (R)0;
+  for (int g = 0; g < L.n; ++g) {
+    const R e = exp_neg(c * L.sig[g]);
+    acc = fma(K == kV ? L.wv[g] : L.wk[g], e, acc);
+  }
+  return acc;
+}
+
+template <typename R>
+__device__ __forceinline__ void lag2_kernel_D(R c, int d, R alpha, const LagNodes<R>& L, R* outv, R* out1) {
+  const R four_pi = (R)kFourPi;
+  if (c * L.inv_dht > (R)0.5 * (R)d) {
+    R fv[3], f1[3];
+    for (int k = 0; k < 3; ++k) {
+      R a, b;
+      e12(c * L.inv_s[k], &a, &b);
+      fv[k] = L.s[k] / four_pi * (a - b);
+      f1[k] = alpha / four_pi * a;
+    }
+    *outv = (fv[0] - (R)2 * fv[1]) + fv[2];
+    *out1 = (f1[0] - (R)2 * f1[1]) + f1[2];
+    return;
+  }
+  R av = (R)0, a1 = (R)0;
+  for (int g = 0; g < L.n; ++g) {
+    const R e = exp_neg(c * L.sig[g]);
+    av = fma(L.wv[g], e, av);
+    a1 = fma(e, fma(L.w3[g], c, -L.w2[g]), a1);
+  }
+  *outv = av;
+  *out1 = a1;
+}
+
+// ---- moments of one piece pair with a tensor Gauss rule (phase 1) ----------------
+template <int OP> struct NMom { static constexpr int n = OP == STBEM_OP_V ? 1 : (OP == STBEM_OP_K ? 2 : 5); };
+
+template <typename R, int OP, bool LAG01>
+__device__ void tensor_moments_impl(const Piece& A, const Piece& B, int d, int n, double ht, double alpha,
+                                    const LagNodes<R>* LN, double* mom) {
+  const int o = gauss_offset(n);
+  const R eax = (R)(A.x1 - A.x0), eay = (R)(A.y1 - A.y0);
+  const R ebx = (R)(B.x1 - B.x0), eby = (R)(B.y1 - B.y0);
+  const R abx = (R)(A.x0 - B.x0), aby = (R)(A.y0 - B.y0);
+  // q = (x - y) . n_b = (A0 - B0) . n_b + xi (e_a . n_b): the trial edge is
+  // orthogonal to its own normal, so the eta term drops out exactly
+  const R qab = (R)((A.x0 - B.x0) * B.nx + (A.y0 - B.y0) * B.ny);
+  const R qea = (R)((A.x1 - A.x0) * B.nx + (A.y1 - A.y0) * B.ny);
+  const R qa = (R)(0.25 * alpha);
+  const R al = (R)alpha;
+  R s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+  for (int a = 0; a < n; ++a) {
+    const R xi = gxr<R>(o + a);
+    const R wa = gwr<R>(o + a);
+    for (int b = 0; b < n; ++b) {
+      const R eta = gxr<R>(o + b);
+      const R w = wa * gwr<R>(o + b);
+      const R dx = (abx + xi * eax) - eta * ebx;
+      const R dy = (aby + xi * eay) - eta * eby;
+      const R c = qa * (dx * dx + dy * dy);
+      if constexpr (OP == STBEM_OP_V) {
+        R k;
+        if constexpr (LAG01) k = lag01<R, kV>(c, d, ht, alpha);
+        else k = lag2_kernel<R, kV>(c, d, al, *LN);
+        s0 += w * k;
+      } else if constexpr (OP == STBEM_OP_K) {
+        R kq;
+        if constexpr (LAG01) kq = lag01<R, kKq>(c, d, ht, alpha);
+        else kq = lag2_kernel<R, kKq>(c, d, al, *LN);
+        const R wk = w * ((qab + xi * qea) * kq);
+        s0 += wk * ((R)1 - eta);
+        s1 += wk * eta;
+      } else {
+        R kv, k1v;
+        if constexpr (LAG01) lag01D<R>(c, d, ht, alpha, &kv, &k1v);
+        else lag2_kernel_D<R>(c, d, al, *LN, &kv, &k1v);
+        s0 += w * kv;
+        const R wk = w * k1v;
+        s1 += wk * ((R)1 - xi) * ((R)1 - eta);
+        s2 += wk * ((R)1 - xi) * eta;
+        s3 += wk * xi * ((R)1 - eta);
+        s4 += wk * xi * eta;
       }
     }
   }
-  if (threadIdx.x == 0) {
-    const size_t base = (size_t)d * N * N;
-    out[base + (size_t)i * N + j] = (T)val;
-    if ((OP == STBEM_OP_V || OP == STBEM_OP_D) && i != j) out[base + (size_t)j * N + i] = (T)val;
+  const double L = A.len * B.len;
+  mom[0] = (double)s0 * L;
+  if (NMom<OP>::n > 1) mom[1] = (double)s1 * L;
+  if (NMom<OP>::n > 2) {
+    mom[2] = (double)s2 * L;
+    mom[3] = (double)s3 * L;
+    mom[4] = (double)s4 * L;
+  }
+}
+
+// ---- moments of one singular pair, FP64 (lags 0 and 1) ------------------------------
+// One CTA per identical or vertex-sharing pair at lag 0 or 1; the rule's
+// points are strided over the threads and reduced in a fixed tree, so the
+// moments do not depend on scheduling.  Slots: identical pairs (i, i) at
+// [0, R), (i, i+1) at [R, 2R), (i, i-1) at [2R, 3R) of the ring of R pieces.
+constexpr int kSingThreads = 128;
+
+template <int OP>
+__global__ void __launch_bounds__(kSingThreads) k_singular(DevMesh M, double* __restrict__ buf) {
+  __shared__ double red[5][kSingThreads];
+  constexpr int NM = NMom<OP>::n;
+  const int N = M.N;
+  const int Rl = OP == STBEM_OP_D ? 2 * N : N;
+  const int slot = blockIdx.x, d = blockIdx.y;
+  const int kind = slot / Rl, i = slot % Rl;
+  const int cls = kind == 0 ? kIdentical : (kind == 1 ? kAdjNext : kAdjPrev);
+  const int j = kind == 0 ? i : (kind == 1 ? (i + 1) % Rl : (i - 1 + Rl) % Rl);
+  const double ht = M.ht, alpha = M.alpha;
+  const Piece A = OP == STBEM_OP_D ? half_piece(M, i) : seg_piece(M, i);
+  const Piece B = OP == STBEM_OP_D ? half_piece(M, j) : seg_piece(M, j);
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  // the identical pair of K contributes nothing (q = 0 on a straight segment)
+  if (!(OP == STBEM_OP_K && kind == 0)) {
+    const int np = singular_points(cls);
+    for (int p = threadIdx.x; p < np; p += kSingThreads) {
+      double xi, eta, w, dx, dy;
+      singular_point(cls, p, A, B, &xi, &eta, &w, &dx, &dy);
+      const double c = 0.25 * alpha * (dx * dx + dy * dy);
+      if constexpr (OP == STBEM_OP_V) {
+        s[0] += w * lag_kernel<kV>(c, d, ht, alpha, c_tab.gx, c_tab.gw);
+      } else if constexpr (OP == STBEM_OP_K) {
+        const double wk = w * ((dx * B.nx + dy * B.ny) * lag_kernel<kKq>(c, d, ht, alpha, c_tab.gx, c_tab.gw));
+        s[0] += wk * (1.0 - eta);
+        s[1] += wk * eta;
+      } else {
+        double kv, k1v;
+        lag01_D64(c, d, ht, alpha, &kv, &k1v);
+        s[0] += w * kv;
+        const double wk = w * k1v;
+        s[1] += wk * (1.0 - xi) * (1.0 - eta);
+        s[2] += wk * (1.0 - xi) * eta;
+        s[3] += wk * xi * (1.0 - eta);
+        s[4] += wk * xi * eta;
+      }
+    }
+  }
+  for (int q = 0; q < NM; ++q) red[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int w = kSingThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < NM; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) {
+    const double L = A.len * B.len;
+    buf[((size_t)d * 3 * Rl + slot) * 5 + threadIdx.x] = (int)threadIdx.x < NM ? red[threadIdx.x][0] * L : 0.0;
+  }
+}
+
+// V, lags >= 2: one thread per upper-triangle entry, one lag per block row.
+template <typename R, typename T>
+__global__ void __launch_bounds__(128) k_lag2_V(DevMesh M, int d_begin, T* __restrict__ out) {
+  __shared__ LagNodes<R> LN;
+  const int N = M.N;
+  const int d = d_begin + blockIdx.y;
+  build_lag_nodes<R>(LN, d, M.ht, M.alpha);
+  __syncthreads();
+  const long long npair = (long long)N * (N + 1) / 2;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  // row i of the upper triangle: rows < i hold S(i) = i N - i (i - 1) / 2 entries
+  const double B2 = 2.0 * N + 1.0;
+  int i = (int)floor((B2 - sqrt(B2 * B2 - 8.0 * (double)p)) * 0.5);
+  auto S = [N](long long r) { return r * N - r * (r - 1) / 2; };
+  while (i > 0 && S(i) > p) --i;
+  while (S(i + 1) <= p) ++i;
+  const int j = i + (int)(p - S(i));
+  double m[1];
+  tensor_moments_impl<R, STBEM_OP_V, false>(seg_piece(M, i), seg_piece(M, j), d, space_order(d), M.ht, M.alpha,
+                                            &LN, m);
+  const size_t base = (size_t)d * N * N;
+  out[base + (size_t)i * N + j] = (T)m[0];
+  if (i != j) out[base + (size_t)j * N + i] = (T)m[0];
+}
+
+// ---- tile geometry -----------------------------------------------------------------
+constexpr int kTileThreads = 256;
+constexpr int kT = 16;                 // entries per tile side (V, D); K rows
+constexpr int kKP = 15, kKJ = kKP + 1; // K: entry columns, trial segment columns
+constexpr int kDP = 2 * kT + 2;        // D: half-segments per tile side
+
+template <int OP> struct Tile {
+  static constexpr int pairs = OP == STBEM_OP_V ? kT * kT : (OP == STBEM_OP_K ? kT * kKJ : kDP * kDP);
+  static constexpr int nm = NMom<OP>::n;
+};
+
+template <int OP, typename R>
+constexpr size_t tile_smem_bytes() {
+  return (((size_t)Tile<OP>::pairs * Tile<OP>::nm * sizeof(double) + 15) / 16) * 16 + sizeof(LagNodes<R>);
+}
+
+// Decode the tile of block x: symmetric operators use upper-triangular tile pairs.
+__device__ __forceinline__ void upper_tile(int bx, int nT, int* rt, int* ct) {
+  int r = 0, rem = bx;
+  while (rem >= nT - r) {
+    rem -= nT - r;
+    ++r;
+  }
+  *rt = r;
+  *ct = r + rem;
+}
+
+// Pieces of tile pair p (phase 1 and 2 share this map); false if the pair
+// contributes nothing.
+template <int OP>
+__device__ __forceinline__ bool tile_pair(const DevMesh& M, int r0, int c0, int p, Piece* A, Piece* B,
+                                          int* ia, int* ib, int* ring) {
+  const int N = M.N;
+  if (OP == STBEM_OP_V) {
+    const int i = r0 + p / kT, j = c0 + p % kT;
+    if (i >= N || j >= N) return false;
+    *ia = i < j ? i : j;
+    *ib = i < j ? j : i;
+    *A = seg_piece(M, *ia);
+    *B = seg_piece(M, *ib);
+    *ring = N;
+    return true;
+  } else if (OP == STBEM_OP_K) {
+    const int i = r0 + p / kKJ;
+    const int j = ((c0 - 1 + p % kKJ) % N + N) % N;
+    if (i >= N || j == i) return false;       // identical pair: q = 0
+    *ia = i;
+    *ib = j;
+    *A = seg_piece(M, i);
+    *B = seg_piece(M, j);
+    *ring = N;
+    return true;
+  } else {
+    const int H = 2 * N;
+    *ia = ((2 * r0 - 1 + p / kDP) % H + H) % H;
+    *ib = ((2 * c0 - 1 + p % kDP) % H + H) % H;
+    *A = half_piece(M, *ia);
+    *B = half_piece(M, *ib);
+    *ring = H;
+    return true;
+  }
+}
+
+// Slot of a singular pair in the lag-0/1 moment buffer: ring R pieces,
+// identical pairs at [0, R), (i, i+1) at [R, 2R), (i, i-1) at [2R, 3R).
+__device__ __forceinline__ int singular_slot(int cls, int ia, int Rl) {
+  return cls == kIdentical ? ia : (cls == kAdjNext ? Rl + ia : 2 * Rl + ia);
+}
+
+template <int OP, typename R, typename T, bool LAG01>
+__global__ void __launch_bounds__(kTileThreads) k_tile(DevMesh M, int d_begin, const double* __restrict__ sing,
+                                                       T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int P = Tile<OP>::pairs, NM = Tile<OP>::nm;
+  double* mom = reinterpret_cast<double*>(smem_raw);
+  LagNodes<R>* LN = reinterpret_cast<LagNodes<R>*>(smem_raw + (((size_t)P * NM * sizeof(double) + 15) / 16) * 16);
+
+  const int N = M.N;
+  const int d = d_begin + blockIdx.y;
+  const double ht = M.ht, alpha = M.alpha;
+  int rt, ct;
+  if (OP == STBEM_OP_K) {
+    const int nP = (N + kKP - 1) / kKP;
+    rt = blockIdx.x / nP;
+    ct = blockIdx.x % nP;
+  } else {
+    upper_tile(blockIdx.x, (N + kT - 1) / kT, &rt, &ct);
+  }
+  const int r0 = rt * kT, c0 = ct * (OP == STBEM_OP_K ? kKP : kT);
+  const int tid = threadIdx.x;
+  if (!LAG01) build_lag_nodes<R>(*LN, d, ht, alpha);
+  __syncthreads();
+
+  // phase 1: whole pairs per thread; at lags 0 and 1 the identical and
+  // vertex-sharing pairs take their FP64 moments from k_singular's buffer
+  for (int p = tid; p < P; p += kTileThreads) {
+    Piece A, B;
+    int ia, ib, ring;
+    double* m = mom + (size_t)p * NM;
+    if (!tile_pair<OP>(M, r0, c0, p, &A, &B, &ia, &ib, &ring)) {
+      for (int q = 0; q < NM; ++q) m[q] = 0.0;
+      continue;
+    }
+    int n;
+    if (!LAG01) {
+      n = space_order(d);
+      tensor_moments_impl<R, OP, false>(A, B, d, n, ht, alpha, LN, m);
+    } else {
+      const int cls = pair_class(ring, ia, ib, A, B);
+      if (cls == kIdentical || cls == kAdjNext || cls == kAdjPrev) {
+        const double* src = sing + ((size_t)d * 3 * ring + singular_slot(cls, ia, ring)) * 5;
+        for (int q = 0; q < NM; ++q) m[q] = src[q];
+        continue;
+      }
+      n = cls == kRegular ? kRegular01 : kNear01;
+      tensor_moments_impl<R, OP, true>(A, B, d, n, ht, alpha, (const LagNodes<R>*)nullptr, m);
+    }
+  }
+  __syncthreads();
+  // phase 3: entries
+  const size_t base = (size_t)d * N * N;
+  if (OP == STBEM_OP_V) {
+    const int i = r0 + tid / kT, j = c0 + tid % kT;
+    if (i < N && j < N) {
+      const T v = (T)mom[tid];
+      out[base + (size_t)i * N + j] = v;
+      if (rt != ct) out[base + (size_t)j * N + i] = v;
+    }
+  } else if (OP == STBEM_OP_K) {
+    if (tid < kT * kKP) {
+      const int si = tid / kKP, sp = tid % kKP;
+      const int i = r0 + si, p = c0 + sp;
+      if (i < N && p < N) {
+        const double val = mom[(size_t)(si * kKJ + sp + 1) * NM + 0] + mom[(size_t)(si * kKJ + sp) * NM + 1];
+        out[base + (size_t)i * N + p] = (T)val;
+      }
+    }
+  } else {
+    const int s = tid / kT, t = tid % kT;
+    const int l = r0 + s, k = c0 + t;
+    // evaluate with the smaller index first; on a diagonal tile both ranges coincide
+    const int lo = l < k ? l : k, hi = l < k ? k : l;
+    const int so = lo - r0, to = hi - c0;
+    if (l < N && k < N && so >= 0 && to >= 0 && so < kT && to < kT) {
+      double val = 0.0;
+      for (int ia = 0; ia < 4; ++ia) {
+        const int qa = 4 * lo + ia;
+        const double ca = M.dcurl[qa], a0 = M.dv0[qa], a1 = M.dv1[qa];
+        const int u = 2 * so + ia;
+        const int ga = M.dpiece[qa];
+        const double nax = M.hnx[ga], nay = M.hny[ga];
+        for (int ib = 0; ib < 4; ++ib) {
+          const int qb = 4 * hi + ib;
+          const double cb = M.dcurl[qb], b0 = M.dv0[qb], b1 = M.dv1[qb];
+          const int v = 2 * to + ib;
+          const int gb = M.dpiece[qb];
+          const double nn = nax * M.hnx[gb] + nay * M.hny[gb];
+          const double* mm = mom + (size_t)(u * kDP + v) * NM;
+          const double I1 = a0 * (b0 * mm[1] + b1 * mm[2]) + a1 * (b0 * mm[3] + b1 * mm[4]);
+          val += ca * cb * mm[0] + nn * I1;
+        }
+      }
+      out[base + (size_t)l * N + k] = (T)val;
+      if (rt != ct) out[base + (size_t)k * N + l] = (T)val;
+    }
   }
 }
 
 // ---- host side ----------------------------------------------------------------
 cudaError_t upload_rule_tables(const RuleTables& t, cudaStream_t s) {
-  return cudaMemcpyToSymbolAsync(c_tab, &t, sizeof(RuleTables), 0, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_tab, &t, sizeof(RuleTables), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  float gxf[kGaussTotal], gwf[kGaussTotal];
+  for (int i = 0; i < kGaussTotal; ++i) {
+    gxf[i] = (float)t.gx[i];
+    gwf[i] = (float)t.gw[i];
+  }
+  e = cudaMemcpyToSymbolAsync(c_gxf, gxf, sizeof(gxf), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbolAsync(c_gwf, gwf, sizeof(gwf), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);   // the host arrays above go out of scope
 }
 
-template <int OP, typename T>
+template <int OP, typename R, typename T>
 static cudaError_t launch_op(const DevMesh& M, T* out, cudaStream_t s) {
   const int N = M.N, nt = M.n_t;
-  const int nl = nt < 2 ? nt : 2;
-  k_lag01<OP, T><<<dim3(N * N, nl), kLag01Threads, 0, s>>>(M, out);
-  count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  const size_t smem = tile_smem_bytes<OP, R>();
+  cudaError_t e = cudaFuncSetAttribute(k_tile<OP, R, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tile<OP, R, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (nt > 2) {
-    // chunk the lag range so that one launch stays well below a second
-    const int chunk = 64;
-    for (int d0 = 2; d0 < nt; d0 += chunk) {
-      const int d1 = d0 + chunk < nt ? d0 + chunk : nt;
-      if (OP == STBEM_OP_V) {
-        const long long total = (long long)(d1 - d0) * N * N;
-        const int threads = 128;
-        const long long blocks = (total + threads - 1) / threads;
-        k_lag2<OP, T><<<(unsigned)blocks, threads, 0, s>>>(M, d0, d1, out);
-      } else if (OP == STBEM_OP_K) {
-        const int tiles = ((N + kKI - 1) / kKI) * ((N + kKP - 1) / kKP);
-        k_lag2_K<T><<<dim3(tiles, d1 - d0), kTileThreads, 0, s>>>(M, d0, d1, out);
-      } else {
-        const int nT = (N + kDT - 1) / kDT;
-        const int tiles = nT * (nT + 1) / 2;
-        k_lag2_D<T><<<dim3(tiles, d1 - d0), kTileThreads, 0, s>>>(M, d0, d1, out);
-      }
-      count_launches(1);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+  int tiles;
+  if (OP == STBEM_OP_K) {
+    tiles = ((N + kT - 1) / kT) * ((N + kKP - 1) / kKP);
+  } else {
+    const int nT = (N + kT - 1) / kT;
+    tiles = nT * (nT + 1) / 2;
+  }
+  // lags 0 and 1: FP64 singular pairs spread over the GPU, then the tiles
+  const int n01 = nt < 2 ? nt : 2;
+  const int Rl = OP == STBEM_OP_D ? 2 * N : N;
+  k_singular<OP><<<dim3(3 * Rl, n01), kSingThreads, 0, s>>>(M, M.sing);
+  k_tile<OP, R, T, true><<<dim3(tiles, n01), kTileThreads, smem, s>>>(M, 0, M.sing, out);
+  count_launches(2);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // lags >= 2 in chunks of at most 64
+  for (int d0 = 2; d0 < nt; d0 += 64) {
+    const int d1 = d0 + 64 < nt ? d0 + 64 : nt;
+    if (OP == STBEM_OP_V) {
+      const long long npair = (long long)N * (N + 1) / 2;
+      k_lag2_V<R, T><<<dim3((unsigned)((npair + 127) / 128), d1 - d0), 128, 0, s>>>(M, d0, out);
+    } else {
+      k_tile<OP, R, T, false><<<dim3(tiles, d1 - d0), kTileThreads, smem, s>>>(M, d0, M.sing, out);
     }
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -594,14 +677,14 @@ static cudaError_t launch_op(const DevMesh& M, T* out, cudaStream_t s) {
 cudaError_t assemble_launch(const DevMesh& M, int op, int prec, void* out, cudaStream_t s) {
   if (prec == STBEM_F64) {
     double* o = static_cast<double*>(out);
-    if (op == STBEM_OP_V) return launch_op<STBEM_OP_V>(M, o, s);
-    if (op == STBEM_OP_K) return launch_op<STBEM_OP_K>(M, o, s);
-    return launch_op<STBEM_OP_D>(M, o, s);
+    if (op == STBEM_OP_V) return launch_op<STBEM_OP_V, double>(M, o, s);
+    if (op == STBEM_OP_K) return launch_op<STBEM_OP_K, double>(M, o, s);
+    return launch_op<STBEM_OP_D, double>(M, o, s);
   }
   float* o = static_cast<float*>(out);
-  if (op == STBEM_OP_V) return launch_op<STBEM_OP_V>(M, o, s);
-  if (op == STBEM_OP_K) return launch_op<STBEM_OP_K>(M, o, s);
-  return launch_op<STBEM_OP_D>(M, o, s);
+  if (op == STBEM_OP_V) return launch_op<STBEM_OP_V, float>(M, o, s);
+  if (op == STBEM_OP_K) return launch_op<STBEM_OP_K, float>(M, o, s);
+  return launch_op<STBEM_OP_D, float>(M, o, s);
 }
 
 }  // namespace stbem

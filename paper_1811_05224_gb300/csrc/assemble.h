@@ -15,6 +15,7 @@ struct DevMesh {
   const int* dpiece;                                         // dual pieces (4N)
   const double *dv0, *dv1, *dcurl;                           // psi at piece ends, d psi/ds
   const double *vx, *vy;                                     // vertices (N)
+  double* sing;      // lag-0/1 moments of the 3 (2N) singular pairs (assembly scratch)
 };
 
 void build_rule_tables(RuleTables* t);

@@ -26,6 +26,7 @@ struct stbem_mesh {
   std::vector<double> h;     // segment lengths (host copy)
   double* dbuf = nullptr;    // device geometry
   int* ibuf = nullptr;
+  double* sbuf = nullptr;    // lag-0/1 singular-pair moments (2 lags x 3 x 2N x 5)
   stbem::DevMesh dev{};
 };
 
@@ -166,6 +167,7 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&m->dbuf, host.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&m->ibuf, dp.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->sbuf, (size_t)2 * 3 * (2 * N) * 5 * sizeof(double));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->dbuf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
@@ -174,6 +176,7 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
   if (e != cudaSuccess) {
     if (m->dbuf) cudaFree(m->dbuf);
     if (m->ibuf) cudaFree(m->ibuf);
+    if (m->sbuf) cudaFree(m->sbuf);
     delete m;
     return cuda_fail(ctx, e, "mesh upload");
   }
@@ -188,6 +191,7 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
   b += 12 * N;
   D.vx = b; D.vy = b + N;
   D.dpiece = m->ibuf;
+  D.sing = m->sbuf;
   *out = m;
   return STBEM_OK;
 }
@@ -199,6 +203,7 @@ void stbem_mesh_destroy(stbem_mesh* m) {
   cudaSetDevice(m->device);
   if (m->dbuf) cudaFree(m->dbuf);
   if (m->ibuf) cudaFree(m->ibuf);
+  if (m->sbuf) cudaFree(m->sbuf);
   cudaSetDevice(prev);
   delete m;
 }
@@ -317,38 +322,38 @@ int stbem_solve_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes) {
   return STBEM_OK;
 }
 
-int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const void* D, const double* L,
-                const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
-                void* work, size_t work_bytes) {
-  if (!ctx) return STBEM_ERR_ARG;
-  if (!V || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve: NULL pointer");
-  if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve: bad sizes");
-  if (vprec != STBEM_F64 && vprec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "solve: bad precision");
-  const int restart = opts->restart, maxit = opts->max_iter;
-  if (restart < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "solve: bad options");
-  const bool prec = opts->precondition != 0;
-  if (prec && (!D || !L)) return fail(ctx, STBEM_ERR_ARG, "solve: preconditioner needs D and L");
-  SolveWork W;
-  if (!carve(work, work_bytes, nt, nx, restart, &W))
-    return fail(ctx, STBEM_ERR_NOMEM, "solve: workspace %zu < %zu bytes", work_bytes, solve_bytes(nt, nx, restart));
-  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve: set device");
-  cudaStream_t s = ctx->stream;
-  const size_t N = (size_t)nt * nx;
-  info->iterations = 0;
-  info->status = STBEM_OK;
-  info->rel_residual = 0.0;
+}  // extern "C"
 
+namespace {
+
+struct GmresOp {
+  int nt, nx, prec;       // operator precision (F64 / F32 lag blocks)
+  const void* V;
+  const void* D;          // NULL: no preconditioner
+  const double* L;
+};
+
+// Right-preconditioned restarted GMRES for V x = f from x = 0 (see stbem_solve).
+// Returns STBEM_OK, STBEM_ERR_NOCONV or STBEM_ERR_NAN (or a CUDA error code).
+int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, double tol, int maxit,
+               int restart, SolveWork& W, int* iters_out, double* relres_out) {
+  cudaStream_t s = ctx->stream;
+  const int nt = op.nt, nx = op.nx;
+  const size_t N = (size_t)nt * nx;
+  const bool prec = op.D != nullptr;
+  *iters_out = 0;
+  *relres_out = 0.0;
   auto applyV = [&](const double* x, double* y) {
-    return stbem::apply_launch(vprec, false, nt, nx, V, 1, x, y, W.apply, s);
+    return stbem::apply_launch(op.prec, false, nt, nx, op.V, 1, x, y, W.apply, s);
   };
   // right preconditioner: y = L^{-1} D L^{-1} x (or y = x)
   auto applyP = [&](const double* x, double* y) -> cudaError_t {
     if (!prec) return cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    cudaError_t e = stbem::diag_div_launch(x, L, W.u, nt, nx, s);
+    cudaError_t e = stbem::diag_div_launch(x, op.L, W.u, nt, nx, s);
     if (e != cudaSuccess) return e;
-    e = stbem::apply_launch(vprec, false, nt, nx, D, 1, W.u, y, W.apply, s);
+    e = stbem::apply_launch(op.prec, false, nt, nx, op.D, 1, W.u, y, W.apply, s);
     if (e != cudaSuccess) return e;
-    return stbem::diag_div_launch(y, L, y, nt, nx, s);
+    return stbem::diag_div_launch(y, op.L, y, nt, nx, s);
   };
   auto norm = [&](const double* x, double* out) -> cudaError_t {
     cudaError_t e = stbem::dots_launch(x, 1, x, N, W.h, s);
@@ -363,10 +368,7 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
   double nf;
   CUDA_TRY(ctx, norm(f, &nf), "solve: norm f");
   CUDA_TRY(ctx, cudaMemsetAsync(w, 0, N * sizeof(double), s), "solve: zero w");
-  if (!std::isfinite(nf)) {
-    info->status = STBEM_ERR_NAN;
-    return fail(ctx, STBEM_ERR_NAN, "solve: right-hand side is not finite");
-  }
+  if (!std::isfinite(nf)) return fail(ctx, STBEM_ERR_NAN, "solve: right-hand side is not finite");
   if (nf == 0.0) return STBEM_OK;
 
   std::vector<double> H((size_t)(restart + 1) * restart, 0.0), cs(restart), sn(restart), g(restart + 1);
@@ -388,13 +390,12 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
     CUDA_TRY(ctx, norm(W.r, &beta), "solve: norm r");
     if (!std::isfinite(beta)) { status = STBEM_ERR_NAN; break; }
     relres = beta / nf;
-    if (relres <= opts->tol) break;
+    if (relres <= tol) break;
     if (iters >= maxit) { status = STBEM_ERR_NOCONV; break; }
     CUDA_TRY(ctx, stbem::scale_launch(W.r, 1.0 / beta, W.Q, N, s), "solve: q0");
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k_done = 0;
-    bool stop_cycle = false;
     for (int k = 0; k < restart; ++k) {
       double* qk = W.Q + (size_t)k * N;
       double* qk1 = W.Q + (size_t)(k + 1) * N;
@@ -412,7 +413,7 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
       for (int t = 0; t <= k; ++t) hcol[t] += h2[t];
       bool bad = !std::isfinite(hk1);
       for (int t = 0; t <= k; ++t) bad = bad || !std::isfinite(hcol[t]);
-      if (bad) { status = STBEM_ERR_NAN; stop_cycle = true; break; }
+      if (bad) { status = STBEM_ERR_NAN; break; }
       if (hk1 > 0.0) CUDA_TRY(ctx, stbem::scale_launch(W.v, 1.0 / hk1, qk1, N, s), "solve: q");
       // Givens rotations on column k
       for (int t = 0; t < k; ++t) {
@@ -430,7 +431,7 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
       ++iters;
       k_done = k + 1;
       const double est = std::fabs(g[k + 1]) / nf;
-      if (est <= opts->tol || iters >= maxit || hk1 == 0.0) break;
+      if (est <= tol || iters >= maxit || hk1 == 0.0) break;
     }
     if (status != STBEM_OK) break;
     // y = H^{-1} g (upper triangular), w += P(Q y)
@@ -445,14 +446,128 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
     CUDA_TRY(ctx, applyP(W.r, W.z), "solve: P Qy");
     CUDA_TRY(ctx, stbem::axpy_launch(1.0, W.z, w, N, s), "solve: update");
     CUDA_TRY(ctx, cudaStreamSynchronize(s), "solve: sync");
-    (void)stop_cycle;
   }
+  *iters_out = iters;
+  *relres_out = relres;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const void* D, const double* L,
+                const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!V || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve: NULL pointer");
+  if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve: bad sizes");
+  if (vprec != STBEM_F64 && vprec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "solve: bad precision");
+  const int restart = opts->restart, maxit = opts->max_iter;
+  if (restart < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "solve: bad options");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!D || !L)) return fail(ctx, STBEM_ERR_ARG, "solve: preconditioner needs D and L");
+  SolveWork W;
+  if (!carve(work, work_bytes, nt, nx, restart, &W))
+    return fail(ctx, STBEM_ERR_NOMEM, "solve: workspace %zu < %zu bytes", work_bytes, solve_bytes(nt, nx, restart));
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve: set device");
+  const GmresOp op{nt, nx, vprec, V, prec ? D : nullptr, L};
+  int iters = 0;
+  double relres = 0.0;
+  const int status = gmres_core(ctx, op, f, w, opts->tol, maxit, restart, W, &iters, &relres);
   info->iterations = iters;
   info->rel_residual = relres;
   info->status = status;
-  if (status != STBEM_OK)
+  if (status == STBEM_ERR_NAN || status == STBEM_ERR_NOCONV)
     return fail(ctx, status, "solve: %s after %d iterations (relres %.3e)",
                 status == STBEM_ERR_NAN ? "NaN" : "no convergence", iters, relres);
+  return status;   // STBEM_OK, or a CUDA error already described
+}
+
+int stbem_solve_mixed_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || restart < 1) return STBEM_ERR_ARG;
+  *bytes = solve_bytes(n_t, n_x, restart) + 2 * (size_t)n_t * n_x * sizeof(double);
+  return STBEM_OK;
+}
+
+int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const float* V32, const float* D32,
+                      const double* L, const double* f, double* w, const stbem_solve_opts* opts,
+                      double inner_tol, stbem_solve_info* info, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!V64 || !V32 || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: NULL pointer");
+  if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: bad sizes");
+  const int restart = opts->restart, maxit = opts->max_iter;
+  if (restart < 1 || maxit < 1 || !(opts->tol > 0) || !(inner_tol > 0) || !(inner_tol < 1))
+    return fail(ctx, STBEM_ERR_ARG, "solve_mixed: bad options");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!D32 || !L)) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: preconditioner needs D and L");
+  const size_t N = (size_t)nt * nx;
+  const size_t need = solve_bytes(nt, nx, restart) + 2 * N * sizeof(double);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "solve_mixed: workspace %zu < %zu bytes", work_bytes, need);
+  SolveWork W;
+  carve(work, solve_bytes(nt, nx, restart), nt, nx, restart, &W);
+  double* r = reinterpret_cast<double*>(static_cast<char*>(work) + solve_bytes(nt, nx, restart));
+  double* dw = r + N;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_mixed: set device");
+  cudaStream_t s = ctx->stream;
+  auto norm = [&](const double* x, double* out) -> cudaError_t {
+    cudaError_t e = stbem::dots_launch(x, 1, x, N, W.h, s);
+    if (e != cudaSuccess) return e;
+    double v;
+    e = cudaMemcpyAsync(&v, W.h, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *out = std::sqrt(v);
+    return e;
+  };
+  info->iterations = 0;
+  info->status = STBEM_OK;
+  info->rel_residual = 0.0;
+  double nf;
+  CUDA_TRY(ctx, norm(f, &nf), "solve_mixed: norm f");
+  CUDA_TRY(ctx, cudaMemsetAsync(w, 0, N * sizeof(double), s), "solve_mixed: zero w");
+  if (!std::isfinite(nf)) {
+    info->status = STBEM_ERR_NAN;
+    return fail(ctx, STBEM_ERR_NAN, "solve_mixed: right-hand side is not finite");
+  }
+  if (nf == 0.0) return STBEM_OK;
+  const GmresOp op{nt, nx, STBEM_F32, V32, prec ? (const void*)D32 : nullptr, L};
+  CUDA_TRY(ctx, cudaMemcpyAsync(r, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "solve_mixed: r");
+  int total = 0, status = STBEM_OK;
+  double relres = 1.0;
+  for (int outer = 0; outer < 30; ++outer) {
+    double nr;
+    CUDA_TRY(ctx, norm(r, &nr), "solve_mixed: norm r");
+    if (!std::isfinite(nr)) { status = STBEM_ERR_NAN; break; }
+    relres = nr / nf;
+    if (relres <= opts->tol) break;
+    if (total >= maxit) { status = STBEM_ERR_NOCONV; break; }
+    // inner: V32 dw = r to inner_tol (relative to r), FP64 Krylov vectors
+    int it = 0;
+    double rr = 0.0;
+    const int st = gmres_core(ctx, op, r, dw, inner_tol, maxit - total, restart, W, &it, &rr);
+    total += it;
+    if (st == STBEM_ERR_NAN) { status = st; break; }
+    if (st != STBEM_OK && st != STBEM_ERR_NOCONV) return st;
+    CUDA_TRY(ctx, stbem::axpy_launch(1.0, dw, w, N, s), "solve_mixed: w += dw");
+    // FP64 residual with the FP64 operator
+    CUDA_TRY(ctx, stbem::apply_launch(STBEM_F64, false, nt, nx, V64, 1, w, W.v, W.apply, s), "solve_mixed: V w");
+    CUDA_TRY(ctx, stbem::sub_launch(f, W.v, r, N, s), "solve_mixed: f - V w");
+    if (it == 0) { status = STBEM_ERR_NOCONV; break; }
+  }
+  info->iterations = total;
+  info->rel_residual = relres;
+  info->status = status;
+  if (status != STBEM_OK)
+    return fail(ctx, status, "solve_mixed: %s after %d inner iterations (relres %.3e)",
+                status == STBEM_ERR_NAN ? "NaN" : "no convergence", total, relres);
+  return STBEM_OK;
+}
+
+int stbem_round_f32(stbem_ctx* ctx, size_t n, const double* src, float* dst) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!src || !dst) return fail(ctx, STBEM_ERR_ARG, "round_f32: NULL pointer");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "round_f32: set device");
+  CUDA_TRY(ctx, stbem::round_f32_launch(src, dst, n, ctx->stream), "round_f32");
   return STBEM_OK;
 }
 

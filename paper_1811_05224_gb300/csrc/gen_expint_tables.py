@@ -1,5 +1,6 @@
 """Generate expint_cheb.inc: Chebyshev coefficients of A(z) = e^z E1(z) and
-B(z) = e^z E2(z) on [1,2], [2,4], [4,8], [8,16].
+B(z) = e^z E2(z) on [1,2], [2,4], [4,8], [8,16]; the Horner coefficients of
+the Ein series; the constants and 2^{-j/64} table of the table-driven e^{-x}.
 
 Each function is interpolated at the 26 Chebyshev points of the first kind of
 the interval, in 40-digit arithmetic (mpmath), and the coefficients of
@@ -16,6 +17,8 @@ import mpmath as mp
 
 mp.mp.dps = 40
 NC = 26
+NCF = 12
+NEIN = 18
 INTERVALS = [(1, 2), (2, 4), (4, 8), (8, 16)]
 
 
@@ -44,6 +47,32 @@ def main():
             c = cheb_coeffs(f, mp.mpf(a), mp.mpf(b))
             lines.append("  {" + ", ".join(mp.nstr(x, 20, min_fixed=0, max_fixed=0) for x in c) + "},")
         lines.append("};")
+    # FP32 copies: the leading 12 coefficients (the tail is below 2e-9 of c0)
+    for name, f in (("kChebE1f", A), ("kChebE2f", B)):
+        lines.append("static __constant__ const float %s[%d][%d] = {" % (name, len(INTERVALS), NCF))
+        for a, b in INTERVALS:
+            c = cheb_coeffs(f, mp.mpf(a), mp.mpf(b))[:NCF]
+            lines.append("  {" + ", ".join(mp.nstr(x, 10, min_fixed=0, max_fixed=0) + "f" for x in c) + "},")
+        lines.append("};")
+    lines.append("constexpr int kChebNf = %d;" % NCF)
+    # Ein(z) = sum_{k>=1} (-1)^{k+1} z^k / (k k!): Horner coefficients, k = 1..18
+    # (the dropped tail is below 1e-17 for |z| <= 1)
+    coef = [(-1) ** (k + 1) / (mp.mpf(k) * mp.factorial(k)) for k in range(1, NEIN + 1)]
+    lines.append("constexpr int kEinTerms = %d;" % NEIN)
+    lines.append("static __constant__ const double kEinCoef[%d] = {%s};" % (
+        NEIN, ", ".join(mp.nstr(c, 20, min_fixed=0, max_fixed=0) for c in coef)))
+    # e^{-x} by reduction to r = x - n ln2/64: table 2^{-j/64}, j = 0..63,
+    # 64/ln2 and a two-part ln2/64 whose leading part has 36 significant bits
+    # (n ln2_hi is exact for n < 2^17, i.e. x < 1.7e3)
+    l = mp.log(2) / 64
+    hi = mp.ldexp(mp.floor(mp.ldexp(l, 36 + 6)), -(36 + 6))
+    lo = l - hi
+    tab = [mp.power(2, -mp.mpf(j) / 64) for j in range(64)]
+    lines.append("constexpr double kInvLn2x64 = %s;" % mp.nstr(64 / mp.log(2), 20, min_fixed=0, max_fixed=0))
+    lines.append("constexpr double kLn2by64Hi = %s;" % mp.nstr(hi, 25, min_fixed=0, max_fixed=0))
+    lines.append("constexpr double kLn2by64Lo = %s;" % mp.nstr(lo, 20, min_fixed=0, max_fixed=0))
+    lines.append("static __constant__ const double kExp2Tab[64] = {%s};" % ", ".join(
+        mp.nstr(t, 20, min_fixed=0, max_fixed=0) for t in tab))
     lines.append("}  // namespace stbem")
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "expint_cheb.inc")
     with open(out, "w") as fh:

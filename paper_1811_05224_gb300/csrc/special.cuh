@@ -2,6 +2,7 @@
 // definitions: E_n(z) = int_1^inf e^{-zt} t^{-n} dt.
 //  * z < 1: E1(z) = -gamma - ln z + Ein(z), Ein(z) = sum_{k>=1} (-1)^{k+1} z^k/(k k!)
 //    (Abramowitz & Stegun 5.1.11), and E2(z) = e^{-z} - z E1(z) (A&S 5.1.14);
+//    e^{-z} here and below from exp_neg_fast;
 //  * 1 <= z < 16: e^z E1 and e^z E2 from 26-term Chebyshev expansions on
 //    [1,2], [2,4], [4,8], [8,16] (coefficients in expint_cheb.inc, generated
 //    by gen_expint_tables.py in 40-digit arithmetic), Clenshaw summation;
@@ -13,6 +14,8 @@
 // exp and log are the platform's; nothing here reproduces their internals.
 #pragma once
 #include "hd.cuh"
+#include <cstring>
+
 #include "expint_cheb.inc"
 
 namespace stbem {
@@ -21,13 +24,41 @@ constexpr double kEulerGamma = 0.577215664901532860606512090082402431;
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kFourPi = 4.0 * 3.141592653589793238462643383279502884;
 
+// Ein(z) for |z| <= 1: Horner sum of the first 18 terms (the tail is below
+// 1e-17 there); coefficients (-1)^{k+1} / (k k!) from expint_cheb.inc.
 STB_HD double ein_series(double z) {
-  double term = 1.0, acc = 0.0;
-  for (int k = 1; k <= 30; ++k) {
-    term = term * z / k;
-    acc = acc + ((k & 1) ? term : -term) / k;
-  }
-  return acc;
+  double acc = kEinCoef[kEinTerms - 1];
+  for (int k = kEinTerms - 2; k >= 0; --k) acc = fma(acc, z, kEinCoef[k]);
+  return acc * z;
+}
+
+// e^{-x}, table-driven (Tang, ACM TOMS 15, 1989): x = n ln2/64 + r with
+// |r| <= ln2/128 (two-part ln2/64 so that n ln2_hi is exact), then
+// e^{-x} = 2^{-(n >> 6)} 2^{-(n & 63)/64} e^{-r}, the middle factor from a
+// 64-entry table and e^{-r} from its Taylor polynomial of degree 5 (remainder
+// |r|^6/720 < 3.4e-17).  Results within 2 ulp of the correctly rounded value
+// (checked on the host against the C library).  Arguments beyond 708, where
+// the result leaves the normal range, go to the library exp.
+STB_HD double exp_neg_fast(double x) {
+  if (!(x < 708.0)) return exp(-x);
+  const double nd = rint(x * kInvLn2x64);
+  const int n = (int)nd;
+  double r = fma(-nd, kLn2by64Hi, x);
+  r = fma(-nd, kLn2by64Lo, r);
+  double p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
+  p = fma(r, p, -1.0 / 6.0);
+  p = fma(r, p, 0.5);
+  p = fma(r, p, -1.0);
+  p = fma(r, p, 1.0);
+  const double t = kExp2Tab[n & 63] * p;
+  const long long bits = (long long)(1023 - (n >> 6)) << 52;   // 2^{-(n >> 6)}, a normal double
+#ifdef __CUDA_ARCH__
+  return t * __longlong_as_double(bits);
+#else
+  double scale;
+  std::memcpy(&scale, &bits, sizeof(scale));
+  return t * scale;
+#endif
 }
 
 // Lentz evaluation of the contracted continued fraction for E_n, n = 1 and 2
@@ -90,16 +121,16 @@ STB_HD void e1e2(double z, double* e1, double* e2) {
   if (z < 1.0) {
     const double E1 = -kEulerGamma - log(z) + ein_series(z);
     *e1 = E1;
-    *e2 = exp(-z) - z * E1;
+    *e2 = exp_neg_fast(z) - z * E1;
   } else if (z < 16.0) {
     const int k = z < 2.0 ? 0 : (z < 4.0 ? 1 : (z < 8.0 ? 2 : 3));
     const double a = (double)(1 << k);
     const double t = 2.0 * z / a - 3.0;
-    const double ez = exp(-z);
+    const double ez = exp_neg_fast(z);
     *e1 = cheb_sum(kChebE1[k], t) * ez;
     *e2 = cheb_sum(kChebE2[k], t) * ez;
   } else {
-    const double ez = exp(-z);
+    const double ez = exp_neg_fast(z);
     *e1 = cf_backward(z, 1) * ez;
     *e2 = cf_backward(z, 2) * ez;
   }
@@ -109,6 +140,66 @@ STB_HD double e1_only(double z) {
   double a, b;
   e1e2(z, &a, &b);
   return a;
+}
+
+// ---- FP32 versions (mixed-precision assembly) ----------------------------------
+// Same definitions in single precision: 12-term series for z < 1, the leading
+// 12 Chebyshev coefficients on [1,16], a depth-9 continued fraction beyond.
+// Relative accuracy about 1e-6, well inside the FP32 assembly tolerance.
+
+STB_HD float ein_series_f(float z) {
+  float term = 1.0f, acc = 0.0f;
+  for (int k = 1; k <= 12; ++k) {
+    term = term * z * (1.0f / (float)k);
+    acc = acc + ((k & 1) ? term : -term) * (1.0f / (float)k);
+  }
+  return acc;
+}
+
+STB_HD float exp_neg_f(float x) {   // e^{-x}
+#ifdef __CUDA_ARCH__
+  return __expf(-x);
+#else
+  return expf(-x);
+#endif
+}
+
+STB_HD float cheb_sum_f(const float* c, float t) {
+  float b1 = 0.0f, b2 = 0.0f;
+  for (int k = kChebNf - 1; k >= 1; --k) {
+    const float b0 = c[k] + 2.0f * t * b1 - b2;
+    b2 = b1;
+    b1 = b0;
+  }
+  return 0.5f * c[0] + t * b1 - b2;
+}
+
+STB_HD float cf_backward_f(float z, int n) {
+  constexpr int K = 9;
+  float f = z + (float)n + 2.0f * K;
+  for (int k = K; k >= 1; --k) {
+    const float a = -(float)k * (float)(n - 1 + k);
+    f = (z + (float)n + 2.0f * (float)(k - 1)) + a / f;
+  }
+  return 1.0f / f;
+}
+
+STB_HD void e1e2_f(float z, float* e1, float* e2) {
+  if (z < 1.0f) {
+    const float E1 = -(float)kEulerGamma - logf(z) + ein_series_f(z);
+    *e1 = E1;
+    *e2 = exp_neg_f(z) - z * E1;
+  } else if (z < 16.0f) {
+    const int k = z < 2.0f ? 0 : (z < 4.0f ? 1 : (z < 8.0f ? 2 : 3));
+    const float t = 2.0f * z * (1.0f / (float)(1 << k)) - 3.0f;
+    const float ez = exp_neg_f(z);
+    *e1 = cheb_sum_f(kChebE1f[k], t) * ez;
+    *e2 = cheb_sum_f(kChebE2f[k], t) * ez;
+  } else {
+    const float ez = exp_neg_f(z);
+    *e1 = cf_backward_f(z, 1) * ez;
+    *e2 = cf_backward_f(z, 2) * ez;
+  }
 }
 
 }  // namespace stbem

@@ -40,7 +40,7 @@ STB_HD double Fk(double c, double s, double alpha) {
 
 template <int K>
 STB_HD double Gk(double c, double s, double alpha) {
-  const double e = exp(-c / s);
+  const double e = exp_neg_fast(c / s);
   if (K == kV) return e / (kFourPi * s);
   if (K == kKq) return alpha * e / (2.0 * kFourPi * s * s);
   return alpha / kFourPi * e * (c / (s * s * s) - 1.0 / (s * s));
@@ -70,10 +70,10 @@ STB_HD double lag1_series(double z, double ht, double alpha) {
   if (K == kV)
     return ht / (2.0 * kPi) *
            (log(2.0) + eh - ef + 0.5 * z * (kEulerGamma + log(2.0 * z) + eh - 2.0 * ef) +
-            exp(-0.5 * z) * expm1(-0.5 * z));
+            exp_neg_fast(0.5 * z) * expm1(-0.5 * z));
   if (K == kKq)
     return alpha / kFourPi *
-           (-exp(-0.5 * z) * expm1(-0.5 * z) / z - 0.5 * (kEulerGamma + log(2.0 * z)) - 0.5 * eh + ef);
+           (-exp_neg_fast(0.5 * z) * expm1(-0.5 * z) / z - 0.5 * (kEulerGamma + log(2.0 * z)) - 0.5 * eh + ef);
   return alpha / kFourPi * (kEulerGamma + log(2.0 * z) + eh - 2.0 * ef);
 }
 

@@ -120,6 +120,11 @@ __global__ void k_diag_div(const double* __restrict__ x, const double* __restric
     y[e] = x[e] / L[e % nx];
 }
 
+__global__ void k_round_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
@@ -162,6 +167,11 @@ cudaError_t axpy_launch(double a, const double* x, double* y, size_t n, cudaStre
 }
 cudaError_t sub_launch(const double* a, const double* b, double* y, size_t n, cudaStream_t s) {
   k_sub<<<grid_for(n), 256, 0, s>>>(a, b, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t round_f32_launch(const double* src, float* dst, size_t n, cudaStream_t s) {
+  k_round_f32<<<grid_for(n), 256, 0, s>>>(src, dst, n);
   count_launches(1);
   return cudaGetLastError();
 }

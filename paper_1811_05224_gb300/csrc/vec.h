@@ -18,4 +18,6 @@ cudaError_t axpy_launch(double a, const double* x, double* y, size_t n, cudaStre
 cudaError_t sub_launch(const double* a, const double* b, double* y, size_t n, cudaStream_t s);  // y = a - b
 // y[m][i] = x[m][i] / L[i]
 cudaError_t diag_div_launch(const double* x, const double* L, double* y, int nt, int nx, cudaStream_t s);
+// dst[i] = (float)src[i]
+cudaError_t round_f32_launch(const double* src, float* dst, size_t n, cudaStream_t s);
 }  // namespace stbem

@@ -1,0 +1,68 @@
+"""The CUDA path's device numerics compiled for the host (same headers) and
+checked on the CPU against the C library / scipy / numpy: the table-driven
+e^{-x}, E1 and E2 in FP64 and FP32, the Ein series, Gauss-Legendre tables."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+from scipy.special import exp1, expn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1811_05224_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    out = os.path.join(tempfile.mkdtemp(), "libnumerics_host.so")
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-I" + CSRC,
+           "-I" + os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "hostcheck", "numerics_shim.cpp"),
+           os.path.join(CSRC, "rules_host.cpp"), "-o", out]
+    subprocess.run(cmd, check=True)
+    L = ctypes.CDLL(out)
+    L.nc_init()
+    return L
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def test_exp_neg_within_two_ulp(lib):
+    x = np.concatenate([np.linspace(0.0, 1.0, 20001), np.linspace(1.0, 707.9, 200001),
+                        np.logspace(-300, 0, 2001)])
+    out = np.zeros_like(x)
+    lib.nc_exp_neg(_d(x), len(x), _d(out))
+    ref = np.exp(-x)
+    ulp = np.spacing(ref)
+    assert np.max(np.abs(out - ref) / ulp) <= 2.0
+
+
+def test_e1_e2_fp64_and_fp32(lib):
+    z = np.concatenate([np.logspace(-12, 0, 400), np.linspace(1.0, 16.5, 2000), np.logspace(1.2, 2.85, 300)])
+    e1, e2 = np.zeros_like(z), np.zeros_like(z)
+    lib.nc_e1e2(_d(z), len(z), _d(e1), _d(e2))
+    assert np.max(np.abs(e1 / exp1(z) - 1)) < 4e-15
+    assert np.max(np.abs(e2 / expn(2, z) - 1)) < 4e-15
+    zf = z[z < 85].astype(np.float32)
+    f1, f2 = np.zeros_like(zf), np.zeros_like(zf)
+    P = ctypes.POINTER(ctypes.c_float)
+    lib.nc_e1e2f(zf.ctypes.data_as(P), len(zf), f1.ctypes.data_as(P), f2.ctypes.data_as(P))
+    zd = zf.astype(np.float64)
+    assert np.max(np.abs(f1 / exp1(zd) - 1)) < 1e-6
+    assert np.max(np.abs(f2 / expn(2, zd) - 1)) < 1e-6
+
+
+def test_ein_and_gauss_tables(lib):
+    z = np.linspace(1e-6, 1.0, 1001)
+    out = np.zeros_like(z)
+    lib.nc_ein(_d(z), len(z), _d(out))
+    ref = exp1(z) + np.euler_gamma + np.log(z)     # Ein = E1 + gamma + ln z
+    assert np.max(np.abs(out - ref)) < 4e-16 * 4
+    for n in (4, 6, 8, 12, 16):
+        x, w = np.zeros(n), np.zeros(n)
+        lib.nc_gauss(n, _d(x), _d(w))
+        xr, wr = np.polynomial.legendre.leggauss(n)
+        assert np.allclose(x, 0.5 * (xr + 1), atol=2e-16) and np.allclose(w, 0.5 * wr, atol=4e-16)
