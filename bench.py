@@ -46,6 +46,10 @@ def _peaks():
 
 # FP64 pipe: 1.25 TFLOP/s nominal dense FP64 for GB300 (recipe table).
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
+# at square256 (lags 2..65) from an ncu capture (profiles/k_tile_D_f64_lag2.md);
+# set to None whenever that kernel changes
+TRAFFIC_D2_BYTES = 1032192 + 2380800
 
 
 def _oracle_sample(n_entries, seed, rng_lags=None):
@@ -246,6 +250,20 @@ def run_ours(args):
     ms_apply = a0.elapsed_time(a1) / reps
     apply_flops = 2.0 * nx * nx * nt * (nt + 1) / 2
     apply_bytes = nt * nx * nx * 8 + 2 * nt * nx * 8
+    # dominant kernel: the FP64 D tile kernel at lags >= 2 (chunks of 64 lags
+    # per launch), timed alone with CUDA events on the launching stream
+    n_lag2_launches = max(1, (nt - 2 + 63) // 64)
+    l2 = []
+    for _ in range(2):
+        c0, c1 = ev(), ev()
+        flush.zero_()
+        c0.record(stream)
+        P.assemble_lags(ctx, mesh, "D", 2, nt, out=D)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        l2.append(c0.elapsed_time(c1))
+    d2_ms_launch = min(l2) / n_lag2_launches
+    d2_flops_launch = d_lag2_flops(nx, nt) / n_lag2_launches
     # per-operator assembly time (separate events, same kernels)
     op_ms = {}
     for op, buf in (("V", V), ("K", K), ("D", D)):
@@ -314,11 +332,7 @@ def run_ours(args):
         c, t = _oracle_sample(96, 12345)
         cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "96 random (op, lag, i, j) entries of %s, single numpy process" % WORKLOAD}
-    # dominant kernel by time: D assembly (FP64 ALU); report the FP64 product
-    # roofline for the Toeplitz apply kernel as well
-    dominant = max(op_ms, key=op_ms.get)
-    flops_entry = _assembly_flops_per_entry(dominant, nt)
-    asm_tflops = flops_entry * nt * nx * nx / (op_ms[dominant] * 1e-3) / 1e12
+    asm_tflops = d2_flops_launch / (d2_ms_launch * 1e-3) / 1e12
     last = infos[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -341,11 +355,13 @@ def run_ours(args):
                       "w_rel_diff_vs_fp64": mixed_rel, "assembly_D_f32_ms": d32_ms,
                       "note": "FP64 V,K; FP32 D (FP64 singular pairs); FP64 refinement around FP32 GMRES"},
         },
-        "roofline": {"kernel": "assemble %s lags>=2 (k_lag2)" % dominant, "bound": "alu",
+        "roofline": {"kernel": "k_tile<D, f64> lags >= 2", "bound": "alu",
                      "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "note": "FP64 peak: nominal 1.25 TFLOP/s (recipe table); algorithmic FP64 "
-                             "flops counted per entry from the discretisation rule"},
+                     "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_D2_BYTES,
+                     "launch_ms": d2_ms_launch, "flops_per_launch": d2_flops_launch,
+                     "note": "peak: nominal FP64 1.25 TFLOP/s; FP64-ALU bound (DRAM traffic is only "
+                             "the written lag blocks); flops counted from the rule, unique half-segment "
+                             "pairs only"},
         "apply_roofline": {"bound": "alu", "achieved": apply_flops / (ms_apply * 1e-3) / 1e12,
                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": apply_flops / (ms_apply * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
@@ -362,37 +378,34 @@ def run_ours(args):
     return 0
 
 
-def _assembly_flops_per_entry(op, nt):
-    """FP64 flops per distinct entry of the lags >= 2 kernel, from the rule.
+def _space_order(d):      # Gauss points per piece at lag d >= 2 (discretisation rule)
+    return 4 if d >= 32 else (6 if d >= 8 else 8)
 
-    Per time-kernel evaluation in the Peano branch (the one the large-lag
-    entries take): one division c/s, one exp, two multiplies and one add for
-    the kernel, one FMA into the sum; exp is counted as 20 FP64 flops and a
-    division as 10 (their polynomial and Newton-iteration costs).  Per entry:
-    (space points) x (Peano nodes of the two intervals) evaluations, summed
-    over lags 2..nt-1 and divided by the lag count.  D has 16 half-segment
-    pairs per entry and two kernels per evaluation sharing the exp."""
-    def space_order(d):       # Gauss points per piece at lag d >= 2
-        return 4 if d >= 32 else (6 if d >= 8 else 8)
 
-    def peano_order(k):       # Gauss nodes on time interval k
-        return 6 if k >= 32 else (8 if k >= 2 else 16)
+def _peano_order(k):      # Gauss nodes on time interval k
+    return 6 if k >= 32 else (8 if k >= 2 else 16)
 
-    per_eval = 20 + 10 + 5 + 2
+
+# FP64 flops of one Peano node of the D kernel: e^{-c sigma} (c sigma, x 64/ln2,
+# two reduction FMAs, five polynomial FMAs, table and scale products: 18) and
+# the two kernel accumulations with the w3 c - w2 factor (3 FMAs: 6).
+D_NODE_FLOPS = 24
+# per quadrature point: x - y (4 FMAs), c (4), weight (1), switch (1), five
+# moments with their bilinear weights (~23)
+D_POINT_FLOPS = 33
+
+
+def d_lag2_flops(n_x, n_t):
+    """Algorithmic FP64 flops of the D_h assembly at lags 2..n_t-1: every
+    unordered half-segment pair integrated once per lag (H (H + 1) / 2 with
+    H = 2 n_x), n(d)^2 points, Peano nodes of the two intervals per point."""
+    H = 2 * n_x
+    pairs = H * (H + 1) // 2
     tot = 0.0
-    for d in range(2, nt):
-        n = space_order(d)
-        nodes = peano_order(d - 1) + peano_order(d)
-        ev = n * n * nodes
-        if op == "K":
-            ev *= 2
-        if op == "D":
-            ev *= 16
-            per_d = per_eval + 8
-        else:
-            per_d = per_eval
-        tot += ev * per_d
-    return tot / max(nt - 2, 1) * (nt - 2) / nt
+    for d in range(2, n_t):
+        nodes = _peano_order(d - 1) + _peano_order(d)
+        tot += pairs * _space_order(d) ** 2 * (D_NODE_FLOPS * nodes + D_POINT_FLOPS)
+    return tot
 
 
 def main():

@@ -99,6 +99,17 @@ int stbem_op_bytes(const stbem_mesh* mesh, int op, int prec, size_t* bytes);
 int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec,
                    void* dev_out);
 
+/* As stbem_assemble, restricted to the lag blocks d in [lag_begin, lag_end)
+ * (0 <= lag_begin <= lag_end <= n_t); dev_out is still the full
+ * n_t x n_x x n_x array and only those blocks are written.  Lag ranges are
+ * independent, so a caller can assemble them in pieces, on several streams of
+ * different contexts, or shard them across devices.  Calls that include lag
+ * 0 or 1 use the mesh's small singular-pair scratch: such calls on one mesh
+ * must not overlap in time.  Errors: STBEM_ERR_ARG (bad op, precision or
+ * range), STBEM_ERR_CUDA. */
+int stbem_assemble_lags(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec, int lag_begin,
+                        int lag_end, void* dev_out);
+
 /* Block-Toeplitz product (Section 3 block structure).
  *   transpose = 0:  y[b][m][i] = sum_{d=0}^{m} sum_j A[d][i][j] x[b][m-d][j]
  *   transpose = 1:  y[b][n][j] = sum_{d=0}^{n_t-1-n} sum_i A[d][i][j] x[b][n+d][i]

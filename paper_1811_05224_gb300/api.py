@@ -91,6 +91,15 @@ def assemble(ctx: Context, mesh: Mesh, op: str, prec: str = "f64", out=None):
     return out
 
 
+def assemble_lags(ctx: Context, mesh: Mesh, op: str, lag_begin: int, lag_end: int, prec: str = "f64", out=None):
+    """Write only the lag blocks [lag_begin, lag_end) of op into out."""
+    p = PRECS[prec]
+    if out is None:
+        out = ctx.empty((mesh.n_t, mesh.n_x, mesh.n_x), DTYPES[p])
+    ctx.check(ctx.lib.stbem_assemble_lags(ctx.h, mesh.h, OPS[op], p, lag_begin, lag_end, _ptr(out)))
+    return out
+
+
 def apply_workspace(ctx: Context, n_t: int, n_x: int, n_rhs: int = 1, prec: str = "f64"):
     nb = ctypes.c_size_t()
     ctx.check(ctx.lib.stbem_apply_workspace_bytes(n_t, n_x, n_rhs, PRECS[prec], ctypes.byref(nb)))

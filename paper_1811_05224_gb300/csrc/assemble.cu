@@ -636,8 +636,8 @@ cudaError_t upload_rule_tables(const RuleTables& t, cudaStream_t s) {
 }
 
 template <int OP, typename R, typename T>
-static cudaError_t launch_op(const DevMesh& M, T* out, cudaStream_t s) {
-  const int N = M.N, nt = M.n_t;
+static cudaError_t launch_op(const DevMesh& M, int lag_begin, int lag_end, T* out, cudaStream_t s) {
+  const int N = M.N;
   const size_t smem = tile_smem_bytes<OP, R>();
   cudaError_t e = cudaFuncSetAttribute(k_tile<OP, R, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
@@ -651,16 +651,18 @@ static cudaError_t launch_op(const DevMesh& M, T* out, cudaStream_t s) {
     tiles = nT * (nT + 1) / 2;
   }
   // lags 0 and 1: FP64 singular pairs spread over the GPU, then the tiles
-  const int n01 = nt < 2 ? nt : 2;
-  const int Rl = OP == STBEM_OP_D ? 2 * N : N;
-  k_singular<OP><<<dim3(3 * Rl, n01), kSingThreads, 0, s>>>(M, M.sing);
-  k_tile<OP, R, T, true><<<dim3(tiles, n01), kTileThreads, smem, s>>>(M, 0, M.sing, out);
-  count_launches(2);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  const int l01 = lag_begin, u01 = lag_end < 2 ? lag_end : 2;
+  if (l01 < u01) {
+    const int Rl = OP == STBEM_OP_D ? 2 * N : N;
+    k_singular<OP><<<dim3(3 * Rl, u01), kSingThreads, 0, s>>>(M, M.sing);
+    k_tile<OP, R, T, true><<<dim3(tiles, u01 - l01), kTileThreads, smem, s>>>(M, l01, M.sing, out);
+    count_launches(2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   // lags >= 2 in chunks of at most 64
-  for (int d0 = 2; d0 < nt; d0 += 64) {
-    const int d1 = d0 + 64 < nt ? d0 + 64 : nt;
+  for (int d0 = lag_begin > 2 ? lag_begin : 2; d0 < lag_end; d0 += 64) {
+    const int d1 = d0 + 64 < lag_end ? d0 + 64 : lag_end;
     if (OP == STBEM_OP_V) {
       const long long npair = (long long)N * (N + 1) / 2;
       k_lag2_V<R, T><<<dim3((unsigned)((npair + 127) / 128), d1 - d0), 128, 0, s>>>(M, d0, out);
@@ -674,17 +676,18 @@ static cudaError_t launch_op(const DevMesh& M, T* out, cudaStream_t s) {
   return cudaSuccess;
 }
 
-cudaError_t assemble_launch(const DevMesh& M, int op, int prec, void* out, cudaStream_t s) {
+cudaError_t assemble_launch(const DevMesh& M, int op, int prec, int lag_begin, int lag_end, void* out,
+                            cudaStream_t s) {
   if (prec == STBEM_F64) {
     double* o = static_cast<double*>(out);
-    if (op == STBEM_OP_V) return launch_op<STBEM_OP_V, double>(M, o, s);
-    if (op == STBEM_OP_K) return launch_op<STBEM_OP_K, double>(M, o, s);
-    return launch_op<STBEM_OP_D, double>(M, o, s);
+    if (op == STBEM_OP_V) return launch_op<STBEM_OP_V, double>(M, lag_begin, lag_end, o, s);
+    if (op == STBEM_OP_K) return launch_op<STBEM_OP_K, double>(M, lag_begin, lag_end, o, s);
+    return launch_op<STBEM_OP_D, double>(M, lag_begin, lag_end, o, s);
   }
   float* o = static_cast<float*>(out);
-  if (op == STBEM_OP_V) return launch_op<STBEM_OP_V, float>(M, o, s);
-  if (op == STBEM_OP_K) return launch_op<STBEM_OP_K, float>(M, o, s);
-  return launch_op<STBEM_OP_D, float>(M, o, s);
+  if (op == STBEM_OP_V) return launch_op<STBEM_OP_V, float>(M, lag_begin, lag_end, o, s);
+  if (op == STBEM_OP_K) return launch_op<STBEM_OP_K, float>(M, lag_begin, lag_end, o, s);
+  return launch_op<STBEM_OP_D, float>(M, lag_begin, lag_end, o, s);
 }
 
 }  // namespace stbem

@@ -23,6 +23,8 @@ void build_rule_tables(RuleTables* t);
 void count_launches(unsigned n);
 unsigned long long launch_count();
 cudaError_t upload_rule_tables(const RuleTables& t, cudaStream_t s);
-cudaError_t assemble_launch(const DevMesh& M, int op, int prec, void* out, cudaStream_t s);
+// Lags [lag_begin, lag_end) of op into out (the full n_t x N x N array).
+cudaError_t assemble_launch(const DevMesh& M, int op, int prec, int lag_begin, int lag_end, void* out,
+                            cudaStream_t s);
 
 }  // namespace stbem

@@ -220,7 +220,20 @@ int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, void* 
   if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown operator %d", op);
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown precision %d", prec);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble: set device");
-  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, out, ctx->stream), "assemble: launch");
+  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, 0, m->n_t, out, ctx->stream), "assemble: launch");
+  return STBEM_OK;
+}
+
+int stbem_assemble_lags(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, int lag_begin, int lag_end,
+                        void* out) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !out) return fail(ctx, STBEM_ERR_ARG, "assemble_lags: NULL mesh or output");
+  if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble_lags: unknown operator %d", op);
+  if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "assemble_lags: unknown precision %d", prec);
+  if (lag_begin < 0 || lag_end > m->n_t || lag_begin > lag_end)
+    return fail(ctx, STBEM_ERR_ARG, "assemble_lags: lag range [%d, %d) outside [0, %d)", lag_begin, lag_end, m->n_t);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble_lags: set device");
+  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, lag_begin, lag_end, out, ctx->stream), "assemble_lags");
   return STBEM_OK;
 }
 

@@ -222,3 +222,19 @@ def test_mixed_precision_solve(ctx):
             w_ref = P.solve(ctx, V, f, D, L, tol=1e-10)[0].cpu().numpy()
         rel = np.linalg.norm(wm.cpu().numpy() - w_ref) / np.linalg.norm(w_ref)
         assert rel <= 1e-6, (name, rel, info)
+
+
+def test_assemble_lags_pieces_equal_full(ctx):
+    """Lag ranges assembled separately reproduce the full assembly exactly."""
+    import paper_1811_05224_gb300 as P
+    X, T, nt, al = SMALL["lshape24"]
+    m = P.Mesh(ctx, X, T, nt, al)
+    for op in "VKD":
+        for prec in ("f64", "f32"):
+            full = P.assemble(ctx, m, op, prec)
+            parts = torch.full_like(full, float("nan"))
+            for a, b in [(0, 1), (1, 3), (3, 11), (11, nt)]:
+                P.assemble_lags(ctx, m, op, a, b, prec, out=parts)
+            assert torch.equal(full, parts), (op, prec)
+    with pytest.raises(Exception):
+        P.assemble_lags(ctx, m, "V", 3, nt + 1)
