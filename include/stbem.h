@@ -45,6 +45,7 @@ extern "C" {
 #define STBEM_ERR_NOCONV (-4)    /* iteration cap reached before tolerance   */
 #define STBEM_ERR_BREAKDOWN (-5) /* GMRES breakdown (zero Krylov vector)     */
 #define STBEM_ERR_NAN (-6)       /* NaN or Inf met in a residual             */
+#define STBEM_ERR_TIMEOUT (-7)   /* a bounded device-side wait gave up       */
 
 /* operators */
 #define STBEM_OP_V 0 /* single layer  <V phi0_k, phi0_l>,   N_x x N_x blocks */
@@ -142,6 +143,24 @@ int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
  * holds (stbem_apply_workspace_bytes() > 32 MiB); STBEM_ERR_CUDA. */
 int stbem_apply_noalloc(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
                         const void* dev_A, int n_rhs, const double* dev_x, double* dev_y);
+
+/* dev_dst[i] = BF16(dev_src[i]) (round to nearest even), i < n, with src in
+ * precision src_prec (STBEM_F64 or STBEM_F32): the operand format of
+ * stbem_apply_tc.  Errors: STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_to_bf16(stbem_ctx* ctx, int src_prec, size_t n, const void* dev_src, void* dev_dst);
+
+/* Many-right-hand-side block-Toeplitz product on the tensor cores (Section 3
+ * block structure; with n_rhs right-hand sides every lag block multiplies a
+ * dense n_x x (n_rhs n_t) matrix):
+ *   y[b][m][i] = sum_{d=0}^{m} sum_j A[d][i][j] x[b][m-d][j]
+ * A (n_t x n_x x n_x) and x (n_rhs x n_t x n_x) in BF16 (stbem_to_bf16),
+ * products accumulated in FP32, y written in FP64 (n_rhs x n_t x n_x).
+ * Requires n_x % 8 == 0 and 16-byte aligned A and x.  Blocks the host: it
+ * reads the kernel's error word afterwards.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_TIMEOUT (a pipeline wait gave up; y is incomplete),
+ * STBEM_ERR_CUDA. */
+int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_bf16, int n_rhs, const void* dev_x_bf16,
+                   double* dev_y);
 
 /* Right-hand side of eq. (4) for u_0 = 0 and the Dirichlet datum
  * g = U*(x - y*, t) (y* outside the domain):

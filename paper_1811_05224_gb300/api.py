@@ -191,3 +191,22 @@ def solve_mixed(ctx: Context, V64, V32, f, D32=None, L=None, tol: float = 1e-8, 
     if code != capi.STBEM_OK and raise_on_fail:
         ctx.check(code)
     return out, res
+
+
+def to_bf16(ctx: Context, src):
+    """BF16 copy (round to nearest even) of an FP64 or FP32 tensor."""
+    out = torch.empty(src.shape, dtype=torch.bfloat16, device=src.device)
+    prec = capi.F64 if src.dtype == torch.float64 else capi.F32
+    ctx.check(ctx.lib.stbem_to_bf16(ctx.h, prec, src.numel(), _ptr(src), _ptr(out)))
+    return out
+
+
+def apply_tc(ctx: Context, A_bf16, x_bf16, out=None):
+    """Tensor-core block-Toeplitz product: BF16 A (n_t, n_x, n_x) times BF16 x
+    (n_rhs, n_t, n_x), FP32 accumulation, FP64 result (n_rhs, n_t, n_x)."""
+    n_t, n_x = A_bf16.shape[0], A_bf16.shape[1]
+    xb = x_bf16 if x_bf16.dim() == 3 else x_bf16.unsqueeze(0)
+    if out is None:
+        out = torch.empty(xb.shape, dtype=torch.float64, device=xb.device)
+    ctx.check(ctx.lib.stbem_apply_tc(ctx.h, n_t, n_x, _ptr(A_bf16), xb.shape[0], _ptr(xb), _ptr(out)))
+    return out if x_bf16.dim() == 3 else out[0]

@@ -18,17 +18,19 @@ STBEM_ERR_NOMEM = -3
 STBEM_ERR_NOCONV = -4
 STBEM_ERR_BREAKDOWN = -5
 STBEM_ERR_NAN = -6
+STBEM_ERR_TIMEOUT = -7
 OP_V, OP_K, OP_D = 0, 1, 2
 F64, F32 = 0, 1
 
 ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOMEM", -4: "ERR_NOCONV",
-             -5: "ERR_BREAKDOWN", -6: "ERR_NAN"}
+             -5: "ERR_BREAKDOWN", -6: "ERR_NAN", -7: "ERR_TIMEOUT"}
 
 EXPORTS = [
     "stbem_version", "stbem_launch_count", "stbem_create", "stbem_destroy", "stbem_last_error", "stbem_mesh_create",
     "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_assemble_lags", "stbem_apply_workspace_bytes",
     "stbem_apply", "stbem_apply_noalloc", "stbem_rhs", "stbem_lumped_mass", "stbem_solve_workspace_bytes", "stbem_solve",
     "stbem_solve_mixed_workspace_bytes", "stbem_solve_mixed", "stbem_round_f32",
+    "stbem_to_bf16", "stbem_apply_tc",
 ]
 
 
@@ -85,6 +87,8 @@ def load(path: str = LIB_PATH):
     L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]
+    L.stbem_to_bf16.argtypes = [vp, i, sz, vp, vp]
+    L.stbem_apply_tc.argtypes = [vp, i, i, vp, i, vp, vp]
     for name in EXPORTS:
         if name not in ("stbem_version", "stbem_launch_count", "stbem_destroy", "stbem_mesh_destroy", "stbem_last_error"):
             getattr(L, name).restype = ctypes.c_int

@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -11,6 +12,7 @@
 #include "assemble.h"
 #include "stbem.h"
 #include "toeplitz.h"
+#include "toeplitz_tc.h"
 #include "vec.h"
 
 struct stbem_ctx {
@@ -274,6 +276,32 @@ int stbem_apply_noalloc(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_
   CUDA_TRY(ctx, stbem::noalloc_scratch_ptr(ctx->device, &scratch), "apply_noalloc: scratch address");
   CUDA_TRY(ctx, stbem::apply_launch(prec, transpose != 0, n_t, n_x, A, n_rhs, x, y, scratch, ctx->stream),
            "apply_noalloc");
+  return STBEM_OK;
+}
+
+int stbem_to_bf16(stbem_ctx* ctx, int src_prec, size_t n, const void* src, void* dst) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!src || !dst) return fail(ctx, STBEM_ERR_ARG, "to_bf16: NULL pointer");
+  if (src_prec != STBEM_F64 && src_prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "to_bf16: bad precision");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "to_bf16: set device");
+  CUDA_TRY(ctx, stbem::to_bf16_launch(src_prec, src, dst, n, ctx->stream), "to_bf16");
+  return STBEM_OK;
+}
+
+int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A || !x || !y) return fail(ctx, STBEM_ERR_ARG, "apply_tc: NULL pointer");
+  if (!stbem::apply_tc_supported(n_t, n_x, n_rhs))
+    return fail(ctx, STBEM_ERR_ARG, "apply_tc: unsupported sizes n_t=%d n_x=%d n_rhs=%d (need n_x %% 8 == 0)", n_t,
+                n_x, n_rhs);
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(x)) & 15)
+    return fail(ctx, STBEM_ERR_ARG, "apply_tc: A and x must be 16-byte aligned");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_tc: set device");
+  CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_tc: reset error word");
+  CUDA_TRY(ctx, stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, ctx->stream), "apply_tc");
+  int flag = 0;
+  CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc: read error word");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc: a pipeline wait timed out");
   return STBEM_OK;
 }
 

@@ -1,0 +1,315 @@
+// Multi-right-hand-side block-Toeplitz product on the 5th-generation tensor
+// cores (tcgen05, sm_103a), BF16 operands with FP32 accumulation:
+//
+//   y[b][m][i] = sum_{d=0}^{m} sum_j A[d][i][j] x[b][m-d][j]
+//
+// (Section 3 block structure; with many right-hand sides each lag is a dense
+// GEMM A^(d) X_shifted).  One CTA owns a 128 x 128 output tile -- rows i of
+// one lag block, columns m (time steps) of one right-hand side b -- and loops
+// over all lags d <= m and 64-wide chunks of j:
+//   * one thread issues TMA loads of A^(d)[i0:i0+128][j0:j0+64] and of
+//     x[b][m0-d : m0-d+128][j0:j0+64] (128B swizzle) into a 4-stage ring;
+//     rows with m - d < 0 lie outside the tensor and arrive as zeros, which is
+//     exactly the causal (block lower triangular) structure;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = N =
+//     128, K = 16) into a 128-column TMEM accumulator and frees each stage with
+//     tcgen05.commit;
+//   * all four warps read the accumulator with tcgen05.ld and write FP64.
+// Every mbarrier wait is bounded (about a second of clock64); on time-out the
+// thread records an error in g_tc_error, skips the rest of its work and the
+// CTA still releases its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "assemble.h"
+#include "toeplitz_tc.h"
+
+namespace stbem {
+
+__device__ int g_tc_error;
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, THREADS = 128;
+constexpr uint32_t A_BYTES = BM * BK * 2;
+constexpr uint32_t B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr size_t SMEM_BYTES = 1024 + STAGES * (size_t)STAGE_BYTES + 256;
+constexpr long long kWaitCycles = 1LL << 31;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// K-major operand in the 128-byte swizzled layout written by TMA: rows of 128 B,
+// 8-row atoms of 1024 B (stride byte offset), descriptor version 1, swizzle
+// mode 2 (128B).  The tile base is 1024-aligned; a K step of 16 BF16 elements
+// advances the start address by 32 B.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = (addr >> 4) & 0x3FFFull;
+  d |= 1ull << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+  d |= 1ull << 46;                   // descriptor version
+  d |= 2ull << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_apply_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int nt, int nx,
+               double* __restrict__ Y) {
+  extern __shared__ unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
+  unsigned char* smA = reinterpret_cast<unsigned char*>(base);
+  unsigned char* smB = smA + STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smB + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
+  const int dmax = min(m0 + BN - 1, nt - 1);  // lags for which some m - d >= 0
+  const int nj = (nx + BK - 1) / BK;
+  const int iters = (dmax + 1) * nj;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % STAGES;
+      const uint32_t round = static_cast<uint32_t>(it / STAGES);
+      if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      const int d = it / nj, j0 = (it % nj) * BK;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_3d(&tmA, &full[s], smA + s * A_BYTES, j0, i0, d);
+      tma_load_3d(&tmX, &full[s], smB + s * B_BYTES, j0, m0 - d, b);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % STAGES;
+      const uint32_t round = static_cast<uint32_t>(it / STAGES);
+      if (!mbar_wait(&full[s], round & 1)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t da = smem_desc(smA + s * A_BYTES);
+      const uint64_t db = smem_desc(smB + s * B_BYTES);
+      for (int k = 0; k < BK / 16; ++k)
+        umma_bf16(tmem, da + (uint64_t)((k * 32) >> 4), db + (uint64_t)((k * 32) >> 4), (it > 0 || k > 0) ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(accum);   // completes when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: warp w holds accumulator rows (TMEM lanes) 32 w .. 32 w + 31
+  bool acc_ok = mbar_wait(accum, 0);
+  acc_ok = __all_sync(0xffffffffu, acc_ok);
+  tc_fence_after();
+  if (acc_ok) {
+    const int gi = i0 + warp * 32 + lane;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(trow + c0, r);
+      if (gi < nx) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int m = m0 + c0 + t;
+          if (m < nt) Y[((size_t)b * nt + m) * nx + gi] = (double)__uint_as_float(r[t]);
+        }
+      }
+    }
+  }
+  if (!ok || !acc_ok) atomicExch(&g_tc_error, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+__global__ void k_to_bf16_f64(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = __double2bfloat16(src[e]);
+}
+__global__ void k_to_bf16_f32(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = __float2bfloat16(src[e]);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool apply_tc_supported(int nt, int nx, int n_rhs) {
+  return nt >= 1 && nx >= 8 && nx % 8 == 0 && n_rhs >= 1 && n_rhs <= 65535 && (nt + BN - 1) / BN <= 65535;
+}
+
+cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
+                            cudaStream_t s) {
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap mA, mX;
+  const cuuint64_t dimA[3] = {(cuuint64_t)nx, (cuuint64_t)nx, (cuuint64_t)nt};
+  const cuuint64_t strA[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * nx * 2};
+  const cuuint64_t dimX[3] = {(cuuint64_t)nx, (cuuint64_t)nt, (cuuint64_t)n_rhs};
+  const cuuint64_t strX[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nt * nx * 2};
+  const cuuint32_t boxA[3] = {BK, BM, 1}, boxX[3] = {BK, BN, 1}, es[3] = {1, 1, 1};
+  CUresult r = enc(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(A_bf16), dimA, strA, boxA, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  r = enc(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X_bf16), dimX, strX, boxX, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((nx + BM - 1) / BM, (nt + BN - 1) / BN, n_rhs);
+  k_apply_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mX, nt, nx, Y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_error_reset(cudaStream_t s) {
+  const int zero = 0;
+  return cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t tc_error_read(int* flag, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(flag, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s) {
+  const size_t blocks_needed = (n + 255) / 256;
+  const int blocks = (int)(blocks_needed < 152 * 16 ? (blocks_needed ? blocks_needed : 1) : 152 * 16);
+  if (src_prec == STBEM_F64)
+    k_to_bf16_f64<<<blocks, 256, 0, s>>>(static_cast<const double*>(src), static_cast<__nv_bfloat16*>(dst), n);
+  else
+    k_to_bf16_f32<<<blocks, 256, 0, s>>>(static_cast<const float*>(src), static_cast<__nv_bfloat16*>(dst), n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace stbem
