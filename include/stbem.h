@@ -227,6 +227,52 @@ int stbem_solve_mixed(stbem_ctx* ctx, int n_t, int n_x, const double* dev_V64, c
  * paper).  Errors: STBEM_ERR_ARG, STBEM_ERR_CUDA. */
 int stbem_round_f32(stbem_ctx* ctx, size_t n, const double* dev_src, float* dev_dst);
 
+/* Three-term BF16 split of an FP64 array: hi = BF16(x), mid = BF16(x - hi),
+ * lo = BF16(x - hi - mid) (mid and lo may be NULL), so that
+ * |x - (hi + mid + lo)| <= ~2^-24 |x|.  Operand format of stbem_apply_tc3 and
+ * stbem_solve_batched.  Errors: STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_bf16_split3(stbem_ctx* ctx, size_t n, const double* dev_src, void* dev_hi, void* dev_mid, void* dev_lo);
+
+/* Accurate many-right-hand-side product on the tensor cores: with A given by
+ * its three BF16 slices (stbem_bf16_split3; dev_A_mid / dev_A_lo may be NULL)
+ * and x (FP64) split the same way inside the call, y = sum of the six slice
+ * products A_s x_t with s + t <= 2, each accumulated in FP32, summed in FP64:
+ * about 1e-6 relative to |A| |x| (the FP32 accumulation), against ~4e-3 for
+ * one BF16 product.  Workspace: stbem_apply_tc3_workspace_bytes() (the three
+ * slices of x).  Blocks the host.  Errors as stbem_apply_tc, STBEM_ERR_NOMEM. */
+int stbem_apply_tc3_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes);
+int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_hi, const void* dev_A_mid,
+                    const void* dev_A_lo, int n_rhs, const double* dev_x, double* dev_y, void* dev_work,
+                    size_t work_bytes);
+
+/* Time averages of g = U*(x - y_k*, t) at the vertices for n_src source
+ * points (host_ystar: 2 n_src doubles): dev_G[k][n][p] as in stbem_rhs. */
+int stbem_rhs_g_batched(stbem_ctx* ctx, const stbem_mesh* mesh, int n_src, const double* host_ystar,
+                        double* dev_G);
+
+/* dev_F[b] += 1/2 M_h dev_G[b] for n_rhs right-hand sides (M_h of eq. (4)). */
+int stbem_half_mass_add(stbem_ctx* ctx, const stbem_mesh* mesh, int n_rhs, const double* dev_G, double* dev_F);
+
+/* Solve V_h W_b = F_b for n_rhs right-hand sides at once (the batched form of
+ * the Section 2 GMRES): lockstep right-preconditioned GMRES on the BF16 V
+ * (dev_V_hi) with the BF16 preconditioner dev_D_bf16 (Section 2, Section 4
+ * lumping, dev_L), both applied on the tensor cores, FP64 Krylov vectors and
+ * orthogonalisation, a Hessenberg matrix and a convergence mask per
+ * right-hand side; each inner solve reduces its residual by inner_tol.  Around
+ * it, refinement with the residual R = F - V W from the three-slice split of V
+ * (dev_V_hi/mid/lo) until ||R_b|| / ||F_b|| <= opts->tol for every b (the
+ * split product limits attainable residuals to ~1e-6).  opts->restart is the
+ * Krylov dimension of an inner solve, opts->max_iter caps inner iterations.
+ * infos: n_rhs results.  Workspace: stbem_solve_batched_workspace_bytes().
+ * Requires n_x % 8 == 0.  Blocks the host.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_NOMEM, STBEM_ERR_NOCONV / _NAN (some right-hand side; see infos),
+ * STBEM_ERR_TIMEOUT, STBEM_ERR_CUDA. */
+int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, size_t* bytes);
+int stbem_solve_batched(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void* dev_V_hi, const void* dev_V_mid,
+                        const void* dev_V_lo, const void* dev_D_bf16, const double* dev_L, const double* dev_F,
+                        double* dev_W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
+                        void* dev_work, size_t work_bytes);
+
 #ifdef __cplusplus
 }
 #endif

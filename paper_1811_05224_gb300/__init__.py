@@ -5,6 +5,6 @@ assembly of V_h, K_h, D_h and block-Toeplitz products inside preconditioned
 GMRES, in hand-written CUDA behind the C ABI of include/stbem.h.
 """
 from .api import (Context, Mesh, apply, apply_tc, assemble, assemble_lags, lumped_mass, rhs,  # noqa: F401
-                  round_f32, solve, solve_mixed, to_bf16)
+                  apply_tc3, bf16_split3, rhs_batched, round_f32, solve, solve_batched, solve_mixed, to_bf16)
 
-__all__ = ["Context", "Mesh", "assemble", "assemble_lags", "apply", "rhs", "lumped_mass", "solve", "solve_mixed", "round_f32", "to_bf16", "apply_tc"]
+__all__ = ["Context", "Mesh", "assemble", "assemble_lags", "apply", "rhs", "lumped_mass", "solve", "solve_mixed", "round_f32", "to_bf16", "apply_tc", "bf16_split3", "apply_tc3", "rhs_batched", "solve_batched"]

@@ -210,3 +210,61 @@ def apply_tc(ctx: Context, A_bf16, x_bf16, out=None):
         out = torch.empty(xb.shape, dtype=torch.float64, device=xb.device)
     ctx.check(ctx.lib.stbem_apply_tc(ctx.h, n_t, n_x, _ptr(A_bf16), xb.shape[0], _ptr(xb), _ptr(out)))
     return out if x_bf16.dim() == 3 else out[0]
+
+
+def bf16_split3(ctx: Context, src):
+    """Three BF16 slices (hi, mid, lo) of an FP64 tensor."""
+    outs = [torch.empty(src.shape, dtype=torch.bfloat16, device=src.device) for _ in range(3)]
+    ctx.check(ctx.lib.stbem_bf16_split3(ctx.h, src.numel(), _ptr(src), _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2])))
+    return outs
+
+
+def apply_tc3(ctx: Context, A_slices, x, out=None, work=None):
+    """Accurate tensor-core product with a three-slice BF16 operator and FP64 x."""
+    n_t, n_x = A_slices[0].shape[0], A_slices[0].shape[1]
+    xb = x if x.dim() == 3 else x.unsqueeze(0)
+    if out is None:
+        out = torch.empty_like(xb)
+    if work is None:
+        nb = ctypes.c_size_t()
+        ctx.check(ctx.lib.stbem_apply_tc3_workspace_bytes(n_t, n_x, xb.shape[0], ctypes.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=xb.device)
+    A = list(A_slices) + [None] * (3 - len(A_slices))
+    ctx.check(ctx.lib.stbem_apply_tc3(ctx.h, n_t, n_x, _ptr(A[0]), _ptr(A[1]), _ptr(A[2]), xb.shape[0], _ptr(xb),
+                                      _ptr(out), _ptr(work), work.numel()))
+    return out if x.dim() == 3 else out[0]
+
+
+def rhs_batched(ctx: Context, mesh: Mesh, K_slices, y_stars):
+    """(G, F) for many sources: G[k] vertex time averages of U*(x - y_k, t),
+    F = 1/2 M_h G + K_h G with K_h from its three BF16 slices (tensor cores)."""
+    ys = np.ascontiguousarray(np.asarray(y_stars, dtype=np.float64).reshape(-1))
+    B = ys.size // 2
+    G = ctx.empty((B, mesh.n_t, mesh.n_x))
+    ctx.check(ctx.lib.stbem_rhs_g_batched(ctx.h, mesh.h, B, ys.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          _ptr(G)))
+    F = apply_tc3(ctx, K_slices, G)
+    ctx.check(ctx.lib.stbem_half_mass_add(ctx.h, mesh.h, B, _ptr(G), _ptr(F)))
+    return G, F
+
+
+def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1e-6, inner_tol: float = 1e-2,
+                  max_iter: int = 400, restart: int = 40, work=None, out=None, raise_on_fail: bool = True):
+    """Many-right-hand-side solve on the tensor cores; returns (W, infos)."""
+    B, n_t, n_x = F.shape
+    opts = capi.SolveOpts(tol, max_iter, restart, int(D_bf16 is not None))
+    infos = (capi.SolveInfo * B)()
+    if out is None:
+        out = torch.empty_like(F)
+    if work is None:
+        nb = ctypes.c_size_t()
+        ctx.check(ctx.lib.stbem_solve_batched_workspace_bytes(n_t, n_x, B, restart, ctypes.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=F.device)
+    Vs = list(V_slices) + [None] * (3 - len(V_slices))
+    code = ctx.lib.stbem_solve_batched(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]), _ptr(D_bf16),
+                                       _ptr(L), _ptr(F), _ptr(out), ctypes.byref(opts), float(inner_tol), infos,
+                                       _ptr(work), work.numel())
+    res = [{"iterations": i.iterations, "status": i.status, "rel_residual": i.rel_residual} for i in infos]
+    if code != capi.STBEM_OK and raise_on_fail:
+        ctx.check(code)
+    return out, res

@@ -298,10 +298,280 @@ int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, c
     return fail(ctx, STBEM_ERR_ARG, "apply_tc: A and x must be 16-byte aligned");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_tc: set device");
   CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_tc: reset error word");
-  CUDA_TRY(ctx, stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, ctx->stream), "apply_tc");
+  CUDA_TRY(ctx, stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, false, ctx->stream), "apply_tc");
   int flag = 0;
   CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc: read error word");
   if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc: a pipeline wait timed out");
+  return STBEM_OK;
+}
+
+
+int stbem_bf16_split3(stbem_ctx* ctx, size_t n, const double* src, void* hi, void* mid, void* lo) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!src || !hi) return fail(ctx, STBEM_ERR_ARG, "bf16_split3: NULL pointer");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "bf16_split3: set device");
+  CUDA_TRY(ctx, stbem::bf16_split3_launch(src, hi, mid, lo, n, ctx->stream), "bf16_split3");
+  return STBEM_OK;
+}
+
+namespace {
+// y = sum over slice pairs (s, t), s + t <= 2, of A_s x_t on the tensor cores,
+// with x split into three BF16 slices in `xs` (3 n_rhs n_t n_x BF16).
+cudaError_t apply_tc3(int nt, int nx, const void* const A[3], int B, const double* x, double* y, void* xs,
+                      cudaStream_t s) {
+  const size_t n = (size_t)B * nt * nx;
+  char* base = static_cast<char*>(xs);
+  void* X[3] = {base, base + n * 2, base + 2 * n * 2};
+  cudaError_t e = stbem::bf16_split3_launch(x, X[0], X[1], X[2], n, s);
+  if (e != cudaSuccess) return e;
+  bool first = true;
+  for (int sa = 0; sa < 3; ++sa)
+    for (int sx = 0; sx + sa < 3; ++sx) {
+      if (!A[sa]) continue;
+      e = stbem::apply_tc_launch(nt, nx, A[sa], B, X[sx], y, !first, s);
+      if (e != cudaSuccess) return e;
+      first = false;
+    }
+  return cudaSuccess;
+}
+}  // namespace
+
+int stbem_apply_tc3_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1) return STBEM_ERR_ARG;
+  *bytes = 3 * (size_t)n_rhs * n_t * n_x * 2;
+  return STBEM_OK;
+}
+
+int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* A_hi, const void* A_mid, const void* A_lo,
+                    int n_rhs, const double* x, double* y, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A_hi || !x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "apply_tc3: NULL pointer");
+  if (!stbem::apply_tc_supported(n_t, n_x, n_rhs)) return fail(ctx, STBEM_ERR_ARG, "apply_tc3: unsupported sizes");
+  if (work_bytes < 3 * (size_t)n_rhs * n_t * n_x * 2) return fail(ctx, STBEM_ERR_NOMEM, "apply_tc3: workspace too small");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_tc3: set device");
+  CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_tc3: reset error word");
+  const void* A[3] = {A_hi, A_mid, A_lo};
+  CUDA_TRY(ctx, apply_tc3(n_t, n_x, A, n_rhs, x, y, work, ctx->stream), "apply_tc3");
+  int flag = 0;
+  CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc3: read error word");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc3: a pipeline wait timed out");
+  return STBEM_OK;
+}
+
+int stbem_rhs_g_batched(stbem_ctx* ctx, const stbem_mesh* m, int n_src, const double* ys, double* G) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !ys || !G || n_src < 1) return fail(ctx, STBEM_ERR_ARG, "rhs_g_batched: bad arguments");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "rhs_g_batched: set device");
+  const size_t N = (size_t)m->n_t * m->N;
+  for (int k = 0; k < n_src; ++k)
+    CUDA_TRY(ctx, stbem::rhs_g_launch(m->dev, ys[2 * k], ys[2 * k + 1], G + k * N, ctx->stream), "rhs_g_batched");
+  return STBEM_OK;
+}
+
+int stbem_half_mass_add(stbem_ctx* ctx, const stbem_mesh* m, int n_rhs, const double* G, double* F) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !G || !F || n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "half_mass_add: bad arguments");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "half_mass_add: set device");
+  CUDA_TRY(ctx, stbem::half_mass_add_launch(m->dev, G, F, ctx->stream, n_rhs), "half_mass_add");
+  return STBEM_OK;
+}
+
+// ---------------------------------------------------------- batched GMRES ------
+namespace {
+
+struct BatchWork {
+  double *Q, *Z, *U, *R, *DW, *h;   // h: device scratch for small batched results
+  void* xb;                          // BF16 vector scratch (3 slices)
+};
+
+size_t batch_bytes(int nt, int nx, int B, int m) {
+  const size_t n = (size_t)B * nt * nx;
+  return ((size_t)(m + 1) * n + 4 * n + (size_t)(m + 4) * B) * sizeof(double) + 3 * n * 2 + 256;
+}
+
+}  // namespace
+
+int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || restart < 1) return STBEM_ERR_ARG;
+  *bytes = batch_bytes(n_t, n_x, n_rhs, restart);
+  return STBEM_OK;
+}
+
+int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
+                        const void* V_lo, const void* D_bf16, const double* Lm, const double* F, double* W,
+                        const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos, void* work,
+                        size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!V_hi || !F || !W || !opts || !infos || !work) return fail(ctx, STBEM_ERR_ARG, "solve_batched: NULL pointer");
+  if (!stbem::apply_tc_supported(nt, nx, B)) return fail(ctx, STBEM_ERR_ARG, "solve_batched: unsupported sizes");
+  const int m = opts->restart, maxit = opts->max_iter;
+  if (m < 1 || maxit < 1 || !(opts->tol > 0) || !(inner_tol > 0) || !(inner_tol < 1))
+    return fail(ctx, STBEM_ERR_ARG, "solve_batched: bad options");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!D_bf16 || !Lm)) return fail(ctx, STBEM_ERR_ARG, "solve_batched: preconditioner needs D and L");
+  if (work_bytes < batch_bytes(nt, nx, B, m)) return fail(ctx, STBEM_ERR_NOMEM, "solve_batched: workspace too small");
+  const size_t N = (size_t)nt * nx, n = (size_t)B * N;
+  BatchWork Wk;
+  double* p = static_cast<double*>(work);
+  Wk.Q = p; p += (size_t)(m + 1) * n;
+  Wk.Z = p; p += n;
+  Wk.U = p; p += n;
+  Wk.R = p; p += n;
+  Wk.DW = p; p += n;
+  Wk.h = p; p += (size_t)(m + 4) * B;
+  Wk.xb = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_batched: set device");
+  cudaStream_t s = ctx->stream;
+  CUDA_TRY(ctx, stbem::tc_error_reset(s), "solve_batched: reset error word");
+  const void* Vs[3] = {V_hi, V_mid, V_lo};
+
+  std::vector<double> hbuf((size_t)(m + 1) * B), h2((size_t)(m + 1) * B), nrm(B), inv(B);
+  auto bnorms = [&](const double* X, std::vector<double>& out) -> cudaError_t {
+    cudaError_t e = stbem::bdots_launch(X, 1, X, B, N, Wk.h, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(out.data(), Wk.h, B * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int b = 0; b < B; ++b) out[b] = std::sqrt(out[b]);
+    return e;
+  };
+  // preconditioner: y = L^{-1} D L^{-1} x on the tensor cores (or y = x)
+  auto applyP = [&](const double* x, double* y) -> cudaError_t {
+    if (!prec) return cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = stbem::diag_div_launch(x, Lm, Wk.Z, B * nt, nx, s);
+    if (e == cudaSuccess) e = stbem::to_bf16_launch(STBEM_F64, Wk.Z, Wk.xb, n, s);
+    if (e == cudaSuccess) e = stbem::apply_tc_launch(nt, nx, D_bf16, B, Wk.xb, y, false, s);
+    if (e == cudaSuccess) e = stbem::diag_div_launch(y, Lm, y, B * nt, nx, s);
+    return e;
+  };
+
+  std::vector<double> normF(B), rn(B);
+  CUDA_TRY(ctx, bnorms(F, normF), "solve_batched: norm F");
+  CUDA_TRY(ctx, cudaMemsetAsync(W, 0, n * sizeof(double), s), "solve_batched: zero W");
+  CUDA_TRY(ctx, cudaMemcpyAsync(Wk.R, F, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "solve_batched: R");
+  for (int b = 0; b < B; ++b) {
+    infos[b].iterations = 0;
+    infos[b].status = std::isfinite(normF[b]) ? STBEM_OK : STBEM_ERR_NAN;
+    infos[b].rel_residual = 0.0;
+  }
+  int total = 0;
+  bool any_active = true;
+  for (int outer = 0; outer < 30 && any_active; ++outer) {
+    CUDA_TRY(ctx, bnorms(Wk.R, rn), "solve_batched: norm R");
+    std::vector<char> active(B, 0);
+    any_active = false;
+    for (int b = 0; b < B; ++b) {
+      const double rel = normF[b] > 0 ? rn[b] / normF[b] : 0.0;
+      if (!std::isfinite(rel)) infos[b].status = STBEM_ERR_NAN;
+      infos[b].rel_residual = rel;
+      active[b] = infos[b].status == STBEM_OK && rel > opts->tol;
+      any_active = any_active || active[b];
+    }
+    if (!any_active) break;
+    if (total >= maxit) {
+      for (int b = 0; b < B; ++b)
+        if (active[b]) infos[b].status = STBEM_ERR_NOCONV;
+      break;
+    }
+    // inner: lockstep GMRES on the BF16 V for all right-hand sides
+    for (int b = 0; b < B; ++b) inv[b] = (active[b] && rn[b] > 0) ? 1.0 / rn[b] : 0.0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(Wk.h, inv.data(), B * sizeof(double), cudaMemcpyHostToDevice, s), "inv");
+    CUDA_TRY(ctx, stbem::bscale_launch(Wk.R, Wk.h, Wk.Q, B, N, s), "q0");
+    std::vector<double> H((size_t)B * (m + 1) * m, 0.0), cs((size_t)B * m), sn((size_t)B * m),
+        g((size_t)B * (m + 1), 0.0);
+    std::vector<int> kb(B, 0);
+    std::vector<char> done(B, 0);
+    for (int b = 0; b < B; ++b) {
+      g[(size_t)b * (m + 1)] = active[b] ? rn[b] : 0.0;
+      done[b] = !active[b];
+    }
+    int kmax = 0;
+    for (int k = 0; k < m; ++k) {
+      double* qk = Wk.Q + (size_t)k * n;
+      double* qk1 = Wk.Q + (size_t)(k + 1) * n;
+      CUDA_TRY(ctx, applyP(qk, Wk.DW), "P q");
+      CUDA_TRY(ctx, stbem::to_bf16_launch(STBEM_F64, Wk.DW, Wk.xb, n, s), "bf16 z");
+      CUDA_TRY(ctx, stbem::apply_tc_launch(nt, nx, V_hi, B, Wk.xb, Wk.U, false, s), "V z");
+      CUDA_TRY(ctx, stbem::bdots_launch(Wk.Q, k + 1, Wk.U, B, N, Wk.h, s), "dots");
+      CUDA_TRY(ctx, stbem::bsub_comb_launch(Wk.Q, k + 1, Wk.h, Wk.U, B, N, s), "orth");
+      CUDA_TRY(ctx, cudaMemcpyAsync(hbuf.data(), Wk.h, (size_t)(k + 1) * B * sizeof(double), cudaMemcpyDeviceToHost, s), "h");
+      CUDA_TRY(ctx, stbem::bdots_launch(Wk.Q, k + 1, Wk.U, B, N, Wk.h, s), "dots2");
+      CUDA_TRY(ctx, stbem::bsub_comb_launch(Wk.Q, k + 1, Wk.h, Wk.U, B, N, s), "orth2");
+      CUDA_TRY(ctx, cudaMemcpyAsync(h2.data(), Wk.h, (size_t)(k + 1) * B * sizeof(double), cudaMemcpyDeviceToHost, s), "h2");
+      CUDA_TRY(ctx, bnorms(Wk.U, nrm), "norm u");
+      for (int b = 0; b < B; ++b) inv[b] = (!done[b] && nrm[b] > 0 && std::isfinite(nrm[b])) ? 1.0 / nrm[b] : 0.0;
+      CUDA_TRY(ctx, cudaMemcpyAsync(Wk.h, inv.data(), B * sizeof(double), cudaMemcpyHostToDevice, s), "inv");
+      CUDA_TRY(ctx, stbem::bscale_launch(Wk.U, Wk.h, qk1, B, N, s), "q");
+      ++total;
+      kmax = k + 1;
+      bool all_done = true;
+      for (int b = 0; b < B; ++b) {
+        if (done[b]) continue;
+        double* Hb = H.data() + (size_t)b * (m + 1) * m;
+        double* gb = g.data() + (size_t)b * (m + 1);
+        double* cb = cs.data() + (size_t)b * m;
+        double* sb = sn.data() + (size_t)b * m;
+        std::vector<double> col(k + 2);
+        for (int t = 0; t <= k; ++t) col[t] = hbuf[(size_t)t * B + b] + h2[(size_t)t * B + b];
+        const double hk1 = nrm[b];
+        bool bad = !std::isfinite(hk1);
+        for (int t = 0; t <= k; ++t) bad = bad || !std::isfinite(col[t]);
+        if (bad) {
+          infos[b].status = STBEM_ERR_NAN;
+          done[b] = 1;
+          kb[b] = 0;
+          continue;
+        }
+        for (int t = 0; t < k; ++t) {
+          const double a = cb[t] * col[t] + sb[t] * col[t + 1];
+          col[t + 1] = -sb[t] * col[t] + cb[t] * col[t + 1];
+          col[t] = a;
+        }
+        const double den = std::hypot(col[k], hk1);
+        cb[k] = den > 0 ? col[k] / den : 1.0;
+        sb[k] = den > 0 ? hk1 / den : 0.0;
+        col[k] = den;
+        gb[k + 1] = -sb[k] * gb[k];
+        gb[k] = cb[k] * gb[k];
+        for (int t = 0; t <= k; ++t) Hb[(size_t)t * m + k] = col[t];
+        kb[b] = k + 1;
+        const double est = std::fabs(gb[k + 1]) / rn[b];
+        if (est <= inner_tol || hk1 == 0.0) done[b] = 1;
+        all_done = all_done && done[b];
+      }
+      if (all_done || total >= maxit) break;
+    }
+    // per right-hand side y_b = H_b^{-1} g_b, zero-padded to kmax
+    std::vector<double> Y((size_t)kmax * B, 0.0);
+    for (int b = 0; b < B; ++b) {
+      const int kk = kb[b];
+      const double* Hb = H.data() + (size_t)b * (m + 1) * m;
+      const double* gb = g.data() + (size_t)b * (m + 1);
+      std::vector<double> y(kk, 0.0);
+      for (int t = kk - 1; t >= 0; --t) {
+        double acc = gb[t];
+        for (int u = t + 1; u < kk; ++u) acc -= Hb[(size_t)t * m + u] * y[u];
+        y[t] = Hb[(size_t)t * m + t] != 0.0 ? acc / Hb[(size_t)t * m + t] : 0.0;
+      }
+      for (int t = 0; t < kk; ++t) Y[(size_t)t * B + b] = y[t];
+      infos[b].iterations = total;
+    }
+    if (kmax > 0) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(Wk.h, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, s), "Y");
+      CUDA_TRY(ctx, stbem::bcomb_launch(Wk.Q, kmax, Wk.h, Wk.U, B, N, s), "QY");
+      CUDA_TRY(ctx, applyP(Wk.U, Wk.DW), "P QY");
+      CUDA_TRY(ctx, stbem::axpy_launch(1.0, Wk.DW, W, n, s), "W += dW");
+    }
+    // refinement residual R = F - V W with the three-slice split of V and W
+    CUDA_TRY(ctx, apply_tc3(nt, nx, Vs, B, W, Wk.U, Wk.xb, s), "V W");
+    CUDA_TRY(ctx, stbem::sub_launch(F, Wk.U, Wk.R, n, s), "R");
+  }
+  int flag = 0;
+  CUDA_TRY(ctx, stbem::tc_error_read(&flag, s), "solve_batched: read error word");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "solve_batched: a tensor-core pipeline wait timed out");
+  int worst = STBEM_OK;
+  for (int b = 0; b < B; ++b)
+    if (infos[b].status != STBEM_OK) worst = infos[b].status;
+  if (worst != STBEM_OK) return fail(ctx, worst, "solve_batched: some right-hand sides did not converge");
   return STBEM_OK;
 }
 

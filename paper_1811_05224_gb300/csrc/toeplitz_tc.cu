@@ -143,7 +143,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_apply_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int nt, int nx,
-               double* __restrict__ Y) {
+               int accumulate, double* __restrict__ Y) {
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
   unsigned char* smA = reinterpret_cast<unsigned char*>(base);
@@ -223,7 +223,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           const int m = m0 + c0 + t;
-          if (m < nt) Y[((size_t)b * nt + m) * nx + gi] = (double)__uint_as_float(r[t]);
+          if (m < nt) {
+            double* yp = Y + ((size_t)b * nt + m) * nx + gi;
+            const double v = (double)__uint_as_float(r[t]);
+            *yp = accumulate ? *yp + v : v;
+          }
         }
       }
     }
@@ -265,7 +269,7 @@ bool apply_tc_supported(int nt, int nx, int n_rhs) {
 }
 
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            cudaStream_t s) {
+                            bool accumulate, cudaStream_t s) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap mA, mX;
@@ -285,7 +289,7 @@ cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const
   cudaError_t e = cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const dim3 grid((nx + BM - 1) / BM, (nt + BN - 1) / BN, n_rhs);
-  k_apply_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mX, nt, nx, Y);
+  k_apply_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -299,6 +303,31 @@ cudaError_t tc_error_read(int* flag, cudaStream_t s) {
   cudaError_t e = cudaMemcpyFromSymbolAsync(flag, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
+}
+
+// Three-term BF16 split of an FP64 array: hi = bf16(x), mid = bf16(x - hi),
+// lo = bf16(x - hi - mid), so that x - (hi + mid + lo) is ~2^-24 |x|.
+__global__ void k_bf16_split3(const double* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                              __nv_bfloat16* __restrict__ mid, __nv_bfloat16* __restrict__ lo, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[e];
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(m);
+    hi[e] = h;
+    if (mid) mid[e] = m;
+    if (lo) lo[e] = __double2bfloat16(r2);
+  }
+}
+
+cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo, size_t n, cudaStream_t s) {
+  const size_t blocks_needed = (n + 255) / 256;
+  const int blocks = (int)(blocks_needed < 152 * 16 ? (blocks_needed ? blocks_needed : 1) : 152 * 16);
+  k_bf16_split3<<<blocks, 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(mid),
+                                        static_cast<__nv_bfloat16*>(lo), n);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s) {

@@ -8,7 +8,9 @@ namespace stbem {
 bool apply_tc_supported(int nt, int nx, int n_rhs);
 // y (FP64) = block-Toeplitz product of BF16 lag blocks A with BF16 x, on tcgen05
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            cudaStream_t s);
+                            bool accumulate, cudaStream_t s);
+// hi/mid/lo BF16 slices of an FP64 array (mid and lo may be NULL)
+cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo, size_t n, cudaStream_t s);
 cudaError_t tc_error_reset(cudaStream_t s);
 cudaError_t tc_error_read(int* flag, cudaStream_t s);
 cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s);

@@ -28,13 +28,14 @@ __global__ void k_rhs_g(DevMesh M, double ysx, double ysy, double* __restrict__ 
   }
 }
 
-// f[m][i] += (1/2) M_h g: M_h[(i,m),(p,m)] = ht h_i / 2 for p in {i, i+1}
-__global__ void k_half_mass_add(DevMesh M, const double* __restrict__ g, double* __restrict__ f) {
-  const int total = M.n_t * M.N;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int i = e % M.N, m = e / M.N;
+// f[b][m][i] += (1/2) M_h g[b]: M_h[(i,m),(p,m)] = ht h_i / 2 for p in {i, i+1}
+__global__ void k_half_mass_add(DevMesh M, int B, const double* __restrict__ g, double* __restrict__ f) {
+  const size_t total = (size_t)B * M.n_t * M.N;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M.N);
+    const size_t row = e - i;                 // start of this (b, m) row
     const int ip = (i + 1) % M.N;
-    const double hm = 0.5 * M.ht * 0.5 * M.slen[i] * (g[e] + g[(size_t)m * M.N + ip]);
+    const double hm = 0.5 * M.ht * 0.5 * M.slen[i] * (g[e] + g[row + ip]);
     f[e] = hm + f[e];
   }
 }
@@ -125,6 +126,52 @@ __global__ void k_round_f32(const double* __restrict__ src, float* __restrict__ 
     dst[e] = (float)src[e];
 }
 
+__global__ void k_bdots(const double* __restrict__ Q, const double* __restrict__ U, int B, size_t n,
+                        double* __restrict__ out) {
+  __shared__ double red[kRedThreads];
+  const int b = blockIdx.x, t = blockIdx.y;
+  const double* q = Q + ((size_t)t * B + b) * n;
+  const double* u = U + (size_t)b * n;
+  double s = 0.0;
+  for (size_t e = threadIdx.x; e < n; e += kRedThreads) s = fma(q[e], u[e], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)t * B + b] = red[0];
+}
+
+__global__ void k_bsub_comb(const double* __restrict__ Q, int k, const double* __restrict__ H,
+                            double* __restrict__ U, int B, size_t n) {
+  const size_t total = (size_t)B * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / n);
+    double v = U[e];
+    for (int t = 0; t < k; ++t) v -= H[(size_t)t * B + b] * Q[(size_t)t * total + e];
+    U[e] = v;
+  }
+}
+
+__global__ void k_bcomb(const double* __restrict__ Q, int k, const double* __restrict__ C, double* __restrict__ Y,
+                        int B, size_t n) {
+  const size_t total = (size_t)B * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / n);
+    double v = 0.0;
+    for (int t = 0; t < k; ++t) v += C[(size_t)t * B + b] * Q[(size_t)t * total + e];
+    Y[e] = v;
+  }
+}
+
+__global__ void k_bscale(const double* __restrict__ X, const double* __restrict__ a, double* __restrict__ Y, int B,
+                         size_t n) {
+  const size_t total = (size_t)B * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    Y[e] = a[e / n] * X[e];
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
@@ -135,8 +182,8 @@ cudaError_t rhs_g_launch(const DevMesh& M, double ysx, double ysy, double* g, cu
   count_launches(1);
   return cudaGetLastError();
 }
-cudaError_t half_mass_add_launch(const DevMesh& M, const double* g, double* f, cudaStream_t s) {
-  k_half_mass_add<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, g, f);
+cudaError_t half_mass_add_launch(const DevMesh& M, const double* g, double* f, cudaStream_t s, int B) {
+  k_half_mass_add<<<grid_for((size_t)B * M.n_t * M.N), 256, 0, s>>>(M, B, g, f);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -167,6 +214,26 @@ cudaError_t axpy_launch(double a, const double* x, double* y, size_t n, cudaStre
 }
 cudaError_t sub_launch(const double* a, const double* b, double* y, size_t n, cudaStream_t s) {
   k_sub<<<grid_for(n), 256, 0, s>>>(a, b, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t bdots_launch(const double* Q, int k, const double* U, int B, size_t n, double* out, cudaStream_t s) {
+  k_bdots<<<dim3(B, k), kRedThreads, 0, s>>>(Q, U, B, n, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t bsub_comb_launch(const double* Q, int k, const double* H, double* U, int B, size_t n, cudaStream_t s) {
+  k_bsub_comb<<<grid_for((size_t)B * n), 256, 0, s>>>(Q, k, H, U, B, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t bcomb_launch(const double* Q, int k, const double* C, double* Y, int B, size_t n, cudaStream_t s) {
+  k_bcomb<<<grid_for((size_t)B * n), 256, 0, s>>>(Q, k, C, Y, B, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t bscale_launch(const double* X, const double* a, double* Y, int B, size_t n, cudaStream_t s) {
+  k_bscale<<<grid_for((size_t)B * n), 256, 0, s>>>(X, a, Y, B, n);
   count_launches(1);
   return cudaGetLastError();
 }

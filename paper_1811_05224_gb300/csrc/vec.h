@@ -5,7 +5,7 @@
 
 namespace stbem {
 cudaError_t rhs_g_launch(const DevMesh& M, double ysx, double ysy, double* g, cudaStream_t s);
-cudaError_t half_mass_add_launch(const DevMesh& M, const double* g, double* f, cudaStream_t s);
+cudaError_t half_mass_add_launch(const DevMesh& M, const double* g, double* f, cudaStream_t s, int B = 1);
 cudaError_t lumped_mass_launch(const DevMesh& M, double* L, cudaStream_t s);
 // out[k] = <Q[k], v>, k = 0..k-1 (deterministic block reductions)
 cudaError_t dots_launch(const double* Q, int k, const double* v, size_t n, double* out, cudaStream_t s);
@@ -18,6 +18,15 @@ cudaError_t axpy_launch(double a, const double* x, double* y, size_t n, cudaStre
 cudaError_t sub_launch(const double* a, const double* b, double* y, size_t n, cudaStream_t s);  // y = a - b
 // y[m][i] = x[m][i] / L[i]
 cudaError_t diag_div_launch(const double* x, const double* L, double* y, int nt, int nx, cudaStream_t s);
+// batched (B right-hand sides of length n each, vectors [B][n], basis [k][B][n]):
+// out[t][b] = <Q[t][b], U[b]>, t < k, one block per dot, fixed-order reduction
+cudaError_t bdots_launch(const double* Q, int k, const double* U, int B, size_t n, double* out, cudaStream_t s);
+// U[b] -= sum_t H[t][b] Q[t][b]
+cudaError_t bsub_comb_launch(const double* Q, int k, const double* H, double* U, int B, size_t n, cudaStream_t s);
+// Y[b] = sum_t C[t][b] Q[t][b]
+cudaError_t bcomb_launch(const double* Q, int k, const double* C, double* Y, int B, size_t n, cudaStream_t s);
+// Y[b] = a[b] X[b]
+cudaError_t bscale_launch(const double* X, const double* a, double* Y, int B, size_t n, cudaStream_t s);
 // dst[i] = (float)src[i]
 cudaError_t round_f32_launch(const double* src, float* dst, size_t n, cudaStream_t s);
 }  // namespace stbem

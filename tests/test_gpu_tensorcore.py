@@ -54,3 +54,46 @@ def test_apply_tc_rejects_bad_sizes(ctx):
     with pytest.raises(capi.StbemError) as e:
         P.apply_tc(ctx, A, x)
     assert e.value.code == capi.STBEM_ERR_ARG
+
+
+def test_apply_tc3_accuracy(ctx):
+    """Three-slice split product: ~1e-6 of |A||x| (FP32 accumulation), far
+    below a single BF16 product."""
+    import paper_1811_05224_gb300 as P
+    rng = np.random.default_rng(5)
+    nt, nx, nb = 40, 48, 2
+    A = torch.as_tensor(rng.standard_normal((nt, nx, nx))).cuda()
+    x = torch.as_tensor(rng.standard_normal((nb, nt, nx))).cuda()
+    y = P.apply_tc3(ctx, P.bf16_split3(ctx, A), x).cpu().numpy()
+    An, xn = A.cpu().numpy(), x.cpu().numpy()
+    for b in range(nb):
+        ref = OS.toeplitz_apply(An, xn[b])
+        mag = OS.toeplitz_apply(np.abs(An), np.abs(xn[b]))
+        assert np.all(np.abs(y[b] - ref) <= 2e-5 * mag)
+        assert float(np.abs(y[b] - ref).max() / mag.max()) < 2e-6
+
+
+def test_batched_solve_matches_fp64_solves(ctx):
+    """Batched tensor-core solve of several right-hand sides against the FP64
+    single-right-hand-side solves (L-shape, seeded sources)."""
+    import paper_1811_05224_gb300 as P
+    import workloads as W
+    X = W.l_shape(48, seed=3)
+    nt = 40
+    m = P.Mesh(ctx, X, 1.0, nt, 1.0)
+    V = P.assemble(ctx, m, "V")
+    K = P.assemble(ctx, m, "K")
+    D = P.assemble(ctx, m, "D")
+    L = P.lumped_mass(ctx, m)
+    ys = W.annulus_sources(4, seed=4)
+    G, F = P.rhs_batched(ctx, m, P.bf16_split3(ctx, K), ys)
+    Wb, infos = P.solve_batched(ctx, P.bf16_split3(ctx, V), F, P.to_bf16(ctx, D), L, tol=2e-6)
+    assert all(i["status"] == 0 for i in infos), infos
+    for b in range(len(ys)):
+        g1, f1 = P.rhs(ctx, m, K, ys[b])
+        # the split product is ~1e-6 of |K||G|; K g cancels, so ~1e-5 of |f|
+        assert float((F[b] - f1).norm() / f1.norm()) < 3e-5
+        w1, info = P.solve(ctx, V, f1, D, L, tol=1e-10)
+        r = F[b] - P.apply(ctx, V, Wb[b])           # FP64 residual of the batched system
+        assert float(r.norm() / F[b].norm()) < 5e-6
+        assert float((Wb[b] - w1).norm() / w1.norm()) < 3e-4
