@@ -155,6 +155,82 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def run_batched(ctx, dev, stream, n_src=256):
+    """square512 with 256 right-hand sides g_k = U*(x - y_k, t), y_k seeded on
+    the annulus 1.2 < |y - (0.5, 0.5)| < 3: batched tensor-core solve, timed
+    with CUDA events, beside one FP64 single-right-hand-side solve."""
+    import torch
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    p = W.config("square512")
+    nt, nx = p.n_t, p.n_x
+    mesh = P.Mesh(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    e = [ev() for _ in range(8)]
+    e[0].record(stream)
+    V = P.assemble(ctx, mesh, "V")
+    e[1].record(stream)
+    K = P.assemble(ctx, mesh, "K")
+    e[2].record(stream)
+    D32 = P.assemble(ctx, mesh, "D", "f32")
+    e[3].record(stream)
+    V3 = P.bf16_split3(ctx, V)
+    K3 = P.bf16_split3(ctx, K)
+    Db = P.to_bf16(ctx, D32)
+    L = P.lumped_mass(ctx, mesh)
+    ys = W.annulus_sources(n_src, seed=4)
+    e[4].record(stream)
+    G, F = P.rhs_batched(ctx, mesh, K3, ys)
+    e[5].record(stream)
+    Wb, infos = P.solve_batched(ctx, V3, F, Db, L, tol=2e-6, inner_tol=1e-2, restart=40, max_iter=400)
+    e[6].record(stream)
+    torch.cuda.synchronize(dev)
+    # tensor-core product alone: V (BF16) on all right-hand sides
+    xb = P.to_bf16(ctx, Wb)
+    for _ in range(2):
+        P.apply_tc(ctx, V3[0], xb)
+    a0, a1 = ev(), ev()
+    a0.record(stream)
+    P.apply_tc(ctx, V3[0], xb)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    tc_ms = a0.elapsed_time(a1)
+    tc_flops = 2.0 * nx * nx * nt * (nt + 1) / 2 * n_src
+    # one FP64 single-right-hand-side solve of the same system for comparison
+    D64 = P.assemble(ctx, mesh, "D")
+    g1, f1 = P.rhs(ctx, mesh, K, ys[0])
+    s0, s1 = ev(), ev()
+    s0.record(stream)
+    w1, info1 = P.solve(ctx, V, f1, D64, L, tol=1e-8)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    one_ms = s0.elapsed_time(s1)
+    rel = float((Wb[0] - w1).norm() / w1.norm())
+    r0 = F[0] - P.apply(ctx, V, Wb[0])
+    peaks = _peaks()
+    bf16_peak = float(peaks.get("bf16_tflops", 1867.6))
+    out = {
+        "workload": "square512 x 256 sources (annulus 1.2..3, seed 4)",
+        "assembly_ms": {"V_f64": e[0].elapsed_time(e[1]), "K_f64": e[1].elapsed_time(e[2]),
+                        "D_f32": e[2].elapsed_time(e[3])},
+        "rhs_ms": e[4].elapsed_time(e[5]),
+        "solve_ms": e[5].elapsed_time(e[6]),
+        "inner_iterations": max(i["iterations"] for i in infos),
+        "max_rel_residual": max(i["rel_residual"] for i in infos),
+        "fp64_rel_residual_rhs0": float(r0.norm() / F[0].norm()),
+        "w_rel_diff_vs_fp64_solve_rhs0": rel,
+        "fp64_single_solve_ms": one_ms, "fp64_single_solve_iterations": info1["iterations"],
+        "fp64_256_sequential_solves_ms_projected": one_ms * n_src,
+        "tc_apply": {"ms": tc_ms, "tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
+                     "frac_of_bf16_peak": tc_flops / (tc_ms * 1e-3) / 1e12 / bf16_peak,
+                     "peak_tflops": bf16_peak, "peak": "measured bf16 burst (MEASURED_PEAKS.json)"},
+    }
+    for t in (V, K, D32, D64, V3, K3, Db, G, F, Wb):
+        del t
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -307,6 +383,10 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     d32_ms = b0.elapsed_time(b1)
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(ctx, dev, stream)
+
     # end to end through the public API with host buffers: vertices in, w out
     verts = np.ascontiguousarray(p.vertices)
     w_host = torch.empty((nt, nx), dtype=torch.float64).pin_memory()
@@ -354,6 +434,7 @@ def run_ours(args):
                       "rel_residual_fp64": mixed_info["rel_residual"],
                       "w_rel_diff_vs_fp64": mixed_rel, "assembly_D_f32_ms": d32_ms,
                       "note": "FP64 V,K; FP32 D (FP64 singular pairs); FP64 refinement around FP32 GMRES"},
+            "batched": batched,
         },
         "roofline": {"kernel": "k_tile<D, f64> lags >= 2", "bound": "alu",
                      "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -415,6 +496,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-right-hand-side square512 component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
     args = ap.parse_args()
