@@ -195,6 +195,13 @@ def run_batched(ctx, dev, stream, n_src=256):
     a1.record(stream)
     torch.cuda.synchronize(dev)
     tc_ms = a0.elapsed_time(a1)
+    # the same product with compensated accumulation (partials of 4 K steps),
+    # as used for the hi x hi slice product of the refinement residual
+    a0.record(stream)
+    P.apply_tc(ctx, V3[0], xb, chunk=4)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    tc4_ms = a0.elapsed_time(a1)
     tc_flops = 2.0 * nx * nx * nt * (nt + 1) / 2 * n_src
     # one FP64 single-right-hand-side solve of the same system for comparison
     D64 = P.assemble(ctx, mesh, "D")
@@ -224,6 +231,8 @@ def run_batched(ctx, dev, stream, n_src=256):
         "tc_apply": {"ms": tc_ms, "tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                      "frac_of_bf16_peak": tc_flops / (tc_ms * 1e-3) / 1e12 / bf16_peak,
                      "peak_tflops": bf16_peak, "peak": "measured bf16 burst (MEASURED_PEAKS.json)"},
+        "tc_apply_compensated_chunk4": {"ms": tc4_ms, "tflops": tc_flops / (tc4_ms * 1e-3) / 1e12,
+                                        "frac_of_bf16_peak": tc_flops / (tc4_ms * 1e-3) / 1e12 / bf16_peak},
     }
     for t in (V, K, D32, D64, V3, K3, Db, G, F, Wb):
         del t

@@ -162,6 +162,15 @@ int stbem_to_bf16(stbem_ctx* ctx, int src_prec, size_t n, const void* dev_src, v
 int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_bf16, int n_rhs, const void* dev_x_bf16,
                    double* dev_y);
 
+/* The same product with compensated accumulation: the tensor cores restart
+ * their FP32 accumulator every `chunk` 64-wide K steps (chunk >= 1; one K
+ * step is four MMA roundings) and each finished partial is added into a Kahan
+ * (sum, compensation) pair per output, so the rounding error no longer grows
+ * with the number of lags.  Same arguments, layout and errors as
+ * stbem_apply_tc, plus STBEM_ERR_ARG for chunk < 1. */
+int stbem_apply_tc_comp(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_bf16, int n_rhs,
+                        const void* dev_x_bf16, double* dev_y, int chunk);
+
 /* Right-hand side of eq. (4) for u_0 = 0 and the Dirichlet datum
  * g = U*(x - y*, t) (y* outside the domain):
  *   dev_g[n][p] = time average of g at vertex p over tau_n,
@@ -236,9 +245,10 @@ int stbem_bf16_split3(stbem_ctx* ctx, size_t n, const double* dev_src, void* dev
 /* Accurate many-right-hand-side product on the tensor cores: with A given by
  * its three BF16 slices (stbem_bf16_split3; dev_A_mid / dev_A_lo may be NULL)
  * and x (FP64) split the same way inside the call, y = sum of the six slice
- * products A_s x_t with s + t <= 2, each accumulated in FP32, summed in FP64:
- * about 1e-6 relative to |A| |x| (the FP32 accumulation), against ~4e-3 for
- * one BF16 product.  Workspace: stbem_apply_tc3_workspace_bytes() (the three
+ * products A_s x_t with s + t <= 2, each with the compensated accumulation of
+ * stbem_apply_tc_comp (partials of 4 K steps for hi x hi, 16 for the rest),
+ * summed in FP64: a few 1e-7 relative to |A| |x|, against ~4e-3 for one BF16
+ * product and ~4e-4 for the uncompensated split product over 512 lags.  Workspace: stbem_apply_tc3_workspace_bytes() (the three
  * slices of x).  Blocks the host.  Errors as stbem_apply_tc, STBEM_ERR_NOMEM. */
 int stbem_apply_tc3_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes);
 int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_hi, const void* dev_A_mid,

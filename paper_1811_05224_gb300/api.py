@@ -201,14 +201,20 @@ def to_bf16(ctx: Context, src):
     return out
 
 
-def apply_tc(ctx: Context, A_bf16, x_bf16, out=None):
+def apply_tc(ctx: Context, A_bf16, x_bf16, out=None, chunk=0):
     """Tensor-core block-Toeplitz product: BF16 A (n_t, n_x, n_x) times BF16 x
-    (n_rhs, n_t, n_x), FP32 accumulation, FP64 result (n_rhs, n_t, n_x)."""
+    (n_rhs, n_t, n_x), FP32 accumulation, FP64 result (n_rhs, n_t, n_x).
+    chunk > 0 selects the compensated accumulation (FP32 partials of `chunk`
+    64-wide K steps, Kahan-summed)."""
     n_t, n_x = A_bf16.shape[0], A_bf16.shape[1]
     xb = x_bf16 if x_bf16.dim() == 3 else x_bf16.unsqueeze(0)
     if out is None:
         out = torch.empty(xb.shape, dtype=torch.float64, device=xb.device)
-    ctx.check(ctx.lib.stbem_apply_tc(ctx.h, n_t, n_x, _ptr(A_bf16), xb.shape[0], _ptr(xb), _ptr(out)))
+    if chunk:
+        ctx.check(ctx.lib.stbem_apply_tc_comp(ctx.h, n_t, n_x, _ptr(A_bf16), xb.shape[0], _ptr(xb), _ptr(out),
+                                              int(chunk)))
+    else:
+        ctx.check(ctx.lib.stbem_apply_tc(ctx.h, n_t, n_x, _ptr(A_bf16), xb.shape[0], _ptr(xb), _ptr(out)))
     return out if x_bf16.dim() == 3 else out[0]
 
 

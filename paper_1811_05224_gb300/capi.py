@@ -30,7 +30,7 @@ EXPORTS = [
     "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_assemble_lags", "stbem_apply_workspace_bytes",
     "stbem_apply", "stbem_apply_noalloc", "stbem_rhs", "stbem_lumped_mass", "stbem_solve_workspace_bytes", "stbem_solve",
     "stbem_solve_mixed_workspace_bytes", "stbem_solve_mixed", "stbem_round_f32",
-    "stbem_to_bf16", "stbem_apply_tc", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
+    "stbem_to_bf16", "stbem_apply_tc", "stbem_apply_tc_comp", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
     "stbem_apply_tc3", "stbem_rhs_g_batched", "stbem_half_mass_add", "stbem_solve_batched_workspace_bytes",
     "stbem_solve_batched",
 ]
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]
     L.stbem_to_bf16.argtypes = [vp, i, sz, vp, vp]
     L.stbem_apply_tc.argtypes = [vp, i, i, vp, i, vp, vp]
+    L.stbem_apply_tc_comp.argtypes = [vp, i, i, vp, i, vp, vp, i]
     L.stbem_bf16_split3.argtypes = [vp, sz, vp, vp, vp, vp]
     L.stbem_apply_tc3_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_apply_tc3.argtypes = [vp, i, i, vp, vp, vp, i, vp, vp, vp, sz]

@@ -288,21 +288,34 @@ int stbem_to_bf16(stbem_ctx* ctx, int src_prec, size_t n, const void* src, void*
   return STBEM_OK;
 }
 
-int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y) {
+namespace {
+int apply_tc_entry(stbem_ctx* ctx, const char* name, int n_t, int n_x, const void* A, int n_rhs, const void* x,
+                   double* y, int chunk) {
   if (!ctx) return STBEM_ERR_ARG;
-  if (!A || !x || !y) return fail(ctx, STBEM_ERR_ARG, "apply_tc: NULL pointer");
+  if (!A || !x || !y) return fail(ctx, STBEM_ERR_ARG, "%s: NULL pointer", name);
   if (!stbem::apply_tc_supported(n_t, n_x, n_rhs))
-    return fail(ctx, STBEM_ERR_ARG, "apply_tc: unsupported sizes n_t=%d n_x=%d n_rhs=%d (need n_x %% 8 == 0)", n_t,
+    return fail(ctx, STBEM_ERR_ARG, "%s: unsupported sizes n_t=%d n_x=%d n_rhs=%d (need n_x %% 8 == 0)", name, n_t,
                 n_x, n_rhs);
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(x)) & 15)
-    return fail(ctx, STBEM_ERR_ARG, "apply_tc: A and x must be 16-byte aligned");
+    return fail(ctx, STBEM_ERR_ARG, "%s: A and x must be 16-byte aligned", name);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_tc: set device");
   CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_tc: reset error word");
-  CUDA_TRY(ctx, stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, false, ctx->stream), "apply_tc");
+  CUDA_TRY(ctx, stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, false, ctx->stream, chunk), "apply_tc");
   int flag = 0;
   CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc: read error word");
-  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc: a pipeline wait timed out");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "%s: a pipeline wait timed out", name);
   return STBEM_OK;
+}
+}  // namespace
+
+int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y) {
+  return apply_tc_entry(ctx, "apply_tc", n_t, n_x, A, n_rhs, x, y, 0);
+}
+
+int stbem_apply_tc_comp(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y,
+                        int chunk) {
+  if (ctx && chunk < 1) return fail(ctx, STBEM_ERR_ARG, "apply_tc_comp: chunk must be >= 1");
+  return apply_tc_entry(ctx, "apply_tc_comp", n_t, n_x, A, n_rhs, x, y, chunk);
 }
 
 
@@ -315,8 +328,18 @@ int stbem_bf16_split3(stbem_ctx* ctx, size_t n, const double* src, void* hi, voi
 }
 
 namespace {
+// 64-wide K steps per FP32 partial in the accurate products.  Each K step is
+// four MMAs, and each MMA adds about 0.7 u (u = 2^-24) of its partial's
+// magnitude in error (measured on GB300: the error of one long FP32 chain
+// grows linearly with its length), so the hi x hi product, which carries the
+// whole magnitude, uses short partials and the five products that are 2^-8
+// smaller or less use long ones.
+constexpr int kTc3ChunkHi = 4;
+constexpr int kTc3ChunkLo = 16;
+
 // y = sum over slice pairs (s, t), s + t <= 2, of A_s x_t on the tensor cores,
-// with x split into three BF16 slices in `xs` (3 n_rhs n_t n_x BF16).
+// with x split into three BF16 slices in `xs` (3 n_rhs n_t n_x BF16), each
+// product Kahan-accumulated over FP32 partials.
 cudaError_t apply_tc3(int nt, int nx, const void* const A[3], int B, const double* x, double* y, void* xs,
                       cudaStream_t s) {
   const size_t n = (size_t)B * nt * nx;
@@ -328,7 +351,8 @@ cudaError_t apply_tc3(int nt, int nx, const void* const A[3], int B, const doubl
   for (int sa = 0; sa < 3; ++sa)
     for (int sx = 0; sx + sa < 3; ++sx) {
       if (!A[sa]) continue;
-      e = stbem::apply_tc_launch(nt, nx, A[sa], B, X[sx], y, !first, s);
+      e = stbem::apply_tc_launch(nt, nx, A[sa], B, X[sx], y, !first, s,
+                                 sa + sx == 0 ? kTc3ChunkHi : kTc3ChunkLo);
       if (e != cudaSuccess) return e;
       first = false;
     }

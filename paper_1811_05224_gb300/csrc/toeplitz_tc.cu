@@ -241,6 +241,184 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Same product with compensated accumulation.  A long FP32 accumulation chain
+// (all lags x all 64-wide K steps of one output tile: up to 4 n_t n_x / 64 MMA
+// roundings) loses accuracy in proportion to its length, which limits the
+// refinement residual of the batched solve.  Here the MMA issuer restarts the
+// accumulator every `chunk` K steps, alternating between two 128-column TMEM
+// buffers, and eight epilogue warps drain each finished chunk into a Kahan
+// (FP32 sum + FP32 compensation) pair per output while the next chunk is being
+// multiplied.  The per-output error is then about (4 chunk + 2) u |partial
+// sums| instead of 4 n_lags n_x / 64 u, u = 2^-24.
+//   warp 0: TMA producer, warp 1: MMA issuer (and TMEM owner),
+//   warps 2..17: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+//   columns 32 ((w - 2) / 4) .. + 31, so that its Kahan pairs (64 floats)
+//   stay in registers.
+constexpr int COMP_THREADS = 576;
+constexpr int COMP_EPI_WARPS = 16;
+constexpr uint32_t COMP_TMEM_COLS = 256;
+constexpr size_t COMP_SMEM_BYTES = 1024 + STAGES * (size_t)STAGE_BYTES + 512;
+
+__global__ void __launch_bounds__(COMP_THREADS, 1)
+    k_apply_tc_comp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int nt, int nx,
+                    int chunk, int accumulate, double* __restrict__ Y) {
+  extern __shared__ unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
+  unsigned char* smA = reinterpret_cast<unsigned char*>(base);
+  unsigned char* smB = smA + STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smB + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;   // [2]: chunk in buffer k complete
+  uint64_t* acc_empty = acc_full + 2;    // [2]: buffer k drained by the epilogue
+  uint64_t* done = acc_empty + 2;        // every MMA issued by warp 1 complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
+  const int dmax = min(m0 + BN - 1, nt - 1);
+  const int nj = (nx + BK - 1) / BK;
+  const int iters = (dmax + 1) * nj;
+  const int nchunks = (iters + chunk - 1) / chunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&acc_full[k], 1);
+      mbar_init(&acc_empty[k], COMP_EPI_WARPS);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, COMP_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % STAGES;
+        const uint32_t round = static_cast<uint32_t>(it / STAGES);
+        if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        const int d = it / nj, j0 = (it % nj) * BK;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_3d(&tmA, &full[s], smA + s * A_BYTES, j0, i0, d);
+        tma_load_3d(&tmX, &full[s], smB + s * B_BYTES, j0, m0 - d, b);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int buf = c & 1;
+        if (c >= 2 && !mbar_wait(&acc_empty[buf], ((c >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
+        const int it_end = min(iters, (c + 1) * chunk);
+        for (int first = 1; it < it_end; ++it, first = 0) {
+          const int s = it % STAGES;
+          const uint32_t round = static_cast<uint32_t>(it / STAGES);
+          if (!mbar_wait(&full[s], round & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da = smem_desc(smA + s * A_BYTES);
+          const uint64_t db = smem_desc(smB + s * B_BYTES);
+          for (int k = 0; k < BK / 16; ++k)
+            umma_bf16(acc, da + (uint64_t)((k * 32) >> 4), db + (uint64_t)((k * 32) >> 4),
+                      (first && k == 0) ? 0u : 1u);
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&acc_full[buf]);
+      }
+      umma_commit(done);
+      if (!mbar_wait(done, 0)) ok = false;
+    }
+    __syncwarp();
+  } else {
+    // epilogue: Kahan sums of the chunk partials, 32 outputs per thread
+    const int q = warp & 3, cq = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    float sum[32], comp[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      sum[t] = 0.f;
+      comp[t] = 0.f;
+    }
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      // after a failed wait the remaining chunks are skipped without waiting
+      const bool got = __all_sync(0xffffffffu, ok && mbar_wait(&acc_full[buf], (c >> 1) & 1));
+      if (!got) ok = false;
+      if (!ok) continue;
+      tc_fence_after();
+      const uint32_t taddr = tmem + lane_base + static_cast<uint32_t>(buf * BN + cq * 32);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        uint32_t r[8];
+        tmem_ld8(taddr + g * 8, r);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float y = __uint_as_float(r[t]) - comp[g * 8 + t];
+          const float s2 = sum[g * 8 + t] + y;
+          comp[g * 8 + t] = (s2 - sum[g * 8 + t]) - y;
+          sum[g * 8 + t] = s2;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+    if (ok) {
+      const int gi = i0 + q * 32 + lane;
+      const int mb = m0 + cq * 32;
+      if (gi < nx) {
+        double* yp = Y + ((size_t)b * nt + mb) * nx + gi;
+        const int tn = nt - mb;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          if (t < tn) {
+            const double v = (double)sum[t] - (double)comp[t];
+            yp[(size_t)t * nx] = accumulate ? yp[(size_t)t * nx] + v : v;
+          }
+        }
+      }
+    }
+  }
+  if (!ok) atomicExch(&g_tc_error, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, COMP_TMEM_COLS);
+  }
+}
+
 __global__ void k_to_bf16_f64(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = __double2bfloat16(src[e]);
@@ -268,28 +446,43 @@ bool apply_tc_supported(int nt, int nx, int n_rhs) {
   return nt >= 1 && nx >= 8 && nx % 8 == 0 && n_rhs >= 1 && n_rhs <= 65535 && (nt + BN - 1) / BN <= 65535;
 }
 
-cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            bool accumulate, cudaStream_t s) {
+namespace {
+cudaError_t make_maps(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, CUtensorMap* mA,
+                      CUtensorMap* mX) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap mA, mX;
   const cuuint64_t dimA[3] = {(cuuint64_t)nx, (cuuint64_t)nx, (cuuint64_t)nt};
   const cuuint64_t strA[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * nx * 2};
   const cuuint64_t dimX[3] = {(cuuint64_t)nx, (cuuint64_t)nt, (cuuint64_t)n_rhs};
   const cuuint64_t strX[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nt * nx * 2};
   const cuuint32_t boxA[3] = {BK, BM, 1}, boxX[3] = {BK, BN, 1}, es[3] = {1, 1, 1};
-  CUresult r = enc(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(A_bf16), dimA, strA, boxA, es,
+  CUresult r = enc(mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(A_bf16), dimA, strA, boxA, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  r = enc(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X_bf16), dimX, strX, boxX, es,
+  r = enc(mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X_bf16), dimX, strX, boxX, es,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
+                            bool accumulate, cudaStream_t s, int chunk) {
+  CUtensorMap mA, mX;
+  cudaError_t e = make_maps(nt, nx, A_bf16, n_rhs, X_bf16, &mA, &mX);
   if (e != cudaSuccess) return e;
   const dim3 grid((nx + BM - 1) / BM, (nt + BN - 1) / BN, n_rhs);
-  k_apply_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
+  if (chunk <= 0) {
+    e = cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    k_apply_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
+  } else {
+    e = cudaFuncSetAttribute(k_apply_tc_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COMP_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    k_apply_tc_comp<<<grid, COMP_THREADS, COMP_SMEM_BYTES, s>>>(mA, mX, nt, nx, chunk, accumulate ? 1 : 0, Y);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -6,9 +6,11 @@
 
 namespace stbem {
 bool apply_tc_supported(int nt, int nx, int n_rhs);
-// y (FP64) = block-Toeplitz product of BF16 lag blocks A with BF16 x, on tcgen05
+// y (FP64) = block-Toeplitz product of BF16 lag blocks A with BF16 x, on tcgen05.
+// chunk <= 0: one FP32 accumulator over the whole chain; chunk > 0: FP32 partials
+// of `chunk` 64-wide K steps each, Kahan-summed (compensated kernel).
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            bool accumulate, cudaStream_t s);
+                            bool accumulate, cudaStream_t s, int chunk = 0);
 // hi/mid/lo BF16 slices of an FP64 array (mid and lo may be NULL)
 cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo, size_t n, cudaStream_t s);
 cudaError_t tc_error_reset(cudaStream_t s);
