@@ -20,7 +20,10 @@ What it computes, all in plain float64 numpy/scipy:
 * ``rhs``        -- the manufactured Dirichlet datum, f = (1/2 M_h + K_h) g and
                     the exact Neumann datum w = d_n u;
 * ``solve``      -- block-Toeplitz products, exact block forward substitution in
-                    time and a right-preconditioned GMRES.
+                    time and a right-preconditioned GMRES;
+* ``gradient``   -- shape (vertex) and alpha derivatives of V_h, K_h, M_h and
+                    g, the adjoint (backward-in-time) solve and the gradient of
+                    ||w_h - w_target||^2.
 
 Parity status of each function (what pins it) is listed in the module
 docstrings; functions without an independent pin say "parity unpinned".

@@ -162,3 +162,69 @@ def lag_1(c, d, ht, alpha, rules):
         return out
     return _split(c, d, ht, lambda cc: _closed(F, cc, d, ht),
                   lambda cc: _peano(G, cc, d, ht, rules))
+
+
+# --- derivatives in c (shape and alpha gradients) ----------------------------------
+#
+# Each entry depends on the geometry and on alpha only through c = alpha r^2 / 4
+# (and, for K, the explicit factor alpha and q), so the gradients need
+# d/dc of every branch above.  With E1' = -e^{-z}/z and E2' = -E1:
+#   d/dc F_V(c, s)  = (1/(4 pi)) (E1 - E2)'(c/s) = -E2(z) / (4 pi z)
+#   d/dc F_Kq(c, s) = -alpha / (8 pi c) (E2(z)/z + E1(z))
+#   d/dc G(c, s)    = -G(c, s) / s            (G = e^{-c/s} x factors of s)
+# The lag-1 forms, written with z = c/ht (d/dc = (1/ht) d/dz):
+#   V: the derivative of the series form,
+#      (1/(4 pi)) [gamma + ln(2 z) + Ein(z/2) - 2 Ein(z) + (2/z) e^{-z/2} expm1(-z/2)],
+#      in which the log terms of E1(z/2) - 2 E1(z) are again combined analytically;
+#   K: D2_1 F_Kq = alpha (E2(z/2) - E2(z)) / (4 pi z) =: alpha B(z) / (4 pi), and
+#      B'(z) = (E1(z) - E1(z/2)/2) / z - B(z) / z = -(e^{-z/2} - e^{-z}) / z^2,
+#      valid for every z (e^{-z/2} - e^{-z} = -e^{-z/2} expm1(-z/2), no cancellation).
+
+def dF_V(c, s):
+    z = c / s
+    return -e2(z) / (FOUR_PI * z)
+
+
+def dF_Kq(c, s, alpha):
+    z = c / s
+    return -alpha / (2.0 * FOUR_PI * c) * (e2(z) / z + e1(z))
+
+
+def dG_V(c, s):
+    return -G_V(c, s) / s
+
+
+def dG_Kq(c, s, alpha):
+    return -G_Kq(c, s, alpha) / s
+
+
+def dlag_V(c, d, ht, alpha, rules):
+    """d/dc of lag_V (same branches)."""
+    c = np.asarray(c, dtype=np.float64)
+    if d == 0:
+        return dF_V(c, ht)
+    if d == 1:
+        z = c / ht
+        out = np.empty_like(c)
+        sm = z < 1.0
+        zs = z[sm]
+        out[sm] = (EULER_GAMMA + np.log(2.0 * zs) + ein(0.5 * zs) - 2.0 * ein(zs)
+                   + 2.0 / zs * np.exp(-0.5 * zs) * np.expm1(-0.5 * zs)) / FOUR_PI
+        out[~sm] = _closed(dF_V, c[~sm], 1, ht)
+        return out
+    return _split(c, d, ht, lambda cc: _closed(dF_V, cc, d, ht),
+                  lambda cc: _peano(dG_V, cc, d, ht, rules))
+
+
+def dlag_Kq(c, d, ht, alpha, rules):
+    """d/dc of lag_Kq (same branches; lag 1 in the closed form above)."""
+    c = np.asarray(c, dtype=np.float64)
+    F = lambda cc, s: dF_Kq(cc, s, alpha)      # noqa: E731
+    G = lambda cc, s: dG_Kq(cc, s, alpha)      # noqa: E731
+    if d == 0:
+        return F(c, ht)
+    if d == 1:
+        z = c / ht
+        return alpha / (FOUR_PI * ht) * np.exp(-0.5 * z) * np.expm1(-0.5 * z) / (z * z)
+    return _split(c, d, ht, lambda cc: _closed(F, cc, d, ht),
+                  lambda cc: _peano(G, cc, d, ht, rules))
