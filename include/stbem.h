@@ -216,6 +216,37 @@ int stbem_solve(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void* dev_V,
                 double* dev_w, const stbem_solve_opts* opts, stbem_solve_info* info,
                 void* dev_work, size_t work_bytes);
 
+/* Adjoint solve V_h^T lambda = b with the same GMRES and options (the
+ * preconditioner becomes L^-1 D_h^T L^-1).  V_h^T is block upper triangular:
+ * its product runs backward in time (lambda_n gathers b from steps n + d).
+ * Arguments, workspace (stbem_solve_workspace_bytes) and errors as
+ * stbem_solve. */
+int stbem_solve_adjoint(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void* dev_V,
+                        const void* dev_D, const double* dev_L, const double* dev_b,
+                        double* dev_lambda, const stbem_solve_opts* opts, stbem_solve_info* info,
+                        void* dev_work, size_t work_bytes);
+
+/* Shape and alpha gradient by the adjoint method (not in the paper, which
+ * does not differentiate; it differentiates the discrete system of eq. (4)).
+ * For w solving V_h w = f, f = 1/2 M_h g + K_h g with g the time averages of
+ * U*(x - y*, t) at the vertices (stbem_rhs), and lambda solving
+ * V_h^T lambda = dL/dw (stbem_solve_adjoint), writes
+ *   dev_dxy[2 k + c] = lambda^T (df/dx_k,c - (dV_h/dx_k,c) w)   (n_x x 2 doubles)
+ *   dev_dalpha[0]    = lambda^T (df/dalpha - (dV_h/dalpha) w),
+ * the derivatives of L with respect to the polygon vertices and alpha.  The
+ * derivatives of V_h and K_h are recomputed tile by tile from the quadrature
+ * of the assembly (same rule, derivative of the integrand) and contracted with
+ * C(d) = sum_m lambda_m x_{m-d}^T (x = w for V_h, g for K_h); nothing of size
+ * n_t n_x^2 n_params is stored.  dev_K: the assembled K (FP64); dev_g, dev_w,
+ * dev_lambda: n_t x n_x doubles.  FP64 throughout.  Workspace:
+ * stbem_grad_workspace_bytes() (two n_t n_x^2 correlation arrays and per-pair
+ * partial sums), 256-byte aligned.  Asynchronous on the context's stream.
+ * Errors: STBEM_ERR_ARG, STBEM_ERR_NOMEM, STBEM_ERR_CUDA. */
+int stbem_grad_workspace_bytes(int n_t, int n_x, size_t* bytes);
+int stbem_grad(stbem_ctx* ctx, const stbem_mesh* mesh, const double* dev_K, double y_star_x,
+               double y_star_y, const double* dev_g, const double* dev_w, const double* dev_lambda,
+               double* dev_dxy, double* dev_dalpha, void* dev_work, size_t work_bytes);
+
 /* Mixed-precision solve of V_h w = f (eq. (4)): FP64 iterative refinement,
  * r = f - V_h w with the FP64 operator dev_V64, around right-preconditioned
  * GMRES (Section 2 preconditioner) on the FP32 operators dev_V32 and dev_D32

@@ -165,6 +165,43 @@ def solve(ctx: Context, V, f, D=None, L=None, tol: float = 1e-8, max_iter: int =
     return out, res
 
 
+def solve_adjoint(ctx: Context, V, b, D=None, L=None, tol: float = 1e-8, max_iter: int = 500,
+                  restart: int = 200, work=None, out=None, raise_on_fail: bool = True):
+    """GMRES for the adjoint V_h^T lam = b (backward in time); returns (lam, info)."""
+    n_t, n_x = V.shape[0], V.shape[1]
+    prec = capi.F64 if V.dtype == torch.float64 else capi.F32
+    opts = capi.SolveOpts(tol, max_iter, restart, int(D is not None))
+    info = capi.SolveInfo()
+    if out is None:
+        out = ctx.empty((n_t, n_x))
+    if work is None:
+        work = solve_workspace(ctx, n_t, n_x, restart)
+    code = ctx.lib.stbem_solve_adjoint(ctx.h, n_t, n_x, prec, _ptr(V), _ptr(D), _ptr(L), _ptr(b), _ptr(out),
+                                       ctypes.byref(opts), ctypes.byref(info), _ptr(work), work.numel())
+    res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
+    if code != capi.STBEM_OK and raise_on_fail:
+        ctx.check(code)
+    return out, res
+
+
+def grad_workspace(ctx: Context, n_t: int, n_x: int):
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_grad_workspace_bytes(n_t, n_x, ctypes.byref(nb)))
+    return torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+
+
+def grad(ctx: Context, mesh: Mesh, K, y_star, g, w, lam, work=None):
+    """lam^T (df/dtheta - dV_h/dtheta w) for the vertices (n_x, 2) and alpha
+    (0-dim tensor), f = 1/2 M_h g + K_h g with g the datum of source y_star."""
+    dxy = ctx.empty((mesh.n_x, 2))
+    dal = ctx.empty((1,))
+    if work is None:
+        work = grad_workspace(ctx, mesh.n_t, mesh.n_x)
+    ctx.check(ctx.lib.stbem_grad(ctx.h, mesh.h, _ptr(K), float(y_star[0]), float(y_star[1]), _ptr(g), _ptr(w),
+                                 _ptr(lam), _ptr(dxy), _ptr(dal), _ptr(work), work.numel()))
+    return dxy, dal[0]
+
+
 def round_f32(ctx: Context, A):
     """FP32 copy of an FP64 operator (rounded by a library kernel)."""
     out = torch.empty(A.shape, dtype=torch.float32, device=A.device)

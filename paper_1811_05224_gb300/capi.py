@@ -32,7 +32,7 @@ EXPORTS = [
     "stbem_solve_mixed_workspace_bytes", "stbem_solve_mixed", "stbem_round_f32",
     "stbem_to_bf16", "stbem_apply_tc", "stbem_apply_tc_comp", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
     "stbem_apply_tc3", "stbem_rhs_g_batched", "stbem_half_mass_add", "stbem_solve_batched_workspace_bytes",
-    "stbem_solve_batched",
+    "stbem_solve_batched", "stbem_solve_adjoint", "stbem_grad_workspace_bytes", "stbem_grad",
 ]
 
 
@@ -86,6 +86,9 @@ def load(path: str = LIB_PATH):
     L.stbem_lumped_mass.argtypes = [vp, vp, vp]
     L.stbem_solve_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
+    L.stbem_solve_adjoint.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
+    L.stbem_grad_workspace_bytes.argtypes = [i, i, P(sz)]
+    L.stbem_grad.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp, sz]
     L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]

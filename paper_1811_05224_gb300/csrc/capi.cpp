@@ -12,6 +12,7 @@
 #include "assemble.h"
 #include "stbem.h"
 #include "toeplitz.h"
+#include "grad.h"
 #include "toeplitz_tc.h"
 #include "vec.h"
 
@@ -80,6 +81,7 @@ int stbem_create(stbem_ctx** out, int device, void* stream) {
   stbem::RuleTables t;
   stbem::build_rule_tables(&t);
   e = stbem::upload_rule_tables(t, ctx->stream);
+  if (e == cudaSuccess) e = stbem::upload_grad_rule_tables(t, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     delete ctx;
@@ -666,6 +668,7 @@ struct GmresOp {
   const void* V;
   const void* D;          // NULL: no preconditioner
   const double* L;
+  bool transpose = false; // solve V^T x = f with the preconditioner L^-1 D^T L^-1
 };
 
 // Right-preconditioned restarted GMRES for V x = f from x = 0 (see stbem_solve).
@@ -679,14 +682,14 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
   *iters_out = 0;
   *relres_out = 0.0;
   auto applyV = [&](const double* x, double* y) {
-    return stbem::apply_launch(op.prec, false, nt, nx, op.V, 1, x, y, W.apply, s);
+    return stbem::apply_launch(op.prec, op.transpose, nt, nx, op.V, 1, x, y, W.apply, s);
   };
   // right preconditioner: y = L^{-1} D L^{-1} x (or y = x)
   auto applyP = [&](const double* x, double* y) -> cudaError_t {
     if (!prec) return cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
     cudaError_t e = stbem::diag_div_launch(x, op.L, W.u, nt, nx, s);
     if (e != cudaSuccess) return e;
-    e = stbem::apply_launch(op.prec, false, nt, nx, op.D, 1, W.u, y, W.apply, s);
+    e = stbem::apply_launch(op.prec, op.transpose, nt, nx, op.D, 1, W.u, y, W.apply, s);
     if (e != cudaSuccess) return e;
     return stbem::diag_div_launch(y, op.L, y, nt, nx, s);
   };
@@ -791,9 +794,10 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
 
 extern "C" {
 
-int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const void* D, const double* L,
-                const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
-                void* work, size_t work_bytes) {
+namespace {
+int solve_impl(stbem_ctx* ctx, bool transpose, int nt, int nx, int vprec, const void* V, const void* D,
+               const double* L, const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
+               void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!V || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve: NULL pointer");
   if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve: bad sizes");
@@ -806,7 +810,8 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
   if (!carve(work, work_bytes, nt, nx, restart, &W))
     return fail(ctx, STBEM_ERR_NOMEM, "solve: workspace %zu < %zu bytes", work_bytes, solve_bytes(nt, nx, restart));
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve: set device");
-  const GmresOp op{nt, nx, vprec, V, prec ? D : nullptr, L};
+  GmresOp op{nt, nx, vprec, V, prec ? D : nullptr, L};
+  op.transpose = transpose;
   int iters = 0;
   double relres = 0.0;
   const int status = gmres_core(ctx, op, f, w, opts->tol, maxit, restart, W, &iters, &relres);
@@ -817,6 +822,38 @@ int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const 
     return fail(ctx, status, "solve: %s after %d iterations (relres %.3e)",
                 status == STBEM_ERR_NAN ? "NaN" : "no convergence", iters, relres);
   return status;   // STBEM_OK, or a CUDA error already described
+}
+}  // namespace
+
+int stbem_solve(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const void* D, const double* L,
+                const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                void* work, size_t work_bytes) {
+  return solve_impl(ctx, false, nt, nx, vprec, V, D, L, f, w, opts, info, work, work_bytes);
+}
+
+int stbem_solve_adjoint(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V, const void* D, const double* L,
+                        const double* b, double* lam, const stbem_solve_opts* opts, stbem_solve_info* info,
+                        void* work, size_t work_bytes) {
+  return solve_impl(ctx, true, nt, nx, vprec, V, D, L, b, lam, opts, info, work, work_bytes);
+}
+
+int stbem_grad_workspace_bytes(int n_t, int n_x, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 3) return STBEM_ERR_ARG;
+  *bytes = stbem::grad_workspace_bytes(n_t, n_x);
+  return STBEM_OK;
+}
+
+int stbem_grad(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, const double* g,
+               const double* w, const double* lam, double* dxy, double* dalpha, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !K || !g || !w || !lam || !dxy || !dalpha || !work) return fail(ctx, STBEM_ERR_ARG, "grad: NULL pointer");
+  if (!std::isfinite(ysx) || !std::isfinite(ysy)) return fail(ctx, STBEM_ERR_ARG, "grad: non-finite source point");
+  const size_t need = stbem::grad_workspace_bytes(m->n_t, m->N);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "grad: workspace %zu < %zu bytes", work_bytes, need);
+  if (reinterpret_cast<uintptr_t>(work) & 255) return fail(ctx, STBEM_ERR_ARG, "grad: workspace must be 256-byte aligned");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "grad: set device");
+  CUDA_TRY(ctx, stbem::grad_launch(m->dev, K, ysx, ysy, g, w, lam, dxy, dalpha, work, ctx->stream), "grad");
+  return STBEM_OK;
 }
 
 int stbem_solve_mixed_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes) {

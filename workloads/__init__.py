@@ -28,6 +28,8 @@ __all__ = [
     "Problem",
     "unit_square",
     "l_shape",
+    "star_corners",
+    "subdivision_matrix",
     "star",
     "annulus_sources",
     "ragged_squares",
@@ -125,6 +127,30 @@ def star(n_vertices: int = 16, seg_per_edge: int = 16, seed: int = 5,
     c = np.asarray(center, dtype=np.float64)
     corners = c + radii[:, None] * np.stack([np.cos(ang), np.sin(ang)], axis=1)
     return _subdivide(corners, [seg_per_edge] * n_vertices)
+
+
+def star_corners(n_vertices: int = 16, seed: int = 5, radii_range=(0.6, 1.0), center=(0.5, 0.5),
+                 radii=None) -> np.ndarray:
+    """The ``n_vertices`` corners of ``star`` (same seeded radii)."""
+    if radii is None:
+        rng = np.random.default_rng(seed)
+        radii = rng.uniform(radii_range[0], radii_range[1], size=n_vertices)
+    radii = np.asarray(radii, dtype=np.float64)
+    ang = 2.0 * np.pi * np.arange(n_vertices) / n_vertices
+    c = np.asarray(center, dtype=np.float64)
+    return c + radii[:, None] * np.stack([np.cos(ang), np.sin(ang)], axis=1)
+
+
+def subdivision_matrix(n_corners: int, seg_per_edge: int) -> np.ndarray:
+    """S (n_corners seg_per_edge x n_corners) with vertices = S @ corners for
+    the equal subdivision of every edge (as ``star``)."""
+    S = np.zeros((n_corners * seg_per_edge, n_corners))
+    for s in range(n_corners):
+        for k in range(seg_per_edge):
+            f = k / seg_per_edge
+            S[s * seg_per_edge + k, s] += 1.0 - f
+            S[s * seg_per_edge + k, (s + 1) % n_corners] += f
+    return S
 
 
 def annulus_sources(n: int, seed: int = 4, r_in: float = 1.2, r_out: float = 3.0,
