@@ -240,6 +240,70 @@ def run_batched(ctx, dev, stream, n_src=256):
     return out
 
 
+def run_grad(ctx, dev, stream):
+    """The differentiation workload: 16-corner star (seeded radii), N_x = 256,
+    N_t = 256, alpha = 1, y* = (1.5, 1.5); loss ||w_h - w_target||^2 with
+    w_target from seeded perturbed corners.  Times the forward solve, the
+    adjoint solve and the assembly-derivative kernels (CUDA events), and checks
+    the gradient in one random direction of (corners, alpha) against an FP64
+    central difference (h = 1e-6)."""
+    import torch
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    C0 = W.star_corners(16, seed=5)
+    S = W.subdivision_matrix(16, 16)
+    T, nt, ys, al = 1.0, 256, (1.5, 1.5), 1.0
+    rng = np.random.default_rng(23)
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+
+    def forward(C, a):
+        mesh = P.Mesh(ctx, S @ C, T, nt, a)
+        V = P.assemble(ctx, mesh, "V")
+        K = P.assemble(ctx, mesh, "K")
+        D = P.assemble(ctx, mesh, "D")
+        L = P.lumped_mass(ctx, mesh)
+        g, f = P.rhs(ctx, mesh, K, ys)
+        w, info = P.solve(ctx, V, f, D, L, tol=1e-12, restart=100, max_iter=2000)
+        return mesh, V, K, D, L, g, w, info
+
+    wt = forward(C0 + 0.01 * rng.standard_normal(C0.shape), al)[6]
+    e = [ev() for _ in range(4)]
+    e[0].record(stream)
+    mesh, V, K, D, L, g, w, info = forward(C0, al)
+    e[1].record(stream)
+    lam, ainfo = P.solve_adjoint(ctx, V, 2.0 * (w - wt), D, L, tol=1e-12, restart=100, max_iter=2000)
+    e[2].record(stream)
+    gwork = P.api.grad_workspace(ctx, nt, mesh.n_x)
+    dxy, dal = P.grad(ctx, mesh, K, ys, g, w, lam, work=gwork)
+    e[3].record(stream)
+    torch.cuda.synchronize(dev)
+    # the derivative kernels alone, once more
+    k0, k1 = ev(), ev()
+    k0.record(stream)
+    P.grad(ctx, mesh, K, ys, g, w, lam, work=gwork)
+    k1.record(stream)
+    torch.cuda.synchronize(dev)
+    gC = S.T @ dxy.cpu().numpy()
+    ga = float(dal)
+    v, va, h = rng.standard_normal(C0.shape), float(rng.standard_normal()), 1e-6
+    Lp = float(((forward(C0 + h * v, al + h * va)[6] - wt) ** 2).sum())
+    Lm = float(((forward(C0 - h * v, al - h * va)[6] - wt) ** 2).sum())
+    fd = (Lp - Lm) / (2 * h)
+    an = float((gC * v).sum() + ga * va)
+    out = {
+        "workload": "star256: 16 corners (radii seed 5), N_x = 256, N_t = 256, alpha = 1, 33 parameters",
+        "forward_ms": e[0].elapsed_time(e[1]), "forward_gmres_iterations": info["iterations"],
+        "adjoint_solve_ms": e[1].elapsed_time(e[2]), "adjoint_iterations": ainfo["iterations"],
+        "grad_kernels_ms": k0.elapsed_time(k1),
+        "backward_ms": e[1].elapsed_time(e[3]),
+        "fd_check": {"directional_derivative": an, "central_difference": fd,
+                     "rel_diff": abs(fd - an) / abs(an), "h": h},
+    }
+    del V, K, D, g, w, lam, gwork
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -395,6 +459,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(ctx, dev, stream)
+    grad = None
+    if not args.no_grad and world == 1:
+        grad = run_grad(ctx, dev, stream)
 
     # end to end through the public API with host buffers: vertices in, w out
     verts = np.ascontiguousarray(p.vertices)
@@ -444,6 +511,7 @@ def run_ours(args):
                       "w_rel_diff_vs_fp64": mixed_rel, "assembly_D_f32_ms": d32_ms,
                       "note": "FP64 V,K; FP32 D (FP64 singular pairs); FP64 refinement around FP32 GMRES"},
             "batched": batched,
+            "grad": grad,
         },
         "roofline": {"kernel": "k_tile<D, f64> lags >= 2", "bound": "alu",
                      "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -506,6 +574,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-right-hand-side square512 component")
+    ap.add_argument("--no-grad", action="store_true", help="skip the star256 differentiation component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
     args = ap.parse_args()
