@@ -314,6 +314,73 @@ int stbem_solve_batched(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void*
                         double* dev_W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
                         void* dev_work, size_t work_bytes);
 
+/* ---- Ragged batches ----------------------------------------------------------
+ * Many independent problems of different sizes (not in the paper, which solves
+ * one problem at a time): every problem has its own polygon, N_x, N_t, T and
+ * alpha.  The batch handle owns the problems' meshes and the work lists of the
+ * persistent launches.  Batch arrays are the problems' arrays concatenated in
+ * problem order (stbem_ragged_offsets gives the start of each):
+ *   operators  sum_p n_t N_x^2 elements (A_p[d][i][j] as for one problem),
+ *   vectors    sum_p n_t N_x doubles   (x_p[n][j]),
+ *   masses     sum_p N_x doubles.
+ * All device arrays are caller-owned. */
+typedef struct stbem_ragged stbem_ragged;
+typedef struct stbem_problem {
+  const double* xy;   /* host: 2 n_x vertex coordinates, counter-clockwise */
+  int n_x, n_t;
+  double T, alpha;
+} stbem_problem;
+
+/* Builds every problem's mesh (errors as stbem_mesh_create). */
+int stbem_ragged_create(stbem_ctx* ctx, int n_problems, const stbem_problem* problems, stbem_ragged** out);
+void stbem_ragged_destroy(stbem_ragged* batch);
+int stbem_ragged_sizes(const stbem_ragged* batch, long long* op_elems, long long* vec_elems, long long* mass_elems);
+/* start offsets (elements) of each problem: host arrays of n_problems (any may be NULL) */
+int stbem_ragged_offsets(const stbem_ragged* batch, long long* op_off, long long* vec_off, long long* mass_off);
+
+/* Lag blocks of op (STBEM_OP_V, K or D, Section 1 eq. (4) / Section 2) for
+ * every problem, precision prec (F64 or F32 as stbem_assemble): one persistent
+ * launch over the lag-0/1 identical and vertex-sharing pairs of all problems,
+ * then one over all (problem, lag, tile) items, largest problems first.
+ * Asynchronous. */
+int stbem_ragged_assemble(stbem_ctx* ctx, stbem_ragged* batch, int op, int prec, void* dev_out);
+/* lumped dual mass (Section 4) of every problem into the masses array */
+int stbem_ragged_lumped_mass(stbem_ctx* ctx, stbem_ragged* batch, double* dev_L);
+
+/* y_p = A_p x_p for every problem (Section 3 block-Toeplitz product): one
+ * persistent launch over all (problem, lag chunk, time tile, row tile) units
+ * and one reduction.  Workspace: stbem_ragged_apply_workspace_bytes (enough
+ * for every lag-chunk length the tuner tries).  Asynchronous. */
+int stbem_ragged_apply_workspace_bytes(const stbem_ragged* batch, size_t* bytes);
+int stbem_ragged_apply(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void* dev_A, const double* dev_x,
+                       double* dev_y, void* dev_work, size_t work_bytes);
+/* Autotuner: times the product with A for each candidate lag-chunk length
+ * (32 .. 512 lags per partial; dev_x, dev_y: batch vectors used as input and
+ * output) with CUDA events and keeps the fastest for every later product and
+ * solve of this batch.  Blocks the host.  stbem_ragged_tune_report returns the
+ * candidates tried and their times (ms). */
+int stbem_ragged_tune(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void* dev_A, const double* dev_x,
+                      double* dev_y, void* dev_work, size_t work_bytes, int* lags_per_chunk);
+int stbem_ragged_tune_report(const stbem_ragged* batch, int max_n, int* candidates, float* ms, int* n_out);
+
+/* Right-hand sides of eq. (4) for every problem, g = U*(x - y_p*, t) with the
+ * source host_ystar[2p], [2p+1]: dev_g (vertex time averages) and
+ * dev_f = 1/2 M_h g + K_h g (dev_K of precision kprec).  Workspace: 256 bytes
+ * plus stbem_ragged_apply_workspace_bytes.  Blocks the host. */
+int stbem_ragged_rhs(stbem_ctx* ctx, stbem_ragged* batch, int kprec, const void* dev_K, const double* host_ystar,
+                     double* dev_g, double* dev_f, void* dev_work, size_t work_bytes);
+
+/* V_p w_p = f_p for every problem: right-preconditioned GMRES (Section 2
+ * preconditioner) in lockstep, per-problem Hessenberg and convergence, the
+ * device part of each Arnoldi step captured once as a CUDA graph and
+ * replayed.  Operators of precision prec (F64 or F32), FP64 vectors; each
+ * problem stops at its true relative residual <= opts->tol.  infos: one per
+ * problem.  Blocks the host.  Errors as stbem_solve. */
+int stbem_ragged_solve_workspace_bytes(const stbem_ragged* batch, int restart, size_t* bytes);
+int stbem_ragged_solve(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void* dev_V, const void* dev_D,
+                       const double* dev_L, const double* dev_f, double* dev_w, const stbem_solve_opts* opts,
+                       stbem_solve_info* infos, void* dev_work, size_t work_bytes);
+
 #ifdef __cplusplus
 }
 #endif

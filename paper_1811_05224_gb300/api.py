@@ -311,3 +311,133 @@ def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1
     if code != capi.STBEM_OK and raise_on_fail:
         ctx.check(code)
     return out, res
+
+
+class Ragged:
+    """A ragged batch: independent problems of different sizes handled by one
+    persistent launch per step (stbem_ragged_*).  ``problems`` is a list of
+    (vertices (n_x, 2), T, n_t, alpha).  Batch arrays are the problems' arrays
+    concatenated; ``view_op`` / ``view_vec`` return one problem's part."""
+
+    def __init__(self, ctx: Context, problems):
+        self.ctx = ctx
+        self._xy = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1)) for v, _, _, _ in problems]
+        arr = (capi.Problem * len(problems))()
+        for k, (v, T, n_t, alpha) in enumerate(problems):
+            arr[k].xy = self._xy[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[k].n_x = self._xy[k].size // 2
+            arr[k].n_t = int(n_t)
+            arr[k].T = float(T)
+            arr[k].alpha = float(alpha)
+        self.P = len(problems)
+        self.n_x = [self._xy[k].size // 2 for k in range(self.P)]
+        self.n_t = [int(p[2]) for p in problems]
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.stbem_ragged_create(ctx.h, self.P, arr, ctypes.byref(h)))
+        self.h = h
+        ll = ctypes.c_longlong
+        a, b, c = ll(), ll(), ll()
+        ctx.check(ctx.lib.stbem_ragged_sizes(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        self.op_elems, self.vec_elems, self.mass_elems = a.value, b.value, c.value
+        oo, vo, mo = (ll * self.P)(), (ll * self.P)(), (ll * self.P)()
+        ctx.check(ctx.lib.stbem_ragged_offsets(self.h, oo, vo, mo))
+        self.op_off, self.vec_off, self.mass_off = list(oo), list(vo), list(mo)
+        self._awork = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.stbem_ragged_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # views of one problem's part of a batch array
+    def view_op(self, A, p):
+        n, t = self.n_x[p], self.n_t[p]
+        return A[self.op_off[p]:self.op_off[p] + t * n * n].view(t, n, n)
+
+    def view_vec(self, x, p):
+        n, t = self.n_x[p], self.n_t[p]
+        return x[self.vec_off[p]:self.vec_off[p] + t * n].view(t, n)
+
+    def view_mass(self, L, p):
+        return L[self.mass_off[p]:self.mass_off[p] + self.n_x[p]]
+
+    def apply_workspace(self):
+        if self._awork is None:
+            nb = ctypes.c_size_t()
+            self.ctx.check(self.ctx.lib.stbem_ragged_apply_workspace_bytes(self.h, ctypes.byref(nb)))
+            self._awork = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self.ctx.device)
+        return self._awork
+
+    def assemble(self, op: str, prec: str = "f64", out=None):
+        p = PRECS[prec]
+        if out is None:
+            out = torch.empty(self.op_elems, dtype=torch.float64 if p == capi.F64 else torch.float32,
+                              device=self.ctx.device)
+        self.ctx.check(self.ctx.lib.stbem_ragged_assemble(self.ctx.h, self.h, OPS[op], p, _ptr(out)))
+        return out
+
+    def lumped_mass(self):
+        L = self.ctx.empty((self.mass_elems,))
+        self.ctx.check(self.ctx.lib.stbem_ragged_lumped_mass(self.ctx.h, self.h, _ptr(L)))
+        return L
+
+    def apply(self, A, x, out=None):
+        p = capi.F64 if A.dtype == torch.float64 else capi.F32
+        if out is None:
+            out = self.ctx.empty((self.vec_elems,))
+        w = self.apply_workspace()
+        self.ctx.check(self.ctx.lib.stbem_ragged_apply(self.ctx.h, self.h, p, _ptr(A), _ptr(x), _ptr(out), _ptr(w),
+                                                        w.numel()))
+        return out
+
+    def tune(self, A, x, y):
+        """Autotune the product's lag-chunk length on A; returns (chosen,
+        {candidate: ms})."""
+        p = capi.F64 if A.dtype == torch.float64 else capi.F32
+        w = self.apply_workspace()
+        best = ctypes.c_int()
+        self.ctx.check(self.ctx.lib.stbem_ragged_tune(self.ctx.h, self.h, p, _ptr(A), _ptr(x), _ptr(y), _ptr(w),
+                                                       w.numel(), ctypes.byref(best)))
+        cand, ms, n = (ctypes.c_int * 16)(), (ctypes.c_float * 16)(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.stbem_ragged_tune_report(self.h, 16, cand, ms, ctypes.byref(n)))
+        return best.value, {cand[k]: ms[k] for k in range(n.value)}
+
+    def rhs(self, K, y_stars):
+        p = capi.F64 if K.dtype == torch.float64 else capi.F32
+        ys = np.ascontiguousarray(np.asarray(y_stars, dtype=np.float64).reshape(-1))
+        g = self.ctx.empty((self.vec_elems,))
+        f = self.ctx.empty((self.vec_elems,))
+        aw = self.apply_workspace()
+        work = torch.empty(aw.numel() + 256 + ((16 * self.P + 255) // 256) * 256, dtype=torch.uint8,
+                           device=self.ctx.device)
+        self.ctx.check(self.ctx.lib.stbem_ragged_rhs(self.ctx.h, self.h, p, _ptr(K),
+                                                      ys.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(g),
+                                                      _ptr(f), _ptr(work), work.numel()))
+        return g, f
+
+    def solve_workspace(self, restart: int):
+        nb = ctypes.c_size_t()
+        self.ctx.check(self.ctx.lib.stbem_ragged_solve_workspace_bytes(self.h, restart, ctypes.byref(nb)))
+        return torch.empty(nb.value, dtype=torch.uint8, device=self.ctx.device)
+
+    def solve(self, V, f, D=None, L=None, tol: float = 1e-8, max_iter: int = 500, restart: int = 60, work=None,
+              out=None, raise_on_fail: bool = True):
+        p = capi.F64 if V.dtype == torch.float64 else capi.F32
+        opts = capi.SolveOpts(tol, max_iter, restart, int(D is not None))
+        infos = (capi.SolveInfo * self.P)()
+        if out is None:
+            out = self.ctx.empty((self.vec_elems,))
+        if work is None:
+            work = self.solve_workspace(restart)
+        code = self.ctx.lib.stbem_ragged_solve(self.ctx.h, self.h, p, _ptr(V), _ptr(D), _ptr(L), _ptr(f), _ptr(out),
+                                               ctypes.byref(opts), infos, _ptr(work), work.numel())
+        res = [{"iterations": x.iterations, "status": x.status, "rel_residual": x.rel_residual} for x in infos]
+        if code != capi.STBEM_OK and raise_on_fail:
+            self.ctx.check(code)
+        return out, res

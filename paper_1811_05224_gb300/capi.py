@@ -33,7 +33,16 @@ EXPORTS = [
     "stbem_to_bf16", "stbem_apply_tc", "stbem_apply_tc_comp", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
     "stbem_apply_tc3", "stbem_rhs_g_batched", "stbem_half_mass_add", "stbem_solve_batched_workspace_bytes",
     "stbem_solve_batched", "stbem_solve_adjoint", "stbem_grad_workspace_bytes", "stbem_grad",
+    "stbem_ragged_create", "stbem_ragged_destroy", "stbem_ragged_sizes", "stbem_ragged_offsets",
+    "stbem_ragged_assemble", "stbem_ragged_lumped_mass", "stbem_ragged_apply_workspace_bytes", "stbem_ragged_apply",
+    "stbem_ragged_tune", "stbem_ragged_tune_report", "stbem_ragged_rhs", "stbem_ragged_solve_workspace_bytes",
+    "stbem_ragged_solve",
 ]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("xy", ctypes.POINTER(ctypes.c_double)), ("n_x", ctypes.c_int), ("n_t", ctypes.c_int),
+                ("T", ctypes.c_double), ("alpha", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -89,6 +98,21 @@ def load(path: str = LIB_PATH):
     L.stbem_solve_adjoint.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
     L.stbem_grad_workspace_bytes.argtypes = [i, i, P(sz)]
     L.stbem_grad.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp, sz]
+    ll = ctypes.c_longlong
+    L.stbem_ragged_create.argtypes = [vp, i, P(Problem), P(vp)]
+    L.stbem_ragged_destroy.argtypes = [vp]
+    L.stbem_ragged_destroy.restype = None
+    L.stbem_ragged_sizes.argtypes = [vp, P(ll), P(ll), P(ll)]
+    L.stbem_ragged_offsets.argtypes = [vp, P(ll), P(ll), P(ll)]
+    L.stbem_ragged_assemble.argtypes = [vp, vp, i, i, vp]
+    L.stbem_ragged_lumped_mass.argtypes = [vp, vp, vp]
+    L.stbem_ragged_apply_workspace_bytes.argtypes = [vp, P(sz)]
+    L.stbem_ragged_apply.argtypes = [vp, vp, i, vp, vp, vp, vp, sz]
+    L.stbem_ragged_tune.argtypes = [vp, vp, i, vp, vp, vp, vp, sz, P(i)]
+    L.stbem_ragged_tune_report.argtypes = [vp, i, P(i), P(ctypes.c_float), P(i)]
+    L.stbem_ragged_rhs.argtypes = [vp, vp, i, vp, P(d), vp, vp, vp, sz]
+    L.stbem_ragged_solve_workspace_bytes.argtypes = [vp, i, P(sz)]
+    L.stbem_ragged_solve.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
     L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]

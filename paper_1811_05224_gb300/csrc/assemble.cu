@@ -231,12 +231,11 @@ __device__ void tensor_moments_impl(const Piece& A, const Piece& B, int d, int n
 constexpr int kSingThreads = 128;
 
 template <int OP>
-__global__ void __launch_bounds__(kSingThreads) k_singular(DevMesh M, double* __restrict__ buf) {
-  __shared__ double red[5][kSingThreads];
+__device__ void singular_body(const DevMesh& M, int slot, int d, double* __restrict__ buf,
+                              double (*red)[kSingThreads]) {
   constexpr int NM = NMom<OP>::n;
   const int N = M.N;
   const int Rl = OP == STBEM_OP_D ? 2 * N : N;
-  const int slot = blockIdx.x, d = blockIdx.y;
   const int kind = slot / Rl, i = slot % Rl;
   const int cls = kind == 0 ? kIdentical : (kind == 1 ? kAdjNext : kAdjPrev);
   const int j = kind == 0 ? i : (kind == 1 ? (i + 1) % Rl : (i - 1 + Rl) % Rl);
@@ -280,6 +279,12 @@ __global__ void __launch_bounds__(kSingThreads) k_singular(DevMesh M, double* __
     const double L = A.len * B.len;
     buf[((size_t)d * 3 * Rl + slot) * 5 + threadIdx.x] = (int)threadIdx.x < NM ? red[threadIdx.x][0] * L : 0.0;
   }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kSingThreads) k_singular(DevMesh M, double* __restrict__ buf) {
+  __shared__ double red[5][kSingThreads];
+  singular_body<OP>(M, blockIdx.x, blockIdx.y, buf, red);
 }
 
 // V, lags >= 2: one thread per upper-triangle entry, one lag per block row.
@@ -377,24 +382,31 @@ __device__ __forceinline__ int singular_slot(int cls, int ia, int Rl) {
   return cls == kIdentical ? ia : (cls == kAdjNext ? Rl + ia : 2 * Rl + ia);
 }
 
+// Number of tiles of one lag block of op on N segments.
+template <int OP>
+__host__ __device__ __forceinline__ int tiles_per_lag(int N) {
+  if (OP == STBEM_OP_K) return ((N + kT - 1) / kT) * ((N + kKP - 1) / kKP);
+  const int nT = (N + kT - 1) / kT;
+  return nT * (nT + 1) / 2;
+}
+
+// One tile of one lag block: all threads of the CTA take part.
 template <int OP, typename R, typename T, bool LAG01>
-__global__ void __launch_bounds__(kTileThreads) k_tile(DevMesh M, int d_begin, const double* __restrict__ sing,
-                                                       T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void tile_body(const DevMesh& M, int d, int tile, const double* __restrict__ sing, T* __restrict__ out,
+                          unsigned char* smem_raw) {
   constexpr int P = Tile<OP>::pairs, NM = Tile<OP>::nm;
   double* mom = reinterpret_cast<double*>(smem_raw);
   LagNodes<R>* LN = reinterpret_cast<LagNodes<R>*>(smem_raw + (((size_t)P * NM * sizeof(double) + 15) / 16) * 16);
 
   const int N = M.N;
-  const int d = d_begin + blockIdx.y;
   const double ht = M.ht, alpha = M.alpha;
   int rt, ct;
   if (OP == STBEM_OP_K) {
     const int nP = (N + kKP - 1) / kKP;
-    rt = blockIdx.x / nP;
-    ct = blockIdx.x % nP;
+    rt = tile / nP;
+    ct = tile % nP;
   } else {
-    upper_tile(blockIdx.x, (N + kT - 1) / kT, &rt, &ct);
+    upper_tile(tile, (N + kT - 1) / kT, &rt, &ct);
   }
   const int r0 = rt * kT, c0 = ct * (OP == STBEM_OP_K ? kKP : kT);
   const int tid = threadIdx.x;
@@ -476,6 +488,79 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(DevMesh M, int d_begin, c
   }
 }
 
+template <int OP, typename R, typename T, bool LAG01>
+__global__ void __launch_bounds__(kTileThreads) k_tile(DevMesh M, int d_begin, const double* __restrict__ sing,
+                                                       T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_body<OP, R, T, LAG01>(M, d_begin + blockIdx.y, blockIdx.x, sing, out, smem_raw);
+}
+
+// ---- ragged batches: one persistent launch over the tiles of many problems --------
+// Work items are (problem, lag, tile) in the order of the host's item table
+// (largest problems first); CTAs take the next item from an atomic counter, so
+// uneven problems balance dynamically.  Item k of the table belongs to the
+// problem slot s with prefix[s] <= k < prefix[s + 1].
+__device__ __forceinline__ int ragged_slot(const long long* __restrict__ prefix, int P, long long item) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kSingThreads) k_ragged_singular(const RaggedProblem* __restrict__ probs,
+                                                                  const int* __restrict__ order,
+                                                                  const long long* __restrict__ prefix, int P,
+                                                                  unsigned long long* __restrict__ counter) {
+  __shared__ double red[5][kSingThreads];
+  __shared__ long long item_s;
+  const long long total = prefix[P];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = ragged_slot(prefix, P, item);
+    const RaggedProblem& pr = probs[order[s]];
+    const long long local = item - prefix[s];
+    const int Rl = OP == STBEM_OP_D ? 2 * pr.M.N : pr.M.N;
+    const int d = (int)(local / (3 * Rl)), slot = (int)(local % (3 * Rl));
+    singular_body<OP>(pr.M, slot, d, pr.M.sing, red);
+    __syncthreads();
+  }
+}
+
+template <int OP, typename R, typename T>
+__global__ void __launch_bounds__(kTileThreads) k_ragged_tile(const RaggedProblem* __restrict__ probs,
+                                                              const int* __restrict__ order,
+                                                              const long long* __restrict__ prefix, int P,
+                                                              unsigned long long* __restrict__ counter,
+                                                              T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long item_s;
+  const long long total = prefix[P];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = ragged_slot(prefix, P, item);
+    const RaggedProblem& pr = probs[order[s]];
+    const long long local = item - prefix[s];
+    const int nt_tiles = tiles_per_lag<OP>(pr.M.N);
+    const int d = (int)(local / nt_tiles), t = (int)(local % nt_tiles);
+    T* o = out + pr.op_off;
+    if (d < 2) tile_body<OP, R, T, true>(pr.M, d, t, pr.M.sing, o, smem_raw);
+    else tile_body<OP, R, T, false>(pr.M, d, t, pr.M.sing, o, smem_raw);
+    __syncthreads();
+  }
+}
+
 // ---- host side ----------------------------------------------------------------
 cudaError_t upload_rule_tables(const RuleTables& t, cudaStream_t s) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_tab, &t, sizeof(RuleTables), 0, cudaMemcpyHostToDevice, s);
@@ -531,6 +616,50 @@ static cudaError_t launch_op(const DevMesh& M, int lag_begin, int lag_end, T* ou
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+int assembly_tiles_per_lag(int op, int N) {
+  if (op == STBEM_OP_V) return tiles_per_lag<STBEM_OP_V>(N);
+  if (op == STBEM_OP_K) return tiles_per_lag<STBEM_OP_K>(N);
+  return tiles_per_lag<STBEM_OP_D>(N);
+}
+
+template <int OP, typename R, typename T>
+static cudaError_t ragged_op(const RaggedProblem* probs, int P, RaggedItems si, RaggedItems ti,
+                             unsigned long long* counters, T* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_singular<OP>, kSingThreads, 0);
+  if (e != cudaSuccess) return e;
+  k_ragged_singular<OP><<<sms * (occ > 0 ? occ : 1), kSingThreads, 0, s>>>(probs, si.order, si.prefix, P, counters);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = tile_smem_bytes<OP, R>();
+  e = cudaFuncSetAttribute(k_ragged_tile<OP, R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_tile<OP, R, T>, kTileThreads, smem);
+  if (e != cudaSuccess) return e;
+  k_ragged_tile<OP, R, T><<<sms * (occ > 0 ? occ : 1), kTileThreads, smem, s>>>(probs, ti.order, ti.prefix, P,
+                                                                                  counters + 1, out);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t ragged_assemble_launch(int op, int prec, const RaggedProblem* probs, int P, RaggedItems si,
+                                   RaggedItems ti, unsigned long long* counters, void* out, cudaStream_t s) {
+  if (prec == STBEM_F64) {
+    double* o = static_cast<double*>(out);
+    if (op == STBEM_OP_V) return ragged_op<STBEM_OP_V, double>(probs, P, si, ti, counters, o, s);
+    if (op == STBEM_OP_K) return ragged_op<STBEM_OP_K, double>(probs, P, si, ti, counters, o, s);
+    return ragged_op<STBEM_OP_D, double>(probs, P, si, ti, counters, o, s);
+  }
+  float* o = static_cast<float*>(out);
+  if (op == STBEM_OP_V) return ragged_op<STBEM_OP_V, float>(probs, P, si, ti, counters, o, s);
+  if (op == STBEM_OP_K) return ragged_op<STBEM_OP_K, float>(probs, P, si, ti, counters, o, s);
+  return ragged_op<STBEM_OP_D, float>(probs, P, si, ti, counters, o, s);
 }
 
 cudaError_t assemble_launch(const DevMesh& M, int op, int prec, int lag_begin, int lag_end, void* out,

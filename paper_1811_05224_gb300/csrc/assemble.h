@@ -18,7 +18,32 @@ struct DevMesh {
   double* sing;      // lag-0/1 moments of the 3 (2N) singular pairs (assembly scratch)
 };
 
+// One problem of a ragged batch: its mesh and the element offsets of its
+// data in the batch's concatenated arrays.
+struct RaggedProblem {
+  DevMesh M;
+  long long op_off;    // lag blocks: n_t x N x N elements from here
+  long long vec_off;   // n_t x N vectors
+  long long mass_off;  // N-vectors (lumped mass)
+};
+
+// Work list of a persistent launch over a ragged batch: problems in the order
+// `order` (P entries, largest first), item counts as prefix sums (P + 1).
+struct RaggedItems {
+  const int* order;
+  const long long* prefix;
+};
+
 void build_rule_tables(RuleTables* t);
+// tiles of one lag block (host copy of the assembly's tiling)
+int assembly_tiles_per_lag(int op, int N);
+// All lag blocks of op for every problem of a ragged batch: one persistent
+// launch for the identical / vertex-sharing pairs at lags 0 and 1 (items:
+// problem x lag x pair slot) and one for the tiles (problem x lag x tile).
+// counters: two device words (reset here).
+cudaError_t ragged_assemble_launch(int op, int prec, const RaggedProblem* probs, int P, RaggedItems sing_items,
+                                   RaggedItems tile_items, unsigned long long* counters, void* out,
+                                   cudaStream_t s);
 // process-wide count of kernel launches (incremented by every launcher)
 void count_launches(unsigned n);
 unsigned long long launch_count();

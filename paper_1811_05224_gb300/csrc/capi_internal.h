@@ -1,0 +1,54 @@
+// Internal definitions shared by the translation units of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "assemble.h"
+#include "stbem.h"
+
+struct stbem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+struct stbem_mesh {
+  int device = 0;
+  int N = 0, n_t = 0;
+  double T = 0, ht = 0, alpha = 0;
+  std::vector<double> h;     // segment lengths (host copy)
+  double* dbuf = nullptr;    // device geometry
+  int* ibuf = nullptr;
+  double* sbuf = nullptr;    // lag-0/1 singular-pair moments (2 lags x 3 x 2N x 5)
+  stbem::DevMesh dev{};
+};
+
+namespace stbem_internal {
+
+inline int fail(stbem_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+inline int cuda_fail(stbem_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, STBEM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+}  // namespace stbem_internal
+
+#define CUDA_TRY(ctx, call, where)                                                  \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) return stbem_internal::cuda_fail(ctx, e_, where);        \
+  } while (0)

@@ -48,14 +48,11 @@ size_t apply_workspace_bytes(int nt, int nx, int n_rhs) {
   return (size_t)n_rhs * p.MT * p.CH * TM * (size_t)nx * sizeof(double);
 }
 
+// One (row tile it, lag chunk ch, right-hand side b, time tile mt) unit.
 template <typename TA, typename TC, bool TRANS>
-__global__ void __launch_bounds__(kApplyThreads)
-k_apply(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
-        const double* __restrict__ x, double* __restrict__ part) {
-  __shared__ TC As[TJ][TI + 1];
-  __shared__ TC Xs[TJ][TM + 1];
-  const int it = blockIdx.x, ch = blockIdx.y;
-  const int b = blockIdx.z / MT, mt = blockIdx.z % MT;
+__device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
+                                           const double* __restrict__ x, double* __restrict__ part, int it,
+                                           int ch, int b, int mt, TC (*As)[TI + 1], TC (*Xs)[TM + 1]) {
   const int m0 = mt * TM, i0 = it * TI;
   const int mmax = min(m0 + TM, nt) - 1;        // largest m in the tile
   const int d0 = ch * DC;
@@ -127,6 +124,77 @@ k_apply(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
   }
 }
 
+template <typename TA, typename TC, bool TRANS>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
+        const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ TC As[TJ][TI + 1];
+  __shared__ TC Xs[TJ][TM + 1];
+  apply_body<TA, TC, TRANS>(nt, nx, MT, CH, DC, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT,
+                            blockIdx.z % MT, As, Xs);
+}
+
+// ---- ragged batches ------------------------------------------------------------------
+__device__ __forceinline__ int ragged_find(const long long* __restrict__ prefix, int P, long long item) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Persistent product over the units of every problem (order: largest first);
+// unit u of a problem is (ch, mt, it) with it fastest, so that concurrent
+// units share lag blocks in L2.
+template <typename TA, typename TC>
+__global__ void __launch_bounds__(kApplyThreads)
+k_ragged_apply(const RaggedApplyPlan* __restrict__ plans, const int* __restrict__ order,
+               const long long* __restrict__ prefix, int P, unsigned long long* __restrict__ counter,
+               const TA* __restrict__ A, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ TC As[TJ][TI + 1];
+  __shared__ TC Xs[TJ][TM + 1];
+  __shared__ long long item_s;
+  const long long total = prefix[P];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = ragged_find(prefix, P, item);
+    const RaggedApplyPlan pl = plans[order[s]];
+    const long long u = item - prefix[s];
+    const int it = (int)(u % pl.IT);
+    const long long r = u / pl.IT;
+    const int mt = (int)(r % pl.MT), ch = (int)(r / pl.MT);
+    apply_body<TA, TC, false>(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, A + pl.a_off, x + pl.v_off, part + pl.part_off,
+                              it, ch, 0, mt, As, Xs);
+    __syncthreads();
+  }
+}
+
+// y = sum of the lag-chunk partials, every problem (vprefix: natural order)
+__global__ void k_ragged_reduce(const RaggedApplyPlan* __restrict__ plans, const long long* __restrict__ vprefix,
+                                int P, const double* __restrict__ part, double* __restrict__ y) {
+  const long long total = vprefix[P];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = ragged_find(vprefix, P, e);
+    const RaggedApplyPlan pl = plans[p];
+    const long long local = e - vprefix[p];
+    const int i = (int)(local % pl.nx), m = (int)(local / pl.nx);
+    const int mt = m / TM, mm = m % TM;
+    const int mmax = min(mt * TM + TM, pl.nt) - 1;
+    const int nch = min(pl.CH, mmax / pl.DC + 1);
+    const double* pt = part + pl.part_off + (((size_t)mt * pl.CH) * TM + mm) * pl.nx + i;
+    double acc = 0.0;
+    for (int c = 0; c < nch; ++c) acc += pt[(size_t)c * TM * pl.nx];
+    y[pl.v_off + local] = acc;
+  }
+}
+
 template <bool TRANS>
 __global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC,
                                const double* __restrict__ part, double* __restrict__ y) {
@@ -191,6 +259,43 @@ cudaError_t noalloc_scratch_ptr(int device, void** ptr) {
   }
   *ptr = g_noalloc_ptr[device];
   return cudaSuccess;
+}
+
+void ragged_apply_plan(int nt, int nx, int lags_per_chunk, RaggedApplyPlan* p) {
+  p->nt = nt;
+  p->nx = nx;
+  p->MT = (nt + TM - 1) / TM;
+  p->IT = (nx + TI - 1) / TI;
+  p->DC = lags_per_chunk < 1 ? 1 : (lags_per_chunk > nt ? nt : lags_per_chunk);
+  p->CH = (nt + p->DC - 1) / p->DC;
+  p->units = (long long)p->IT * p->MT * p->CH;
+  p->part_elems = (long long)p->MT * p->CH * TM * nx;
+}
+
+cudaError_t ragged_apply_launch(int prec, const RaggedApplyPlan* plans, RaggedItems items, const long long* vprefix,
+                                int P, unsigned long long* counter, const void* A, const double* x, double* y,
+                                double* part, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (prec == STBEM_F64) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply<double, double>, kApplyThreads, 0);
+    if (e != cudaSuccess) return e;
+    k_ragged_apply<double, double><<<sms * (occ > 0 ? occ : 1), kApplyThreads, 0, s>>>(
+        plans, items.order, items.prefix, P, counter, static_cast<const double*>(A), x, part);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply<float, float>, kApplyThreads, 0);
+    if (e != cudaSuccess) return e;
+    k_ragged_apply<float, float><<<sms * (occ > 0 ? occ : 1), kApplyThreads, 0, s>>>(
+        plans, items.order, items.prefix, P, counter, static_cast<const float*>(A), x, part);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ragged_reduce<<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
+  count_launches(2);
+  return cudaGetLastError();
 }
 
 cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,

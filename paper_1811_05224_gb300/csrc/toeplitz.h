@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 
+#include "assemble.h"
 #include "stbem.h"
 
 namespace stbem {
@@ -14,4 +15,19 @@ constexpr int kNoAllocMaxDevices = 64;
 cudaError_t noalloc_scratch_ptr(int device, void** ptr);
 cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
                          const double* x, double* y, void* work, cudaStream_t s);
+
+// Product plan of one problem of a ragged batch with `lags_per_chunk` lags per
+// partial (the tuned shape) and the offsets of its data.
+struct RaggedApplyPlan {
+  int nt, nx, MT, IT, CH, DC;
+  long long units, part_elems;
+  long long a_off, v_off, part_off;
+};
+void ragged_apply_plan(int nt, int nx, int lags_per_chunk, RaggedApplyPlan* p);
+// y = A x for every problem: one persistent launch over all units (items:
+// problem order + unit prefix sums), then one reduction over all outputs
+// (vprefix: n_t N_x prefix sums in problem order).  counter: one device word.
+cudaError_t ragged_apply_launch(int prec, const RaggedApplyPlan* plans, RaggedItems items, const long long* vprefix,
+                                int P, unsigned long long* counter, const void* A, const double* x, double* y,
+                                double* part, cudaStream_t s);
 }  // namespace stbem

@@ -172,6 +172,116 @@ __global__ void k_bscale(const double* __restrict__ X, const double* __restrict_
     Y[e] = a[e / n] * X[e];
 }
 
+// ---- ragged batches: P problems, vectors concatenated (vprefix[p] = start) -----
+__device__ __forceinline__ int seg_of(const long long* __restrict__ prefix, int P, long long e) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// out[t][p] = <Q[t] | seg p, U | seg p>; one block per (p, t), fixed-order reduction
+__global__ void __launch_bounds__(256) k_rdots(const double* __restrict__ Q, size_t ldq,
+                                               const double* __restrict__ U, const long long* __restrict__ vp,
+                                               int P, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int p = blockIdx.x, t = blockIdx.y;
+  const double* q = Q + (size_t)t * ldq;
+  double acc = 0.0;
+  for (long long e = vp[p] + threadIdx.x; e < vp[p + 1]; e += 256) acc = fma(q[e], U[e], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)t * P + p] = red[0];
+}
+
+// U -= sum_t H[t][p] Q[t] (sign = -1) or Y = sum_t H[t][p] Q[t] (sign = 0)
+__global__ void k_rcomb(const double* __restrict__ Q, size_t ldq, int k, const double* __restrict__ H,
+                        const long long* __restrict__ vp, int P, int sub, double* __restrict__ U) {
+  const long long n = vp[P];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int p = seg_of(vp, P, e);
+    double acc = 0.0;
+    for (int t = 0; t < k; ++t) acc = fma(H[(size_t)t * P + p], Q[(size_t)t * ldq + e], acc);
+    U[e] = sub ? U[e] - acc : acc;
+  }
+}
+
+// Y = a[p] X per segment
+__global__ void k_rscale(const double* __restrict__ X, const double* __restrict__ a, const long long* __restrict__ vp,
+                         int P, double* __restrict__ Y) {
+  const long long n = vp[P];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    Y[e] = a[seg_of(vp, P, e)] * X[e];
+}
+
+// nrm[p] = sqrt(sq[p]); inv[p] = 1 / nrm[p] for active problems with a
+// positive finite norm, else 0
+__global__ void k_rinv(const double* __restrict__ sq, const int* __restrict__ active, int P, double* __restrict__ nrm,
+                       double* __restrict__ inv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double v = sqrt(sq[p]);
+  nrm[p] = v;
+  inv[p] = (active[p] && v > 0.0 && isfinite(v)) ? 1.0 / v : 0.0;
+}
+
+// y[e] = x[e] / L[mass_off + i] per problem
+__global__ void k_rdiag_div(const RaggedProblem* __restrict__ probs, const long long* __restrict__ vp, int P,
+                            const double* __restrict__ x, const double* __restrict__ L, double* __restrict__ y) {
+  const long long n = vp[P];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int p = seg_of(vp, P, e);
+    const int N = probs[p].M.N;
+    const int i = (int)((e - vp[p]) % N);
+    y[e] = x[e] / L[probs[p].mass_off + i];
+  }
+}
+
+// right-hand side data of every problem (source ystar[p]) and masses
+__global__ void k_rrhs_g(const RaggedProblem* __restrict__ probs, const long long* __restrict__ vp, int P,
+                         const double* __restrict__ ystar, double* __restrict__ g) {
+  const long long n = vp[P];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int p = seg_of(vp, P, e);
+    const DevMesh& M = probs[p].M;
+    const long long local = e - vp[p];
+    const int q = (int)(local % M.N), t = (int)(local / M.N);
+    const double dx = M.vx[q] - ystar[2 * p], dy = M.vy[q] - ystar[2 * p + 1];
+    const double a = M.alpha * (dx * dx + dy * dy) / 4.0;
+    const double E1 = e1_only(a / ((double)(t + 1) * M.ht));
+    const double E0 = t > 0 ? e1_only(a / ((double)t * M.ht)) : 0.0;
+    g[e] = (E1 - E0) * M.alpha / (4.0 * kPi) / M.ht;
+  }
+}
+
+__global__ void k_rhalf_mass_add(const RaggedProblem* __restrict__ probs, const long long* __restrict__ vp, int P,
+                                 const double* __restrict__ g, double* __restrict__ f) {
+  const long long n = vp[P];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int p = seg_of(vp, P, e);
+    const DevMesh& M = probs[p].M;
+    const int i = (int)((e - vp[p]) % M.N);
+    const long long row = e - i;
+    const int ip = (i + 1) % M.N;
+    f[e] += 0.5 * M.ht * 0.5 * M.slen[i] * (g[e] + g[row + ip]);
+  }
+}
+
+__global__ void k_rlumped(const RaggedProblem* __restrict__ probs, int P, double* __restrict__ L) {
+  const int p = blockIdx.y;
+  const DevMesh& M = probs[p].M;
+  const int N = M.N;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < N; l += gridDim.x * blockDim.x)
+    L[probs[p].mass_off + l] = M.ht * (M.slen[(l - 1 + N) % N] + 2.0 * M.slen[l] + M.slen[(l + 1) % N]) / 4.0;
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
@@ -248,4 +358,57 @@ cudaError_t diag_div_launch(const double* x, const double* L, double* y, int nt,
   return cudaGetLastError();
 }
 
+}  // namespace stbem
+
+namespace stbem {
+static int rgrid(long long n) {
+  const long long b = (n + 255) / 256;
+  return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
+}
+cudaError_t rdots_launch(const double* Q, size_t ldq, int k, const double* U, const long long* vp, int P,
+                         double* out, cudaStream_t s) {
+  k_rdots<<<dim3(P, k), 256, 0, s>>>(Q, ldq, U, vp, P, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rcomb_launch(const double* Q, size_t ldq, int k, const double* H, const long long* vp, int P, bool sub,
+                         double* U, long long n, cudaStream_t s) {
+  k_rcomb<<<rgrid(n), 256, 0, s>>>(Q, ldq, k, H, vp, P, sub ? 1 : 0, U);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rscale_launch(const double* X, const double* a, const long long* vp, int P, double* Y, long long n,
+                          cudaStream_t s) {
+  k_rscale<<<rgrid(n), 256, 0, s>>>(X, a, vp, P, Y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rinv_launch(const double* sq, const int* active, int P, double* nrm, double* inv, cudaStream_t s) {
+  k_rinv<<<(P + 127) / 128, 128, 0, s>>>(sq, active, P, nrm, inv);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rdiag_div_launch(const RaggedProblem* probs, const long long* vp, int P, const double* x, const double* L,
+                             double* y, long long n, cudaStream_t s) {
+  k_rdiag_div<<<rgrid(n), 256, 0, s>>>(probs, vp, P, x, L, y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rrhs_g_launch(const RaggedProblem* probs, const long long* vp, int P, const double* ystar, double* g,
+                          long long n, cudaStream_t s) {
+  k_rrhs_g<<<rgrid(n), 256, 0, s>>>(probs, vp, P, ystar, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rhalf_mass_add_launch(const RaggedProblem* probs, const long long* vp, int P, const double* g, double* f,
+                                  long long n, cudaStream_t s) {
+  k_rhalf_mass_add<<<rgrid(n), 256, 0, s>>>(probs, vp, P, g, f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t rlumped_launch(const RaggedProblem* probs, int P, int max_n, double* L, cudaStream_t s) {
+  k_rlumped<<<dim3((max_n + 127) / 128, P), 128, 0, s>>>(probs, P, L);
+  count_launches(1);
+  return cudaGetLastError();
+}
 }  // namespace stbem

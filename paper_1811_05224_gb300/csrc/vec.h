@@ -27,6 +27,24 @@ cudaError_t bsub_comb_launch(const double* Q, int k, const double* H, double* U,
 cudaError_t bcomb_launch(const double* Q, int k, const double* C, double* Y, int B, size_t n, cudaStream_t s);
 // Y[b] = a[b] X[b]
 cudaError_t bscale_launch(const double* X, const double* a, double* Y, int B, size_t n, cudaStream_t s);
+// ragged batches (P problems; vectors concatenated, vp = P + 1 prefix offsets):
+// out[t][p] = <Q[t], U> on segment p (Q[t] = Q + t ldq), t < k
+cudaError_t rdots_launch(const double* Q, size_t ldq, int k, const double* U, const long long* vp, int P,
+                         double* out, cudaStream_t s);
+// sub: U -= sum_t H[t][p] Q[t]; else U = sum_t H[t][p] Q[t]  (segment p)
+cudaError_t rcomb_launch(const double* Q, size_t ldq, int k, const double* H, const long long* vp, int P, bool sub,
+                         double* U, long long n, cudaStream_t s);
+cudaError_t rscale_launch(const double* X, const double* a, const long long* vp, int P, double* Y, long long n,
+                          cudaStream_t s);
+// nrm = sqrt(sq), inv = active && nrm > 0 ? 1 / nrm : 0
+cudaError_t rinv_launch(const double* sq, const int* active, int P, double* nrm, double* inv, cudaStream_t s);
+cudaError_t rdiag_div_launch(const RaggedProblem* probs, const long long* vp, int P, const double* x, const double* L,
+                             double* y, long long n, cudaStream_t s);
+cudaError_t rrhs_g_launch(const RaggedProblem* probs, const long long* vp, int P, const double* ystar, double* g,
+                          long long n, cudaStream_t s);
+cudaError_t rhalf_mass_add_launch(const RaggedProblem* probs, const long long* vp, int P, const double* g, double* f,
+                                  long long n, cudaStream_t s);
+cudaError_t rlumped_launch(const RaggedProblem* probs, int P, int max_n, double* L, cudaStream_t s);
 // dst[i] = (float)src[i]
 cudaError_t round_f32_launch(const double* src, float* dst, size_t n, cudaStream_t s);
 }  // namespace stbem
