@@ -61,11 +61,17 @@ __device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int D
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;        // rows tx*4.., time ty*2..
   const double* xb = x + (size_t)b * nt * nx;
+  // FP32 products are summed in FP32 over one lag block's columns only and
+  // flushed into FP64 after every lag, so no FP32 chain is longer than N_x
   TC acc[2][4];
+  double acc64[2][4];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = (TC)0;
+    for (int c = 0; c < 4; ++c) {
+      acc[a][c] = (TC)0;
+      acc64[a][c] = 0.0;
+    }
 
   for (int d = d0; d < d1; ++d) {
     const TA* Ad = A + (size_t)d * nx * nx;
@@ -109,6 +115,21 @@ __device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int D
       }
       __syncthreads();
     }
+    if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc64[a][c] += (double)acc[a][c];
+          acc[a][c] = (TC)0;
+        }
+    }
+  }
+  if constexpr (sizeof(TC) == 8) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc64[a][c] = (double)acc[a][c];
   }
   // partial tile -> part[b][mt][ch][mm][i]
   double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TM) * nx;
@@ -119,7 +140,7 @@ __device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int D
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int gi = i0 + tx * 4 + c;
-      if (gi < nx) pt[(size_t)mm * nx + gi] = (double)acc[a][c];
+      if (gi < nx) pt[(size_t)mm * nx + gi] = acc64[a][c];
     }
   }
 }

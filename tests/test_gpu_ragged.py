@@ -132,3 +132,21 @@ def test_ragged_rejects_bad_arguments(ctx, batch):
     assert code == capi.STBEM_ERR_ARG
     code = ctx.lib.stbem_ragged_assemble(ctx.h, R.h, capi.OP_V, 5, out.data_ptr())
     assert code == capi.STBEM_ERR_ARG
+
+
+def test_ragged_solve_fp32_operators(ctx, batch):
+    """FP32 operators (FP64 singular pairs), FP64 vectors: the product sums
+    FP32 terms over one lag block's columns and flushes into FP64 per lag, so
+    the residual reaches 1e-7; the batch's solutions agree with the
+    single-problem FP32 solves to the solver tolerance times kappa (~100)."""
+    import paper_1811_05224_gb300 as P
+    R, meshes, _ = batch
+    V, K, D = R.assemble("V", "f32"), R.assemble("K"), R.assemble("D", "f32")
+    L = R.lumped_mass()
+    ys = [(1.5, 1.5), (1.3, 1.4), (1.8, -0.2), (2.0, 0.4), (-0.7, 0.5)]
+    _, f = R.rhs(K, ys)
+    w, infos = R.solve(V, f, D, L, tol=1e-7, restart=30, max_iter=400)
+    assert all(i["status"] == 0 and i["rel_residual"] <= 1e-7 for i in infos), infos
+    for p, m in enumerate(meshes):
+        w1, _ = P.solve(ctx, R.view_op(V, p), R.view_vec(f, p), R.view_op(D, p), R.view_mass(L, p), tol=1e-7)
+        assert float((R.view_vec(w, p) - w1).norm() / w1.norm()) < 2e-5, p
