@@ -49,9 +49,12 @@ struct stbem_ragged {
   // products
   int lags_per_chunk = 0;                       // 0: not tuned yet
   std::vector<stbem::RaggedApplyPlan> plans;
-  stbem::RaggedApplyPlan* d_plans = nullptr;
+  stbem::RaggedApplyPlan* d_plans = nullptr;    // generic tiles (FP64, and FP32 when N_x % 4 != 0)
   long long* d_aprefix = nullptr;               // P + 1 (problem order)
-  long long part_elems = 0;
+  bool fp32_tiles = false;                      // every N_x % 4 == 0: register-tiled FP32 kernel
+  stbem::RaggedApplyPlan* d_plans32 = nullptr;
+  long long* d_aprefix32 = nullptr;
+  long long part_elems = 0;                     // max over both plan sets
   std::vector<int> tuned_candidates;
   std::vector<float> tuned_ms;
   // solve: pinned host buffers and captured graphs
@@ -77,14 +80,14 @@ void free_graphs(stbem_ragged* R) {
 }
 
 // plans for a lag-chunk length; returns the partial-sum elements needed
-long long build_plans(stbem_ragged* R, int lpc, std::vector<stbem::RaggedApplyPlan>* out,
+long long build_plans(stbem_ragged* R, int lpc, bool fp32_tiles, std::vector<stbem::RaggedApplyPlan>* out,
                       std::vector<long long>* aprefix) {
   const int P = R->P;
   out->assign(P, {});
   long long part = 0;
   for (int p = 0; p < P; ++p) {
     stbem::RaggedApplyPlan& pl = (*out)[p];
-    stbem::ragged_apply_plan(R->nt[p], R->nx[p], lpc, &pl);
+    stbem::ragged_apply_plan(R->nt[p], R->nx[p], lpc, fp32_tiles, &pl);
     pl.a_off = R->op_off[p];
     pl.v_off = R->vec_off[p];
     pl.part_off = part;
@@ -95,11 +98,11 @@ long long build_plans(stbem_ragged* R, int lpc, std::vector<stbem::RaggedApplyPl
   return part;
 }
 
-cudaError_t upload_plans(stbem_ragged* R, const std::vector<stbem::RaggedApplyPlan>& plans,
-                         const std::vector<long long>& aprefix, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyAsync(R->d_plans, plans.data(), plans.size() * sizeof(plans[0]), cudaMemcpyHostToDevice, s);
+cudaError_t upload_plans(const std::vector<stbem::RaggedApplyPlan>& plans, const std::vector<long long>& aprefix,
+                         stbem::RaggedApplyPlan* d_plans, long long* d_aprefix, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(d_plans, plans.data(), plans.size() * sizeof(plans[0]), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(R->d_aprefix, aprefix.data(), aprefix.size() * sizeof(long long), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(d_aprefix, aprefix.data(), aprefix.size() * sizeof(long long), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
 }
@@ -107,13 +110,20 @@ cudaError_t upload_plans(stbem_ragged* R, const std::vector<stbem::RaggedApplyPl
 long long part_elems_for(stbem_ragged* R, int lpc) {
   std::vector<stbem::RaggedApplyPlan> pl;
   std::vector<long long> pre;
-  return build_plans(R, lpc, &pl, &pre);
+  long long n = build_plans(R, lpc, false, &pl, &pre);
+  if (R->fp32_tiles) n = std::max(n, build_plans(R, lpc, true, &pl, &pre));
+  return n;
 }
 
 int set_chunk(stbem_ctx* ctx, stbem_ragged* R, int lpc) {
   std::vector<long long> pre;
-  R->part_elems = build_plans(R, lpc, &R->plans, &pre);
-  CUDA_TRY(ctx, upload_plans(R, R->plans, pre, ctx->stream), "ragged: upload product plans");
+  R->part_elems = build_plans(R, lpc, false, &R->plans, &pre);
+  CUDA_TRY(ctx, upload_plans(R->plans, pre, R->d_plans, R->d_aprefix, ctx->stream), "ragged: upload product plans");
+  if (R->fp32_tiles) {
+    std::vector<stbem::RaggedApplyPlan> p32;
+    R->part_elems = std::max(R->part_elems, build_plans(R, lpc, true, &p32, &pre));
+    CUDA_TRY(ctx, upload_plans(p32, pre, R->d_plans32, R->d_aprefix32, ctx->stream), "ragged: upload FP32 plans");
+  }
   R->lags_per_chunk = lpc;
   free_graphs(R);   // captured steps refer to the old plans' partial layout
   return STBEM_OK;
@@ -121,7 +131,9 @@ int set_chunk(stbem_ctx* ctx, stbem_ragged* R, int lpc) {
 
 cudaError_t rapply(stbem_ragged* R, int prec, const void* A, const double* x, double* y, double* part,
                    cudaStream_t s) {
-  return stbem::ragged_apply_launch(prec, R->d_plans, {R->d_order, R->d_aprefix}, R->d_vprefix, R->P,
+  const bool t32 = prec == STBEM_F32 && R->fp32_tiles;
+  return stbem::ragged_apply_launch(prec, t32, t32 ? R->d_plans32 : R->d_plans,
+                                    {R->d_order, t32 ? R->d_aprefix32 : R->d_aprefix}, R->d_vprefix, R->P,
                                     R->d_counters + 2, A, x, y, part, s);
 }
 
@@ -157,6 +169,8 @@ int stbem_ragged_create(stbem_ctx* ctx, int n, const stbem_problem* probs, stbem
     R->mass_elems += m->N;
     R->max_nx = std::max(R->max_nx, m->N);
   }
+  R->fp32_tiles = true;
+  for (int v : R->nx) R->fp32_tiles = R->fp32_tiles && stbem::ragged_fp32_tiles_ok(v);
   // largest problems first (work ~ n_t N_x^2)
   R->order.resize(n);
   std::iota(R->order.begin(), R->order.end(), 0);
@@ -185,6 +199,8 @@ int stbem_ragged_create(stbem_ctx* ctx, int n, const stbem_problem* probs, stbem
   if (e == cudaSuccess) e = cudaMalloc(&R->d_counters, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&R->d_plans, n * sizeof(stbem::RaggedApplyPlan));
   if (e == cudaSuccess) e = cudaMalloc(&R->d_aprefix, (n + 1) * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&R->d_plans32, n * sizeof(stbem::RaggedApplyPlan));
+  if (e == cudaSuccess) e = cudaMalloc(&R->d_aprefix32, (n + 1) * sizeof(long long));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&R->gs, cudaStreamNonBlocking);
   cudaStream_t s = ctx->stream;
   if (e == cudaSuccess) e = cudaMemcpyAsync(R->d_probs, hp.data(), n * sizeof(hp[0]), cudaMemcpyHostToDevice, s);
@@ -210,7 +226,8 @@ void stbem_ragged_destroy(stbem_ragged* R) {
   free_graphs(R);
   for (auto* m : R->meshes) stbem_mesh_destroy(m);
   for (void* p : {(void*)R->d_probs, (void*)R->d_order, (void*)R->d_sing_prefix, (void*)R->d_tile_prefix,
-                  (void*)R->d_vprefix, (void*)R->d_counters, (void*)R->d_plans, (void*)R->d_aprefix})
+                  (void*)R->d_vprefix, (void*)R->d_counters, (void*)R->d_plans, (void*)R->d_aprefix,
+                  (void*)R->d_plans32, (void*)R->d_aprefix32})
     if (p) cudaFree(p);
   if (R->h_buf) cudaFreeHost(R->h_buf);
   if (R->h_mask) cudaFreeHost(R->h_mask);

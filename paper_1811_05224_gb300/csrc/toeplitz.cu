@@ -14,6 +14,7 @@
 // chunk order, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "assemble.h"
@@ -27,10 +28,10 @@ struct ApplyPlan {
   int MT, IT, CH, DC;
 };
 
-static ApplyPlan make_plan(int nt, int nx) {
+static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI) {
   ApplyPlan p;
-  p.MT = (nt + TM - 1) / TM;
-  p.IT = (nx + TI - 1) / TI;
+  p.MT = (nt + tm - 1) / tm;
+  p.IT = (nx + ti - 1) / ti;
   // aim at ~4 waves of 152 SMs of (tile, chunk) units
   const long long target = 4 * 152;
   long long per_chunk = (long long)p.IT * ((p.MT + 1) / 2);
@@ -43,9 +44,24 @@ static ApplyPlan make_plan(int nt, int nx) {
   return p;
 }
 
+// FP32 forward products use the register-tiled kernel (128 x 64 tiles) when
+// rows are 16-byte aligned and its causal tiles alone fill two waves of
+// 2 x 152 CTAs; smaller products keep the 64 x 32 tiles, which need fewer
+// lag chunks (and partial sums) for the same parallelism.
+static bool use_apply32(int nx) { return nx % 4 == 0; }
+static bool use_apply32(int nt, int nx, int n_rhs) {
+  const long long it = (nx + 127) / 128, mt = (nt + 63) / 64;
+  return use_apply32(nx) && (long long)n_rhs * it * mt * (mt + 1) / 2 >= 2 * 2 * 152;
+}
+
 size_t apply_workspace_bytes(int nt, int nx, int n_rhs) {
   const ApplyPlan p = make_plan(nt, nx);
-  return (size_t)n_rhs * p.MT * p.CH * TM * (size_t)nx * sizeof(double);
+  size_t b = (size_t)n_rhs * p.MT * p.CH * TM * (size_t)nx * sizeof(double);
+  if (use_apply32(nt, nx, n_rhs)) {
+    const ApplyPlan q = make_plan(nt, nx, 64, 128);
+    b = std::max(b, (size_t)n_rhs * q.MT * q.CH * 64 * (size_t)nx * sizeof(double));
+  }
+  return b;
 }
 
 // One (row tile it, lag chunk ch, right-hand side b, time tile mt) unit.
@@ -155,6 +171,115 @@ k_apply(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
                             blockIdx.z % MT, As, Xs);
 }
 
+// ---- FP32 forward product, register-tiled ----------------------------------------------
+// A CTA owns 128 rows x 64 time steps (one right-hand side, one lag chunk);
+// thread (ty, tx) of 16 x 16 computes rows ty*8.. and steps tx*4.. from float4
+// shared-memory reads (32 FFMA per 3 loads).  Each lag's FP32 partial (a chain
+// of N_x terms) is added into a compensated (hi, lo) FP32 pair per output
+// (Knuth's two-sum, 6 FP32 operations), so lags accumulate without FP32 loss
+// and without FP64 arithmetic, which runs at 1/72 of the FP32 rate here.
+// Requires N_x % 4 == 0 (16-byte rows).
+constexpr int TI4 = 128, TM4 = 64, TJ4 = 16;
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (v - bp);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int DC, const float* __restrict__ A,
+                                             const double* __restrict__ x, double* __restrict__ part, int it, int ch,
+                                             int b, int mt, float (*As)[TI4], float (*Xs)[TM4]) {
+  const int m0 = mt * TM4, i0 = it * TI4;
+  const int mmax = min(m0 + TM4, nt) - 1;
+  const int d0 = ch * DC;
+  if (d0 > mmax) return;
+  const int d1 = min(d0 + DC, mmax + 1);
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const double* xb = x + (size_t)b * nt * nx;
+  float hi[8][4], lo[8][4];
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      hi[c][a] = 0.f;
+      lo[c][a] = 0.f;
+    }
+  for (int d = d0; d < d1; ++d) {
+    const float* Ad = A + (size_t)d * nx * nx;
+    float acc[8][4];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc[c][a] = 0.f;
+    for (int j0 = 0; j0 < nx; j0 += TJ4) {
+      // A tile: 128 rows x 16 columns as float4 along j, stored transposed
+#pragma unroll
+      for (int q = 0; q < (TI4 * TJ4 / 4) / 256; ++q) {
+        const int e = tid + q * 256;
+        const int ii = e % TI4, jq = e / TI4;
+        const int gi = i0 + ii, gj = j0 + jq * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gi < nx && gj < nx) v = *reinterpret_cast<const float4*>(Ad + (size_t)gi * nx + gj);
+        As[jq * 4 + 0][ii] = v.x;
+        As[jq * 4 + 1][ii] = v.y;
+        As[jq * 4 + 2][ii] = v.z;
+        As[jq * 4 + 3][ii] = v.w;
+      }
+      // x tile: x[m - d][j0 + jj] for the 64 steps of the tile
+#pragma unroll
+      for (int q = 0; q < (TM4 * TJ4) / 256; ++q) {
+        const int e = tid + q * 256;
+        const int jj = e % TJ4, mm = e / TJ4;
+        const int m = m0 + mm, gj = j0 + jj;
+        float v = 0.f;
+        if (m <= mmax && m - d >= 0 && gj < nx) v = (float)xb[(size_t)(m - d) * nx + gj];
+        Xs[jj][mm] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < TJ4; ++jj) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[jj][ty * 8]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[jj][ty * 8 + 4]);
+        const float4 xv = *reinterpret_cast<const float4*>(&Xs[jj][tx * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int a = 0; a < 4; ++a) acc[c][a] = fmaf(av[c], bv[a], acc[c][a]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) two_sum_add(hi[c][a], lo[c][a], acc[c][a]);
+  }
+  double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TM4) * nx;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int mm = tx * 4 + a;
+    if (m0 + mm > mmax) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int gi = i0 + ty * 8 + c;
+      if (gi < nx) pt[(size_t)mm * nx + gi] = (double)hi[c][a] + (double)lo[c][a];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_apply32(int nt, int nx, int MT, int CH, int DC, const float* __restrict__ A, const double* __restrict__ x,
+          double* __restrict__ part) {
+  __shared__ __align__(16) float As[TJ4][TI4];
+  __shared__ __align__(16) float Xs[TJ4][TM4];
+  apply32_body(nt, nx, MT, CH, DC, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT, blockIdx.z % MT, As, Xs);
+}
+
 // ---- ragged batches ------------------------------------------------------------------
 __device__ __forceinline__ int ragged_find(const long long* __restrict__ prefix, int P, long long item) {
   int lo = 0, hi = P;
@@ -196,7 +321,34 @@ k_ragged_apply(const RaggedApplyPlan* __restrict__ plans, const int* __restrict_
   }
 }
 
+__global__ void __launch_bounds__(256, 2)
+k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restrict__ order,
+                 const long long* __restrict__ prefix, int P, unsigned long long* __restrict__ counter,
+                 const float* __restrict__ A, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ __align__(16) float As[TJ4][TI4];
+  __shared__ __align__(16) float Xs[TJ4][TM4];
+  __shared__ long long item_s;
+  const long long total = prefix[P];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = ragged_find(prefix, P, item);
+    const RaggedApplyPlan pl = plans[order[s]];
+    const long long u = item - prefix[s];
+    const int it = (int)(u % pl.IT);
+    const long long r = u / pl.IT;
+    const int mt = (int)(r % pl.MT), ch = (int)(r / pl.MT);
+    apply32_body(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, A + pl.a_off, x + pl.v_off, part + pl.part_off, it, ch, 0, mt,
+                 As, Xs);
+    __syncthreads();
+  }
+}
+
 // y = sum of the lag-chunk partials, every problem (vprefix: natural order)
+template <int TM_>
 __global__ void k_ragged_reduce(const RaggedApplyPlan* __restrict__ plans, const long long* __restrict__ vprefix,
                                 int P, const double* __restrict__ part, double* __restrict__ y) {
   const long long total = vprefix[P];
@@ -206,17 +358,17 @@ __global__ void k_ragged_reduce(const RaggedApplyPlan* __restrict__ plans, const
     const RaggedApplyPlan pl = plans[p];
     const long long local = e - vprefix[p];
     const int i = (int)(local % pl.nx), m = (int)(local / pl.nx);
-    const int mt = m / TM, mm = m % TM;
-    const int mmax = min(mt * TM + TM, pl.nt) - 1;
+    const int mt = m / TM_, mm = m % TM_;
+    const int mmax = min(mt * TM_ + TM_, pl.nt) - 1;
     const int nch = min(pl.CH, mmax / pl.DC + 1);
-    const double* pt = part + pl.part_off + (((size_t)mt * pl.CH) * TM + mm) * pl.nx + i;
+    const double* pt = part + pl.part_off + (((size_t)mt * pl.CH) * TM_ + mm) * pl.nx + i;
     double acc = 0.0;
-    for (int c = 0; c < nch; ++c) acc += pt[(size_t)c * TM * pl.nx];
+    for (int c = 0; c < nch; ++c) acc += pt[(size_t)c * TM_ * pl.nx];
     y[pl.v_off + local] = acc;
   }
 }
 
-template <bool TRANS>
+template <bool TRANS, int TM_ = TM>
 __global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC,
                                const double* __restrict__ part, double* __restrict__ y) {
   const size_t total = (size_t)n_rhs * nt * nx;
@@ -225,20 +377,36 @@ __global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC
     const int i = (int)(e % nx);
     const int m = (int)((e / nx) % nt);       // time index in the computed order
     const int b = (int)(e / ((size_t)nx * nt));
-    const int mt = m / TM, mm = m % TM;
-    const int mmax = min(mt * TM + TM, nt) - 1;
+    const int mt = m / TM_, mm = m % TM_;
+    const int mmax = min(mt * TM_ + TM_, nt) - 1;
     const int nch = min(CH, mmax / DC + 1);
-    const double* pt = part + ((((size_t)b * MT + mt) * CH) * TM + mm) * nx + i;
+    const double* pt = part + ((((size_t)b * MT + mt) * CH) * TM_ + mm) * nx + i;
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += pt[(size_t)c * TM * nx];
+    for (int c = 0; c < nch; ++c) s += pt[(size_t)c * TM_ * nx];
     const int mo = TRANS ? (nt - 1 - m) : m;
     y[((size_t)b * nt + mo) * nx + i] = s;
   }
 }
 
+static cudaError_t launch32(int nt, int nx, const float* A, int n_rhs, const double* x, double* y, double* part,
+                            cudaStream_t s) {
+  const ApplyPlan p = make_plan(nt, nx, TM4, TI4);
+  k_apply32<<<dim3(p.IT, p.CH, n_rhs * p.MT), 256, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, A, x, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launches(2);
+  const size_t total = (size_t)n_rhs * nt * nx;
+  const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+  k_apply_reduce<false, TM4><<<blocks, 256, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
+  return cudaGetLastError();
+}
+
 template <typename TA, typename TC>
 static cudaError_t launch(bool trans, int nt, int nx, const TA* A, int n_rhs, const double* x,
                           double* y, double* part, cudaStream_t s) {
+  if constexpr (sizeof(TA) == 4) {
+    if (!trans && use_apply32(nt, nx, n_rhs)) return launch32(nt, nx, A, n_rhs, x, y, part, s);
+  }
   const ApplyPlan p = make_plan(nt, nx);
   dim3 grid(p.IT, p.CH, n_rhs * p.MT);
   if (trans)
@@ -282,20 +450,23 @@ cudaError_t noalloc_scratch_ptr(int device, void** ptr) {
   return cudaSuccess;
 }
 
-void ragged_apply_plan(int nt, int nx, int lags_per_chunk, RaggedApplyPlan* p) {
+void ragged_apply_plan(int nt, int nx, int lags_per_chunk, bool fp32_tiles, RaggedApplyPlan* p) {
+  const int tm = fp32_tiles ? TM4 : TM, ti = fp32_tiles ? TI4 : TI;
   p->nt = nt;
   p->nx = nx;
-  p->MT = (nt + TM - 1) / TM;
-  p->IT = (nx + TI - 1) / TI;
+  p->MT = (nt + tm - 1) / tm;
+  p->IT = (nx + ti - 1) / ti;
   p->DC = lags_per_chunk < 1 ? 1 : (lags_per_chunk > nt ? nt : lags_per_chunk);
   p->CH = (nt + p->DC - 1) / p->DC;
   p->units = (long long)p->IT * p->MT * p->CH;
-  p->part_elems = (long long)p->MT * p->CH * TM * nx;
+  p->part_elems = (long long)p->MT * p->CH * tm * nx;
 }
 
-cudaError_t ragged_apply_launch(int prec, const RaggedApplyPlan* plans, RaggedItems items, const long long* vprefix,
-                                int P, unsigned long long* counter, const void* A, const double* x, double* y,
-                                double* part, cudaStream_t s) {
+bool ragged_fp32_tiles_ok(int nx) { return use_apply32(nx); }
+
+cudaError_t ragged_apply_launch(int prec, bool fp32_tiles, const RaggedApplyPlan* plans, RaggedItems items,
+                                const long long* vprefix, int P, unsigned long long* counter, const void* A,
+                                const double* x, double* y, double* part, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
@@ -306,6 +477,11 @@ cudaError_t ragged_apply_launch(int prec, const RaggedApplyPlan* plans, RaggedIt
     if (e != cudaSuccess) return e;
     k_ragged_apply<double, double><<<sms * (occ > 0 ? occ : 1), kApplyThreads, 0, s>>>(
         plans, items.order, items.prefix, P, counter, static_cast<const double*>(A), x, part);
+  } else if (fp32_tiles) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply32, 256, 0);
+    if (e != cudaSuccess) return e;
+    k_ragged_apply32<<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(plans, items.order, items.prefix, P, counter,
+                                                              static_cast<const float*>(A), x, part);
   } else {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply<float, float>, kApplyThreads, 0);
     if (e != cudaSuccess) return e;
@@ -314,7 +490,10 @@ cudaError_t ragged_apply_launch(int prec, const RaggedApplyPlan* plans, RaggedIt
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_ragged_reduce<<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
+  if (prec != STBEM_F64 && fp32_tiles)
+    k_ragged_reduce<TM4><<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
+  else
+    k_ragged_reduce<TM><<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -23,11 +23,15 @@ struct RaggedApplyPlan {
   long long units, part_elems;
   long long a_off, v_off, part_off;
 };
-void ragged_apply_plan(int nt, int nx, int lags_per_chunk, RaggedApplyPlan* p);
+// fp32_tiles: the plan of the register-tiled FP32 kernel (128 x 64 tiles,
+// needs ragged_fp32_tiles_ok(nx) for every problem), else the generic one.
+void ragged_apply_plan(int nt, int nx, int lags_per_chunk, bool fp32_tiles, RaggedApplyPlan* p);
+bool ragged_fp32_tiles_ok(int nx);
 // y = A x for every problem: one persistent launch over all units (items:
 // problem order + unit prefix sums), then one reduction over all outputs
 // (vprefix: n_t N_x prefix sums in problem order).  counter: one device word.
-cudaError_t ragged_apply_launch(int prec, const RaggedApplyPlan* plans, RaggedItems items, const long long* vprefix,
-                                int P, unsigned long long* counter, const void* A, const double* x, double* y,
-                                double* part, cudaStream_t s);
+// prec F32 with fp32_tiles uses the register-tiled kernel and its plans.
+cudaError_t ragged_apply_launch(int prec, bool fp32_tiles, const RaggedApplyPlan* plans, RaggedItems items,
+                                const long long* vprefix, int P, unsigned long long* counter, const void* A,
+                                const double* x, double* y, double* part, cudaStream_t s);
 }  // namespace stbem

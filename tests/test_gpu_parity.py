@@ -96,11 +96,19 @@ def test_assembly_sampled_full_size(ctx):
             assert err.max() <= 1.0, (op, d, pairs[int(err.argmax())], err.max())
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", None)])
 def test_apply_matches_oracle(ctx, prec, tol):
+    """FP32: every lag's products are summed in FP32 over that lag's N_x
+    columns and the lags are combined without FP32 loss, so with x rounded to
+    FP32 the error is at most (N_x + 2) u of |A||x|, u = 2^-24.  Cases cover
+    the register-tiled kernel (N_x % 4 == 0 on a grid of causal tiles that
+    fills the GPU: 640 steps x 12 right-hand sides, 896 steps x 6, both with a
+    partial row tile) and the generic one (all the others)."""
     import paper_1811_05224_gb300 as P
     rng = np.random.default_rng(3)
-    for nt, nx, nb in [(37, 45, 3), (1, 7, 1), (70, 64, 2), (5, 130, 1)]:
+    for nt, nx, nb in [(37, 45, 3), (1, 7, 1), (70, 64, 2), (5, 130, 1), (130, 132, 2), (300, 256, 1),
+                       (640, 8, 12), (896, 20, 6)]:
+        tol_c = tol if tol is not None else (nx + 2) * 2.0 ** -24
         A = rng.standard_normal((nt, nx, nx))
         x = rng.standard_normal((nb, nt, nx))
         dt = torch.float64 if prec == "f64" else torch.float32
@@ -112,7 +120,7 @@ def test_apply_matches_oracle(ctx, prec, tol):
             for b in range(nb):
                 ref = OS.toeplitz_apply(Aeff, x[b], transpose=tr)
                 mag = OS.toeplitz_apply(np.abs(Aeff), np.abs(x[b]), transpose=tr)
-                assert np.all(np.abs(y[b] - ref) <= tol * mag + 1e-300), (nt, nx, tr)
+                assert np.all(np.abs(y[b] - ref) <= tol_c * mag + 1e-300), (nt, nx, tr)
 
 
 def test_rhs_matches_oracle(ctx):
