@@ -113,16 +113,19 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// K-major, N (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
+constexpr uint32_t idesc_for(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+constexpr uint32_t kIdesc = idesc_for(BN);
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate,
+                                          uint32_t idesc = kIdesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -141,9 +144,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Plain kernel, output tile 128 x BN_ (BN_ = 128 or 256 time steps).
+template <int BN_>
+struct TcTile {
+  static constexpr uint32_t b_bytes = BN_ * BK * 2;
+  static constexpr uint32_t stage_bytes = A_BYTES + b_bytes;
+  static constexpr uint32_t tmem_cols = BN_;
+  static constexpr size_t smem_bytes = 1024 + STAGES * (size_t)stage_bytes + 256;
+  static constexpr uint32_t idesc = idesc_for(BN_);
+};
+
+template <int BN_>
 __global__ void __launch_bounds__(THREADS, 1)
     k_apply_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int nt, int nx,
                int accumulate, double* __restrict__ Y) {
+  using TT = TcTile<BN_>;
+  constexpr int BN = BN_;
+  constexpr uint32_t B_BYTES = TT::b_bytes, STAGE_BYTES = TT::stage_bytes, TMEM_COLS = TT::tmem_cols;
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
   unsigned char* smA = reinterpret_cast<unsigned char*>(base);
@@ -202,7 +219,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint64_t da = smem_desc(smA + s * A_BYTES);
       const uint64_t db = smem_desc(smB + s * B_BYTES);
       for (int k = 0; k < BK / 16; ++k)
-        umma_bf16(tmem, da + (uint64_t)((k * 32) >> 4), db + (uint64_t)((k * 32) >> 4), (it > 0 || k > 0) ? 1u : 0u);
+        umma_bf16(tmem, da + (uint64_t)((k * 32) >> 4), db + (uint64_t)((k * 32) >> 4), (it > 0 || k > 0) ? 1u : 0u,
+                  TT::idesc);
       umma_commit(&empty[s]);
     }
     umma_commit(accum);   // completes when every MMA issued above has completed
@@ -448,14 +466,14 @@ bool apply_tc_supported(int nt, int nx, int n_rhs) {
 
 namespace {
 cudaError_t make_maps(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, CUtensorMap* mA,
-                      CUtensorMap* mX) {
+                      CUtensorMap* mX, int bn) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   const cuuint64_t dimA[3] = {(cuuint64_t)nx, (cuuint64_t)nx, (cuuint64_t)nt};
   const cuuint64_t strA[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * nx * 2};
   const cuuint64_t dimX[3] = {(cuuint64_t)nx, (cuuint64_t)nt, (cuuint64_t)n_rhs};
   const cuuint64_t strX[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nt * nx * 2};
-  const cuuint32_t boxA[3] = {BK, BM, 1}, boxX[3] = {BK, BN, 1}, es[3] = {1, 1, 1};
+  const cuuint32_t boxA[3] = {BK, BM, 1}, boxX[3] = {BK, (cuuint32_t)bn, 1}, es[3] = {1, 1, 1};
   CUresult r = enc(mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(A_bf16), dimA, strA, boxA, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -471,13 +489,22 @@ cudaError_t make_maps(int nt, int nx, const void* A_bf16, int n_rhs, const void*
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
                             bool accumulate, cudaStream_t s, int chunk) {
   CUtensorMap mA, mX;
-  cudaError_t e = make_maps(nt, nx, A_bf16, n_rhs, X_bf16, &mA, &mX);
+  // plain products on more than 128 steps take 128 x 256 tiles (N = 256 MMAs:
+  // a third less shared-memory operand traffic per flop)
+  const int bn = (chunk <= 0 && nt > 128) ? 256 : BN;
+  cudaError_t e = make_maps(nt, nx, A_bf16, n_rhs, X_bf16, &mA, &mX, bn);
   if (e != cudaSuccess) return e;
-  const dim3 grid((nx + BM - 1) / BM, (nt + BN - 1) / BN, n_rhs);
-  if (chunk <= 0) {
-    e = cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  const dim3 grid((nx + BM - 1) / BM, (nt + bn - 1) / bn, n_rhs);
+  if (chunk <= 0 && bn == 256) {
+    e = cudaFuncSetAttribute(k_apply_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcTile<256>::smem_bytes);
     if (e != cudaSuccess) return e;
-    k_apply_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
+    k_apply_tc<256><<<grid, THREADS, TcTile<256>::smem_bytes, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
+  } else if (chunk <= 0) {
+    e = cudaFuncSetAttribute(k_apply_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcTile<128>::smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_apply_tc<128><<<grid, THREADS, TcTile<128>::smem_bytes, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
   } else {
     e = cudaFuncSetAttribute(k_apply_tc_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COMP_SMEM_BYTES);
     if (e != cudaSuccess) return e;
