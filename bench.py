@@ -655,11 +655,70 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the 64-problem ragged component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
+    ap.add_argument("--component", choices=["tc", "grad"], default=None,
+                    help="run one kernel family alone on a small case (for ncu captures) and print its timing")
+    ap.add_argument("--size", type=int, default=256, help="N_x = N_t of --component's case")
+    ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --component tc")
     args = ap.parse_args()
     globals()["WORKLOAD"] = args.workload
+    if args.component:
+        return run_component(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
+
+
+def run_component(args):
+    """One kernel family on a small case, for profiling: 'tc' = the BF16
+    tensor-core product (plain and compensated) of a unit-square V with
+    --rhs right-hand sides; 'grad' = the gradient kernels on a 16-corner star
+    with N_x = N_t = --size.  Warm-up, then timed calls with CUDA events."""
+    import torch
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = P.Context(0, stream)
+    n = args.size
+    out = {"component": args.component, "size": n}
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    if args.component == "tc":
+        mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
+        Vb = P.to_bf16(ctx, P.assemble(ctx, mesh, "V"))
+        g = torch.Generator(device="cpu").manual_seed(3)
+        xb = torch.randn((args.rhs, n, n), generator=g, dtype=torch.float64).to(dev).to(torch.bfloat16)
+        y = torch.empty((args.rhs, n, n), dtype=torch.float64, device=dev)
+        flops = 2.0 * n * n * n * (n + 1) / 2 * args.rhs
+        for chunk in (0, 4):
+            for _ in range(2):
+                P.apply_tc(ctx, Vb, xb, out=y, chunk=chunk)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            P.apply_tc(ctx, Vb, xb, out=y, chunk=chunk)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            out["plain" if chunk == 0 else "compensated4"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+        out["rhs"] = args.rhs
+    else:
+        S = W.subdivision_matrix(16, n // 16)
+        mesh = P.Mesh(ctx, S @ W.star_corners(16, seed=5), 1.0, n, 1.0)
+        K = P.assemble(ctx, mesh, "K")
+        g, _ = P.rhs(ctx, mesh, K, (1.5, 1.5))
+        gen = torch.Generator(device="cpu").manual_seed(5)
+        lam = torch.randn((n, n), generator=gen, dtype=torch.float64).to(dev)
+        w = torch.randn((n, n), generator=gen, dtype=torch.float64).to(dev)
+        work = P.api.grad_workspace(ctx, n, n)
+        for _ in range(2):
+            P.grad(ctx, mesh, K, (1.5, 1.5), g, w, lam, work=work)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        P.grad(ctx, mesh, K, (1.5, 1.5), g, w, lam, work=work)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out["grad_ms"] = e0.elapsed_time(e1)
+    print(json.dumps(out))
+    return 0
 
 
 if __name__ == "__main__":
