@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
 # at square256 (lags 2..65) from an ncu capture (profiles/k_tile_D_f64_lag2.md);
 # set to None whenever that kernel changes
-TRAFFIC_D2_BYTES = 1032192 + 2380800
+TRAFFIC_D2_BYTES = 1083392 + 2333952
 
 
 def _oracle_sample(n_entries, seed, rng_lags=None):
