@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
 # at square256 (lags 2..65) from an ncu capture (profiles/k_tile_D_f64_lag2.md);
 # set to None whenever that kernel changes
-TRAFFIC_D2_BYTES = 1083392 + 2333952
+TRAFFIC_D2_BYTES = 726272 + 96000   # DRAM bytes of one 64-lag launch (lags 32..95, ncu)
 
 
 def _oracle_sample(n_entries, seed, rng_lags=None):
@@ -472,17 +472,19 @@ def run_ours(args):
     ms_apply = a0.elapsed_time(a1) / reps
     apply_flops = 2.0 * nx * nx * nt * (nt + 1) / 2
     apply_bytes = nt * nx * nx * 8 + 2 * nt * nx * 8
-    # dominant kernel: the FP64 D tile kernel at lags >= 2 (chunks of 64 lags
-    # per launch), timed alone with CUDA events on the launching stream
-    n_lag2_launches = max(1, (nt - 2 + 63) // 64)
+    # dominant kernel: the FP64 D tile kernel at lags >= 2 (two lags per CTA,
+    # launches split at the space-order changes and every 64 lags), timed
+    # alone with CUDA events on the launching stream; launches counted
     l2 = []
     for _ in range(2):
         c0, c1 = ev(), ev()
         flush.zero_()
+        n_before = lib.stbem_launch_count()
         c0.record(stream)
         P.assemble_lags(ctx, mesh, "D", 2, nt, out=D)
         c1.record(stream)
         torch.cuda.synchronize(dev)
+        n_lag2_launches = max(1, lib.stbem_launch_count() - n_before)
         l2.append(c0.elapsed_time(c1))
     d2_ms_launch = min(l2) / n_lag2_launches
     d2_flops_launch = d_lag2_flops(nx, nt) / n_lag2_launches
@@ -590,7 +592,7 @@ def run_ours(args):
             "grad": grad,
             "ragged": ragged,
         },
-        "roofline": {"kernel": "k_tile<D, f64> lags >= 2", "bound": "alu",
+        "roofline": {"kernel": "k_tile_ml<D, f64, 2 lags> lags >= 2", "bound": "alu",
                      "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_D2_BYTES,
                      "launch_ms": d2_ms_launch, "flops_per_launch": d2_flops_launch,

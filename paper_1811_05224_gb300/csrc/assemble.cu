@@ -28,6 +28,8 @@
 // (STBEM_F32: FP32 arithmetic everywhere except the deferred FP64 pairs).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "assemble.h"
 #include "pairs.cuh"
 #include "rule.cuh"
@@ -223,6 +225,182 @@ __device__ void tensor_moments_impl(const Piece& A, const Piece& B, int d, int n
   }
 }
 
+// ---- several consecutive lags at once (lags >= 2) ----------------------------------
+// Values of D2_d F (K = kV or kKq) for the T.L lags d0.. of the table at one c.
+// The closed form applies to a prefix of the lags (its switch c / (d ht) > d/2
+// moves to larger c as d grows); F at the shared times is evaluated once.  The
+// Peano lags use intervals lc .. L, each evaluated once: its left-role sum
+// serves lag i, its right-role sum lag i - 1.
+template <typename R, int K>
+__device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (&out)[kMaxLagsML]) {
+  const int L = T.L;
+  const R four_pi = (R)kFourPi;
+  int lc = 0;
+  while (lc < L && c * T.inv_dht[lc] > (R)0.5 * (R)(T.d0 + lc)) ++lc;
+  if (lc > 0) {
+    R F[kMaxLagsML + 2];
+#pragma unroll
+    for (int j = 0; j < kMaxLagsML + 2; ++j) {
+      if (j >= lc + 2) break;
+      R a, b;
+      e12(c * T.inv_s[j], &a, &b);
+      F[j] = K == kV ? T.s[j] / four_pi * (a - b) : alpha / ((R)2 * four_pi * c) * T.s[j] * b;
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxLagsML; ++l)
+      if (l < lc) out[l] = (F[l + 2] - (R)2 * F[l + 1]) + F[l];
+  }
+  if (lc < L) {
+    const R* lw = K == kV ? T.lv : T.lk;
+    const R* rw = K == kV ? T.rv : T.rk;
+    R carry = (R)0;
+    for (int i = lc; i <= L; ++i) {
+      R sl = (R)0, sr = (R)0;
+      const int g0 = T.off[i], g1 = T.off[i + 1];
+      if (i < L && i > lc) {
+        for (int g = g0; g < g1; ++g) {
+          const R e = exp_neg(c * T.sig[g]);
+          sl = fma(lw[g], e, sl);
+          sr = fma(rw[g], e, sr);
+        }
+      } else if (i < L) {
+        for (int g = g0; g < g1; ++g) sl = fma(lw[g], exp_neg(c * T.sig[g]), sl);
+      } else {
+        for (int g = g0; g < g1; ++g) sr = fma(rw[g], exp_neg(c * T.sig[g]), sr);
+      }
+#pragma unroll
+      for (int l = 0; l < kMaxLagsML; ++l)
+        if (l == i - 1 && i > lc) out[l] = carry + sr;
+      carry = sl;
+    }
+  }
+}
+
+// D_h's two kernels (F_V and F_1) for the lags of the table at one c.
+template <typename R>
+__device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R (&ov)[kMaxLagsML],
+                                            R (&o1)[kMaxLagsML]) {
+  const int L = T.L;
+  const R four_pi = (R)kFourPi;
+  int lc = 0;
+  while (lc < L && c * T.inv_dht[lc] > (R)0.5 * (R)(T.d0 + lc)) ++lc;
+  if (lc > 0) {
+    R Fv[kMaxLagsML + 2], F1[kMaxLagsML + 2];
+#pragma unroll
+    for (int j = 0; j < kMaxLagsML + 2; ++j) {
+      if (j >= lc + 2) break;
+      R a, b;
+      e12(c * T.inv_s[j], &a, &b);
+      Fv[j] = T.s[j] / four_pi * (a - b);
+      F1[j] = alpha / four_pi * a;
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxLagsML; ++l)
+      if (l < lc) {
+        ov[l] = (Fv[l + 2] - (R)2 * Fv[l + 1]) + Fv[l];
+        o1[l] = (F1[l + 2] - (R)2 * F1[l + 1]) + F1[l];
+      }
+  }
+  if (lc < L) {
+    R cv = (R)0, c1 = (R)0;
+    for (int i = lc; i <= L; ++i) {
+      R slv = (R)0, srv = (R)0, sl1 = (R)0, sr1 = (R)0;
+      const int g0 = T.off[i], g1 = T.off[i + 1];
+      const bool wl = i < L, wr = i > lc;
+      for (int g = g0; g < g1; ++g) {
+        const R e = exp_neg(c * T.sig[g]);
+        if (wl) {
+          slv = fma(T.lv[g], e, slv);
+          sl1 = fma(e, fma(T.l3[g], c, -T.l2[g]), sl1);
+        }
+        if (wr) {
+          srv = fma(T.rv[g], e, srv);
+          sr1 = fma(e, fma(T.r3[g], c, -T.r2[g]), sr1);
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kMaxLagsML; ++l)
+        if (l == i - 1 && wr) {
+          ov[l] = cv + srv;
+          o1[l] = c1 + sr1;
+        }
+      cv = slv;
+      c1 = sl1;
+    }
+  }
+}
+
+// Moments of one piece pair for the lags of the table, tensor Gauss rule of
+// order n; mom[l * ls + q] for lag l and moment q (as tensor_moments_impl).
+template <typename R, int OP>
+__device__ void tensor_moments_ml(const Piece& A, const Piece& B, int n, double alpha, const MLNodes<R>& T,
+                                  double* mom, int ls) {
+  const int o = gauss_offset(n);
+  const R eax = (R)(A.x1 - A.x0), eay = (R)(A.y1 - A.y0);
+  const R ebx = (R)(B.x1 - B.x0), eby = (R)(B.y1 - B.y0);
+  const R abx = (R)(A.x0 - B.x0), aby = (R)(A.y0 - B.y0);
+  const R qab = (R)((A.x0 - B.x0) * B.nx + (A.y0 - B.y0) * B.ny);
+  const R qea = (R)((A.x1 - A.x0) * B.nx + (A.y1 - A.y0) * B.ny);
+  const R qa = (R)(0.25 * alpha);
+  const R al = (R)alpha;
+  constexpr int NM = NMom<OP>::n;
+  R acc[kMaxLagsML][NM];
+#pragma unroll
+  for (int l = 0; l < kMaxLagsML; ++l)
+#pragma unroll
+    for (int q = 0; q < NM; ++q) acc[l][q] = (R)0;
+  for (int a = 0; a < n; ++a) {
+    const R xi = gxr<R>(o + a);
+    const R wa = gwr<R>(o + a);
+    for (int b = 0; b < n; ++b) {
+      const R eta = gxr<R>(o + b);
+      const R w = wa * gwr<R>(o + b);
+      const R dx = (abx + xi * eax) - eta * ebx;
+      const R dy = (aby + xi * eay) - eta * eby;
+      const R c = qa * (dx * dx + dy * dy);
+      if constexpr (OP == STBEM_OP_V) {
+        R k[kMaxLagsML];
+        ml_kernel<R, kV>(c, al, T, k);
+#pragma unroll
+        for (int l = 0; l < kMaxLagsML; ++l)
+          if (l < T.L) acc[l][0] += w * k[l];
+      } else if constexpr (OP == STBEM_OP_K) {
+        R k[kMaxLagsML];
+        ml_kernel<R, kKq>(c, al, T, k);
+        const R wq = w * (qab + xi * qea);
+#pragma unroll
+        for (int l = 0; l < kMaxLagsML; ++l)
+          if (l < T.L) {
+            const R wk = wq * k[l];
+            acc[l][0] += wk * ((R)1 - eta);
+            acc[l][1] += wk * eta;
+          }
+      } else {
+        R kv[kMaxLagsML], k1[kMaxLagsML];
+        ml_kernel_D<R>(c, al, T, kv, k1);
+        const R b11 = ((R)1 - xi) * ((R)1 - eta), b10 = ((R)1 - xi) * eta;
+        const R b01 = xi * ((R)1 - eta), b00 = xi * eta;
+#pragma unroll
+        for (int l = 0; l < kMaxLagsML; ++l)
+          if (l < T.L) {
+            acc[l][0] += w * kv[l];
+            const R wk = w * k1[l];
+            acc[l][1] += wk * b11;
+            acc[l][2] += wk * b10;
+            acc[l][3] += wk * b01;
+            acc[l][4] += wk * b00;
+          }
+      }
+    }
+  }
+  const double LL = A.len * B.len;
+#pragma unroll
+  for (int l = 0; l < kMaxLagsML; ++l)
+    if (l < T.L)
+#pragma unroll
+      for (int q = 0; q < NM; ++q) mom[l * ls + q] = (double)acc[l][q] * LL;
+}
+
 // ---- moments of one singular pair, FP64 (lags 0 and 1) ------------------------------
 // One CTA per identical or vertex-sharing pair at lag 0 or 1; the rule's
 // points are strided over the threads and reduced in a fixed tree, so the
@@ -313,6 +491,33 @@ __global__ void __launch_bounds__(128) k_lag2_V(DevMesh M, int d_begin, T* __res
   if (i != j) out[base + (size_t)j * N + i] = (T)m[0];
 }
 
+// V, lags >= 2, L consecutive lags per block row (one table per CTA).
+template <typename R, typename T>
+__global__ void __launch_bounds__(128) k_lag2_V_ml(DevMesh M, int d_begin, int d_end, int L, T* __restrict__ out) {
+  __shared__ MLNodes<R> TN;
+  const int N = M.N;
+  const int d0 = d_begin + blockIdx.y * L;
+  const int nl = min(L, d_end - d0);
+  build_ml_nodes<R>(TN, d0, nl, M.ht, M.alpha);
+  __syncthreads();
+  const long long npair = (long long)N * (N + 1) / 2;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const double B2 = 2.0 * N + 1.0;
+  int i = (int)floor((B2 - sqrt(B2 * B2 - 8.0 * (double)p)) * 0.5);
+  auto S = [N](long long r) { return r * N - r * (r - 1) / 2; };
+  while (i > 0 && S(i) > p) --i;
+  while (S(i + 1) <= p) ++i;
+  const int j = i + (int)(p - S(i));
+  double m[kMaxLagsML];
+  tensor_moments_ml<R, STBEM_OP_V>(seg_piece(M, i), seg_piece(M, j), space_order(d0), M.alpha, TN, m, 1);
+  for (int l = 0; l < nl; ++l) {
+    const size_t base = (size_t)(d0 + l) * N * N;
+    out[base + (size_t)i * N + j] = (T)m[l];
+    if (i != j) out[base + (size_t)j * N + i] = (T)m[l];
+  }
+}
+
 // ---- tile geometry -----------------------------------------------------------------
 constexpr int kTileThreads = 256;
 constexpr int kT = 16;                 // entries per tile side (V, D); K rows
@@ -390,6 +595,60 @@ __host__ __device__ __forceinline__ int tiles_per_lag(int N) {
   return nT * (nT + 1) / 2;
 }
 
+// Phase 3 of a tile: entries of one lag block from its pair moments.
+template <int OP, typename T>
+__device__ __forceinline__ void tile_entries(const DevMesh& M, int rt, int ct, int r0, int c0,
+                                             const double* __restrict__ mom, size_t base, T* __restrict__ out) {
+  constexpr int NM = Tile<OP>::nm;
+  const int N = M.N;
+  const int tid = threadIdx.x;
+  if (OP == STBEM_OP_V) {
+    const int i = r0 + tid / kT, j = c0 + tid % kT;
+    if (i < N && j < N) {
+      const T v = (T)mom[tid];
+      out[base + (size_t)i * N + j] = v;
+      if (rt != ct) out[base + (size_t)j * N + i] = v;
+    }
+  } else if (OP == STBEM_OP_K) {
+    if (tid < kT * kKP) {
+      const int si = tid / kKP, sp = tid % kKP;
+      const int i = r0 + si, p = c0 + sp;
+      if (i < N && p < N) {
+        const double val = mom[(size_t)(si * kKJ + sp + 1) * NM + 0] + mom[(size_t)(si * kKJ + sp) * NM + 1];
+        out[base + (size_t)i * N + p] = (T)val;
+      }
+    }
+  } else {
+    const int s = tid / kT, t = tid % kT;
+    const int l = r0 + s, k = c0 + t;
+    // evaluate with the smaller index first; on a diagonal tile both ranges coincide
+    const int lo = l < k ? l : k, hi = l < k ? k : l;
+    const int so = lo - r0, to = hi - c0;
+    if (l < N && k < N && so >= 0 && to >= 0 && so < kT && to < kT) {
+      double val = 0.0;
+      for (int ia = 0; ia < 4; ++ia) {
+        const int qa = 4 * lo + ia;
+        const double ca = M.dcurl[qa], a0 = M.dv0[qa], a1 = M.dv1[qa];
+        const int u = 2 * so + ia;
+        const int ga = M.dpiece[qa];
+        const double nax = M.hnx[ga], nay = M.hny[ga];
+        for (int ib = 0; ib < 4; ++ib) {
+          const int qb = 4 * hi + ib;
+          const double cb = M.dcurl[qb], b0 = M.dv0[qb], b1 = M.dv1[qb];
+          const int v = 2 * to + ib;
+          const int gb = M.dpiece[qb];
+          const double nn = nax * M.hnx[gb] + nay * M.hny[gb];
+          const double* mm = mom + (size_t)(u * kDP + v) * NM;
+          const double I1 = a0 * (b0 * mm[1] + b1 * mm[2]) + a1 * (b0 * mm[3] + b1 * mm[4]);
+          val += ca * cb * mm[0] + nn * I1;
+        }
+      }
+      out[base + (size_t)l * N + k] = (T)val;
+      if (rt != ct) out[base + (size_t)k * N + l] = (T)val;
+    }
+  }
+}
+
 // One tile of one lag block: all threads of the CTA take part.
 template <int OP, typename R, typename T, bool LAG01>
 __device__ void tile_body(const DevMesh& M, int d, int tile, const double* __restrict__ sing, T* __restrict__ out,
@@ -440,52 +699,106 @@ __device__ void tile_body(const DevMesh& M, int d, int tile, const double* __res
   }
   __syncthreads();
   // phase 3: entries
-  const size_t base = (size_t)d * N * N;
-  if (OP == STBEM_OP_V) {
-    const int i = r0 + tid / kT, j = c0 + tid % kT;
-    if (i < N && j < N) {
-      const T v = (T)mom[tid];
-      out[base + (size_t)i * N + j] = v;
-      if (rt != ct) out[base + (size_t)j * N + i] = v;
-    }
-  } else if (OP == STBEM_OP_K) {
-    if (tid < kT * kKP) {
-      const int si = tid / kKP, sp = tid % kKP;
-      const int i = r0 + si, p = c0 + sp;
-      if (i < N && p < N) {
-        const double val = mom[(size_t)(si * kKJ + sp + 1) * NM + 0] + mom[(size_t)(si * kKJ + sp) * NM + 1];
-        out[base + (size_t)i * N + p] = (T)val;
-      }
-    }
+  tile_entries<OP, T>(M, rt, ct, r0, c0, mom, (size_t)d * N * N, out);
+}
+
+// L consecutive lags >= 2 of one tile: phase 1 integrates every pair for all
+// L lags at once (shared Peano intervals and closed-form times), phase 3
+// gathers each lag's entries.  Shared memory: L moment arrays + the table.
+template <int OP, int LM>
+struct TileML {
+  static constexpr size_t mom_bytes = (((size_t)LM * Tile<OP>::pairs * Tile<OP>::nm * sizeof(double) + 15) / 16) * 16;
+};
+template <int OP, typename R, int LM>
+constexpr size_t tile_ml_smem_bytes() {
+  return TileML<OP, LM>::mom_bytes + sizeof(MLNodes<R>);
+}
+
+template <int OP, typename R, typename T, int LM>
+__device__ void tile_body_ml(const DevMesh& M, int d0, int nl, int tile, T* __restrict__ out,
+                             unsigned char* smem_raw) {
+  constexpr int P = Tile<OP>::pairs, NM = Tile<OP>::nm;
+  double* mom = reinterpret_cast<double*>(smem_raw);
+  MLNodes<R>* TN = reinterpret_cast<MLNodes<R>*>(smem_raw + TileML<OP, LM>::mom_bytes);
+  const int N = M.N;
+  int rt, ct;
+  if (OP == STBEM_OP_K) {
+    const int nP = (N + kKP - 1) / kKP;
+    rt = tile / nP;
+    ct = tile % nP;
   } else {
-    const int s = tid / kT, t = tid % kT;
-    const int l = r0 + s, k = c0 + t;
-    // evaluate with the smaller index first; on a diagonal tile both ranges coincide
-    const int lo = l < k ? l : k, hi = l < k ? k : l;
-    const int so = lo - r0, to = hi - c0;
-    if (l < N && k < N && so >= 0 && to >= 0 && so < kT && to < kT) {
-      double val = 0.0;
-      for (int ia = 0; ia < 4; ++ia) {
-        const int qa = 4 * lo + ia;
-        const double ca = M.dcurl[qa], a0 = M.dv0[qa], a1 = M.dv1[qa];
-        const int u = 2 * so + ia;
-        const int ga = M.dpiece[qa];
-        const double nax = M.hnx[ga], nay = M.hny[ga];
-        for (int ib = 0; ib < 4; ++ib) {
-          const int qb = 4 * hi + ib;
-          const double cb = M.dcurl[qb], b0 = M.dv0[qb], b1 = M.dv1[qb];
-          const int v = 2 * to + ib;
-          const int gb = M.dpiece[qb];
-          const double nn = nax * M.hnx[gb] + nay * M.hny[gb];
-          const double* mm = mom + (size_t)(u * kDP + v) * NM;
-          const double I1 = a0 * (b0 * mm[1] + b1 * mm[2]) + a1 * (b0 * mm[3] + b1 * mm[4]);
-          val += ca * cb * mm[0] + nn * I1;
-        }
-      }
-      out[base + (size_t)l * N + k] = (T)val;
-      if (rt != ct) out[base + (size_t)k * N + l] = (T)val;
-    }
+    upper_tile(tile, (N + kT - 1) / kT, &rt, &ct);
   }
+  const int r0 = rt * kT, c0 = ct * (OP == STBEM_OP_K ? kKP : kT);
+  build_ml_nodes<R>(*TN, d0, nl, M.ht, M.alpha);
+  __syncthreads();
+  const int n = space_order(d0);
+  for (int p = threadIdx.x; p < P; p += kTileThreads) {
+    Piece A, B;
+    int ia, ib, ring;
+    double* m = mom + (size_t)p * NM;
+    if (!tile_pair<OP>(M, r0, c0, p, &A, &B, &ia, &ib, &ring)) {
+      for (int l = 0; l < nl; ++l)
+        for (int q = 0; q < NM; ++q) m[(size_t)l * P * NM + q] = 0.0;
+      continue;
+    }
+    tensor_moments_ml<R, OP>(A, B, n, M.alpha, *TN, m, P * NM);
+  }
+  __syncthreads();
+  for (int l = 0; l < nl; ++l)
+    tile_entries<OP, T>(M, rt, ct, r0, c0, mom + (size_t)l * P * NM, (size_t)(d0 + l) * N * N, out);
+}
+
+template <int OP, typename R, typename T, int LM>
+__global__ void __launch_bounds__(kTileThreads) k_tile_ml(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int d0 = d_begin + blockIdx.y * LM;
+  tile_body_ml<OP, R, T, LM>(M, d0, min(LM, d_end - d0), blockIdx.x, out, smem_raw);
+}
+
+// Lag groups of one operator on n_t steps: lags 0 and 1 one at a time, then
+// runs of up to LM consecutive lags that never cross the space-order changes
+// at d = 8 and 32 (the same runs as the single-problem launches).
+// (FP32 D keeps one lag per tile: its exponentials are cheap MUFU operations,
+// so sharing intervals saves little and the doubled moment storage costs
+// occupancy.)
+template <int OP, typename R>
+__host__ __device__ constexpr int lag_group_len() {
+  return OP == STBEM_OP_D ? (sizeof(R) == 4 ? 1 : 2) : kMaxLagsML;
+}
+
+__host__ __device__ inline int lag_groups(int nt, int LM) {
+  int g = nt < 2 ? nt : 2;
+  const int seg[4] = {2, 8, 32, 1 << 30};
+  for (int k = 0; k < 3; ++k) {
+    const int lo = seg[k], hi = nt < seg[k + 1] ? nt : seg[k + 1];
+    if (hi > lo) g += (hi - lo + LM - 1) / LM;
+  }
+  return g;
+}
+
+__host__ __device__ inline void lag_group(int nt, int LM, int g, int* d0, int* nl) {
+  const int l01 = nt < 2 ? nt : 2;
+  if (g < l01) {
+    *d0 = g;
+    *nl = 1;
+    return;
+  }
+  g -= l01;
+  const int seg[4] = {2, 8, 32, 1 << 30};
+  for (int k = 0; k < 3; ++k) {
+    const int lo = seg[k], hi = nt < seg[k + 1] ? nt : seg[k + 1];
+    if (hi <= lo) continue;
+    const int n = (hi - lo + LM - 1) / LM;
+    if (g < n) {
+      *d0 = lo + g * LM;
+      *nl = (hi - *d0) < LM ? (hi - *d0) : LM;
+      return;
+    }
+    g -= n;
+  }
+  *d0 = 0;
+  *nl = 0;
 }
 
 template <int OP, typename R, typename T, bool LAG01>
@@ -553,10 +866,14 @@ __global__ void __launch_bounds__(kTileThreads) k_ragged_tile(const RaggedProble
     const RaggedProblem& pr = probs[order[s]];
     const long long local = item - prefix[s];
     const int nt_tiles = tiles_per_lag<OP>(pr.M.N);
-    const int d = (int)(local / nt_tiles), t = (int)(local % nt_tiles);
+    const int g = (int)(local / nt_tiles), t = (int)(local % nt_tiles);
+    int d0, nl;
+    constexpr int LM = lag_group_len<OP, R>();
+    lag_group(pr.M.n_t, LM, g, &d0, &nl);
     T* o = out + pr.op_off;
-    if (d < 2) tile_body<OP, R, T, true>(pr.M, d, t, pr.M.sing, o, smem_raw);
-    else tile_body<OP, R, T, false>(pr.M, d, t, pr.M.sing, o, smem_raw);
+    if (d0 < 2) tile_body<OP, R, T, true>(pr.M, d0, t, pr.M.sing, o, smem_raw);
+    else if (LM == 1) tile_body<OP, R, T, false>(pr.M, d0, t, pr.M.sing, o, smem_raw);
+    else tile_body_ml<OP, R, T, LM>(pr.M, d0, nl, t, o, smem_raw);
     __syncthreads();
   }
 }
@@ -602,20 +919,44 @@ static cudaError_t launch_op(const DevMesh& M, int lag_begin, int lag_end, T* ou
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // lags >= 2 in chunks of at most 64
-  for (int d0 = lag_begin > 2 ? lag_begin : 2; d0 < lag_end; d0 += 64) {
-    const int d1 = d0 + 64 < lag_end ? d0 + 64 : lag_end;
-    if (OP == STBEM_OP_V) {
-      const long long npair = (long long)N * (N + 1) / 2;
-      k_lag2_V<R, T><<<dim3((unsigned)((npair + 127) / 128), d1 - d0), 128, 0, s>>>(M, d0, out);
-    } else {
-      k_tile<OP, R, T, false><<<dim3(tiles, d1 - d0), kTileThreads, smem, s>>>(M, d0, M.sing, out);
-    }
-    count_launches(1);
-    e = cudaGetLastError();
+  // lags >= 2: L consecutive lags per CTA (one space order per launch, so
+  // launches split at the order changes d = 8 and 32), at most 64 lags each
+  constexpr int LM = lag_group_len<OP, R>();
+  const size_t smem_ml = tile_ml_smem_bytes<OP, R, LM>();
+  if (OP != STBEM_OP_V && LM > 1) {
+    e = cudaFuncSetAttribute(k_tile_ml<OP, R, T, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ml);
     if (e != cudaSuccess) return e;
   }
+  const int seg[4] = {2, 8, 32, 1 << 30};
+  for (int sg = 0; sg < 3; ++sg) {
+    const int lo = std::max(std::max(lag_begin, 2), seg[sg]), hi = std::min(lag_end, seg[sg + 1]);
+    for (int d0 = lo; d0 < hi; d0 += 64) {
+      const int d1 = std::min(d0 + 64, hi);
+      const int chunks = (d1 - d0 + LM - 1) / LM;
+      if (OP == STBEM_OP_V) {
+        const long long npair = (long long)N * (N + 1) / 2;
+        k_lag2_V_ml<R, T><<<dim3((unsigned)((npair + 127) / 128), chunks), 128, 0, s>>>(M, d0, d1, LM, out);
+      } else if (LM == 1) {
+        k_tile<OP, R, T, false><<<dim3(tiles, d1 - d0), kTileThreads, smem, s>>>(M, d0, M.sing, out);
+      } else {
+        k_tile_ml<OP, R, T, LM><<<dim3(tiles, chunks), kTileThreads, smem_ml, s>>>(M, d0, d1, out);
+      }
+      count_launches(1);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
   return cudaSuccess;
+}
+
+int assembly_lag_groups(int op, int prec, int nt) {
+  if (prec == STBEM_F64)
+    return lag_groups(nt, op == STBEM_OP_V   ? lag_group_len<STBEM_OP_V, double>()
+                          : op == STBEM_OP_K ? lag_group_len<STBEM_OP_K, double>()
+                                             : lag_group_len<STBEM_OP_D, double>());
+  return lag_groups(nt, op == STBEM_OP_V   ? lag_group_len<STBEM_OP_V, float>()
+                        : op == STBEM_OP_K ? lag_group_len<STBEM_OP_K, float>()
+                                           : lag_group_len<STBEM_OP_D, float>());
 }
 
 int assembly_tiles_per_lag(int op, int N) {
@@ -637,7 +978,7 @@ static cudaError_t ragged_op(const RaggedProblem* probs, int P, RaggedItems si, 
   k_ragged_singular<OP><<<sms * (occ > 0 ? occ : 1), kSingThreads, 0, s>>>(probs, si.order, si.prefix, P, counters);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = tile_smem_bytes<OP, R>();
+  const size_t smem = std::max(tile_smem_bytes<OP, R>(), tile_ml_smem_bytes<OP, R, lag_group_len<OP, R>()>());
   e = cudaFuncSetAttribute(k_ragged_tile<OP, R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_tile<OP, R, T>, kTileThreads, smem);

@@ -37,10 +37,14 @@ struct RaggedItems {
 void build_rule_tables(RuleTables* t);
 // tiles of one lag block (host copy of the assembly's tiling)
 int assembly_tiles_per_lag(int op, int N);
+// lag groups of op on n_t steps (lags 0, 1 singly, then runs of consecutive
+// lags assembled together); the ragged tile items are groups x tiles
+int assembly_lag_groups(int op, int prec, int nt);
 // All lag blocks of op for every problem of a ragged batch: one persistent
 // launch for the identical / vertex-sharing pairs at lags 0 and 1 (items:
 // problem x lag x pair slot) and one for the tiles (problem x lag x tile).
 // counters: two device words (reset here).
+// tile_items must have been counted with assembly_lag_groups(op, prec, n_t).
 cudaError_t ragged_assemble_launch(int op, int prec, const RaggedProblem* probs, int P, RaggedItems sing_items,
                                    RaggedItems tile_items, unsigned long long* counters, void* out,
                                    cudaStream_t s);

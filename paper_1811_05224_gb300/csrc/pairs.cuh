@@ -157,4 +157,64 @@ static __device__ void build_lag_nodes(LagNodes<R>& L, int d, double ht, double 
   }
 }
 
+// ---- time-node tables for L consecutive lags (lags >= 2) ----------------------------
+// The Peano form of lag d integrates over the time intervals d - 1 (hat tau)
+// and d (hat 1 - tau), so lags d0 .. d0 + L - 1 use the L + 1 intervals
+// d0 - 1 .. d0 + L - 1 and each interior interval serves two lags; the closed
+// form of those lags needs F at the L + 2 times (d0 - 1 + j) ht.  One table
+// per CTA holds every node of those intervals with its weights for the left
+// role (hat tau, the interval is lag k + 1's left) and the right role
+// (hat 1 - tau, lag k's right).  Factors as in LagNodes.
+constexpr int kMaxLagsML = 4;
+constexpr int kMaxNodesML = 16 + 8 * kMaxLagsML;
+template <typename R>
+struct MLNodes {
+  int d0, L;
+  int off[kMaxLagsML + 2];            // interval i = 0..L starts at off[i]; off[L + 1] = total
+  R inv_dht[kMaxLagsML];              // 1 / (d ht) of each lag (closed / Peano switch)
+  R s[kMaxLagsML + 2], inv_s[kMaxLagsML + 2];   // (d0 - 1 + j) ht, j = 0..L+1
+  R sig[kMaxNodesML];
+  R lv[kMaxNodesML], rv[kMaxNodesML], lk[kMaxNodesML], rk[kMaxNodesML];
+  R l3[kMaxNodesML], r3[kMaxNodesML], l2[kMaxNodesML], r2[kMaxNodesML];
+};
+
+template <typename R>
+static __device__ void build_ml_nodes(MLNodes<R>& T, int d0, int L, double ht, double alpha) {
+  int off[kMaxLagsML + 2];
+  off[0] = 0;
+  for (int i = 0; i <= L; ++i) off[i + 1] = off[i] + peano_order(d0 - 1 + i);
+  const int total = off[L + 1];
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    int i = 0;
+    while (off[i + 1] <= g) ++i;
+    const int k = d0 - 1 + i, n = peano_order(k), o = gauss_offset(n);
+    const double t = c_tab.gx[o + g - off[i]], w = c_tab.gw[o + g - off[i]];
+    const double sv = ((double)k + t) * ht;
+    const double sig = 1.0 / sv;
+    const double base = ht * ht * w;
+    const double fv = base * sig / kFourPi, fk = base * alpha * sig * sig / (2.0 * kFourPi);
+    const double f3 = base * alpha * sig * sig * sig / kFourPi, f2 = base * alpha * sig * sig / kFourPi;
+    T.sig[g] = (R)sig;
+    T.lv[g] = (R)(fv * t);
+    T.rv[g] = (R)(fv * (1.0 - t));
+    T.lk[g] = (R)(fk * t);
+    T.rk[g] = (R)(fk * (1.0 - t));
+    T.l3[g] = (R)(f3 * t);
+    T.r3[g] = (R)(f3 * (1.0 - t));
+    T.l2[g] = (R)(f2 * t);
+    T.r2[g] = (R)(f2 * (1.0 - t));
+  }
+  if (threadIdx.x == 0) {
+    T.d0 = d0;
+    T.L = L;
+    for (int i = 0; i <= L + 1; ++i) T.off[i] = off[i];
+    for (int l = 0; l < L; ++l) T.inv_dht[l] = (R)(1.0 / ((double)(d0 + l) * ht));
+    for (int j = 0; j <= L + 1; ++j) {
+      const double sj = (double)(d0 - 1 + j) * ht;
+      T.s[j] = (R)sj;
+      T.inv_s[j] = (R)(1.0 / sj);
+    }
+  }
+}
+
 }  // namespace stbem

@@ -43,7 +43,7 @@ struct stbem_ragged {
   stbem::RaggedProblem* d_probs = nullptr;
   int* d_order = nullptr;
   long long* d_sing_prefix = nullptr;           // 3 ops x (P + 1)
-  long long* d_tile_prefix = nullptr;           // 3 ops x (P + 1)
+  long long* d_tile_prefix = nullptr;           // 2 precisions x 3 ops x (P + 1)
   long long* d_vprefix = nullptr;               // P + 1, natural order
   unsigned long long* d_counters = nullptr;     // 4 words
   // products
@@ -179,15 +179,19 @@ int stbem_ragged_create(stbem_ctx* ctx, int n, const stbem_problem* probs, stbem
   });
   std::vector<stbem::RaggedProblem> hp(n);
   for (int p = 0; p < n; ++p) hp[p] = {R->meshes[p]->dev, R->op_off[p], R->vec_off[p], R->mass_off[p]};
-  std::vector<long long> sp(3 * (n + 1), 0), tp(3 * (n + 1), 0), vp(n + 1, 0);
+  std::vector<long long> sp(3 * (n + 1), 0), tp(6 * (n + 1), 0), vp(n + 1, 0);
   for (int op = 0; op < 3; ++op)
     for (int s = 0; s < n; ++s) {
       const int p = R->order[s];
       const int Rl = op == STBEM_OP_D ? 2 * R->nx[p] : R->nx[p];
       const int l01 = R->nt[p] < 2 ? R->nt[p] : 2;
       sp[op * (n + 1) + s + 1] = sp[op * (n + 1) + s] + (long long)l01 * 3 * Rl;
-      tp[op * (n + 1) + s + 1] =
-          tp[op * (n + 1) + s] + (long long)R->nt[p] * stbem::assembly_tiles_per_lag(op, R->nx[p]);
+      for (int pi = 0; pi < 2; ++pi) {
+        const int prec = pi == 0 ? STBEM_F64 : STBEM_F32;
+        long long* t = tp.data() + (size_t)(pi * 3 + op) * (n + 1);
+        t[s + 1] = t[s] + (long long)stbem::assembly_lag_groups(op, prec, R->nt[p]) *
+                              stbem::assembly_tiles_per_lag(op, R->nx[p]);
+      }
     }
   for (int p = 0; p < n; ++p) vp[p + 1] = vp[p] + (long long)R->nt[p] * R->nx[p];
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -261,7 +265,8 @@ int stbem_ragged_assemble(stbem_ctx* ctx, stbem_ragged* R, int op, int prec, voi
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "ragged_assemble: set device");
   const int P = R->P;
   stbem::RaggedItems si{R->d_order, R->d_sing_prefix + (size_t)op * (P + 1)};
-  stbem::RaggedItems ti{R->d_order, R->d_tile_prefix + (size_t)op * (P + 1)};
+  const int pi = prec == STBEM_F64 ? 0 : 1;
+  stbem::RaggedItems ti{R->d_order, R->d_tile_prefix + (size_t)(pi * 3 + op) * (P + 1)};
   CUDA_TRY(ctx, stbem::ragged_assemble_launch(op, prec, R->d_probs, P, si, ti, R->d_counters, out, ctx->stream),
            "ragged_assemble");
   return STBEM_OK;

@@ -3,7 +3,8 @@ one persistent launch per step.
 
 * assembly of V, K, D for every problem against the single-problem assembly
   (FP64: same rule, summation order may differ, 1e-13 of the lag block's
-  largest entry; FP32 the same kernels with R = float);
+  largest entry; FP32: error against the FP64 blocks no worse than the
+  single-problem FP32 path's);
 * the ragged product against the oracle's Toeplitz product (FP64, within
   1e-13 of |A||x|), before and after autotuning;
 * right-hand sides and lumped masses against the single-problem calls;
@@ -56,9 +57,16 @@ def test_ragged_assembly_matches_single(ctx, batch, op):
         got = R.view_op(A, p)
         scale = ref.abs().amax(dim=(1, 2), keepdim=True)
         assert bool(((got - ref).abs() <= 1e-13 * scale + 1e-300).all()), (op, p)
-        ref32 = P.assemble(ctx, m, op, "f32")
-        got32 = R.view_op(A32, p)
-        assert bool(((got32.double() - ref32.double()).abs() <= 1e-6 * scale.float() + 1e-30).all()), (op, p)
+        # FP32: the ragged launch runs one lag per tile, the single-problem
+        # assembly several lags per tile, so their FP32 sums round
+        # differently; D and K entries are signed sums whose terms cancel, so
+        # the check is accuracy against the FP64 blocks: no worse than the
+        # single-problem FP32 path (itself parity-tested against the oracle)
+        ref32 = P.assemble(ctx, m, op, "f32").double()
+        got32 = R.view_op(A32, p).double()
+        e_single = (ref32 - ref).abs().amax(dim=(1, 2), keepdim=True)
+        e_ragged = (got32 - ref).abs().amax(dim=(1, 2), keepdim=True)
+        assert bool((e_ragged <= 2.0 * e_single + 1e-7 * scale).all()), (op, p)
 
 
 def test_ragged_apply_matches_oracle_and_tuner(ctx, batch):
