@@ -1,6 +1,6 @@
 """Generate expint_cheb.inc: Chebyshev coefficients of A(z) = e^z E1(z) and
 B(z) = e^z E2(z) on [1,2], [2,4], [4,8], [8,16]; the Horner coefficients of
-the Ein series; the constants and 2^{-j/64} table of the table-driven e^{-x}.
+the Ein series; the constants and 2^{-j/256} table of the table-driven e^{-x}.
 
 Each function is interpolated at the 26 Chebyshev points of the first kind of
 the interval, in 40-digit arithmetic (mpmath), and the coefficients of
@@ -61,17 +61,18 @@ def main():
     lines.append("constexpr int kEinTerms = %d;" % NEIN)
     lines.append("static __constant__ const double kEinCoef[%d] = {%s};" % (
         NEIN, ", ".join(mp.nstr(c, 20, min_fixed=0, max_fixed=0) for c in coef)))
-    # e^{-x} by reduction to r = x - n ln2/64: table 2^{-j/64}, j = 0..63,
-    # 64/ln2 and a two-part ln2/64 whose leading part has 36 significant bits
-    # (n ln2_hi is exact for n < 2^17, i.e. x < 1.7e3)
-    l = mp.log(2) / 64
-    hi = mp.ldexp(mp.floor(mp.ldexp(l, 36 + 6)), -(36 + 6))
+    # e^{-x} by reduction to r = x - n ln2/256: table 2^{-j/256}, j = 0..255,
+    # 256/ln2 and a two-part ln2/256 whose leading part has 34 significant
+    # bits (n ln2_hi is exact for n < 2^19, i.e. x < 1.4e3)
+    l = mp.log(2) / 256
+    e = int(mp.floor(mp.log(l, 2)))            # l = 1.xx * 2^e
+    hi = mp.ldexp(mp.floor(mp.ldexp(l, 33 - e)), -(33 - e))
     lo = l - hi
-    tab = [mp.power(2, -mp.mpf(j) / 64) for j in range(64)]
-    lines.append("constexpr double kInvLn2x64 = %s;" % mp.nstr(64 / mp.log(2), 20, min_fixed=0, max_fixed=0))
-    lines.append("constexpr double kLn2by64Hi = %s;" % mp.nstr(hi, 25, min_fixed=0, max_fixed=0))
-    lines.append("constexpr double kLn2by64Lo = %s;" % mp.nstr(lo, 20, min_fixed=0, max_fixed=0))
-    lines.append("static __constant__ const double kExp2Tab[64] = {%s};" % ", ".join(
+    tab = [mp.power(2, -mp.mpf(j) / 256) for j in range(256)]
+    lines.append("constexpr double kInvLn2x256 = %s;" % mp.nstr(256 / mp.log(2), 20, min_fixed=0, max_fixed=0))
+    lines.append("constexpr double kLn2by256Hi = %s;" % mp.nstr(hi, 25, min_fixed=0, max_fixed=0))
+    lines.append("constexpr double kLn2by256Lo = %s;" % mp.nstr(lo, 20, min_fixed=0, max_fixed=0))
+    lines.append("static __constant__ const double kExp2Tab[256] = {%s};" % ", ".join(
         mp.nstr(t, 20, min_fixed=0, max_fixed=0) for t in tab))
     lines.append("}  // namespace stbem")
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "expint_cheb.inc")

@@ -32,32 +32,39 @@ STB_HD double ein_series(double z) {
   return acc * z;
 }
 
-// e^{-x}, table-driven (Tang, ACM TOMS 15, 1989): x = n ln2/64 + r with
-// |r| <= ln2/128 (two-part ln2/64 so that n ln2_hi is exact), then
-// e^{-x} = 2^{-(n >> 6)} 2^{-(n & 63)/64} e^{-r}, the middle factor from a
-// 64-entry table and e^{-r} from its Taylor polynomial of degree 5 (remainder
-// |r|^6/720 < 3.4e-17).  Results within 2 ulp of the correctly rounded value
-// (checked on the host against the C library).  Arguments beyond 708, where
-// the result leaves the normal range, go to the library exp.
+// e^{-x}, table-driven (Tang, ACM TOMS 15, 1989): x = n ln2/256 + r with
+// |r| <= ln2/512 (two-part ln2/256 so that n ln2_hi is exact), then
+// e^{-x} = 2^{-(n >> 8)} 2^{-(n & 255)/256} e^{-r}, the middle factor from a
+// 256-entry table and e^{-r} from its Taylor polynomial of degree 4 (remainder
+// |r|^5/120 < 4e-17).  The power of two is applied by subtracting n >> 8 from
+// the exponent field (an integer operation): for x < 700 the table-times-
+// polynomial value lies in [2^-2, 2) and the result stays a normal number.
+// Results within 2 ulp of the correctly rounded value (checked on the host
+// against the C library).  Arguments from 700 on go to the library exp.
 STB_HD double exp_neg_fast(double x) {
-  if (!(x < 708.0)) return exp(-x);
-  const double nd = rint(x * kInvLn2x64);
+  if (!(x < 700.0)) return exp(-x);
+  const double nd = rint(x * kInvLn2x256);
   const int n = (int)nd;
-  double r = fma(-nd, kLn2by64Hi, x);
-  r = fma(-nd, kLn2by64Lo, r);
-  double p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
-  p = fma(r, p, -1.0 / 6.0);
+  double r = fma(-nd, kLn2by256Hi, x);
+  r = fma(-nd, kLn2by256Lo, r);
+  double p = fma(r, 1.0 / 24.0, -1.0 / 6.0);
   p = fma(r, p, 0.5);
   p = fma(r, p, -1.0);
   p = fma(r, p, 1.0);
-  const double t = kExp2Tab[n & 63] * p;
-  const long long bits = (long long)(1023 - (n >> 6)) << 52;   // 2^{-(n >> 6)}, a normal double
+  const double t = kExp2Tab[n & 255] * p;
+  long long bits;
 #ifdef __CUDA_ARCH__
-  return t * __longlong_as_double(bits);
+  bits = __double_as_longlong(t);
 #else
-  double scale;
-  std::memcpy(&scale, &bits, sizeof(scale));
-  return t * scale;
+  std::memcpy(&bits, &t, sizeof(bits));
+#endif
+  bits -= (long long)(n >> 8) << 52;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(bits);
+#else
+  double out;
+  std::memcpy(&out, &bits, sizeof(out));
+  return out;
 #endif
 }
 
