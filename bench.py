@@ -671,7 +671,7 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the 64-problem ragged component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
-    ap.add_argument("--component", choices=["tc", "grad"], default=None,
+    ap.add_argument("--component", choices=["tc", "grad", "precision"], default=None,
                     help="run one kernel family alone on a small case (for ncu captures) and print its timing")
     ap.add_argument("--size", type=int, default=256, help="N_x = N_t of --component's case")
     ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --component tc")
@@ -682,6 +682,60 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
+
+
+def run_precision(ctx, dev, stream):
+    """The precision workload at full size: L-shape (seeded lengths),
+    N_x = N_t = 1024, alpha = 0.5.  FP64 path: V, K, D in FP64 (8.6 GB each),
+    GMRES to 1e-8 preconditioned with M_h^{-1} D_h M_h^{-T} (the consistent
+    mixed mass: on this non-uniform mesh the lumped mass needs ~30x more
+    iterations).  Mixed path: V and K in FP64 (the right-hand side and the
+    refinement residual), D in FP32 with FP64 singular pairs, V rounded to
+    FP32; FP32 inner GMRES, FP64 refinement to 1e-8.  Both timed with CUDA
+    events; w compared."""
+    import torch
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    p = W.config("lshape1024")
+    m = P.Mesh(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    e = [ev() for _ in range(8)]
+    e[0].record(stream)
+    V = P.assemble(ctx, m, "V")
+    e[1].record(stream)
+    K = P.assemble(ctx, m, "K")
+    e[2].record(stream)
+    g, f = P.rhs(ctx, m, K, p.y_star)
+    L = P.lumped_mass(ctx, m)
+    del K
+    torch.cuda.empty_cache()
+    e[3].record(stream)
+    D32 = P.assemble(ctx, m, "D", "f32")
+    V32 = P.round_f32(ctx, V)
+    Minv = P.mixed_mass_inverse(ctx, m)
+    e[4].record(stream)
+    wm, im = P.solve_mixed(ctx, V, V32, f, D32, Minv, tol=1e-8, inner_tol=1e-4, max_iter=400, restart=60)
+    e[5].record(stream)
+    del V32
+    torch.cuda.empty_cache()
+    D = P.assemble(ctx, m, "D")
+    e[6].record(stream)
+    w, i64 = P.solve(ctx, V, f, D, Minv, tol=1e-8, max_iter=400, restart=60)
+    e[7].record(stream)
+    torch.cuda.synchronize(dev)
+    r = f - P.apply(ctx, V, wm)
+    out = {
+        "workload": "lshape1024: N_x = N_t = 1024, alpha = 0.5, seeded lengths (seed 3)",
+        "assembly_ms": {"V_f64": e[0].elapsed_time(e[1]), "K_f64": e[1].elapsed_time(e[2]),
+                        "D_f32_and_V_round": e[3].elapsed_time(e[4]), "D_f64": e[5].elapsed_time(e[6])},
+        "mixed_solve_ms": e[4].elapsed_time(e[5]), "mixed_inner_iterations": im["iterations"],
+        "fp64_solve_ms": e[6].elapsed_time(e[7]), "fp64_iterations": i64["iterations"],
+        "mixed_fp64_rel_residual": float(r.norm() / f.norm()),
+        "w_rel_diff_mixed_vs_fp64": float((wm - w).norm() / w.norm()),
+        "mixed_path_ms": e[3].elapsed_time(e[5]), "fp64_path_ms": e[5].elapsed_time(e[7]),
+    }
+    print(json.dumps(out))
+    return 0
 
 
 def run_component(args):
@@ -698,6 +752,8 @@ def run_component(args):
     n = args.size
     out = {"component": args.component, "size": n}
     ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    if args.component == "precision":
+        return run_precision(ctx, dev, stream)
     if args.component == "tc":
         mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
         Vb = P.to_bf16(ctx, P.assemble(ctx, mesh, "V"))

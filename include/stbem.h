@@ -185,12 +185,26 @@ int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* mesh, const double* dev_K,
  * the row sums of M_h[l,k] = <phi0_k, psi_l> (Section 2). n_x doubles. */
 int stbem_lumped_mass(stbem_ctx* ctx, const stbem_mesh* mesh, double* dev_L);
 
+/* The consistent mixed mass of Section 2, M_h[l][k] = <phi0_k, psi_l> of one
+ * time step (cyclic tridiagonal, not symmetric), inverted on the host by
+ * Gauss-Jordan elimination with partial pivoting (N^3 work, once per mesh) and
+ * written to dev_Minv (n_x x n_x doubles, row-major).  The paper's Section 4
+ * lumps M_h instead (stbem_lumped_mass); with precondition = 2 the solvers use
+ * this exact inverse, C_V^{-1} = M_h^{-1} D_h M_h^{-T} as printed in
+ * Section 4, which keeps the iteration counts bounded on non-uniform meshes
+ * where lumping does not.  Blocks the host.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_CUDA. */
+int stbem_mixed_mass_inverse(stbem_ctx* ctx, const stbem_mesh* mesh, double* dev_Minv);
+
 /* GMRES options and result. */
 typedef struct stbem_solve_opts {
   double tol;       /* stop at ||f - V w|| / ||f|| <= tol (paper: 1e-8)     */
   int max_iter;     /* total iteration cap                                 */
   int restart;      /* Krylov dimension before restart                     */
-  int precondition; /* 1: right preconditioning by C_V^{-1} (needs D, L)   */
+  int precondition; /* 0: none; 1: C_V^{-1} = L^{-1} D_h L^{-1} with the   */
+                    /* lumped mass (dev_L: n_x doubles, Section 4); 2:     */
+                    /* C_V^{-1} = M_h^{-1} D_h M_h^{-T} (dev_L: n_x x n_x,  */
+                    /* stbem_mixed_mass_inverse)                           */
 } stbem_solve_opts;
 
 typedef struct stbem_solve_info {

@@ -253,3 +253,19 @@ def lumped_dual_mass(mesh: BoundaryMesh):
     "lumped mass matrix")."""
     h = mesh.h
     return mesh.ht * (np.roll(h, 1) + 2.0 * h + np.roll(h, -1)) / 4.0
+
+
+def mixed_mass_matrix(mesh: BoundaryMesh):
+    """The consistent mixed mass M_h[l, k] = <phi0_k, psi_l> of one time step
+    (Section 2; the time factor is ht): psi_l is linear on each of its four
+    half-segments (dual_pieces), so its integral over the part of gamma_k it
+    covers is the trapezoid (value at start + value at end) / 2 x length.
+    Row l has entries at k = l - 1, l, l + 1 (cyclic); its row sums are the
+    lumped masses of lumped_dual_mass."""
+    N = mesh.N
+    M = np.zeros((N, N))
+    for l in range(N):
+        for piece, v0, v1, _ in mesh.dual_pieces(l):
+            k = mesh.hs_seg[piece]
+            M[l, k] += 0.5 * (v0 + v1) * mesh.hs_len[piece]
+    return mesh.ht * M

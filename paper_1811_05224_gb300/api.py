@@ -132,6 +132,20 @@ def rhs(ctx: Context, mesh: Mesh, K, y_star, work=None):
     return g, f
 
 
+def mixed_mass_inverse(ctx: Context, mesh: Mesh):
+    """M_h^{-1} (n_x x n_x) of the consistent mixed mass; passing it as L to a
+    solver selects the preconditioner M_h^{-1} D_h M_h^{-T}."""
+    out = ctx.empty((mesh.n_x, mesh.n_x))
+    ctx.check(ctx.lib.stbem_mixed_mass_inverse(ctx.h, mesh.h, _ptr(out)))
+    return out
+
+
+def _prec_mode(D, L):
+    if D is None:
+        return 0
+    return 2 if (L is not None and L.dim() == 2) else 1
+
+
 def lumped_mass(ctx: Context, mesh: Mesh):
     L = ctx.empty((mesh.n_x,))
     ctx.check(ctx.lib.stbem_lumped_mass(ctx.h, mesh.h, _ptr(L)))
@@ -151,7 +165,7 @@ def solve(ctx: Context, V, f, D=None, L=None, tol: float = 1e-8, max_iter: int =
     prec = capi.F64 if V.dtype == torch.float64 else capi.F32
     if D is not None and D.dtype != V.dtype:
         raise ValueError("V and D must share a precision")
-    opts = capi.SolveOpts(tol, max_iter, restart, int(D is not None))
+    opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(D, L))
     info = capi.SolveInfo()
     if out is None:
         out = ctx.empty((n_t, n_x))
@@ -170,7 +184,7 @@ def solve_adjoint(ctx: Context, V, b, D=None, L=None, tol: float = 1e-8, max_ite
     """GMRES for the adjoint V_h^T lam = b (backward in time); returns (lam, info)."""
     n_t, n_x = V.shape[0], V.shape[1]
     prec = capi.F64 if V.dtype == torch.float64 else capi.F32
-    opts = capi.SolveOpts(tol, max_iter, restart, int(D is not None))
+    opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(D, L))
     info = capi.SolveInfo()
     if out is None:
         out = ctx.empty((n_t, n_x))
@@ -213,7 +227,7 @@ def solve_mixed(ctx: Context, V64, V32, f, D32=None, L=None, tol: float = 1e-8, 
                 max_iter: int = 500, restart: int = 200, work=None, out=None, raise_on_fail: bool = True):
     """FP64 iterative refinement around preconditioned GMRES on FP32 operators."""
     n_t, n_x = V64.shape[0], V64.shape[1]
-    opts = capi.SolveOpts(tol, max_iter, restart, int(D32 is not None))
+    opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(D32, L))
     info = capi.SolveInfo()
     if out is None:
         out = ctx.empty((n_t, n_x))

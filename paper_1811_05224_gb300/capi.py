@@ -36,7 +36,7 @@ EXPORTS = [
     "stbem_ragged_create", "stbem_ragged_destroy", "stbem_ragged_sizes", "stbem_ragged_offsets",
     "stbem_ragged_assemble", "stbem_ragged_lumped_mass", "stbem_ragged_apply_workspace_bytes", "stbem_ragged_apply",
     "stbem_ragged_tune", "stbem_ragged_tune_report", "stbem_ragged_rhs", "stbem_ragged_solve_workspace_bytes",
-    "stbem_ragged_solve",
+    "stbem_ragged_solve", "stbem_mixed_mass_inverse",
 ]
 
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
     L.stbem_solve.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
     L.stbem_solve_adjoint.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
     L.stbem_grad_workspace_bytes.argtypes = [i, i, P(sz)]
+    L.stbem_mixed_mass_inverse.argtypes = [vp, vp, vp]
     L.stbem_grad.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp, sz]
     ll = ctypes.c_longlong
     L.stbem_ragged_create.argtypes = [vp, i, P(Problem), P(vp)]

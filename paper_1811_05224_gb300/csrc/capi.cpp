@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "assemble.h"
@@ -400,6 +401,8 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
     return fail(ctx, STBEM_ERR_ARG, "solve_batched: bad options");
   const bool prec = opts->precondition != 0;
   if (prec && (!D_bf16 || !Lm)) return fail(ctx, STBEM_ERR_ARG, "solve_batched: preconditioner needs D and L");
+  if (opts->precondition == 2)
+    return fail(ctx, STBEM_ERR_ARG, "solve_batched: the lumped mass (precondition = 1) only");
   if (work_bytes < batch_bytes(nt, nx, B, m)) return fail(ctx, STBEM_ERR_NOMEM, "solve_batched: workspace too small");
   const size_t N = (size_t)nt * nx, n = (size_t)B * N;
   BatchWork Wk;
@@ -634,6 +637,7 @@ struct GmresOp {
   const void* D;          // NULL: no preconditioner
   const double* L;
   bool transpose = false; // solve V^T x = f with the preconditioner L^-1 D^T L^-1
+  int mass = 1;           // 1: L = lumped diagonal (N); 2: L = M_h^-1 (N x N), y = M^-1 D M^-T x
 };
 
 // Right-preconditioned restarted GMRES for V x = f from x = 0 (see stbem_solve).
@@ -649,11 +653,18 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
   auto applyV = [&](const double* x, double* y) {
     return stbem::apply_launch(op.prec, op.transpose, nt, nx, op.V, 1, x, y, W.apply, s);
   };
-  // right preconditioner: y = L^{-1} D L^{-1} x (or y = x)
+  // right preconditioner: y = L^{-1} D L^{-1} x (lumped mixed mass), or
+  // y = M^{-1} D M^{-T} x per time step (consistent mixed mass), or y = x
   auto applyP = [&](const double* x, double* y) -> cudaError_t {
     if (!prec) return cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    cudaError_t e = stbem::diag_div_launch(x, op.L, W.u, nt, nx, s);
+    cudaError_t e = op.mass == 2 ? stbem::blockmul_launch(nt, nx, op.L, true, x, W.u, s)
+                                 : stbem::diag_div_launch(x, op.L, W.u, nt, nx, s);
     if (e != cudaSuccess) return e;
+    if (op.mass == 2) {
+      e = stbem::apply_launch(op.prec, op.transpose, nt, nx, op.D, 1, W.u, W.v, W.apply, s);
+      if (e != cudaSuccess) return e;
+      return stbem::blockmul_launch(nt, nx, op.L, false, W.v, y, s);
+    }
     e = stbem::apply_launch(op.prec, op.transpose, nt, nx, op.D, 1, W.u, y, W.apply, s);
     if (e != cudaSuccess) return e;
     return stbem::diag_div_launch(y, op.L, y, nt, nx, s);
@@ -777,6 +788,7 @@ int solve_impl(stbem_ctx* ctx, bool transpose, int nt, int nx, int vprec, const 
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve: set device");
   GmresOp op{nt, nx, vprec, V, prec ? D : nullptr, L};
   op.transpose = transpose;
+  op.mass = opts->precondition == 2 ? 2 : 1;
   int iters = 0;
   double relres = 0.0;
   const int status = gmres_core(ctx, op, f, w, opts->tol, maxit, restart, W, &iters, &relres);
@@ -800,6 +812,56 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V
                         const double* b, double* lam, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* work, size_t work_bytes) {
   return solve_impl(ctx, true, nt, nx, vprec, V, D, L, b, lam, opts, info, work, work_bytes);
+}
+
+int stbem_mixed_mass_inverse(stbem_ctx* ctx, const stbem_mesh* m, double* dev_Minv) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !dev_Minv) return fail(ctx, STBEM_ERR_ARG, "mixed_mass_inverse: NULL pointer");
+  const int N = m->N;
+  const std::vector<double>& h = m->h;
+  // M[l][k] = ht int_{gamma_k} psi_l: psi_l is linear on its four half-segments,
+  // with values a_l at x_l and b_l at x_{l+1} (the bends), 1 at the midpoint
+  std::vector<double> A((size_t)N * N, 0.0), Inv((size_t)N * N, 0.0);
+  for (int l = 0; l < N; ++l) {
+    const int lm = (l - 1 + N) % N, lp = (l + 1) % N;
+    const double a = h[lm] / (h[lm] + h[l]), b = h[lp] / (h[l] + h[lp]);
+    A[(size_t)l * N + l] += m->ht * h[l] * (a + 2.0 + b) / 4.0;
+    A[(size_t)l * N + lm] += m->ht * h[lm] * a / 4.0;
+    A[(size_t)l * N + lp] += m->ht * h[lp] * b / 4.0;
+    Inv[(size_t)l * N + l] = 1.0;
+  }
+  // Gauss-Jordan elimination with partial pivoting (M is cyclic tridiagonal
+  // but not symmetric; N^3 host work, once per mesh)
+  for (int c = 0; c < N; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < N; ++r)
+      if (std::fabs(A[(size_t)r * N + c]) > std::fabs(A[(size_t)piv * N + c])) piv = r;
+    if (!(std::fabs(A[(size_t)piv * N + c]) > 0.0)) return fail(ctx, STBEM_ERR_ARG, "mixed_mass_inverse: singular");
+    if (piv != c)
+      for (int k = 0; k < N; ++k) {
+        std::swap(A[(size_t)c * N + k], A[(size_t)piv * N + k]);
+        std::swap(Inv[(size_t)c * N + k], Inv[(size_t)piv * N + k]);
+      }
+    const double inv = 1.0 / A[(size_t)c * N + c];
+    for (int k = 0; k < N; ++k) {
+      A[(size_t)c * N + k] *= inv;
+      Inv[(size_t)c * N + k] *= inv;
+    }
+    for (int r = 0; r < N; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * N + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < N; ++k) {
+        A[(size_t)r * N + k] -= f * A[(size_t)c * N + k];
+        Inv[(size_t)r * N + k] -= f * Inv[(size_t)c * N + k];
+      }
+    }
+  }
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "mixed_mass_inverse: set device");
+  CUDA_TRY(ctx, cudaMemcpyAsync(dev_Minv, Inv.data(), Inv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+           "mixed_mass_inverse: upload");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "mixed_mass_inverse: sync");
+  return STBEM_OK;
 }
 
 int stbem_grad_workspace_bytes(int n_t, int n_x, size_t* bytes) {
@@ -867,7 +929,8 @@ int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const f
     return fail(ctx, STBEM_ERR_NAN, "solve_mixed: right-hand side is not finite");
   }
   if (nf == 0.0) return STBEM_OK;
-  const GmresOp op{nt, nx, STBEM_F32, V32, prec ? (const void*)D32 : nullptr, L};
+  GmresOp op{nt, nx, STBEM_F32, V32, prec ? (const void*)D32 : nullptr, L};
+  op.mass = opts->precondition == 2 ? 2 : 1;
   CUDA_TRY(ctx, cudaMemcpyAsync(r, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "solve_mixed: r");
   int total = 0, status = STBEM_OK;
   double relres = 1.0;

@@ -490,6 +490,8 @@ int stbem_ragged_solve(stbem_ctx* ctx, stbem_ragged* R, int prec, const void* V,
   if (m < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "ragged_solve: bad options");
   const bool prec_on = opts->precondition != 0;
   if (prec_on && (!D || !L)) return fail(ctx, STBEM_ERR_ARG, "ragged_solve: preconditioner needs D and L");
+  if (opts->precondition == 2)
+    return fail(ctx, STBEM_ERR_ARG, "ragged_solve: the lumped mass (precondition = 1) only");
   if (work_bytes < ragged_solve_bytes(R, m, R->part_elems))
     return fail(ctx, STBEM_ERR_NOMEM, "ragged_solve: workspace too small");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "ragged_solve: set device");

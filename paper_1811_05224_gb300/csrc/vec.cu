@@ -412,3 +412,53 @@ cudaError_t rlumped_launch(const RaggedProblem* probs, int P, int max_n, double*
   return cudaGetLastError();
 }
 }  // namespace stbem
+
+namespace stbem {
+// Y[m] = B X[m] (trans = 0) or B^T X[m] (trans = 1) for every time step m:
+// Y (rows x N) = X (rows x N) op(B)^T, B an N x N row-major FP64 matrix.
+// 64 x 64 output tiles (steps x entries), 16-wide chunks of the sum.
+__global__ void __launch_bounds__(256) k_blockmul(int rows, int N, const double* __restrict__ B, int trans,
+                                                  const double* __restrict__ X, double* __restrict__ Y) {
+  __shared__ double Xs[16][65], Bs[16][65];
+  const int m0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int j0 = 0; j0 < N; j0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int jj = e % 16, r = e / 16;
+      const int m = m0 + r, i = i0 + r, j = j0 + jj;
+      Xs[jj][r] = (m < rows && j < N) ? X[(size_t)m * N + j] : 0.0;
+      Bs[jj][r] = (i < N && j < N) ? (trans ? B[(size_t)j * N + i] : B[(size_t)i * N + j]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      double xv[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xv[q] = Xs[jj][ty * 4 + q];
+        bv[q] = Bs[jj][tx * 4 + q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[q][r] = fma(xv[q], bv[r], acc[q][r]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int m = m0 + ty * 4 + q, i = i0 + tx * 4 + r;
+      if (m < rows && i < N) Y[(size_t)m * N + i] = acc[q][r];
+    }
+}
+
+cudaError_t blockmul_launch(int rows, int N, const double* B, bool trans, const double* X, double* Y,
+                            cudaStream_t s) {
+  k_blockmul<<<dim3((N + 63) / 64, (rows + 63) / 64), 256, 0, s>>>(rows, N, B, trans ? 1 : 0, X, Y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+}  // namespace stbem

@@ -45,6 +45,9 @@ cudaError_t rrhs_g_launch(const RaggedProblem* probs, const long long* vp, int P
 cudaError_t rhalf_mass_add_launch(const RaggedProblem* probs, const long long* vp, int P, const double* g, double* f,
                                   long long n, cudaStream_t s);
 cudaError_t rlumped_launch(const RaggedProblem* probs, int P, int max_n, double* L, cudaStream_t s);
+// Y[m] = B X[m] (or B^T X[m]) for each of `rows` steps; B N x N row-major (FP64)
+cudaError_t blockmul_launch(int rows, int N, const double* B, bool trans, const double* X, double* Y,
+                            cudaStream_t s);
 // dst[i] = (float)src[i]
 cudaError_t round_f32_launch(const double* src, float* dst, size_t n, cudaStream_t s);
 }  // namespace stbem

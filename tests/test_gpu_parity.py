@@ -246,3 +246,36 @@ def test_assemble_lags_pieces_equal_full(ctx):
             assert torch.equal(full, parts), (op, prec)
     with pytest.raises(Exception):
         P.assemble_lags(ctx, m, "V", 3, nt + 1)
+
+
+def test_consistent_mixed_mass_preconditioner(ctx):
+    """stbem_mixed_mass_inverse against the inverse of the oracle's consistent
+    mixed mass, and the solves preconditioned with M_h^{-1} D_h M_h^{-T}
+    (forward and adjoint) against the oracle's exact block substitutions, on
+    the non-uniform L-shape where the lumped mass needs more iterations."""
+    import paper_1811_05224_gb300 as P
+    from oracle import gradient as OG
+    X, T, nt, al = W.l_shape(48, seed=3), 1.0, 24, 0.5
+    m, om = _pair(ctx, X, T, nt, al)
+    Minv = P.mixed_mass_inverse(ctx, m).cpu().numpy()
+    Mref = OA.mixed_mass_matrix(om)
+    assert np.abs(Minv @ Mref - np.eye(om.N)).max() <= 1e-12
+    V = P.assemble(ctx, m, "V")
+    K = P.assemble(ctx, m, "K")
+    D = P.assemble(ctx, m, "D")
+    L = P.lumped_mass(ctx, m)
+    g, f = P.rhs(ctx, m, K, (1.5, 1.5))
+    Vn, fn = V.cpu().numpy(), f.cpu().numpy()
+    wref = OS.forward_substitution(Vn, fn)
+    w2, i2 = P.solve(ctx, V, f, D, P.mixed_mass_inverse(ctx, m), tol=1e-11)
+    w1, i1 = P.solve(ctx, V, f, D, L, tol=1e-11)
+    assert float(np.linalg.norm(w2.cpu().numpy() - wref) / np.linalg.norm(wref)) < 1e-9
+    assert i2["iterations"] <= i1["iterations"]
+    b = np.random.default_rng(4).standard_normal((nt, om.N))
+    lam, _ = P.solve_adjoint(ctx, V, torch.as_tensor(b).cuda(), D, P.mixed_mass_inverse(ctx, m), tol=1e-11)
+    lref = OG.backward_substitution(Vn, b)
+    assert float(np.linalg.norm(lam.cpu().numpy() - lref) / np.linalg.norm(lref)) < 1e-9
+    # the mixed-precision solve with the same preconditioner (FP32 D)
+    wm, im = P.solve_mixed(ctx, V, P.round_f32(ctx, V), f, P.assemble(ctx, m, "D", "f32"),
+                           P.mixed_mass_inverse(ctx, m), tol=1e-10, inner_tol=1e-4)
+    assert float(np.linalg.norm(wm.cpu().numpy() - wref) / np.linalg.norm(wref)) < 1e-7

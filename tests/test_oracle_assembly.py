@@ -259,3 +259,22 @@ def test_positive_definite_square32():
         M = dense(assembly.assemble(o, m))
         ev = np.linalg.eigvalsh(0.5 * (M + M.T))
         assert ev.min() > 0, (o, ev.min())
+
+
+def test_mixed_mass_matrix_pins():
+    """Consistent mixed mass M[l, k] = <phi0_k, psi_l>: row sums are the lumped
+    masses ht (h_{l-1} + 2 h_l + h_{l+1}) / 4 (closed form), column sums are
+    ht h_k (the dual hats sum to one on Gamma), and a uniform ring gives
+    ht h tridiag(1/8, 3/4, 1/8)."""
+    from oracle.assembly import lumped_dual_mass, mixed_mass_matrix
+    m = BoundaryMesh(W.l_shape(24, seed=3), 1.0, 4, 0.5)
+    M = mixed_mass_matrix(m)
+    hm, h0, hp = np.roll(m.h, 1), m.h, np.roll(m.h, -1)
+    assert np.allclose(M.sum(1), m.ht * (hm + 2 * h0 + hp) / 4, rtol=1e-14, atol=0)
+    assert np.allclose(M.sum(0), m.ht * m.h, rtol=1e-14, atol=0)
+    assert np.allclose(M.sum(1), lumped_dual_mass(m), rtol=1e-14, atol=0)
+    u = BoundaryMesh(W.unit_square(3), 1.0, 5, 1.0)
+    Mu = mixed_mass_matrix(u)
+    h = u.h[0]
+    ref = u.ht * h * (0.75 * np.eye(12) + 0.125 * (np.roll(np.eye(12), 1, 1) + np.roll(np.eye(12), -1, 1)))
+    assert np.allclose(Mu, ref, rtol=1e-14, atol=1e-18)
