@@ -606,7 +606,7 @@ def run_ours(args):
             "grad": grad,
             "ragged": ragged,
         },
-        "roofline": {"kernel": "k_tile_ml<D, f64, 2 lags> lags >= 2", "bound": "alu",
+        "roofline": {"kernel": "k_tile_ml<D, f64, 4 lags> lags >= 2", "bound": "alu",
                      "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_D2_BYTES,
                      "launch_ms": d2_ms_launch, "flops_per_launch": d2_flops_launch,

@@ -231,23 +231,23 @@ __device__ void tensor_moments_impl(const Piece& A, const Piece& B, int d, int n
 // moves to larger c as d grows); F at the shared times is evaluated once.  The
 // Peano lags use intervals lc .. L, each evaluated once: its left-role sum
 // serves lag i, its right-role sum lag i - 1.
-template <typename R, int K>
-__device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (&out)[kMaxLagsML]) {
+template <typename R, int K, int NL>
+__device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (&out)[NL]) {
   const int L = T.L;
   const R four_pi = (R)kFourPi;
   int lc = 0;
   while (lc < L && c * T.inv_dht[lc] > (R)0.5 * (R)(T.d0 + lc)) ++lc;
   if (lc > 0) {
-    R F[kMaxLagsML + 2];
+    R F[NL + 2];
 #pragma unroll
-    for (int j = 0; j < kMaxLagsML + 2; ++j) {
+    for (int j = 0; j < NL + 2; ++j) {
       if (j >= lc + 2) break;
       R a, b;
       e12(c * T.inv_s[j], &a, &b);
       F[j] = K == kV ? T.s[j] / four_pi * (a - b) : alpha / ((R)2 * four_pi * c) * T.s[j] * b;
     }
 #pragma unroll
-    for (int l = 0; l < kMaxLagsML; ++l)
+    for (int l = 0; l < NL; ++l)
       if (l < lc) out[l] = (F[l + 2] - (R)2 * F[l + 1]) + F[l];
   }
   if (lc < L) {
@@ -269,7 +269,7 @@ __device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (
         for (int g = g0; g < g1; ++g) sr = fma(rw[g], exp_neg(c * T.sig[g]), sr);
       }
 #pragma unroll
-      for (int l = 0; l < kMaxLagsML; ++l)
+      for (int l = 0; l < NL; ++l)
         if (l == i - 1 && i > lc) out[l] = carry + sr;
       carry = sl;
     }
@@ -277,17 +277,16 @@ __device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (
 }
 
 // D_h's two kernels (F_V and F_1) for the lags of the table at one c.
-template <typename R>
-__device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R (&ov)[kMaxLagsML],
-                                            R (&o1)[kMaxLagsML]) {
+template <typename R, int NL>
+__device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R (&ov)[NL], R (&o1)[NL]) {
   const int L = T.L;
   const R four_pi = (R)kFourPi;
   int lc = 0;
   while (lc < L && c * T.inv_dht[lc] > (R)0.5 * (R)(T.d0 + lc)) ++lc;
   if (lc > 0) {
-    R Fv[kMaxLagsML + 2], F1[kMaxLagsML + 2];
+    R Fv[NL + 2], F1[NL + 2];
 #pragma unroll
-    for (int j = 0; j < kMaxLagsML + 2; ++j) {
+    for (int j = 0; j < NL + 2; ++j) {
       if (j >= lc + 2) break;
       R a, b;
       e12(c * T.inv_s[j], &a, &b);
@@ -295,7 +294,7 @@ __device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R
       F1[j] = alpha / four_pi * a;
     }
 #pragma unroll
-    for (int l = 0; l < kMaxLagsML; ++l)
+    for (int l = 0; l < NL; ++l)
       if (l < lc) {
         ov[l] = (Fv[l + 2] - (R)2 * Fv[l + 1]) + Fv[l];
         o1[l] = (F1[l + 2] - (R)2 * F1[l + 1]) + F1[l];
@@ -319,7 +318,7 @@ __device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R
         }
       }
 #pragma unroll
-      for (int l = 0; l < kMaxLagsML; ++l)
+      for (int l = 0; l < NL; ++l)
         if (l == i - 1 && wr) {
           ov[l] = cv + srv;
           o1[l] = c1 + sr1;
@@ -332,7 +331,7 @@ __device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R
 
 // Moments of one piece pair for the lags of the table, tensor Gauss rule of
 // order n; mom[l * ls + q] for lag l and moment q (as tensor_moments_impl).
-template <typename R, int OP>
+template <typename R, int OP, int NL>
 __device__ void tensor_moments_ml(const Piece& A, const Piece& B, int n, double alpha, const MLNodes<R>& T,
                                   double* mom, int ls) {
   const int o = gauss_offset(n);
@@ -344,9 +343,9 @@ __device__ void tensor_moments_ml(const Piece& A, const Piece& B, int n, double 
   const R qa = (R)(0.25 * alpha);
   const R al = (R)alpha;
   constexpr int NM = NMom<OP>::n;
-  R acc[kMaxLagsML][NM];
+  R acc[NL][NM];
 #pragma unroll
-  for (int l = 0; l < kMaxLagsML; ++l)
+  for (int l = 0; l < NL; ++l)
 #pragma unroll
     for (int q = 0; q < NM; ++q) acc[l][q] = (R)0;
   for (int a = 0; a < n; ++a) {
@@ -359,29 +358,29 @@ __device__ void tensor_moments_ml(const Piece& A, const Piece& B, int n, double 
       const R dy = (aby + xi * eay) - eta * eby;
       const R c = qa * (dx * dx + dy * dy);
       if constexpr (OP == STBEM_OP_V) {
-        R k[kMaxLagsML];
-        ml_kernel<R, kV>(c, al, T, k);
+        R k[NL];
+        ml_kernel<R, kV, NL>(c, al, T, k);
 #pragma unroll
-        for (int l = 0; l < kMaxLagsML; ++l)
+        for (int l = 0; l < NL; ++l)
           if (l < T.L) acc[l][0] += w * k[l];
       } else if constexpr (OP == STBEM_OP_K) {
-        R k[kMaxLagsML];
-        ml_kernel<R, kKq>(c, al, T, k);
+        R k[NL];
+        ml_kernel<R, kKq, NL>(c, al, T, k);
         const R wq = w * (qab + xi * qea);
 #pragma unroll
-        for (int l = 0; l < kMaxLagsML; ++l)
+        for (int l = 0; l < NL; ++l)
           if (l < T.L) {
             const R wk = wq * k[l];
             acc[l][0] += wk * ((R)1 - eta);
             acc[l][1] += wk * eta;
           }
       } else {
-        R kv[kMaxLagsML], k1[kMaxLagsML];
-        ml_kernel_D<R>(c, al, T, kv, k1);
+        R kv[NL], k1[NL];
+        ml_kernel_D<R, NL>(c, al, T, kv, k1);
         const R b11 = ((R)1 - xi) * ((R)1 - eta), b10 = ((R)1 - xi) * eta;
         const R b01 = xi * ((R)1 - eta), b00 = xi * eta;
 #pragma unroll
-        for (int l = 0; l < kMaxLagsML; ++l)
+        for (int l = 0; l < NL; ++l)
           if (l < T.L) {
             acc[l][0] += w * kv[l];
             const R wk = w * k1[l];
@@ -395,7 +394,7 @@ __device__ void tensor_moments_ml(const Piece& A, const Piece& B, int n, double 
   }
   const double LL = A.len * B.len;
 #pragma unroll
-  for (int l = 0; l < kMaxLagsML; ++l)
+  for (int l = 0; l < NL; ++l)
     if (l < T.L)
 #pragma unroll
       for (int q = 0; q < NM; ++q) mom[l * ls + q] = (double)acc[l][q] * LL;
@@ -510,7 +509,7 @@ __global__ void __launch_bounds__(128) k_lag2_V_ml(DevMesh M, int d_begin, int d
   while (S(i + 1) <= p) ++i;
   const int j = i + (int)(p - S(i));
   double m[kMaxLagsML];
-  tensor_moments_ml<R, STBEM_OP_V>(seg_piece(M, i), seg_piece(M, j), space_order(d0), M.alpha, TN, m, 1);
+  tensor_moments_ml<R, STBEM_OP_V, kMaxLagsML>(seg_piece(M, i), seg_piece(M, j), space_order(d0), M.alpha, TN, m, 1);
   for (int l = 0; l < nl; ++l) {
     const size_t base = (size_t)(d0 + l) * N * N;
     out[base + (size_t)i * N + j] = (T)m[l];
@@ -742,7 +741,7 @@ __device__ void tile_body_ml(const DevMesh& M, int d0, int nl, int tile, T* __re
         for (int q = 0; q < NM; ++q) m[(size_t)l * P * NM + q] = 0.0;
       continue;
     }
-    tensor_moments_ml<R, OP>(A, B, n, M.alpha, *TN, m, P * NM);
+    tensor_moments_ml<R, OP, LM>(A, B, n, M.alpha, *TN, m, P * NM);
   }
   __syncthreads();
   for (int l = 0; l < nl; ++l)
@@ -764,7 +763,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_ml(DevMesh M, int d_begin
 // occupancy.)
 template <int OP, typename R>
 __host__ __device__ constexpr int lag_group_len() {
-  return OP == STBEM_OP_D ? (sizeof(R) == 4 ? 1 : 2) : kMaxLagsML;
+  return OP == STBEM_OP_D ? (sizeof(R) == 4 ? 1 : 4) : kMaxLagsML;   // D: 4 moment arrays fill shared memory
 }
 
 __host__ __device__ inline int lag_groups(int nt, int LM) {

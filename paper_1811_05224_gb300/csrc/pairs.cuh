@@ -165,7 +165,7 @@ static __device__ void build_lag_nodes(LagNodes<R>& L, int d, double ht, double 
 // per CTA holds every node of those intervals with its weights for the left
 // role (hat tau, the interval is lag k + 1's left) and the right role
 // (hat 1 - tau, lag k's right).  Factors as in LagNodes.
-constexpr int kMaxLagsML = 4;
+constexpr int kMaxLagsML = 8;
 constexpr int kMaxNodesML = 16 + 8 * kMaxLagsML;
 template <typename R>
 struct MLNodes {
