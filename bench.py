@@ -646,16 +646,25 @@ D_NODE_FLOPS = 24
 D_POINT_FLOPS = 33
 
 
-def d_lag2_flops(n_x, n_t):
+def d_lag2_flops(n_x, n_t, lags_per_group=4):
     """Algorithmic FP64 flops of the D_h assembly at lags 2..n_t-1: every
     unordered half-segment pair integrated once per lag (H (H + 1) / 2 with
-    H = 2 n_x), n(d)^2 points, Peano nodes of the two intervals per point."""
+    H = 2 n_x), n(d)^2 points per pair; each group of consecutive lags (as the
+    kernel assembles them: runs of lags_per_group within the space-order
+    segments [2, 8), [8, 32), [32, n_t), split every 64 lags) evaluates the
+    Peano nodes of its L + 1 time intervals once per point, plus the per-lag
+    point work."""
     H = 2 * n_x
     pairs = H * (H + 1) // 2
     tot = 0.0
-    for d in range(2, n_t):
-        nodes = _peano_order(d - 1) + _peano_order(d)
-        tot += pairs * _space_order(d) ** 2 * (D_NODE_FLOPS * nodes + D_POINT_FLOPS)
+    for lo, hi in ((2, 8), (8, 32), (32, n_t)):
+        hi = min(hi, n_t)
+        for d0 in range(lo, hi, 64):
+            d1 = min(d0 + 64, hi)
+            for g0 in range(d0, d1, lags_per_group):
+                L = min(lags_per_group, d1 - g0)
+                nodes = sum(_peano_order(g0 - 1 + i) for i in range(L + 1))
+                tot += pairs * _space_order(g0) ** 2 * (D_NODE_FLOPS * nodes + D_POINT_FLOPS * L)
     return tot
 
 
