@@ -637,9 +637,11 @@ def _peano_order(k):      # Gauss nodes on time interval k
     return 6 if k >= 32 else (8 if k >= 2 else 16)
 
 
-# FP64 flops of one Peano node of the D kernel: e^{-c sigma} (c sigma, x 64/ln2,
-# two reduction FMAs, five polynomial FMAs, table and scale products: 18) and
-# the two kernel accumulations with the w3 c - w2 factor (3 FMAs: 6).
+# FP64 flops of one Peano node of the D kernel: e^{-c sigma} (c sigma, x 256/ln2,
+# two reduction FMAs, four polynomial FMAs, the table product: 15; the power
+# of two is an integer exponent add) and the kernel accumulations, 6 flops per
+# role (one FMA for F_V, two for the w3 c - w2 factor of F_1); in a group of 4
+# lags the 5 intervals serve 8 roles, 1.6 per node: 15 + 9.6 ~ 24.
 D_NODE_FLOPS = 24
 # per quadrature point: x - y (4 FMAs), c (4), weight (1), switch (1), five
 # moments with their bilinear weights (~23)
