@@ -118,6 +118,46 @@ __device__ __forceinline__ void lag01D(R c, int d, double ht, double alpha, R* k
   }
 }
 
+// Lags 0 and 1 together at one c (FP64): lag 0 is F(ht) and the closed form of
+// lag 1 is F(2 ht) - 2 F(ht), so F(ht) is evaluated once for both.  Same
+// operations in the same order as the one-lag evaluation (lag_kernel,
+// lag01_D64), so both give identical results.
+template <int K>
+__device__ __forceinline__ void lag01_pair(double c, double ht, double alpha, double* k0, double* k1) {
+  const double z = c / ht;
+  double a1, b1;
+  e1e2(z, &a1, &b1);
+  const double F1 = K == kV ? ht / kFourPi * (a1 - b1) : alpha / (2.0 * kFourPi * c) * ht * b1;
+  *k0 = F1;
+  if (z < 1.0) {
+    *k1 = lag1_series<K>(z, ht, alpha);
+    return;
+  }
+  double a2, b2;
+  e1e2(c / (2.0 * ht), &a2, &b2);
+  const double F2 = K == kV ? (2.0 * ht) / kFourPi * (a2 - b2) : alpha / (2.0 * kFourPi * c) * (2.0 * ht) * b2;
+  *k1 = F2 - 2.0 * F1;
+}
+
+__device__ __forceinline__ void lag01_D64_pair(double c, double ht, double alpha, double* v0, double* o0, double* v1,
+                                               double* o1) {
+  const double z = c / ht;
+  double a1, b1;
+  e1e2(z, &a1, &b1);
+  const double fv = ht / kFourPi * (a1 - b1), f1 = alpha / kFourPi * a1;
+  *v0 = fv;
+  *o0 = f1;
+  if (z < 1.0) {
+    *v1 = lag1_series<kV>(z, ht, alpha);
+    *o1 = lag1_series<k1>(z, ht, alpha);
+    return;
+  }
+  double a2, b2;
+  e1e2(c / (2.0 * ht), &a2, &b2);
+  *v1 = (2.0 * ht) / kFourPi * (a2 - b2) - 2.0 * fv;
+  *o1 = alpha / kFourPi * a2 - 2.0 * f1;
+}
+
 // D2_d F_V (K = kV) or D2_d F_K / q (K = kKq) at lag d >= 2 from the tables.
 template <typename R, int K>
 __device__ __forceinline__ R lag2_kernel(R c, int d, R alpha, const LagNodes<R>& L) {
@@ -398,6 +438,70 @@ __device__ void tensor_moments_ml(const Piece& A, const Piece& B, int n, double 
     if (l < T.L)
 #pragma unroll
       for (int q = 0; q < NM; ++q) mom[l * ls + q] = (double)acc[l][q] * LL;
+}
+
+// Moments of one regular or near piece pair at lags 0 and 1 together (FP64):
+// mom[q] for lag 0, mom[ls + q] for lag 1.
+template <int OP>
+__device__ void tensor_moments_01(const Piece& A, const Piece& B, int n, double ht, double alpha, double* mom,
+                                  int ls) {
+  const int o = gauss_offset(n);
+  const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
+  const double ebx = B.x1 - B.x0, eby = B.y1 - B.y0;
+  const double abx = A.x0 - B.x0, aby = A.y0 - B.y0;
+  const double qab = (A.x0 - B.x0) * B.nx + (A.y0 - B.y0) * B.ny;
+  const double qea = (A.x1 - A.x0) * B.nx + (A.y1 - A.y0) * B.ny;
+  const double qa = 0.25 * alpha;
+  constexpr int NM = NMom<OP>::n;
+  double acc[2][NM];
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int q = 0; q < NM; ++q) acc[l][q] = 0.0;
+  for (int a = 0; a < n; ++a) {
+    const double xi = c_tab.gx[o + a], wa = c_tab.gw[o + a];
+    for (int b = 0; b < n; ++b) {
+      const double eta = c_tab.gx[o + b];
+      const double w = wa * c_tab.gw[o + b];
+      const double dx = (abx + xi * eax) - eta * ebx;
+      const double dy = (aby + xi * eay) - eta * eby;
+      const double c = qa * (dx * dx + dy * dy);
+      if constexpr (OP == STBEM_OP_V) {
+        double k0, k1;
+        lag01_pair<kV>(c, ht, alpha, &k0, &k1);
+        acc[0][0] += w * k0;
+        acc[1][0] += w * k1;
+      } else if constexpr (OP == STBEM_OP_K) {
+        double k0, k1;
+        lag01_pair<kKq>(c, ht, alpha, &k0, &k1);
+        const double q = qab + xi * qea;
+        const double w0 = w * (q * k0), w1 = w * (q * k1);
+        acc[0][0] += w0 * (1.0 - eta);
+        acc[0][1] += w0 * eta;
+        acc[1][0] += w1 * (1.0 - eta);
+        acc[1][1] += w1 * eta;
+      } else {
+        double v0, o0, v1, o1;
+        lag01_D64_pair(c, ht, alpha, &v0, &o0, &v1, &o1);
+        const double wo0 = w * o0, wo1 = w * o1;
+        acc[0][0] += w * v0;
+        acc[1][0] += w * v1;
+        acc[0][1] += wo0 * (1.0 - xi) * (1.0 - eta);
+        acc[0][2] += wo0 * (1.0 - xi) * eta;
+        acc[0][3] += wo0 * xi * (1.0 - eta);
+        acc[0][4] += wo0 * xi * eta;
+        acc[1][1] += wo1 * (1.0 - xi) * (1.0 - eta);
+        acc[1][2] += wo1 * (1.0 - xi) * eta;
+        acc[1][3] += wo1 * xi * (1.0 - eta);
+        acc[1][4] += wo1 * xi * eta;
+      }
+    }
+  }
+  const double LL = A.len * B.len;
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int q = 0; q < NM; ++q) mom[l * ls + q] = acc[l][q] * LL;
 }
 
 // ---- moments of one singular pair, FP64 (lags 0 and 1) ------------------------------
@@ -748,6 +852,60 @@ __device__ void tile_body_ml(const DevMesh& M, int d0, int nl, int tile, T* __re
     tile_entries<OP, T>(M, rt, ct, r0, c0, mom + (size_t)l * P * NM, (size_t)(d0 + l) * N * N, out);
 }
 
+// Lags 0 and 1 of one tile together (FP64 compute): regular and near pairs
+// integrated once for both lags, identical and vertex-sharing pairs from the
+// singular-pair buffer; then each lag's entries.
+template <int OP, typename T>
+__device__ void tile_body_01(const DevMesh& M, int tile, const double* __restrict__ sing, T* __restrict__ out,
+                             unsigned char* smem_raw) {
+  constexpr int P = Tile<OP>::pairs, NM = Tile<OP>::nm;
+  double* mom = reinterpret_cast<double*>(smem_raw);
+  const int N = M.N;
+  int rt, ct;
+  if (OP == STBEM_OP_K) {
+    const int nP = (N + kKP - 1) / kKP;
+    rt = tile / nP;
+    ct = tile % nP;
+  } else {
+    upper_tile(tile, (N + kT - 1) / kT, &rt, &ct);
+  }
+  const int r0 = rt * kT, c0 = ct * (OP == STBEM_OP_K ? kKP : kT);
+  for (int p = threadIdx.x; p < P; p += kTileThreads) {
+    Piece A, B;
+    int ia, ib, ring;
+    double* m = mom + (size_t)p * NM;
+    if (!tile_pair<OP>(M, r0, c0, p, &A, &B, &ia, &ib, &ring)) {
+      for (int l = 0; l < 2; ++l)
+        for (int q = 0; q < NM; ++q) m[(size_t)l * P * NM + q] = 0.0;
+      continue;
+    }
+    const int cls = pair_class(ring, ia, ib, A, B);
+    if (cls == kIdentical || cls == kAdjNext || cls == kAdjPrev) {
+      for (int l = 0; l < 2; ++l) {
+        const double* src = sing + ((size_t)l * 3 * ring + singular_slot(cls, ia, ring)) * 5;
+        for (int q = 0; q < NM; ++q) m[(size_t)l * P * NM + q] = src[q];
+      }
+      continue;
+    }
+    tensor_moments_01<OP>(A, B, cls == kRegular ? kRegular01 : kNear01, M.ht, M.alpha, m, P * NM);
+  }
+  __syncthreads();
+  for (int l = 0; l < 2; ++l)
+    tile_entries<OP, T>(M, rt, ct, r0, c0, mom + (size_t)l * P * NM, (size_t)l * N * N, out);
+}
+
+template <int OP, typename T>
+__global__ void __launch_bounds__(kTileThreads) k_tile_01(DevMesh M, const double* __restrict__ sing,
+                                                          T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_body_01<OP, T>(M, blockIdx.x, sing, out, smem_raw);
+}
+
+template <int OP>
+constexpr size_t tile_01_smem_bytes() {
+  return (((size_t)2 * Tile<OP>::pairs * Tile<OP>::nm * sizeof(double) + 15) / 16) * 16;
+}
+
 template <int OP, typename R, typename T, int LM>
 __global__ void __launch_bounds__(kTileThreads) k_tile_ml(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -766,8 +924,9 @@ __host__ __device__ constexpr int lag_group_len() {
   return OP == STBEM_OP_D ? (sizeof(R) == 4 ? 1 : 4) : kMaxLagsML;   // D: 4 moment arrays fill shared memory
 }
 
-__host__ __device__ inline int lag_groups(int nt, int LM) {
-  int g = nt < 2 ? nt : 2;
+// (FP64: lags 0 and 1 form one group; FP32: one each, pair01 = false.)
+__host__ __device__ inline int lag_groups(int nt, int LM, bool pair01) {
+  int g = nt < 2 ? nt : (pair01 ? 1 : 2);
   const int seg[4] = {2, 8, 32, 1 << 30};
   for (int k = 0; k < 3; ++k) {
     const int lo = seg[k], hi = nt < seg[k + 1] ? nt : seg[k + 1];
@@ -776,11 +935,11 @@ __host__ __device__ inline int lag_groups(int nt, int LM) {
   return g;
 }
 
-__host__ __device__ inline void lag_group(int nt, int LM, int g, int* d0, int* nl) {
-  const int l01 = nt < 2 ? nt : 2;
+__host__ __device__ inline void lag_group(int nt, int LM, bool pair01, int g, int* d0, int* nl) {
+  const int l01 = nt < 2 ? nt : (pair01 ? 1 : 2);
   if (g < l01) {
     *d0 = g;
-    *nl = 1;
+    *nl = (pair01 && nt >= 2) ? 2 : 1;
     return;
   }
   g -= l01;
@@ -868,9 +1027,11 @@ __global__ void __launch_bounds__(kTileThreads) k_ragged_tile(const RaggedProble
     const int g = (int)(local / nt_tiles), t = (int)(local % nt_tiles);
     int d0, nl;
     constexpr int LM = lag_group_len<OP, R>();
-    lag_group(pr.M.n_t, LM, g, &d0, &nl);
+    constexpr bool P01 = sizeof(R) == 8;
+    lag_group(pr.M.n_t, LM, P01, g, &d0, &nl);
     T* o = out + pr.op_off;
-    if (d0 < 2) tile_body<OP, R, T, true>(pr.M, d0, t, pr.M.sing, o, smem_raw);
+    if (d0 == 0 && nl == 2) tile_body_01<OP, T>(pr.M, t, pr.M.sing, o, smem_raw);
+    else if (d0 < 2) tile_body<OP, R, T, true>(pr.M, d0, t, pr.M.sing, o, smem_raw);
     else if (LM == 1) tile_body<OP, R, T, false>(pr.M, d0, t, pr.M.sing, o, smem_raw);
     else tile_body_ml<OP, R, T, LM>(pr.M, d0, nl, t, o, smem_raw);
     __syncthreads();
@@ -913,7 +1074,15 @@ static cudaError_t launch_op(const DevMesh& M, int lag_begin, int lag_end, T* ou
   if (l01 < u01) {
     const int Rl = OP == STBEM_OP_D ? 2 * N : N;
     k_singular<OP><<<dim3(3 * Rl, u01), kSingThreads, 0, s>>>(M, M.sing);
-    k_tile<OP, R, T, true><<<dim3(tiles, u01 - l01), kTileThreads, smem, s>>>(M, l01, M.sing, out);
+    if (sizeof(R) == 8 && l01 == 0 && u01 == 2) {
+      // FP64: both lags in one pass (shared closed-form evaluations)
+      const size_t smem01 = tile_01_smem_bytes<OP>();
+      e = cudaFuncSetAttribute(k_tile_01<OP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem01);
+      if (e != cudaSuccess) return e;
+      k_tile_01<OP, T><<<tiles, kTileThreads, smem01, s>>>(M, M.sing, out);
+    } else {
+      k_tile<OP, R, T, true><<<dim3(tiles, u01 - l01), kTileThreads, smem, s>>>(M, l01, M.sing, out);
+    }
     count_launches(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -952,10 +1121,10 @@ int assembly_lag_groups(int op, int prec, int nt) {
   if (prec == STBEM_F64)
     return lag_groups(nt, op == STBEM_OP_V   ? lag_group_len<STBEM_OP_V, double>()
                           : op == STBEM_OP_K ? lag_group_len<STBEM_OP_K, double>()
-                                             : lag_group_len<STBEM_OP_D, double>());
+                                             : lag_group_len<STBEM_OP_D, double>(), true);
   return lag_groups(nt, op == STBEM_OP_V   ? lag_group_len<STBEM_OP_V, float>()
                         : op == STBEM_OP_K ? lag_group_len<STBEM_OP_K, float>()
-                                           : lag_group_len<STBEM_OP_D, float>());
+                                           : lag_group_len<STBEM_OP_D, float>(), false);
 }
 
 int assembly_tiles_per_lag(int op, int N) {
@@ -977,7 +1146,8 @@ static cudaError_t ragged_op(const RaggedProblem* probs, int P, RaggedItems si, 
   k_ragged_singular<OP><<<sms * (occ > 0 ? occ : 1), kSingThreads, 0, s>>>(probs, si.order, si.prefix, P, counters);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = std::max(tile_smem_bytes<OP, R>(), tile_ml_smem_bytes<OP, R, lag_group_len<OP, R>()>());
+  const size_t smem = std::max(std::max(tile_smem_bytes<OP, R>(), tile_ml_smem_bytes<OP, R, lag_group_len<OP, R>()>()),
+                               sizeof(R) == 8 ? tile_01_smem_bytes<OP>() : (size_t)0);
   e = cudaFuncSetAttribute(k_ragged_tile<OP, R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_tile<OP, R, T>, kTileThreads, smem);
