@@ -8,7 +8,9 @@
 //    by gen_expint_tables.py in 40-digit arithmetic), Clenshaw summation;
 //  * z >= 16: the continued fraction of A&S 5.1.22 in its even (contracted)
 //    form, E_n(z) = e^{-z} / (z + n - 1 n / (z + n + 2 - 2 (n+1) / (z + n + 4 - ...))),
-//    evaluated backward at a fixed depth of 14 (converged to < 1e-16 there).
+//    truncated at a fixed depth of 14 (converged to < 1e-16 there) and
+//    evaluated by forward numerator / denominator recurrences (one division),
+//    or backward from z = 700 on.
 //    The Lentz evaluation (Lentz, Appl. Opt. 15, 1976) of the same fraction is
 //    kept as cf_e1e2 for checks.
 // exp and log are the platform's; nothing here reproduces their internals.
@@ -112,6 +114,27 @@ STB_HD double cf_backward(double z, int n) {
   return 1.0 / f;
 }
 
+// The same depth-14 convergent by the forward recurrences of its numerators
+// and denominators (the fundamental recurrence formulas), P_j = b_j P_{j-1} +
+// a_j P_{j-2} and likewise Q_j, with one division at the end instead of one per
+// level; both functions n = 1, 2 together.  For 16 <= z < 700 the P_j stay
+// below (z + 28)^14 < 1e41.  Returns the reciprocals 1 / f (as cf_backward).
+STB_HD void cf_forward12(double z, double* r1, double* r2) {
+  constexpr int K = 14;
+  double p1m = 1.0, q1m = 0.0, p1 = z + 1.0, q1 = 1.0;   // n = 1: b_j = z + 1 + 2 j
+  double p2m = 1.0, q2m = 0.0, p2 = z + 2.0, q2 = 1.0;   // n = 2: b_j = z + 2 + 2 j
+  for (int j = 1; j <= K; ++j) {
+    const double b1 = z + 1.0 + 2.0 * (double)j, a1 = -(double)j * (double)j;
+    const double b2 = z + 2.0 + 2.0 * (double)j, a2 = -(double)j * (double)(j + 1);
+    const double np1 = fma(b1, p1, a1 * p1m), nq1 = fma(b1, q1, a1 * q1m);
+    const double np2 = fma(b2, p2, a2 * p2m), nq2 = fma(b2, q2, a2 * q2m);
+    p1m = p1; q1m = q1; p1 = np1; q1 = nq1;
+    p2m = p2; q2m = q2; p2 = np2; q2 = nq2;
+  }
+  *r1 = q1 / p1;
+  *r2 = q2 / p2;
+}
+
 // Clenshaw sum of c0/2 + sum_{k>=1} c_k T_k(t).
 STB_HD double cheb_sum(const double* c, double t) {
   double b1 = 0.0, b2 = 0.0;
@@ -136,6 +159,12 @@ STB_HD void e1e2(double z, double* e1, double* e2) {
     const double ez = exp_neg_fast(z);
     *e1 = cheb_sum(kChebE1[k], t) * ez;
     *e2 = cheb_sum(kChebE2[k], t) * ez;
+  } else if (z < 700.0) {
+    const double ez = exp_neg_fast(z);
+    double r1, r2;
+    cf_forward12(z, &r1, &r2);
+    *e1 = r1 * ez;
+    *e2 = r2 * ez;
   } else {
     const double ez = exp_neg_fast(z);
     *e1 = cf_backward(z, 1) * ez;
