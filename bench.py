@@ -611,8 +611,8 @@ def run_ours(args):
                      "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_D2_BYTES,
                      "launch_ms": d2_ms_launch, "flops_per_launch": d2_flops_launch,
                      "note": "peak: nominal FP64 1.25 TFLOP/s; FP64-ALU bound (DRAM traffic is only "
-                             "the written lag blocks); flops counted from the rule, unique half-segment "
-                             "pairs only"},
+                             "the written lag blocks); algorithmic flops: unique half-segment pairs, each "
+                             "group of 4 lags evaluating its 5 Peano intervals once"},
         "apply_roofline": {"bound": "alu", "achieved": apply_flops / (ms_apply * 1e-3) / 1e12,
                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": apply_flops / (ms_apply * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
