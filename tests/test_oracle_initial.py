@@ -1,0 +1,262 @@
+"""Pins of the oracle's initial-data operator M_h^0 and the Section 4 example.
+
+* moments: on Omega = union of axis-parallel rectangles (the unit square, a
+  jittered triangulation of it, the L-shape), sum_j M0[m][i][j] p(y_j) for
+  p in {1, y_1, y_2} is the integral over gamma_i x tau_m of
+  int_Omega U*(x - y, t) p(y) dy, because P1 reproduces linear p exactly.
+  U* is a product of two 1D Gaussians of variance 2t/alpha, so the inner
+  integral is a product of erf/exp closed forms; the outer two integrals are
+  adaptive quadrature (QUADPACK);
+* single entries of every pair class (touching by an edge, touching by a
+  vertex, near, regular) at m = 0 and 1 against nested adaptive quadrature of
+  the triple integral, the time integral taken exactly (G differences);
+* the Section 4 example data (g, exact Neumann datum) against quadrature;
+* the Section 4 example end to end: w_h converges to the exact Neumann datum
+  (and does not without the M_h^0 u_0 term); GMRES counts against Table 1.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import dblquad, quad
+from scipy.special import erf, exp1
+
+import workloads as W
+from oracle import assembly, rhs, solve
+from oracle import initial as I
+from oracle.geometry import BoundaryMesh
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _gauss_moments(x, lo, hi, sig):
+    """int_lo^hi g(x - y) dy and int_lo^hi y g(x - y) dy for the 1D Gaussian
+    g(u) = exp(-u^2 / sig^2) / (sig sqrt(pi))."""
+    e0 = 0.5 * (erf((x - lo) / sig) - erf((x - hi) / sig))
+    e1 = x * e0 + sig / (2.0 * np.sqrt(np.pi)) * (np.exp(-(x - lo) ** 2 / sig ** 2)
+                                                  - np.exp(-(x - hi) ** 2 / sig ** 2))
+    return e0, e1
+
+
+def _moment(bm, rects, i, m, p):
+    """int_{tau_m} int_{gamma_i} int_Omega U*(x - y, t) p(y) dy ds dt with
+    Omega the union of the disjoint rectangles ``rects``."""
+    a, b, h, al = bm.a[i], bm.b[i], bm.h[i], bm.alpha
+
+    def inner(t):
+        sig = np.sqrt(4.0 * t / al)
+
+        def fx(s):
+            x = a + s * (b - a)
+            tot = 0.0
+            for (lo1, hi1, lo2, hi2) in rects:
+                a0, a1 = _gauss_moments(x[0], lo1, hi1, sig)
+                b0, b1 = _gauss_moments(x[1], lo2, hi2, sig)
+                tot += (a0 * b0, a1 * b0, a0 * b1)[p]
+            return tot
+        return quad(fx, 0.0, 1.0, epsabs=0.0, epsrel=1e-13, limit=200)[0] * h
+    return quad(inner, m * bm.ht, (m + 1) * bm.ht, epsabs=0.0, epsrel=1e-13, limit=200)[0]
+
+
+def _check_moments(bm, dom, rects, rows, tol):
+    M0 = I.assemble(bm, dom)
+    Y = dom.nodes
+    pv = [np.ones(dom.M), Y[:, 0], Y[:, 1]]
+    worst = 0.0
+    for m in range(bm.n_t):
+        for i in rows:
+            for p in range(3):
+                ref = _moment(bm, rects, i, m, p)
+                got = M0[m, i] @ pv[p]
+                worst = max(worst, abs(got - ref) / abs(ref))
+    assert worst <= tol, worst
+
+
+SQUARE = [(0.0, 1.0, 0.0, 1.0)]
+LSHAPE = [(0.0, 1.0, 0.0, 0.5), (0.0, 0.5, 0.5, 1.0)]
+
+
+def test_m0_moments_unit_square():
+    """Paper's setting (alpha = 10, ht = h): every m, rows at corners and
+    side interiors."""
+    n = 4
+    bm = BoundaryMesh(W.unit_square(n), 1.0, n, 10.0)
+    dom = I.DomainMesh(*W.square_triangulation(n), bm)
+    _check_moments(bm, dom, SQUARE, [0, 1, 2, 3, 4, 9, 15], 2e-9)
+
+
+def test_m0_moments_jittered_triangulation():
+    """Irregular triangles (interior nodes moved), alpha = 1, N_t != n."""
+    n = 4
+    bm = BoundaryMesh(W.unit_square(n), 1.0, 6, 1.0)
+    dom = I.DomainMesh(*W.square_triangulation(n, jitter=0.3, seed=11), bm)
+    _check_moments(bm, dom, SQUARE, [0, 2, 5, 11], 2e-9)
+
+
+def test_m0_moments_lshape_reentrant_corner():
+    """L-shape (re-entrant corner at vertex 8 of l_shape(16)): rows at and
+    next to the re-entrant corner."""
+    bm = BoundaryMesh(W.l_shape(16, jitter=(1.0, 1.0)), 1.0, 4, 10.0)
+    dom = I.DomainMesh(*W.lshape_triangulation(4), bm)
+    _check_moments(bm, dom, LSHAPE, [0, 5, 7, 8, 9], 2e-9)
+
+
+def _entry_bruteforce(bm, dom, i, k, c, m, tol=1e-11):
+    """Contribution of triangle k, corner c to M0[m][i][tris[k, c]]: x on
+    gamma_i, y over the triangle as y_1 slices, all by adaptive quadrature."""
+    V = dom.nodes[dom.tris[k]]
+    a, b = bm.a[i], bm.b[i]
+    al, ht = bm.alpha, bm.ht
+    e1v, e2v = V[1] - V[0], V[2] - V[0]
+    det = e1v[0] * e2v[1] - e1v[1] * e2v[0]
+
+    def lam(y1, y2):
+        d0 = np.array([y1, y2]) - V[0]
+        u1 = (d0[0] * e2v[1] - d0[1] * e2v[0]) / det
+        u2 = (e1v[0] * d0[1] - e1v[1] * d0[0]) / det
+        return (1.0 - u1 - u2, u1, u2)[c]
+
+    def dG(r2):
+        v = exp1(al * r2 / (4.0 * (m + 1) * ht))
+        if m > 0:
+            v -= exp1(al * r2 / (4.0 * m * ht))
+        return al / (4.0 * np.pi) * v
+
+    def y2_range(y1):
+        pts = []
+        for p, q in ((0, 1), (1, 2), (0, 2)):
+            P, Q = V[p], V[q]
+            if P[0] != Q[0] and min(P[0], Q[0]) <= y1 <= max(P[0], Q[0]):
+                pts.append(P[1] + (y1 - P[0]) / (Q[0] - P[0]) * (Q[1] - P[1]))
+        return min(pts), max(pts)
+
+    lo1, hi1 = V[:, 0].min(), V[:, 0].max()
+
+    def over_x(s):
+        x = a + s * (b - a)
+
+        def fy1(y1):
+            lo, hi = y2_range(y1)
+            return quad(lambda y2: dG((x[0] - y1) ** 2 + (x[1] - y2) ** 2) * lam(y1, y2), lo, hi,
+                        epsabs=0.0, epsrel=tol, limit=200)[0]
+        pts = [q for q in [x[0]] + V[:, 0].tolist() if lo1 < q < hi1]
+        return quad(fy1, lo1, hi1, points=pts or None, epsabs=0.0, epsrel=tol, limit=200)[0]
+    return quad(over_x, 0.0, 1.0, epsabs=0.0, epsrel=tol, limit=200)[0] * bm.h[i]
+
+
+def _entry_rule(bm, dom, i, k, c, m, cls):
+    r = I.DEFAULT_M0_RULES
+    if cls == I.T_CLS and m == 0:
+        r2, wl = I.polar_points(bm, dom, i, k)
+        return I.G(r2, bm.ht, bm.alpha) @ wl[:, c]
+    order = r.order(I.N_CLS if cls == I.T_CLS else cls, m)
+    r2, wl = I.tensor_points(bm, dom, np.array([i]), np.array([k]), order)
+    dG = I.G(r2, (m + 1) * bm.ht, bm.alpha) - I.G(r2, m * bm.ht, bm.alpha)
+    return float((dG * wl[..., c]).sum())
+
+
+def test_m0_single_entries_against_bruteforce():
+    n = 4
+    bm = BoundaryMesh(W.unit_square(n), 1.0, n, 10.0)
+    dom = I.DomainMesh(*W.square_triangulation(n, jitter=0.2, seed=3), bm)
+    cls = I.classify(bm, dom)
+    i = 1
+    tri = dom.tris
+    shared = [(int(dom.bnode[i]) in t) + (int(dom.bnode[i + 1]) in t) for t in tri]
+    picks = {
+        "edge": next(k for k in range(dom.K) if shared[k] == 2),
+        "vertex": next(k for k in range(dom.K) if shared[k] == 1),
+        "near": next(k for k in range(dom.K) if cls[i, k] == I.N_CLS),
+        "regular": next(k for k in range(dom.K) if cls[i, k] == I.R_CLS),
+    }
+    cases = [("edge", 0, 0), ("edge", 0, 2), ("vertex", 0, 2), ("vertex", 0, 0), ("near", 0, 1),
+             ("regular", 0, 0), ("edge", 1, 1), ("regular", 1, 2)]
+    for name, m, c in cases:
+        k = picks[name]
+        ref = _entry_bruteforce(bm, dom, i, k, c, m, tol=1e-10)
+        got = _entry_rule(bm, dom, i, k, c, m, cls[i, k])
+        assert abs(got - ref) <= 5e-9 * abs(ref), (name, m, c, got, ref)
+
+
+def test_classes_and_domain_validation():
+    n = 4
+    bm = BoundaryMesh(W.unit_square(n), 1.0, n, 10.0)
+    nodes, tris = W.square_triangulation(n)
+    dom = I.DomainMesh(nodes, tris, bm)
+    cls = I.classify(bm, dom)
+    # touching pairs: exactly the triangles with x_i or x_{i+1} as a vertex
+    for i in range(bm.N):
+        ends = {int(dom.bnode[i]), int(dom.bnode[(i + 1) % bm.N])}
+        for k in range(dom.K):
+            assert (cls[i, k] == I.T_CLS) == bool(ends & set(dom.tris[k].tolist()))
+    # every boundary vertex is snapped onto its node exactly
+    assert np.array_equal(dom.nodes[dom.bnode], bm.X)
+    with pytest.raises(ValueError):
+        I.DomainMesh(nodes, tris[:, ::-1], bm)                 # clockwise triangles
+    with pytest.raises(ValueError):
+        I.DomainMesh(nodes * 1.01, tris, bm)                   # not conforming
+    with pytest.raises(ValueError):
+        I.DomainMesh(nodes, np.where(tris == 3, nodes.shape[0], tris), bm)
+
+
+def test_planewave_data_against_quadrature():
+    """g is the time average of u(x_p, .); Q_h w the element average of
+    w = d_n u = exp(-t/alpha) cos(x . d) (d . n)."""
+    th = np.pi / 8
+    d = np.array([np.cos(th), np.sin(th)])
+    bm = BoundaryMesh(W.l_shape(16, seed=3), 1.0, 5, 10.0)
+    al, ht = bm.alpha, bm.ht
+    g = I.planewave_g(bm, th)
+    wq = I.planewave_w_projection(bm, th)
+    for n_ in (0, 4):
+        for p in (0, 7, 11):
+            ref = quad(lambda t: np.exp(-t / al) * np.sin(bm.X[p] @ d), n_ * ht, (n_ + 1) * ht,
+                       epsabs=0.0, epsrel=1e-13)[0] / ht
+            assert abs(g[n_, p] - ref) <= 1e-13 * abs(ref) + 1e-16
+            i = p
+            ref = dblquad(lambda s, t: np.exp(-t / al) * np.cos((bm.a[i] + s * (bm.b[i] - bm.a[i])) @ d)
+                          * (bm.n[i] @ d), n_ * ht, (n_ + 1) * ht, 0.0, 1.0, epsabs=0.0, epsrel=1e-13)[0]
+            ref /= ht
+            assert abs(wq[n_, i] - ref) <= 1e-12 * abs(ref) + 1e-15
+
+
+def _section4(L):
+    n = 2 ** L
+    bm = BoundaryMesh(W.unit_square(n), 1.0, n, 10.0)
+    dom = I.DomainMesh(*W.square_triangulation(n), bm)
+    V = assembly.assemble('V', bm)
+    K = assembly.assemble('K', bm)
+    D = assembly.assemble('D', bm)
+    M0 = I.assemble(bm, dom)
+    g = I.planewave_g(bm)
+    f = rhs.f_vec(bm, K, g) - I.apply(M0, I.planewave_u0(dom))
+    return bm, V, K, D, g, f
+
+
+def test_section4_example_converges_and_matches_table1():
+    """Q = (0,1)^3, alpha = 10, u = exp(-t/alpha) sin(x1 cos(pi/8) + x2
+    sin(pi/8)), levels L = 2, 3 (N = 64, 256): the error of w_h against the
+    exact Neumann datum falls faster than h, and is O(1) without M_h^0 u_0.
+    GMRES (1e-8) without preconditioner takes Table 1's counts within one;
+    with the lumped preconditioner M^-1 D_h M^-1 the counts stay within 4 of
+    the paper's (the paper's quadrature and GMRES details are not given)."""
+    tab = np.loadtxt(os.path.join(HERE, 'golden', 'table1_gmres_iterations.txt'))
+    errs = []
+    for L in (2, 3):
+        bm, V, K, D, g, f = _section4(L)
+        w = solve.forward_substitution(V, f)
+        wex = I.planewave_w_projection(bm)
+        errs.append(rhs.l2_rel_error(bm, w, wex))
+        w0 = solve.forward_substitution(V, rhs.f_vec(bm, K, g))
+        assert rhs.l2_rel_error(bm, w0, wex) > 1.0
+        Lm = assembly.lumped_dual_mass(bm)
+        A = lambda v: solve.toeplitz_apply(V, v)                     # noqa: E731
+        P = lambda v: solve.toeplitz_apply(D, v / Lm) / Lm            # noqa: E731
+        plain = solve.gmres(A, f, None, tol=1e-8)[1]
+        prec = solve.gmres(A, f, P, tol=1e-8)[1]
+        row = tab[tab[:, 0] == L][0]
+        assert int(row[1]) == bm.N * bm.n_t
+        assert abs(plain - row[2]) <= 1, (L, plain, row[2])
+        assert abs(prec - row[3]) <= 4 and prec <= plain, (L, prec, row[3])
+    assert errs[1] < errs[0] and np.log2(errs[0] / errs[1]) > 1.0, errs
+    assert errs[1] < 0.02

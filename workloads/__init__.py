@@ -14,7 +14,11 @@ sizes are the workloads this repository is measured on:
 * ``l_shape``       -- [0,1]^2 minus [0.5,1]^2 with seeded segment lengths;
 * ``star``          -- a star polygon with seeded radii, every edge subdivided;
 * ``annulus_sources`` -- seeded source points y_k outside the domain;
-* ``ragged_squares``  -- seeded (N_x, N_t) pairs for a ragged batch.
+* ``ragged_squares``  -- seeded (N_x, N_t) pairs for a ragged batch;
+* ``square_triangulation`` -- a P1 triangulation Omega_h of [0,1]^2 whose
+  boundary nodes are the vertices of ``unit_square`` (for the initial datum);
+* ``lshape_triangulation``  -- the same grid on the L-shape, conforming with
+  ``l_shape(4 n, jitter=(1, 1))`` (equal segments).
 
 All random draws use ``numpy.random.default_rng(seed)``.
 """
@@ -33,6 +37,8 @@ __all__ = [
     "star",
     "annulus_sources",
     "ragged_squares",
+    "square_triangulation",
+    "lshape_triangulation",
     "config",
     "CONFIG_NAMES",
 ]
@@ -170,6 +176,58 @@ def ragged_squares(n_problems: int = 64, seed: int = 41, k_range=(16, 128),
     ks = rng.integers(k_range[0], k_range[1] + 1, size=n_problems)
     nts = rng.integers(nt_range[0], nt_range[1] + 1, size=n_problems)
     return [(int(4 * k), int(nt)) for k, nt in zip(ks, nts)]
+
+
+def square_triangulation(n_per_side: int, jitter: float = 0.0, seed: int = 7):
+    """Triangulation of [0,1]^2: (n+1)^2 grid nodes, 2 n^2 triangles.
+
+    Node (k, l) sits at (k/n, l/n), index l (n+1) + k.  Cell (k, l) is split
+    along its diagonal from (k, l) to (k+1, l+1); both triangles are listed
+    counter-clockwise.  With ``jitter`` > 0 every interior node moves by a
+    seeded uniform offset of at most ``jitter`` / n per coordinate (jitter <
+    0.5 keeps every triangle positively oriented).  The boundary nodes are the
+    vertices of ``unit_square(n)`` (equal up to rounding of the side
+    parametrisation).  Returns (nodes (M, 2) float64, tris (2 n^2, 3) int64).
+    """
+    n = int(n_per_side)
+    g = np.arange(n + 1, dtype=np.float64) / n
+    X, Y = np.meshgrid(g, g)            # X[l, k] = k/n, Y[l, k] = l/n
+    nodes = np.stack([X.ravel(), Y.ravel()], axis=1)
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        inner = (X.ravel() > 0) & (X.ravel() < 1) & (Y.ravel() > 0) & (Y.ravel() < 1)
+        off = rng.uniform(-jitter / n, jitter / n, size=(int(inner.sum()), 2))
+        nodes[inner] += off
+    tris = []
+    for l in range(n):
+        for k in range(n):
+            p00 = l * (n + 1) + k
+            p10, p01, p11 = p00 + 1, p00 + n + 1, p00 + n + 2
+            tris.append((p00, p10, p11))
+            tris.append((p00, p11, p01))
+    return nodes, np.asarray(tris, dtype=np.int64)
+
+
+def lshape_triangulation(n_per_unit: int):
+    """Triangulation of [0,1]^2 minus [0.5,1]^2 on the grid of spacing 1/n
+    (n even): the cells of ``square_triangulation(n)`` outside the removed
+    quadrant, with the unused nodes dropped.  Its boundary nodes are the
+    vertices of ``l_shape(4 n, jitter=(1, 1))``.  Returns (nodes, tris)."""
+    n = int(n_per_unit)
+    if n % 2:
+        raise ValueError("lshape_triangulation needs an even n")
+    nodes, tris = square_triangulation(n)
+    keep = []
+    for l in range(n):
+        for k in range(n):
+            if not (k >= n // 2 and l >= n // 2):
+                c = 2 * (l * n + k)
+                keep += [c, c + 1]
+    tris = tris[keep]
+    used = np.unique(tris)
+    remap = -np.ones(nodes.shape[0], dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    return nodes[used], remap[tris]
 
 
 CONFIG_NAMES = ("square32", "square64", "square256", "lshape1024", "square512", "star256")
