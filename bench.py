@@ -304,6 +304,126 @@ def run_grad(ctx, dev, stream):
     return out
 
 
+def m0_evaluations(n_x, nodes, tris, n_t, alpha, T=1.0):
+    """Algorithmic count of kernel evaluations G(r, t_k) of the M_h^0 rule on a
+    triangulation: per (segment, triangle) pair and order range [b, e) of the
+    rule, order^3 points times the distinct times t_b .. t_e (t_0 = 0 costs
+    nothing), plus 2*8*3*12*12 polar points per touching pair at m = 0.  The
+    pair classes and orders follow the rule (touching by shared vertex,
+    rho^2 = 4 m ht / (alpha s^2) steps); the near class only changes the
+    order at m = 0 and is counted as regular there (a lower bound)."""
+    ht = T / n_t
+    X = np.asarray(nodes, dtype=np.float64)
+    tr = np.asarray(tris)
+    e = [np.sqrt(((X[tr[:, a]] - X[tr[:, (a + 1) % 3]]) ** 2).sum(1)) for a in range(3)]
+    diam = np.maximum.reduce(e)
+    # unit square boundary: segment length 1 / (n_x / 4); s = max(h, diam)
+    h = 4.0 / n_x
+    s = np.maximum(h, diam)
+    steps = ((1e4, 3), (144.0, 4), (5.0, 6), (1.44, 8), (0.0, 12))
+    tot = 0.0
+    for sk in np.unique(s):
+        cnt = n_x * float((s == sk).sum())
+        orders = []
+        for m in range(1, n_t):
+            r2 = (4.0 * m * ht) / (alpha * sk * sk)
+            orders.append(next(o for thr, o in steps if r2 >= thr))
+        # runs of equal order: points x (steps + 1)
+        m = 0
+        while m < len(orders):
+            o, k = orders[m], m
+            while k < len(orders) and orders[k] == o:
+                k += 1
+            tot += cnt * o ** 3 * (k - m + 1)
+            m = k
+        tot += cnt * 8 ** 3            # m = 0, regular order
+    return tot
+
+
+def run_initial(ctx, dev, stream, L=6):
+    """The paper's Section 4 example at level L (Q = (0,1)^3, alpha = 10,
+    u = exp(-t/alpha) sin(x1 cos(pi/8) + x2 sin(pi/8)), 2^L segments per side,
+    N_t = 2^L, structured triangulation of Omega): times the matrix-free
+    M_h^0 u_0 product and the assembled M_h^0, the whole right-hand side and
+    both GMRES solves; reports the iteration counts next to Table 1's and the
+    error of w_h against the exact Neumann datum."""
+    import torch
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    n = 2 ** L
+    al = 10.0
+    X = W.unit_square(n)
+    nodes, tris = W.square_triangulation(n)
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    e = [ev() for _ in range(6)]
+    e[0].record(stream)
+    mesh = P.Mesh(ctx, X, 1.0, n, al)
+    dom = P.Domain(ctx, mesh, nodes, tris)
+    V = P.assemble(ctx, mesh, "V")
+    K = P.assemble(ctx, mesh, "K")
+    D = P.assemble(ctx, mesh, "D")
+    Lm = P.lumped_mass(ctx, mesh)
+    e[1].record(stream)
+    g, u0 = P.planewave_data(ctx, dom)
+    work = P.api.m0_workspace(ctx, dom)
+    f = P.rhs_initial(ctx, dom, K, g, u0, work=work)
+    e[2].record(stream)
+    w, info = P.solve(ctx, V, f, D, Lm, tol=1e-8)
+    e[3].record(stream)
+    w0, info0 = P.solve(ctx, V, f, tol=1e-8, max_iter=1000)
+    e[4].record(stream)
+    torch.cuda.synchronize(dev)
+    # the M_h^0 product alone (matrix-free), and the stored operator
+    y = torch.zeros((n, 4 * n), dtype=torch.float64, device=dev)
+    k0, k1 = ev(), ev()
+    k0.record(stream)
+    P.m0_apply(ctx, dom, u0, out=y, work=work)
+    k1.record(stream)
+    torch.cuda.synchronize(dev)
+    asm_ms = None
+    if n * 4 * n * dom.n_nodes * 8 <= 4e9:
+        M0 = torch.empty((n, 4 * n, dom.n_nodes), dtype=torch.float64, device=dev)
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        P.m0_assemble(ctx, dom, M0)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        asm_ms = a0.elapsed_time(a1)
+        del M0
+    # exact Neumann datum w = d_n u averaged over the elements (closed form)
+    th = np.pi / 8
+    dd = np.array([np.cos(th), np.sin(th)])
+    Xb = np.roll(X, -1, axis=0)
+    hseg = np.sqrt(((Xb - X) ** 2).sum(1))
+    tt = (Xb - X) / hseg[:, None]
+    nn = np.stack([tt[:, 1], -tt[:, 0]], axis=1)
+    t = np.arange(n + 1) / n
+    tavg = al * n * (np.exp(-t[:-1] / al) - np.exp(-t[1:] / al))
+    savg = np.cos(0.5 * (X + Xb) @ dd) * np.sinc(0.5 * hseg * (tt @ dd) / np.pi)
+    wex = tavg[:, None] * (savg * (nn @ dd))[None, :]
+    wn = w.cpu().numpy()
+    wts = hseg[None, :] / n
+    err = float(np.sqrt((wts * (wn - wex) ** 2).sum() / (wts * wex ** 2).sum()))
+    table1 = {2: (14, 17), 3: (19, 18), 4: (24, 20), 5: (35, 20), 6: (50, 20), 7: (67, 20), 8: (91, 19),
+              9: (122, 19)}
+    m0_ms = k0.elapsed_time(k1)
+    evals = m0_evaluations(4 * n, nodes, tris, n, al)
+    out = {
+        "workload": "Section 4 example, level %d: unit square, N_x = %d, N_t = %d, N = %d, alpha = 10, "
+                    "%d nodes / %d triangles" % (L, 4 * n, n, 4 * n * n, dom.n_nodes, dom.n_tris),
+        "m0_apply_ms": m0_ms, "m0_assemble_ms": asm_ms,
+        "m0_kernel_evaluations": evals, "m0_evaluations_per_s": evals / (m0_ms * 1e-3),
+        "setup_assembly_ms": e[0].elapsed_time(e[1]), "rhs_ms": e[1].elapsed_time(e[2]),
+        "gmres_prec_ms": e[2].elapsed_time(e[3]), "gmres_prec_iterations": info["iterations"],
+        "gmres_plain_ms": e[3].elapsed_time(e[4]), "gmres_plain_iterations": info0["iterations"],
+        "table1_iterations": {"plain": table1[L][0], "preconditioned": table1[L][1]},
+        "w_l2_rel_error_vs_exact": err,
+    }
+    del V, K, D, w, w0, f, g, u0, y, work
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ragged(ctx, dev, stream):
     """Ragged batch: 64 unit squares with N_x = 4k (k seeded in [16, 128]) and
     N_t seeded in [64, 512] (seed 41), alpha = 1, T = 1, sources seeded on the
@@ -551,6 +671,9 @@ def run_ours(args):
     grad = None
     if not args.no_grad and world == 1:
         grad = run_grad(ctx, dev, stream)
+    initial = None
+    if not args.no_initial and world == 1:
+        initial = run_initial(ctx, dev, stream)
     ragged = None
     if not args.no_ragged and world == 1:
         ragged = run_ragged(ctx, dev, stream)
@@ -605,6 +728,7 @@ def run_ours(args):
             "batched": batched,
             "grad": grad,
             "ragged": ragged,
+            "initial": initial,
         },
         "roofline": {"kernel": "k_tile_ml<D, f64, 4 lags> lags >= 2", "bound": "alu",
                      "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -680,9 +804,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-right-hand-side square512 component")
     ap.add_argument("--no-grad", action="store_true", help="skip the star256 differentiation component")
     ap.add_argument("--no-ragged", action="store_true", help="skip the 64-problem ragged component")
+    ap.add_argument("--no-initial", action="store_true", help="skip the Section 4 example (M_h^0) component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
-    ap.add_argument("--component", choices=["tc", "grad", "precision"], default=None,
+    ap.add_argument("--component", choices=["tc", "grad", "precision", "initial"], default=None,
                     help="run one kernel family alone on a small case (for ncu captures) and print its timing")
     ap.add_argument("--size", type=int, default=256, help="N_x = N_t of --component's case")
     ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --component tc")
@@ -765,6 +890,11 @@ def run_component(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
     if args.component == "precision":
         return run_precision(ctx, dev, stream)
+    if args.component == "initial":
+        # --size is the level L of the Section 4 example (2^L segments per side)
+        res = run_initial(ctx, dev, stream, L=n if n <= 9 else 6)
+        print(json.dumps(res), flush=True)
+        return 0
     if args.component == "tc":
         mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
         Vb = P.to_bf16(ctx, P.assemble(ctx, mesh, "V"))

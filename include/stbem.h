@@ -395,6 +395,53 @@ int stbem_ragged_solve(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void
                        const double* dev_L, const double* dev_f, double* dev_w, const stbem_solve_opts* opts,
                        stbem_solve_info* infos, void* dev_work, size_t work_bytes);
 
+/* ---- Initial datum (Section 1, eq. (4): M_h^0 u_0) ------------------------
+ * The initial datum u_0 is discretised in S_h^1(Omega_h), the continuous
+ * piecewise linear functions on a triangulation of the domain, and
+ *   M_h^0[(m,i), j] = int_{tau_m} int_{gamma_i} int_Omega U*(x - y, t) phi_j(y) dy ds_x dt
+ * (U* the fundamental solution of Section 1, no 1/alpha factor); the
+ * right-hand side of eq. (4) is (1/2 M_h + K_h) g - M_h^0 u_0.  The time
+ * integral is exact (differences of alpha/(4 pi) E1(alpha r^2 / (4 t)) at
+ * t_m, t_{m+1}); space by the repository's rule per (segment, triangle) pair:
+ * tensor Gauss rules whose order depends on the pair class (touching / near /
+ * regular) and on m, a polar rule with a sinh transformation for touching
+ * pairs at m = 0.  Entries are stored dense as M0[m][i][j] (m slowest). */
+typedef struct stbem_domain stbem_domain;
+
+/* Triangulation Omega_h of the domain bounded by mesh.  host_nodes: 2*n_nodes
+ * doubles (x, y pairs); host_tris: 3*n_tris node indices, every triangle
+ * counter-clockwise with positive area.  Every vertex of mesh must coincide
+ * (within 1e-12 of the nodes' bounding-box size) with a node, which is then
+ * moved onto the vertex exactly.  The mesh must outlive the domain.  Errors:
+ * STBEM_ERR_ARG (NULL, too few nodes/triangles, index out of range, a
+ * clockwise or degenerate triangle, a vertex that is not a node),
+ * STBEM_ERR_CUDA. */
+int stbem_domain_create(stbem_ctx* ctx, const stbem_mesh* mesh, const double* host_nodes, int n_nodes,
+                        const int* host_tris, int n_tris, stbem_domain** out);
+void stbem_domain_destroy(stbem_domain* dom);
+/* Sizes, the number of triangle colours (one assembly launch each) and, if
+ * host_bnode is not NULL, the node index of every boundary vertex (n_x ints). */
+int stbem_domain_info(const stbem_domain* dom, int* n_nodes, int* n_tris, int* n_colors, int* host_bnode);
+/* n_t * n_x * n_nodes * sizeof(double). */
+int stbem_m0_bytes(const stbem_domain* dom, size_t* bytes);
+/* dev_M0[m][i][j] (FP64, stbem_m0_bytes, caller-owned): overwritten.
+ * Deterministic (fixed summation order).  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_CUDA. */
+int stbem_m0_assemble(stbem_ctx* ctx, const stbem_domain* dom, double* dev_M0);
+/* Matrix-free product: dev_y[b][m][i] += scale * (M_h^0 dev_u0[b])[m][i] for
+ * b < n_rhs, dev_u0[b] the n_nodes nodal values, computed with the same rule
+ * as stbem_m0_assemble without storing M_h^0.  n_t <= 6144.  Workspace:
+ * stbem_m0_apply_workspace_bytes (per-block partial sums).  Errors:
+ * STBEM_ERR_ARG, STBEM_ERR_NOMEM (workspace too small), STBEM_ERR_CUDA. */
+int stbem_m0_apply_workspace_bytes(const stbem_domain* dom, size_t* bytes);
+int stbem_m0_apply(stbem_ctx* ctx, const stbem_domain* dom, int n_rhs, const double* dev_u0, double scale,
+                   double* dev_y, void* dev_work, size_t work_bytes);
+/* Data of the Section 4 example u(x, t) = exp(-t/alpha) sin(x . d),
+ * d = (cos theta, sin theta) (the paper: theta = pi/8): dev_g[n][p] the time
+ * average of u at vertex p over tau_n, dev_u0[j] = u(y_j, 0) at the nodes.
+ * Either pointer may be NULL.  Errors: STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_planewave_data(stbem_ctx* ctx, const stbem_domain* dom, double theta, double* dev_g, double* dev_u0);
+
 #ifdef __cplusplus
 }
 #endif

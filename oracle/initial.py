@@ -30,9 +30,14 @@ Rules:
     collapsed (conical product) rule on omega, y = v0 + u ((1-v)(v1-v0) +
     v (v2-v0)), dy = 2|omega| u du dv, u and v n-point Gauss-Legendre on
     [0,1]; barycentrics lambda = (1-u, u(1-v), uv);
-  * the order depends on the class and on m through ``order(cls, m)``; the m
-    of one order range share their points, so G is evaluated once per point
-    and time t_m;
+  * m = 0: order 8 (R) or 12 (N);
+  * m >= 1 (every class): the kernel G(., t_{m+1}) - G(., t_m) is an
+    entire function of r^2 whose only length scale is the diffusion length
+    sqrt(4 t_m / alpha), so the order follows rho^2 = 4 m ht / (alpha s^2),
+    s = max(h_i, diam omega): rho^2 >= 1e4, 144, 5, 1.44, else -> order 3,
+    4, 6, 8, 12 (thresholds measured for 1e-11 relative per pair).  rho^2 is
+    a quotient of products (no sums), so every implementation switches at the
+    same m;
   * T at m = 0 (G(., t_1) has a log r singularity where omega touches
     gamma_i): polar rule.  gamma_i is split at its midpoint; a half that ends
     at a shared vertex gets n_outer Gauss points graded toward that vertex
@@ -68,9 +73,14 @@ T_CLS, N_CLS, R_CLS = 2, 1, 0
 
 @dataclass(frozen=True)
 class M0Rules:
-    # (first m, order) steps for the tensor rule, per class
-    orders_R: tuple = ((0, 8), (2, 6), (8, 4))
-    orders_N: tuple = ((0, 12), (2, 8), (8, 6))
+    # m = 0: tensor order per class (touching pairs: polar rule)
+    order0_R: int = 8
+    order0_N: int = 12
+    # m >= 1, every class: order by rho^2 = 4 m ht / (alpha s^2),
+    # s = max(h_i, diam omega) (the diffusion length sqrt(4 t_m / alpha) over
+    # the pair's size): the first (rho^2 threshold, order) step with
+    # rho^2 >= threshold.  Thresholds measured for 1e-11 relative per pair.
+    steps: tuple = ((1e4, 3), (144.0, 4), (5.0, 6), (1.44, 8), (0.0, 12))
     near_ratio: float = 1.0
     n_outer: int = 8        # polar rule: Gauss points per half of gamma_i
     n_radial: int = 12
@@ -78,26 +88,15 @@ class M0Rules:
     grading: int = 3        # rho = v^grading
     degenerate: float = 1e-12   # |A2| <= degenerate L^2: sub-triangle skipped
 
-    def order(self, cls: int, m: int) -> int:
-        steps = self.orders_R if cls == R_CLS else self.orders_N
-        n = steps[0][1]
-        for start, o in steps:
-            if m >= start:
-                n = o
-        return n
-
-    def ranges(self, cls: int, n_t: int):
-        """[(m_begin, m_end, order)] covering the m >= m_first of the class
-        (T and N use the N orders; T's m = 0 goes to the polar rule)."""
-        steps = self.orders_R if cls == R_CLS else self.orders_N
-        first = 1 if cls == T_CLS else 0
-        out = []
-        for k, (start, o) in enumerate(steps):
-            end = steps[k + 1][0] if k + 1 < len(steps) else n_t
-            b, e = max(start, first), min(end, n_t)
-            if b < e:
-                out.append((b, e, o))
-        return out
+    def order(self, cls: int, m: int, rho2: float) -> int:
+        """Tensor order of a pair of class cls at step m (T at m = 0 uses the
+        polar rule instead)."""
+        if m == 0:
+            return self.order0_R if cls == R_CLS else self.order0_N
+        for thr, o in self.steps:
+            if rho2 >= thr:
+                return o
+        raise AssertionError("unreachable")
 
 
 DEFAULT_M0_RULES = M0Rules()
@@ -268,6 +267,12 @@ def polar_points(bmesh, dom, i, k, rules=DEFAULT_M0_RULES):
     return np.concatenate(r2s), np.concatenate(wls)
 
 
+def rho2(bmesh, dom, I, Kt, m):
+    """rho^2 = 4 m ht / (alpha s^2), s = max(h_i, diam_k), for pairs (I, Kt)."""
+    s = np.maximum(bmesh.h[I], dom.diam[Kt])
+    return 4.0 * m * bmesh.ht / (bmesh.alpha * s * s)
+
+
 def assemble(bmesh: BoundaryMesh, dom: DomainMesh, rules=DEFAULT_M0_RULES, magnitude=False, chunk=4096):
     """M0[m][i][j], shape (N_t, N_x, M).  With ``magnitude`` also returns S,
     the same sums with |G(t_{m+1})| + |G(t_m)| in place of the difference
@@ -277,34 +282,35 @@ def assemble(bmesh: BoundaryMesh, dom: DomainMesh, rules=DEFAULT_M0_RULES, magni
     out = np.zeros((nt, N, M))
     mag = np.zeros((nt, N, M)) if magnitude else None
     cls = classify(bmesh, dom, rules)
-    for c in (R_CLS, N_CLS, T_CLS):
-        I, Kt = np.nonzero(cls == c)
-        if I.size == 0:
-            continue
-        for (mb, me, order) in rules.ranges(c, nt):
-            for p0 in range(0, I.size, chunk):
-                Ii, Kk = I[p0:p0 + chunk], Kt[p0:p0 + chunk]
-                r2, wl = tensor_points(bmesh, dom, Ii, Kk, order)
-                Gs = [G(r2, k * ht, al) for k in range(mb, me + 1)]
+    I_all, K_all = np.nonzero(np.ones((N, dom.K), dtype=bool))
+    C_all = cls[I_all, K_all]
+    for m in range(nt):
+        live = C_all != T_CLS if m == 0 else np.ones(C_all.shape, dtype=bool)
+        r2m = rho2(bmesh, dom, I_all, K_all, m)
+        orders = np.array([rules.order(c, m, r) for c, r in zip(C_all, r2m)], dtype=np.int64)
+        for order in np.unique(orders[live]):
+            sel = np.nonzero(live & (orders == order))[0]
+            for p0 in range(0, sel.size, chunk):
+                Ii, Kk = I_all[sel[p0:p0 + chunk]], K_all[sel[p0:p0 + chunk]]
+                r2, wl = tensor_points(bmesh, dom, Ii, Kk, int(order))
+                Gb, Ga = G(r2, (m + 1) * ht, al), G(r2, m * ht, al)
+                val = np.einsum('pq,pqc->pc', Gb - Ga, wl)
                 J = dom.tris[Kk]
-                for m in range(mb, me):
-                    dG = Gs[m - mb + 1] - Gs[m - mb]
-                    val = np.einsum('pq,pqc->pc', dG, wl)
-                    for cc in range(3):
-                        np.add.at(out[m], (Ii, J[:, cc]), val[:, cc])
-                    if magnitude:
-                        sG = np.abs(Gs[m - mb + 1]) + np.abs(Gs[m - mb])
-                        mv = np.einsum('pq,pqc->pc', sG, np.abs(wl))
-                        for cc in range(3):
-                            np.add.at(mag[m], (Ii, J[:, cc]), mv[:, cc])
-        if c == T_CLS:
-            for i, k in zip(I, Kt):
-                r2, wl = polar_points(bmesh, dom, i, k, rules)
-                val = G(r2, ht, al) @ wl
                 for cc in range(3):
-                    out[0, i, dom.tris[k, cc]] += val[cc]
-                    if magnitude:
-                        mag[0, i, dom.tris[k, cc]] += np.abs(G(r2, ht, al)) @ np.abs(wl[:, cc])
+                    np.add.at(out[m], (Ii, J[:, cc]), val[:, cc])
+                if magnitude:
+                    mv = np.einsum('pq,pqc->pc', np.abs(Gb) + np.abs(Ga), np.abs(wl))
+                    for cc in range(3):
+                        np.add.at(mag[m], (Ii, J[:, cc]), mv[:, cc])
+    # touching pairs, m = 0: polar rule
+    for i, k in zip(*np.nonzero(cls == T_CLS)):
+        r2, wl = polar_points(bmesh, dom, i, k, rules)
+        Gv = G(r2, ht, al)
+        val = Gv @ wl
+        for cc in range(3):
+            out[0, i, dom.tris[k, cc]] += val[cc]
+            if magnitude:
+                mag[0, i, dom.tris[k, cc]] += np.abs(Gv) @ np.abs(wl[:, cc])
     return (out, mag) if magnitude else out
 
 

@@ -82,6 +82,90 @@ class Mesh:
             pass
 
 
+class Domain:
+    """Triangulation Omega_h of the domain bounded by ``mesh`` (nodes (M, 2),
+    triangles (K, 3) counter-clockwise, boundary vertices among the nodes)."""
+
+    def __init__(self, ctx: Context, mesh: Mesh, nodes, tris):
+        nd = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1))
+        tr = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1))
+        self.ctx, self.mesh = ctx, mesh
+        self.n_nodes = nd.size // 2
+        self.n_tris = tr.size // 3
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.stbem_domain_create(ctx.h, mesh.h, nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              self.n_nodes, tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                              self.n_tris, ctypes.byref(h)))
+        self.h = h
+
+    def info(self):
+        """(n_nodes, n_tris, n_colors, bnode) with bnode[p] the node of vertex p."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        bn = np.zeros(self.mesh.n_x, dtype=np.int32)
+        self.ctx.check(self.ctx.lib.stbem_domain_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                                      bn.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return a.value, b.value, c.value, bn
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.stbem_domain_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def m0_assemble(ctx: Context, dom: Domain, out=None):
+    """M_h^0 as M0[m][i][j] (n_t x n_x x n_nodes, FP64)."""
+    if out is None:
+        out = ctx.empty((dom.mesh.n_t, dom.mesh.n_x, dom.n_nodes))
+    ctx.check(ctx.lib.stbem_m0_assemble(ctx.h, dom.h, _ptr(out)))
+    return out
+
+
+def m0_workspace(ctx: Context, dom: Domain):
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_m0_apply_workspace_bytes(dom.h, ctypes.byref(nb)))
+    return torch.empty(max(nb.value, 8), dtype=torch.uint8, device=ctx.device)
+
+
+def m0_apply(ctx: Context, dom: Domain, u0, scale: float = 1.0, out=None, work=None):
+    """out += scale * M_h^0 u0, matrix-free (u0: [n_rhs,] n_nodes; out: [n_rhs,]
+    n_t x n_x, zeros when not given)."""
+    ub = u0 if u0.dim() == 2 else u0.unsqueeze(0)
+    n_rhs = ub.shape[0]
+    if out is None:
+        out = torch.zeros((n_rhs, dom.mesh.n_t, dom.mesh.n_x), dtype=torch.float64, device=ctx.device)
+        ret = out if u0.dim() == 2 else out[0]
+    else:
+        ret = out
+    if work is None:
+        work = m0_workspace(ctx, dom)
+    ctx.check(ctx.lib.stbem_m0_apply(ctx.h, dom.h, n_rhs, _ptr(ub), float(scale), _ptr(out), _ptr(work),
+                                     work.numel()))
+    return ret
+
+
+def planewave_data(ctx: Context, dom: Domain, theta: float = np.pi / 8):
+    """(g, u0) of the Section 4 example u = exp(-t/alpha) sin(x . d)."""
+    g = ctx.empty((dom.mesh.n_t, dom.mesh.n_x))
+    u0 = ctx.empty((dom.n_nodes,))
+    ctx.check(ctx.lib.stbem_planewave_data(ctx.h, dom.h, float(theta), _ptr(g), _ptr(u0)))
+    return g, u0
+
+
+def rhs_initial(ctx: Context, dom: Domain, K, g, u0, work=None):
+    """f = 1/2 M_h g + K_h g - M_h^0 u0 (eq. (4)), M_h^0 u0 matrix-free."""
+    mesh = dom.mesh
+    f = apply(ctx, K, g)
+    ctx.check(ctx.lib.stbem_half_mass_add(ctx.h, mesh.h, 1, _ptr(g), _ptr(f)))
+    m0_apply(ctx, dom, u0, -1.0, out=f, work=work)
+    return f
+
+
 def assemble(ctx: Context, mesh: Mesh, op: str, prec: str = "f64", out=None):
     """Lag blocks A[d][i][j] of op in {'V','K','D'} (n_t x n_x x n_x)."""
     p = PRECS[prec]

@@ -37,6 +37,8 @@ EXPORTS = [
     "stbem_ragged_assemble", "stbem_ragged_lumped_mass", "stbem_ragged_apply_workspace_bytes", "stbem_ragged_apply",
     "stbem_ragged_tune", "stbem_ragged_tune_report", "stbem_ragged_rhs", "stbem_ragged_solve_workspace_bytes",
     "stbem_ragged_solve", "stbem_mixed_mass_inverse",
+    "stbem_domain_create", "stbem_domain_destroy", "stbem_domain_info", "stbem_m0_bytes", "stbem_m0_assemble",
+    "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data",
 ]
 
 
@@ -127,8 +129,18 @@ def load(path: str = LIB_PATH):
     L.stbem_half_mass_add.argtypes = [vp, vp, i, vp, vp]
     L.stbem_solve_batched_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
     L.stbem_solve_batched.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
+    L.stbem_domain_create.argtypes = [vp, vp, P(d), i, P(i), i, P(vp)]
+    L.stbem_domain_destroy.argtypes = [vp]
+    L.stbem_domain_destroy.restype = None
+    L.stbem_domain_info.argtypes = [vp, P(i), P(i), P(i), P(i)]
+    L.stbem_m0_bytes.argtypes = [vp, P(sz)]
+    L.stbem_m0_assemble.argtypes = [vp, vp, vp]
+    L.stbem_m0_apply_workspace_bytes.argtypes = [vp, P(sz)]
+    L.stbem_m0_apply.argtypes = [vp, vp, i, vp, d, vp, vp, sz]
+    L.stbem_planewave_data.argtypes = [vp, vp, d, vp, vp]
     for name in EXPORTS:
-        if name not in ("stbem_version", "stbem_launch_count", "stbem_destroy", "stbem_mesh_destroy", "stbem_last_error"):
+        if name not in ("stbem_version", "stbem_launch_count", "stbem_destroy", "stbem_mesh_destroy", "stbem_last_error",
+                        "stbem_domain_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

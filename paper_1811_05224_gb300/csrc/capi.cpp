@@ -15,6 +15,7 @@
 #include "stbem.h"
 #include "toeplitz.h"
 #include "grad.h"
+#include "initial.h"
 #include "toeplitz_tc.h"
 #include "vec.h"
 
@@ -48,6 +49,7 @@ int stbem_create(stbem_ctx** out, int device, void* stream) {
   stbem::build_rule_tables(&t);
   e = stbem::upload_rule_tables(t, ctx->stream);
   if (e == cudaSuccess) e = stbem::upload_grad_rule_tables(t, ctx->stream);
+  if (e == cudaSuccess) e = stbem::upload_m0_rule_tables(t, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     delete ctx;
@@ -134,6 +136,7 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
   m->ht = T / n_t;
   m->alpha = alpha;
   m->h = h;
+  m->xy.assign(xy, xy + 2 * N);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&m->dbuf, host.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&m->ibuf, dp.size() * sizeof(int));

@@ -21,6 +21,7 @@ struct stbem_mesh {
   int N = 0, n_t = 0;
   double T = 0, ht = 0, alpha = 0;
   std::vector<double> h;     // segment lengths (host copy)
+  std::vector<double> xy;    // vertices (host copy, 2 N)
   double* dbuf = nullptr;    // device geometry
   int* ibuf = nullptr;
   double* sbuf = nullptr;    // lag-0/1 singular-pair moments (2 lags x 3 x 2N x 5)

@@ -172,10 +172,28 @@ STB_HD void e1e2(double z, double* e1, double* e2) {
   }
 }
 
+// E1 alone: the E1 half of e1e2, the same operations in the same order
+// (bitwise the same value), without the E2 work.
 STB_HD double e1_only(double z) {
-  double a, b;
-  e1e2(z, &a, &b);
-  return a;
+  if (z < 1.0) return -kEulerGamma - log(z) + ein_series(z);
+  if (z < 16.0) {
+    const int k = z < 2.0 ? 0 : (z < 4.0 ? 1 : (z < 8.0 ? 2 : 3));
+    const double a = (double)(1 << k);
+    const double t = 2.0 * z / a - 3.0;
+    return cheb_sum(kChebE1[k], t) * exp_neg_fast(z);
+  }
+  const double ez = exp_neg_fast(z);
+  if (z < 700.0) {
+    constexpr int K = 14;
+    double pm = 1.0, qm = 0.0, p = z + 1.0, q = 1.0;
+    for (int j = 1; j <= K; ++j) {
+      const double b = z + 1.0 + 2.0 * (double)j, a = -(double)j * (double)j;
+      const double np = fma(b, p, a * pm), nq = fma(b, q, a * qm);
+      pm = p; qm = q; p = np; q = nq;
+    }
+    return (q / p) * ez;
+  }
+  return cf_backward(z, 1) * ez;
 }
 
 // ---- FP32 versions (mixed-precision assembly) ----------------------------------

@@ -46,6 +46,12 @@ def test_e1_e2_fp64_and_fp32(lib):
     lib.nc_e1e2(_d(z), len(z), _d(e1), _d(e2))
     assert np.max(np.abs(e1 / exp1(z) - 1)) < 4e-15
     assert np.max(np.abs(e2 / expn(2, z) - 1)) < 4e-15
+    # E1 alone: the same operations as the E1 half of e1e2, bitwise
+    zz = np.concatenate([z, np.linspace(690.0, 760.0, 301)])
+    a, b, c = np.zeros_like(zz), np.zeros_like(zz), np.zeros_like(zz)
+    lib.nc_e1e2(_d(zz), len(zz), _d(a), _d(b))
+    lib.nc_e1only(_d(zz), len(zz), _d(c))
+    assert np.array_equal(a, c)
     zf = z[z < 85].astype(np.float32)
     f1, f2 = np.zeros_like(zf), np.zeros_like(zf)
     P = ctypes.POINTER(ctypes.c_float)
@@ -61,7 +67,7 @@ def test_ein_and_gauss_tables(lib):
     lib.nc_ein(_d(z), len(z), _d(out))
     ref = exp1(z) + np.euler_gamma + np.log(z)     # Ein = E1 + gamma + ln z
     assert np.max(np.abs(out - ref)) < 4e-16 * 4
-    for n in (4, 6, 8, 12, 16):
+    for n in (3, 4, 6, 8, 12, 16):
         x, w = np.zeros(n), np.zeros(n)
         lib.nc_gauss(n, _d(x), _d(w))
         xr, wr = np.polynomial.legendre.leggauss(n)

@@ -93,6 +93,16 @@ def test_m0_moments_jittered_triangulation():
     _check_moments(bm, dom, SQUARE, [0, 2, 5, 11], 2e-9)
 
 
+def test_m0_moments_smooth_regime():
+    """alpha = 0.002: the diffusion length exceeds the pairs' size by 36x at
+    m = 1, so the rule steps down to orders 4 and 3."""
+    n = 4
+    bm = BoundaryMesh(W.unit_square(n), 1.0, 12, 0.002)
+    dom = I.DomainMesh(*W.square_triangulation(n, jitter=0.2, seed=5), bm)
+    assert I.DEFAULT_M0_RULES.order(I.R_CLS, 8, I.rho2(bm, dom, np.array([0]), np.array([9]), 8)[0]) == 3
+    _check_moments(bm, dom, SQUARE, [0, 3, 6], 2e-9)
+
+
 def test_m0_moments_lshape_reentrant_corner():
     """L-shape (re-entrant corner at vertex 8 of l_shape(16)): rows at and
     next to the re-entrant corner."""
@@ -149,7 +159,7 @@ def _entry_rule(bm, dom, i, k, c, m, cls):
     if cls == I.T_CLS and m == 0:
         r2, wl = I.polar_points(bm, dom, i, k)
         return I.G(r2, bm.ht, bm.alpha) @ wl[:, c]
-    order = r.order(I.N_CLS if cls == I.T_CLS else cls, m)
+    order = r.order(I.N_CLS if cls == I.T_CLS else cls, m, I.rho2(bm, dom, np.array([i]), np.array([k]), m)[0])
     r2, wl = I.tensor_points(bm, dom, np.array([i]), np.array([k]), order)
     dG = I.G(r2, (m + 1) * bm.ht, bm.alpha) - I.G(r2, m * bm.ht, bm.alpha)
     return float((dG * wl[..., c]).sum())
