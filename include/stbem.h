@@ -436,6 +436,24 @@ int stbem_m0_assemble(stbem_ctx* ctx, const stbem_domain* dom, double* dev_M0);
 int stbem_m0_apply_workspace_bytes(const stbem_domain* dom, size_t* bytes);
 int stbem_m0_apply(stbem_ctx* ctx, const stbem_domain* dom, int n_rhs, const double* dev_u0, double scale,
                    double* dev_y, void* dev_work, size_t work_bytes);
+/* Evaluation of u in Q by the representation formula (Section 1, eq. (2)):
+ *   u_h(x, t) = int_Omega U*(x - y, t) u0_h(y) dy + 1/alpha int_Sigma U* w_h
+ *             - 1/alpha int_Sigma d_{n_y} U* g_h
+ * at n_points points dev_xy[2p], [2p+1] and times dev_t[p] (device arrays),
+ * with w_h = dev_w[n][i] (piecewise constant, e.g. the solution of
+ * stbem_solve), g_h = dev_g[n][p] (vertex values per step, as stbem_rhs and
+ * stbem_planewave_data produce) and u0_h = dev_u0[j] on dom's nodes (dom and
+ * dev_u0 NULL: u_0 = 0).  Time integrals exact; space by the repository's
+ * rule: 16 / 12 / 8 Gauss points per segment at distance below 2 h / 4 h /
+ * beyond, and per triangle the collapsed rule with the order of the M_h^0
+ * step table at rho^2 = 4 t / (alpha diam^2).  Meant for points inside the
+ * domain at least half a segment from the boundary, 0 < t <= T (no check of
+ * the points; the times are not checked against T).  dev_u: n_points values.
+ * Errors: STBEM_ERR_ARG (NULL arrays, u0 without a domain, a domain of
+ * another mesh), STBEM_ERR_CUDA. */
+int stbem_evaluate(stbem_ctx* ctx, const stbem_mesh* mesh, const stbem_domain* dom, int n_points,
+                   const double* dev_xy, const double* dev_t, const double* dev_w, const double* dev_g,
+                   const double* dev_u0, double* dev_u);
 /* Data of the Section 4 example u(x, t) = exp(-t/alpha) sin(x . d),
  * d = (cos theta, sin theta) (the paper: theta = pi/8): dev_g[n][p] the time
  * average of u at vertex p over tau_n, dev_u0[j] = u(y_j, 0) at the nodes.

@@ -157,6 +157,20 @@ def planewave_data(ctx: Context, dom: Domain, theta: float = np.pi / 8):
     return g, u0
 
 
+def evaluate(ctx: Context, mesh: Mesh, points, times, w, g, dom: Domain = None, u0=None):
+    """u_h at interior points (P x 2) and times (P,) by the representation
+    formula, eq. (2), from w (n_t x n_x), g (n_t x n_x) and, with a domain,
+    the nodal initial datum u0.  points and times may be host arrays."""
+    pts = torch.as_tensor(np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 2)) if not
+                          torch.is_tensor(points) else points, dtype=torch.float64).to(ctx.device).contiguous()
+    ts = torch.as_tensor(np.ascontiguousarray(np.asarray(times, dtype=np.float64).reshape(-1)) if not
+                         torch.is_tensor(times) else times, dtype=torch.float64).to(ctx.device).contiguous()
+    out = ctx.empty((ts.numel(),))
+    ctx.check(ctx.lib.stbem_evaluate(ctx.h, mesh.h, dom.h if dom is not None else None, ts.numel(), _ptr(pts),
+                                     _ptr(ts), _ptr(w), _ptr(g), _ptr(u0), _ptr(out)))
+    return out
+
+
 def rhs_initial(ctx: Context, dom: Domain, K, g, u0, work=None):
     """f = 1/2 M_h g + K_h g - M_h^0 u0 (eq. (4)), M_h^0 u0 matrix-free."""
     mesh = dom.mesh

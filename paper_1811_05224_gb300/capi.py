@@ -38,7 +38,7 @@ EXPORTS = [
     "stbem_ragged_tune", "stbem_ragged_tune_report", "stbem_ragged_rhs", "stbem_ragged_solve_workspace_bytes",
     "stbem_ragged_solve", "stbem_mixed_mass_inverse",
     "stbem_domain_create", "stbem_domain_destroy", "stbem_domain_info", "stbem_m0_bytes", "stbem_m0_assemble",
-    "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data",
+    "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data", "stbem_evaluate",
 ]
 
 
@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
     L.stbem_m0_apply_workspace_bytes.argtypes = [vp, P(sz)]
     L.stbem_m0_apply.argtypes = [vp, vp, i, vp, d, vp, vp, sz]
     L.stbem_planewave_data.argtypes = [vp, vp, d, vp, vp]
+    L.stbem_evaluate.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("stbem_version", "stbem_launch_count", "stbem_destroy", "stbem_mesh_destroy", "stbem_last_error",
                         "stbem_domain_destroy"):

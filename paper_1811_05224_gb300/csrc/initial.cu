@@ -425,6 +425,120 @@ __global__ void k_planewave(DevMesh M, DevDomain D, double ct, double st, double
   if (u0 && t < D.M) u0[t] = sin(D.nx[t] * ct + D.ny[t] * st);
 }
 
+// ---- evaluation of u in Q by the representation formula, eq. (2) ----------
+//
+// u_h(x, t) = sum_j u0_j int_Omega U*(x - y, t) phi_j dy
+//           + 1/alpha sum_{n, i} w[n][i] int_{gamma_i} [G(r, s_n) - G(r, s_{n+1})] ds
+//           - 1/alpha sum_{n, p} g[n][p] int_Gamma phi_p [H(r, s_n) - H(r, s_{n+1})] ds,
+// s_n = t - t_n, s_{n+1} = t - min(t_{n+1}, t) (the time integrals exactly),
+// G(r, s) = alpha/(4 pi) E1(alpha r^2 / (4 s)), H(r, s) = alpha q / (2 pi r^2)
+// e^{-alpha r^2 / (4 s)}, q = (x - y) . n_y, both 0 for s <= 0.  Rules: per
+// segment 16 / 12 / 8 Gauss points for dist(x, gamma_i) < 2 h_i / < 4 h_i /
+// beyond; per triangle the collapsed n x n rule with n from the step table at
+// rho^2 = 4 t / (alpha diam^2).  One block per point; threads over segments,
+// then over triangles; G and H are evaluated once per time s_k and shared by
+// the two steps that meet there; fixed-order block reduction.
+
+constexpr int kEvalThreads = 256;
+
+__device__ __forceinline__ int boundary_order(double dist, double h) {
+  return dist < 2.0 * h ? 16 : (dist < 4.0 * h ? 12 : 8);
+}
+
+__device__ __forceinline__ int volume_order(double t, double alpha, double diam) {
+  const double r2 = (4.0 * t) / (alpha * diam * diam);
+  for (int k = 0; k < kM0NSteps; ++k)
+    if (r2 >= m0_step_threshold(k)) return m0_step_order(k);
+  return m0_step_order(kM0NSteps - 1);
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_eval_points(DevMesh M, DevDomain D, int has_volume,
+                                                              const double* __restrict__ xy,
+                                                              const double* __restrict__ tp,
+                                                              const double* __restrict__ w,
+                                                              const double* __restrict__ g,
+                                                              const double* __restrict__ u0,
+                                                              double* __restrict__ u) {
+  __shared__ double red[kEvalThreads / 32];
+  const int p = blockIdx.x;
+  const double x0 = xy[2 * p], x1 = xy[2 * p + 1], t = tp[p];
+  const double al = M.alpha, ht = M.ht;
+  const int N = M.N;
+  int n_last = (int)ceil(t / ht);
+  n_last = n_last < M.n_t ? n_last : M.n_t;
+  const double cG = al / kFourPi, ca = 0.25 * al;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < N; i += kEvalThreads) {
+    const double ax = M.sx0[i], ay = M.sy0[i], bx = M.sx1[i], by = M.sy1[i], h = M.slen[i];
+    const double nx = M.snx[i], ny = M.sny[i];
+    const int nb = boundary_order(pt_seg(x0, x1, ax, ay, bx, by), h);
+    const int go = gauss_offset(nb);
+    const int ip = i + 1 == N ? 0 : i + 1;
+    double si = 0.0;
+    for (int q = 0; q < nb; ++q) {
+      const double xi = c_m0tab.gx[go + q], wq = c_m0tab.gw[go + q] * h;
+      const double dx = x0 - (ax + xi * (bx - ax)), dy = x1 - (ay + xi * (by - ay));
+      const double r2 = dx * dx + dy * dy;
+      const double qn = dx * nx + dy * ny;
+      const double c2 = ca * r2;
+      const double hq = al * qn / (2.0 * kPi * r2);
+      // s_0 = t
+      double Gp = cG * e1_only(c2 / t);
+      double Hp = hq * exp_neg_fast(c2 / t);
+      double sw = 0.0, sg = 0.0;
+      for (int n = 0; n < n_last; ++n) {
+        const double tn1 = (double)(n + 1) * ht;
+        const double s1 = n + 1 < n_last ? t - tn1 : t - (tn1 < t ? tn1 : t);
+        double Gn = 0.0, Hn = 0.0;
+        if (s1 > 0.0) {
+          Gn = cG * e1_only(c2 / s1);
+          Hn = hq * exp_neg_fast(c2 / s1);
+        }
+        sw = fma(w[(size_t)n * N + i], Gp - Gn, sw);
+        const double gv = g[(size_t)n * N + i] * (1.0 - xi) + g[(size_t)n * N + ip] * xi;
+        sg = fma(gv, Hp - Hn, sg);
+        Gp = Gn;
+        Hp = Hn;
+      }
+      si = fma(wq, sw - sg, si);
+    }
+    acc += si / al;
+  }
+  if (has_volume) {
+    const double cU = al / (kFourPi * t);
+    for (int k = threadIdx.x; k < D.K; k += kEvalThreads) {
+      const int j0 = D.tri[3 * k], j1 = D.tri[3 * k + 1], j2 = D.tri[3 * k + 2];
+      const double v0x = D.nx[j0], v0y = D.ny[j0];
+      const double e1x = D.nx[j1] - v0x, e1y = D.ny[j1] - v0y, e2x = D.nx[j2] - v0x, e2y = D.ny[j2] - v0y;
+      const double u00 = u0[j0], u01 = u0[j1], u02 = u0[j2];
+      const int n = volume_order(t, al, D.diam[k]);
+      const int go = gauss_offset(n);
+      double sv = 0.0;
+      for (int a = 0; a < n; ++a) {
+        const double U = c_m0tab.gx[go + a], wu = c_m0tab.gw[go + a] * U;
+        for (int b = 0; b < n; ++b) {
+          const double V = c_m0tab.gx[go + b];
+          const double yx = v0x + U * ((1.0 - V) * e1x + V * e2x);
+          const double yy = v0y + U * ((1.0 - V) * e1y + V * e2y);
+          const double dx = x0 - yx, dy = x1 - yy;
+          const double r2 = dx * dx + dy * dy;
+          const double uh = (1.0 - U) * u00 + U * (1.0 - V) * u01 + U * V * u02;
+          sv = fma(wu * c_m0tab.gw[go + b], cU * exp_neg_fast(ca * r2 / t) * uh, sv);
+        }
+      }
+      acc = fma(2.0 * D.area[k], sv, acc);
+    }
+  }
+  const double ws = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kEvalThreads / 32; ++k) s += red[k];
+    u[p] = s;
+  }
+}
+
 }  // namespace
 
 cudaError_t upload_m0_rule_tables(const RuleTables& t, cudaStream_t s) {
@@ -463,6 +577,16 @@ cudaError_t m0_apply_launch(const DevMesh& M, const DevDomain& D, const double* 
   const long long n = (long long)M.N * M.n_t;
   k_m0_apply_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M.N, M.n_t, nc, part, scale, y);
   count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t evaluate_launch(const DevMesh& M, const DevDomain* D, int n_points, const double* xy, const double* t,
+                            const double* w, const double* g, const double* u0, double* u, cudaStream_t s) {
+  if (n_points <= 0) return cudaSuccess;
+  DevDomain dd{};
+  if (D) dd = *D;
+  k_eval_points<<<n_points, kEvalThreads, 0, s>>>(M, dd, D && u0 ? 1 : 0, xy, t, w, g, u0, u);
+  count_launches(1);
   return cudaGetLastError();
 }
 

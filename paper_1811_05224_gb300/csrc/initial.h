@@ -32,6 +32,11 @@ size_t m0_apply_workspace_bytes(int nt, int N, int K);
 cudaError_t m0_apply_launch(const DevMesh& M, const DevDomain& D, const double* u0, double scale, double* y,
                             void* work, cudaStream_t s);
 
+// u_h at n_points points (xy: 2 n_points) and times t (n_points) by the
+// representation formula, eq. (2); D and u0 may be NULL (u_0 = 0).
+cudaError_t evaluate_launch(const DevMesh& M, const DevDomain* D, int n_points, const double* xy, const double* t,
+                            const double* w, const double* g, const double* u0, double* u, cudaStream_t s);
+
 // Section 4 example u = exp(-t/alpha) sin(x . d), d = (cos theta, sin theta):
 // g[n][p] time averages at the vertices, u0[j] nodal values.
 cudaError_t planewave_launch(const DevMesh& M, const DevDomain& D, double theta, double* g, double* u0,

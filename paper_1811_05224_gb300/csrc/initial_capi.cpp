@@ -244,6 +244,23 @@ int stbem_m0_apply(stbem_ctx* ctx, const stbem_domain* d, int n_rhs, const doubl
   return STBEM_OK;
 }
 
+int stbem_evaluate(stbem_ctx* ctx, const stbem_mesh* mesh, const stbem_domain* d, int n_points,
+                   const double* dev_xy, const double* dev_t, const double* dev_w, const double* dev_g,
+                   const double* dev_u0, double* dev_u) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!mesh) return fail(ctx, STBEM_ERR_ARG, "evaluate: NULL mesh");
+  if (n_points < 0) return fail(ctx, STBEM_ERR_ARG, "evaluate: n_points < 0");
+  if (n_points == 0) return STBEM_OK;
+  if (!dev_xy || !dev_t || !dev_w || !dev_g || !dev_u) return fail(ctx, STBEM_ERR_ARG, "evaluate: NULL array");
+  if (dev_u0 && !d) return fail(ctx, STBEM_ERR_ARG, "evaluate: u0 given without a domain");
+  if (d && d->mesh != mesh) return fail(ctx, STBEM_ERR_ARG, "evaluate: domain built on another mesh");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "evaluate");
+  CUDA_TRY(ctx, stbem::evaluate_launch(mesh->dev, d ? &d->dev : nullptr, n_points, dev_xy, dev_t, dev_w, dev_g,
+                                       dev_u0, dev_u, ctx->stream),
+           "evaluate launch");
+  return STBEM_OK;
+}
+
 int stbem_planewave_data(stbem_ctx* ctx, const stbem_domain* d, double theta, double* dev_g, double* dev_u0) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!d) return fail(ctx, STBEM_ERR_ARG, "planewave_data: NULL domain");
