@@ -14,7 +14,7 @@
 // 31 consecutive times t_{m0} .. t_{m0+31}; the points are computed 32 at a
 // time, one per lane, and broadcast by shuffles; lane l evaluates
 // G(t_{m0+l}) and takes G(t_{m0+l-1}) from lane l - 1.  The remaining steps
-// (and m = 0) in chunks of up to 6: lanes over the rule's points, per-lane
+// (and m = 0) in chunks of up to 3: lanes over the rule's points, per-lane
 // sums per step, one warp reduction per step.
 //
 // Assembly writes M0[m][i][j] += for the three vertices of the triangle; it is
@@ -35,9 +35,15 @@ namespace {
 
 __constant__ RuleTables c_m0tab;
 
+#ifndef STBEM_M0_MINB
+#define STBEM_M0_MINB 5     // resident blocks per SM the pair kernels are compiled for
+#endif
 constexpr int kM0Warps = 4;
 constexpr int kM0Threads = 32 * kM0Warps;
-constexpr int kShortMax = 6;        // steps per chunk of the points-per-lane path
+#ifndef STBEM_M0_SHORT
+#define STBEM_M0_SHORT 3    // steps per chunk of the points-per-lane path
+#endif
+constexpr int kShortMax = STBEM_M0_SHORT;
 constexpr int kApplyChunk = 64;     // triangles per block of the product
 
 enum { kClsR = 0, kClsN = 1, kClsT = 2 };
@@ -354,7 +360,7 @@ __device__ void pair_unit(const DevMesh& M, const DevDomain& D, int i, int k, co
   }
 }
 
-__global__ void __launch_bounds__(kM0Threads) k_m0_assemble(DevMesh M, DevDomain D, const int* __restrict__ tris,
+__global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_assemble(DevMesh M, DevDomain D, const int* __restrict__ tris,
                                                             int n_tris, double* __restrict__ M0) {
   const long long unit = (long long)blockIdx.x * kM0Warps + (threadIdx.x >> 5);
   if (unit >= (long long)M.N * n_tris) return;
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(kM0Threads) k_m0_assemble(DevMesh M, DevDomain
 
 // block (chunk, i): triangles chunk*kApplyChunk .. +kApplyChunk, warp w takes
 // every kM0Warps-th; per-warp rows of per-m sums, then the block's sum.
-__global__ void __launch_bounds__(kM0Threads) k_m0_apply(DevMesh M, DevDomain D, const double* __restrict__ u0,
+__global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_apply(DevMesh M, DevDomain D, const double* __restrict__ u0,
                                                          double* __restrict__ part, int n_chunks) {
   extern __shared__ double ysm[];    // kM0Warps x n_t
   const int chunk = blockIdx.x, i = blockIdx.y;
