@@ -1,13 +1,18 @@
 """Generate expint_cheb.inc: Chebyshev coefficients of A(z) = e^z E1(z) and
-B(z) = e^z E2(z) on [1,2], [2,4], [4,8], [8,16]; the Horner coefficients of
-the Ein series; the constants and 2^{-j/256} table of the table-driven e^{-x}.
+B(z) = e^z E2(z) on [1, 16); the Horner coefficients of the Ein series; the
+constants and 2^{-j/256} table of the table-driven e^{-x}.
 
-Each function is interpolated at the 26 Chebyshev points of the first kind of
-the interval, in 40-digit arithmetic (mpmath), and the coefficients of
-    f(z) = c_0 / 2 + sum_{k=1}^{25} c_k T_k(t),  t = (2 z - a - b) / (b - a)
-are written as double literals.  On each interval the nearest singularity of
-A and B is the log branch point at z = 0, three half-widths from the centre,
-so the coefficients decay like (3 + sqrt 8)^{-k}: 26 terms reach ~1e-19.
+FP64: eight intervals [a_k, a_{k+1}], a_k the double nearest 2^{k/2}
+(ratio sqrt 2).  The device maps z to t = fma(z, s_k, o_k) with the double
+constants s_k = 2 / (a_{k+1} - a_k), o_k = -(a_k + a_{k+1}) / (a_{k+1} - a_k);
+the coefficients are fitted through that same map, z = (t - o_k) / s_k, at
+the Chebyshev points of the first kind, in 40-digit arithmetic (mpmath):
+    f = c_0 / 2 + sum_{k>=1} c_k T_k(t).
+On each interval the nearest singularity of A and B is the log branch point
+at z = 0, (1 + sqrt 2) / (sqrt 2 - 1) = 5.83 half-widths from the centre, so
+the coefficients decay like 11.66^{-k}: 18 terms reach ~1e-19.
+FP32: the leading 12 coefficients on the four intervals [1,2], [2,4], [4,8],
+[8,16] (26-point fits).
 
 Run from the repository root:  python paper_1811_05224_gb300/csrc/gen_expint_tables.py
 """
@@ -16,13 +21,39 @@ import os
 import mpmath as mp
 
 mp.mp.dps = 40
-NC = 26
+NC = 18
+NC_F32_FIT = 26
 NCF = 12
 NEIN = 18
 INTERVALS = [(1, 2), (2, 4), (4, 8), (8, 16)]
+N_INT64 = 8
 
 
-def cheb_coeffs(f, a, b, n=NC):
+def f64_intervals():
+    """Endpoints a_k (doubles nearest 2^{k/2}) and the device's map constants."""
+    a = [float(mp.power(2, mp.mpf(k) / 2)) for k in range(N_INT64 + 1)]
+    out = []
+    for k in range(N_INT64):
+        lo, hi = a[k], a[k + 1]
+        s = 2.0 / (hi - lo)
+        o = -(lo + hi) / (hi - lo)
+        out.append((lo, hi, s, o))
+    return out
+
+
+def cheb_coeffs_map(f, s, o, n=NC):
+    """Chebyshev coefficients in t of f((t - o) / s) on t in [-1, 1]."""
+    s, o = mp.mpf(s), mp.mpf(o)
+    nodes = [mp.cos(mp.pi * (j + mp.mpf(1) / 2) / n) for j in range(n)]
+    vals = [f((t - o) / s) for t in nodes]
+    out = []
+    for k in range(n):
+        acc = mp.fsum(v * mp.cos(k * mp.pi * (j + mp.mpf(1) / 2) / n) for j, v in enumerate(vals))
+        out.append(2 * acc / n)
+    return out
+
+
+def cheb_coeffs(f, a, b, n=NC_F32_FIT):
     nodes = [mp.cos(mp.pi * (j + mp.mpf(1) / 2) / n) for j in range(n)]
     vals = [f((b - a) / mp.mpf(2) * t + (a + b) / mp.mpf(2)) for t in nodes]
     out = []
@@ -35,18 +66,27 @@ def cheb_coeffs(f, a, b, n=NC):
 def main():
     A = lambda z: mp.e ** z * mp.e1(z)            # noqa: E731
     B = lambda z: mp.e ** z * mp.expint(2, z)     # noqa: E731
+    iv = f64_intervals()
     lines = ["// Generated by gen_expint_tables.py: Chebyshev coefficients of",
-             "// A(z) = e^z E1(z) and B(z) = e^z E2(z), %d terms per interval," % NC,
-             "// intervals [1,2], [2,4], [4,8], [8,16]; f = c0/2 + sum_k c_k T_k(t).",
+             "// A(z) = e^z E1(z) and B(z) = e^z E2(z) on [1, 16): FP64 %d terms on each of" % NC,
+             "// %d intervals [a_k, a_{k+1}] (a_k = 2^{k/2}), t = fma(z, kChebS[k], kChebO[k]);" % N_INT64,
+             "// FP32 %d terms on [1,2], [2,4], [4,8], [8,16]; f = c0/2 + sum_k c_k T_k(t)." % NCF,
              "#pragma once", "namespace stbem {",
              "constexpr int kChebN = %d;" % NC,
-             "constexpr int kChebIntervals = %d;" % len(INTERVALS)]
+             "constexpr int kChebIntervals = %d;" % N_INT64]
+    r = lambda x: repr(float(x))               # noqa: E731  shortest round-trip double literal
+    lines.append("static __constant__ const double kChebSplit[4] = {%s};" % ", ".join(r(iv[2 * e][1]) for e in range(4)))
+    lines.append("static __constant__ const double kChebS[%d] = {%s};" % (N_INT64, ", ".join(r(x[2]) for x in iv)))
+    lines.append("static __constant__ const double kChebO[%d] = {%s};" % (N_INT64, ", ".join(r(x[3]) for x in iv)))
+    tails = []
     for name, f in (("kChebE1", A), ("kChebE2", B)):
-        lines.append("static __constant__ const double %s[%d][%d] = {" % (name, len(INTERVALS), NC))
-        for a, b in INTERVALS:
-            c = cheb_coeffs(f, mp.mpf(a), mp.mpf(b))
+        lines.append("static __constant__ const double %s[%d][%d] = {" % (name, N_INT64, NC))
+        for lo, hi, sk, ok in iv:
+            c = cheb_coeffs_map(f, sk, ok)
+            tails.append(abs(c[-1] / c[0]))
             lines.append("  {" + ", ".join(mp.nstr(x, 20, min_fixed=0, max_fixed=0) for x in c) + "},")
         lines.append("};")
+    print("largest |c_last / c_0|: %.2e" % max(tails))
     # FP32 copies: the leading 12 coefficients (the tail is below 2e-9 of c0)
     for name, f in (("kChebE1f", A), ("kChebE2f", B)):
         lines.append("static __constant__ const float %s[%d][%d] = {" % (name, len(INTERVALS), NCF))

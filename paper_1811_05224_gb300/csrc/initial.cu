@@ -45,6 +45,7 @@ constexpr int kM0Threads = 32 * kM0Warps;
 #endif
 constexpr int kShortMax = STBEM_M0_SHORT;
 constexpr int kApplyChunk = 64;     // triangles per block of the product
+constexpr int kGCarry = 512;        // points whose G(t) a warp carries between step groups
 
 enum { kClsR = 0, kClsN = 1, kClsT = 2 };
 
@@ -246,8 +247,11 @@ struct Sink {
   }
 };
 
+// gc: this warp's kGCarry doubles of shared memory (G at the first time of
+// the next step group, per point, for ranges of at most kGCarry points)
 template <bool APPLY>
-__device__ void pair_unit(const DevMesh& M, const DevDomain& D, int i, int k, const Sink<APPLY>& sink) {
+__device__ void pair_unit(const DevMesh& M, const DevDomain& D, int i, int k, const Sink<APPLY>& sink,
+                          double* gc) {
   constexpr int NV = APPLY ? 1 : 3;
   const int lane = threadIdx.x & 31;
   Seg S;
@@ -332,12 +336,15 @@ __device__ void pair_unit(const DevMesh& M, const DevDomain& D, int i, int k, co
 #pragma unroll
       for (int mm = 0; mm < kShortMax; ++mm)
         for (int c = 0; c < NV; ++c) acc[mm][c] = 0.0;
+      const bool carry = nq <= kGCarry;
       for (int q = lane; q < nq; q += 32) {
         double r2, wl[3], v[3];
         tensor_point(S, T, n, q, &r2, wl);
         contract(wl, v);
         const double c2 = ca * r2;
-        double Gp = c0 == 0 ? 0.0 : e1_only(c2 * inv_t[0]);
+        // G(t_{c0}): 0 at t_0, carried from the previous group of this range
+        // (same time, same value), else evaluated
+        double Gp = c0 == 0 ? 0.0 : (carry && c0 > e_long ? gc[q] : e1_only(c2 * inv_t[0]));
 #pragma unroll
         for (int mm = 0; mm < kShortMax; ++mm) {
           if (c0 + mm < ce) {
@@ -347,6 +354,7 @@ __device__ void pair_unit(const DevMesh& M, const DevDomain& D, int i, int k, co
             Gp = Gn;
           }
         }
+        if (carry) gc[q] = Gp;
       }
 #pragma unroll
       for (int mm = 0; mm < kShortMax; ++mm) {
@@ -362,6 +370,7 @@ __device__ void pair_unit(const DevMesh& M, const DevDomain& D, int i, int k, co
 
 __global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_assemble(DevMesh M, DevDomain D, const int* __restrict__ tris,
                                                             int n_tris, double* __restrict__ M0) {
+  __shared__ double gcache[kM0Warps * kGCarry];
   const long long unit = (long long)blockIdx.x * kM0Warps + (threadIdx.x >> 5);
   if (unit >= (long long)M.N * n_tris) return;
   const int i = (int)(unit / n_tris);
@@ -373,7 +382,7 @@ __global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_assemble(DevMe
   sink.i = i;
   for (int c = 0; c < 3; ++c) sink.j[c] = D.tri[3 * k + c];
   sink.ysm = nullptr;
-  pair_unit<false>(M, D, i, k, sink);
+  pair_unit<false>(M, D, i, k, sink, gcache + (threadIdx.x >> 5) * kGCarry);
 }
 
 // block (chunk, i): triangles chunk*kApplyChunk .. +kApplyChunk, warp w takes
@@ -381,6 +390,7 @@ __global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_assemble(DevMe
 __global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_apply(DevMesh M, DevDomain D, const double* __restrict__ u0,
                                                          double* __restrict__ part, int n_chunks) {
   extern __shared__ double ysm[];    // kM0Warps x n_t
+  __shared__ double gcache[kM0Warps * kGCarry];
   const int chunk = blockIdx.x, i = blockIdx.y;
   const int nt = M.n_t;
   for (int t = threadIdx.x; t < kM0Warps * nt; t += kM0Threads) ysm[t] = 0.0;
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(kM0Threads, STBEM_M0_MINB) k_m0_apply(DevMesh 
       sink.j[c] = D.tri[3 * k + c];
       sink.u[c] = u0[sink.j[c]];
     }
-    pair_unit<true>(M, D, i, k, sink);
+    pair_unit<true>(M, D, i, k, sink, gcache + w * kGCarry);
     __syncwarp();
   }
   __syncthreads();

@@ -3,9 +3,10 @@
 //  * z < 1: E1(z) = -gamma - ln z + Ein(z), Ein(z) = sum_{k>=1} (-1)^{k+1} z^k/(k k!)
 //    (Abramowitz & Stegun 5.1.11), and E2(z) = e^{-z} - z E1(z) (A&S 5.1.14);
 //    e^{-z} here and below from exp_neg_fast;
-//  * 1 <= z < 16: e^z E1 and e^z E2 from 26-term Chebyshev expansions on
-//    [1,2], [2,4], [4,8], [8,16] (coefficients in expint_cheb.inc, generated
-//    by gen_expint_tables.py in 40-digit arithmetic), Clenshaw summation;
+//  * 1 <= z < 16: e^z E1 and e^z E2 from 18-term Chebyshev expansions on the
+//    eight intervals [2^{k/2}, 2^{(k+1)/2}] (coefficients in expint_cheb.inc,
+//    generated by gen_expint_tables.py in 40-digit arithmetic), Clenshaw
+//    summation;
 //  * z >= 16: the continued fraction of A&S 5.1.22 in its even (contracted)
 //    form, E_n(z) = e^{-z} / (z + n - 1 n / (z + n + 2 - 2 (n+1) / (z + n + 4 - ...))),
 //    truncated at a fixed depth of 14 (converged to < 1e-16 there) and
@@ -146,6 +147,13 @@ STB_HD double cheb_sum(const double* c, double t) {
   return 0.5 * c[0] + t * b1 - b2;
 }
 
+// Interval of the FP64 Chebyshev tables for 1 <= z < 16: [a_k, a_{k+1}],
+// a_k = 2^{k/2} (the split inside each octave [2^e, 2^{e+1}) at sqrt 2 2^e).
+STB_HD int cheb_interval(double z) {
+  const int e = z < 2.0 ? 0 : (z < 4.0 ? 1 : (z < 8.0 ? 2 : 3));
+  return 2 * e + (z >= kChebSplit[e] ? 1 : 0);
+}
+
 // E1(z), E2(z) for z > 0.
 STB_HD void e1e2(double z, double* e1, double* e2) {
   if (z < 1.0) {
@@ -153,9 +161,8 @@ STB_HD void e1e2(double z, double* e1, double* e2) {
     *e1 = E1;
     *e2 = exp_neg_fast(z) - z * E1;
   } else if (z < 16.0) {
-    const int k = z < 2.0 ? 0 : (z < 4.0 ? 1 : (z < 8.0 ? 2 : 3));
-    const double a = (double)(1 << k);
-    const double t = 2.0 * z / a - 3.0;
+    const int k = cheb_interval(z);
+    const double t = fma(z, kChebS[k], kChebO[k]);
     const double ez = exp_neg_fast(z);
     *e1 = cheb_sum(kChebE1[k], t) * ez;
     *e2 = cheb_sum(kChebE2[k], t) * ez;
@@ -177,9 +184,8 @@ STB_HD void e1e2(double z, double* e1, double* e2) {
 STB_HD double e1_only(double z) {
   if (z < 1.0) return -kEulerGamma - log(z) + ein_series(z);
   if (z < 16.0) {
-    const int k = z < 2.0 ? 0 : (z < 4.0 ? 1 : (z < 8.0 ? 2 : 3));
-    const double a = (double)(1 << k);
-    const double t = 2.0 * z / a - 3.0;
+    const int k = cheb_interval(z);
+    const double t = fma(z, kChebS[k], kChebO[k]);
     return cheb_sum(kChebE1[k], t) * exp_neg_fast(z);
   }
   const double ez = exp_neg_fast(z);
