@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
 # at square256 (lags 2..65) from an ncu capture (profiles/k_tile_D_f64_lag2.md);
 # set to None whenever that kernel changes
-TRAFFIC_D2_BYTES = 719872 + 54016   # DRAM bytes of one 64-lag launch (lags 32..95, ncu)
+TRAFFIC_D2_BYTES = 770816 + 51712   # DRAM bytes of one 64-lag launch (lags 32..95, ncu)
 
 
 def _oracle_sample(n_entries, seed, rng_lags=None):
