@@ -430,7 +430,7 @@ int stbem_m0_bytes(const stbem_domain* dom, size_t* bytes);
 int stbem_m0_assemble(stbem_ctx* ctx, const stbem_domain* dom, double* dev_M0);
 /* Matrix-free product: dev_y[b][m][i] += scale * (M_h^0 dev_u0[b])[m][i] for
  * b < n_rhs, dev_u0[b] the n_nodes nodal values, computed with the same rule
- * as stbem_m0_assemble without storing M_h^0.  n_t <= 6144.  Workspace:
+ * as stbem_m0_assemble without storing M_h^0.  n_t <= 6144, n_x <= 65535.  Workspace:
  * stbem_m0_apply_workspace_bytes (per-block partial sums).  Errors:
  * STBEM_ERR_ARG, STBEM_ERR_NOMEM (workspace too small), STBEM_ERR_CUDA. */
 int stbem_m0_apply_workspace_bytes(const stbem_domain* dom, size_t* bytes);

@@ -233,6 +233,7 @@ int stbem_m0_apply(stbem_ctx* ctx, const stbem_domain* d, int n_rhs, const doubl
   if (!d || !dev_u0 || !dev_y || !dev_work) return fail(ctx, STBEM_ERR_ARG, "m0_apply: NULL argument");
   if (n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "m0_apply: need n_rhs >= 1");
   if (d->mesh->n_t > 6144) return fail(ctx, STBEM_ERR_ARG, "m0_apply: n_t above 6144");
+  if (d->mesh->N > 65535) return fail(ctx, STBEM_ERR_ARG, "m0_apply: n_x above 65535");
   const size_t need = stbem::m0_apply_workspace_bytes(d->mesh->n_t, d->mesh->N, d->K);
   if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "m0_apply: workspace %zu < %zu bytes", work_bytes, need);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "m0_apply");
