@@ -23,6 +23,8 @@ What it computes, all in plain float64 numpy/scipy:
                     time and a right-preconditioned GMRES;
 * ``initial``    -- the initial-data operator M_h^0 on a triangulation of
                     Omega (eq. (4)) and the data of the Section 4 example;
+* ``evaluate``   -- u in Q by the representation formula (eq. (2)) from the
+                    discrete Cauchy data and initial datum;
 * ``gradient``   -- shape (vertex) and alpha derivatives of V_h, K_h, M_h and
                     g, the adjoint (backward-in-time) solve and the gradient of
                     ||w_h - w_target||^2.
