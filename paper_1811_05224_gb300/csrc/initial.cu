@@ -5,17 +5,20 @@
 // phi_j the P1 hat functions of a triangulation Omega_h.  The time integral is
 // exact, int_{tau_m} U*(r, t) dt = G(r, t_{m+1}) - G(r, t_m) with
 // G(r, s) = alpha/(4 pi) E1(alpha r^2 / (4 s)), G(r, 0) = 0.  Space: per pair
-// (segment i, triangle k) the rule of rule.cuh (tensor rule of an order that
-// depends on the pair class and the m range; polar rule for touching pairs at
-// m = 0).  Within one m range all m share the rule's points, so E1 is
-// evaluated once per (point, time t_m).
+// (segment i, triangle k) the rule of rule.cuh: at m = 0 a tensor rule whose
+// order follows the pair class, or the polar rule for touching pairs; for
+// m >= 1 a tensor rule whose order follows rho^2 = 4 m ht / (alpha s^2), the
+// diffusion length over the pair size.  The m of one order range share the
+// rule's points, so E1 is evaluated once per (point, time t_m).
 //
 // One warp per pair.  Full chunks of 31 steps of one order range: lanes over
 // 31 consecutive times t_{m0} .. t_{m0+31}; the points are computed 32 at a
 // time, one per lane, and broadcast by shuffles; lane l evaluates
 // G(t_{m0+l}) and takes G(t_{m0+l-1}) from lane l - 1.  The remaining steps
-// (and m = 0) in chunks of up to 3: lanes over the rule's points, per-lane
-// sums per step, one warp reduction per step.
+// (and m = 0) in groups of up to 3: lanes over the rule's points, per-lane
+// sums per step, one warp reduction per step; each point's G at the first
+// time of the next group is carried in shared memory (ranges of at most 512
+// points).
 //
 // Assembly writes M0[m][i][j] += for the three vertices of the triangle; it is
 // launched once per colour of a node-disjoint colouring of the triangles, so
