@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "capi_internal.h"
+#include "domain_host.h"
 #include "initial.h"
 #include "stbem.h"
 
@@ -25,39 +26,6 @@ struct stbem_domain {
   stbem::DevDomain dev{};
 };
 
-namespace {
-
-// Greedy colouring: each triangle takes the smallest colour not used by a
-// triangle that shares one of its nodes (processed in index order).
-std::vector<int> colour_triangles(int M, int K, const std::vector<int>& tri, int* n_colors) {
-  std::vector<int> off(M + 1, 0), adj(3 * K);
-  for (int t = 0; t < 3 * K; ++t) ++off[tri[t] + 1];
-  for (int j = 0; j < M; ++j) off[j + 1] += off[j];
-  std::vector<int> fill(off.begin(), off.end() - 1);
-  for (int k = 0; k < K; ++k)
-    for (int c = 0; c < 3; ++c) adj[fill[tri[3 * k + c]]++] = k;
-  std::vector<int> col(K, -1);
-  std::vector<int> used;
-  int nc = 0;
-  for (int k = 0; k < K; ++k) {
-    used.assign(nc + 1, 0);
-    for (int c = 0; c < 3; ++c) {
-      const int j = tri[3 * k + c];
-      for (int a = off[j]; a < off[j + 1]; ++a) {
-        const int o = col[adj[a]];
-        if (o >= 0) used[o] = 1;
-      }
-    }
-    int pick = 0;
-    while (pick < nc && used[pick]) ++pick;
-    col[k] = pick;
-    nc = std::max(nc, pick + 1);
-  }
-  *n_colors = nc;
-  return col;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -84,27 +52,9 @@ int stbem_domain_create(stbem_ctx* ctx, const stbem_mesh* mesh, const double* ho
     if (tri[t] < 0 || tri[t] >= M) return fail(ctx, STBEM_ERR_ARG, "domain: triangle index out of range");
   // boundary vertex p -> the nearest node, which must lie within 1e-12 x diameter
   const double diam = std::max(hi[0] - lo[0], hi[1] - lo[1]);
-  const double tol = 1e-12 * diam;
-  std::vector<int> byx(M);
-  for (int j = 0; j < M; ++j) byx[j] = j;
-  std::sort(byx.begin(), byx.end(), [&](int a, int b) { return x[a] < x[b] || (x[a] == x[b] && a < b); });
   std::vector<int> bnode(N);
-  for (int p = 0; p < N; ++p) {
-    const double px = mesh->xy[2 * p], py = mesh->xy[2 * p + 1];
-    auto it = std::lower_bound(byx.begin(), byx.end(), px - tol, [&](int a, double v) { return x[a] < v; });
-    int best = -1;
-    double bd = 1e300;
-    for (; it != byx.end() && x[*it] <= px + tol; ++it) {
-      const double dx = x[*it] - px, dy = y[*it] - py;
-      const double d = std::sqrt(dx * dx + dy * dy);
-      if (d < bd || (d == bd && *it < best)) {
-        bd = d;
-        best = *it;
-      }
-    }
-    if (best < 0 || bd > tol) return fail(ctx, STBEM_ERR_ARG, "domain: boundary vertex %d is not a node", p);
-    bnode[p] = best;
-  }
+  const int bad = stbem::match_boundary_nodes(x, y, mesh->xy.data(), N, 1e-12 * diam, bnode.data());
+  if (bad >= 0) return fail(ctx, STBEM_ERR_ARG, "domain: boundary vertex %d is not a node", bad);
   for (int p = 0; p < N; ++p) {
     x[bnode[p]] = mesh->xy[2 * p];
     y[bnode[p]] = mesh->xy[2 * p + 1];
@@ -124,7 +74,7 @@ int stbem_domain_create(stbem_ctx* ctx, const stbem_mesh* mesh, const double* ho
     dmax[k] = dm;
   }
   int nc = 0;
-  const std::vector<int> col = colour_triangles(M, K, tri, &nc);
+  const std::vector<int> col = stbem::colour_triangles(M, K, tri, &nc);
   std::vector<int> lists;
   lists.reserve(K);
   stbem_domain* d = new stbem_domain();
