@@ -25,6 +25,8 @@ What it computes, all in plain float64 numpy/scipy:
                     Omega (eq. (4)) and the data of the Section 4 example;
 * ``evaluate``   -- u in Q by the representation formula (eq. (2)) from the
                     discrete Cauchy data and initial datum;
+* ``nonuniform``  -- V_h, K_h, D_h blocks on non-uniform time grids (block
+                    lower triangular, not Toeplitz), their solve and data;
 * ``gradient``   -- shape (vertex) and alpha derivatives of V_h, K_h, M_h and
                     g, the adjoint (backward-in-time) solve and the gradient of
                     ||w_h - w_target||^2.

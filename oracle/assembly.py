@@ -60,7 +60,7 @@ def _rule(code, d, rules):
 
 
 def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
-                   wa0, wa1, wb0, wb1, rules=DEFAULT_RULES, chunk=2048, magnitude=False):
+                   wa0, wa1, wb0, wb1, rules=DEFAULT_RULES, chunk=2048, magnitude=False, tfun=None):
     """int_a int_b k_d(x, y) wa(x) wb(y) ds_y ds_x for arrays of piece pairs.
 
     kind: 'V' (D2_d F_V), 'K' (D2_d F_K, uses the trial normal NB) or '1'
@@ -69,6 +69,9 @@ def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
     wa(xi) = wa0 + (wa1 - wa0) xi.
     With magnitude=True the sum of the absolute values of the point terms is
     returned instead (the scale of the rounding error of the sum).
+    tfun(kind, c), if given, replaces the uniform-grid time integrals at lag
+    d (lag_V, lag_Kq / q, lag_1) by another pair of time steps' integrals
+    (non-uniform grids); d still selects the spatial rule.
     """
     n = len(cls)
     out = np.zeros(n)
@@ -91,15 +94,18 @@ def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
                 dx = p[None, :, None] * ea + q[None, :, None] * eb
             r2 = (dx * dx).sum(-1)
             c = 0.25 * alpha * r2
-            if kind == 'V':
+            if kind not in ('V', 'K', '1'):
+                raise ValueError(kind)
+            if tfun is not None:
+                k = tfun(kind, c)
+            elif kind == 'V':
                 k = lag_V(c, d, ht, alpha, rules)
             elif kind == 'K':
-                qn = (dx * NB[sel, None, :]).sum(-1)
-                k = qn * lag_Kq(c, d, ht, alpha, rules)
-            elif kind == '1':
-                k = lag_1(c, d, ht, alpha, rules)
+                k = lag_Kq(c, d, ht, alpha, rules)
             else:
-                raise ValueError(kind)
+                k = lag_1(c, d, ht, alpha, rules)
+            if kind == 'K':
+                k = (dx * NB[sel, None, :]).sum(-1) * k
             fa = wa0[sel, None] + (wa1 - wa0)[sel, None] * xi[None, :]
             fb = wb0[sel, None] + (wb1 - wb0)[sel, None] * eta[None, :]
             terms = w[None, :] * k * fa * fb
@@ -111,7 +117,7 @@ def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
 
 # --- V_h ----------------------------------------------------------------------
 
-def V_entries(mesh: BoundaryMesh, d, I, J, rules=DEFAULT_RULES):
+def V_entries(mesh: BoundaryMesh, d, I, J, rules=DEFAULT_RULES, tfun=None):
     """V^(d)[i][j] = int_{gamma_i} int_{gamma_j} D2_d F_V ds_y ds_x."""
     I, J = np.asarray(I), np.asarray(J)
     a, b = np.minimum(I, J), np.maximum(I, J)
@@ -119,12 +125,12 @@ def V_entries(mesh: BoundaryMesh, d, I, J, rules=DEFAULT_RULES):
     one = np.ones(a.shape)
     return pair_integrals('V', d, mesh, mesh.a[a], mesh.b[a], mesh.h[a],
                           mesh.a[b], mesh.b[b], mesh.h[b],
-                          mesh.n[b], cls, one, one, one, one, rules)
+                          mesh.n[b], cls, one, one, one, one, rules, tfun=tfun)
 
 
 # --- K_h ----------------------------------------------------------------------
 
-def K_entries(mesh: BoundaryMesh, d, I, P, rules=DEFAULT_RULES, magnitude=False):
+def K_entries(mesh: BoundaryMesh, d, I, P, rules=DEFAULT_RULES, magnitude=False, tfun=None):
     """K^(d)[i][p] = sum_{j in {p-1, p}} int_{gamma_i} int_{gamma_j}
     D2_d F_K(x, y) phi_p(y) ds_y ds_x, phi_p the P1 hat at vertex p.
 
@@ -145,7 +151,7 @@ def K_entries(mesh: BoundaryMesh, d, I, P, rules=DEFAULT_RULES, magnitude=False)
         one = np.ones(ii.shape)
         val = pair_integrals('K', d, mesh, mesh.a[ii], mesh.b[ii], mesh.h[ii],
                              mesh.a[jj], mesh.b[jj], mesh.h[jj], mesh.n[jj], cls,
-                             one, one, w0 * one, w1 * one, rules, magnitude=magnitude)
+                             one, one, w0 * one, w1 * one, rules, magnitude=magnitude, tfun=tfun)
         total[keep] += val
     return total
 
@@ -164,7 +170,7 @@ def _dual_tables(mesh):
     return idx, v0, v1, dp
 
 
-def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False):
+def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False, tfun=None):
     """D^(d)[l][k] = <D psi_k, psi_l> at lag d (form written above).
 
     magnitude=True returns S = sum over pieces and quadrature points of the
@@ -192,10 +198,11 @@ def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False)
     B0, B1, LB = mesh.hs0[pb], mesh.hs1[pb], mesh.hs_len[pb]
     NB = mesh.hs_n[pb]
     IV = pair_integrals('V', d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
-                        one, one, one, one, rules, magnitude=magnitude)
+                        one, one, one, one, rules, magnitude=magnitude, tfun=tfun)
     I1 = pair_integrals('1', d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
                         v0[ra[:, 0], ra[:, 1]], v1[ra[:, 0], ra[:, 1]],
-                        v0[rb[:, 0], rb[:, 1]], v1[rb[:, 0], rb[:, 1]], rules, magnitude=magnitude)
+                        v0[rb[:, 0], rb[:, 1]], v1[rb[:, 0], rb[:, 1]], rules, magnitude=magnitude,
+                        tfun=tfun)
     curl = dp[ra[:, 0], ra[:, 1]] * dp[rb[:, 0], rb[:, 1]]
     nn = (mesh.hs_n[pa] * mesh.hs_n[pb]).sum(-1)
     if magnitude:
