@@ -56,10 +56,11 @@ def nested(kind, c, m, n):
     return mp.quad(inner, outer)
 
 
-# (m, n, c): d = 0 small / large z; d = 1 small z (unequal steps 0.05, 0.02 /
-# 0.04, 0.05) and large z; d = 2 Peano and closed; d = 4 Peano with a plateau
-CASES = [(3, 3, 1e-4), (3, 3, 0.05), (2, 1, 1e-4), (4, 3, 2e-3), (4, 3, 0.08),
-         (4, 2, 2e-3), (4, 2, 0.3), (6, 2, 3e-3), (7, 3, 1e-2), (7, 1, 0.9)]
+# (m, n, c), one per branch: d = 0; d = 1 small z (unequal steps 0.02, 0.03)
+# and large z; d = 2 Peano and closed; d = 4 Peano with a plateau (steps
+# 0.07, 0.02); d = 6 closed
+CASES = [(3, 3, 1e-4), (2, 1, 1e-4), (4, 3, 0.08), (4, 2, 2e-3), (4, 2, 0.3), (6, 2, 3e-3),
+         (7, 1, 0.9)]
 
 
 @pytest.mark.parametrize("kind", ["V", "K", "1"])
