@@ -16,6 +16,7 @@
 #include "toeplitz.h"
 #include "grad.h"
 #include "initial.h"
+#include "mass_host.h"
 #include "toeplitz_tc.h"
 #include "vec.h"
 
@@ -820,46 +821,11 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V
 int stbem_mixed_mass_inverse(stbem_ctx* ctx, const stbem_mesh* m, double* dev_Minv) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!m || !dev_Minv) return fail(ctx, STBEM_ERR_ARG, "mixed_mass_inverse: NULL pointer");
-  const int N = m->N;
-  const std::vector<double>& h = m->h;
-  // M[l][k] = ht int_{gamma_k} psi_l: psi_l is linear on its four half-segments,
-  // with values a_l at x_l and b_l at x_{l+1} (the bends), 1 at the midpoint
-  std::vector<double> A((size_t)N * N, 0.0), Inv((size_t)N * N, 0.0);
-  for (int l = 0; l < N; ++l) {
-    const int lm = (l - 1 + N) % N, lp = (l + 1) % N;
-    const double a = h[lm] / (h[lm] + h[l]), b = h[lp] / (h[l] + h[lp]);
-    A[(size_t)l * N + l] += m->ht * h[l] * (a + 2.0 + b) / 4.0;
-    A[(size_t)l * N + lm] += m->ht * h[lm] * a / 4.0;
-    A[(size_t)l * N + lp] += m->ht * h[lp] * b / 4.0;
-    Inv[(size_t)l * N + l] = 1.0;
-  }
-  // Gauss-Jordan elimination with partial pivoting (M is cyclic tridiagonal
-  // but not symmetric; N^3 host work, once per mesh)
-  for (int c = 0; c < N; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < N; ++r)
-      if (std::fabs(A[(size_t)r * N + c]) > std::fabs(A[(size_t)piv * N + c])) piv = r;
-    if (!(std::fabs(A[(size_t)piv * N + c]) > 0.0)) return fail(ctx, STBEM_ERR_ARG, "mixed_mass_inverse: singular");
-    if (piv != c)
-      for (int k = 0; k < N; ++k) {
-        std::swap(A[(size_t)c * N + k], A[(size_t)piv * N + k]);
-        std::swap(Inv[(size_t)c * N + k], Inv[(size_t)piv * N + k]);
-      }
-    const double inv = 1.0 / A[(size_t)c * N + c];
-    for (int k = 0; k < N; ++k) {
-      A[(size_t)c * N + k] *= inv;
-      Inv[(size_t)c * N + k] *= inv;
-    }
-    for (int r = 0; r < N; ++r) {
-      if (r == c) continue;
-      const double f = A[(size_t)r * N + c];
-      if (f == 0.0) continue;
-      for (int k = 0; k < N; ++k) {
-        A[(size_t)r * N + k] -= f * A[(size_t)c * N + k];
-        Inv[(size_t)r * N + k] -= f * Inv[(size_t)c * N + k];
-      }
-    }
-  }
+  // the cyclic tridiagonal mixed mass of one step, inverted on the host
+  // (Gauss-Jordan with partial pivoting; M is not symmetric; N^3 host work,
+  // once per mesh)
+  std::vector<double> A = stbem::mixed_mass_matrix(m->h, m->ht), Inv;
+  if (!stbem::gauss_jordan_inverse(A, m->N, Inv)) return fail(ctx, STBEM_ERR_ARG, "mixed_mass_inverse: singular");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "mixed_mass_inverse: set device");
   CUDA_TRY(ctx, cudaMemcpyAsync(dev_Minv, Inv.data(), Inv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
            "mixed_mass_inverse: upload");
