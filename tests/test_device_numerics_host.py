@@ -1,6 +1,8 @@
 """The CUDA path's device numerics compiled for the host (same headers) and
 checked on the CPU against the C library / scipy / numpy: the table-driven
-e^{-x}, E1 and E2 in FP64 and FP32, the Ein series, Gauss-Legendre tables."""
+e^{-x}, E1 and E2 in FP64 and FP32, the Ein series, Gauss-Legendre tables,
+and the double time integrals of every branch (timeint.cuh) against the
+oracle's (oracle.timeint, the same rule written independently)."""
 import ctypes
 import os
 import subprocess
@@ -72,3 +74,22 @@ def test_ein_and_gauss_tables(lib):
         lib.nc_gauss(n, _d(x), _d(w))
         xr, wr = np.polynomial.legendre.leggauss(n)
         assert np.allclose(x, 0.5 * (xr + 1), atol=2e-16) and np.allclose(w, 0.5 * wr, atol=4e-16)
+
+
+def test_time_integrals_match_oracle(lib):
+    """lag_kernel (d = 0; d = 1 series and closed; d >= 2 closed and Peano)
+    against oracle.timeint over c spanning both sides of every switch.  Both
+    evaluate the same formulas with their own E1/E2 (within 2e-15 of each
+    other); the closed second differences amplify that by at most their
+    cancellation, bounded here by 1e-12 relative."""
+    from oracle import timeint
+    from oracle.rules import DEFAULT_RULES as R
+    ht, alpha = 1.0 / 64.0, 0.7
+    c = np.logspace(-9, 3, 241)
+    for d in (0, 1, 2, 3, 7, 8, 31, 32, 100, 300):
+        for kind, ref_fn in ((0, timeint.lag_V), (1, timeint.lag_Kq), (2, timeint.lag_1)):
+            out = np.zeros_like(c)
+            lib.nc_lag(kind, _d(c), len(c), d, ctypes.c_double(ht), ctypes.c_double(alpha), _d(out))
+            ref = ref_fn(c, d, ht, alpha, R)
+            big = np.abs(ref) > 1e-280
+            assert np.all(np.abs(out[big] - ref[big]) <= 1e-12 * np.abs(ref[big])), (d, kind)
