@@ -1,6 +1,6 @@
 // Host build of the CUDA path's device numerics (special.cuh, timeint.cuh,
 // rules_host.cpp) for CPU tests: the same source, compiled for the host.
-#include "timeint.cuh"
+#include "dtimeint.cuh"
 namespace stbem { void build_rule_tables(RuleTables* t); }
 static stbem::RuleTables T;
 extern "C" {
@@ -15,6 +15,25 @@ void nc_lag(int kind, const double* c, int n, int d, double ht, double alpha, do
     out[i] = kind == 0 ? stbem::lag_kernel<stbem::kV>(c[i], d, ht, alpha, T.gx, T.gw)
            : kind == 1 ? stbem::lag_kernel<stbem::kKq>(c[i], d, ht, alpha, T.gx, T.gw)
                        : stbem::lag_kernel<stbem::k1>(c[i], d, ht, alpha, T.gx, T.gw);
+}
+// lags 0, 1: dlag01 (value and c-derivative); lags >= 2, closed branch: the
+// second difference of dF_closed
+void nc_dlag(int kind, const double* c, int n, int d, double ht, double alpha, double* k, double* dk) {
+  for (int i = 0; i < n; ++i) {
+    if (d <= 1) {
+      if (kind == 0) stbem::dlag01<stbem::kV>(c[i], d, ht, alpha, k + i, dk + i);
+      else stbem::dlag01<stbem::kKq>(c[i], d, ht, alpha, k + i, dk + i);
+      continue;
+    }
+    double f[3], df[3];
+    for (int q = 0; q < 3; ++q) {
+      const double s = (double)(d + 1 - q) * ht;
+      if (kind == 0) stbem::dF_closed<stbem::kV>(c[i], s, 1.0 / s, alpha, &f[q], &df[q]);
+      else stbem::dF_closed<stbem::kKq>(c[i], s, 1.0 / s, alpha, &f[q], &df[q]);
+    }
+    k[i] = (f[0] - 2.0 * f[1]) + f[2];
+    dk[i] = (df[0] - 2.0 * df[1]) + df[2];
+  }
 }
 void nc_gauss(int n, double* x, double* w) {
   const int o = stbem::gauss_offset(n);

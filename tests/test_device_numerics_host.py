@@ -93,3 +93,23 @@ def test_time_integrals_match_oracle(lib):
             ref = ref_fn(c, d, ht, alpha, R)
             big = np.abs(ref) > 1e-280
             assert np.all(np.abs(out[big] - ref[big]) <= 1e-12 * np.abs(ref[big])), (d, kind)
+
+
+def test_time_integral_c_derivatives_match_oracle(lib):
+    """dtimeint.cuh (the gradient kernels' values and d/dc: lags 0 and 1, and
+    the closed second difference at lags >= 2 where c / (d ht) > d / 2)
+    against oracle.timeint's dlag_V / dlag_Kq."""
+    from oracle import timeint
+    from oracle.rules import DEFAULT_RULES as R
+    ht, alpha = 1.0 / 64.0, 0.7
+    for d in (0, 1, 2, 5, 40):
+        c = np.logspace(-9, 3, 241)
+        if d >= 2:
+            c = c[c / (d * ht) > 0.5 * d]
+        for kind, vf, df in ((0, timeint.lag_V, timeint.dlag_V), (1, timeint.lag_Kq, timeint.dlag_Kq)):
+            k, dk = np.zeros_like(c), np.zeros_like(c)
+            lib.nc_dlag(kind, _d(c), len(c), d, ctypes.c_double(ht), ctypes.c_double(alpha), _d(k), _d(dk))
+            rv, rd = vf(c, d, ht, alpha, R), df(c, d, ht, alpha, R)
+            for got, ref in ((k, rv), (dk, rd)):
+                big = np.abs(ref) > 1e-280
+                assert np.all(np.abs(got[big] - ref[big]) <= 1e-12 * np.abs(ref[big])), (d, kind)
