@@ -71,6 +71,23 @@ def test_time_integrals_against_nested_quadrature(kind):
         assert abs(got - ref) <= 1e-10 * abs(ref) + 1e-300, (kind, m, n, c, got, ref)
 
 
+def test_geometric_grid_ratio_four():
+    """Steps growing by a factor of 4 (the largest ratio the rule is stated
+    for): d >= 2 blocks, Peano and closed, against nested quadrature."""
+    global T_NODES
+    saved = T_NODES
+    h0 = 0.01
+    T_NODES = np.array([0.0, h0, 5 * h0, 21 * h0, 85 * h0])
+    try:
+        for m, n, c in ((2, 0, 4e-5), (3, 1, 1e-5), (3, 0, 0.03)):
+            for kind in ("V", "1"):
+                got = float(NU.time_integral(kind, np.array([c]), T_NODES, m, n, ALPHA)[0])
+                ref = float(nested(kind, c, m, n))
+                assert abs(got - ref) <= 1e-12 * abs(ref), (kind, m, n, c, got, ref)
+    finally:
+        T_NODES = saved
+
+
 def test_uniform_grid_equals_toeplitz_blocks():
     m = BoundaryMesh(W.l_shape(8, seed=3), 1.0, 6, 0.8)
     t = np.arange(7) * m.ht
