@@ -1,6 +1,7 @@
 // Host build of the CUDA path's device numerics (special.cuh, timeint.cuh,
 // rules_host.cpp) for CPU tests: the same source, compiled for the host.
 #include "dtimeint.cuh"
+#include "nonuniform_time.cuh"
 namespace stbem { void build_rule_tables(RuleTables* t); }
 static stbem::RuleTables T;
 extern "C" {
@@ -34,6 +35,13 @@ void nc_dlag(int kind, const double* c, int n, int d, double ht, double alpha, d
     k[i] = (f[0] - 2.0 * f[1]) + f[2];
     dk[i] = (df[0] - 2.0 * df[1]) + df[2];
   }
+}
+void nc_nu_time(int kind, const double* c, int n, int d, double s1, double s2, double s3, double s4,
+                double alpha, double* out) {
+  for (int i = 0; i < n; ++i)
+    out[i] = kind == 0 ? stbem::nu_time_integral<stbem::kV>(c[i], d, s1, s2, s3, s4, alpha, T.gx, T.gw)
+           : kind == 1 ? stbem::nu_time_integral<stbem::kKq>(c[i], d, s1, s2, s3, s4, alpha, T.gx, T.gw)
+                       : stbem::nu_time_integral<stbem::k1>(c[i], d, s1, s2, s3, s4, alpha, T.gx, T.gw);
 }
 void nc_gauss(int n, double* x, double* w) {
   const int o = stbem::gauss_offset(n);

@@ -113,3 +113,26 @@ def test_time_integral_c_derivatives_match_oracle(lib):
             for got, ref in ((k, rv), (dk, rd)):
                 big = np.abs(ref) > 1e-280
                 assert np.all(np.abs(got[big] - ref[big]) <= 1e-12 * np.abs(ref[big])), (d, kind)
+
+
+def test_nonuniform_time_integrals_match_oracle(lib):
+    """nonuniform_time.cuh (the device form of the non-uniform grids' time
+    integrals: d = 0; d = 1 series and closed; d >= 2 closed and Peano with
+    up to three pieces) against oracle.nonuniform on a graded grid and on a
+    uniform one, over c spanning every switch."""
+    from oracle import nonuniform as NU
+    alpha = 0.7
+    grids = [np.array([0.0, 0.02, 0.05, 0.07, 0.11, 0.16, 0.19, 0.26, 0.30, 0.37, 0.41]),
+             np.arange(11) / 64.0]
+    c = np.logspace(-9, 1, 161)
+    for t in grids:
+        for m in range(10):
+            for n in range(m + 1):
+                s = (t[m + 1] - t[n], t[m + 1] - t[n + 1], t[m] - t[n], t[m] - t[n + 1])
+                for kind, name in ((0, "V"), (1, "K"), (2, "1")):
+                    out = np.zeros_like(c)
+                    lib.nc_nu_time(kind, _d(c), len(c), m - n, *[ctypes.c_double(x) for x in s],
+                                   ctypes.c_double(alpha), _d(out))
+                    ref = NU.time_integral(name, c, t, m, n, alpha)
+                    big = np.abs(ref) > 1e-280
+                    assert np.all(np.abs(out[big] - ref[big]) <= 1e-12 * np.abs(ref[big])), (m, n, name)
