@@ -34,6 +34,8 @@ space integrals on tiny meshes, symmetry, invariances, K = 0 on collinear
 pairs, the D_h form against the non-integrated kernel on separated supports,
 positive definiteness of V_h).
 """
+import math
+
 import numpy as np
 
 from .geometry import (ADJ_NEXT, ADJ_PREV, IDENTICAL, NEAR, REGULAR,
@@ -60,7 +62,8 @@ def _rule(code, d, rules):
 
 
 def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
-                   wa0, wa1, wb0, wb1, rules=DEFAULT_RULES, chunk=2048, magnitude=False, tfun=None):
+                   wa0, wa1, wb0, wb1, rules=DEFAULT_RULES, chunk=2048, magnitude=False, tfun=None,
+                   keep_terms=False):
     """int_a int_b k_d(x, y) wa(x) wb(y) ds_y ds_x for arrays of piece pairs.
 
     kind: 'V' (D2_d F_V), 'K' (D2_d F_K, uses the trial normal NB) or '1'
@@ -72,9 +75,11 @@ def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
     tfun(kind, c), if given, replaces the uniform-grid time integrals at lag
     d (lag_V, lag_Kq / q, lag_1) by another pair of time steps' integrals
     (non-uniform grids); d still selects the spatial rule.
+    With keep_terms=True an object array is returned instead whose entry k
+    holds pair k's point terms (times LA LB), unsummed.
     """
     n = len(cls)
-    out = np.zeros(n)
+    out = np.empty(n, dtype=object) if keep_terms else np.zeros(n)
     ht, alpha = mesh.ht, mesh.alpha
     codes = np.unique(cls) if d < 2 else np.array([-1])
     for code in codes:
@@ -111,7 +116,11 @@ def pair_integrals(kind, d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
             terms = w[None, :] * k * fa * fb
             if magnitude:
                 terms = np.abs(terms)
-            out[sel] = terms.sum(-1) * LA[sel] * LB[sel]
+            if keep_terms:
+                for r, e in enumerate(sel):
+                    out[e] = terms[r] * (LA[e] * LB[e])
+            else:
+                out[sel] = terms.sum(-1) * LA[sel] * LB[sel]
     return out
 
 
@@ -170,12 +179,16 @@ def _dual_tables(mesh):
     return idx, v0, v1, dp
 
 
-def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False, tfun=None):
+def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False, tfun=None, exact=False):
     """D^(d)[l][k] = <D psi_k, psi_l> at lag d (form written above).
 
     magnitude=True returns S = sum over pieces and quadrature points of the
     absolute values of the terms of the sum, the scale against which rounding
-    in any evaluation order of this signed sum is measured."""
+    in any evaluation order of this signed sum is measured.  exact=True sums
+    all point terms of each entry (both terms of the form, all 16 piece pairs)
+    with math.fsum, i.e. exactly rounded: only the rounding of the terms
+    themselves remains, so any other evaluation order can be measured against
+    it in units of eps S."""
     L, K = np.asarray(L), np.asarray(K)
     lo, hi = np.minimum(L, K), np.maximum(L, K)
     idx, v0, v1, dp = _dual_tables(mesh)
@@ -198,15 +211,21 @@ def D_entries(mesh: BoundaryMesh, d, L, K, rules=DEFAULT_RULES, magnitude=False,
     B0, B1, LB = mesh.hs0[pb], mesh.hs1[pb], mesh.hs_len[pb]
     NB = mesh.hs_n[pb]
     IV = pair_integrals('V', d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
-                        one, one, one, one, rules, magnitude=magnitude, tfun=tfun)
+                        one, one, one, one, rules, magnitude=magnitude, tfun=tfun, keep_terms=exact)
     I1 = pair_integrals('1', d, mesh, A0, A1, LA, B0, B1, LB, NB, cls,
                         v0[ra[:, 0], ra[:, 1]], v1[ra[:, 0], ra[:, 1]],
                         v0[rb[:, 0], rb[:, 1]], v1[rb[:, 0], rb[:, 1]], rules, magnitude=magnitude,
-                        tfun=tfun)
+                        tfun=tfun, keep_terms=exact)
     curl = dp[ra[:, 0], ra[:, 1]] * dp[rb[:, 0], rb[:, 1]]
     nn = (mesh.hs_n[pa] * mesh.hs_n[pb]).sum(-1)
     if magnitude:
         curl, nn = np.abs(curl), np.abs(nn)
+    if exact:
+        parts = [[] for _ in range(E)]
+        for r in range(eo.size):
+            parts[eo[r]].append(curl[r] * IV[r])
+            parts[eo[r]].append(nn[r] * I1[r])
+        return np.array([math.fsum(np.concatenate(p)) for p in parts])
     contrib = curl * IV + nn * I1
     out = np.zeros(E)
     np.add.at(out, eo, contrib)
@@ -224,10 +243,11 @@ def _all_pairs(N, symmetric):
     return I, J
 
 
-def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None, magnitude=False):
+def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None, magnitude=False, exact=False):
     """Lag blocks A[d][i][j] (N_t x N_x x N_x) of op in {'V', 'K', 'D'}.
 
-    magnitude=True (K and D) returns the term-magnitude sums S instead."""
+    magnitude=True (K and D) returns the term-magnitude sums S instead;
+    exact=True (D) the exactly summed entries of D_entries."""
     N = mesh.N
     lags = range(mesh.n_t) if lags is None else lags
     sym = op in ('V', 'D')
@@ -235,7 +255,12 @@ def assemble(op: str, mesh: BoundaryMesh, rules=DEFAULT_RULES, lags=None, magnit
     fn = {'V': V_entries, 'K': K_entries, 'D': D_entries}[op]
     out = np.zeros((len(list(lags)), N, N))
     for k, d in enumerate(lags):
-        vals = fn(mesh, d, I, J, rules, magnitude=True) if magnitude else fn(mesh, d, I, J, rules)
+        if magnitude:
+            vals = fn(mesh, d, I, J, rules, magnitude=True)
+        elif exact:
+            vals = fn(mesh, d, I, J, rules, exact=True)
+        else:
+            vals = fn(mesh, d, I, J, rules)
         out[k, I, J] = vals
         if sym:
             out[k, J, I] = vals

@@ -18,8 +18,12 @@ Section 2) and a pair of time steps of I_h at lag d.
   lags d >= 2 in closed form when z_d = alpha r^2 / (4 d ht) > d / 2, else in
   the Peano form with ``peano_order(k)`` Gauss nodes on time interval k.
 
-Orders were chosen by measuring against brute-force adaptive quadrature
-(tests/test_oracle_bruteforce.py pins the result).
+Orders were chosen by measuring against brute-force adaptive quadrature;
+tests/test_oracle_assembly.py pins the result in every regime: lags 0-2 on
+tiny meshes, and lags 8, 9, 31, 32, 33, 100 (and 255) on the meshes where one
+step's diffusion length is shortest against the pieces (unit square with
+h = 1/16 and N_t = 512, the seeded L-shape at its shortest and longest
+segments, the alpha = 10 example at level 4, the star).
 """
 from dataclasses import dataclass
 

@@ -18,12 +18,42 @@ from oracle.geometry import BoundaryMesh
 mp = pytest.importorskip("mpmath")
 
 
+def g_kernel(kind, c, s, al):
+    """The time kernel G whose double integral over two steps is wanted, with
+    c = alpha r^2 / 4: (1/alpha) U* for V, (1/alpha) d_{n_y} U* / q for K and
+    d_s U* for the time term of D (Section 1, U* = alpha/(4 pi s) e^{-c/s})."""
+    e = np.exp(-c / s)
+    if kind == 'V':
+        return e / (4 * np.pi * s)
+    if kind == 'K':
+        return al * e / (8 * np.pi * s * s)
+    return al / (4 * np.pi) * e * (c / s ** 3 - 1.0 / (s * s))
+
+
+def d2_hat(kind, r2, d, ht, al):
+    """The same double time integral at a lag d >= 2 written as one integral:
+    the box of tau_m convolved with the box of tau_n is the hat
+    ht - |s - d ht| on [(d-1) ht, (d+1) ht], so the entry is the integral of
+    hat x G there, by adaptive QUADPACK on each side of the peak.  G is smooth
+    on that interval (s >= ht > 0), and no second difference cancels, so this
+    stays exact at large lags where the closed form loses ~d^2 ulp."""
+    c = 0.25 * al * r2
+
+    def f(s):
+        return (ht - abs(s - d * ht)) * g_kernel(kind, c, s, al)
+    o = dict(epsabs=0.0, epsrel=1e-13, limit=200)
+    return integrate.quad(f, (d - 1) * ht, d * ht, **o)[0] + integrate.quad(f, d * ht, (d + 1) * ht, **o)[0]
+
+
 def d2(kind, r2, d, ht, al):
     """Exact double time integral of the V / K(/q) / D-time kernel at lag d.
 
-    For z = alpha r^2 / (4 ht) >= 1e-3 (and the lags d <= 3 used here) the
-    closed form in double precision loses at most ~1/z digits, so it is used
-    directly; below that the same closed form runs in 25-digit mpmath."""
+    Lags d >= 2 use the hat form d2_hat.  At lags 0 and 1 with
+    z = alpha r^2 / (4 ht) >= 1e-3 the closed form in double precision loses
+    at most ~1/z digits, so it is used directly; below that the same closed
+    form runs in 25-digit mpmath."""
+    if d >= 2:
+        return d2_hat(kind, r2, d, ht, al)
     if al * r2 / (4.0 * ht) >= 1e-3:
         from scipy.special import exp1, expn
         c = al * r2 / 4.0
@@ -107,25 +137,36 @@ def bf_V(m, i, j, d):
     return piece_integral('V', m, m.a[i], m.b[i], m.a[j], m.b[j], m.n[j], d)
 
 
+def _collinear(m, i, j):
+    """Pieces i and j on one straight line: q = (x - y) . n_y vanishes there."""
+    cr = lambda u, v: u[0] * v[1] - u[1] * v[0]     # noqa: E731
+    return abs(cr(m.t[i], m.t[j])) < 1e-12 and abs(cr(m.t[i], m.a[j] - m.a[i])) < 1e-12 * m.h[i]
+
+
 def bf_K(m, i, p, d):
     N = m.N
     tot = 0.0
     for j, wb in ((p % N, (1.0, 0.0)), ((p - 1) % N, (0.0, 1.0))):
-        if j == i:
-            continue
+        if j == i or _collinear(m, i, j):
+            continue            # the double-layer kernel is identically 0 there
         tot += piece_integral('K', m, m.a[i], m.b[i], m.a[j], m.b[j], m.n[j], d, wb=wb)
     return tot
 
 
-def bf_D(m, l, k, d):
-    tot = 0.0
+def bf_D(m, l, k, d, magnitude=False):
+    """D entry by brute force; with magnitude=True also the sum of the
+    magnitudes of its 2 x 16 piece integrals (each is only accurate to
+    QUADPACK's epsrel, so a D entry that cancels is known to ~1e-12 of it)."""
+    tot, mag = 0.0, 0.0
     for pa, a0, a1, sa in m.dual_pieces(l):
         for pb, b0, b1, sb in m.dual_pieces(k):
             A0, A1, B0, B1 = m.hs0[pa], m.hs1[pa], m.hs0[pb], m.hs1[pb]
-            tot += sa * sb * piece_integral('V', m, A0, A1, B0, B1, m.hs_n[pb], d)
-            tot += (m.hs_n[pa] @ m.hs_n[pb]) * piece_integral(
+            a = sa * sb * piece_integral('V', m, A0, A1, B0, B1, m.hs_n[pb], d)
+            b = (m.hs_n[pa] @ m.hs_n[pb]) * piece_integral(
                 '1', m, A0, A1, B0, B1, m.hs_n[pb], d, wa=(a0, a1), wb=(b0, b1))
-    return tot
+            tot += a + b
+            mag += abs(a) + abs(b)
+    return (tot, mag) if magnitude else tot
 
 
 def _meshes():
@@ -174,6 +215,87 @@ def test_D_entries_brute_force_lshape():
     for l, k, d in [(2, 3, 0), (1, 5, 1)]:
         got = assembly.D_entries(m, d, np.array([l]), np.array([k]))[0]
         _check(got, bf_D(m, l, k, d), abs(got))
+
+
+@pytest.mark.parametrize("kind", ['V', 'K', '1'])
+def test_hat_form_matches_closed_form(kind):
+    """d2_hat (adaptive quadrature of hat x G) against the closed-form second
+    difference in 40-digit mpmath, at lags where the spatial rule changes
+    and far beyond; this pins the time part of the high-lag brute force."""
+    mp.mp.dps = 40
+    ht, al = 1.0 / 512, 0.7
+    for d in (4, 8, 32, 100, 400):
+        for r2 in (1e-6, 1e-3, 3e-2, 0.5):
+            c = mp.mpf(al) * mp.mpf(r2) / 4
+
+            def F(s):
+                s = mp.mpf(s)
+                z = c / s
+                if kind == 'V':
+                    return s / (4 * mp.pi) * (mp.e1(z) - mp.expint(2, z))
+                if kind == 'K':
+                    return mp.mpf(al) / (8 * mp.pi * c) * s * mp.expint(2, z)
+                return mp.mpf(al) / (4 * mp.pi) * mp.e1(z)
+            ref = float(F((d + 1) * ht) - 2 * F(d * ht) + F((d - 1) * ht))
+            got = d2_hat(kind, r2, d, ht, al)
+            assert abs(got - ref) <= 1e-12 * abs(ref), (kind, d, r2, got, ref)
+
+
+def _high_lag_cases():
+    """Meshes where the diffusion length of one step is shortest against the
+    pieces among the workloads, with the lags around the changes of the
+    spatial order (8 and 6 points at d = 8, 4 points from d = 32)."""
+    lsh = W.config('lshape1024')
+    star = W.star_corners(16, seed=5)
+    return {
+        # ragged batch extreme: h = 1/16 with N_t = 512 (sqrt(4 d ht / alpha) = 4 h at d = 8)
+        'square_h16_nt512': (BoundaryMesh(W.unit_square(16), 1.0, 512, 1.0), (8, 9, 31, 32, 33, 100)),
+        # the precision workload: seeded lengths in [0.5, 1.5] h, pairs at the shortest and longest
+        'lshape1024': (BoundaryMesh(lsh.vertices, lsh.T, lsh.n_t, lsh.alpha), (8, 9, 31, 32, 33, 100)),
+        # the paper's example (alpha = 10) at level 4: sqrt(4 d ht / alpha) = 7.2 h at d = 8
+        'section4_L4': (BoundaryMesh(W.unit_square(16), 1.0, 16, 10.0), (8, 9, 15)),
+        # the differentiation workload: corners with unequal edges
+        'star256': (BoundaryMesh(W.subdivision_matrix(16, 16) @ star, 1.0, 256, 1.0), (8, 32, 100, 255)),
+    }
+
+
+def _pairs_around(m, i):
+    N = m.N
+    return [(i, i), (i, (i + 1) % N), ((i - 1) % N, i), (i, (i + 2) % N), (i, (i + 5) % N),
+            (i, (i + N // 2) % N)]
+
+
+@pytest.mark.parametrize("name", ['square_h16_nt512', 'lshape1024', 'section4_L4', 'star256'])
+def test_high_lag_entries_brute_force(name):
+    """V, K and D entries of every pair class at lags >= 8 (the 6- and
+    4-point spatial rules) against adaptive quadrature in space with the hat
+    form in time, to the rule's stated bound 2e-11 (floored at 1e-6 of the
+    largest entry of the lag).  On the L-shape the pairs sit at the shortest
+    and the longest segment."""
+    m, lags = _high_lag_cases()[name]
+    centres = [int(np.argmin(m.h)), int(np.argmax(m.h))] if name == 'lshape1024' else [0]
+    pairs = [p for i in centres for p in _pairs_around(m, i)]
+    I = np.array([p[0] for p in pairs])
+    J = np.array([p[1] for p in pairs])
+    for d in lags:
+        V = assembly.V_entries(m, d, I, J)
+        K = assembly.K_entries(m, d, I, J)
+        sV, sK = np.abs(V).max(), np.abs(K).max()
+        for (i, j), v, kk in zip(pairs, V, K):
+            _check(v, bf_V(m, min(i, j), max(i, j), d), sV)
+            rk = bf_K(m, i, j, d)
+            if rk == 0.0:       # trial support collinear with gamma_i: K = 0, the rule gives noise
+                assert abs(kk) <= 1e-12 * sK, (d, i, j, kk, sK)
+            else:
+                _check(kk, rk, sK)
+        # D: identical, adjacent and separated dual functions at the first centre
+        c = centres[0]
+        dp = [(c, c), (c, (c + 1) % m.N), (c, (c + 3) % m.N)]
+        Dg = assembly.D_entries(m, d, np.array([p[0] for p in dp]), np.array([p[1] for p in dp]))
+        for (l, k), got in zip(dp, Dg):
+            ref, mag = bf_D(m, l, k, d, magnitude=True)
+            assert abs(got - ref) <= 2e-11 * max(abs(ref), 1e-6 * np.abs(Dg).max()) + 2e-12 * mag, \
+                (d, l, k, got, ref, mag)
 
 
 def test_hypersingular_form_matches_normal_derivative_kernel():
@@ -248,6 +370,20 @@ def test_K_vanishes_on_collinear_pairs_and_V_D_symmetric():
     for o in 'VD':
         A = assembly.assemble(o, m)
         assert np.array_equal(A, np.transpose(A, (0, 2, 1)))
+
+
+def test_exact_sum_D_within_rounding_of_plain_sum():
+    """exact=True (math.fsum over every point term of an entry) differs from
+    the plain numpy sums by rounding only: at most a few eps S, S the sum of
+    the term magnitudes; both are symmetric in (l, k)."""
+    m = BoundaryMesh(W.l_shape(16, seed=3), 1.0, 5, 0.5)
+    D = assembly.assemble('D', m)
+    De = assembly.assemble('D', m, exact=True)
+    S = assembly.assemble('D', m, magnitude=True)
+    assert np.all(np.abs(D - De) <= 4 * 2.0 ** -52 * S)
+    assert np.array_equal(De, np.transpose(De, (0, 2, 1)))
+    # lag-0 diagonal entries (no cancellation) agree to a few ulp
+    assert np.allclose(np.diagonal(D[0]), np.diagonal(De[0]), rtol=1e-14, atol=0)
 
 
 def test_positive_definite_square32():
