@@ -45,7 +45,8 @@ def test_assembly_matches_oracle(ctx, name, op):
     import paper_1811_05224_gb300 as P
     m, om = _pair(ctx, *SMALL[name])
     A = P.assemble(ctx, m, op, "f64").cpu().numpy()
-    B = OA.assemble(op, om)
+    # D against the exactly summed oracle entries (its rounding is measured in eps S)
+    B = OA.assemble(op, om, exact=(op == "D"))
     if op == "D":
         err = d_rel_err(A, B, OA.assemble("D", om, magnitude=True))
         assert err.max() <= 1.0, (name, op, err.max(), int(err.argmax()))
@@ -87,11 +88,11 @@ def test_assembly_sampled_full_size(ctx):
             J = np.array([b for _, b in pairs])
             got = A[d, torch.as_tensor(I), torch.as_tensor(J)].cpu().numpy()
             fn = {"V": OA.V_entries, "K": OA.K_entries, "D": OA.D_entries}[op]
-            ref = fn(om, d, I, J)
+            ref = fn(om, d, I, J, exact=True) if op == "D" else fn(om, d, I, J)
             scale = float(A[d].abs().max())
             den = 1e-12 * np.maximum(np.abs(ref), 1e-6 * scale)
             if op == "D":
-                den = den + 1e-14 * OA.D_entries(om, d, I, J, magnitude=True)
+                den = den + 4e-15 * OA.D_entries(om, d, I, J, magnitude=True)
             err = np.abs(got - ref) / den
             assert err.max() <= 1.0, (op, d, pairs[int(err.argmax())], err.max())
 
@@ -265,7 +266,9 @@ def test_consistent_mixed_mass_preconditioner(ctx):
     D = P.assemble(ctx, m, "D")
     L = P.lumped_mass(ctx, m)
     g, f = P.rhs(ctx, m, K, (1.5, 1.5))
-    Vn, fn = V.cpu().numpy(), f.cpu().numpy()
+    # references from the oracle's V (exact block substitutions), on the
+    # same right-hand side
+    Vn, fn = OA.assemble("V", om), f.cpu().numpy()
     wref = OS.forward_substitution(Vn, fn)
     w2, i2 = P.solve(ctx, V, f, D, P.mixed_mass_inverse(ctx, m), tol=1e-11)
     w1, i1 = P.solve(ctx, V, f, D, L, tol=1e-11)
