@@ -43,7 +43,8 @@ extern "C" {
 #define STBEM_ERR_CUDA (-2)      /* a CUDA runtime call failed               */
 #define STBEM_ERR_NOMEM (-3)     /* caller workspace too small               */
 #define STBEM_ERR_NOCONV (-4)    /* iteration cap reached before tolerance   */
-#define STBEM_ERR_BREAKDOWN (-5) /* GMRES breakdown (zero Krylov vector)     */
+#define STBEM_ERR_BREAKDOWN (-5) /* GMRES breakdown: a zero Givens pivot,    */
+                                 /* i.e. a singular (preconditioned) operator */
 #define STBEM_ERR_NAN (-6)       /* NaN or Inf met in a residual             */
 #define STBEM_ERR_TIMEOUT (-7)   /* a bounded device-side wait gave up       */
 
@@ -71,6 +72,15 @@ const char* stbem_version(void);
 /* Number of CUDA kernels this library has launched in the process (all
  * contexts); a diagnostic counter with no counterpart in the paper. */
 unsigned long long stbem_launch_count(void);
+
+/* Measured arithmetic-pipe rates of the context's device (a diagnostic with
+ * no counterpart in the paper; the denominators of the rooflines of the
+ * ALU-bound kernels): host_out[0] = FP64 FMA TFLOP/s, host_out[1] = FP32 FMA
+ * TFLOP/s, host_out[2] = MUFU ex2 results per second in units of 1e12.
+ * Independent FMA / ex2 chains on every SM, timed with CUDA events on the
+ * context's stream (about 50 ms).  Blocks the host.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_CUDA. */
+int stbem_pipe_peaks(stbem_ctx* ctx, double* host_out);
 
 /* Boundary mesh Gamma_h x I_h (Section 1: tensor-product decomposition of
  * Sigma).  host_xy: 2*n_x doubles (x_0, y_0, x_1, y_1, ...), a closed
@@ -118,7 +128,11 @@ int stbem_assemble_lags(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec
  * are FP64, n_rhs x n_t x n_x, and must not overlap.  Accumulation is in the
  * precision of A (FP64 for F64, FP32 for F32).  dev_work must hold
  * stbem_apply_workspace_bytes() bytes (partial sums over lag chunks, so the
- * result is deterministic).  Errors: STBEM_ERR_ARG, STBEM_ERR_NOMEM. */
+ * result is deterministic).  The workspace size and the launch shape depend
+ * on the SM count of the device that is current when they are computed.
+ * Errors: STBEM_ERR_ARG (also when n_rhs times the number of 32-step time
+ * tiles exceeds 65535, the grid limit: split the right-hand sides),
+ * STBEM_ERR_NOMEM. */
 int stbem_apply_workspace_bytes(int n_t, int n_x, int n_rhs, int prec, size_t* bytes);
 int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
                 const void* dev_A, int n_rhs, const double* dev_x, double* dev_y,
@@ -132,13 +146,15 @@ int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
  * arguments and result as stbem_apply, minus the workspace: the lag-chunk
  * partial sums go to a fixed scratch array inside the library's device image
  * (32 MiB; every GPU that loads the library holds it until the process exits).
- * The first call on a device looks up that array's device address; make that
- * first call before any stream capture.  Calls share the one array: two calls
+ * The first call in each CUDA context of a device looks up that array's device
+ * address (after a cudaDeviceReset the next call looks it up again in the new
+ * context); make that first call before any stream capture.  Calls share the one array: two calls
  * that overlap on the GPU (other streams, other threads, other contexts on the
  * same device) race on it and must be serialised by the caller.  Each call
  * writes every scratch entry it later reads, so nothing has to start at zero
  * and the previous call's leftovers are never read.  Allocates nothing (no
- * cudaMalloc, no allocating library call).  Errors: STBEM_ERR_ARG;
+ * cudaMalloc, no allocating library call).  Errors: STBEM_ERR_ARG (as
+ * stbem_apply, including the grid limit on n_rhs);
  * STBEM_ERR_NOMEM if the product needs more scratch than the fixed array
  * holds (stbem_apply_workspace_bytes() > 32 MiB); STBEM_ERR_CUDA. */
 int stbem_apply_noalloc(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x,
@@ -161,6 +177,20 @@ int stbem_to_bf16(stbem_ctx* ctx, int src_prec, size_t n, const void* dev_src, v
  * STBEM_ERR_CUDA. */
 int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_bf16, int n_rhs, const void* dev_x_bf16,
                    double* dev_y);
+
+/* Diagnostic with no counterpart in the paper: exercises the time-out path of
+ * the tensor-core product.  With stall != 0, every later plain tensor-core
+ * product (stbem_apply_tc, and those inside stbem_solve_batched; any context)
+ * makes its kernel wait on a pipeline barrier that no thread
+ * ever arrives on, and every pipeline wait of that kernel gives up after
+ * wait_cycles SM clock cycles (>= 1024).  The kernel then lets the tensor-
+ * memory operations and copies it has issued complete (each such wait bounded
+ * by about one second), releases its tensor memory and exits; the call
+ * returns STBEM_ERR_TIMEOUT and y is incomplete.  stall = 0 restores normal
+ * operation (wait_cycles is then ignored).  Must not be changed while a
+ * tensor-core call is in progress on another thread.  Errors: STBEM_ERR_ARG
+ * (stall != 0 with wait_cycles < 1024). */
+int stbem_debug_tc_stall(int stall, long long wait_cycles);
 
 /* The same product with compensated accumulation: the tensor cores restart
  * their FP32 accumulator every `chunk` 64-wide K steps (chunk >= 1; one K
@@ -224,7 +254,10 @@ int stbem_solve_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes);
  * the same precision; dev_D and dev_L may be NULL when opts->precondition is
  * 0); dev_L: lumped dual mass (n_x doubles); dev_f, dev_w: n_t x n_x doubles.
  * Blocks the host (reads a residual each iteration).  Returns STBEM_OK,
- * STBEM_ERR_NOCONV, _BREAKDOWN or _NAN (also stored in info->status). */
+ * STBEM_ERR_NOCONV (opts->max_iter reached), _BREAKDOWN (a Krylov step gave a
+ * zero pivot, so V_h or the preconditioner is singular; w then holds the
+ * iterate of the last completed restart cycle) or _NAN (also stored in
+ * info->status). */
 int stbem_solve(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void* dev_V,
                 const void* dev_D, const double* dev_L, const double* dev_f,
                 double* dev_w, const stbem_solve_opts* opts, stbem_solve_info* info,
@@ -315,18 +348,24 @@ int stbem_half_mass_add(stbem_ctx* ctx, const stbem_mesh* mesh, int n_rhs, const
  * orthogonalisation, a Hessenberg matrix and a convergence mask per
  * right-hand side; each inner solve reduces its residual by inner_tol.  Around
  * it, refinement with the residual R = F - V W from the three-slice split of V
- * (dev_V_hi/mid/lo) until ||R_b|| / ||F_b|| <= opts->tol for every b (the
- * split product limits attainable residuals to ~1e-6).  opts->restart is the
- * Krylov dimension of an inner solve, opts->max_iter caps inner iterations.
- * infos: n_rhs results.  Workspace: stbem_solve_batched_workspace_bytes().
- * Requires n_x % 8 == 0.  Blocks the host.  Errors: STBEM_ERR_ARG,
- * STBEM_ERR_NOMEM, STBEM_ERR_NOCONV / _NAN (some right-hand side; see infos),
- * STBEM_ERR_TIMEOUT, STBEM_ERR_CUDA. */
-int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, size_t* bytes);
+ * (dev_V_hi/mid/lo); that product is accurate to a few 1e-7 of |V||W|, which
+ * limits attainable residuals to ~1e-6.  With dev_V64 (the FP64 operator, may
+ * be NULL) refinement continues, once every relative residual is below 2e-6,
+ * on the FP64 residual F - V64 W (CUDA-core FP64 product of all right-hand
+ * sides), so that ||R_b|| / ||F_b|| <= opts->tol holds for the FP64 operator
+ * and the solutions carry FP64-solve accuracy; without it the stop is on the
+ * split residual.  opts->restart is the Krylov dimension of an inner solve,
+ * opts->max_iter caps inner iterations.  infos: n_rhs results (rel_residual:
+ * the last residual tested).  Workspace: stbem_solve_batched_workspace_bytes()
+ * with fp64_residual != 0 when dev_V64 is given (it then adds the FP64
+ * product's partial sums).  Requires n_x % 8 == 0.  Blocks the host.  Errors:
+ * STBEM_ERR_ARG, STBEM_ERR_NOMEM, STBEM_ERR_NOCONV / _NAN / _BREAKDOWN (some
+ * right-hand side; see infos), STBEM_ERR_TIMEOUT, STBEM_ERR_CUDA. */
+int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, int fp64_residual, size_t* bytes);
 int stbem_solve_batched(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void* dev_V_hi, const void* dev_V_mid,
-                        const void* dev_V_lo, const void* dev_D_bf16, const double* dev_L, const double* dev_F,
-                        double* dev_W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
-                        void* dev_work, size_t work_bytes);
+                        const void* dev_V_lo, const void* dev_D_bf16, const double* dev_L, const double* dev_V64,
+                        const double* dev_F, double* dev_W, const stbem_solve_opts* opts, double inner_tol,
+                        stbem_solve_info* infos, void* dev_work, size_t work_bytes);
 
 /* ---- Ragged batches ----------------------------------------------------------
  * Many independent problems of different sizes (not in the paper, which solves

@@ -314,6 +314,14 @@ def grad(ctx: Context, mesh: Mesh, K, y_star, g, w, lam, work=None):
     return dxy, dal[0]
 
 
+def pipe_peaks(ctx: Context):
+    """Measured pipe rates of the context's GPU (stbem_pipe_peaks): FP64 and
+    FP32 FMA TFLOP/s and MUFU ex2 results per second (1e12)."""
+    out = (ctypes.c_double * 3)()
+    ctx.check(ctx.lib.stbem_pipe_peaks(ctx.h, out))
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1], "ex2_tera_per_s": out[2]}
+
+
 def round_f32(ctx: Context, A):
     """FP32 copy of an FP64 operator (rounded by a library kernel)."""
     out = torch.empty(A.shape, dtype=torch.float32, device=A.device)
@@ -390,22 +398,30 @@ def apply_tc3(ctx: Context, A_slices, x, out=None, work=None):
     return out if x.dim() == 3 else out[0]
 
 
-def rhs_batched(ctx: Context, mesh: Mesh, K_slices, y_stars):
+def rhs_batched(ctx: Context, mesh: Mesh, K, y_stars):
     """(G, F) for many sources: G[k] vertex time averages of U*(x - y_k, t),
-    F = 1/2 M_h G + K_h G with K_h from its three BF16 slices (tensor cores)."""
+    F = 1/2 M_h G + K_h G.  K is the FP64 operator (an FP64 CUDA-core product
+    of all right-hand sides: F to FP64 accuracy) or a tuple of its three BF16
+    slices (the compensated tensor-core product, a few 1e-7 of |K||G|)."""
     ys = np.ascontiguousarray(np.asarray(y_stars, dtype=np.float64).reshape(-1))
     B = ys.size // 2
     G = ctx.empty((B, mesh.n_t, mesh.n_x))
     ctx.check(ctx.lib.stbem_rhs_g_batched(ctx.h, mesh.h, B, ys.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                           _ptr(G)))
-    F = apply_tc3(ctx, K_slices, G)
+    if isinstance(K, (tuple, list)):
+        F = apply_tc3(ctx, K, G)
+    else:
+        F = apply(ctx, K, G)
     ctx.check(ctx.lib.stbem_half_mass_add(ctx.h, mesh.h, B, _ptr(G), _ptr(F)))
     return G, F
 
 
 def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1e-6, inner_tol: float = 1e-2,
-                  max_iter: int = 400, restart: int = 40, work=None, out=None, raise_on_fail: bool = True):
-    """Many-right-hand-side solve on the tensor cores; returns (W, infos)."""
+                  max_iter: int = 400, restart: int = 40, work=None, out=None, raise_on_fail: bool = True,
+                  V64=None):
+    """Many-right-hand-side solve on the tensor cores; returns (W, infos).
+    With the FP64 operator V64 the refinement finishes on FP64 residuals
+    (FP64-solve accuracy for tol down to 1e-8 and below)."""
     B, n_t, n_x = F.shape
     opts = capi.SolveOpts(tol, max_iter, restart, int(D_bf16 is not None))
     infos = (capi.SolveInfo * B)()
@@ -413,12 +429,13 @@ def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1
         out = torch.empty_like(F)
     if work is None:
         nb = ctypes.c_size_t()
-        ctx.check(ctx.lib.stbem_solve_batched_workspace_bytes(n_t, n_x, B, restart, ctypes.byref(nb)))
+        ctx.check(ctx.lib.stbem_solve_batched_workspace_bytes(n_t, n_x, B, restart, int(V64 is not None),
+                                                              ctypes.byref(nb)))
         work = torch.empty(nb.value, dtype=torch.uint8, device=F.device)
     Vs = list(V_slices) + [None] * (3 - len(V_slices))
     code = ctx.lib.stbem_solve_batched(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]), _ptr(D_bf16),
-                                       _ptr(L), _ptr(F), _ptr(out), ctypes.byref(opts), float(inner_tol), infos,
-                                       _ptr(work), work.numel())
+                                       _ptr(L), _ptr(V64), _ptr(F), _ptr(out), ctypes.byref(opts),
+                                       float(inner_tol), infos, _ptr(work), work.numel())
     res = [{"iterations": i.iterations, "status": i.status, "rel_residual": i.rel_residual} for i in infos]
     if code != capi.STBEM_OK and raise_on_fail:
         ctx.check(code)

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libstbem.so")
-SOURCES = ["assemble.cu", "grad.cu", "initial.cu", "toeplitz.cu", "toeplitz_tc.cu", "vec.cu", "capi.cpp", "initial_capi.cpp",
-           "ragged.cpp", "rules_host.cpp"]
+SOURCES = ["assemble.cu", "grad.cu", "initial.cu", "toeplitz.cu", "toeplitz_tc.cu", "vec.cu", "peaks.cu", "capi.cpp",
+           "initial_capi.cpp", "ragged.cpp", "rules_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

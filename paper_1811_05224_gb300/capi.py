@@ -30,7 +30,7 @@ EXPORTS = [
     "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_assemble_lags", "stbem_apply_workspace_bytes",
     "stbem_apply", "stbem_apply_noalloc", "stbem_rhs", "stbem_lumped_mass", "stbem_solve_workspace_bytes", "stbem_solve",
     "stbem_solve_mixed_workspace_bytes", "stbem_solve_mixed", "stbem_round_f32",
-    "stbem_to_bf16", "stbem_apply_tc", "stbem_apply_tc_comp", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
+    "stbem_to_bf16", "stbem_apply_tc", "stbem_apply_tc_comp", "stbem_debug_tc_stall", "stbem_pipe_peaks", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
     "stbem_apply_tc3", "stbem_rhs_g_batched", "stbem_half_mass_add", "stbem_solve_batched_workspace_bytes",
     "stbem_solve_batched", "stbem_solve_adjoint", "stbem_grad_workspace_bytes", "stbem_grad",
     "stbem_ragged_create", "stbem_ragged_destroy", "stbem_ragged_sizes", "stbem_ragged_offsets",
@@ -121,14 +121,17 @@ def load(path: str = LIB_PATH):
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]
     L.stbem_to_bf16.argtypes = [vp, i, sz, vp, vp]
     L.stbem_apply_tc.argtypes = [vp, i, i, vp, i, vp, vp]
+    L.stbem_debug_tc_stall.argtypes = [i, ctypes.c_longlong]
+    L.stbem_pipe_peaks.argtypes = [vp, P(d)]
     L.stbem_apply_tc_comp.argtypes = [vp, i, i, vp, i, vp, vp, i]
     L.stbem_bf16_split3.argtypes = [vp, sz, vp, vp, vp, vp]
     L.stbem_apply_tc3_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_apply_tc3.argtypes = [vp, i, i, vp, vp, vp, i, vp, vp, vp, sz]
     L.stbem_rhs_g_batched.argtypes = [vp, vp, i, P(d), vp]
     L.stbem_half_mass_add.argtypes = [vp, vp, i, vp, vp]
-    L.stbem_solve_batched_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
-    L.stbem_solve_batched.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
+    L.stbem_solve_batched_workspace_bytes.argtypes = [i, i, i, i, i, P(sz)]
+    L.stbem_solve_batched.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo),
+                                      vp, sz]
     L.stbem_domain_create.argtypes = [vp, vp, P(d), i, P(i), i, P(vp)]
     L.stbem_domain_destroy.argtypes = [vp]
     L.stbem_domain_destroy.restype = None

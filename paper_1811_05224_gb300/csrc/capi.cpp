@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/stbem.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -224,6 +225,8 @@ int stbem_apply(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x, const
   if (n_t < 1 || n_x < 1 || n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "apply: bad sizes");
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "apply: bad precision");
   if ((const void*)x == (const void*)y) return fail(ctx, STBEM_ERR_ARG, "apply: x and y overlap");
+  if (!stbem::apply_grid_fits(n_t, n_x, n_rhs))
+    return fail(ctx, STBEM_ERR_ARG, "apply: n_rhs x time tiles exceeds the grid limit 65535; split the right-hand sides");
   const size_t need = stbem::apply_workspace_bytes(n_t, n_x, n_rhs);
   if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "apply: workspace %zu < %zu bytes", work_bytes, need);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply: set device");
@@ -238,6 +241,9 @@ int stbem_apply_noalloc(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_
   if (n_t < 1 || n_x < 1 || n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: bad sizes");
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: bad precision");
   if ((const void*)x == (const void*)y) return fail(ctx, STBEM_ERR_ARG, "apply_noalloc: x and y overlap");
+  if (!stbem::apply_grid_fits(n_t, n_x, n_rhs))
+    return fail(ctx, STBEM_ERR_ARG,
+                "apply_noalloc: n_rhs x time tiles exceeds the grid limit 65535; split the right-hand sides");
   const size_t need = stbem::apply_workspace_bytes(n_t, n_x, n_rhs);
   if (need > stbem::kNoAllocScratchBytes)
     return fail(ctx, STBEM_ERR_NOMEM,
@@ -282,6 +288,20 @@ int apply_tc_entry(stbem_ctx* ctx, const char* name, int n_t, int n_x, const voi
 
 int stbem_apply_tc(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y) {
   return apply_tc_entry(ctx, "apply_tc", n_t, n_x, A, n_rhs, x, y, 0);
+}
+
+int stbem_pipe_peaks(stbem_ctx* ctx, double* host_out) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!host_out) return fail(ctx, STBEM_ERR_ARG, "pipe_peaks: NULL pointer");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "pipe_peaks: set device");
+  CUDA_TRY(ctx, stbem::pipe_peaks(host_out, ctx->stream), "pipe_peaks");
+  return STBEM_OK;
+}
+
+int stbem_debug_tc_stall(int stall, long long wait_cycles) {
+  if (stall && wait_cycles < 1024) return STBEM_ERR_ARG;
+  stbem::tc_set_stall(stall ? wait_cycles : 0);
+  return STBEM_OK;
 }
 
 int stbem_apply_tc_comp(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y,
@@ -380,23 +400,33 @@ struct BatchWork {
   void* xb;                          // BF16 vector scratch (3 slices)
 };
 
-size_t batch_bytes(int nt, int nx, int B, int m) {
+size_t batch_base_bytes(int nt, int nx, int B, int m) {
   const size_t n = (size_t)B * nt * nx;
   return ((size_t)(m + 1) * n + 4 * n + (size_t)(m + 4) * B) * sizeof(double) + 3 * n * 2 + 256;
 }
+// with an FP64 residual operator: + the FP64 product's lag-chunk partial sums
+size_t batch_bytes(int nt, int nx, int B, int m, bool fp64_residual) {
+  size_t b = batch_base_bytes(nt, nx, B, m);
+  if (fp64_residual) b = ((b + 255) & ~(size_t)255) + stbem::apply_workspace_bytes(nt, nx, B);
+  return b;
+}
+
+// The three-slice tensor-core residual is accurate to a few 1e-7 of |V||W|;
+// refinement switches to the FP64 residual below this relative residual.
+constexpr double kTc3ResidualFloor = 2e-6;
 
 }  // namespace
 
-int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, size_t* bytes) {
+int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, int fp64_residual, size_t* bytes) {
   if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || restart < 1) return STBEM_ERR_ARG;
-  *bytes = batch_bytes(n_t, n_x, n_rhs, restart);
+  *bytes = batch_bytes(n_t, n_x, n_rhs, restart, fp64_residual != 0);
   return STBEM_OK;
 }
 
 int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
-                        const void* V_lo, const void* D_bf16, const double* Lm, const double* F, double* W,
-                        const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos, void* work,
-                        size_t work_bytes) {
+                        const void* V_lo, const void* D_bf16, const double* Lm, const double* V64, const double* F,
+                        double* W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
+                        void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!V_hi || !F || !W || !opts || !infos || !work) return fail(ctx, STBEM_ERR_ARG, "solve_batched: NULL pointer");
   if (!stbem::apply_tc_supported(nt, nx, B)) return fail(ctx, STBEM_ERR_ARG, "solve_batched: unsupported sizes");
@@ -407,7 +437,10 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
   if (prec && (!D_bf16 || !Lm)) return fail(ctx, STBEM_ERR_ARG, "solve_batched: preconditioner needs D and L");
   if (opts->precondition == 2)
     return fail(ctx, STBEM_ERR_ARG, "solve_batched: the lumped mass (precondition = 1) only");
-  if (work_bytes < batch_bytes(nt, nx, B, m)) return fail(ctx, STBEM_ERR_NOMEM, "solve_batched: workspace too small");
+  if (V64 && !stbem::apply_grid_fits(nt, nx, B))
+    return fail(ctx, STBEM_ERR_ARG, "solve_batched: too many right-hand sides for the FP64 residual product");
+  if (work_bytes < batch_bytes(nt, nx, B, m, V64 != nullptr))
+    return fail(ctx, STBEM_ERR_NOMEM, "solve_batched: workspace too small");
   const size_t N = (size_t)nt * nx, n = (size_t)B * N;
   BatchWork Wk;
   double* p = static_cast<double*>(work);
@@ -418,6 +451,8 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
   Wk.DW = p; p += n;
   Wk.h = p; p += (size_t)(m + 4) * B;
   Wk.xb = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
+  // FP64 product partial sums after the base workspace
+  void* part64 = static_cast<char*>(work) + ((batch_base_bytes(nt, nx, B, m) + 255) & ~(size_t)255);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_batched: set device");
   cudaStream_t s = ctx->stream;
   CUDA_TRY(ctx, stbem::tc_error_reset(s), "solve_batched: reset error word");
@@ -451,18 +486,36 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
     infos[b].status = std::isfinite(normF[b]) ? STBEM_OK : STBEM_ERR_NAN;
     infos[b].rel_residual = 0.0;
   }
+  // refinement residual R = F - V W: the three-slice tensor-core product
+  // first, then (with V64) the FP64 product once that one reaches its floor
+  bool fp64_phase = false;
+  const double tol_tc = V64 ? std::max(opts->tol, kTc3ResidualFloor) : opts->tol;
+  auto residual = [&]() -> cudaError_t {
+    cudaError_t e = fp64_phase ? stbem::apply_launch(STBEM_F64, false, nt, nx, V64, B, W, Wk.U, part64, s)
+                               : apply_tc3(nt, nx, Vs, B, W, Wk.U, Wk.xb, s);
+    if (e == cudaSuccess) e = stbem::sub_launch(F, Wk.U, Wk.R, n, s);
+    return e;
+  };
   int total = 0;
   bool any_active = true;
-  for (int outer = 0; outer < 30 && any_active; ++outer) {
+  for (int outer = 0; outer < 40 && any_active; ++outer) {
     CUDA_TRY(ctx, bnorms(Wk.R, rn), "solve_batched: norm R");
     std::vector<char> active(B, 0);
     any_active = false;
+    const double target = fp64_phase ? opts->tol : tol_tc;
     for (int b = 0; b < B; ++b) {
       const double rel = normF[b] > 0 ? rn[b] / normF[b] : 0.0;
       if (!std::isfinite(rel)) infos[b].status = STBEM_ERR_NAN;
       infos[b].rel_residual = rel;
-      active[b] = infos[b].status == STBEM_OK && rel > opts->tol;
+      active[b] = infos[b].status == STBEM_OK && rel > target;
       any_active = any_active || active[b];
+    }
+    if (!any_active && V64 && !fp64_phase && opts->tol < tol_tc) {
+      // the tensor-core residual is at its floor: continue on the FP64 residual
+      fp64_phase = true;
+      CUDA_TRY(ctx, residual(), "solve_batched: FP64 residual");
+      any_active = true;
+      continue;
     }
     if (!any_active) break;
     if (total >= maxit) {
@@ -525,6 +578,12 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
           col[t] = a;
         }
         const double den = std::hypot(col[k], hk1);
+        if (!(den > 0.0)) {        // zero pivot: singular preconditioned operator
+          infos[b].status = STBEM_ERR_BREAKDOWN;
+          done[b] = 1;
+          kb[b] = k;
+          continue;
+        }
         cb[k] = den > 0 ? col[k] / den : 1.0;
         sb[k] = den > 0 ? hk1 / den : 0.0;
         col[k] = den;
@@ -559,9 +618,8 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
       CUDA_TRY(ctx, applyP(Wk.U, Wk.DW), "P QY");
       CUDA_TRY(ctx, stbem::axpy_launch(1.0, Wk.DW, W, n, s), "W += dW");
     }
-    // refinement residual R = F - V W with the three-slice split of V and W
-    CUDA_TRY(ctx, apply_tc3(nt, nx, Vs, B, W, Wk.U, Wk.xb, s), "V W");
-    CUDA_TRY(ctx, stbem::sub_launch(F, Wk.U, Wk.R, n, s), "R");
+    // refinement residual R = F - V W (the current phase's product)
+    CUDA_TRY(ctx, residual(), "solve_batched: residual");
   }
   int flag = 0;
   CUDA_TRY(ctx, stbem::tc_error_read(&flag, s), "solve_batched: read error word");
@@ -740,6 +798,9 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
         hcol[t] = a;
       }
       const double den = std::hypot(hcol[k], hk1);
+      // a zero pivot: (V P) q_k has no component outside the earlier basis
+      // and none along it, so the preconditioned operator is singular
+      if (!(den > 0.0)) { status = STBEM_ERR_BREAKDOWN; break; }
       cs[k] = hcol[k] / den;
       sn[k] = hk1 / den;
       hcol[k] = den;
@@ -799,9 +860,11 @@ int solve_impl(stbem_ctx* ctx, bool transpose, int nt, int nx, int vprec, const 
   info->iterations = iters;
   info->rel_residual = relres;
   info->status = status;
-  if (status == STBEM_ERR_NAN || status == STBEM_ERR_NOCONV)
+  if (status == STBEM_ERR_NAN || status == STBEM_ERR_NOCONV || status == STBEM_ERR_BREAKDOWN)
     return fail(ctx, status, "solve: %s after %d iterations (relres %.3e)",
-                status == STBEM_ERR_NAN ? "NaN" : "no convergence", iters, relres);
+                status == STBEM_ERR_NAN ? "NaN"
+                : status == STBEM_ERR_NOCONV ? "no convergence" : "breakdown (singular operator)",
+                iters, relres);
   return status;   // STBEM_OK, or a CUDA error already described
 }
 }  // namespace
@@ -915,7 +978,7 @@ int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const f
     double rr = 0.0;
     const int st = gmres_core(ctx, op, r, dw, inner_tol, maxit - total, restart, W, &it, &rr);
     total += it;
-    if (st == STBEM_ERR_NAN) { status = st; break; }
+    if (st == STBEM_ERR_NAN || st == STBEM_ERR_BREAKDOWN) { status = st; break; }
     if (st != STBEM_OK && st != STBEM_ERR_NOCONV) return st;
     CUDA_TRY(ctx, stbem::axpy_launch(1.0, dw, w, N, s), "solve_mixed: w += dw");
     // FP64 residual with the FP64 operator
@@ -928,7 +991,9 @@ int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const f
   info->status = status;
   if (status != STBEM_OK)
     return fail(ctx, status, "solve_mixed: %s after %d inner iterations (relres %.3e)",
-                status == STBEM_ERR_NAN ? "NaN" : "no convergence", total, relres);
+                status == STBEM_ERR_NAN ? "NaN"
+                : status == STBEM_ERR_NOCONV ? "no convergence" : "breakdown (singular operator)",
+                total, relres);
   return STBEM_OK;
 }
 

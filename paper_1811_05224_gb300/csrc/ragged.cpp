@@ -632,6 +632,13 @@ int stbem_ragged_solve(stbem_ctx* ctx, stbem_ragged* R, int prec, const void* V,
           col[t] = a;
         }
         const double den = std::hypot(col[k], hk1);
+        if (!(den > 0.0)) {        // zero pivot: singular preconditioned operator
+          infos[p].status = STBEM_ERR_BREAKDOWN;
+          infos[p].iterations = total;
+          done[p] = 1;
+          kb[p] = k;
+          continue;
+        }
         cp[k] = den > 0 ? col[k] / den : 1.0;
         sp[k] = den > 0 ? hk1 / den : 0.0;
         col[k] = den;

@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "assemble.h"
+#include "device_info.h"
 #include "toeplitz.h"
 
 namespace stbem {
@@ -32,8 +33,8 @@ static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI) {
   ApplyPlan p;
   p.MT = (nt + tm - 1) / tm;
   p.IT = (nx + ti - 1) / ti;
-  // aim at ~4 waves of 152 SMs of (tile, chunk) units
-  const long long target = 4 * 152;
+  // aim at ~4 waves of (tile, chunk) units over the device's SMs
+  const long long target = 4LL * sm_count();
   long long per_chunk = (long long)p.IT * ((p.MT + 1) / 2);
   if (per_chunk < 1) per_chunk = 1;
   int ch = (int)((target + per_chunk - 1) / per_chunk);
@@ -46,12 +47,12 @@ static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI) {
 
 // FP32 forward products use the register-tiled kernel (128 x 64 tiles) when
 // rows are 16-byte aligned and its causal tiles alone fill two waves of
-// 2 x 152 CTAs; smaller products keep the 64 x 32 tiles, which need fewer
+// 2 CTAs per SM; smaller products keep the 64 x 32 tiles, which need fewer
 // lag chunks (and partial sums) for the same parallelism.
 static bool use_apply32(int nx) { return nx % 4 == 0; }
 static bool use_apply32(int nt, int nx, int n_rhs) {
   const long long it = (nx + 127) / 128, mt = (nt + 63) / 64;
-  return use_apply32(nx) && (long long)n_rhs * it * mt * (mt + 1) / 2 >= 2 * 2 * 152;
+  return use_apply32(nx) && (long long)n_rhs * it * mt * (mt + 1) / 2 >= 2LL * 2 * sm_count();
 }
 
 size_t apply_workspace_bytes(int nt, int nx, int n_rhs) {
@@ -396,7 +397,7 @@ static cudaError_t launch32(int nt, int nx, const float* A, int n_rhs, const dou
   if (e != cudaSuccess) return e;
   count_launches(2);
   const size_t total = (size_t)n_rhs * nt * nx;
-  const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+  const int blocks = stride_grid(total, 256, 16);
   k_apply_reduce<false, TM4><<<blocks, 256, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
   return cudaGetLastError();
 }
@@ -418,7 +419,7 @@ static cudaError_t launch(bool trans, int nt, int nx, const TA* A, int n_rhs, co
   count_launches(2);
   const size_t total = (size_t)n_rhs * nt * nx;
   const int threads = 256;
-  const int blocks = (int)((total + threads - 1) / threads < 152 * 16 ? (total + threads - 1) / threads : 152 * 16);
+  const int blocks = stride_grid(total, threads, 16);
   if (trans)
     k_apply_reduce<true><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
   else
@@ -435,19 +436,59 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes /
 
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+static unsigned long long g_noalloc_ctx_id[kNoAllocMaxDevices] = {};
+
+// Unique id of the current CUDA context (driver entry points cuCtxGetCurrent
+// and cuCtxGetId, fetched through the runtime).  Ids are never reused, so a
+// context created after cudaDeviceReset has a new one.
+static cudaError_t current_context_id(unsigned long long* id) {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* p = nullptr;
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r1, r2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &q, 12000, cudaEnableDefault, &r2);
+    if (e != cudaSuccess) return e;
+    if (r1 != cudaDriverEntryPointSuccess || r2 != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    get_current = reinterpret_cast<GetCurrent>(p);
+    get_id = reinterpret_cast<GetId>(q);
+  }
+  void* c = nullptr;
+  if (get_current(&c) != 0 || !c) return cudaErrorDeviceUninitialized;
+  return get_id(c, id) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 cudaError_t noalloc_scratch_ptr(int device, void** ptr) {
   if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
-    // the caller has made `device` current; resolve the symbol on it once
+  // the caller has made `device` current (and so created its context)
+  unsigned long long id = 0;
+  cudaError_t e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  if (!g_noalloc_ptr[device] || g_noalloc_ctx_id[device] != id) {
+    // first call in this context of the device: resolve the symbol once
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[device] = p;
+    g_noalloc_ctx_id[device] = id;
   }
   *ptr = g_noalloc_ptr[device];
   return cudaSuccess;
+}
+
+bool apply_grid_fits(int nt, int nx, int n_rhs) {
+  const ApplyPlan p = make_plan(nt, nx);
+  if ((long long)n_rhs * p.MT > 65535) return false;
+  if (use_apply32(nt, nx, n_rhs)) {
+    const ApplyPlan q = make_plan(nt, nx, TM4, TI4);
+    if ((long long)n_rhs * q.MT > 65535) return false;
+  }
+  return true;
 }
 
 void ragged_apply_plan(int nt, int nx, int lags_per_chunk, bool fp32_tiles, RaggedApplyPlan* p) {

@@ -11,8 +11,16 @@ size_t apply_workspace_bytes(int nt, int nx, int n_rhs);
 constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
 constexpr int kNoAllocMaxDevices = 64;
 // Device address of that scratch on `device` (which must be current); the
-// first call per device resolves it with cudaGetSymbolAddress.
+// first call in each CUDA context of a device resolves it with
+// cudaGetSymbolAddress (so a context made after cudaDeviceReset gets a fresh
+// lookup), later calls reuse it.
 cudaError_t noalloc_scratch_ptr(int device, void** ptr);
+// The product's grid (n_rhs x time tiles in gridDim.z) is within the launch
+// limit of 65535; larger right-hand-side counts must be split by the caller.
+bool apply_grid_fits(int nt, int nx, int n_rhs);
+// Measured pipe rates of the current device: out[0] FP64 FMA TFLOP/s,
+// out[1] FP32 FMA TFLOP/s, out[2] MUFU ex2 results per second (1e12).
+cudaError_t pipe_peaks(double* out, cudaStream_t s);
 cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
                          const double* x, double* y, void* work, cudaStream_t s);
 

@@ -26,6 +26,7 @@
 #include <cstdint>
 
 #include "assemble.h"
+#include "device_info.h"
 #include "toeplitz_tc.h"
 
 namespace stbem {
@@ -68,12 +69,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// After a failed pipeline wait some TMA loads may still be in flight into this
+// CTA's shared memory: the producer waits (bounded) for the last load it
+// issued on every stage before the CTA releases its resources and exits.
+__device__ __forceinline__ void drain_loads(uint64_t* full, int issued) {
+  for (int s = 0; s < STAGES && s < issued; ++s) {
+    const int last = s + ((issued - 1 - s) / STAGES) * STAGES;   // last iteration that used stage s
+    mbar_wait(&full[s], static_cast<uint32_t>(last / STAGES) & 1);
+  }
 }
 
 __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1,
@@ -157,7 +168,7 @@ struct TcTile {
 template <int BN_>
 __global__ void __launch_bounds__(THREADS, 1)
     k_apply_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int nt, int nx,
-               int accumulate, double* __restrict__ Y) {
+               int accumulate, double* __restrict__ Y, long long stall_cycles) {
   using TT = TcTile<BN_>;
   constexpr int BN = BN_;
   constexpr uint32_t B_BYTES = TT::b_bytes, STAGE_BYTES = TT::stage_bytes, TMEM_COLS = TT::tmem_cols;
@@ -168,13 +179,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(smB + STAGES * B_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* stallbar = accum + 1;     // diagnostic: a barrier no thread arrives on
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(stallbar + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
   const int dmax = min(m0 + BN - 1, nt - 1);  // lags for which some m - d >= 0
   const int nj = (nx + BK - 1) / BK;
   const int iters = (dmax + 1) * nj;
+  // pipeline waits give up after this many cycles (short in the diagnostic)
+  const long long limit = stall_cycles > 0 ? stall_cycles : kWaitCycles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -182,6 +196,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(accum, 1);
+    mbar_init(stallbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -191,13 +206,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  int issued = 0;
 
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int it = 0; it < iters; ++it) {
       const int s = it % STAGES;
       const uint32_t round = static_cast<uint32_t>(it / STAGES);
-      if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+      if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, limit)) {
         ok = false;
         break;
       }
@@ -205,13 +221,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(&tmA, &full[s], smA + s * A_BYTES, j0, i0, d);
       tma_load_3d(&tmX, &full[s], smB + s * B_BYTES, j0, m0 - d, b);
+      issued = it + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    for (int it = 0; it < iters; ++it) {
+    // MMA issuer (in the diagnostic it first waits on a barrier nobody arrives on)
+    if (stall_cycles > 0 && !mbar_wait(stallbar, 0, limit)) ok = false;
+    for (int it = 0; it < iters && ok; ++it) {
       const int s = it % STAGES;
       const uint32_t round = static_cast<uint32_t>(it / STAGES);
-      if (!mbar_wait(&full[s], round & 1)) {
+      if (!mbar_wait(&full[s], round & 1, limit)) {
         ok = false;
         break;
       }
@@ -226,8 +244,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     umma_commit(accum);   // completes when every MMA issued above has completed
   }
   __syncwarp();
+  // on any failure, let the loads already issued land before going on
+  if (__syncthreads_or(!ok) && warp == 0 && lane == 0) drain_loads(full, issued);
 
   // epilogue: warp w holds accumulator rows (TMEM lanes) 32 w .. 32 w + 31
+  // (this wait keeps the full limit: TMEM is released only after the MMAs)
   bool acc_ok = mbar_wait(accum, 0);
   acc_ok = __all_sync(0xffffffffu, acc_ok);
   tc_fence_after();
@@ -328,6 +349,7 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  int issued = 0;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -342,6 +364,7 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
         mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load_3d(&tmA, &full[s], smA + s * A_BYTES, j0, i0, d);
         tma_load_3d(&tmX, &full[s], smB + s * B_BYTES, j0, m0 - d, b);
+        issued = it + 1;
       }
     }
     __syncwarp();
@@ -429,6 +452,8 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
     }
   }
   if (!ok) atomicExch(&g_tc_error, 1);
+  // on any failure, let the loads already issued land before exiting
+  if (__syncthreads_or(!ok) && warp == 0 && lane == 0) drain_loads(full, issued);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -486,8 +511,13 @@ cudaError_t make_maps(int nt, int nx, const void* A_bf16, int n_rhs, const void*
 }
 }  // namespace
 
+static std::atomic<long long> g_stall_cycles{0};
+
+void tc_set_stall(long long cycles) { g_stall_cycles.store(cycles > 0 ? cycles : 0); }
+
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
                             bool accumulate, cudaStream_t s, int chunk) {
+  const long long stall = g_stall_cycles.load();
   CUtensorMap mA, mX;
   // plain products on more than 128 steps take 128 x 256 tiles (N = 256 MMAs:
   // a third less shared-memory operand traffic per flop)
@@ -499,12 +529,14 @@ cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const
     e = cudaFuncSetAttribute(k_apply_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TcTile<256>::smem_bytes);
     if (e != cudaSuccess) return e;
-    k_apply_tc<256><<<grid, THREADS, TcTile<256>::smem_bytes, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
+    k_apply_tc<256><<<grid, THREADS, TcTile<256>::smem_bytes, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y,
+                                                                      stall);
   } else if (chunk <= 0) {
     e = cudaFuncSetAttribute(k_apply_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TcTile<128>::smem_bytes);
     if (e != cudaSuccess) return e;
-    k_apply_tc<128><<<grid, THREADS, TcTile<128>::smem_bytes, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y);
+    k_apply_tc<128><<<grid, THREADS, TcTile<128>::smem_bytes, s>>>(mA, mX, nt, nx, accumulate ? 1 : 0, Y,
+                                                                      stall);
   } else {
     e = cudaFuncSetAttribute(k_apply_tc_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COMP_SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -542,8 +574,7 @@ __global__ void k_bf16_split3(const double* __restrict__ src, __nv_bfloat16* __r
 }
 
 cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo, size_t n, cudaStream_t s) {
-  const size_t blocks_needed = (n + 255) / 256;
-  const int blocks = (int)(blocks_needed < 152 * 16 ? (blocks_needed ? blocks_needed : 1) : 152 * 16);
+  const int blocks = stride_grid(n, 256, 16);
   k_bf16_split3<<<blocks, 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(mid),
                                         static_cast<__nv_bfloat16*>(lo), n);
   count_launches(1);
@@ -551,8 +582,7 @@ cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo,
 }
 
 cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s) {
-  const size_t blocks_needed = (n + 255) / 256;
-  const int blocks = (int)(blocks_needed < 152 * 16 ? (blocks_needed ? blocks_needed : 1) : 152 * 16);
+  const int blocks = stride_grid(n, 256, 16);
   if (src_prec == STBEM_F64)
     k_to_bf16_f64<<<blocks, 256, 0, s>>>(static_cast<const double*>(src), static_cast<__nv_bfloat16*>(dst), n);
   else

@@ -14,6 +14,10 @@ cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const
 // hi/mid/lo BF16 slices of an FP64 array (mid and lo may be NULL)
 cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo, size_t n, cudaStream_t s);
 cudaError_t tc_error_reset(cudaStream_t s);
+// Diagnostic: cycles > 0 makes every later plain tensor-core product wait on a
+// barrier no thread arrives on (its pipeline waits limited to `cycles`), so it
+// times out and reports through the error word; 0 restores normal operation.
+void tc_set_stall(long long cycles);
 cudaError_t tc_error_read(int* flag, cudaStream_t s);
 cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s);
 }  // namespace stbem

@@ -2,6 +2,7 @@
 // blocks of GMRES (dot products, linear combinations, diagonal scaling).
 #include <cuda_runtime.h>
 
+#include "device_info.h"
 #include "special.cuh"
 #include "vec.h"
 
@@ -282,10 +283,7 @@ __global__ void k_rlumped(const RaggedProblem* __restrict__ probs, int P, double
     L[probs[p].mass_off + l] = M.ht * (M.slen[(l - 1 + N) % N] + 2.0 * M.slen[l] + M.slen[(l + 1) % N]) / 4.0;
 }
 
-static int grid_for(size_t n) {
-  size_t b = (n + 255) / 256;
-  return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
-}
+static int grid_for(size_t n) { return stride_grid(n, 256, 8); }
 
 cudaError_t rhs_g_launch(const DevMesh& M, double ysx, double ysy, double* g, cudaStream_t s) {
   k_rhs_g<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, ysx, ysy, g);
@@ -361,10 +359,7 @@ cudaError_t diag_div_launch(const double* x, const double* L, double* y, int nt,
 }  // namespace stbem
 
 namespace stbem {
-static int rgrid(long long n) {
-  const long long b = (n + 255) / 256;
-  return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
-}
+static int rgrid(long long n) { return stride_grid(n < 0 ? 0 : (size_t)n, 256, 8); }
 cudaError_t rdots_launch(const double* Q, size_t ldq, int k, const double* U, const long long* vp, int P,
                          double* out, cudaStream_t s) {
   k_rdots<<<dim3(P, k), 256, 0, s>>>(Q, ldq, U, vp, P, out);
