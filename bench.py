@@ -19,6 +19,7 @@ Multi-GPU (torchrun, N > 1): every rank runs its own copy of the workload
 (independent problems, no collective on the data path; weak scaling).
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -45,8 +46,10 @@ def _peaks():
         return {}
 
 
-# FP64 pipe: 1.25 TFLOP/s nominal dense FP64 for GB300 (recipe table).
-FP64_PEAK_TFLOPS = 1.25
+# FP64 pipe: 1.25 TFLOP/s nominal dense FP64 for GB300 (recipe table); the
+# roofline divides by the FP64 FMA rate measured in the same run
+# (stbem_pipe_peaks) and reports the nominal fraction beside it.
+FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
 # at square256 (lags 2..65) from an ncu capture (profiles/k_tile_D_f64_lag2.md);
 # set to None whenever that kernel changes
@@ -82,27 +85,74 @@ def _cores():
         return os.cpu_count() or 1
 
 
+def W_config():
+    import workloads as W
+    return W.config(WORKLOAD)
+
+
+def _config(p, l2):
+    return {"workload": WORKLOAD, "n_x": p.n_x, "n_t": p.n_t, "alpha": p.alpha, "T": p.T,
+            "y_star": list(p.y_star), "precision": "fp64 assembly + fp64 GMRES", "l2": l2}
+
+
+def _oracle_worker(args):
+    n, seed = args
+    return _oracle_sample(n, seed)
+
+
+class OraclePool:
+    """The oracle on every host core: one single-threaded worker process per
+    core (BLAS and OpenMP pinned to one thread each), started with 'spawn' so
+    that it is safe after CUDA has been initialised in the parent."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or _cores()
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.blas_threads = 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_worker, [(3, 1 + w) for w in range(self.cores)])    # imports, warm-up
+
+    def step(self, per_worker, seed):
+        """Every worker evaluates per_worker random entries; returns (entries,
+        wall seconds of the parallel region)."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, [(per_worker, seed * 1000 + w) for w in range(self.cores)])
+        return sum(c for c, _ in res), time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+ORACLE_PER_WORKER = 1024     # entries per worker per step (about 1 s of one core)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n_entries = 96
-    for _ in range(args.warmup):
-        _oracle_sample(24, 1000)
+    pool = OraclePool()
+    for k in range(args.warmup):
+        pool.step(64, 100 + k)
     times, counts = [], []
     for k in range(args.steps):
-        c, t = _oracle_sample(n_entries, 2000 + k)
+        c, t = pool.step(ORACLE_PER_WORKER, 2000 + k)
         counts.append(c)
         times.append(t)
+    pool.close()
     value = sum(counts) / sum(times)
-    sample = ("%d random (op, lag, i, j) entries of %s per step, uniform over the 3 operators, lags "
-              "and index pairs; single numpy process" % (n_entries, WORKLOAD))
+    sample = ("%d random (op, lag, i, j) entries of %s per step (%d per worker), uniform over the 3 "
+              "operators, lags and index pairs; %d single-threaded numpy worker processes"
+              % (ORACLE_PER_WORKER * pool.cores, WORKLOAD, ORACLE_PER_WORKER, pool.cores))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": _config(W_config(), "n/a (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "blas_threads": pool.blas_threads,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -178,14 +228,16 @@ def run_batched(ctx, dev, stream, n_src=256):
     D32 = P.assemble(ctx, mesh, "D", "f32")
     e[3].record(stream)
     V3 = P.bf16_split3(ctx, V)
-    K3 = P.bf16_split3(ctx, K)
     Db = P.to_bf16(ctx, D32)
     L = P.lumped_mass(ctx, mesh)
     ys = W.annulus_sources(n_src, seed=4)
     e[4].record(stream)
-    G, F = P.rhs_batched(ctx, mesh, K3, ys)
+    # F = 1/2 M G + K G with the FP64 K product of all 256 right-hand sides
+    G, F = P.rhs_batched(ctx, mesh, K, ys)
     e[5].record(stream)
-    Wb, infos = P.solve_batched(ctx, V3, F, Db, L, tol=2e-6, inner_tol=1e-2, restart=40, max_iter=400)
+    # BF16 tensor-core inner solves; refinement on the three-slice residual,
+    # then on the FP64 residual to 1e-8 (FP64-solve accuracy)
+    Wb, infos = P.solve_batched(ctx, V3, F, Db, L, tol=1e-8, inner_tol=1e-2, restart=40, max_iter=600, V64=V)
     e[6].record(stream)
     torch.cuda.synchronize(dev)
     # tensor-core product alone: V (BF16) on all right-hand sides
@@ -215,7 +267,10 @@ def run_batched(ctx, dev, stream, n_src=256):
     s1.record(stream)
     torch.cuda.synchronize(dev)
     one_ms = s0.elapsed_time(s1)
-    rel = float((Wb[0] - w1).norm() / w1.norm())
+    # accuracy reference: the FP64 solve of right-hand side 0 to 1e-11
+    w_acc, _ = P.solve(ctx, V, f1, D64, L, tol=1e-11)
+    rel = float((Wb[0] - w_acc).norm() / w_acc.norm())
+    rel_fp64_path = float((w1 - w_acc).norm() / w_acc.norm())
     r0 = F[0] - P.apply(ctx, V, Wb[0])
     peaks = _peaks()
     bf16_peak = float(peaks.get("bf16_tflops", 1867.6))
@@ -224,11 +279,14 @@ def run_batched(ctx, dev, stream, n_src=256):
         "assembly_ms": {"V_f64": e[0].elapsed_time(e[1]), "K_f64": e[1].elapsed_time(e[2]),
                         "D_f32": e[2].elapsed_time(e[3])},
         "rhs_ms": e[4].elapsed_time(e[5]),
+        "rhs_note": "F = 1/2 M G + K G, FP64 CUDA-core K product of all right-hand sides",
         "solve_ms": e[5].elapsed_time(e[6]),
+        "solve_note": "BF16 tensor-core lockstep GMRES, refinement on three-slice then FP64 residuals, tol 1e-8",
         "inner_iterations": max(i["iterations"] for i in infos),
-        "max_rel_residual": max(i["rel_residual"] for i in infos),
+        "max_fp64_rel_residual": max(i["rel_residual"] for i in infos),
         "fp64_rel_residual_rhs0": float(r0.norm() / F[0].norm()),
-        "w_rel_diff_vs_fp64_solve_rhs0": rel,
+        "w_rel_diff_vs_fp64_solve_1e-11_rhs0": rel,
+        "fp64_path_1e-8_w_rel_diff_vs_fp64_solve_1e-11_rhs0": rel_fp64_path,
         "fp64_single_solve_ms": one_ms, "fp64_single_solve_iterations": info1["iterations"],
         "fp64_256_sequential_solves_ms_projected": one_ms * n_src,
         "tc_apply": {"ms": tc_ms, "tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
@@ -237,8 +295,7 @@ def run_batched(ctx, dev, stream, n_src=256):
         "tc_apply_compensated_chunk4": {"ms": tc4_ms, "tflops": tc_flops / (tc4_ms * 1e-3) / 1e12,
                                         "frac_of_bf16_peak": tc_flops / (tc4_ms * 1e-3) / 1e12 / bf16_peak},
     }
-    for t in (V, K, D32, D64, V3, K3, Db, G, F, Wb):
-        del t
+    del V, K, D32, D64, V3, Db, G, F, Wb
     torch.cuda.empty_cache()
     return out
 
@@ -270,15 +327,30 @@ def run_grad(ctx, dev, stream):
         return mesh, V, K, D, L, g, w, info
 
     wt = forward(C0 + 0.01 * rng.standard_normal(C0.shape), al)[6]
-    e = [ev() for _ in range(4)]
+    e = [ev() for _ in range(6)]
     e[0].record(stream)
     mesh, V, K, D, L, g, w, info = forward(C0, al)
     e[1].record(stream)
-    lam, ainfo = P.solve_adjoint(ctx, V, 2.0 * (w - wt), D, L, tol=1e-12, restart=100, max_iter=2000)
-    e[2].record(stream)
+    # workspaces and the adjoint right-hand side outside the timed intervals
+    awork = P.api.solve_workspace(ctx, nt, mesh.n_x, 100)
     gwork = P.api.grad_workspace(ctx, nt, mesh.n_x)
-    dxy, dal = P.grad(ctx, mesh, K, ys, g, w, lam, work=gwork)
+    rhs_adj = 2.0 * (w - wt)
+    torch.cuda.synchronize(dev)
+    e[2].record(stream)
+    lam, ainfo = P.solve_adjoint(ctx, V, rhs_adj, D, L, tol=1e-12, restart=100, max_iter=2000, work=awork)
     e[3].record(stream)
+    e[4].record(stream)
+    dxy, dal = P.grad(ctx, mesh, K, ys, g, w, lam, work=gwork)
+    e[5].record(stream)
+    torch.cuda.synchronize(dev)
+    # the forward solve alone with the same options and workspace, for the
+    # per-iteration comparison with the adjoint solve
+    _, f_fwd = P.rhs(ctx, mesh, K, ys)
+    torch.cuda.synchronize(dev)
+    s0, s1 = ev(), ev()
+    s0.record(stream)
+    _, finfo = P.solve(ctx, V, f_fwd, D, L, tol=1e-12, restart=100, max_iter=2000, work=awork)
+    s1.record(stream)
     torch.cuda.synchronize(dev)
     # the derivative kernels alone, once more
     k0, k1 = ev(), ev()
@@ -296,13 +368,16 @@ def run_grad(ctx, dev, stream):
     out = {
         "workload": "star256: 16 corners (radii seed 5), N_x = 256, N_t = 256, alpha = 1, 33 parameters",
         "forward_ms": e[0].elapsed_time(e[1]), "forward_gmres_iterations": info["iterations"],
-        "adjoint_solve_ms": e[1].elapsed_time(e[2]), "adjoint_iterations": ainfo["iterations"],
+        "adjoint_solve_ms": e[2].elapsed_time(e[3]), "adjoint_iterations": ainfo["iterations"],
+        "forward_solve_ms": s0.elapsed_time(s1), "forward_solve_iterations": finfo["iterations"],
+        "adjoint_vs_forward_ms_per_iteration": (e[2].elapsed_time(e[3]) / max(1, ainfo["iterations"])) /
+                                               (s0.elapsed_time(s1) / max(1, finfo["iterations"])),
         "grad_kernels_ms": k0.elapsed_time(k1),
-        "backward_ms": e[1].elapsed_time(e[3]),
+        "backward_ms": e[2].elapsed_time(e[3]) + e[4].elapsed_time(e[5]),
         "fd_check": {"directional_derivative": an, "central_difference": fd,
                      "rel_diff": abs(fd - an) / abs(an), "h": h},
     }
-    del V, K, D, g, w, lam, gwork
+    del V, K, D, g, w, lam, gwork, awork
     torch.cuda.empty_cache()
     return out
 
@@ -449,7 +524,8 @@ def run_ragged(ctx, dev, stream):
     annulus 1.2..3 (seed 4).  FP32 operators (FP64 singular pairs), one
     persistent launch per operator for all 64 problems; the product's lag
     chunk autotuned; lockstep GMRES (FP64 vectors, graph-captured Arnoldi
-    steps) to 1e-6 on all problems, beside the same 64 solves one at a time."""
+    steps) inside FP64 refinement (FP64 V residuals) to 1e-8 on all problems,
+    beside the same 64 solves one at a time."""
     import torch
     import workloads as W
     import paper_1811_05224_gb300 as P
@@ -479,23 +555,37 @@ def run_ragged(ctx, dev, stream):
     torch.cuda.synchronize(dev)
     apply_ms = a0.elapsed_time(a1)
     flops = sum(2.0 * nx * nx * nt * (nt + 1) / 2 for nx, nt in pr)
-    work = R.solve_workspace(40)
-    R.solve(V, f, D, L, tol=1e-6, restart=40, max_iter=400, work=work)      # captures the graphs
+    # FP64 V for the refinement residuals (FP64 accuracy of every solution)
+    v0, v1 = ev(), ev()
+    v0.record(stream)
+    V64 = R.assemble("V", "f64")
+    v1.record(stream)
+    torch.cuda.synchronize(dev)
+    work = R.solve_mixed_workspace(40)
+    R.solve_mixed(V64, V, f, D, L, tol=1e-8, inner_tol=1e-4, restart=40, max_iter=600, work=work)   # graphs
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    w, infos = R.solve(V, f, D, L, tol=1e-6, restart=40, max_iter=400, work=work)
+    w, infos = R.solve_mixed(V64, V, f, D, L, tol=1e-8, inner_tol=1e-4, restart=40, max_iter=600, work=work)
     torch.cuda.synchronize(dev)
     solve_ms = 1e3 * (time.perf_counter() - t0)
-    # the same systems one at a time
-    sw = P.api.solve_workspace(ctx, max(nt for _, nt in pr), max(nx for nx, _ in pr), 40)
+    # the same systems one at a time (single-problem mixed solve, same operators)
+    nt_max, nx_max = max(nt for _, nt in pr), max(nx for nx, _ in pr)
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_solve_mixed_workspace_bytes(nt_max, nx_max, 40, ctypes.byref(nb)))
+    sw = torch.empty(nb.value, dtype=torch.uint8, device=dev)
     t0 = time.perf_counter()
-    worst = 0.0
+    worst, worst_res = 0.0, 0.0
     for p in range(len(probs)):
-        wp, _ = P.solve(ctx, R.view_op(V, p), R.view_vec(f, p), R.view_op(D, p), R.view_mass(L, p), tol=1e-6,
-                        restart=40, max_iter=400, work=sw)
+        fp = R.view_vec(f, p)
+        wp, _ = P.solve_mixed(ctx, R.view_op(V64, p), R.view_op(V, p), fp, R.view_op(D, p), R.view_mass(L, p),
+                              tol=1e-8, inner_tol=1e-4, restart=40, max_iter=600, work=sw)
         worst = max(worst, float((wp - R.view_vec(w, p)).norm() / wp.norm()))
     torch.cuda.synchronize(dev)
     seq_ms = 1e3 * (time.perf_counter() - t0)
+    for p in range(len(probs)):
+        fp = R.view_vec(f, p)
+        rp = fp - P.apply(ctx, R.view_op(V64, p), R.view_vec(w, p))
+        worst_res = max(worst_res, float(rp.norm() / fp.norm()))
     entries = 3 * R.op_elems
     out = {
         "workload": "64 unit squares, N_x = 4k (k in [16,128]), N_t in [64,512] (seed 41), alpha = 1",
@@ -505,12 +595,15 @@ def run_ragged(ctx, dev, stream):
         "assembly_entries_per_s": entries / (sum(asm_ms.values()) * 1e-3),
         "apply_ms": apply_ms, "apply_gflops": flops / (apply_ms * 1e-3) / 1e9,
         "tuned_lags_per_chunk": best, "tuner_ms": report,
-        "solve_ms": solve_ms, "lockstep_iterations": max(i["iterations"] for i in infos),
-        "max_rel_residual": max(i["rel_residual"] for i in infos),
+        "assembly_V_f64_ms": v0.elapsed_time(v1),
+        "solve_ms": solve_ms, "lockstep_inner_iterations": max(i["iterations"] for i in infos),
+        "solve_note": "FP32 lockstep GMRES inside FP64 refinement (FP64 V residuals), tol 1e-8",
+        "max_fp64_rel_residual": worst_res,
         "sequential_solves_ms": seq_ms,
+        "sequential_note": "the 64 single-problem mixed solves (stbem_solve_mixed), same operators and tolerance",
         "max_w_rel_diff_vs_sequential": worst,
     }
-    del V, K, D, f, g, y, w, work, sw
+    del V, K, D, V64, f, g, y, w, work, sw
     R.close()
     torch.cuda.empty_cache()
     return out
@@ -696,6 +789,22 @@ def run_ours(args):
     ragged = None
     if not args.no_ragged and world == 1:
         ragged = run_ragged(ctx, dev, stream)
+    precision = None
+    if not args.no_precision and world == 1:
+        precision = run_precision(ctx, dev, stream)
+    # measured pipe peaks of this GPU (FP64 FMA is the assembly's and the
+    # single-right-hand-side product's roofline)
+    peaks = P.pipe_peaks(ctx)
+    fp64_peak = peaks["fp64_tflops"]
+    hbm_gbs = float(_peaks().get("hbm_gbs", 6784.2))
+    # GMRES roofline: per iteration k (from 0) one V and one D apply at their
+    # roofline times plus the two Gram-Schmidt passes over k + 1 basis vectors
+    # (read twice, updated once: 4 (k + 1) N doubles through HBM), and one
+    # more V apply for the final true residual
+    it_last = infos[-1]["iterations"]
+    t_apply = max(apply_bytes / (hbm_gbs * 1e9), apply_flops / (fp64_peak * 1e12))
+    t_gs = sum(4.0 * (k + 1) * nt * nx * 8 / (hbm_gbs * 1e9) for k in range(it_last))
+    gmres_roof_ms = 1e3 * ((2 * it_last + 1) * t_apply + t_gs)
 
     # end to end through the public API with host buffers: vertices in, w out
     verts = np.ascontiguousarray(p.vertices)
@@ -719,18 +828,21 @@ def run_ours(args):
     # oracle CPU baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        c, t = _oracle_sample(96, 12345)
-        cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "96 random (op, lag, i, j) entries of %s, single numpy process" % WORKLOAD}
+        pool = OraclePool()
+        c, t = pool.step(ORACLE_PER_WORKER, 12345)
+        pool.close()
+        cpu = {"value": c / t, "unit": UNIT, "cores": pool.cores, "blas_threads": pool.blas_threads,
+               "kind": "oracle",
+               "sample": "%d random (op, lag, i, j) entries of %s (%d per worker), uniform over the 3 operators, "
+                         "lags and index pairs; %d single-threaded numpy worker processes (spawn)"
+                         % (c, WORKLOAD, ORACLE_PER_WORKER, pool.cores)}
     asm_tflops = d2_flops_launch / (d2_ms_launch * 1e-3) / 1e12
     last = infos[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_x": nx, "n_t": nt, "alpha": p.alpha, "T": p.T,
-                   "y_star": list(p.y_star), "precision": "fp64 assembly + fp64 GMRES",
-                   "l2": "256 MB buffer written between steps"},
+        "config": _config(p, "256 MB buffer written between steps"),
         "components": {
             "assembly_entries_per_s": asm_rate,
             "assembly_ms": {k: round(v, 3) for k, v in op_ms.items()},
@@ -739,6 +851,14 @@ def run_ours(args):
             "apply_f64_gflops": apply_flops / (ms_apply * 1e-3) / 1e9,
             "gmres_ms": statistics.mean(ms_solve), "gmres_iterations": last["iterations"],
             "gmres_rel_residual": last["rel_residual"],
+            "gmres_roofline_ms": gmres_roof_ms,
+            "gmres_roofline_frac": gmres_roof_ms / statistics.mean(ms_solve),
+            "gmres_roofline_note": "iterations x (V apply + D apply at max(bytes / HBM, flops / measured FP64)) "
+                                   "+ Gram-Schmidt traffic + final residual apply, over the GMRES time "
+                                   "(right-hand side excluded)",
+            "peaks": dict(peaks, hbm_gbs=hbm_gbs, note="fp64/fp32/ex2 measured in this run by stbem_pipe_peaks; "
+                                                       "hbm from MEASURED_PEAKS.json"),
+            "precision": precision,
             "mixed": {"step_ms": statistics.mean(mixed_ms), "solve_ms": statistics.mean(mixed_solve_ms),
                       "inner_iterations": mixed_info["iterations"],
                       "rel_residual_fp64": mixed_info["rel_residual"],
@@ -750,15 +870,18 @@ def run_ours(args):
             "initial": initial,
         },
         "roofline": {"kernel": "k_tile_ml<D, f64, 4 lags> lags >= 2", "bound": "alu",
-                     "achieved": asm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": asm_tflops / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_D2_BYTES,
+                     "achieved": asm_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": asm_tflops / fp64_peak, "traffic": TRAFFIC_D2_BYTES,
                      "launch_ms": d2_ms_launch, "flops_per_launch": d2_flops_launch,
-                     "note": "peak: nominal FP64 1.25 TFLOP/s; FP64-ALU bound (DRAM traffic is only "
+                     "nominal_peak": FP64_NOMINAL_TFLOPS, "frac_of_nominal": asm_tflops / FP64_NOMINAL_TFLOPS,
+                     "note": "peak: FP64 FMA rate measured in this run (stbem_pipe_peaks), nominal 1.25 "
+                             "TFLOP/s beside it; FP64-ALU bound (DRAM traffic is only "
                              "the written lag blocks); algorithmic flops: unique half-segment pairs, each "
                              "group of 4 lags evaluating its 5 Peano intervals once"},
         "apply_roofline": {"bound": "alu", "achieved": apply_flops / (ms_apply * 1e-3) / 1e12,
-                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": apply_flops / (ms_apply * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+                           "peak": fp64_peak, "unit": "TFLOP/s",
+                           "frac": apply_flops / (ms_apply * 1e-3) / 1e12 / fp64_peak,
+                           "frac_of_nominal": apply_flops / (ms_apply * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(verts.nbytes),
                 "d2h_bytes_per_step": int(nt * nx * 8)},
@@ -824,6 +947,8 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the star256 differentiation component")
     ap.add_argument("--no-ragged", action="store_true", help="skip the 64-problem ragged component")
     ap.add_argument("--no-initial", action="store_true", help="skip the Section 4 example (M_h^0) component")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the L-shape N_x = N_t = 1024 mixed-versus-FP64 component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
     ap.add_argument("--component", choices=["tc", "grad", "precision", "initial"], default=None,
@@ -889,8 +1014,11 @@ def run_precision(ctx, dev, stream):
         "w_rel_diff_mixed_vs_fp64": float((wm - w).norm() / w.norm()),
         "mixed_path_ms": e[3].elapsed_time(e[5]), "fp64_path_ms": e[5].elapsed_time(e[7]),
     }
-    print(json.dumps(out))
-    return 0
+    r2 = f - P.apply(ctx, V, w)
+    out["fp64_rel_residual"] = float(r2.norm() / f.norm())
+    del V, D, D32, wm, w, f, g, L, Minv, r, r2
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_component(args):
@@ -908,7 +1036,8 @@ def run_component(args):
     out = {"component": args.component, "size": n}
     ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
     if args.component == "precision":
-        return run_precision(ctx, dev, stream)
+        print(json.dumps(run_precision(ctx, dev, stream)), flush=True)
+        return 0
     if args.component == "initial":
         # --size is the level L of the Section 4 example (2^L segments per side)
         res = run_initial(ctx, dev, stream, L=n if n <= 9 else 6)

@@ -47,6 +47,7 @@ extern "C" {
                                  /* i.e. a singular (preconditioned) operator */
 #define STBEM_ERR_NAN (-6)       /* NaN or Inf met in a residual             */
 #define STBEM_ERR_TIMEOUT (-7)   /* a bounded device-side wait gave up       */
+#define STBEM_ERR_REDUCE (-8)    /* the caller's all-reduce callback failed  */
 
 /* operators */
 #define STBEM_OP_V 0 /* single layer  <V phi0_k, phi0_l>,   N_x x N_x blocks */
@@ -273,6 +274,67 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void*
                         double* dev_lambda, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* dev_work, size_t work_bytes);
 
+/* ---- Lag sharding of one problem across ranks (Section 3) -------------------
+ * The paper distributes the blocks of its block-lower-triangular matrices over
+ * processes.  On a uniform time grid all blocks at one lag are equal, so here
+ * the lag block is the unit: a rank holds the blocks of some lags, computes
+ * its part of every product, y_r[m] = sum_{d held} A^(d) x[m - d], and one
+ * sum over ranks (an all-reduce of n_t x n_x doubles) completes the product.
+ * Vectors, the right-hand side, the preconditioner's masses and the GMRES
+ * recurrences are replicated on every rank; only the operators are split. */
+
+/* Lag ranges of `rank` among n_ranks: chunks of `chunk` consecutive lags dealt
+ * in snake order (0, 1, .., R-1, R-1, .., 0, 0, ..), so that the work
+ * sum (n_t - d) and the number of blocks balance across ranks; adjacent chunks
+ * of one rank are merged.  host_ranges receives 2 * (*n_ranges) ints
+ * [begin, end) in increasing order; *n_ranges may be 0 (more ranks than
+ * chunks).  Host only, no device needed.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_NOMEM (*n_ranges > max_ranges; *n_ranges tells how many). */
+int stbem_lag_shard(int n_t, int n_ranks, int rank, int chunk, int max_ranges, int* host_ranges, int* n_ranges);
+
+/* As stbem_assemble_lags, but the blocks of the lags [lag_begin, lag_end) are
+ * written compactly: block d to dev_blocks + (d - lag_begin) n_x^2 elements
+ * (dev_blocks holds (lag_end - lag_begin) n_x^2 elements).  Errors as
+ * stbem_assemble_lags. */
+int stbem_assemble_lag_blocks(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec, int lag_begin, int lag_end,
+                              void* dev_blocks);
+
+/* The block-Toeplitz product restricted to the lags [lag_begin, lag_end):
+ *   transpose = 0: y[b][m] (=, or += with accumulate) sum_{d in range, d <= m} A^(d) x[b][m-d]
+ *   transpose = 1: y[b][n] (=, or +=) sum_{d in range, n + d < n_t} A^(d)^T x[b][n+d]
+ * with dev_A_blocks holding those blocks compactly (block d at
+ * (d - lag_begin) n_x^2).  Accumulation, layouts and workspace
+ * (stbem_apply_lags_workspace_bytes with n_lags = lag_end - lag_begin) as
+ * stbem_apply.  Errors as stbem_apply. */
+int stbem_apply_lags_workspace_bytes(int n_t, int n_x, int n_lags, int n_rhs, size_t* bytes);
+int stbem_apply_lags(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x, int lag_begin, int lag_end,
+                     const void* dev_A_blocks, int n_rhs, const double* dev_x, double* dev_y, int accumulate,
+                     void* dev_work, size_t work_bytes);
+
+/* All-reduce (sum over ranks, in place) of n doubles at dev_buf, supplied by
+ * the caller (e.g. NCCL or gloo through torch.distributed).  It is called on
+ * the host after this rank's partial product has been enqueued on the
+ * context's stream; it must sum over ranks what that stream has produced and
+ * leave the result in dev_buf before later work on the stream reads it (for
+ * a collective on another stream: make it wait for the context's stream, and
+ * the context's stream for it).  Returns 0 on success. */
+typedef int (*stbem_allreduce_fn)(double* dev_buf, size_t n, void* user);
+
+/* Lag-sharded stbem_solve: the same right-preconditioned GMRES on every rank,
+ * whose V and D products are the rank's lag ranges (stbem_lag_shard;
+ * host_ranges, n_ranges, the same for V and D) of the compact operators
+ * dev_V_blocks and dev_D_blocks, followed by allreduce(y, n_t n_x, user).
+ * Every rank must call it with the same f, L and options; all ranks then
+ * perform the same iterations and return the same w.  A rank holding no lags
+ * passes n_ranges = 0 (its partial products are zero).  Workspace:
+ * stbem_solve_sharded_workspace_bytes.  Errors as stbem_solve, and
+ * STBEM_ERR_REDUCE when the callback returns non-zero (the solve stops). */
+int stbem_solve_sharded_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes);
+int stbem_solve_sharded(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void* dev_V_blocks,
+                        const void* dev_D_blocks, int n_ranges, const int* host_ranges, stbem_allreduce_fn allreduce,
+                        void* user, const double* dev_L, const double* dev_f, double* dev_w,
+                        const stbem_solve_opts* opts, stbem_solve_info* info, void* dev_work, size_t work_bytes);
+
 /* Shape and alpha gradient by the adjoint method (not in the paper, which
  * does not differentiate; it differentiates the discrete system of eq. (4)).
  * For w solving V_h w = f, f = 1/2 M_h g + K_h g with g the time averages of
@@ -433,6 +495,24 @@ int stbem_ragged_solve_workspace_bytes(const stbem_ragged* batch, int restart, s
 int stbem_ragged_solve(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void* dev_V, const void* dev_D,
                        const double* dev_L, const double* dev_f, double* dev_w, const stbem_solve_opts* opts,
                        stbem_solve_info* infos, void* dev_work, size_t work_bytes);
+
+/* V_p w_p = f_p for every problem to FP64 accuracy with FP32 inner solves
+ * (the batched counterpart of stbem_solve_mixed): FP64 iterative refinement,
+ * r_p = f_p - V64_p w_p with the FP64 operators dev_V64, around the lockstep
+ * solve of stbem_ragged_solve on the FP32 operators dev_V32 (and dev_D32 with
+ * the lumped masses dev_L as preconditioner, opts->precondition = 1; NULL D32
+ * and precondition = 0 for none), each inner solve reducing its residual by
+ * inner_tol (0 < inner_tol < 1).  A problem stops once its FP64 residual
+ * ||r_p|| / ||f_p|| <= opts->tol; its later corrections are not computed.
+ * opts->max_iter caps the inner iterations (lockstep count); infos[p]
+ * reports each problem's inner iterations and final FP64 residual.
+ * Workspace: stbem_ragged_solve_mixed_workspace_bytes.  Blocks the host.
+ * Errors as stbem_ragged_solve. */
+int stbem_ragged_solve_mixed_workspace_bytes(const stbem_ragged* batch, int restart, size_t* bytes);
+int stbem_ragged_solve_mixed(stbem_ctx* ctx, stbem_ragged* batch, const double* dev_V64, const float* dev_V32,
+                             const float* dev_D32, const double* dev_L, const double* dev_f, double* dev_w,
+                             const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos, void* dev_work,
+                             size_t work_bytes);
 
 /* ---- Initial datum (Section 1, eq. (4): M_h^0 u_0) ------------------------
  * The initial datum u_0 is discretised in S_h^1(Omega_h), the continuous

@@ -8,6 +8,7 @@ from .api import (Context, Domain, Mesh, Ragged, apply, pipe_peaks, evaluate, m0
                   apply_tc3, bf16_split3, grad, rhs_batched, round_f32, solve, solve_adjoint, solve_batched,
                   solve_mixed, to_bf16)
 from .autograd import neumann_solve  # noqa: F401
+from . import shard  # noqa: F401
 
 __all__ = ["Context", "Mesh", "pipe_peaks", "assemble", "assemble_lags", "apply", "rhs", "lumped_mass", "solve", "solve_mixed", "round_f32", "to_bf16", "apply_tc", "bf16_split3", "apply_tc3", "rhs_batched", "solve_batched", "solve_adjoint", "grad",
            "neumann_solve", "Ragged", "mixed_mass_inverse", "Domain", "m0_assemble", "m0_apply", "planewave_data",

@@ -219,6 +219,25 @@ def apply(ctx: Context, A, x, transpose: bool = False, work=None, out=None):
     return out if x.dim() == 3 else out[0]
 
 
+def apply_lags(ctx: Context, A_blocks, lag_begin: int, lag_end: int, n_t: int, x, transpose: bool = False,
+               out=None, accumulate: bool = False, work=None):
+    """Block-Toeplitz product over the lags [lag_begin, lag_end) only, with
+    A_blocks holding those blocks (block d at A_blocks[d - lag_begin])."""
+    prec = capi.F64 if A_blocks.dtype == torch.float64 else capi.F32
+    n_x = A_blocks.shape[1]
+    xb = x if x.dim() == 3 else x.unsqueeze(0)
+    n_rhs = xb.shape[0]
+    if out is None:
+        out = torch.empty_like(xb)
+    if work is None:
+        nb = ctypes.c_size_t()
+        ctx.check(ctx.lib.stbem_apply_lags_workspace_bytes(n_t, n_x, lag_end - lag_begin, n_rhs, ctypes.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+    ctx.check(ctx.lib.stbem_apply_lags(ctx.h, prec, int(transpose), n_t, n_x, lag_begin, lag_end, _ptr(A_blocks),
+                                       n_rhs, _ptr(xb), _ptr(out), int(accumulate), _ptr(work), work.numel()))
+    return out if x.dim() == 3 else out[0]
+
+
 def rhs(ctx: Context, mesh: Mesh, K, y_star, work=None):
     """(g, f): vertex time averages of g = U*(x - y*, t) and f = 1/2 M_h g + K_h g."""
     g = ctx.empty((mesh.n_t, mesh.n_x))
@@ -566,6 +585,29 @@ class Ragged:
             work = self.solve_workspace(restart)
         code = self.ctx.lib.stbem_ragged_solve(self.ctx.h, self.h, p, _ptr(V), _ptr(D), _ptr(L), _ptr(f), _ptr(out),
                                                ctypes.byref(opts), infos, _ptr(work), work.numel())
+        res = [{"iterations": x.iterations, "status": x.status, "rel_residual": x.rel_residual} for x in infos]
+        if code != capi.STBEM_OK and raise_on_fail:
+            self.ctx.check(code)
+        return out, res
+
+    def solve_mixed_workspace(self, restart: int):
+        nb = ctypes.c_size_t()
+        self.ctx.check(self.ctx.lib.stbem_ragged_solve_mixed_workspace_bytes(self.h, restart, ctypes.byref(nb)))
+        return torch.empty(nb.value, dtype=torch.uint8, device=self.ctx.device)
+
+    def solve_mixed(self, V64, V32, f, D32=None, L=None, tol: float = 1e-8, inner_tol: float = 1e-4,
+                    max_iter: int = 500, restart: int = 60, work=None, out=None, raise_on_fail: bool = True):
+        """FP64 refinement (residuals with the FP64 V64) around lockstep FP32
+        solves (V32, D32): every problem to an FP64 residual <= tol."""
+        opts = capi.SolveOpts(tol, max_iter, restart, int(D32 is not None))
+        infos = (capi.SolveInfo * self.P)()
+        if out is None:
+            out = self.ctx.empty((self.vec_elems,))
+        if work is None:
+            work = self.solve_mixed_workspace(restart)
+        code = self.ctx.lib.stbem_ragged_solve_mixed(self.ctx.h, self.h, _ptr(V64), _ptr(V32), _ptr(D32), _ptr(L),
+                                                     _ptr(f), _ptr(out), ctypes.byref(opts), float(inner_tol),
+                                                     infos, _ptr(work), work.numel())
         res = [{"iterations": x.iterations, "status": x.status, "rel_residual": x.rel_residual} for x in infos]
         if code != capi.STBEM_OK and raise_on_fail:
             self.ctx.check(code)

@@ -19,11 +19,12 @@ STBEM_ERR_NOCONV = -4
 STBEM_ERR_BREAKDOWN = -5
 STBEM_ERR_NAN = -6
 STBEM_ERR_TIMEOUT = -7
+STBEM_ERR_REDUCE = -8
 OP_V, OP_K, OP_D = 0, 1, 2
 F64, F32 = 0, 1
 
 ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOMEM", -4: "ERR_NOCONV",
-             -5: "ERR_BREAKDOWN", -6: "ERR_NAN", -7: "ERR_TIMEOUT"}
+             -5: "ERR_BREAKDOWN", -6: "ERR_NAN", -7: "ERR_TIMEOUT", -8: "ERR_REDUCE"}
 
 EXPORTS = [
     "stbem_version", "stbem_launch_count", "stbem_create", "stbem_destroy", "stbem_last_error", "stbem_mesh_create",
@@ -36,10 +37,16 @@ EXPORTS = [
     "stbem_ragged_create", "stbem_ragged_destroy", "stbem_ragged_sizes", "stbem_ragged_offsets",
     "stbem_ragged_assemble", "stbem_ragged_lumped_mass", "stbem_ragged_apply_workspace_bytes", "stbem_ragged_apply",
     "stbem_ragged_tune", "stbem_ragged_tune_report", "stbem_ragged_rhs", "stbem_ragged_solve_workspace_bytes",
-    "stbem_ragged_solve", "stbem_mixed_mass_inverse",
+    "stbem_ragged_solve", "stbem_ragged_solve_mixed_workspace_bytes", "stbem_ragged_solve_mixed",
+    "stbem_mixed_mass_inverse", "stbem_lag_shard", "stbem_assemble_lag_blocks", "stbem_apply_lags_workspace_bytes",
+    "stbem_apply_lags", "stbem_solve_sharded_workspace_bytes", "stbem_solve_sharded",
     "stbem_domain_create", "stbem_domain_destroy", "stbem_domain_info", "stbem_m0_bytes", "stbem_m0_assemble",
     "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data", "stbem_evaluate",
 ]
+
+
+# int (*)(double* dev_buf, size_t n, void* user): the caller's all-reduce
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 
 class Problem(ctypes.Structure):
@@ -116,6 +123,8 @@ def load(path: str = LIB_PATH):
     L.stbem_ragged_rhs.argtypes = [vp, vp, i, vp, P(d), vp, vp, vp, sz]
     L.stbem_ragged_solve_workspace_bytes.argtypes = [vp, i, P(sz)]
     L.stbem_ragged_solve.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
+    L.stbem_ragged_solve_mixed_workspace_bytes.argtypes = [vp, i, P(sz)]
+    L.stbem_ragged_solve_mixed.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]
@@ -123,6 +132,13 @@ def load(path: str = LIB_PATH):
     L.stbem_apply_tc.argtypes = [vp, i, i, vp, i, vp, vp]
     L.stbem_debug_tc_stall.argtypes = [i, ctypes.c_longlong]
     L.stbem_pipe_peaks.argtypes = [vp, P(d)]
+    L.stbem_lag_shard.argtypes = [i, i, i, i, i, P(i), P(i)]
+    L.stbem_assemble_lag_blocks.argtypes = [vp, vp, i, i, i, i, vp]
+    L.stbem_apply_lags_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_apply_lags.argtypes = [vp, i, i, i, i, i, i, vp, i, vp, vp, i, vp, sz]
+    L.stbem_solve_sharded_workspace_bytes.argtypes = [i, i, i, P(sz)]
+    L.stbem_solve_sharded.argtypes = [vp, i, i, i, vp, vp, i, P(i), ALLREDUCE_FN, vp, vp, vp, vp, P(SolveOpts),
+                                      P(SolveInfo), vp, sz]
     L.stbem_apply_tc_comp.argtypes = [vp, i, i, vp, i, vp, vp, i]
     L.stbem_bf16_split3.argtypes = [vp, sz, vp, vp, vp, vp]
     L.stbem_apply_tc3_workspace_bytes.argtypes = [i, i, i, P(sz)]

@@ -13,6 +13,7 @@
 
 #include "assemble.h"
 #include "capi_internal.h"
+#include "shard_host.h"
 #include "stbem.h"
 #include "toeplitz.h"
 #include "grad.h"
@@ -700,7 +701,51 @@ struct GmresOp {
   const double* L;
   bool transpose = false; // solve V^T x = f with the preconditioner L^-1 D^T L^-1
   int mass = 1;           // 1: L = lumped diagonal (N); 2: L = M_h^-1 (N x N), y = M^-1 D M^-T x
+  // lag sharding: V and D hold only the lag ranges [ranges[2k], ranges[2k+1])
+  // (blocks in range order); every product is this rank's partial sum
+  // followed by the caller's all-reduce.  n_ranges < 0: full operators.
+  int n_ranges = -1;
+  const int* ranges = nullptr;
+  stbem_allreduce_fn reduce = nullptr;
+  void* reduce_user = nullptr;
 };
+
+// y = A x with A one of op's operators (full, or this rank's lag ranges then
+// the all-reduce).  A failing callback sets *reduce_rc and returns an error.
+cudaError_t op_product(const GmresOp& op, const void* A, const double* x, double* y, void* work, cudaStream_t s,
+                       int* reduce_rc) {
+  if (op.n_ranges < 0) return stbem::apply_launch(op.prec, op.transpose, op.nt, op.nx, A, 1, x, y, work, s);
+  const size_t N = (size_t)op.nt * op.nx;
+  const size_t elt = op.prec == STBEM_F64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = cudaSuccess;
+  if (op.n_ranges == 0) e = cudaMemsetAsync(y, 0, N * sizeof(double), s);
+  size_t off = 0;
+  for (int k = 0; k < op.n_ranges && e == cudaSuccess; ++k) {
+    const int a = op.ranges[2 * k], b = op.ranges[2 * k + 1];
+    const void* Ak = static_cast<const char*>(A) + off * op.nx * op.nx * elt;
+    e = stbem::apply_range_launch(op.prec, op.transpose, op.nt, op.nx, a, b, Ak, 1, x, y, k > 0, work, s);
+    off += (size_t)(b - a);
+  }
+  if (e != cudaSuccess) return e;
+  const int rc = op.reduce(y, N, op.reduce_user);
+  if (rc != 0) {
+    *reduce_rc = rc;
+    return cudaErrorUnknown;
+  }
+  return cudaSuccess;
+}
+
+// An operator product inside gmres_core: a failed all-reduce callback is
+// reported as STBEM_ERR_REDUCE, other failures as CUDA errors.
+#define OP_TRY(call, where)                                                                          \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      if (reduce_rc) return fail(ctx, STBEM_ERR_REDUCE, "%s: all-reduce callback returned %d", where, \
+                                 reduce_rc);                                                        \
+      return stbem_internal::cuda_fail(ctx, e_, where);                                             \
+    }                                                                                               \
+  } while (0)
 
 // Right-preconditioned restarted GMRES for V x = f from x = 0 (see stbem_solve).
 // Returns STBEM_OK, STBEM_ERR_NOCONV or STBEM_ERR_NAN (or a CUDA error code).
@@ -712,9 +757,8 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
   const bool prec = op.D != nullptr;
   *iters_out = 0;
   *relres_out = 0.0;
-  auto applyV = [&](const double* x, double* y) {
-    return stbem::apply_launch(op.prec, op.transpose, nt, nx, op.V, 1, x, y, W.apply, s);
-  };
+  int reduce_rc = 0;
+  auto applyV = [&](const double* x, double* y) { return op_product(op, op.V, x, y, W.apply, s, &reduce_rc); };
   // right preconditioner: y = L^{-1} D L^{-1} x (lumped mixed mass), or
   // y = M^{-1} D M^{-T} x per time step (consistent mixed mass), or y = x
   auto applyP = [&](const double* x, double* y) -> cudaError_t {
@@ -723,11 +767,11 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
                                  : stbem::diag_div_launch(x, op.L, W.u, nt, nx, s);
     if (e != cudaSuccess) return e;
     if (op.mass == 2) {
-      e = stbem::apply_launch(op.prec, op.transpose, nt, nx, op.D, 1, W.u, W.v, W.apply, s);
+      e = op_product(op, op.D, W.u, W.v, W.apply, s, &reduce_rc);
       if (e != cudaSuccess) return e;
       return stbem::blockmul_launch(nt, nx, op.L, false, W.v, y, s);
     }
-    e = stbem::apply_launch(op.prec, op.transpose, nt, nx, op.D, 1, W.u, y, W.apply, s);
+    e = op_product(op, op.D, W.u, y, W.apply, s, &reduce_rc);
     if (e != cudaSuccess) return e;
     return stbem::diag_div_launch(y, op.L, y, nt, nx, s);
   };
@@ -758,7 +802,7 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
     if (first) {
       CUDA_TRY(ctx, cudaMemcpyAsync(W.r, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "solve: r");
     } else {
-      CUDA_TRY(ctx, applyV(w, W.v), "solve: V w");
+      OP_TRY(applyV(w, W.v), "solve: V w");
       CUDA_TRY(ctx, stbem::sub_launch(f, W.v, W.r, N, s), "solve: f - V w");
     }
     first = false;
@@ -775,8 +819,8 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
     for (int k = 0; k < restart; ++k) {
       double* qk = W.Q + (size_t)k * N;
       double* qk1 = W.Q + (size_t)(k + 1) * N;
-      CUDA_TRY(ctx, applyP(qk, W.z), "solve: precondition");
-      CUDA_TRY(ctx, applyV(W.z, W.v), "solve: V z");
+      OP_TRY(applyP(qk, W.z), "solve: precondition");
+      OP_TRY(applyV(W.z, W.v), "solve: V z");
       // classical Gram-Schmidt, twice
       CUDA_TRY(ctx, stbem::dots_launch(W.Q, k + 1, W.v, N, W.h, s), "solve: dots");
       CUDA_TRY(ctx, stbem::sub_combination_launch(W.Q, k + 1, W.h, W.v, N, s), "solve: orth");
@@ -822,7 +866,7 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
     }
     CUDA_TRY(ctx, cudaMemcpyAsync(W.h, y.data(), k_done * sizeof(double), cudaMemcpyHostToDevice, s), "solve: y");
     CUDA_TRY(ctx, stbem::combination_launch(W.Q, k_done, W.h, W.r, N, s), "solve: Qy");
-    CUDA_TRY(ctx, applyP(W.r, W.z), "solve: P Qy");
+    OP_TRY(applyP(W.r, W.z), "solve: P Qy");
     CUDA_TRY(ctx, stbem::axpy_launch(1.0, W.z, w, N, s), "solve: update");
     CUDA_TRY(ctx, cudaStreamSynchronize(s), "solve: sync");
   }
@@ -879,6 +923,130 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V
                         const double* b, double* lam, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* work, size_t work_bytes) {
   return solve_impl(ctx, true, nt, nx, vprec, V, D, L, b, lam, opts, info, work, work_bytes);
+}
+
+// ---------------------------------------------------------- lag sharding ------
+
+int stbem_lag_shard(int n_t, int n_ranks, int rank, int chunk, int max_ranges, int* host_ranges, int* n_ranges) {
+  if (n_t < 1 || n_ranks < 1 || rank < 0 || rank >= n_ranks || chunk < 1 || max_ranges < 0 || !n_ranges)
+    return STBEM_ERR_ARG;
+  const std::vector<int> r = stbem::lag_ranges(n_t, n_ranks, rank, chunk);
+  const int n = (int)r.size() / 2;
+  *n_ranges = n;
+  if (n > max_ranges || (n > 0 && !host_ranges)) return STBEM_ERR_NOMEM;
+  std::copy(r.begin(), r.end(), host_ranges);
+  return STBEM_OK;
+}
+
+int stbem_assemble_lag_blocks(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, int lag_begin, int lag_end,
+                              void* dev_blocks) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !dev_blocks) return fail(ctx, STBEM_ERR_ARG, "assemble_lag_blocks: NULL mesh or output");
+  if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble_lag_blocks: unknown operator %d", op);
+  if (prec != STBEM_F64 && prec != STBEM_F32)
+    return fail(ctx, STBEM_ERR_ARG, "assemble_lag_blocks: unknown precision %d", prec);
+  if (lag_begin < 0 || lag_end > m->n_t || lag_begin > lag_end)
+    return fail(ctx, STBEM_ERR_ARG, "assemble_lag_blocks: lag range [%d, %d) outside [0, %d)", lag_begin, lag_end,
+                m->n_t);
+  if (lag_begin == lag_end) return STBEM_OK;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble_lag_blocks: set device");
+  // The kernels write block d at base + d N^2 and only for d in the range;
+  // with the base moved down by lag_begin blocks (integer address arithmetic)
+  // block d lands at dev_blocks + (d - lag_begin) N^2, inside the caller's array.
+  const size_t elt = prec == STBEM_F64 ? sizeof(double) : sizeof(float);
+  const uintptr_t shifted = reinterpret_cast<uintptr_t>(dev_blocks) - (uintptr_t)lag_begin * m->N * m->N * elt;
+  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, lag_begin, lag_end, reinterpret_cast<void*>(shifted),
+                                       ctx->stream),
+           "assemble_lag_blocks");
+  return STBEM_OK;
+}
+
+int stbem_apply_lags_workspace_bytes(int n_t, int n_x, int n_lags, int n_rhs, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_lags < 1 || n_lags > n_t || n_rhs < 1) return STBEM_ERR_ARG;
+  *bytes = stbem::apply_range_workspace_bytes(n_t, n_x, n_lags, n_rhs);
+  return STBEM_OK;
+}
+
+int stbem_apply_lags(stbem_ctx* ctx, int prec, int transpose, int n_t, int n_x, int lag_begin, int lag_end,
+                     const void* A_blocks, int n_rhs, const double* x, double* y, int accumulate, void* work,
+                     size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A_blocks || !x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "apply_lags: NULL pointer");
+  if (n_t < 1 || n_x < 1 || n_rhs < 1 || lag_begin < 0 || lag_end > n_t || lag_begin >= lag_end)
+    return fail(ctx, STBEM_ERR_ARG, "apply_lags: bad sizes or lag range [%d, %d)", lag_begin, lag_end);
+  if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "apply_lags: bad precision");
+  if ((const void*)x == (const void*)y) return fail(ctx, STBEM_ERR_ARG, "apply_lags: x and y overlap");
+  if (!stbem::apply_grid_fits(n_t, n_x, n_rhs))
+    return fail(ctx, STBEM_ERR_ARG, "apply_lags: n_rhs x time tiles exceeds the grid limit 65535");
+  const size_t need = stbem::apply_range_workspace_bytes(n_t, n_x, lag_end - lag_begin, n_rhs);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "apply_lags: workspace %zu < %zu bytes", work_bytes, need);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_lags: set device");
+  CUDA_TRY(ctx, stbem::apply_range_launch(prec, transpose != 0, n_t, n_x, lag_begin, lag_end, A_blocks, n_rhs, x, y,
+                                          accumulate != 0, work, ctx->stream),
+           "apply_lags");
+  return STBEM_OK;
+}
+
+namespace {
+// the largest product workspace over every lag-range length
+size_t any_range_apply_bytes(int nt, int nx) {
+  size_t b = 0;
+  for (int nl = 1; nl <= nt; ++nl) b = std::max(b, stbem::apply_range_workspace_bytes(nt, nx, nl, 1));
+  return b;
+}
+}  // namespace
+
+int stbem_solve_sharded_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || restart < 1) return STBEM_ERR_ARG;
+  *bytes = solve_bytes(n_t, n_x, restart) - stbem::apply_workspace_bytes(n_t, n_x, 1) + any_range_apply_bytes(n_t, n_x);
+  return STBEM_OK;
+}
+
+int stbem_solve_sharded(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V_blocks, const void* D_blocks,
+                        int n_ranges, const int* host_ranges, stbem_allreduce_fn allreduce, void* user,
+                        const double* L, const double* f, double* w, const stbem_solve_opts* opts,
+                        stbem_solve_info* info, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!f || !w || !opts || !info || !work || !allreduce) return fail(ctx, STBEM_ERR_ARG, "solve_sharded: NULL pointer");
+  if (nt < 1 || nx < 1 || n_ranges < 0 || (n_ranges > 0 && (!host_ranges || !V_blocks)))
+    return fail(ctx, STBEM_ERR_ARG, "solve_sharded: bad sizes or ranges");
+  for (int k = 0; k < n_ranges; ++k) {
+    const int a = host_ranges[2 * k], b = host_ranges[2 * k + 1];
+    if (a < 0 || b > nt || a >= b || (k > 0 && a < host_ranges[2 * k - 1]))
+      return fail(ctx, STBEM_ERR_ARG, "solve_sharded: lag range %d [%d, %d) invalid", k, a, b);
+  }
+  if (vprec != STBEM_F64 && vprec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "solve_sharded: bad precision");
+  const int restart = opts->restart, maxit = opts->max_iter;
+  if (restart < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "solve_sharded: bad options");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!L || (n_ranges > 0 && !D_blocks)))
+    return fail(ctx, STBEM_ERR_ARG, "solve_sharded: preconditioner needs D and L");
+  size_t need = 0;
+  stbem_solve_sharded_workspace_bytes(nt, nx, restart, &need);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "solve_sharded: workspace %zu < %zu bytes", work_bytes, need);
+  SolveWork W;
+  carve(work, work_bytes, nt, nx, restart, &W);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_sharded: set device");
+  // D non-NULL signals the preconditioner to gmres_core; a rank without lags
+  // never reads it
+  GmresOp op{nt, nx, vprec, V_blocks ? V_blocks : work, prec ? (D_blocks ? D_blocks : work) : nullptr, L};
+  op.mass = opts->precondition == 2 ? 2 : 1;
+  op.n_ranges = n_ranges;
+  op.ranges = host_ranges;
+  op.reduce = allreduce;
+  op.reduce_user = user;
+  int iters = 0;
+  double relres = 0.0;
+  const int status = gmres_core(ctx, op, f, w, opts->tol, maxit, restart, W, &iters, &relres);
+  info->iterations = iters;
+  info->rel_residual = relres;
+  info->status = status;
+  if (status == STBEM_ERR_NAN || status == STBEM_ERR_NOCONV || status == STBEM_ERR_BREAKDOWN)
+    return fail(ctx, status, "solve_sharded: %s after %d iterations (relres %.3e)",
+                status == STBEM_ERR_NAN ? "NaN"
+                : status == STBEM_ERR_NOCONV ? "no convergence" : "breakdown (singular operator)",
+                iters, relres);
+  return status;
 }
 
 int stbem_mixed_mass_inverse(stbem_ctx* ctx, const stbem_mesh* m, double* dev_Minv) {

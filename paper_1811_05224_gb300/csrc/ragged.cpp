@@ -685,4 +685,116 @@ int stbem_ragged_solve(stbem_ctx* ctx, stbem_ragged* R, int prec, const void* V,
   return STBEM_OK;
 }
 
+
+int stbem_ragged_solve_mixed_workspace_bytes(const stbem_ragged* R, int restart, size_t* bytes) {
+  if (!R || !bytes || restart < 1) return STBEM_ERR_ARG;
+  size_t inner = 0;
+  const int rc = stbem_ragged_solve_workspace_bytes(R, restart, &inner);
+  if (rc != STBEM_OK) return rc;
+  const size_t n = (size_t)R->vec_elems, P = (size_t)R->P;
+  *bytes = align256(inner) + 2 * align256(n * sizeof(double)) + 2 * align256(P * sizeof(double));
+  return STBEM_OK;
+}
+
+// FP64 iterative refinement around the lockstep solve: r = f - V64 w with the
+// FP64 operators, inner lockstep GMRES on the FP32 operators (V32, D32) for
+// the corrections; converged problems get a zero right-hand side, so they
+// stop iterating.
+int stbem_ragged_solve_mixed(stbem_ctx* ctx, stbem_ragged* R, const double* V64, const float* V32, const float* D32,
+                             const double* L, const double* f, double* w, const stbem_solve_opts* opts,
+                             double inner_tol, stbem_solve_info* infos, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!R || !V64 || !V32 || !f || !w || !opts || !infos || !work)
+    return fail(ctx, STBEM_ERR_ARG, "ragged_solve_mixed: NULL argument");
+  const int m = opts->restart, maxit = opts->max_iter;
+  if (m < 1 || maxit < 1 || !(opts->tol > 0) || !(inner_tol > 0) || !(inner_tol < 1))
+    return fail(ctx, STBEM_ERR_ARG, "ragged_solve_mixed: bad options");
+  size_t need = 0, inner = 0;
+  stbem_ragged_solve_mixed_workspace_bytes(R, m, &need);
+  stbem_ragged_solve_workspace_bytes(R, m, &inner);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "ragged_solve_mixed: workspace too small");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "ragged_solve_mixed: set device");
+  const int P = R->P;
+  const size_t n = (size_t)R->vec_elems;
+  char* base = static_cast<char*>(work);
+  double* r = reinterpret_cast<double*>(base + align256(inner));
+  double* dw = r + align256(n * sizeof(double)) / sizeof(double);
+  double* sq = dw + align256(n * sizeof(double)) / sizeof(double);
+  double* msk = sq + align256(P * sizeof(double)) / sizeof(double);
+  // the FP64 product's partial sums share the inner solve's product scratch
+  RWork Wi;
+  carve_ragged(work, R, m, &Wi);
+  cudaStream_t s = ctx->stream;
+  std::vector<double> hv(P);
+  auto norms = [&](const double* x, std::vector<double>& out) -> cudaError_t {
+    cudaError_t e = stbem::rdots_launch(x, n, 1, x, R->d_vprefix, P, sq, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hv.data(), sq, P * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    out.resize(P);
+    for (int p = 0; p < P; ++p) out[p] = std::sqrt(hv[p]);
+    return e;
+  };
+  std::vector<double> normF, rn;
+  CUDA_TRY(ctx, norms(f, normF), "ragged_solve_mixed: norm f");
+  CUDA_TRY(ctx, cudaMemsetAsync(w, 0, n * sizeof(double), s), "ragged_solve_mixed: w = 0");
+  CUDA_TRY(ctx, cudaMemcpyAsync(r, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "ragged_solve_mixed: r");
+  for (int p = 0; p < P; ++p) {
+    infos[p].iterations = 0;
+    infos[p].rel_residual = 0.0;
+    infos[p].status = std::isfinite(normF[p]) ? STBEM_OK : STBEM_ERR_NAN;
+  }
+  std::vector<stbem_solve_info> ii(P);
+  int total = 0;
+  for (int outer = 0; outer < 30; ++outer) {
+    CUDA_TRY(ctx, norms(r, rn), "ragged_solve_mixed: norm r");
+    bool any = false;
+    std::vector<double> keep(P, 0.0);
+    for (int p = 0; p < P; ++p) {
+      const double rel = normF[p] > 0 ? rn[p] / normF[p] : 0.0;
+      if (!std::isfinite(rel) && infos[p].status == STBEM_OK) infos[p].status = STBEM_ERR_NAN;
+      infos[p].rel_residual = rel;
+      const bool active = infos[p].status == STBEM_OK && rel > opts->tol;
+      keep[p] = active ? 1.0 : 0.0;
+      any = any || active;
+    }
+    if (!any) break;
+    if (total >= maxit) {
+      for (int p = 0; p < P; ++p)
+        if (keep[p] != 0.0) infos[p].status = STBEM_ERR_NOCONV;
+      break;
+    }
+    // right-hand sides of the corrections: the active problems' residuals
+    CUDA_TRY(ctx, cudaMemcpyAsync(msk, keep.data(), P * sizeof(double), cudaMemcpyHostToDevice, s), "mask");
+    CUDA_TRY(ctx, stbem::rscale_launch(r, msk, R->d_vprefix, P, dw, (long long)n, s), "mask r");
+    stbem_solve_opts io = *opts;
+    io.tol = inner_tol;
+    io.max_iter = maxit - total;
+    // correction: V32 c = (masked r), right-hand side in dw, c into r
+    const int rc = stbem_ragged_solve(ctx, R, STBEM_F32, V32, D32, L, dw, r, &io, ii.data(), base, inner);
+    if (rc != STBEM_OK && rc != STBEM_ERR_NOCONV && rc != STBEM_ERR_NAN && rc != STBEM_ERR_BREAKDOWN) return rc;
+    int it = 0;
+    for (int p = 0; p < P; ++p) {
+      if (keep[p] == 0.0) continue;
+      it = std::max(it, ii[p].iterations);
+      infos[p].iterations += ii[p].iterations;
+      if (ii[p].status == STBEM_ERR_NAN || ii[p].status == STBEM_ERR_BREAKDOWN) infos[p].status = ii[p].status;
+    }
+    total += it;
+    CUDA_TRY(ctx, stbem::axpy_launch(1.0, r, w, n, s), "ragged_solve_mixed: w += c");
+    CUDA_TRY(ctx, rapply(R, STBEM_F64, V64, w, dw, Wi.part, s), "ragged_solve_mixed: V64 w");
+    CUDA_TRY(ctx, stbem::sub_launch(f, dw, r, n, s), "ragged_solve_mixed: r = f - V64 w");
+    if (it == 0) {
+      for (int p = 0; p < P; ++p)
+        if (keep[p] != 0.0 && infos[p].status == STBEM_OK) infos[p].status = STBEM_ERR_NOCONV;
+      break;
+    }
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(s), "ragged_solve_mixed: finish");
+  int worst = STBEM_OK;
+  for (int p = 0; p < P; ++p)
+    if (infos[p].status != STBEM_OK) worst = infos[p].status;
+  if (worst != STBEM_OK) return fail(ctx, worst, "ragged_solve_mixed: some problems did not converge");
+  return STBEM_OK;
+}
+
 }  // extern "C"

@@ -29,7 +29,10 @@ struct ApplyPlan {
   int MT, IT, CH, DC;
 };
 
-static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI) {
+// Plan of a product over the nlag lags of a range (nlag = nt: all of them).
+static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI, int nlag = -1) {
+  if (nlag < 0) nlag = nt;
+  if (nlag < 1) nlag = 1;
   ApplyPlan p;
   p.MT = (nt + tm - 1) / tm;
   p.IT = (nx + ti - 1) / ti;
@@ -39,9 +42,9 @@ static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI) {
   if (per_chunk < 1) per_chunk = 1;
   int ch = (int)((target + per_chunk - 1) / per_chunk);
   if (ch < 1) ch = 1;
-  if (ch > nt) ch = nt;
-  p.DC = (nt + ch - 1) / ch;
-  p.CH = (nt + p.DC - 1) / p.DC;
+  if (ch > nlag) ch = nlag;
+  p.DC = (nlag + ch - 1) / ch;
+  p.CH = (nlag + p.DC - 1) / p.DC;
   return p;
 }
 
@@ -55,26 +58,30 @@ static bool use_apply32(int nt, int nx, int n_rhs) {
   return use_apply32(nx) && (long long)n_rhs * it * mt * (mt + 1) / 2 >= 2LL * 2 * sm_count();
 }
 
-size_t apply_workspace_bytes(int nt, int nx, int n_rhs) {
-  const ApplyPlan p = make_plan(nt, nx);
+size_t apply_range_workspace_bytes(int nt, int nx, int nlag, int n_rhs) {
+  const ApplyPlan p = make_plan(nt, nx, TM, TI, nlag);
   size_t b = (size_t)n_rhs * p.MT * p.CH * TM * (size_t)nx * sizeof(double);
   if (use_apply32(nt, nx, n_rhs)) {
-    const ApplyPlan q = make_plan(nt, nx, 64, 128);
+    const ApplyPlan q = make_plan(nt, nx, 64, 128, nlag);
     b = std::max(b, (size_t)n_rhs * q.MT * q.CH * 64 * (size_t)nx * sizeof(double));
   }
   return b;
 }
 
-// One (row tile it, lag chunk ch, right-hand side b, time tile mt) unit.
+size_t apply_workspace_bytes(int nt, int nx, int n_rhs) { return apply_range_workspace_bytes(nt, nx, nt, n_rhs); }
+
+// One (row tile it, lag chunk ch, right-hand side b, time tile mt) unit over
+// the lags [lag_lo, lag_hi); A points at the block of lag lag_lo.
 template <typename TA, typename TC, bool TRANS>
-__device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
-                                           const double* __restrict__ x, double* __restrict__ part, int it,
-                                           int ch, int b, int mt, TC (*As)[TI + 1], TC (*Xs)[TM + 1]) {
+__device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi,
+                                           const TA* __restrict__ A, const double* __restrict__ x,
+                                           double* __restrict__ part, int it, int ch, int b, int mt,
+                                           TC (*As)[TI + 1], TC (*Xs)[TM + 1]) {
   const int m0 = mt * TM, i0 = it * TI;
   const int mmax = min(m0 + TM, nt) - 1;        // largest m in the tile
-  const int d0 = ch * DC;
-  if (d0 > mmax) return;
-  const int d1 = min(d0 + DC, mmax + 1);
+  const int d0 = lag_lo + ch * DC;
+  if (d0 > mmax || d0 >= lag_hi) return;
+  const int d1 = min(min(d0 + DC, mmax + 1), lag_hi);
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;        // rows tx*4.., time ty*2..
   const double* xb = x + (size_t)b * nt * nx;
@@ -91,7 +98,7 @@ __device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int D
     }
 
   for (int d = d0; d < d1; ++d) {
-    const TA* Ad = A + (size_t)d * nx * nx;
+    const TA* Ad = A + (size_t)(d - lag_lo) * nx * nx;
     for (int j0 = 0; j0 < nx; j0 += TJ) {
       // A tile: element (row i0+ii, column j0+jj)
 #pragma unroll
@@ -164,12 +171,12 @@ __device__ __forceinline__ void apply_body(int nt, int nx, int MT, int CH, int D
 
 template <typename TA, typename TC, bool TRANS>
 __global__ void __launch_bounds__(kApplyThreads)
-k_apply(int nt, int nx, int MT, int CH, int DC, const TA* __restrict__ A,
+k_apply(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const TA* __restrict__ A,
         const double* __restrict__ x, double* __restrict__ part) {
   __shared__ TC As[TJ][TI + 1];
   __shared__ TC Xs[TJ][TM + 1];
-  apply_body<TA, TC, TRANS>(nt, nx, MT, CH, DC, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT,
-                            blockIdx.z % MT, As, Xs);
+  apply_body<TA, TC, TRANS>(nt, nx, MT, CH, DC, lag_lo, lag_hi, A, x, part, blockIdx.x, blockIdx.y,
+                            blockIdx.z / MT, blockIdx.z % MT, As, Xs);
 }
 
 // ---- FP32 forward product, register-tiled ----------------------------------------------
@@ -190,14 +197,15 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   lo += err;
 }
 
-__device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int DC, const float* __restrict__ A,
-                                             const double* __restrict__ x, double* __restrict__ part, int it, int ch,
-                                             int b, int mt, float (*As)[TI4], float (*Xs)[TM4]) {
+__device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi,
+                                             const float* __restrict__ A, const double* __restrict__ x,
+                                             double* __restrict__ part, int it, int ch, int b, int mt,
+                                             float (*As)[TI4], float (*Xs)[TM4]) {
   const int m0 = mt * TM4, i0 = it * TI4;
   const int mmax = min(m0 + TM4, nt) - 1;
-  const int d0 = ch * DC;
-  if (d0 > mmax) return;
-  const int d1 = min(d0 + DC, mmax + 1);
+  const int d0 = lag_lo + ch * DC;
+  if (d0 > mmax || d0 >= lag_hi) return;
+  const int d1 = min(min(d0 + DC, mmax + 1), lag_hi);
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const double* xb = x + (size_t)b * nt * nx;
@@ -210,7 +218,7 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
       lo[c][a] = 0.f;
     }
   for (int d = d0; d < d1; ++d) {
-    const float* Ad = A + (size_t)d * nx * nx;
+    const float* Ad = A + (size_t)(d - lag_lo) * nx * nx;
     float acc[8][4];
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -274,11 +282,12 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
 }
 
 __global__ void __launch_bounds__(256, 2)
-k_apply32(int nt, int nx, int MT, int CH, int DC, const float* __restrict__ A, const double* __restrict__ x,
-          double* __restrict__ part) {
+k_apply32(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const float* __restrict__ A,
+          const double* __restrict__ x, double* __restrict__ part) {
   __shared__ __align__(16) float As[TJ4][TI4];
   __shared__ __align__(16) float Xs[TJ4][TM4];
-  apply32_body(nt, nx, MT, CH, DC, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT, blockIdx.z % MT, As, Xs);
+  apply32_body(nt, nx, MT, CH, DC, lag_lo, lag_hi, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT,
+               blockIdx.z % MT, As, Xs);
 }
 
 // ---- ragged batches ------------------------------------------------------------------
@@ -316,8 +325,8 @@ k_ragged_apply(const RaggedApplyPlan* __restrict__ plans, const int* __restrict_
     const int it = (int)(u % pl.IT);
     const long long r = u / pl.IT;
     const int mt = (int)(r % pl.MT), ch = (int)(r / pl.MT);
-    apply_body<TA, TC, false>(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, A + pl.a_off, x + pl.v_off, part + pl.part_off,
-                              it, ch, 0, mt, As, Xs);
+    apply_body<TA, TC, false>(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, 0, pl.nt, A + pl.a_off, x + pl.v_off,
+                              part + pl.part_off, it, ch, 0, mt, As, Xs);
     __syncthreads();
   }
 }
@@ -342,8 +351,8 @@ k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restric
     const int it = (int)(u % pl.IT);
     const long long r = u / pl.IT;
     const int mt = (int)(r % pl.MT), ch = (int)(r / pl.MT);
-    apply32_body(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, A + pl.a_off, x + pl.v_off, part + pl.part_off, it, ch, 0, mt,
-                 As, Xs);
+    apply32_body(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, 0, pl.nt, A + pl.a_off, x + pl.v_off, part + pl.part_off, it,
+                 ch, 0, mt, As, Xs);
     __syncthreads();
   }
 }
@@ -369,8 +378,11 @@ __global__ void k_ragged_reduce(const RaggedApplyPlan* __restrict__ plans, const
   }
 }
 
+// y (= or +=) the sum of the lag-chunk partials of a product over the lags
+// [lag_lo, lag_lo + CH DC): chunk c holds lags lag_lo + c DC .., written only
+// where it has a lag <= the tile's last step (mmax)
 template <bool TRANS, int TM_ = TM>
-__global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC,
+__global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC, int lag_lo, int accumulate,
                                const double* __restrict__ part, double* __restrict__ y) {
   const size_t total = (size_t)n_rhs * nt * nx;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -380,50 +392,54 @@ __global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC
     const int b = (int)(e / ((size_t)nx * nt));
     const int mt = m / TM_, mm = m % TM_;
     const int mmax = min(mt * TM_ + TM_, nt) - 1;
-    const int nch = min(CH, mmax / DC + 1);
+    const int nch = mmax < lag_lo ? 0 : min(CH, (mmax - lag_lo) / DC + 1);
     const double* pt = part + ((((size_t)b * MT + mt) * CH) * TM_ + mm) * nx + i;
     double s = 0.0;
     for (int c = 0; c < nch; ++c) s += pt[(size_t)c * TM_ * nx];
     const int mo = TRANS ? (nt - 1 - m) : m;
-    y[((size_t)b * nt + mo) * nx + i] = s;
+    double* yp = y + ((size_t)b * nt + mo) * nx + i;
+    *yp = accumulate ? *yp + s : s;
   }
 }
 
-static cudaError_t launch32(int nt, int nx, const float* A, int n_rhs, const double* x, double* y, double* part,
-                            cudaStream_t s) {
-  const ApplyPlan p = make_plan(nt, nx, TM4, TI4);
-  k_apply32<<<dim3(p.IT, p.CH, n_rhs * p.MT), 256, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, A, x, part);
+static cudaError_t launch32(int nt, int nx, int lag_lo, int lag_hi, const float* A, int n_rhs, const double* x,
+                            double* y, bool accumulate, double* part, cudaStream_t s) {
+  const ApplyPlan p = make_plan(nt, nx, TM4, TI4, lag_hi - lag_lo);
+  k_apply32<<<dim3(p.IT, p.CH, n_rhs * p.MT), 256, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, lag_lo, lag_hi, A, x, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launches(2);
   const size_t total = (size_t)n_rhs * nt * nx;
   const int blocks = stride_grid(total, 256, 16);
-  k_apply_reduce<false, TM4><<<blocks, 256, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
+  k_apply_reduce<false, TM4><<<blocks, 256, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, lag_lo, accumulate ? 1 : 0,
+                                                    part, y);
   return cudaGetLastError();
 }
 
 template <typename TA, typename TC>
-static cudaError_t launch(bool trans, int nt, int nx, const TA* A, int n_rhs, const double* x,
-                          double* y, double* part, cudaStream_t s) {
+static cudaError_t launch(bool trans, int nt, int nx, int lag_lo, int lag_hi, const TA* A, int n_rhs,
+                          const double* x, double* y, bool accumulate, double* part, cudaStream_t s) {
   if constexpr (sizeof(TA) == 4) {
-    if (!trans && use_apply32(nt, nx, n_rhs)) return launch32(nt, nx, A, n_rhs, x, y, part, s);
+    if (!trans && use_apply32(nt, nx, n_rhs)) return launch32(nt, nx, lag_lo, lag_hi, A, n_rhs, x, y, accumulate,
+                                                               part, s);
   }
-  const ApplyPlan p = make_plan(nt, nx);
+  const ApplyPlan p = make_plan(nt, nx, TM, TI, lag_hi - lag_lo);
   dim3 grid(p.IT, p.CH, n_rhs * p.MT);
   if (trans)
-    k_apply<TA, TC, true><<<grid, kApplyThreads, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, A, x, part);
+    k_apply<TA, TC, true><<<grid, kApplyThreads, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, lag_lo, lag_hi, A, x, part);
   else
-    k_apply<TA, TC, false><<<grid, kApplyThreads, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, A, x, part);
+    k_apply<TA, TC, false><<<grid, kApplyThreads, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, lag_lo, lag_hi, A, x, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launches(2);
   const size_t total = (size_t)n_rhs * nt * nx;
   const int threads = 256;
   const int blocks = stride_grid(total, threads, 16);
+  const int acc = accumulate ? 1 : 0;
   if (trans)
-    k_apply_reduce<true><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
+    k_apply_reduce<true><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, lag_lo, acc, part, y);
   else
-    k_apply_reduce<false><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, part, y);
+    k_apply_reduce<false><<<blocks, threads, 0, s>>>(nt, nx, n_rhs, p.MT, p.CH, p.DC, lag_lo, acc, part, y);
   return cudaGetLastError();
 }
 
@@ -539,12 +555,19 @@ cudaError_t ragged_apply_launch(int prec, bool fp32_tiles, const RaggedApplyPlan
   return cudaGetLastError();
 }
 
-cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
-                         const double* x, double* y, void* work, cudaStream_t s) {
+cudaError_t apply_range_launch(int prec, bool trans, int nt, int nx, int lag_lo, int lag_hi, const void* A,
+                               int n_rhs, const double* x, double* y, bool accumulate, void* work, cudaStream_t s) {
   double* part = static_cast<double*>(work);
   if (prec == STBEM_F64)
-    return launch<double, double>(trans, nt, nx, static_cast<const double*>(A), n_rhs, x, y, part, s);
-  return launch<float, float>(trans, nt, nx, static_cast<const float*>(A), n_rhs, x, y, part, s);
+    return launch<double, double>(trans, nt, nx, lag_lo, lag_hi, static_cast<const double*>(A), n_rhs, x, y,
+                                  accumulate, part, s);
+  return launch<float, float>(trans, nt, nx, lag_lo, lag_hi, static_cast<const float*>(A), n_rhs, x, y, accumulate,
+                              part, s);
+}
+
+cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
+                         const double* x, double* y, void* work, cudaStream_t s) {
+  return apply_range_launch(prec, trans, nt, nx, 0, nt, A, n_rhs, x, y, false, work, s);
 }
 
 }  // namespace stbem

@@ -23,6 +23,11 @@ bool apply_grid_fits(int nt, int nx, int n_rhs);
 cudaError_t pipe_peaks(double* out, cudaStream_t s);
 cudaError_t apply_launch(int prec, bool trans, int nt, int nx, const void* A, int n_rhs,
                          const double* x, double* y, void* work, cudaStream_t s);
+// The product restricted to the lags [lag_lo, lag_hi): A holds those lag
+// blocks only (block d at A[d - lag_lo]); y = (accumulate ? y : 0) + sum.
+size_t apply_range_workspace_bytes(int nt, int nx, int nlag, int n_rhs);
+cudaError_t apply_range_launch(int prec, bool trans, int nt, int nx, int lag_lo, int lag_hi, const void* A,
+                               int n_rhs, const double* x, double* y, bool accumulate, void* work, cudaStream_t s);
 
 // Product plan of one problem of a ragged batch with `lags_per_chunk` lags per
 // partial (the tuned shape) and the offsets of its data.

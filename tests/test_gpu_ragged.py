@@ -126,8 +126,10 @@ def test_ragged_solve_matches_single_and_oracle(ctx, batch, precondition):
         # true residual of the batch's solution
         r = fp - P.apply(ctx, Vp, R.view_vec(w, p))
         assert float(r.norm() / fp.norm()) <= 1.01e-11, p
-    # one problem against the oracle's exact block forward substitution
-    Vn = R.view_op(V, 1).cpu().numpy()
+    # one problem against the oracle's exact block forward substitution with the oracle's V
+    from oracle import assembly as OA
+    from oracle.geometry import BoundaryMesh
+    Vn = OA.assemble("V", BoundaryMesh(*_problems()[1]))
     wref = OS.forward_substitution(Vn, R.view_vec(f, 1).cpu().numpy())
     assert float(np.linalg.norm(R.view_vec(w, 1).cpu().numpy() - wref) / np.linalg.norm(wref)) < 1e-8
 
@@ -158,3 +160,32 @@ def test_ragged_solve_fp32_operators(ctx, batch):
     for p, m in enumerate(meshes):
         w1, _ = P.solve(ctx, R.view_op(V, p), R.view_vec(f, p), R.view_op(D, p), R.view_mass(L, p), tol=1e-7)
         assert float((R.view_vec(w, p) - w1).norm() / w1.norm()) < 2e-5, p
+
+
+def test_ragged_mixed_solve_reaches_fp64_accuracy(ctx, batch):
+    """FP32 lockstep solves inside FP64 refinement (residuals with the FP64
+    V): every problem's FP64 residual <= 1e-10 and w within 1e-8 of the
+    oracle's block forward substitution (oracle V, same f) for the L-shape,
+    and within 1e-8 of the single-problem FP64 solves for the others."""
+    import paper_1811_05224_gb300 as P
+    from oracle import assembly as OA
+    from oracle.geometry import BoundaryMesh
+    R, meshes, probs = batch
+    V64 = R.assemble("V")
+    V32, D32 = R.assemble("V", "f32"), R.assemble("D", "f32")
+    K = R.assemble("K")
+    L = R.lumped_mass()
+    ys = [(1.5, 1.5), (1.3, 1.4), (1.8, -0.2), (2.0, 0.4), (-0.7, 0.5)]
+    _, f = R.rhs(K, ys)
+    w, infos = R.solve_mixed(V64, V32, f, D32, L, tol=1e-10, inner_tol=1e-3, restart=30, max_iter=800)
+    assert all(i["status"] == 0 and i["rel_residual"] <= 1e-10 for i in infos), infos
+    D64 = R.assemble("D")
+    for p, m in enumerate(meshes):
+        fp = R.view_vec(f, p)
+        r = fp - P.apply(ctx, R.view_op(V64, p), R.view_vec(w, p))
+        assert float(r.norm() / fp.norm()) <= 1.01e-10, p
+        w1, _ = P.solve(ctx, R.view_op(V64, p), fp, R.view_op(D64, p), R.view_mass(L, p), tol=1e-12)
+        assert float((R.view_vec(w, p) - w1).norm() / w1.norm()) < 1e-8, p
+    Vo = OA.assemble("V", BoundaryMesh(*probs[1]))
+    wref = OS.forward_substitution(Vo, R.view_vec(f, 1).cpu().numpy())
+    assert float(np.linalg.norm(R.view_vec(w, 1).cpu().numpy() - wref) / np.linalg.norm(wref)) < 1e-8
