@@ -70,16 +70,22 @@ class ShardedOperator:
     order), with the full problem's sizes."""
 
     def __init__(self, ctx: Context, mesh: Mesh, op: str, ranges, prec: str = "f64"):
-        self.ctx, self.n_t, self.n_x, self.prec = ctx, mesh.n_t, mesh.n_x, prec
+        self.ctx, self.n_t, self.n_x, self.prec, self.op = ctx, mesh.n_t, mesh.n_x, prec, op
         self.ranges = list(ranges)
         n_lags = sum(b - a for a, b in self.ranges)
         dt = torch.float64 if prec == "f64" else torch.float32
         self.blocks = torch.empty((max(1, n_lags), mesh.n_x, mesh.n_x), dtype=dt, device=ctx.device)
+        self.assemble(mesh)
+
+    def assemble(self, mesh: Mesh):
+        """(Re)assemble this rank's blocks on `mesh` (same sizes) in place."""
+        ctx = self.ctx
         k = 0
         for a, b in self.ranges:
-            ctx.check(ctx.lib.stbem_assemble_lag_blocks(ctx.h, mesh.h, OPS[op], PRECS[prec], a, b,
+            ctx.check(ctx.lib.stbem_assemble_lag_blocks(ctx.h, mesh.h, OPS[self.op], PRECS[self.prec], a, b,
                                                         _ptr(self.blocks[k:k + (b - a)])))
             k += b - a
+        return self
 
     def offsets(self):
         out, k = [], 0

@@ -46,3 +46,9 @@ def test_single_process_is_a_no_op():
     import bench
     assert bench.max_over_ranks(7.0, "cpu") == 7.0
     assert bench.weak_value(500, 1, 250.0) == pytest.approx(2000.0)
+
+
+def test_strong_value_counts_the_one_problem_once():
+    import bench
+    # one sharded problem of 3000 units finished by the slowest rank in 250 ms
+    assert bench.strong_value(3000, 250.0) == pytest.approx(12000.0)
