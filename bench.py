@@ -54,9 +54,10 @@ def _peaks():
 # (stbem_pipe_peaks) and reports the nominal fraction beside it.
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
-# at square256 (lags 2..65) from an ncu capture (profiles/k_tile_D_f64_lag2.md);
-# set to None whenever that kernel changes
-TRAFFIC_D2_BYTES = 770816 + 51712   # DRAM bytes of one 64-lag launch (lags 32..95, ncu)
+# at square256 (the launch of lags 32..95) from the ncu capture of the current
+# kernel (profiles/k_tile_D_f64_lag2.md gives the command); set to None
+# whenever that kernel changes until it is captured again
+TRAFFIC_D2_BYTES = 219392 + 58880
 
 
 def _oracle_sample(n_entries, seed, rng_lags=None):
@@ -612,6 +613,80 @@ def run_ragged(ctx, dev, stream):
     return out
 
 
+def run_nonuniform(ctx, dev, stream, n=128, q=1.5):
+    """Non-uniform time grid (Section 1 allows any decomposition of (0, T)):
+    unit square with N_x = n, graded nodes t_j = (j / n)^q on T = 1, alpha = 1,
+    g = U*(x - y*, t), y* = (1.5, 1.5).  All n (n + 1) / 2 blocks of V, K, D
+    assembled and stored packed (no Toeplitz structure), the block product
+    (every block read once) timed against max(bytes / HBM, flops / FP64) and
+    the preconditioned GMRES (lumped mass per step) to 1e-8."""
+    import torch
+    import workloads as W
+    import paper_1811_05224_gb300 as P
+    t = (np.arange(n + 1) / n) ** q
+    mesh = P.GradedMesh(ctx, W.unit_square(n // 4), t, 1.0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
+    blocks = n * (n + 1) // 2
+    ops, asm_ms = {}, {}
+    for op in "VKD":
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        ops[op] = P.nu_assemble(ctx, mesh, op)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        asm_ms[op] = a0.elapsed_time(a1)
+    g, f = P.nu_rhs(ctx, mesh, ops["K"], (1.5, 1.5))
+    L = P.nu_lumped_mass(ctx, mesh)
+    x = torch.randn(n, n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        P.nu_apply(ctx, ops["V"], n, x, out=y)
+    reps = 10
+    p0, p1 = ev(), ev()
+    p0.record(stream)
+    for _ in range(reps):
+        P.nu_apply(ctx, ops["V"], n, x, out=y)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    apply_ms = p0.elapsed_time(p1) / reps
+    nbytes = blocks * n * n * 8 + 2 * n * n * 8
+    flops = 2.0 * blocks * n * n
+    s0, s1 = ev(), ev()
+    s0.record(stream)
+    w, info = P.nu_solve(ctx, ops["V"], f, ops["D"], L, tol=1e-8)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    w0, info0 = P.nu_solve(ctx, ops["V"], f, tol=1e-8, max_iter=1000)
+    # the same problem on a uniform grid of n steps: iteration counts
+    mu = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
+    Vu, Ku, Du = (P.assemble(ctx, mu, o) for o in "VKD")
+    _, fu = P.rhs(ctx, mu, Ku, (1.5, 1.5))
+    _, infou = P.solve(ctx, Vu, fu, Du, P.lumped_mass(ctx, mu), tol=1e-8)
+    hbm = float(_peaks().get("hbm_gbs", 6784.2))
+    fp64 = P.pipe_peaks(ctx)["fp64_tflops"]
+    out = {
+        "workload": "unit square N_x = %d, graded t_j = (j / %d)^%g (step ratio up to %.2f), alpha = 1, "
+                    "%d packed blocks per operator (%.2f GB)" % (n, n, q, float(np.max(np.diff(t)[1:] /
+                                                                                      np.diff(t)[:-1])),
+                                                                  blocks, blocks * n * n * 8 / 1e9),
+        "assembly_ms": asm_ms,
+        "assembly_entries_per_s": 3 * blocks * n * n / (sum(asm_ms.values()) * 1e-3),
+        "block_apply_ms": apply_ms, "block_apply_gbs": nbytes / (apply_ms * 1e-3) / 1e9,
+        "block_apply_gflops": flops / (apply_ms * 1e-3) / 1e9,
+        "block_apply_roofline_ms": 1e3 * max(nbytes / (hbm * 1e9), flops / (fp64 * 1e12)),
+        "block_apply_roofline_frac": 1e3 * max(nbytes / (hbm * 1e9), flops / (fp64 * 1e12)) / apply_ms,
+        "block_apply_note": "roofline max(bytes / HBM, flops / FP64): 2 flops per 8 bytes need 1.7 TFLOP/s at "
+                            "the HBM rate, above GB300's FP64 rate, so the product is FP64-bound",
+        "gmres_prec_ms": s0.elapsed_time(s1), "gmres_prec_iterations": info["iterations"],
+        "gmres_prec_rel_residual": info["rel_residual"],
+        "gmres_plain_iterations": info0["iterations"],
+        "uniform_grid_prec_iterations": infou["iterations"],
+    }
+    del ops, g, f, L, x, y, w, w0, Vu, Ku, Du, fu
+    torch.cuda.empty_cache()
+    return out
+
+
 def max_over_ranks(ms, device):
     """The slowest rank's time: all ranks run their own problem and the job
     ends with the last one (a no-op without an initialised process group)."""
@@ -825,6 +900,9 @@ def run_ours(args):
     precision = None
     if not args.no_precision and world == 1:
         precision = run_precision(ctx, dev, stream)
+    nonuniform = None
+    if not args.no_nonuniform and world == 1:
+        nonuniform = run_nonuniform(ctx, dev, stream)
     # measured pipe peaks of this GPU (FP64 FMA is the assembly's and the
     # single-right-hand-side product's roofline)
     peaks = P.pipe_peaks(ctx)
@@ -897,6 +975,7 @@ def run_ours(args):
             "peaks": dict(peaks, hbm_gbs=hbm_gbs, note="fp64/fp32/ex2 measured in this run by stbem_pipe_peaks; "
                                                        "hbm from MEASURED_PEAKS.json"),
             "precision": precision,
+            "nonuniform": nonuniform,
             "mixed": {"step_ms": statistics.mean(mixed_ms), "solve_ms": statistics.mean(mixed_solve_ms),
                       "inner_iterations": mixed_info["iterations"],
                       "rel_residual_fp64": mixed_info["rel_residual"],
@@ -985,6 +1064,8 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the star256 differentiation component")
     ap.add_argument("--no-ragged", action="store_true", help="skip the 64-problem ragged component")
     ap.add_argument("--no-initial", action="store_true", help="skip the Section 4 example (M_h^0) component")
+    ap.add_argument("--no-nonuniform", action="store_true",
+                    help="skip the graded-time-grid (packed blocks) component")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the L-shape N_x = N_t = 1024 mixed-versus-FP64 component")
     ap.add_argument("--workload", default=WORKLOAD,

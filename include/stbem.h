@@ -274,6 +274,51 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void*
                         double* dev_lambda, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* dev_work, size_t work_bytes);
 
+/* ---- Non-uniform time grids (Section 1: any decomposition of (0, T)) ------
+ * With time nodes 0 = t_0 < .. < t_{n_t} = T the block of test step m and
+ * trial step n <= m depends on (m, n), not on m - n alone: the matrices stay
+ * block lower triangular but are not Toeplitz, so all n_t (n_t + 1) / 2
+ * blocks are assembled and stored, packed as A[p][i][j] with
+ * p = m (m + 1) / 2 + n (N_x x N_x each, FP64).  Time integrals:
+ * F(s1) - F(s2) - F(s3) + F(s4), s1 = t_{m+1} - t_n, s2 = t_{m+1} - t_{n+1},
+ * s3 = t_m - t_n, s4 = t_m - t_{n+1} (F = 0 for s <= 0), evaluated as on a
+ * uniform grid (closed form; the series form with the log terms cancelled at
+ * d = m - n = 1; the Peano form over the trapezoid of the overlap length at
+ * d >= 2); space rule of the uniform lag d.  Reduces to the Toeplitz blocks
+ * on a uniform grid (to rounding).  The rule is stated for neighbouring steps
+ * within a ratio of 4. */
+
+/* A boundary mesh on the time nodes host_t[0..n_t] (t_0 = 0, increasing;
+ * T = t_{n_t}); otherwise as stbem_mesh_create.  The uniform-grid calls
+ * (stbem_assemble, stbem_rhs, ...) reject such a mesh with STBEM_ERR_ARG;
+ * every mesh (uniform ones too) can be used with the stbem_nu_* calls. */
+int stbem_mesh_create_graded(stbem_ctx* ctx, const double* host_xy, int n_x, const double* host_t, int n_t,
+                             double alpha, stbem_mesh** out);
+/* Bytes of one packed operator: n_t (n_t + 1) / 2 n_x^2 doubles. */
+int stbem_nu_op_bytes(const stbem_mesh* mesh, size_t* bytes);
+/* All blocks of op (V, K or D) into dev_out (packed, FP64).  Errors:
+ * STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_nu_assemble(stbem_ctx* ctx, const stbem_mesh* mesh, int op, double* dev_out);
+/* Block lower-triangular product y[m] = sum_{n <= m} A[p(m, n)] x[n] (x, y:
+ * n_t x n_x doubles, not overlapping); every block is read once.  Errors:
+ * STBEM_ERR_ARG, STBEM_ERR_CUDA. */
+int stbem_nu_apply(stbem_ctx* ctx, int n_t, int n_x, const double* dev_A, const double* dev_x, double* dev_y);
+/* Right-hand side of eq. (4) for g = U*(x - y*, t), u_0 = 0: dev_g[n][p] the
+ * time average of g at vertex p over tau_n, dev_f = 1/2 M_h g + K_h g with
+ * M_h[(i,m),(p,m)] = h_m h_i / 2 and the packed dev_K. */
+int stbem_nu_rhs(stbem_ctx* ctx, const stbem_mesh* mesh, const double* dev_K, double y_star_x, double y_star_y,
+                 double* dev_g, double* dev_f);
+/* Lumped dual mass of every step (Section 4 lumping, the step length h_m in
+ * place of ht): dev_L[m][l] = h_m (h_{l-1} + 2 h_l + h_{l+1}) / 4. */
+int stbem_nu_lumped_mass(stbem_ctx* ctx, const stbem_mesh* mesh, double* dev_L);
+/* stbem_solve for packed operators: right-preconditioned GMRES (Section 2
+ * preconditioner, opts->precondition = 0 or 1 with dev_L from
+ * stbem_nu_lumped_mass).  Workspace: stbem_solve_workspace_bytes.  Errors
+ * as stbem_solve. */
+int stbem_nu_solve(stbem_ctx* ctx, int n_t, int n_x, const double* dev_V, const double* dev_D, const double* dev_L,
+                   const double* dev_f, double* dev_w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                   void* dev_work, size_t work_bytes);
+
 /* ---- Lag sharding of one problem across ranks (Section 3) -------------------
  * The paper distributes the blocks of its block-lower-triangular matrices over
  * processes.  On a uniform time grid all blocks at one lag are equal, so here

@@ -4,7 +4,8 @@ The hot path of the preconditioned space-time Galerkin BEM (arXiv:1811.05224):
 assembly of V_h, K_h, D_h and block-Toeplitz products inside preconditioned
 GMRES, in hand-written CUDA behind the C ABI of include/stbem.h.
 """
-from .api import (Context, Domain, Mesh, Ragged, apply, pipe_peaks, evaluate, m0_apply, m0_assemble, planewave_data, rhs_initial, apply_tc, assemble, assemble_lags, lumped_mass, mixed_mass_inverse, rhs,  # noqa: F401
+from .api import (Context, Domain, GradedMesh, Mesh, Ragged, apply, pipe_peaks, nu_apply, nu_assemble, nu_lumped_mass,
+                  nu_rhs, nu_solve, evaluate, m0_apply, m0_assemble, planewave_data, rhs_initial, apply_tc, assemble, assemble_lags, lumped_mass, mixed_mass_inverse, rhs,  # noqa: F401
                   apply_tc3, bf16_split3, grad, rhs_batched, round_f32, solve, solve_adjoint, solve_batched,
                   solve_mixed, to_bf16)
 from .autograd import neumann_solve  # noqa: F401

@@ -82,6 +82,77 @@ class Mesh:
             pass
 
 
+class GradedMesh(Mesh):
+    """Polygon boundary mesh x the non-uniform time grid t (n_t + 1 nodes,
+    t_0 = 0, increasing): operators are the packed blocks of the nu_* calls."""
+
+    def __init__(self, ctx: Context, vertices, t, alpha: float):
+        xy = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
+        tn = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1))
+        self.ctx = ctx
+        self.n_x = xy.size // 2
+        self.n_t = tn.size - 1
+        self.T = float(tn[-1])
+        self.alpha = float(alpha)
+        self.vertices = xy.reshape(-1, 2).copy()
+        self.t = tn.copy()
+        h = ctypes.c_void_p()
+        P = ctypes.POINTER(ctypes.c_double)
+        ctx.check(ctx.lib.stbem_mesh_create_graded(ctx.h, xy.ctypes.data_as(P), self.n_x, tn.ctypes.data_as(P),
+                                                   self.n_t, self.alpha, ctypes.byref(h)))
+        self.h = h
+
+
+def nu_assemble(ctx: Context, mesh: Mesh, op: str, out=None):
+    """Packed blocks A[p] (p = m (m + 1) / 2 + n, n <= m) of op on mesh's time grid."""
+    nt, nx = mesh.n_t, mesh.n_x
+    if out is None:
+        out = ctx.empty((nt * (nt + 1) // 2, nx, nx))
+    ctx.check(ctx.lib.stbem_nu_assemble(ctx.h, mesh.h, OPS[op], _ptr(out)))
+    return out
+
+
+def nu_apply(ctx: Context, A, n_t: int, x, out=None):
+    """y[m] = sum_{n <= m} A[p(m, n)] x[n] (x: n_t x n_x)."""
+    if out is None:
+        out = torch.empty_like(x)
+    ctx.check(ctx.lib.stbem_nu_apply(ctx.h, n_t, x.shape[-1], _ptr(A), _ptr(x), _ptr(out)))
+    return out
+
+
+def nu_rhs(ctx: Context, mesh: Mesh, K, y_star):
+    """(g, f) of eq. (4) on mesh's time grid for g = U*(x - y*, t)."""
+    g = ctx.empty((mesh.n_t, mesh.n_x))
+    f = ctx.empty((mesh.n_t, mesh.n_x))
+    ctx.check(ctx.lib.stbem_nu_rhs(ctx.h, mesh.h, _ptr(K), float(y_star[0]), float(y_star[1]), _ptr(g), _ptr(f)))
+    return g, f
+
+
+def nu_lumped_mass(ctx: Context, mesh: Mesh):
+    """L[m][l] = h_m (h_{l-1} + 2 h_l + h_{l+1}) / 4."""
+    L = ctx.empty((mesh.n_t, mesh.n_x))
+    ctx.check(ctx.lib.stbem_nu_lumped_mass(ctx.h, mesh.h, _ptr(L)))
+    return L
+
+
+def nu_solve(ctx: Context, V, f, D=None, L=None, tol: float = 1e-8, max_iter: int = 500, restart: int = 200,
+             work=None, out=None, raise_on_fail: bool = True):
+    """GMRES for the packed V (and preconditioner D, L) on a non-uniform grid."""
+    n_t, n_x = f.shape
+    opts = capi.SolveOpts(tol, max_iter, restart, int(D is not None))
+    info = capi.SolveInfo()
+    if out is None:
+        out = ctx.empty((n_t, n_x))
+    if work is None:
+        work = solve_workspace(ctx, n_t, n_x, restart)
+    code = ctx.lib.stbem_nu_solve(ctx.h, n_t, n_x, _ptr(V), _ptr(D), _ptr(L), _ptr(f), _ptr(out),
+                                  ctypes.byref(opts), ctypes.byref(info), _ptr(work), work.numel())
+    res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
+    if code != capi.STBEM_OK and raise_on_fail:
+        ctx.check(code)
+    return out, res
+
+
 class Domain:
     """Triangulation Omega_h of the domain bounded by ``mesh`` (nodes (M, 2),
     triangles (K, 3) counter-clockwise, boundary vertices among the nodes)."""

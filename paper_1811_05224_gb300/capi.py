@@ -40,6 +40,8 @@ EXPORTS = [
     "stbem_ragged_solve", "stbem_ragged_solve_mixed_workspace_bytes", "stbem_ragged_solve_mixed",
     "stbem_mixed_mass_inverse", "stbem_lag_shard", "stbem_assemble_lag_blocks", "stbem_apply_lags_workspace_bytes",
     "stbem_apply_lags", "stbem_solve_sharded_workspace_bytes", "stbem_solve_sharded",
+    "stbem_mesh_create_graded", "stbem_nu_op_bytes", "stbem_nu_assemble", "stbem_nu_apply", "stbem_nu_rhs",
+    "stbem_nu_lumped_mass", "stbem_nu_solve",
     "stbem_domain_create", "stbem_domain_destroy", "stbem_domain_info", "stbem_m0_bytes", "stbem_m0_assemble",
     "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data", "stbem_evaluate",
 ]
@@ -133,6 +135,13 @@ def load(path: str = LIB_PATH):
     L.stbem_debug_tc_stall.argtypes = [i, ctypes.c_longlong]
     L.stbem_pipe_peaks.argtypes = [vp, P(d)]
     L.stbem_lag_shard.argtypes = [i, i, i, i, i, P(i), P(i)]
+    L.stbem_mesh_create_graded.argtypes = [vp, P(d), i, P(d), i, d, P(vp)]
+    L.stbem_nu_op_bytes.argtypes = [vp, P(sz)]
+    L.stbem_nu_assemble.argtypes = [vp, vp, i, vp]
+    L.stbem_nu_apply.argtypes = [vp, i, i, vp, vp, vp]
+    L.stbem_nu_rhs.argtypes = [vp, vp, vp, d, d, vp, vp]
+    L.stbem_nu_lumped_mass.argtypes = [vp, vp, vp]
+    L.stbem_nu_solve.argtypes = [vp, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
     L.stbem_assemble_lag_blocks.argtypes = [vp, vp, i, i, i, i, vp]
     L.stbem_apply_lags_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
     L.stbem_apply_lags.argtypes = [vp, i, i, i, i, i, i, vp, i, vp, vp, i, vp, sz]

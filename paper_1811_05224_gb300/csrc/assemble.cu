@@ -34,6 +34,7 @@
 #include "pairs.cuh"
 #include "rule.cuh"
 #include "timeint.cuh"
+#include "nonuniform_time.cuh"
 
 namespace stbem {
 
@@ -49,6 +50,17 @@ template <> __device__ __forceinline__ float gwr<float>(int i) { return c_gwf[i]
 
 __device__ __forceinline__ double exp_neg(double x) { return exp_neg_fast(x); }
 __device__ __forceinline__ float exp_neg(float x) { return exp_neg_f(x); }
+// e^{-c sigma_g} at node g of a multi-lag table: FP64 from the pre-scaled
+// nodes and the table copy in shared memory (`fast`: c sigk_max is below the
+// table method's range, tested once per point), FP32 by the MUFU exponential
+template <typename T>
+__device__ __forceinline__ double ml_exp(double c, const T& tab, int g, bool fast) {
+  return fast ? exp_prod_fast(c, tab.sigk[g], tab.etab) : exp_neg_fast(c * tab.sig[g]);
+}
+template <typename T>
+__device__ __forceinline__ float ml_exp(float c, const T& tab, int g, bool) {
+  return exp_neg_f(c * tab.sig[g]);
+}
 __device__ __forceinline__ void e12(double z, double* a, double* b) { e1e2(z, a, b); }
 __device__ __forceinline__ void e12(float z, float* a, float* b) { e1e2_f(z, a, b); }
 
@@ -276,7 +288,8 @@ __device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (
   const int L = T.L;
   const R four_pi = (R)kFourPi;
   int lc = 0;
-  while (lc < L && c * T.inv_dht[lc] > (R)0.5 * (R)(T.d0 + lc)) ++lc;
+  while (lc < L && c > T.cthr[lc]) ++lc;
+  const bool fast = c * T.sigk_max < (R)kExpProdMax;
   if (lc > 0) {
     R F[NL + 2];
 #pragma unroll
@@ -299,14 +312,14 @@ __device__ __forceinline__ void ml_kernel(R c, R alpha, const MLNodes<R>& T, R (
       const int g0 = T.off[i], g1 = T.off[i + 1];
       if (i < L && i > lc) {
         for (int g = g0; g < g1; ++g) {
-          const R e = exp_neg(c * T.sig[g]);
+          const R e = ml_exp(c, T, g, fast);
           sl = fma(lw[g], e, sl);
           sr = fma(rw[g], e, sr);
         }
       } else if (i < L) {
-        for (int g = g0; g < g1; ++g) sl = fma(lw[g], exp_neg(c * T.sig[g]), sl);
+        for (int g = g0; g < g1; ++g) sl = fma(lw[g], ml_exp(c, T, g, fast), sl);
       } else {
-        for (int g = g0; g < g1; ++g) sr = fma(rw[g], exp_neg(c * T.sig[g]), sr);
+        for (int g = g0; g < g1; ++g) sr = fma(rw[g], ml_exp(c, T, g, fast), sr);
       }
 #pragma unroll
       for (int l = 0; l < NL; ++l)
@@ -322,7 +335,8 @@ __device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R
   const int L = T.L;
   const R four_pi = (R)kFourPi;
   int lc = 0;
-  while (lc < L && c * T.inv_dht[lc] > (R)0.5 * (R)(T.d0 + lc)) ++lc;
+  while (lc < L && c > T.cthr[lc]) ++lc;
+  const bool fast = c * T.sigk_max < (R)kExpProdMax;
   if (lc > 0) {
     R Fv[NL + 2], F1[NL + 2];
 #pragma unroll
@@ -347,7 +361,7 @@ __device__ __forceinline__ void ml_kernel_D(R c, R alpha, const MLNodes<R>& T, R
       const int g0 = T.off[i], g1 = T.off[i + 1];
       const bool wl = i < L, wr = i > lc;
       for (int g = g0; g < g1; ++g) {
-        const R e = exp_neg(c * T.sig[g]);
+        const R e = ml_exp(c, T, g, fast);
         if (wl) {
           slv = fma(T.lv[g], e, slv);
           sl1 = fma(e, fma(T.l3[g], c, -T.l2[g]), sl1);
@@ -698,10 +712,15 @@ __host__ __device__ __forceinline__ int tiles_per_lag(int N) {
   return nT * (nT + 1) / 2;
 }
 
-// Phase 3 of a tile: entries of one lag block from its pair moments.
+// Phase 3 of a tile: entries of one lag block from its pair moments.  With
+// `mirrored` (D on a diagonal tile) only the half-pairs (u, v) with u <= v
+// were integrated; (v, u) is the same pair with the roles exchanged, whose
+// moments are those of (u, v) with the two mixed ones (1 - xi) eta and
+// xi (1 - eta) swapped (both kernels depend on |x - y| only).
 template <int OP, typename T>
 __device__ __forceinline__ void tile_entries(const DevMesh& M, int rt, int ct, int r0, int c0,
-                                             const double* __restrict__ mom, size_t base, T* __restrict__ out) {
+                                             const double* __restrict__ mom, size_t base, T* __restrict__ out,
+                                             bool mirrored = false) {
   constexpr int NM = Tile<OP>::nm;
   const int N = M.N;
   const int tid = threadIdx.x;
@@ -741,8 +760,10 @@ __device__ __forceinline__ void tile_entries(const DevMesh& M, int rt, int ct, i
           const int v = 2 * to + ib;
           const int gb = M.dpiece[qb];
           const double nn = nax * M.hnx[gb] + nay * M.hny[gb];
-          const double* mm = mom + (size_t)(u * kDP + v) * NM;
-          const double I1 = a0 * (b0 * mm[1] + b1 * mm[2]) + a1 * (b0 * mm[3] + b1 * mm[4]);
+          const bool mir = mirrored && v < u;
+          const double* mm = mom + (size_t)(mir ? v * kDP + u : u * kDP + v) * NM;
+          const double m2 = mir ? mm[3] : mm[2], m3 = mir ? mm[2] : mm[3];
+          const double I1 = a0 * (b0 * mm[1] + b1 * m2) + a1 * (b0 * m3 + b1 * mm[4]);
           val += ca * cb * mm[0] + nn * I1;
         }
       }
@@ -836,7 +857,10 @@ __device__ void tile_body_ml(const DevMesh& M, int d0, int nl, int tile, T* __re
   build_ml_nodes<R>(*TN, d0, nl, M.ht, M.alpha);
   __syncthreads();
   const int n = space_order(d0);
+  // D on a diagonal tile: the half-pair block is symmetric, integrate u <= v only
+  const bool mirrored = OP == STBEM_OP_D && rt == ct;
   for (int p = threadIdx.x; p < P; p += kTileThreads) {
+    if (mirrored && p % kDP < p / kDP) continue;
     Piece A, B;
     int ia, ib, ring;
     double* m = mom + (size_t)p * NM;
@@ -849,7 +873,7 @@ __device__ void tile_body_ml(const DevMesh& M, int d0, int nl, int tile, T* __re
   }
   __syncthreads();
   for (int l = 0; l < nl; ++l)
-    tile_entries<OP, T>(M, rt, ct, r0, c0, mom + (size_t)l * P * NM, (size_t)(d0 + l) * N * N, out);
+    tile_entries<OP, T>(M, rt, ct, r0, c0, mom + (size_t)l * P * NM, (size_t)(d0 + l) * N * N, out, mirrored);
 }
 
 // Lags 0 and 1 of one tile together (FP64 compute): regular and near pairs
@@ -1036,6 +1060,302 @@ __global__ void __launch_bounds__(kTileThreads) k_ragged_tile(const RaggedProble
     else tile_body_ml<OP, R, T, LM>(pr.M, d0, nl, t, o, smem_raw);
     __syncthreads();
   }
+}
+
+// ---- non-uniform time grids -------------------------------------------------------
+// Section 1 allows any decomposition 0 = t_0 < .. < t_{n_t} = T of (0, T).  The
+// Galerkin block of test step m and trial step n <= m then depends on (m, n),
+// not on m - n alone: blocks are stored packed, p = m (m + 1) / 2 + n.  Time:
+// with s1 = t_{m+1} - t_n, s2 = t_{m+1} - t_{n+1}, s3 = t_m - t_n,
+// s4 = t_m - t_{n+1} the integral over tau_m x tau_n is
+// F(s1) - F(s2) - F(s3) + F(s4) (F = 0 for s <= 0); branches as the host-checked
+// nonuniform_time.cuh: d = m - n = 0 closed; d = 1 the series form for
+// z = c / s_c < 1 (s_c = (s1 + s4) / 2), else closed; d >= 2 closed when
+// z > d / 2, else the Peano form over the trapezoid of the overlap length,
+// whose nodes and weights (up to three linear pieces, peano_order nodes each)
+// are tabulated per block as the uniform lag tables are.  Space: the uniform
+// rule with the lag d (classes, orders, singular rules at d <= 1).
+constexpr int kMaxNodesNU = 48;
+struct BlockTime {
+  int d, n;
+  double s[4], inv_sc;
+  double sig[kMaxNodesNU], wv[kMaxNodesNU], wk[kMaxNodesNU], w3[kMaxNodesNU], w2[kMaxNodesNU];
+};
+
+__device__ __forceinline__ void nu_block_index(long long p, int* m, int* n) {
+  int mm = (int)floor((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while ((long long)mm * (mm + 1) / 2 > p) --mm;
+  while ((long long)(mm + 1) * (mm + 2) / 2 <= p) ++mm;
+  *m = mm;
+  *n = (int)(p - (long long)mm * (mm + 1) / 2);
+}
+
+// thread 0 builds the block's table (a few dozen nodes)
+__device__ void build_block_time(BlockTime& B, const double* __restrict__ tn, int m, int n, double alpha) {
+  if (threadIdx.x != 0) return;
+  B.d = m - n;
+  B.s[0] = tn[m + 1] - tn[n];
+  B.s[1] = tn[m + 1] - tn[n + 1];
+  B.s[2] = tn[m] - tn[n];
+  B.s[3] = tn[m] - tn[n + 1];
+  B.inv_sc = 1.0 / (0.5 * (B.s[0] + B.s[3]));
+  int g = 0;
+  if (B.d >= 2) {
+    const double pt[4] = {B.s[3], fmin(B.s[1], B.s[2]), fmax(B.s[1], B.s[2]), B.s[0]};
+    const double plateau = pt[1] - pt[0];
+    for (int piece = 0; piece < 3; ++piece) {
+      const double lo = pt[piece], L = pt[piece + 1] - pt[piece];
+      if (!(L > 0.0)) continue;
+      const int q = peano_order((int)rint(lo / L)), o = gauss_offset(q);
+      for (int k = 0; k < q && g < kMaxNodesNU; ++k, ++g) {
+        const double x = c_tab.gx[o + k];
+        const double wt = piece == 0 ? x * L : (piece == 1 ? plateau : (1.0 - x) * L);
+        const double sv = lo + x * L, sig = 1.0 / sv;
+        const double W = L * c_tab.gw[o + k] * wt;
+        B.sig[g] = sig;
+        B.wv[g] = W * sig / kFourPi;
+        B.wk[g] = W * alpha * sig * sig / (2.0 * kFourPi);
+        B.w3[g] = W * alpha * sig * sig * sig / kFourPi;
+        B.w2[g] = W * alpha * sig * sig / kFourPi;
+      }
+    }
+  }
+  B.n = g;
+}
+
+template <int K>
+__device__ __forceinline__ double nu_closed(double c, const BlockTime& B, double alpha) {
+  const double a = Fk<K>(c, B.s[0], alpha) - Fk<K>(c, B.s[1], alpha);
+  if (B.d == 1) return a - Fk<K>(c, B.s[2], alpha);
+  return (a - Fk<K>(c, B.s[2], alpha)) + Fk<K>(c, B.s[3], alpha);
+}
+
+// kernel K (kV, kKq = K / q, k1) of the block at c = alpha r^2 / 4
+template <int K>
+__device__ double nu_kernel(double c, const BlockTime& B, double alpha) {
+  if (B.d == 0) return Fk<K>(c, B.s[0], alpha);
+  const double z = c * B.inv_sc;
+  if (B.d == 1) return z < 1.0 ? nu_lag1_series<K>(c, B.s[0], B.s[1], B.s[2], alpha) : nu_closed<K>(c, B, alpha);
+  if (z > 0.5 * (double)B.d) return nu_closed<K>(c, B, alpha);
+  double acc = 0.0;
+  for (int g = 0; g < B.n; ++g) {
+    const double e = exp_neg_fast(c * B.sig[g]);
+    if (K == kV) acc = fma(B.wv[g], e, acc);
+    else if (K == kKq) acc = fma(B.wk[g], e, acc);
+    else acc = fma(e, fma(B.w3[g], c, -B.w2[g]), acc);
+  }
+  return acc;
+}
+
+// D's two kernels (kV and k1) of the block: one exponential per Peano node
+__device__ __forceinline__ void nu_kernel_D(double c, const BlockTime& B, double alpha, double* kv, double* k1v) {
+  if (B.d >= 2 && !(c * B.inv_sc > 0.5 * (double)B.d)) {
+    double av = 0.0, a1 = 0.0;
+    for (int g = 0; g < B.n; ++g) {
+      const double e = exp_neg_fast(c * B.sig[g]);
+      av = fma(B.wv[g], e, av);
+      a1 = fma(e, fma(B.w3[g], c, -B.w2[g]), a1);
+    }
+    *kv = av;
+    *k1v = a1;
+    return;
+  }
+  *kv = nu_kernel<kV>(c, B, alpha);
+  *k1v = nu_kernel<k1>(c, B, alpha);
+}
+
+// moments of one regular / near pair (tensor Gauss rule of order n) of the block
+template <int OP>
+__device__ void nu_tensor_moments(const Piece& A, const Piece& Bp, int n, const BlockTime& B, double alpha,
+                                  double* mom) {
+  const int o = gauss_offset(n);
+  const double eax = A.x1 - A.x0, eay = A.y1 - A.y0;
+  const double ebx = Bp.x1 - Bp.x0, eby = Bp.y1 - Bp.y0;
+  const double abx = A.x0 - Bp.x0, aby = A.y0 - Bp.y0;
+  const double qab = (A.x0 - Bp.x0) * Bp.nx + (A.y0 - Bp.y0) * Bp.ny;
+  const double qea = (A.x1 - A.x0) * Bp.nx + (A.y1 - A.y0) * Bp.ny;
+  const double qa = 0.25 * alpha;
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+  for (int a = 0; a < n; ++a) {
+    const double xi = c_tab.gx[o + a], wa = c_tab.gw[o + a];
+    for (int b = 0; b < n; ++b) {
+      const double eta = c_tab.gx[o + b];
+      const double w = wa * c_tab.gw[o + b];
+      const double dx = (abx + xi * eax) - eta * ebx;
+      const double dy = (aby + xi * eay) - eta * eby;
+      const double c = qa * (dx * dx + dy * dy);
+      if constexpr (OP == STBEM_OP_V) {
+        s0 += w * nu_kernel<kV>(c, B, alpha);
+      } else if constexpr (OP == STBEM_OP_K) {
+        const double wk = w * ((qab + xi * qea) * nu_kernel<kKq>(c, B, alpha));
+        s0 += wk * (1.0 - eta);
+        s1 += wk * eta;
+      } else {
+        double kv, k1v;
+        nu_kernel_D(c, B, alpha, &kv, &k1v);
+        s0 += w * kv;
+        const double wk = w * k1v;
+        s1 += wk * (1.0 - xi) * (1.0 - eta);
+        s2 += wk * (1.0 - xi) * eta;
+        s3 += wk * xi * (1.0 - eta);
+        s4 += wk * xi * eta;
+      }
+    }
+  }
+  const double L = A.len * Bp.len;
+  const double sv[5] = {s0, s1, s2, s3, s4};
+  for (int q = 0; q < NMom<OP>::n; ++q) mom[q] = sv[q] * L;
+}
+
+// moments of one identical / vertex-sharing pair (d <= 1), the whole CTA
+// striding over the rule's points, fixed-order tree reduction
+template <int OP>
+__device__ void nu_singular_moments(const Piece& A, const Piece& Bp, int cls, const BlockTime& B, double alpha,
+                                    double* mom, double (*red)[kTileThreads]) {
+  constexpr int NM = NMom<OP>::n;
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int np = singular_points(cls);
+  for (int p = threadIdx.x; p < np; p += kTileThreads) {
+    double xi, eta, w, dx, dy;
+    singular_point(cls, p, A, Bp, &xi, &eta, &w, &dx, &dy);
+    const double c = 0.25 * alpha * (dx * dx + dy * dy);
+    if constexpr (OP == STBEM_OP_V) {
+      s[0] += w * nu_kernel<kV>(c, B, alpha);
+    } else if constexpr (OP == STBEM_OP_K) {
+      const double wk = w * ((dx * Bp.nx + dy * Bp.ny) * nu_kernel<kKq>(c, B, alpha));
+      s[0] += wk * (1.0 - eta);
+      s[1] += wk * eta;
+    } else {
+      s[0] += w * nu_kernel<kV>(c, B, alpha);
+      const double wk = w * nu_kernel<k1>(c, B, alpha);
+      s[1] += wk * (1.0 - xi) * (1.0 - eta);
+      s[2] += wk * (1.0 - xi) * eta;
+      s[3] += wk * xi * (1.0 - eta);
+      s[4] += wk * xi * eta;
+    }
+  }
+  for (int q = 0; q < NM; ++q) red[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int h = kTileThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int q = 0; q < NM; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < NM) mom[threadIdx.x] = red[threadIdx.x][0] * (A.len * Bp.len);
+  __syncthreads();
+}
+
+template <int OP>
+constexpr size_t nu_tile_smem_bytes() {
+  return (((size_t)Tile<OP>::pairs * Tile<OP>::nm * sizeof(double) + 15) / 16) * 16 + sizeof(BlockTime);
+}
+
+// One tile of one block (m, n) = packed index p0 + blockIdx.y.
+template <int OP>
+__global__ void __launch_bounds__(kTileThreads) k_nu_tile(DevMesh M, const double* __restrict__ tn, long long p0,
+                                                          double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[5][kTileThreads];
+  __shared__ int sing[Tile<OP>::pairs];
+  __shared__ int n_sing;
+  constexpr int P = Tile<OP>::pairs, NM = Tile<OP>::nm;
+  double* mom = reinterpret_cast<double*>(smem_raw);
+  BlockTime* BT = reinterpret_cast<BlockTime*>(smem_raw + ((P * NM * sizeof(double) + 15) / 16) * 16);
+  const long long p = p0 + blockIdx.y;
+  int m, n;
+  nu_block_index(p, &m, &n);
+  const int d = m - n;
+  const int N = M.N;
+  int rt, ct;
+  if (OP == STBEM_OP_K) {
+    const int nP = (N + kKP - 1) / kKP;
+    rt = blockIdx.x / nP;
+    ct = blockIdx.x % nP;
+  } else {
+    upper_tile(blockIdx.x, (N + kT - 1) / kT, &rt, &ct);
+  }
+  const int r0 = rt * kT, c0 = ct * (OP == STBEM_OP_K ? kKP : kT);
+  build_block_time(*BT, tn, m, n, M.alpha);
+  if (threadIdx.x == 0) n_sing = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < P; q += kTileThreads) {
+    Piece A, B;
+    int ia, ib, ring;
+    double* mq = mom + (size_t)q * NM;
+    if (!tile_pair<OP>(M, r0, c0, q, &A, &B, &ia, &ib, &ring)) {
+      for (int k = 0; k < NM; ++k) mq[k] = 0.0;
+      continue;
+    }
+    int order = space_order(d);
+    if (d <= 1) {
+      const int cls = pair_class(ring, ia, ib, A, B);
+      if (cls == kIdentical || cls == kAdjNext || cls == kAdjPrev) {
+        sing[atomicAdd(&n_sing, 1)] = q;       // the whole CTA integrates it below
+        continue;
+      }
+      order = cls == kRegular ? kRegular01 : kNear01;
+    }
+    nu_tensor_moments<OP>(A, B, order, *BT, M.alpha, mq);
+  }
+  __syncthreads();
+  const int ns = n_sing;
+  for (int k = 0; k < ns; ++k) {
+    const int q = sing[k];
+    Piece A, B;
+    int ia, ib, ring;
+    tile_pair<OP>(M, r0, c0, q, &A, &B, &ia, &ib, &ring);
+    nu_singular_moments<OP>(A, B, pair_class(ring, ia, ib, A, B), *BT, M.alpha, mom + (size_t)q * NM, red);
+  }
+  __syncthreads();
+  tile_entries<OP, double>(M, rt, ct, r0, c0, mom, (size_t)p * N * N, out);
+}
+
+// y[m][i] = sum_{n <= m} sum_j A[p(m, n)][i][j] x[n][j]: one warp per (m, i)
+// row, rows of the latest steps (the longest) first; coalesced row reads,
+// lane partial sums reduced by shuffles in a fixed order.
+__global__ void __launch_bounds__(256) k_nu_apply(int nt, int nx, const double* __restrict__ A,
+                                                  const double* __restrict__ x, double* __restrict__ y) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long long)nt * nx) return;
+  const int m = nt - 1 - (int)(warp / nx), i = (int)(warp % nx);
+  double acc = 0.0;
+  const size_t base_m = (size_t)m * (m + 1) / 2;
+  for (int n = 0; n <= m; ++n) {
+    const double* row = A + ((base_m + n) * nx + i) * (size_t)nx;
+    const double* xn = x + (size_t)n * nx;
+    for (int j = lane; j < nx; j += 32) acc = fma(row[j], xn[j], acc);
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) y[(size_t)m * nx + i] = acc;
+}
+
+cudaError_t nu_assemble_launch(const DevMesh& M, const double* tn, int op, double* out, cudaStream_t s) {
+  const int N = M.N, nt = M.n_t;
+  const long long blocks = (long long)nt * (nt + 1) / 2;
+  auto run = [&](auto kern, size_t smem, int tiles) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    for (long long p0 = 0; p0 < blocks; p0 += 65535) {
+      const unsigned nb = (unsigned)std::min<long long>(65535, blocks - p0);
+      kern<<<dim3(tiles, nb), kTileThreads, smem, s>>>(M, tn, p0, out);
+      count_launches(1);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (op == STBEM_OP_V) return run(k_nu_tile<STBEM_OP_V>, nu_tile_smem_bytes<STBEM_OP_V>(), tiles_per_lag<STBEM_OP_V>(N));
+  if (op == STBEM_OP_K) return run(k_nu_tile<STBEM_OP_K>, nu_tile_smem_bytes<STBEM_OP_K>(), tiles_per_lag<STBEM_OP_K>(N));
+  return run(k_nu_tile<STBEM_OP_D>, nu_tile_smem_bytes<STBEM_OP_D>(), tiles_per_lag<STBEM_OP_D>(N));
+}
+
+cudaError_t nu_apply_launch(int nt, int nx, const double* A, const double* x, double* y, cudaStream_t s) {
+  const long long threads = (long long)nt * nx * 32;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  k_nu_apply<<<blocks, 256, 0, s>>>(nt, nx, A, x, y);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // ---- host side ----------------------------------------------------------------

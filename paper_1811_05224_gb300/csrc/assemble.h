@@ -55,5 +55,10 @@ cudaError_t upload_rule_tables(const RuleTables& t, cudaStream_t s);
 // Lags [lag_begin, lag_end) of op into out (the full n_t x N x N array).
 cudaError_t assemble_launch(const DevMesh& M, int op, int prec, int lag_begin, int lag_end, void* out,
                             cudaStream_t s);
+// Non-uniform time grid (tn: n_t + 1 device time nodes): every block (m, n),
+// n <= m, of op into out, packed p = m (m + 1) / 2 + n, N x N each (FP64).
+cudaError_t nu_assemble_launch(const DevMesh& M, const double* tn, int op, double* out, cudaStream_t s);
+// y[m] = sum_{n <= m} A[p(m, n)] x[n] for packed blocks (one right-hand side).
+cudaError_t nu_apply_launch(int nt, int nx, const double* A, const double* x, double* y, cudaStream_t s);
 
 }  // namespace stbem

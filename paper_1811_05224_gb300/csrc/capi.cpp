@@ -24,6 +24,7 @@
 
 using stbem_internal::cuda_fail;
 using stbem_internal::fail;
+using stbem_internal::reject_graded;
 
 namespace {
 
@@ -144,6 +145,11 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
   if (e == cudaSuccess) e = cudaMalloc(&m->dbuf, host.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&m->ibuf, dp.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&m->sbuf, (size_t)2 * 3 * (2 * N) * 5 * sizeof(double));
+  std::vector<double> tn(n_t + 1);
+  for (int k = 0; k <= n_t; ++k) tn[k] = k == n_t ? T : (double)k * m->ht;
+  if (e == cudaSuccess) e = cudaMalloc(&m->tbuf, tn.size() * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->tbuf, tn.data(), tn.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->dbuf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
@@ -153,6 +159,7 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
     if (m->dbuf) cudaFree(m->dbuf);
     if (m->ibuf) cudaFree(m->ibuf);
     if (m->sbuf) cudaFree(m->sbuf);
+    if (m->tbuf) cudaFree(m->tbuf);
     delete m;
     return cuda_fail(ctx, e, "mesh upload");
   }
@@ -180,8 +187,36 @@ void stbem_mesh_destroy(stbem_mesh* m) {
   if (m->dbuf) cudaFree(m->dbuf);
   if (m->ibuf) cudaFree(m->ibuf);
   if (m->sbuf) cudaFree(m->sbuf);
+  if (m->tbuf) cudaFree(m->tbuf);
   cudaSetDevice(prev);
   delete m;
+}
+
+int stbem_mesh_create_graded(stbem_ctx* ctx, const double* xy, int n_x, const double* t, int n_t, double alpha,
+                             stbem_mesh** out) {
+  if (!ctx || !out) return STBEM_ERR_ARG;
+  *out = nullptr;
+  if (!t) return fail(ctx, STBEM_ERR_ARG, "mesh_graded: NULL time nodes");
+  if (n_t < 1) return fail(ctx, STBEM_ERR_ARG, "mesh_graded: need n_t >= 1 (got %d)", n_t);
+  if (t[0] != 0.0) return fail(ctx, STBEM_ERR_ARG, "mesh_graded: t_0 must be 0");
+  for (int k = 0; k < n_t; ++k)
+    if (!(t[k + 1] > t[k]) || !std::isfinite(t[k + 1]))
+      return fail(ctx, STBEM_ERR_ARG, "mesh_graded: time nodes must increase (t_%d = %g, t_%d = %g)", k, t[k],
+                  k + 1, t[k + 1]);
+  stbem_mesh* m = nullptr;
+  const int rc = stbem_mesh_create(ctx, xy, n_x, t[n_t], n_t, alpha, &m);
+  if (rc != STBEM_OK) return rc;
+  const cudaError_t e = cudaMemcpyAsync(m->tbuf, t, (size_t)(n_t + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                                        ctx->stream);
+  const cudaError_t e2 = e == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e;
+  if (e2 != cudaSuccess) {
+    stbem_mesh_destroy(m);
+    return cuda_fail(ctx, e2, "mesh_graded: time nodes");
+  }
+  m->graded = true;
+  m->tnodes.assign(t, t + n_t + 1);
+  *out = m;
+  return STBEM_OK;
 }
 
 int stbem_op_bytes(const stbem_mesh* m, int op, int prec, size_t* bytes) {
@@ -192,6 +227,7 @@ int stbem_op_bytes(const stbem_mesh* m, int op, int prec, size_t* bytes) {
 
 int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, void* out) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "assemble")) return rg;
   if (!m || !out) return fail(ctx, STBEM_ERR_ARG, "assemble: NULL mesh or output");
   if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown operator %d", op);
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown precision %d", prec);
@@ -203,6 +239,7 @@ int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, void* 
 int stbem_assemble_lags(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, int lag_begin, int lag_end,
                         void* out) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "assemble_lags")) return rg;
   if (!m || !out) return fail(ctx, STBEM_ERR_ARG, "assemble_lags: NULL mesh or output");
   if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble_lags: unknown operator %d", op);
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "assemble_lags: unknown precision %d", prec);
@@ -377,6 +414,7 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* A_hi, const vo
 
 int stbem_rhs_g_batched(stbem_ctx* ctx, const stbem_mesh* m, int n_src, const double* ys, double* G) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "rhs_g_batched")) return rg;
   if (!m || !ys || !G || n_src < 1) return fail(ctx, STBEM_ERR_ARG, "rhs_g_batched: bad arguments");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "rhs_g_batched: set device");
   const size_t N = (size_t)m->n_t * m->N;
@@ -387,6 +425,7 @@ int stbem_rhs_g_batched(stbem_ctx* ctx, const stbem_mesh* m, int n_src, const do
 
 int stbem_half_mass_add(stbem_ctx* ctx, const stbem_mesh* m, int n_rhs, const double* G, double* F) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "half_mass_add")) return rg;
   if (!m || !G || !F || n_rhs < 1) return fail(ctx, STBEM_ERR_ARG, "half_mass_add: bad arguments");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "half_mass_add: set device");
   CUDA_TRY(ctx, stbem::half_mass_add_launch(m->dev, G, F, ctx->stream, n_rhs), "half_mass_add");
@@ -635,6 +674,7 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
 int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, double* g,
               double* f, void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "rhs")) return rg;
   if (!m || !K || !g || !f || !work) return fail(ctx, STBEM_ERR_ARG, "rhs: NULL pointer");
   const size_t need = stbem::apply_workspace_bytes(m->n_t, m->N, 1);
   if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "rhs: workspace %zu < %zu bytes", work_bytes, need);
@@ -647,6 +687,7 @@ int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, 
 
 int stbem_lumped_mass(stbem_ctx* ctx, const stbem_mesh* m, double* L) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "lumped_mass")) return rg;
   if (!m || !L) return fail(ctx, STBEM_ERR_ARG, "lumped: NULL pointer");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "lumped: set device");
   CUDA_TRY(ctx, stbem::lumped_mass_launch(m->dev, L, ctx->stream), "lumped");
@@ -708,12 +749,16 @@ struct GmresOp {
   const int* ranges = nullptr;
   stbem_allreduce_fn reduce = nullptr;
   void* reduce_user = nullptr;
+  // non-uniform time grid: V and D are packed blocks (forward products only)
+  // and L holds the lumped mass of every step (n_t x n_x)
+  bool packed = false;
 };
 
 // y = A x with A one of op's operators (full, or this rank's lag ranges then
 // the all-reduce).  A failing callback sets *reduce_rc and returns an error.
 cudaError_t op_product(const GmresOp& op, const void* A, const double* x, double* y, void* work, cudaStream_t s,
                        int* reduce_rc) {
+  if (op.packed) return stbem::nu_apply_launch(op.nt, op.nx, static_cast<const double*>(A), x, y, s);
   if (op.n_ranges < 0) return stbem::apply_launch(op.prec, op.transpose, op.nt, op.nx, A, 1, x, y, work, s);
   const size_t N = (size_t)op.nt * op.nx;
   const size_t elt = op.prec == STBEM_F64 ? sizeof(double) : sizeof(float);
@@ -763,8 +808,10 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
   // y = M^{-1} D M^{-T} x per time step (consistent mixed mass), or y = x
   auto applyP = [&](const double* x, double* y) -> cudaError_t {
     if (!prec) return cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    // the lumped mass per step (packed) is divided elementwise over all n_t n_x
+    const int dr = op.packed ? 1 : nt, dc = op.packed ? nt * nx : nx;
     cudaError_t e = op.mass == 2 ? stbem::blockmul_launch(nt, nx, op.L, true, x, W.u, s)
-                                 : stbem::diag_div_launch(x, op.L, W.u, nt, nx, s);
+                                 : stbem::diag_div_launch(x, op.L, W.u, dr, dc, s);
     if (e != cudaSuccess) return e;
     if (op.mass == 2) {
       e = op_product(op, op.D, W.u, W.v, W.apply, s, &reduce_rc);
@@ -773,7 +820,7 @@ int gmres_core(stbem_ctx* ctx, const GmresOp& op, const double* f, double* w, do
     }
     e = op_product(op, op.D, W.u, y, W.apply, s, &reduce_rc);
     if (e != cudaSuccess) return e;
-    return stbem::diag_div_launch(y, op.L, y, nt, nx, s);
+    return stbem::diag_div_launch(y, op.L, y, dr, dc, s);
   };
   auto norm = [&](const double* x, double* out) -> cudaError_t {
     cudaError_t e = stbem::dots_launch(x, 1, x, N, W.h, s);
@@ -925,6 +972,85 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V
   return solve_impl(ctx, true, nt, nx, vprec, V, D, L, b, lam, opts, info, work, work_bytes);
 }
 
+// ------------------------------------------------- non-uniform time grids ------
+
+int stbem_nu_op_bytes(const stbem_mesh* m, size_t* bytes) {
+  if (!m || !bytes) return STBEM_ERR_ARG;
+  *bytes = (size_t)m->n_t * (m->n_t + 1) / 2 * m->N * m->N * sizeof(double);
+  return STBEM_OK;
+}
+
+int stbem_nu_assemble(stbem_ctx* ctx, const stbem_mesh* m, int op, double* out) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !out) return fail(ctx, STBEM_ERR_ARG, "nu_assemble: NULL mesh or output");
+  if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "nu_assemble: unknown operator %d", op);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "nu_assemble: set device");
+  CUDA_TRY(ctx, stbem::nu_assemble_launch(m->dev, m->tbuf, op, out, ctx->stream), "nu_assemble");
+  return STBEM_OK;
+}
+
+int stbem_nu_apply(stbem_ctx* ctx, int n_t, int n_x, const double* A, const double* x, double* y) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A || !x || !y) return fail(ctx, STBEM_ERR_ARG, "nu_apply: NULL pointer");
+  if (n_t < 1 || n_x < 1) return fail(ctx, STBEM_ERR_ARG, "nu_apply: bad sizes");
+  if (x == y) return fail(ctx, STBEM_ERR_ARG, "nu_apply: x and y overlap");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "nu_apply: set device");
+  CUDA_TRY(ctx, stbem::nu_apply_launch(n_t, n_x, A, x, y, ctx->stream), "nu_apply");
+  return STBEM_OK;
+}
+
+int stbem_nu_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, double* g,
+                 double* f) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !K || !g || !f) return fail(ctx, STBEM_ERR_ARG, "nu_rhs: NULL pointer");
+  if (!std::isfinite(ysx) || !std::isfinite(ysy)) return fail(ctx, STBEM_ERR_ARG, "nu_rhs: non-finite source");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "nu_rhs: set device");
+  CUDA_TRY(ctx, stbem::nu_rhs_launch(m->dev, m->tbuf, ysx, ysy, g, ctx->stream), "nu_rhs: g");
+  CUDA_TRY(ctx, stbem::nu_apply_launch(m->n_t, m->N, K, g, f, ctx->stream), "nu_rhs: K g");
+  CUDA_TRY(ctx, stbem::nu_half_mass_add_launch(m->dev, m->tbuf, g, f, ctx->stream), "nu_rhs: mass");
+  return STBEM_OK;
+}
+
+int stbem_nu_lumped_mass(stbem_ctx* ctx, const stbem_mesh* m, double* L) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!m || !L) return fail(ctx, STBEM_ERR_ARG, "nu_lumped_mass: NULL pointer");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "nu_lumped_mass: set device");
+  CUDA_TRY(ctx, stbem::nu_lumped_launch(m->dev, m->tbuf, L, ctx->stream), "nu_lumped_mass");
+  return STBEM_OK;
+}
+
+int stbem_nu_solve(stbem_ctx* ctx, int nt, int nx, const double* V, const double* D, const double* L,
+                   const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info, void* work,
+                   size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!V || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "nu_solve: NULL pointer");
+  if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "nu_solve: bad sizes");
+  const int restart = opts->restart, maxit = opts->max_iter;
+  if (restart < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "nu_solve: bad options");
+  if (opts->precondition != 0 && opts->precondition != 1)
+    return fail(ctx, STBEM_ERR_ARG, "nu_solve: precondition must be 0 or 1 (lumped mass per step)");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!D || !L)) return fail(ctx, STBEM_ERR_ARG, "nu_solve: preconditioner needs D and L");
+  SolveWork W;
+  if (!carve(work, work_bytes, nt, nx, restart, &W))
+    return fail(ctx, STBEM_ERR_NOMEM, "nu_solve: workspace %zu < %zu bytes", work_bytes, solve_bytes(nt, nx, restart));
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "nu_solve: set device");
+  GmresOp op{nt, nx, STBEM_F64, V, prec ? D : nullptr, L};
+  op.packed = true;
+  int iters = 0;
+  double relres = 0.0;
+  const int status = gmres_core(ctx, op, f, w, opts->tol, maxit, restart, W, &iters, &relres);
+  info->iterations = iters;
+  info->rel_residual = relres;
+  info->status = status;
+  if (status == STBEM_ERR_NAN || status == STBEM_ERR_NOCONV || status == STBEM_ERR_BREAKDOWN)
+    return fail(ctx, status, "nu_solve: %s after %d iterations (relres %.3e)",
+                status == STBEM_ERR_NAN ? "NaN"
+                : status == STBEM_ERR_NOCONV ? "no convergence" : "breakdown (singular operator)",
+                iters, relres);
+  return status;
+}
+
 // ---------------------------------------------------------- lag sharding ------
 
 int stbem_lag_shard(int n_t, int n_ranks, int rank, int chunk, int max_ranges, int* host_ranges, int* n_ranges) {
@@ -941,6 +1067,7 @@ int stbem_lag_shard(int n_t, int n_ranks, int rank, int chunk, int max_ranges, i
 int stbem_assemble_lag_blocks(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, int lag_begin, int lag_end,
                               void* dev_blocks) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "assemble_lag_blocks")) return rg;
   if (!m || !dev_blocks) return fail(ctx, STBEM_ERR_ARG, "assemble_lag_blocks: NULL mesh or output");
   if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble_lag_blocks: unknown operator %d", op);
   if (prec != STBEM_F64 && prec != STBEM_F32)
@@ -1051,6 +1178,7 @@ int stbem_solve_sharded(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V
 
 int stbem_mixed_mass_inverse(stbem_ctx* ctx, const stbem_mesh* m, double* dev_Minv) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "mixed_mass_inverse")) return rg;
   if (!m || !dev_Minv) return fail(ctx, STBEM_ERR_ARG, "mixed_mass_inverse: NULL pointer");
   // the cyclic tridiagonal mixed mass of one step, inverted on the host
   // (Gauss-Jordan with partial pivoting; M is not symmetric; N^3 host work,
@@ -1073,6 +1201,7 @@ int stbem_grad_workspace_bytes(int n_t, int n_x, size_t* bytes) {
 int stbem_grad(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, const double* g,
                const double* w, const double* lam, double* dxy, double* dalpha, void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "grad")) return rg;
   if (!m || !K || !g || !w || !lam || !dxy || !dalpha || !work) return fail(ctx, STBEM_ERR_ARG, "grad: NULL pointer");
   if (!std::isfinite(ysx) || !std::isfinite(ysy)) return fail(ctx, STBEM_ERR_ARG, "grad: non-finite source point");
   const size_t need = stbem::grad_workspace_bytes(m->n_t, m->N);

@@ -25,6 +25,9 @@ struct stbem_mesh {
   double* dbuf = nullptr;    // device geometry
   int* ibuf = nullptr;
   double* sbuf = nullptr;    // lag-0/1 singular-pair moments (2 lags x 3 x 2N x 5)
+  double* tbuf = nullptr;    // the n_t + 1 time nodes (uniform k T / n_t unless graded)
+  std::vector<double> tnodes;  // host copy of a graded mesh's nodes
+  bool graded = false;       // non-uniform time grid: only the stbem_nu_* calls apply
   stbem::DevMesh dev{};
 };
 
@@ -44,6 +47,14 @@ inline int fail(stbem_ctx* ctx, int code, const char* fmt, ...) {
 
 inline int cuda_fail(stbem_ctx* ctx, cudaError_t e, const char* where) {
   return fail(ctx, STBEM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// The uniform-grid calls (Toeplitz lag blocks) reject a mesh with a
+// non-uniform time grid; its operators are the packed blocks of stbem_nu_*.
+inline int reject_graded(stbem_ctx* ctx, const stbem_mesh* m, const char* name) {
+  if (m && m->graded)
+    return fail(ctx, STBEM_ERR_ARG, "%s: the mesh has a non-uniform time grid (use the stbem_nu_* calls)", name);
+  return STBEM_OK;
 }
 
 }  // namespace stbem_internal

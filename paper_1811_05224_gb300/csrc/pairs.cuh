@@ -173,9 +173,13 @@ struct MLNodes {
   int off[kMaxLagsML + 2];            // interval i = 0..L starts at off[i]; off[L + 1] = total
   R inv_dht[kMaxLagsML];              // 1 / (d ht) of each lag (closed / Peano switch)
   R s[kMaxLagsML + 2], inv_s[kMaxLagsML + 2];   // (d0 - 1 + j) ht, j = 0..L+1
-  R sig[kMaxNodesML];
+  R cthr[kMaxLagsML];                 // lag d0 + l uses the closed form where c > d^2 ht / 2
+  R sig[kMaxNodesML];                 // 1 / s at the nodes (FP32 e^{-c sig}; FP64 fallback)
+  R sigk[kMaxNodesML];                // (2048 / ln2) / s: FP64 e^{-c sig} = exp_prod_fast(c, sigk)
+  R sigk_max;                         // the largest sigk (first node): c sigk_max < kExpProdMax
   R lv[kMaxNodesML], rv[kMaxNodesML], lk[kMaxNodesML], rk[kMaxNodesML];
   R l3[kMaxNodesML], r3[kMaxNodesML], l2[kMaxNodesML], r2[kMaxNodesML];
+  double etab[sizeof(R) == 8 ? 2048 : 1];  // FP64: copy of the 2^{-j/2048} table (divergent reads)
 };
 
 template <typename R>
@@ -195,6 +199,7 @@ static __device__ void build_ml_nodes(MLNodes<R>& T, int d0, int L, double ht, d
     const double fv = base * sig / kFourPi, fk = base * alpha * sig * sig / (2.0 * kFourPi);
     const double f3 = base * alpha * sig * sig * sig / kFourPi, f2 = base * alpha * sig * sig / kFourPi;
     T.sig[g] = (R)sig;
+    T.sigk[g] = (R)(kInvLn2x2048 / sv);
     T.lv[g] = (R)(fv * t);
     T.rv[g] = (R)(fv * (1.0 - t));
     T.lk[g] = (R)(fk * t);
@@ -204,9 +209,17 @@ static __device__ void build_ml_nodes(MLNodes<R>& T, int d0, int L, double ht, d
     T.l2[g] = (R)(f2 * t);
     T.r2[g] = (R)(f2 * (1.0 - t));
   }
+  if (sizeof(R) == 8)
+    for (int j = threadIdx.x; j < 2048; j += blockDim.x) T.etab[j] = kExp2Tab2048[j];
   if (threadIdx.x == 0) {
     T.d0 = d0;
     T.L = L;
+    // the nodes' s increase with g, so node 0 has the largest sigma
+    T.sigk_max = (R)(kInvLn2x2048 / (((double)(d0 - 1) + c_tab.gx[gauss_offset(peano_order(d0 - 1))]) * ht));
+    for (int l = 0; l < L; ++l) {
+      const double d = (double)(d0 + l);
+      T.cthr[l] = (R)(0.5 * d * (d * ht));
+    }
     for (int i = 0; i <= L + 1; ++i) T.off[i] = off[i];
     for (int l = 0; l < L; ++l) T.inv_dht[l] = (R)(1.0 / ((double)(d0 + l) * ht));
     for (int j = 0; j <= L + 1; ++j) {

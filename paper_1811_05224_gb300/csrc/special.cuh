@@ -71,6 +71,50 @@ STB_HD double exp_neg_fast(double x) {
 #endif
 }
 
+// e^{-c k} for the hot loops, k = sigma 2048/ln2 pre-scaled in a node table
+// (the same table method with 2048 entries): t = fma(c, k, 1.5 2^52) rounds the
+// exact product c k to the nearest integer n, the low word of t (no
+// conversion instruction); r = fma(c, k, -n) is the exact remainder, |r| <= 1/2,
+// rounded once; e^{-c k ln2/2048} = 2^{-(n >> 11)} 2^{-(n & 2047)/2048}
+// e^{-r ln2/2048}, the last factor by its cubic Taylor polynomial (remainder
+// below 4e-17).  The product c k is never rounded on its own, so only k's
+// rounding (|x| eps, x = c sigma) enters besides the final 2 ulp; checked on
+// the host.  Requires 0 <= c k < kExpProdMax (the caller tests it); tab: the
+// 2048 values 2^{-j/2048} (kExp2Tab2048 or a copy in shared memory).
+constexpr double kExpProdMax = 700.0 * kInvLn2x2048;
+STB_HD double exp_prod_fast(double c, double k, const double* tab) {
+  const double kRound = 6755399441055744.0;   // 1.5 2^52
+  const double t = fma(c, k, kRound);
+#ifdef __CUDA_ARCH__
+  const double nd = __dsub_rn(t, kRound);
+  const int n = __double2loint(t);
+#else
+  const double nd = t - kRound;
+  long long tb;
+  std::memcpy(&tb, &t, sizeof(tb));
+  const int n = (int)(tb & 0xffffffffLL);
+#endif
+  const double r = fma(c, k, -nd);
+  double p = fma(r, kExpProdC3, kExpProdC2);
+  p = fma(r, p, kExpProdC1);
+  p = fma(r, p, 1.0);
+  const double v = tab[n & 2047] * p;
+  long long bits;
+#ifdef __CUDA_ARCH__
+  bits = __double_as_longlong(v);
+#else
+  std::memcpy(&bits, &v, sizeof(bits));
+#endif
+  bits -= (long long)(n >> 11) << 52;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(bits);
+#else
+  double out;
+  std::memcpy(&out, &bits, sizeof(out));
+  return out;
+#endif
+}
+
 // Lentz evaluation of the contracted continued fraction for E_n, n = 1 and 2
 // together; returns the fractions without the e^{-z} factor.
 STB_HD void cf_e1e2(double z, double* f1, double* f2) {

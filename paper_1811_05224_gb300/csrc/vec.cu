@@ -285,6 +285,58 @@ __global__ void k_rlumped(const RaggedProblem* __restrict__ probs, int P, double
 
 static int grid_for(size_t n) { return stride_grid(n, 256, 8); }
 
+// ---- non-uniform time grids (tn: the n_t + 1 time nodes) ----------------------------
+// g[n][p] = (1/h_n) int_{tau_n} U*(x_p - y*, t) dt, h_n = t_{n+1} - t_n
+__global__ void k_nu_rhs_g(DevMesh M, const double* __restrict__ tn, double ysx, double ysy, double* __restrict__ g) {
+  const int total = M.n_t * M.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int p = e % M.N, n = e / M.N;
+    const double dx = M.vx[p] - ysx, dy = M.vy[p] - ysy;
+    const double a = M.alpha * (dx * dx + dy * dy) / 4.0;
+    const double E1 = e1_only(a / tn[n + 1]);
+    const double E0 = n > 0 ? e1_only(a / tn[n]) : 0.0;
+    g[e] = (E1 - E0) * M.alpha / (4.0 * kPi) / (tn[n + 1] - tn[n]);
+  }
+}
+
+// f[m][i] += (1/2) M_h g: M_h[(i,m),(p,m)] = h_m h_i / 2 for p in {i, i+1}
+__global__ void k_nu_half_mass_add(DevMesh M, const double* __restrict__ tn, const double* __restrict__ g,
+                                   double* __restrict__ f) {
+  const int total = M.n_t * M.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e % M.N, m = e / M.N;
+    const int row = e - i, ip = (i + 1) % M.N;
+    const double hm = 0.5 * (tn[m + 1] - tn[m]) * 0.5 * M.slen[i] * (g[e] + g[row + ip]);
+    f[e] = hm + f[e];
+  }
+}
+
+// L[m][l] = h_m (h_{l-1} + 2 h_l + h_{l+1}) / 4: the lumped dual mass of step m
+__global__ void k_nu_lumped(DevMesh M, const double* __restrict__ tn, double* __restrict__ L) {
+  const int total = M.n_t * M.N;
+  const int N = M.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int l = e % N, m = e / N;
+    L[e] = (tn[m + 1] - tn[m]) * (M.slen[(l - 1 + N) % N] + 2.0 * M.slen[l] + M.slen[(l + 1) % N]) / 4.0;
+  }
+}
+
+cudaError_t nu_rhs_launch(const DevMesh& M, const double* tn, double ysx, double ysy, double* g, cudaStream_t s) {
+  k_nu_rhs_g<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, tn, ysx, ysy, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t nu_half_mass_add_launch(const DevMesh& M, const double* tn, const double* g, double* f, cudaStream_t s) {
+  k_nu_half_mass_add<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, tn, g, f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t nu_lumped_launch(const DevMesh& M, const double* tn, double* L, cudaStream_t s) {
+  k_nu_lumped<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, tn, L);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t rhs_g_launch(const DevMesh& M, double ysx, double ysy, double* g, cudaStream_t s) {
   k_rhs_g<<<grid_for((size_t)M.n_t * M.N), 256, 0, s>>>(M, ysx, ysy, g);
   count_launches(1);

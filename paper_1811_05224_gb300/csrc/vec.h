@@ -50,4 +50,8 @@ cudaError_t blockmul_launch(int rows, int N, const double* B, bool trans, const 
                             cudaStream_t s);
 // dst[i] = (float)src[i]
 cudaError_t round_f32_launch(const double* src, float* dst, size_t n, cudaStream_t s);
+// non-uniform time grids (tn: n_t + 1 device time nodes)
+cudaError_t nu_rhs_launch(const DevMesh& M, const double* tn, double ysx, double ysy, double* g, cudaStream_t s);
+cudaError_t nu_half_mass_add_launch(const DevMesh& M, const double* tn, const double* g, double* f, cudaStream_t s);
+cudaError_t nu_lumped_launch(const DevMesh& M, const double* tn, double* L, cudaStream_t s);
 }  // namespace stbem

@@ -7,6 +7,9 @@ static stbem::RuleTables T;
 extern "C" {
 void nc_init() { stbem::build_rule_tables(&T); }
 void nc_exp_neg(const double* x, int n, double* out) { for (int i = 0; i < n; ++i) out[i] = stbem::exp_neg_fast(x[i]); }
+void nc_exp_prod(const double* c, const double* k, int n, double* out) {
+  for (int i = 0; i < n; ++i) out[i] = stbem::exp_prod_fast(c[i], k[i], stbem::kExp2Tab2048);
+}
 void nc_e1e2(const double* z, int n, double* e1, double* e2) { for (int i = 0; i < n; ++i) stbem::e1e2(z[i], e1 + i, e2 + i); }
 void nc_e1only(const double* z, int n, double* e1) { for (int i = 0; i < n; ++i) e1[i] = stbem::e1_only(z[i]); }
 void nc_e1e2f(const float* z, int n, float* e1, float* e2) { for (int i = 0; i < n; ++i) stbem::e1e2_f(z[i], e1 + i, e2 + i); }

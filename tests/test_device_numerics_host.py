@@ -42,6 +42,27 @@ def test_exp_neg_within_two_ulp(lib):
     assert np.max(np.abs(out - ref) / ulp) <= 2.0
 
 
+def test_exp_prod_within_two_ulp(lib):
+    """e^{-c k ln2/2048} of the hot loops (k = sigma 2048/ln2 from a node
+    table) against extended-precision numpy for the same c and k: the product
+    c k is rounded to its integer part by a fused multiply-add and the
+    remainder is exact, so the errors are the table, the cubic and the final
+    product."""
+    rng = np.random.default_rng(4)
+    kmax = 700.0 * 2048 / np.log(2.0)
+    y = np.concatenate([np.linspace(0.0, 3.0, 20001), np.linspace(3.0, kmax, 300001)[:-1],
+                        np.logspace(-300, 0, 2001)])
+    k = np.exp(rng.uniform(np.log(1e-3), np.log(1e6), y.size))      # node values over a wide range
+    c = y / k
+    out = np.zeros_like(y)
+    lib.nc_exp_prod(_d(c), _d(k), len(y), _d(out))
+    l = np.log(np.longdouble(2)) / np.longdouble(2048)
+    ref = np.exp(-(c.astype(np.longdouble) * k.astype(np.longdouble)) * l)
+    ulp = np.spacing(ref.astype(np.float64))
+    err = np.abs(out.astype(np.longdouble) - ref) / ulp.astype(np.longdouble)
+    assert float(err.max()) <= 2.5, float(err.max())
+
+
 def test_e1_e2_fp64_and_fp32(lib):
     z = np.concatenate([np.logspace(-12, 0, 400), np.linspace(1.0, 16.5, 2000), np.logspace(1.2, 2.85, 300)])
     e1, e2 = np.zeros_like(z), np.zeros_like(z)
