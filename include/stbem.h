@@ -440,6 +440,51 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_hi, cons
                     const void* dev_A_lo, int n_rhs, const double* dev_x, double* dev_y, void* dev_work,
                     size_t work_bytes);
 
+/* ---- Exact-slice products (FP64-grade accuracy on the BF16 tensor cores) -----
+ * The block-Toeplitz product of eq. (5)'s lag blocks with many right-hand
+ * sides, y[b][m] = sum_{d <= m} A[d] x[b][m - d] (the product the GMRES of
+ * Section 2 repeats), computed from integer slices: each row r of an FP64
+ * matrix (a row i of a lag block A[d], or the values x[b][n][.] of one step)
+ * gets a power-of-two scale 2^e_r (max |row| < 2^e_r) and n_slices signed
+ * integer slices q_s of 6 bits, row = 2^e_r sum_s q_s 2^{-6 (s + 1)}
+ * (|q_0| <= 64, |q_s| <= 32 after), stored as BF16 (exact).  The product
+ * multiplies every slice pair (s, t) with s + t < n_slices on the tensor
+ * cores; the integer sums of one lag, one s + t and at most 1024 columns are
+ * exact in the FP32 accumulator, and they are combined in double-float with
+ * their powers of two, so the only errors are the dropped pairs and the final
+ * rounding: about 2^(-6 n_slices) |A| |x| per entry (n_slices = 7: a few
+ * 1e-12 of |A| |x|, versus ~1e-7 for stbem_apply_tc3 and ~4e-3 for one BF16
+ * product).  n_slices is 4..8. */
+typedef struct stbem_exact_operand {
+  int n_slices;         /* 4..8 */
+  const void* slices;   /* device, BF16 [n_slices][rows][cols], 16-byte aligned */
+  const int* row_exp;   /* device, int32 [rows]: e_r (-16384 for a zero row) */
+} stbem_exact_operand;
+
+/* Slices of an FP64 row-major matrix dev_src (rows x cols) into dev_slices
+ * (BF16 [n_slices][rows][cols]) and dev_row_exp (int32 [rows]).  For lag
+ * blocks rows = n_t n_x, cols = n_x; for right-hand sides rows = n_rhs n_t,
+ * cols = n_x.  Asynchronous on the context's stream.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_CUDA. */
+int stbem_exact_slices(stbem_ctx* ctx, long long rows, int cols, int n_slices, const double* dev_src,
+                       void* dev_slices, int* dev_row_exp);
+
+/* y (FP64, [n_rhs][n_t][n_x]) = the block-Toeplitz product of the sliced lag
+ * blocks A (rows n_t n_x) with the sliced right-hand sides x (rows n_rhs n_t),
+ * both with the same n_slices.  Requires n_x % 8 == 0, n_t <= 4096,
+ * n_rhs <= 65535.  One launch of 128 x 128 output tiles; its pipeline waits
+ * are bounded (STBEM_ERR_TIMEOUT).  Blocks the host.  Errors: STBEM_ERR_ARG,
+ * STBEM_ERR_TIMEOUT, STBEM_ERR_CUDA. */
+int stbem_apply_tc_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* A, int n_rhs,
+                         const stbem_exact_operand* x, double* dev_y);
+
+/* The same product with x in FP64 ([n_rhs][n_t][n_x]), sliced inside the call
+ * into dev_work (stbem_apply_exact_workspace_bytes(), 256-byte aligned).
+ * Blocks the host.  Errors as stbem_apply_tc_exact, STBEM_ERR_NOMEM. */
+int stbem_apply_exact_workspace_bytes(int n_t, int n_x, int n_rhs, int n_slices, size_t* bytes);
+int stbem_apply_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* A, int n_rhs,
+                      const double* dev_x, double* dev_y, void* dev_work, size_t work_bytes);
+
 /* Time averages of g = U*(x - y_k*, t) at the vertices for n_src source
  * points (host_ystar: 2 n_src doubles): dev_G[k][n][p] as in stbem_rhs. */
 int stbem_rhs_g_batched(stbem_ctx* ctx, const stbem_mesh* mesh, int n_src, const double* host_ystar,
@@ -473,6 +518,22 @@ int stbem_solve_batched(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void*
                         const void* dev_V_lo, const void* dev_D_bf16, const double* dev_L, const double* dev_V64,
                         const double* dev_F, double* dev_W, const stbem_solve_opts* opts, double inner_tol,
                         stbem_solve_info* infos, void* dev_work, size_t work_bytes);
+
+/* stbem_solve_batched with the exact-slice operator V_exact (stbem_exact_slices
+ * of the FP64 V) in place of dev_V64: once every relative residual is below
+ * 2e-6, refinement continues on F - V W from the exact-slice product (about
+ * 2^(-6 n_slices) |V| |W|, a few 1e-12 at n_slices = 7) on the tensor cores
+ * instead of the FP64 CUDA-core product.  Workspace:
+ * stbem_solve_batched_exact_workspace_bytes() (the base workspace plus the
+ * slices of W), 256-byte aligned.  Requires, besides the sizes of
+ * stbem_solve_batched, n_t <= 4096.  Errors as stbem_solve_batched. */
+int stbem_solve_batched_exact_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, int n_slices,
+                                              size_t* bytes);
+int stbem_solve_batched_exact(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void* dev_V_hi,
+                              const void* dev_V_mid, const void* dev_V_lo, const void* dev_D_bf16,
+                              const double* dev_L, const stbem_exact_operand* V_exact, const double* dev_F,
+                              double* dev_W, const stbem_solve_opts* opts, double inner_tol,
+                              stbem_solve_info* infos, void* dev_work, size_t work_bytes);
 
 /* ---- Ragged batches ----------------------------------------------------------
  * Many independent problems of different sizes (not in the paper, which solves

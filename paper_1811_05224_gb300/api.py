@@ -488,17 +488,73 @@ def apply_tc3(ctx: Context, A_slices, x, out=None, work=None):
     return out if x.dim() == 3 else out[0]
 
 
+class ExactOperand:
+    """Exact-slice form of an FP64 tensor whose last axis is a row: ``slices``
+    (BF16, (n_slices,) + shape) and ``row_exp`` (int32, shape[:-1]), with
+    row = 2^row_exp sum_s slices[s] 2^(-6 (s + 1)) to 6 n_slices bits."""
+
+    def __init__(self, ctx: Context, src, n_slices: int = 7):
+        if src.dtype != torch.float64 or not src.is_contiguous():
+            raise ValueError("ExactOperand: a contiguous FP64 tensor is required")
+        self.shape = tuple(src.shape)
+        self.n_slices = int(n_slices)
+        cols = src.shape[-1]
+        rows = src.numel() // cols
+        self.slices = torch.empty((self.n_slices,) + self.shape, dtype=torch.bfloat16, device=src.device)
+        self.row_exp = torch.empty(self.shape[:-1], dtype=torch.int32, device=src.device)
+        ctx.check(ctx.lib.stbem_exact_slices(ctx.h, rows, cols, self.n_slices, _ptr(src), _ptr(self.slices),
+                                             _ptr(self.row_exp)))
+
+    def c_struct(self):
+        return capi.ExactOperand(self.n_slices, self.slices.data_ptr(), self.row_exp.data_ptr())
+
+
+def exact_slices(ctx: Context, src, n_slices: int = 7):
+    """The exact-slice form (ExactOperand) of FP64 lag blocks (n_t, n_x, n_x)
+    or right-hand sides (n_rhs, n_t, n_x)."""
+    return ExactOperand(ctx, src, n_slices)
+
+
+def apply_exact(ctx: Context, A, x, out=None, work=None):
+    """Block-Toeplitz product on the tensor cores to FP64-grade accuracy (about
+    2^(-6 n_slices) |A| |x|): A an ExactOperand of lag blocks, x FP64
+    (n_rhs, n_t, n_x) or (n_t, n_x), or an ExactOperand of it."""
+    n_t, n_x = A.shape[0], A.shape[1]
+    sa = A.c_struct()
+    if isinstance(x, ExactOperand):
+        B = x.shape[0] if len(x.shape) == 3 else 1
+        if out is None:
+            out = torch.empty((B, n_t, n_x), dtype=torch.float64, device=A.slices.device)
+        sx = x.c_struct()
+        ctx.check(ctx.lib.stbem_apply_tc_exact(ctx.h, n_t, n_x, ctypes.byref(sa), B, ctypes.byref(sx), _ptr(out)))
+        return out if len(x.shape) == 3 else out[0]
+    xb = x if x.dim() == 3 else x.unsqueeze(0)
+    if out is None:
+        out = torch.empty_like(xb)
+    if work is None:
+        nb = ctypes.c_size_t()
+        ctx.check(ctx.lib.stbem_apply_exact_workspace_bytes(n_t, n_x, xb.shape[0], A.n_slices, ctypes.byref(nb)))
+        work = torch.empty(nb.value, dtype=torch.uint8, device=xb.device)
+    ctx.check(ctx.lib.stbem_apply_exact(ctx.h, n_t, n_x, ctypes.byref(sa), xb.shape[0], _ptr(xb), _ptr(out),
+                                        _ptr(work), work.numel()))
+    return out if x.dim() == 3 else out[0]
+
+
 def rhs_batched(ctx: Context, mesh: Mesh, K, y_stars):
     """(G, F) for many sources: G[k] vertex time averages of U*(x - y_k, t),
     F = 1/2 M_h G + K_h G.  K is the FP64 operator (an FP64 CUDA-core product
-    of all right-hand sides: F to FP64 accuracy) or a tuple of its three BF16
-    slices (the compensated tensor-core product, a few 1e-7 of |K||G|)."""
+    of all right-hand sides: F to FP64 accuracy), its ExactOperand (the
+    exact-slice tensor-core product, a few 1e-12 of |K||G| at 7 slices) or a
+    tuple of its three BF16 slices (the compensated tensor-core product, a few
+    1e-7 of |K||G|)."""
     ys = np.ascontiguousarray(np.asarray(y_stars, dtype=np.float64).reshape(-1))
     B = ys.size // 2
     G = ctx.empty((B, mesh.n_t, mesh.n_x))
     ctx.check(ctx.lib.stbem_rhs_g_batched(ctx.h, mesh.h, B, ys.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                           _ptr(G)))
-    if isinstance(K, (tuple, list)):
+    if isinstance(K, ExactOperand):
+        F = apply_exact(ctx, K, G)
+    elif isinstance(K, (tuple, list)):
         F = apply_tc3(ctx, K, G)
     else:
         F = apply(ctx, K, G)
@@ -510,22 +566,35 @@ def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1
                   max_iter: int = 400, restart: int = 40, work=None, out=None, raise_on_fail: bool = True,
                   V64=None):
     """Many-right-hand-side solve on the tensor cores; returns (W, infos).
-    With the FP64 operator V64 the refinement finishes on FP64 residuals
-    (FP64-solve accuracy for tol down to 1e-8 and below)."""
+    With V64 the refinement finishes on residuals of that operator: the FP64
+    lag blocks (an FP64 CUDA-core product) or their ExactOperand (the
+    exact-slice tensor-core product); either gives FP64-solve accuracy for tol
+    down to 1e-8 and below."""
     B, n_t, n_x = F.shape
     opts = capi.SolveOpts(tol, max_iter, restart, int(D_bf16 is not None))
     infos = (capi.SolveInfo * B)()
     if out is None:
         out = torch.empty_like(F)
+    exact = isinstance(V64, ExactOperand)
     if work is None:
         nb = ctypes.c_size_t()
-        ctx.check(ctx.lib.stbem_solve_batched_workspace_bytes(n_t, n_x, B, restart, int(V64 is not None),
-                                                              ctypes.byref(nb)))
+        if exact:
+            ctx.check(ctx.lib.stbem_solve_batched_exact_workspace_bytes(n_t, n_x, B, restart, V64.n_slices,
+                                                                        ctypes.byref(nb)))
+        else:
+            ctx.check(ctx.lib.stbem_solve_batched_workspace_bytes(n_t, n_x, B, restart, int(V64 is not None),
+                                                                  ctypes.byref(nb)))
         work = torch.empty(nb.value, dtype=torch.uint8, device=F.device)
     Vs = list(V_slices) + [None] * (3 - len(V_slices))
-    code = ctx.lib.stbem_solve_batched(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]), _ptr(D_bf16),
-                                       _ptr(L), _ptr(V64), _ptr(F), _ptr(out), ctypes.byref(opts),
-                                       float(inner_tol), infos, _ptr(work), work.numel())
+    if exact:
+        sv = V64.c_struct()
+        code = ctx.lib.stbem_solve_batched_exact(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]),
+                                                 _ptr(D_bf16), _ptr(L), ctypes.byref(sv), _ptr(F), _ptr(out),
+                                                 ctypes.byref(opts), float(inner_tol), infos, _ptr(work), work.numel())
+    else:
+        code = ctx.lib.stbem_solve_batched(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]), _ptr(D_bf16),
+                                           _ptr(L), _ptr(V64), _ptr(F), _ptr(out), ctypes.byref(opts),
+                                           float(inner_tol), infos, _ptr(work), work.numel())
     res = [{"iterations": i.iterations, "status": i.status, "rel_residual": i.rel_residual} for i in infos]
     if code != capi.STBEM_OK and raise_on_fail:
         ctx.check(code)

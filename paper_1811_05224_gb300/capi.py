@@ -44,6 +44,8 @@ EXPORTS = [
     "stbem_nu_lumped_mass", "stbem_nu_solve",
     "stbem_domain_create", "stbem_domain_destroy", "stbem_domain_info", "stbem_m0_bytes", "stbem_m0_assemble",
     "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data", "stbem_evaluate",
+    "stbem_exact_slices", "stbem_apply_tc_exact", "stbem_apply_exact_workspace_bytes", "stbem_apply_exact",
+    "stbem_solve_batched_exact_workspace_bytes", "stbem_solve_batched_exact",
 ]
 
 
@@ -59,6 +61,10 @@ class Problem(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
                 ("precondition", ctypes.c_int)]
+
+
+class ExactOperand(ctypes.Structure):
+    _fields_ = [("n_slices", ctypes.c_int), ("slices", ctypes.c_void_p), ("row_exp", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -157,6 +163,13 @@ def load(path: str = LIB_PATH):
     L.stbem_solve_batched_workspace_bytes.argtypes = [i, i, i, i, i, P(sz)]
     L.stbem_solve_batched.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo),
                                       vp, sz]
+    L.stbem_exact_slices.argtypes = [vp, ctypes.c_longlong, i, i, vp, vp, vp]
+    L.stbem_apply_tc_exact.argtypes = [vp, i, i, P(ExactOperand), i, P(ExactOperand), vp]
+    L.stbem_apply_exact_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_apply_exact.argtypes = [vp, i, i, P(ExactOperand), i, vp, vp, vp, sz]
+    L.stbem_solve_batched_exact_workspace_bytes.argtypes = [i, i, i, i, i, P(sz)]
+    L.stbem_solve_batched_exact.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(ExactOperand), vp, vp, P(SolveOpts),
+                                            d, P(SolveInfo), vp, sz]
     L.stbem_domain_create.argtypes = [vp, vp, P(d), i, P(i), i, P(vp)]
     L.stbem_domain_destroy.argtypes = [vp]
     L.stbem_domain_destroy.restype = None

@@ -412,6 +412,96 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* A_hi, const vo
   return STBEM_OK;
 }
 
+// ------------------------------------------------ exact-slice products ------
+namespace {
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// workspace of the x side of an exact product: S slices of n values + n / n_x exponents
+size_t exact_x_bytes(int nt, int nx, int B, int S) {
+  const size_t n = (size_t)B * nt * nx;
+  return align256((size_t)S * n * 2) + (size_t)B * nt * sizeof(int);
+}
+
+int check_exact_operand(stbem_ctx* ctx, const char* name, const stbem_exact_operand* A) {
+  if (!A || !A->slices || !A->row_exp) return fail(ctx, STBEM_ERR_ARG, "%s: NULL operand", name);
+  if (A->n_slices < stbem::kExactMinSlices || A->n_slices > stbem::kExactMaxSlices)
+    return fail(ctx, STBEM_ERR_ARG, "%s: n_slices must be in %d..%d", name, stbem::kExactMinSlices,
+                stbem::kExactMaxSlices);
+  if (reinterpret_cast<uintptr_t>(A->slices) & 15) return fail(ctx, STBEM_ERR_ARG, "%s: slices not 16-byte aligned", name);
+  return STBEM_OK;
+}
+
+// y = A x with x in FP64: slice x into `work`, then the exact product
+cudaError_t apply_exact(int nt, int nx, const stbem_exact_operand& A, int B, const double* x, double* y, void* work,
+                        cudaStream_t s) {
+  const int S = A.n_slices;
+  const size_t n = (size_t)B * nt * nx;
+  void* xs = work;
+  int* xe = reinterpret_cast<int*>(static_cast<char*>(work) + align256((size_t)S * n * 2));
+  cudaError_t e = stbem::exact_slices_launch(x, (long long)B * nt, nx, S, xs, xe, s);
+  if (e == cudaSuccess) e = stbem::apply_tc_exact_launch(nt, nx, S, A.slices, A.row_exp, B, xs, xe, y, s);
+  return e;
+}
+}  // namespace
+
+int stbem_exact_slices(stbem_ctx* ctx, long long rows, int cols, int n_slices, const double* src, void* slices,
+                       int* row_exp) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!src || !slices || !row_exp) return fail(ctx, STBEM_ERR_ARG, "exact_slices: NULL pointer");
+  if (rows < 0 || cols < 1 || n_slices < stbem::kExactMinSlices || n_slices > stbem::kExactMaxSlices)
+    return fail(ctx, STBEM_ERR_ARG, "exact_slices: bad sizes rows=%lld cols=%d n_slices=%d", rows, cols, n_slices);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "exact_slices: set device");
+  CUDA_TRY(ctx, stbem::exact_slices_launch(src, rows, cols, n_slices, slices, row_exp, ctx->stream), "exact_slices");
+  return STBEM_OK;
+}
+
+int stbem_apply_tc_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* A, int n_rhs,
+                         const stbem_exact_operand* x, double* y) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (const int r = check_exact_operand(ctx, "apply_tc_exact", A)) return r;
+  if (const int r = check_exact_operand(ctx, "apply_tc_exact", x)) return r;
+  if (!y) return fail(ctx, STBEM_ERR_ARG, "apply_tc_exact: NULL pointer");
+  if (x->n_slices != A->n_slices) return fail(ctx, STBEM_ERR_ARG, "apply_tc_exact: A and x differ in n_slices");
+  if (!stbem::apply_tc_exact_supported(n_t, n_x, n_rhs, A->n_slices))
+    return fail(ctx, STBEM_ERR_ARG, "apply_tc_exact: unsupported sizes n_t=%d n_x=%d n_rhs=%d", n_t, n_x, n_rhs);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_tc_exact: set device");
+  CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_tc_exact: reset error word");
+  CUDA_TRY(ctx, stbem::apply_tc_exact_launch(n_t, n_x, A->n_slices, A->slices, A->row_exp, n_rhs, x->slices,
+                                             x->row_exp, y, ctx->stream),
+           "apply_tc_exact");
+  int flag = 0;
+  CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc_exact: read error word");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc_exact: a pipeline wait timed out");
+  return STBEM_OK;
+}
+
+int stbem_apply_exact_workspace_bytes(int n_t, int n_x, int n_rhs, int n_slices, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || n_slices < stbem::kExactMinSlices ||
+      n_slices > stbem::kExactMaxSlices)
+    return STBEM_ERR_ARG;
+  *bytes = exact_x_bytes(n_t, n_x, n_rhs, n_slices);
+  return STBEM_OK;
+}
+
+int stbem_apply_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* A, int n_rhs, const double* x,
+                      double* y, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (const int r = check_exact_operand(ctx, "apply_exact", A)) return r;
+  if (!x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "apply_exact: NULL pointer");
+  if (!stbem::apply_tc_exact_supported(n_t, n_x, n_rhs, A->n_slices))
+    return fail(ctx, STBEM_ERR_ARG, "apply_exact: unsupported sizes n_t=%d n_x=%d n_rhs=%d", n_t, n_x, n_rhs);
+  if (reinterpret_cast<uintptr_t>(work) & 255) return fail(ctx, STBEM_ERR_ARG, "apply_exact: workspace not 256-byte aligned");
+  const size_t need = exact_x_bytes(n_t, n_x, n_rhs, A->n_slices);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "apply_exact: workspace %zu < %zu bytes", work_bytes, need);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_exact: set device");
+  CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_exact: reset error word");
+  CUDA_TRY(ctx, apply_exact(n_t, n_x, *A, n_rhs, x, y, work, ctx->stream), "apply_exact");
+  int flag = 0;
+  CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_exact: read error word");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_exact: a pipeline wait timed out");
+  return STBEM_OK;
+}
+
 int stbem_rhs_g_batched(stbem_ctx* ctx, const stbem_mesh* m, int n_src, const double* ys, double* G) {
   if (!ctx) return STBEM_ERR_ARG;
   if (const int rg = reject_graded(ctx, m, "rhs_g_batched")) return rg;
@@ -444,10 +534,12 @@ size_t batch_base_bytes(int nt, int nx, int B, int m) {
   const size_t n = (size_t)B * nt * nx;
   return ((size_t)(m + 1) * n + 4 * n + (size_t)(m + 4) * B) * sizeof(double) + 3 * n * 2 + 256;
 }
-// with an FP64 residual operator: + the FP64 product's lag-chunk partial sums
-size_t batch_bytes(int nt, int nx, int B, int m, bool fp64_residual) {
+// with an FP64 residual operator: + the FP64 product's lag-chunk partial sums;
+// with an exact-slice one (exact_slices > 0): + the slices of W
+size_t batch_bytes(int nt, int nx, int B, int m, bool fp64_residual, int exact_slices = 0) {
   size_t b = batch_base_bytes(nt, nx, B, m);
   if (fp64_residual) b = ((b + 255) & ~(size_t)255) + stbem::apply_workspace_bytes(nt, nx, B);
+  else if (exact_slices > 0) b = ((b + 255) & ~(size_t)255) + exact_x_bytes(nt, nx, B, exact_slices);
   return b;
 }
 
@@ -463,10 +555,22 @@ int stbem_solve_batched_workspace_bytes(int n_t, int n_x, int n_rhs, int restart
   return STBEM_OK;
 }
 
-int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
-                        const void* V_lo, const void* D_bf16, const double* Lm, const double* V64, const double* F,
-                        double* W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
-                        void* work, size_t work_bytes) {
+int stbem_solve_batched_exact_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, int n_slices,
+                                              size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || restart < 1 || n_slices < stbem::kExactMinSlices ||
+      n_slices > stbem::kExactMaxSlices)
+    return STBEM_ERR_ARG;
+  *bytes = batch_bytes(n_t, n_x, n_rhs, restart, false, n_slices);
+  return STBEM_OK;
+}
+
+namespace {
+// The batched solve; the refinement's final residual phase uses the FP64
+// operator V64, the exact-slice operator Vx, or neither.
+int solve_batched_impl(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid, const void* V_lo,
+                       const void* D_bf16, const double* Lm, const double* V64, const stbem_exact_operand* Vx,
+                       const double* F, double* W, const stbem_solve_opts* opts, double inner_tol,
+                       stbem_solve_info* infos, void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!V_hi || !F || !W || !opts || !infos || !work) return fail(ctx, STBEM_ERR_ARG, "solve_batched: NULL pointer");
   if (!stbem::apply_tc_supported(nt, nx, B)) return fail(ctx, STBEM_ERR_ARG, "solve_batched: unsupported sizes");
@@ -479,7 +583,14 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
     return fail(ctx, STBEM_ERR_ARG, "solve_batched: the lumped mass (precondition = 1) only");
   if (V64 && !stbem::apply_grid_fits(nt, nx, B))
     return fail(ctx, STBEM_ERR_ARG, "solve_batched: too many right-hand sides for the FP64 residual product");
-  if (work_bytes < batch_bytes(nt, nx, B, m, V64 != nullptr))
+  if (Vx) {
+    if (const int r = check_exact_operand(ctx, "solve_batched_exact", Vx)) return r;
+    if (!stbem::apply_tc_exact_supported(nt, nx, B, Vx->n_slices))
+      return fail(ctx, STBEM_ERR_ARG, "solve_batched_exact: unsupported sizes for the exact product");
+    if (reinterpret_cast<uintptr_t>(work) & 255)
+      return fail(ctx, STBEM_ERR_ARG, "solve_batched_exact: workspace not 256-byte aligned");
+  }
+  if (work_bytes < batch_bytes(nt, nx, B, m, V64 != nullptr, Vx ? Vx->n_slices : 0))
     return fail(ctx, STBEM_ERR_NOMEM, "solve_batched: workspace too small");
   const size_t N = (size_t)nt * nx, n = (size_t)B * N;
   BatchWork Wk;
@@ -491,7 +602,8 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
   Wk.DW = p; p += n;
   Wk.h = p; p += (size_t)(m + 4) * B;
   Wk.xb = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
-  // FP64 product partial sums after the base workspace
+  // the final residual product's scratch after the base workspace (FP64
+  // partial sums, or the slices of W)
   void* part64 = static_cast<char*>(work) + ((batch_base_bytes(nt, nx, B, m) + 255) & ~(size_t)255);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_batched: set device");
   cudaStream_t s = ctx->stream;
@@ -527,12 +639,15 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
     infos[b].rel_residual = 0.0;
   }
   // refinement residual R = F - V W: the three-slice tensor-core product
-  // first, then (with V64) the FP64 product once that one reaches its floor
+  // first, then (with V64 or Vx) the FP64 or exact-slice product once that
+  // one reaches its floor
   bool fp64_phase = false;
-  const double tol_tc = V64 ? std::max(opts->tol, kTc3ResidualFloor) : opts->tol;
+  const bool final_phase = V64 || Vx;
+  const double tol_tc = final_phase ? std::max(opts->tol, kTc3ResidualFloor) : opts->tol;
   auto residual = [&]() -> cudaError_t {
-    cudaError_t e = fp64_phase ? stbem::apply_launch(STBEM_F64, false, nt, nx, V64, B, W, Wk.U, part64, s)
-                               : apply_tc3(nt, nx, Vs, B, W, Wk.U, Wk.xb, s);
+    cudaError_t e = !fp64_phase ? apply_tc3(nt, nx, Vs, B, W, Wk.U, Wk.xb, s)
+                    : Vx        ? apply_exact(nt, nx, *Vx, B, W, Wk.U, part64, s)
+                                : stbem::apply_launch(STBEM_F64, false, nt, nx, V64, B, W, Wk.U, part64, s);
     if (e == cudaSuccess) e = stbem::sub_launch(F, Wk.U, Wk.R, n, s);
     return e;
   };
@@ -550,7 +665,7 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
       active[b] = infos[b].status == STBEM_OK && rel > target;
       any_active = any_active || active[b];
     }
-    if (!any_active && V64 && !fp64_phase && opts->tol < tol_tc) {
+    if (!any_active && final_phase && !fp64_phase && opts->tol < tol_tc) {
       // the tensor-core residual is at its floor: continue on the FP64 residual
       fp64_phase = true;
       CUDA_TRY(ctx, residual(), "solve_batched: FP64 residual");
@@ -669,6 +784,24 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
     if (infos[b].status != STBEM_OK) worst = infos[b].status;
   if (worst != STBEM_OK) return fail(ctx, worst, "solve_batched: some right-hand sides did not converge");
   return STBEM_OK;
+}
+}  // namespace
+
+int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
+                        const void* V_lo, const void* D_bf16, const double* Lm, const double* V64, const double* F,
+                        double* W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
+                        void* work, size_t work_bytes) {
+  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, V64, nullptr, F, W, opts, inner_tol,
+                            infos, work, work_bytes);
+}
+
+int stbem_solve_batched_exact(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
+                              const void* V_lo, const void* D_bf16, const double* Lm, const stbem_exact_operand* Vx,
+                              const double* F, double* W, const stbem_solve_opts* opts, double inner_tol,
+                              stbem_solve_info* infos, void* work, size_t work_bytes) {
+  if (ctx && !Vx) return fail(ctx, STBEM_ERR_ARG, "solve_batched_exact: NULL operand");
+  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, nullptr, Vx, F, W, opts, inner_tol,
+                            infos, work, work_bytes);
 }
 
 int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, double* g,

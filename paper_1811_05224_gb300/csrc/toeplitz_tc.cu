@@ -287,6 +287,32 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// three 8-column TMEM loads, then one wait
+__device__ __forceinline__ void tmem_ld8x3(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t (&r)[8],
+                                           uint32_t (&h)[8], uint32_t (&l)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]),
+        "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7])
+      : "r"(a0), "r"(a1), "r"(a2)
+      : "memory");
+}
+
+// two 8-column TMEM stores, then a wait for their completion
+__device__ __forceinline__ void tmem_st8x2(uint32_t a0, uint32_t a1, const uint32_t (&h)[8], const uint32_t (&l)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%10, %11, %12, %13, %14, %15, %16, %17};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(a0),
+      "r"(a1), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]), "r"(l[0]),
+      "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7])
+      : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -296,7 +322,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // roundings) loses accuracy in proportion to its length, which limits the
 // refinement residual of the batched solve.  Here the MMA issuer restarts the
 // accumulator every `chunk` K steps, alternating between two 128-column TMEM
-// buffers, and eight epilogue warps drain each finished chunk into a Kahan
+// buffers, and sixteen epilogue warps drain each finished chunk into a Kahan
 // (FP32 sum + FP32 compensation) pair per output while the next chunk is being
 // multiplied.  The per-output error is then about (4 chunk + 2) u |partial
 // sums| instead of 4 n_lags n_x / 64 u, u = 2^-24.
@@ -462,6 +488,286 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
   }
 }
 
+// ---- exact-slice product (FP64-grade accuracy on the BF16 tensor cores) --------
+// A and x are split into S integer slices of kSliceBits bits each, with a
+// power-of-two scale per row of A (lag d, row i: 2^{eA[d][i]}) and per row of
+// x (right-hand side b, step n: 2^{eX[b][n]}):
+//   A[d][i][j]  = sum_s a_s[d][i][j] 2^{eA[d][i] - 6 (s + 1)},  |a_0| <= 64, |a_s| <= 32,
+//   x[b][n][j]  = sum_t x_t[b][n][j] 2^{eX[b][n] - 6 (t + 1)},
+// so that a slice pair (s, t) contributes at 2^{eA + eX - 6 (s + t + 2)}.  The
+// slice products are exact (12-bit integers), and a sum over at most 1024
+// columns of the up to S <= 8 pairs with the same s + t stays below
+// 1024 (4096 + 1024 (S - 2)) <= 10 2^20 < 2^24, so the FP32 tensor-core
+// accumulator holds every partial sum exactly, whatever its internal rounding.
+// The accumulator therefore restarts for every group (lag d, k = s + t, block
+// of 1024 columns); each finished exact group is scaled by its power of two
+// and added into a double-float (FP32 sum + FP32 error by Knuth's two-sum) per
+// output y[b][m][i], relative to 2^{max_d eA[d][i] + max_{n <= m} eX[b][n]}
+// (an upper bound of every contribution's scale; output steps with only small
+// x keep their own small scale).  Pairs with s + t >= S are dropped: with
+// S = 7 the product is accurate to a few 1e-12 of |A| |x|.
+//   warp 0: TMA producer, warp 1: MMA issuer (TMEM owner), warps 2..17: the
+//   epilogue; warp w owns TMEM lanes 32 (w % 4) .. + 31 and columns
+//   32 ((w - 2) / 4) .. + 31 of the tile.  The double-float sums live in TMEM
+//   too (columns 256.. and 384..), next to the two accumulator buffers
+//   (0.., 128..), so that the epilogue holds no per-output arrays.
+constexpr int kSliceBits = 6;
+constexpr int kExactJSteps = 16;                 // 64-wide K steps per group: 1024 columns
+constexpr int kZeroRowExp = -16384;              // scale of an all-zero row
+constexpr int EX_THREADS = 576;
+constexpr int EX_EPI_WARPS = 16;
+constexpr uint32_t EX_TMEM_COLS = 512;
+constexpr uint32_t EX_HI_COL = 256, EX_LO_COL = 384;
+constexpr int kExactMaxSteps = 4096;             // eX of one right-hand side staged in shared memory
+constexpr size_t EX_SMEM_BYTES = 1024 + STAGES * (size_t)STAGE_BYTES + 512 + 2 * kExactMaxSteps * sizeof(int);
+
+__device__ __forceinline__ void tma_load_4d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// 2^e as a float for e <= 0 (0 below the subnormal range)
+__device__ __forceinline__ float pow2f(int e) {
+  if (e < -149) return 0.0f;
+  if (e < -126) return __int_as_float(1 << (e + 149));
+  return __int_as_float((e + 127) << 23);
+}
+
+template <int S>
+__global__ void __launch_bounds__(EX_THREADS, 1)
+    k_apply_tc_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
+                     const int* __restrict__ eA, const int* __restrict__ eX, int nt, int nx,
+                     double* __restrict__ Y) {
+  extern __shared__ unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
+  unsigned char* smA = reinterpret_cast<unsigned char*>(base);
+  unsigned char* smB = smA + STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smB + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;   // [2]: group in buffer k complete
+  uint64_t* acc_empty = acc_full + 2;    // [2]: buffer k drained by the epilogue
+  uint64_t* done = acc_empty + 2;        // every MMA issued by warp 1 complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* eXs = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(full) + 512);   // this b's step scales
+  int* eXp = eXs + kExactMaxSteps;                                                     // their prefix maxima
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
+  const int dmax = min(m0 + BN - 1, nt - 1);
+  const int nj = (nx + BK - 1) / BK;
+  const int nb = (nj + kExactJSteps - 1) / kExactJSteps;
+  const int ngroups = (dmax + 1) * S * nb;       // (d, k, jb), jb fastest
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&acc_full[k], 1);
+      mbar_init(&acc_empty[k], EX_EPI_WARPS);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {   // step scales and their running maximum (a warp scan per 32 steps)
+    int carry = kZeroRowExp;
+    for (int c0 = 0; c0 < nt; c0 += 32) {
+      const int n = c0 + lane;
+      const int v = n < nt ? eX[(size_t)b * nt + n] : kZeroRowExp;
+      int pm = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, pm, off);
+        if (lane >= off) pm = max(pm, u);
+      }
+      pm = max(pm, carry);
+      if (n < nt) {
+        eXs[n] = v;
+        eXp[n] = pm;
+      }
+      carry = __shfl_sync(0xffffffffu, pm, 31);
+    }
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, EX_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  int issued = 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int d = g / (S * nb), k = (g / nb) % S, jb = g % nb;
+        const int j_lo = jb * kExactJSteps, j_hi = min(nj, j_lo + kExactJSteps);
+        for (int s = 0; s <= k && ok; ++s)
+          for (int jc = j_lo; jc < j_hi; ++jc, ++it) {
+            const int st = it % STAGES;
+            const uint32_t round = static_cast<uint32_t>(it / STAGES);
+            if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&full[st], STAGE_BYTES);
+            tma_load_4d(&tmA, &full[st], smA + st * A_BYTES, jc * BK, i0, d, s);
+            tma_load_4d(&tmX, &full[st], smB + st * B_BYTES, jc * BK, m0 - d, b, k - s);
+            issued = it + 1;
+          }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int buf = g & 1, k = (g / nb) % S, jb = g % nb;
+        const int nsteps = (k + 1) * (min(nj, (jb + 1) * kExactJSteps) - jb * kExactJSteps);
+        if (g >= 2 && !mbar_wait(&acc_empty[buf], ((g >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
+        const int it_end = it + nsteps;
+        for (int first = 1; it < it_end; ++it, first = 0) {
+          const int st = it % STAGES;
+          const uint32_t round = static_cast<uint32_t>(it / STAGES);
+          if (!mbar_wait(&full[st], round & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da = smem_desc(smA + st * A_BYTES);
+          const uint64_t db = smem_desc(smB + st * B_BYTES);
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma_bf16(acc, da + (uint64_t)((kk * 32) >> 4), db + (uint64_t)((kk * 32) >> 4),
+                      (first && kk == 0) ? 0u : 1u);
+          umma_commit(&empty[st]);
+        }
+        if (ok) umma_commit(&acc_full[buf]);
+      }
+      umma_commit(done);
+      if (!mbar_wait(done, 0)) ok = false;
+    }
+    __syncwarp();
+  } else {
+    // epilogue: row i = i0 + 32 q + lane, columns m = m0 + 32 cq + t
+    const int q = warp & 3, cq = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    const int i = i0 + q * 32 + lane;
+    const int mb = m0 + cq * 32;
+    // reference scale of y[b][m][i]: 2^{eAmax + eXp[m]}, eAmax the row's
+    // largest over the tile's lags (rows i >= n_x and steps outside
+    // 0..n_t - 1 were zero-filled by the loads, so their partials are 0: the
+    // clamped indexes give them finite scales)
+    const int ic = min(i, nx - 1);
+    int eAmax = kZeroRowExp;
+    for (int d = 0; d <= dmax; ++d) eAmax = max(eAmax, eA[(size_t)d * nx + ic]);
+    const uint32_t tcol = tmem + lane_base + static_cast<uint32_t>(cq * 32);
+    int er = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      const int buf = g & 1, d = g / (S * nb), k = (g / nb) % S;
+      if (g % (S * nb) == 0) er = eA[(size_t)d * nx + ic] - eAmax;
+      // after a failed wait the remaining groups are skipped without waiting
+      const bool got = __all_sync(0xffffffffu, ok && mbar_wait(&acc_full[buf], (g >> 1) & 1));
+      if (!got) ok = false;
+      if (!ok) continue;
+      tc_fence_after();
+      const int ek = -kSliceBits * (k + 2);
+#pragma unroll 1
+      for (int gg = 0; gg < 4; ++gg) {
+        uint32_t r[8], h[8], l[8];
+        const uint32_t c0 = static_cast<uint32_t>(gg * 8);
+        if (g == 0) {
+          tmem_ld8(tcol + buf * BN + c0, r);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) h[t] = l[t] = 0u;
+        } else {
+          tmem_ld8x3(tcol + buf * BN + c0, tcol + EX_HI_COL + c0, tcol + EX_LO_COL + c0, r, h, l);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int mc = min(mb + gg * 8 + t, nt - 1), n = min(max(mb + gg * 8 + t - d, 0), nt - 1);
+          const float v = __uint_as_float(r[t]) * pow2f(er + ek + eXs[n] - eXp[mc]);   // exact power-of-two scaling
+          const float hv = __uint_as_float(h[t]);
+          const float sm = hv + v;
+          const float bp = sm - hv;
+          h[t] = __float_as_uint(sm);
+          l[t] = __float_as_uint(__uint_as_float(l[t]) + ((hv - (sm - bp)) + (v - bp)));
+        }
+        tmem_st8x2(tcol + EX_HI_COL + c0, tcol + EX_LO_COL + c0, h, l);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+    if (ok) {   // warp-uniform: the TMEM loads are .sync.aligned
+#pragma unroll 1
+      for (int gg = 0; gg < 4; ++gg) {
+        uint32_t h[8], l[8];
+        tmem_ld8(tcol + EX_HI_COL + gg * 8, h);
+        tmem_ld8(tcol + EX_LO_COL + gg * 8, l);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int m = mb + gg * 8 + t;
+          if (i < nx && m < nt)
+            Y[((size_t)b * nt + m) * nx + i] =
+                ldexp((double)__uint_as_float(h[t]) + (double)__uint_as_float(l[t]), eAmax + eXp[m]);
+        }
+      }
+    }
+  }
+  if (!ok) atomicExch(&g_tc_error, 1);
+  // on any failure, let the loads already issued land before exiting
+  if (__syncthreads_or(!ok) && warp == 0 && lane == 0) drain_loads(full, issued);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, EX_TMEM_COLS);
+  }
+}
+
+// Integer slices of the rows of an FP64 matrix (rows x cols, row-major): per
+// row e = the exponent with max |row| < 2^e (kZeroRowExp for a zero row), then
+// R = row 2^{-e} and, S times, q = rint(R 2^6) (the slice), R = R 2^6 - q (exact
+// steps: scaling by powers of two, an integer and a remainder below 1/2).
+// One warp per row.
+__global__ void k_exact_slices(const double* __restrict__ src, long long rows, int cols, int S,
+                               __nv_bfloat16* __restrict__ out, int* __restrict__ rexp) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const double* row = src + w * (long long)cols;
+  double mx = 0.0;
+  for (int j = lane; j < cols; j += 32) mx = fmax(mx, fabs(row[j]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  int e = kZeroRowExp;
+  if (mx > 0.0) {
+    int ex;
+    frexp(mx, &ex);          // mx = f 2^ex, f in [1/2, 1): mx < 2^ex
+    e = ex;
+  }
+  if (lane == 0) rexp[w] = e;
+  const size_t plane = (size_t)rows * cols;
+  for (int j = lane; j < cols; j += 32) {
+    double R = ldexp(row[j], -e);
+    for (int s = 0; s < S; ++s) {
+      const double qv = rint(R * 64.0);
+      out[(size_t)s * plane + w * (long long)cols + j] = __double2bfloat16(qv);
+      R = R * 64.0 - qv;
+    }
+  }
+}
+
 __global__ void k_to_bf16_f64(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = __double2bfloat16(src[e]);
@@ -542,6 +848,69 @@ cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const
     if (e != cudaSuccess) return e;
     k_apply_tc_comp<<<grid, COMP_THREADS, COMP_SMEM_BYTES, s>>>(mA, mX, nt, nx, chunk, accumulate ? 1 : 0, Y);
   }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+bool apply_tc_exact_supported(int nt, int nx, int n_rhs, int n_slices) {
+  return apply_tc_supported(nt, nx, n_rhs) && nt <= kExactMaxSteps && n_slices >= kExactMinSlices &&
+         n_slices <= kExactMaxSlices;
+}
+
+cudaError_t exact_slices_launch(const double* src, long long rows, int cols, int n_slices, void* slices,
+                                int* row_exp, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  const int threads = 256;
+  const long long blocks = (rows * 32 + threads - 1) / threads;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_exact_slices<<<(unsigned)blocks, threads, 0, s>>>(src, rows, cols, n_slices,
+                                                     static_cast<__nv_bfloat16*>(slices), row_exp);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+namespace {
+template <int S>
+cudaError_t launch_exact_s(const CUtensorMap& mA, const CUtensorMap& mX, dim3 grid, const int* eA, const int* eX,
+                           int nt, int nx, double* Y, cudaStream_t s) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_apply_tc_exact<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EX_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  k_apply_tc_exact<S><<<grid, EX_THREADS, EX_SMEM_BYTES, s>>>(mA, mX, eA, eX, nt, nx, Y);
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_slices, const int* A_exp, int n_rhs,
+                                  const void* X_slices, const int* X_exp, double* Y, cudaStream_t s) {
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // A slices [S][nt][nx][nx] and x slices [S][n_rhs][nt][nx], BF16, as 4-D maps
+  CUtensorMap mA, mX;
+  const cuuint64_t dimA[4] = {(cuuint64_t)nx, (cuuint64_t)nx, (cuuint64_t)nt, (cuuint64_t)n_slices};
+  const cuuint64_t strA[3] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * nx * 2, (cuuint64_t)nt * nx * nx * 2};
+  const cuuint64_t dimX[4] = {(cuuint64_t)nx, (cuuint64_t)nt, (cuuint64_t)n_rhs, (cuuint64_t)n_slices};
+  const cuuint64_t strX[3] = {(cuuint64_t)nx * 2, (cuuint64_t)nt * nx * 2, (cuuint64_t)n_rhs * nt * nx * 2};
+  const cuuint32_t boxA[4] = {BK, BM, 1, 1}, boxX[4] = {BK, BN, 1, 1}, es[4] = {1, 1, 1, 1};
+  CUresult r = enc(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(A_slices), dimA, strA, boxA, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  r = enc(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(X_slices), dimX, strX, boxX, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const dim3 grid((nx + BM - 1) / BM, (nt + BN - 1) / BN, n_rhs);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (n_slices) {
+    case 4: e = launch_exact_s<4>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
+    case 5: e = launch_exact_s<5>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
+    case 6: e = launch_exact_s<6>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
+    case 7: e = launch_exact_s<7>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
+    case 8: e = launch_exact_s<8>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }

@@ -19,5 +19,15 @@ cudaError_t tc_error_reset(cudaStream_t s);
 // times out and reports through the error word; 0 restores normal operation.
 void tc_set_stall(long long cycles);
 cudaError_t tc_error_read(int* flag, cudaStream_t s);
+// Exact-slice product (FP64-grade): S = n_slices integer slices of 6 bits per
+// operand with power-of-two row scales (see exact_slices_launch), every slice
+// pair with s + t < S multiplied exactly on the BF16 tensor cores.
+constexpr int kExactMinSlices = 4, kExactMaxSlices = 8;
+bool apply_tc_exact_supported(int nt, int nx, int n_rhs, int n_slices);
+// slices [n_slices][rows][cols] BF16, row_exp [rows]
+cudaError_t exact_slices_launch(const double* src, long long rows, int cols, int n_slices, void* slices,
+                                int* row_exp, cudaStream_t s);
+cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_slices, const int* A_exp, int n_rhs,
+                                  const void* X_slices, const int* X_exp, double* Y, cudaStream_t s);
 cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s);
 }  // namespace stbem
