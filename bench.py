@@ -212,10 +212,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_batched(ctx, dev, stream, n_src=256):
+def run_batched(ctx, dev, stream, n_src=256, fp64_residual=False):
     """square512 with 256 right-hand sides g_k = U*(x - y_k, t), y_k seeded on
-    the annulus 1.2 < |y - (0.5, 0.5)| < 3: batched tensor-core solve, timed
-    with CUDA events, beside one FP64 single-right-hand-side solve."""
+    the annulus 1.2 < |y - (0.5, 0.5)| < 3: batched tensor-core solve to
+    FP64-solve accuracy, timed with CUDA events, beside one FP64
+    single-right-hand-side solve.  F and the final refinement residuals use
+    the exact-slice tensor-core product (7 slices); with fp64_residual the
+    same solve on FP64 CUDA-core residuals is timed as well."""
     import torch
     import workloads as W
     import paper_1811_05224_gb300 as P
@@ -234,74 +237,128 @@ def run_batched(ctx, dev, stream, n_src=256):
     V3 = P.bf16_split3(ctx, V)
     Db = P.to_bf16(ctx, D32)
     L = P.lumped_mass(ctx, mesh)
+    Vx = P.exact_slices(ctx, V, 7)
+    Kx = P.exact_slices(ctx, K, 7)
     ys = W.annulus_sources(n_src, seed=4)
     e[4].record(stream)
-    # F = 1/2 M G + K G with the FP64 K product of all 256 right-hand sides
-    G, F = P.rhs_batched(ctx, mesh, K, ys)
+    # F = 1/2 M G + K G with the exact-slice K product of all 256 right-hand sides
+    G, F = P.rhs_batched(ctx, mesh, Kx, ys)
     e[5].record(stream)
     # BF16 tensor-core inner solves; refinement on the three-slice residual,
-    # then on the FP64 residual to 1e-8 (FP64-solve accuracy)
-    Wb, infos = P.solve_batched(ctx, V3, F, Db, L, tol=1e-8, inner_tol=1e-2, restart=40, max_iter=600, V64=V)
+    # then on the exact-slice residual to 1e-8 (FP64-solve accuracy)
+    Wb, infos = P.solve_batched(ctx, V3, F, Db, L, tol=1e-8, inner_tol=1e-2, restart=40, max_iter=600, V64=Vx)
     e[6].record(stream)
     torch.cuda.synchronize(dev)
-    # tensor-core product alone: V (BF16) on all right-hand sides
+    s0, s1 = ev(), ev()
+    # products alone on all right-hand sides: BF16, compensated BF16, exact-slice
     xb = P.to_bf16(ctx, Wb)
     for _ in range(2):
         P.apply_tc(ctx, V3[0], xb)
-    a0, a1 = ev(), ev()
-    a0.record(stream)
-    P.apply_tc(ctx, V3[0], xb)
-    a1.record(stream)
-    torch.cuda.synchronize(dev)
-    tc_ms = a0.elapsed_time(a1)
-    # the same product with compensated accumulation (partials of 4 K steps),
-    # as used for the hi x hi slice product of the refinement residual
-    a0.record(stream)
-    P.apply_tc(ctx, V3[0], xb, chunk=4)
-    a1.record(stream)
-    torch.cuda.synchronize(dev)
-    tc4_ms = a0.elapsed_time(a1)
+
+    def timed(fn):
+        s0.record(stream)
+        r = fn()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        return r, s0.elapsed_time(s1)
+
+    _, tc_ms = timed(lambda: P.apply_tc(ctx, V3[0], xb))
+    # the compensated accumulation (partials of 4 K steps) of the hi x hi slice
+    # product of the three-slice residual
+    _, tc4_ms = timed(lambda: P.apply_tc(ctx, V3[0], xb, chunk=4))
+    xwork = torch.empty(int(_exact_work_bytes(ctx, nt, nx, n_src, 7)), dtype=torch.uint8, device=dev)
+    yx = torch.empty_like(Wb)
+    P.apply_exact(ctx, Vx, Wb, out=yx, work=xwork)
+    _, ex_ms = timed(lambda: P.apply_exact(ctx, Vx, Wb, out=yx, work=xwork))
+    _, sl_ms = timed(lambda: P.exact_slices(ctx, Wb, 7))
     tc_flops = 2.0 * nx * nx * nt * (nt + 1) / 2 * n_src
+    # FP64 CUDA-core product of 8 right-hand sides: accuracy of the exact-slice
+    # product and of F, and the FP64 rate
+    y64, y64_ms = timed(lambda: P.apply(ctx, V, Wb[:8]))
+    # error against the row-scale bound n_x sum_d max|V[d][i]| max|W[b][m - d]|
+    # (the exact-slice error is relative to row maxima, not to |V| |W|
+    # elementwise: early steps of W span hundreds of decades along a row)
+    ra = V.abs().amax(dim=2)
+    rx = Wb[:8].abs().amax(dim=2)
+    Mb = torch.zeros_like(y64)
+    for d in range(nt):
+        Mb[:, d:, :] += rx[:, :nt - d, None] * ra[d][None, None, :]
+    Mb *= nx
+    ex_err = float(((yx[:8] - y64).abs() / Mb.clamp_min(1e-300)).max())
+    ex_norm = float(max((yx[b] - y64[b]).norm() / y64[b].norm() for b in range(8)))
+    del ra, rx, Mb
+    _, F8 = P.rhs_batched(ctx, mesh, K, ys[:8])
+    f_rel = float(max((F[b] - F8[b]).norm() / F8[b].norm() for b in range(8)))
+    fp64_solve = None
+    if fp64_residual:
+        s0.record(stream)
+        _, F64 = P.rhs_batched(ctx, mesh, K, ys)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        rhs64_ms = s0.elapsed_time(s1)
+        (W64, inf64), solve64_ms = timed(lambda: P.solve_batched(ctx, V3, F64, Db, L, tol=1e-8, inner_tol=1e-2,
+                                                                 restart=40, max_iter=600, V64=V))
+        fp64_solve = {"rhs_ms": rhs64_ms, "solve_ms": solve64_ms,
+                      "inner_iterations": max(i["iterations"] for i in inf64),
+                      "note": "the same solve with F and the final residuals from the FP64 CUDA-core product"}
+        del F64, W64
     # one FP64 single-right-hand-side solve of the same system for comparison
     D64 = P.assemble(ctx, mesh, "D")
     g1, f1 = P.rhs(ctx, mesh, K, ys[0])
-    s0, s1 = ev(), ev()
-    s0.record(stream)
-    w1, info1 = P.solve(ctx, V, f1, D64, L, tol=1e-8)
-    s1.record(stream)
-    torch.cuda.synchronize(dev)
-    one_ms = s0.elapsed_time(s1)
+    (w1, info1), one_ms = timed(lambda: P.solve(ctx, V, f1, D64, L, tol=1e-8))
     # accuracy reference: the FP64 solve of right-hand side 0 to 1e-11
     w_acc, _ = P.solve(ctx, V, f1, D64, L, tol=1e-11)
     rel = float((Wb[0] - w_acc).norm() / w_acc.norm())
     rel_fp64_path = float((w1 - w_acc).norm() / w_acc.norm())
-    r0 = F[0] - P.apply(ctx, V, Wb[0])
+    r0 = f1 - P.apply(ctx, V, Wb[0])
     peaks = _peaks()
     bf16_peak = float(peaks.get("bf16_tflops", 1867.6))
+    ex_exec = tc_flops * 28                                   # 7 slices: 28 slice-pair products
     out = {
         "workload": "square512 x 256 sources (annulus 1.2..3, seed 4)",
         "assembly_ms": {"V_f64": e[0].elapsed_time(e[1]), "K_f64": e[1].elapsed_time(e[2]),
                         "D_f32": e[2].elapsed_time(e[3])},
+        "slices_ms": e[3].elapsed_time(e[4]),
+        "slices_note": "three BF16 slices of V, BF16 D, exact slices (7 x 6 bits) of V and K",
         "rhs_ms": e[4].elapsed_time(e[5]),
-        "rhs_note": "F = 1/2 M G + K G, FP64 CUDA-core K product of all right-hand sides",
+        "rhs_note": "F = 1/2 M G + K G, exact-slice tensor-core K product of all right-hand sides",
+        "F_rel_diff_vs_fp64_product_8rhs": f_rel,
         "solve_ms": e[5].elapsed_time(e[6]),
-        "solve_note": "BF16 tensor-core lockstep GMRES, refinement on three-slice then FP64 residuals, tol 1e-8",
+        "solve_note": "BF16 tensor-core lockstep GMRES, refinement on three-slice then exact-slice residuals, tol 1e-8",
         "inner_iterations": max(i["iterations"] for i in infos),
-        "max_fp64_rel_residual": max(i["rel_residual"] for i in infos),
-        "fp64_rel_residual_rhs0": float(r0.norm() / F[0].norm()),
+        "max_rel_residual": max(i["rel_residual"] for i in infos),
+        "fp64_rel_residual_rhs0": float(r0.norm() / f1.norm()),
         "w_rel_diff_vs_fp64_solve_1e-11_rhs0": rel,
         "fp64_path_1e-8_w_rel_diff_vs_fp64_solve_1e-11_rhs0": rel_fp64_path,
         "fp64_single_solve_ms": one_ms, "fp64_single_solve_iterations": info1["iterations"],
         "fp64_256_sequential_solves_ms_projected": one_ms * n_src,
+        "fp64_residual_solve": fp64_solve,
         "tc_apply": {"ms": tc_ms, "tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                      "frac_of_bf16_peak": tc_flops / (tc_ms * 1e-3) / 1e12 / bf16_peak,
                      "peak_tflops": bf16_peak, "peak": "measured bf16 burst (MEASURED_PEAKS.json)"},
         "tc_apply_compensated_chunk4": {"ms": tc4_ms, "tflops": tc_flops / (tc4_ms * 1e-3) / 1e12,
                                         "frac_of_bf16_peak": tc_flops / (tc4_ms * 1e-3) / 1e12 / bf16_peak},
+        "exact_apply": {"ms": ex_ms, "slice_x_ms": sl_ms,
+                        "fp64_equivalent_tflops": tc_flops / (ex_ms * 1e-3) / 1e12,
+                        "bf16_tflops_executed": ex_exec / (ex_ms * 1e-3) / 1e12,
+                        "frac_of_bf16_peak": ex_exec / (ex_ms * 1e-3) / 1e12 / bf16_peak,
+                        "max_err_over_rowmax_bound_8rhs": ex_err,
+                        "max_normwise_rel_err_8rhs": ex_norm,
+                        "fp64_cuda_core_8rhs_ms": y64_ms,
+                        "fp64_cuda_core_tflops": tc_flops * 8 / n_src / (y64_ms * 1e-3) / 1e12,
+                        "note": "7 slices x 6 bits, 28 slice-pair BF16 products, exact FP32 group sums, "
+                                "double-float combination; includes slicing W"},
     }
-    del V, K, D32, D64, V3, Db, G, F, Wb
+    del V, K, D32, D64, V3, Db, G, F, Wb, Vx, Kx, xwork, yx
     torch.cuda.empty_cache()
     return out
+
+
+def _exact_work_bytes(ctx, nt, nx, B, S):
+    import ctypes
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_apply_exact_workspace_bytes(nt, nx, B, S, ctypes.byref(nb)))
+    return nb.value
 
 
 def run_grad(ctx, dev, stream):
@@ -887,7 +944,7 @@ def run_ours(args):
 
     batched = None
     if not args.no_batched and world == 1:
-        batched = run_batched(ctx, dev, stream)
+        batched = run_batched(ctx, dev, stream, fp64_residual=args.batched_fp64_residual)
     grad = None
     if not args.no_grad and world == 1:
         grad = run_grad(ctx, dev, stream)
@@ -1061,6 +1118,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-right-hand-side square512 component")
+    ap.add_argument("--batched-fp64-residual", action="store_true",
+                    help="also time the batched solve on FP64 CUDA-core residuals (about a minute)")
     ap.add_argument("--no-grad", action="store_true", help="skip the star256 differentiation component")
     ap.add_argument("--no-ragged", action="store_true", help="skip the 64-problem ragged component")
     ap.add_argument("--no-initial", action="store_true", help="skip the Section 4 example (M_h^0) component")
@@ -1142,8 +1201,8 @@ def run_precision(ctx, dev, stream):
 
 def run_component(args):
     """One kernel family on a small case, for profiling: 'tc' = the BF16
-    tensor-core product (plain and compensated) of a unit-square V with
-    --rhs right-hand sides; 'grad' = the gradient kernels on a 16-corner star
+    tensor-core products (plain, compensated and exact-slice) of a
+    unit-square V with --rhs right-hand sides; 'grad' = the gradient kernels on a 16-corner star
     with N_x = N_t = --size.  Warm-up, then timed calls with CUDA events."""
     import torch
     import workloads as W
@@ -1164,21 +1223,30 @@ def run_component(args):
         return 0
     if args.component == "tc":
         mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
-        Vb = P.to_bf16(ctx, P.assemble(ctx, mesh, "V"))
+        V = P.assemble(ctx, mesh, "V")
+        Vb = P.to_bf16(ctx, V)
+        Vx = P.exact_slices(ctx, V, 7)
+        del V
         g = torch.Generator(device="cpu").manual_seed(3)
-        xb = torch.randn((args.rhs, n, n), generator=g, dtype=torch.float64).to(dev).to(torch.bfloat16)
+        x64 = torch.randn((args.rhs, n, n), generator=g, dtype=torch.float64).to(dev)
+        xb = x64.to(torch.bfloat16)
         y = torch.empty((args.rhs, n, n), dtype=torch.float64, device=dev)
+        xwork = torch.empty(int(_exact_work_bytes(ctx, n, n, args.rhs, 7)), dtype=torch.uint8, device=dev)
         flops = 2.0 * n * n * n * (n + 1) / 2 * args.rhs
-        for chunk in (0, 4):
+        runs = {"plain": lambda: P.apply_tc(ctx, Vb, xb, out=y),
+                "compensated4": lambda: P.apply_tc(ctx, Vb, xb, out=y, chunk=4),
+                "exact7": lambda: P.apply_exact(ctx, Vx, x64, out=y, work=xwork)}
+        for name, fn in runs.items():
             for _ in range(2):
-                P.apply_tc(ctx, Vb, xb, out=y, chunk=chunk)
+                fn()
             e0, e1 = ev(), ev()
             e0.record(stream)
-            P.apply_tc(ctx, Vb, xb, out=y, chunk=chunk)
+            fn()
             e1.record(stream)
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1)
-            out["plain" if chunk == 0 else "compensated4"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+            out[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+        out["exact7"]["bf16_tflops_executed"] = out["exact7"]["tflops"] * 28
         out["rhs"] = args.rhs
     else:
         S = W.subdivision_matrix(16, n // 16)

@@ -451,10 +451,16 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_hi, cons
  * multiplies every slice pair (s, t) with s + t < n_slices on the tensor
  * cores; the integer sums of one lag, one s + t and at most 1024 columns are
  * exact in the FP32 accumulator, and they are combined in double-float with
- * their powers of two, so the only errors are the dropped pairs and the final
- * rounding: about 2^(-6 n_slices) |A| |x| per entry (n_slices = 7: a few
- * 1e-12 of |A| |x|, versus ~1e-7 for stbem_apply_tc3 and ~4e-3 for one BF16
- * product).  n_slices is 4..8. */
+ * their powers of two, so the only errors are the truncated slice tails and
+ * the dropped pairs, relative to the row scales:
+ *   |y[b][m][i] - (A x)[b][m][i]|
+ *     <= 2^(-6 n_slices) (1 + n_slices / 4) n_x sum_d 2^(eA[d][i] + eX[b][m-d]).
+ * Rows whose entries span many decades (the early time steps of a density
+ * with a distant source) keep this accuracy relative to their maxima only.
+ * Normwise the product is accurate to a few 1e-13 at n_slices = 7 on the
+ * batched heat problem (versus ~1e-7 for stbem_apply_tc3 and ~4e-3 for one
+ * BF16 product).  Contributions more than 2^-125 below
+ * 2^(max_d eA[d][i] + max_{n <= m} eX[b][n]) are dropped.  n_slices is 4..8. */
 typedef struct stbem_exact_operand {
   int n_slices;         /* 4..8 */
   const void* slices;   /* device, BF16 [n_slices][rows][cols], 16-byte aligned */
@@ -521,8 +527,8 @@ int stbem_solve_batched(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void*
 
 /* stbem_solve_batched with the exact-slice operator V_exact (stbem_exact_slices
  * of the FP64 V) in place of dev_V64: once every relative residual is below
- * 2e-6, refinement continues on F - V W from the exact-slice product (about
- * 2^(-6 n_slices) |V| |W|, a few 1e-12 at n_slices = 7) on the tensor cores
+ * 2e-6, refinement continues on F - V W from the exact-slice product (normwise
+ * a few 1e-13 at n_slices = 7; see stbem_exact_operand) on the tensor cores
  * instead of the FP64 CUDA-core product.  Workspace:
  * stbem_solve_batched_exact_workspace_bytes() (the base workspace plus the
  * slices of W), 256-byte aligned.  Requires, besides the sizes of

@@ -516,9 +516,10 @@ def exact_slices(ctx: Context, src, n_slices: int = 7):
 
 
 def apply_exact(ctx: Context, A, x, out=None, work=None):
-    """Block-Toeplitz product on the tensor cores to FP64-grade accuracy (about
-    2^(-6 n_slices) |A| |x|): A an ExactOperand of lag blocks, x FP64
-    (n_rhs, n_t, n_x) or (n_t, n_x), or an ExactOperand of it."""
+    """Block-Toeplitz product on the tensor cores to FP64-grade accuracy
+    relative to the row scales (at most 2^(-6 n_slices) (1 + n_slices / 4)
+    n_x sum_d 2^(eA[d][i] + eX[b][m - d])): A an ExactOperand of lag blocks,
+    x FP64 (n_rhs, n_t, n_x) or (n_t, n_x), or an ExactOperand of it."""
     n_t, n_x = A.shape[0], A.shape[1]
     sa = A.c_struct()
     if isinstance(x, ExactOperand):
@@ -544,7 +545,7 @@ def rhs_batched(ctx: Context, mesh: Mesh, K, y_stars):
     """(G, F) for many sources: G[k] vertex time averages of U*(x - y_k, t),
     F = 1/2 M_h G + K_h G.  K is the FP64 operator (an FP64 CUDA-core product
     of all right-hand sides: F to FP64 accuracy), its ExactOperand (the
-    exact-slice tensor-core product, a few 1e-12 of |K||G| at 7 slices) or a
+    exact-slice tensor-core product, normwise a few 1e-13 at 7 slices) or a
     tuple of its three BF16 slices (the compensated tensor-core product, a few
     1e-7 of |K||G|)."""
     ys = np.ascontiguousarray(np.asarray(y_stars, dtype=np.float64).reshape(-1))

@@ -80,10 +80,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
 // After a failed pipeline wait some TMA loads may still be in flight into this
 // CTA's shared memory: the producer waits (bounded) for the last load it
 // issued on every stage before the CTA releases its resources and exits.
-__device__ __forceinline__ void drain_loads(uint64_t* full, int issued) {
-  for (int s = 0; s < STAGES && s < issued; ++s) {
-    const int last = s + ((issued - 1 - s) / STAGES) * STAGES;   // last iteration that used stage s
-    mbar_wait(&full[s], static_cast<uint32_t>(last / STAGES) & 1);
+__device__ __forceinline__ void drain_loads(uint64_t* full, int issued, int stages = STAGES) {
+  for (int s = 0; s < stages && s < issued; ++s) {
+    const int last = s + ((issued - 1 - s) / stages) * stages;   // last iteration that used stage s
+    mbar_wait(&full[s], static_cast<uint32_t>(last / stages) & 1);
   }
 }
 
@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(stallbar + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
+  // grid (row tiles, right-hand sides, step tiles), step tiles longest first
+  const int i0 = blockIdx.x * BM, b = blockIdx.y, m0 = (gridDim.z - 1 - blockIdx.z) * BN;
   const int dmax = min(m0 + BN - 1, nt - 1);  // lags for which some m - d >= 0
   const int nj = (nx + BK - 1) / BK;
   const int iters = (dmax + 1) * nj;
@@ -350,7 +351,8 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
+  // grid (row tiles, right-hand sides, step tiles), step tiles longest first
+  const int i0 = blockIdx.x * BM, b = blockIdx.y, m0 = (gridDim.z - 1 - blockIdx.z) * BN;
   const int dmax = min(m0 + BN - 1, nt - 1);
   const int nj = (nx + BK - 1) / BK;
   const int iters = (dmax + 1) * nj;
@@ -504,8 +506,9 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
 // and added into a double-float (FP32 sum + FP32 error by Knuth's two-sum) per
 // output y[b][m][i], relative to 2^{max_d eA[d][i] + max_{n <= m} eX[b][n]}
 // (an upper bound of every contribution's scale; output steps with only small
-// x keep their own small scale).  Pairs with s + t >= S are dropped: with
-// S = 7 the product is accurate to a few 1e-12 of |A| |x|.
+// x keep their own small scale).  Pairs with s + t >= S are dropped.  The
+// error is relative to the row scales, at most 2^{-6S} (1 + S / 4) n_x
+// sum_d 2^{eA[d][i] + eX[b][m-d]} (S = 7: a few 1e-12 of that sum).
 //   warp 0: TMA producer, warp 1: MMA issuer (TMEM owner), warps 2..17: the
 //   epilogue; warp w owns TMEM lanes 32 (w % 4) .. + 31 and columns
 //   32 ((w - 2) / 4) .. + 31 of the tile.  The double-float sums live in TMEM
@@ -518,8 +521,10 @@ constexpr int EX_THREADS = 576;
 constexpr int EX_EPI_WARPS = 16;
 constexpr uint32_t EX_TMEM_COLS = 512;
 constexpr uint32_t EX_HI_COL = 256, EX_LO_COL = 384;
+constexpr int EX_STAGES = 6;                     // 192 KB of operands in flight
 constexpr int kExactMaxSteps = 4096;             // eX of one right-hand side staged in shared memory
-constexpr size_t EX_SMEM_BYTES = 1024 + STAGES * (size_t)STAGE_BYTES + 512 + 2 * kExactMaxSteps * sizeof(int);
+constexpr size_t EX_SMEM_BYTES =
+    1024 + EX_STAGES * (size_t)STAGE_BYTES + 512 + 2 * kExactMaxSteps * sizeof(short);
 
 __device__ __forceinline__ void tma_load_4d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1,
                                             int c2, int c3) {
@@ -545,25 +550,29 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
   unsigned char* smA = reinterpret_cast<unsigned char*>(base);
-  unsigned char* smB = smA + STAGES * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smB + STAGES * B_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;   // [2]: group in buffer k complete
+  unsigned char* smB = smA + EX_STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smB + EX_STAGES * B_BYTES);
+  uint64_t* empty = full + EX_STAGES;
+  uint64_t* acc_full = empty + EX_STAGES;   // [2]: group in buffer k complete
   uint64_t* acc_empty = acc_full + 2;    // [2]: buffer k drained by the epilogue
   uint64_t* done = acc_empty + 2;        // every MMA issued by warp 1 complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  int* eXs = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(full) + 512);   // this b's step scales
-  int* eXp = eXs + kExactMaxSteps;                                                     // their prefix maxima
+  // this b's step scales and their prefix maxima (16-bit: -16384 .. 1025)
+  short* eXs = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(full) + 512);
+  short* eXp = eXs + kExactMaxSteps;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * BM, m0 = blockIdx.y * BN, b = blockIdx.z;
+  // grid (row tiles, right-hand sides, step tiles): the step tiles run in
+  // decreasing order of m0, so the longest tiles (most lags) start first and
+  // the short ones fill the tail
+  const int i0 = blockIdx.x * BM, b = blockIdx.y, m0 = (gridDim.z - 1 - blockIdx.z) * BN;
   const int dmax = min(m0 + BN - 1, nt - 1);
   const int nj = (nx + BK - 1) / BK;
   const int nb = (nj + kExactJSteps - 1) / kExactJSteps;
   const int ngroups = (dmax + 1) * S * nb;       // (d, k, jb), jb fastest
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < EX_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -588,8 +597,8 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
       }
       pm = max(pm, carry);
       if (n < nt) {
-        eXs[n] = v;
-        eXp[n] = pm;
+        eXs[n] = static_cast<short>(v);
+        eXp[n] = static_cast<short>(pm);
       }
       carry = __shfl_sync(0xffffffffu, pm, 31);
     }
@@ -610,8 +619,8 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
         const int j_lo = jb * kExactJSteps, j_hi = min(nj, j_lo + kExactJSteps);
         for (int s = 0; s <= k && ok; ++s)
           for (int jc = j_lo; jc < j_hi; ++jc, ++it) {
-            const int st = it % STAGES;
-            const uint32_t round = static_cast<uint32_t>(it / STAGES);
+            const int st = it % EX_STAGES;
+            const uint32_t round = static_cast<uint32_t>(it / EX_STAGES);
             if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1)) {
               ok = false;
               break;
@@ -638,8 +647,8 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
         const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
         const int it_end = it + nsteps;
         for (int first = 1; it < it_end; ++it, first = 0) {
-          const int st = it % STAGES;
-          const uint32_t round = static_cast<uint32_t>(it / STAGES);
+          const int st = it % EX_STAGES;
+          const uint32_t round = static_cast<uint32_t>(it / EX_STAGES);
           if (!mbar_wait(&full[st], round & 1)) {
             ok = false;
             break;
@@ -727,7 +736,7 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
   }
   if (!ok) atomicExch(&g_tc_error, 1);
   // on any failure, let the loads already issued land before exiting
-  if (__syncthreads_or(!ok) && warp == 0 && lane == 0) drain_loads(full, issued);
+  if (__syncthreads_or(!ok) && warp == 0 && lane == 0) drain_loads(full, issued, EX_STAGES);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -830,7 +839,7 @@ cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const
   const int bn = (chunk <= 0 && nt > 128) ? 256 : BN;
   cudaError_t e = make_maps(nt, nx, A_bf16, n_rhs, X_bf16, &mA, &mX, bn);
   if (e != cudaSuccess) return e;
-  const dim3 grid((nx + BM - 1) / BM, (nt + bn - 1) / bn, n_rhs);
+  const dim3 grid((nx + BM - 1) / BM, n_rhs, (nt + bn - 1) / bn);
   if (chunk <= 0 && bn == 256) {
     e = cudaFuncSetAttribute(k_apply_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TcTile<256>::smem_bytes);
@@ -900,7 +909,7 @@ cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_sl
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const dim3 grid((nx + BM - 1) / BM, (nt + BN - 1) / BN, n_rhs);
+  const dim3 grid((nx + BM - 1) / BM, n_rhs, (nt + BN - 1) / BN);
   cudaError_t e = cudaErrorInvalidValue;
   switch (n_slices) {
     case 4: e = launch_exact_s<4>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;

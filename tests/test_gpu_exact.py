@@ -113,8 +113,9 @@ def test_apply_exact_integer_data_is_exact(ctx):
 
 def test_apply_exact_wide_dynamic_range(ctx):
     """Lag blocks decaying by 2^-40 per lag, right-hand-side steps from 1e-80
-    to 1 and a zero step: each output keeps its accuracy relative to its own
-    |A| |x| (the per-output reference scale follows the largest step so far)."""
+    to 1 and a zero step, each row without internal range: each output keeps
+    its accuracy relative to its own |A| |x| (per-row scales, and a
+    per-output reference scale that follows the largest step so far)."""
     import paper_1811_05224_gb300 as P
     rng = np.random.default_rng(13)
     nt, nx, B = 9, 48, 2
@@ -129,6 +130,29 @@ def test_apply_exact_wide_dynamic_range(ctx):
     assert np.all(err <= 16 * 2.0 ** -42 * mag + 2 * nt * nx * U64 * mag + 1e-300), \
         float((err / (mag + 1e-300)).max())
     assert np.all(np.abs(y[:, 0]) > 0)           # the 1e-80 step is not flushed
+
+
+def test_apply_exact_rows_with_internal_range(ctx):
+    """Rows whose entries span hundreds of decades (like the early steps of
+    a density whose source is far away: e^(-r^2 / 4t) along the boundary) and
+    local lag blocks: the error stays within the row-scale bound, and
+    normwise within 32 2^-42 (about 4 2^-42 in a CPU emulation); small
+    entries of such rows are not resolved relative to themselves (the
+    documented limit of per-row scales)."""
+    import paper_1811_05224_gb300 as P
+    rng = np.random.default_rng(19)
+    nt, nx, B = 12, 64, 2
+    j = np.arange(nx)
+    A = rng.standard_normal((nt, nx, nx)) * np.exp(-0.5 * (j[:, None] - j[None, :]) ** 2)[None]
+    t = (np.arange(nt) + 1.0) / nt
+    x = rng.standard_normal((B, nt, nx)) * np.exp(-(j[None, None, :] / 8.0) ** 2 / (4 * t[None, :, None]))
+    Ax = P.exact_slices(ctx, torch.as_tensor(A).cuda(), 7)
+    y = P.apply_exact(ctx, Ax, torch.as_tensor(x).cuda()).cpu().numpy()
+    ref, mag, M = _ref(A, x)
+    err = np.abs(y - ref)
+    assert np.all(err <= _bound(7, M, mag, nt, nx))
+    for b in range(B):
+        assert np.linalg.norm(y[b] - ref[b]) <= 32 * 2.0 ** -42 * np.linalg.norm(ref[b])
 
 
 def test_apply_exact_error_falls_with_slices(ctx):
