@@ -440,6 +440,39 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_hi, cons
                     const void* dev_A_lo, int n_rhs, const double* dev_x, double* dev_y, void* dev_work,
                     size_t work_bytes);
 
+/* ---- Tuned launch parameters ---------------------------------------------------
+ * A process-wide table of tuned launch parameters (the plain tensor-core
+ * product's tile width, the ragged product's tile family and lag-chunk
+ * length), keyed by "device|kernel|shape" strings with "name=value" values,
+ * optionally mirrored to a text file ("key<TAB>value" lines after a header;
+ * rewritten whole through a temporary file on every store) so that a later
+ * process reuses earlier measurements.  The STBEM_TUNE_CACHE environment
+ * variable names the default file.  These calls make no CUDA call.
+ * stbem_tune_cache_path: NULL or "" keeps the table in memory only; otherwise
+ * the file's entries are merged in (a missing file is an empty table;
+ * STBEM_ERR_ARG if it exists but cannot be read).
+ * stbem_tune_cache_get: STBEM_OK and the value (NUL-terminated) in host_value,
+ * STBEM_ERR_ARG if the key is absent, STBEM_ERR_NOMEM if cap is too small.
+ * stbem_tune_cache_put: keys and values must be non-empty with no tabs or line
+ * breaks (else STBEM_ERR_ARG, also when the file cannot be written).
+ * stbem_tune_cache_clear: drops the in-process entries, not the file's. */
+int stbem_tune_cache_path(const char* path);
+int stbem_tune_cache_get(const char* key, char* host_value, size_t cap);
+int stbem_tune_cache_put(const char* key, const char* value);
+int stbem_tune_cache_clear(void);
+
+/* Tile-width tuner of the plain tensor-core product (stbem_apply_tc, and the
+ * products inside stbem_solve_batched): times 128 x 128 and 128 x 256 output
+ * tiles (steps per tile; 256 only when n_t > 128) on this shape (A, x, y as in
+ * stbem_apply_tc; y is overwritten) and records the faster in the tune cache,
+ * which every later product of the same (n_t, n_x, n_rhs) on this device
+ * consults; untuned shapes take 256 for n_t > 128.  With a cached entry the
+ * call only reports it (*from_cache = 1).  tile_n, from_cache may be NULL.
+ * Blocks the host.  Errors as stbem_apply_tc, and STBEM_ERR_ARG when the
+ * cache file cannot be written. */
+int stbem_tc_tune(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_bf16, int n_rhs, const void* dev_x_bf16,
+                  double* dev_y, int* tile_n, int* from_cache);
+
 /* ---- Exact-slice products (FP64-grade accuracy on the BF16 tensor cores) -----
  * The block-Toeplitz product of eq. (5)'s lag blocks with many right-hand
  * sides, y[b][m] = sum_{d <= m} A[d] x[b][m - d] (the product the GMRES of
@@ -581,14 +614,22 @@ int stbem_ragged_lumped_mass(stbem_ctx* ctx, stbem_ragged* batch, double* dev_L)
 int stbem_ragged_apply_workspace_bytes(const stbem_ragged* batch, size_t* bytes);
 int stbem_ragged_apply(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void* dev_A, const double* dev_x,
                        double* dev_y, void* dev_work, size_t work_bytes);
-/* Autotuner: times the product with A for each candidate lag-chunk length
- * (32 .. 512 lags per partial; dev_x, dev_y: batch vectors used as input and
- * output) with CUDA events and keeps the fastest for every later product and
- * solve of this batch.  Blocks the host.  stbem_ragged_tune_report returns the
- * candidates tried and their times (ms). */
+/* Autotuner: times the product with A (dev_x, dev_y: batch vectors used as
+ * input and output) with CUDA events for each candidate tile family (FP32
+ * products: the register-tiled kernel, which needs every N_x % 4 == 0, and
+ * the generic tiles; FP64: the generic tiles) and lag-chunk length (32 .. 512
+ * lags per partial), and keeps the fastest for every later product and solve
+ * of this batch.  The choice is recorded in the tune cache (stbem_tune_cache_*)
+ * under the device, the precision and the batch's (N_x, N_t) list; when the
+ * cache already holds an entry for them the call applies it without timing.
+ * lags_per_chunk / tiles32 (may be NULL) receive the choice.  Blocks the host.
+ * stbem_ragged_tune_report returns the candidates timed by the last call
+ * (lag-chunk length, tile family 1 = register tiles, time in ms; none when the
+ * choice came from the cache, *from_cache = 1). */
 int stbem_ragged_tune(stbem_ctx* ctx, stbem_ragged* batch, int prec, const void* dev_A, const double* dev_x,
-                      double* dev_y, void* dev_work, size_t work_bytes, int* lags_per_chunk);
-int stbem_ragged_tune_report(const stbem_ragged* batch, int max_n, int* candidates, float* ms, int* n_out);
+                      double* dev_y, void* dev_work, size_t work_bytes, int* lags_per_chunk, int* tiles32);
+int stbem_ragged_tune_report(const stbem_ragged* batch, int max_n, int* candidates, int* tiles32, float* ms,
+                             int* n_out, int* from_cache);
 
 /* Right-hand sides of eq. (4) for every problem, g = U*(x - y_p*, t) with the
  * source host_ystar[2p], [2p+1]: dev_g (vertex time averages) and

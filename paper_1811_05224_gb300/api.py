@@ -602,6 +602,47 @@ def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1
     return out, res
 
 
+def tune_cache(path):
+    """Back the tuned-launch-parameter cache with a text file (None: memory
+    only); entries already in the file are loaded.  The STBEM_TUNE_CACHE
+    environment variable sets the default file."""
+    code = capi.load().stbem_tune_cache_path(None if path is None else str(path).encode())
+    if code != capi.STBEM_OK:
+        raise capi.StbemError(code, "tune cache file %s cannot be read" % path)
+
+
+def tune_cache_get(key: str):
+    """The cached value for key, or None."""
+    buf = ctypes.create_string_buffer(512)
+    code = capi.load().stbem_tune_cache_get(key.encode(), buf, len(buf))
+    return buf.value.decode() if code == capi.STBEM_OK else None
+
+
+def tune_cache_put(key: str, value: str):
+    code = capi.load().stbem_tune_cache_put(key.encode(), value.encode())
+    if code != capi.STBEM_OK:
+        raise capi.StbemError(code, "tune cache: bad entry or unwritable file")
+
+
+def tune_cache_clear():
+    """Forget every in-process entry (the backing file is kept)."""
+    capi.load().stbem_tune_cache_clear()
+
+
+def tc_tune(ctx: Context, A_bf16, x_bf16, out=None):
+    """Pick the plain tensor-core product's tile width (128 or 256 steps) for
+    this shape by timing both (or take the cached choice); later products of
+    the shape use it.  Returns (tile_n, from_cache)."""
+    n_t, n_x = A_bf16.shape[0], A_bf16.shape[1]
+    xb = x_bf16 if x_bf16.dim() == 3 else x_bf16.unsqueeze(0)
+    if out is None:
+        out = torch.empty(xb.shape, dtype=torch.float64, device=xb.device)
+    tn, cached = ctypes.c_int(), ctypes.c_int()
+    ctx.check(ctx.lib.stbem_tc_tune(ctx.h, n_t, n_x, _ptr(A_bf16), xb.shape[0], _ptr(xb), _ptr(out),
+                                    ctypes.byref(tn), ctypes.byref(cached)))
+    return tn.value, bool(cached.value)
+
+
 class Ragged:
     """A ragged batch: independent problems of different sizes handled by one
     persistent launch per step (stbem_ragged_*).  ``problems`` is a list of
@@ -686,16 +727,23 @@ class Ragged:
         return out
 
     def tune(self, A, x, y):
-        """Autotune the product's lag-chunk length on A; returns (chosen,
-        {candidate: ms})."""
+        """Autotune the product on A over the tile family (FP32 register tiles
+        or generic tiles) and the lag-chunk length, or take the choice the
+        tune cache holds for these shapes on this device.  Returns (choice,
+        report): choice = {"tiles32", "lags_per_chunk", "from_cache"},
+        report = {"tiles32=T lpc=C": ms} of the candidates timed (empty when
+        the choice came from the cache)."""
         p = capi.F64 if A.dtype == torch.float64 else capi.F32
         w = self.apply_workspace()
-        best = ctypes.c_int()
+        best, t32b = ctypes.c_int(), ctypes.c_int()
         self.ctx.check(self.ctx.lib.stbem_ragged_tune(self.ctx.h, self.h, p, _ptr(A), _ptr(x), _ptr(y), _ptr(w),
-                                                       w.numel(), ctypes.byref(best)))
-        cand, ms, n = (ctypes.c_int * 16)(), (ctypes.c_float * 16)(), ctypes.c_int()
-        self.ctx.check(self.ctx.lib.stbem_ragged_tune_report(self.h, 16, cand, ms, ctypes.byref(n)))
-        return best.value, {cand[k]: ms[k] for k in range(n.value)}
+                                                       w.numel(), ctypes.byref(best), ctypes.byref(t32b)))
+        cand, t32, ms = (ctypes.c_int * 32)(), (ctypes.c_int * 32)(), (ctypes.c_float * 32)()
+        n, cached = ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.stbem_ragged_tune_report(self.h, 32, cand, t32, ms, ctypes.byref(n),
+                                                              ctypes.byref(cached)))
+        report = {"tiles32=%d lpc=%d" % (t32[k], cand[k]): ms[k] for k in range(min(n.value, 32))}
+        return {"tiles32": t32b.value, "lags_per_chunk": best.value, "from_cache": bool(cached.value)}, report
 
     def rhs(self, K, y_stars):
         p = capi.F64 if K.dtype == torch.float64 else capi.F32

@@ -46,6 +46,7 @@ EXPORTS = [
     "stbem_m0_apply_workspace_bytes", "stbem_m0_apply", "stbem_planewave_data", "stbem_evaluate",
     "stbem_exact_slices", "stbem_apply_tc_exact", "stbem_apply_exact_workspace_bytes", "stbem_apply_exact",
     "stbem_solve_batched_exact_workspace_bytes", "stbem_solve_batched_exact",
+    "stbem_tune_cache_path", "stbem_tune_cache_get", "stbem_tune_cache_put", "stbem_tune_cache_clear", "stbem_tc_tune",
 ]
 
 
@@ -126,8 +127,13 @@ def load(path: str = LIB_PATH):
     L.stbem_ragged_lumped_mass.argtypes = [vp, vp, vp]
     L.stbem_ragged_apply_workspace_bytes.argtypes = [vp, P(sz)]
     L.stbem_ragged_apply.argtypes = [vp, vp, i, vp, vp, vp, vp, sz]
-    L.stbem_ragged_tune.argtypes = [vp, vp, i, vp, vp, vp, vp, sz, P(i)]
-    L.stbem_ragged_tune_report.argtypes = [vp, i, P(i), P(ctypes.c_float), P(i)]
+    L.stbem_ragged_tune.argtypes = [vp, vp, i, vp, vp, vp, vp, sz, P(i), P(i)]
+    L.stbem_ragged_tune_report.argtypes = [vp, i, P(i), P(i), P(ctypes.c_float), P(i), P(i)]
+    L.stbem_tune_cache_path.argtypes = [ctypes.c_char_p]
+    L.stbem_tune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p, sz]
+    L.stbem_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p]
+    L.stbem_tune_cache_clear.argtypes = []
+    L.stbem_tc_tune.argtypes = [vp, i, i, vp, i, vp, vp, P(i), P(i)]
     L.stbem_ragged_rhs.argtypes = [vp, vp, i, vp, P(d), vp, vp, vp, sz]
     L.stbem_ragged_solve_workspace_bytes.argtypes = [vp, i, P(sz)]
     L.stbem_ragged_solve.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]

@@ -20,6 +20,7 @@
 #include "initial.h"
 #include "mass_host.h"
 #include "toeplitz_tc.h"
+#include "tune_cache.h"
 #include "vec.h"
 
 using stbem_internal::cuda_fail;
@@ -409,6 +410,89 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* A_hi, const vo
   int flag = 0;
   CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc3: read error word");
   if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc3: a pipeline wait timed out");
+  return STBEM_OK;
+}
+
+// ------------------------------------------------- tuned launch parameters ----
+int stbem_tune_cache_path(const char* path) {
+  return stbem::tune_cache_set_path(path) ? STBEM_OK : STBEM_ERR_ARG;
+}
+
+int stbem_tune_cache_get(const char* key, char* value, size_t cap) {
+  if (!key || !value || cap == 0) return STBEM_ERR_ARG;
+  std::string v;
+  if (!stbem::tune_cache_get(key, &v)) return STBEM_ERR_ARG;
+  if (v.size() + 1 > cap) return STBEM_ERR_NOMEM;
+  std::memcpy(value, v.c_str(), v.size() + 1);
+  return STBEM_OK;
+}
+
+int stbem_tune_cache_put(const char* key, const char* value) {
+  if (!key || !value || !stbem::tune_cache_token_ok(key) || !stbem::tune_cache_token_ok(value)) return STBEM_ERR_ARG;
+  return stbem::tune_cache_put(key, value) ? STBEM_OK : STBEM_ERR_ARG;   // the backing file cannot be written
+}
+
+int stbem_tune_cache_clear(void) {
+  stbem::tune_cache_clear();
+  return STBEM_OK;
+}
+
+int stbem_tc_tune(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, const void* x, double* y, int* tile_n,
+                  int* from_cache) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (!A || !x || !y) return fail(ctx, STBEM_ERR_ARG, "tc_tune: NULL pointer");
+  if (!stbem::apply_tc_supported(n_t, n_x, n_rhs))
+    return fail(ctx, STBEM_ERR_ARG, "tc_tune: unsupported sizes n_t=%d n_x=%d n_rhs=%d", n_t, n_x, n_rhs);
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(x)) & 15)
+    return fail(ctx, STBEM_ERR_ARG, "tc_tune: A and x must be 16-byte aligned");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "tc_tune: set device");
+  const std::string key = stbem::tc_plain_tune_key(n_t, n_x, n_rhs);
+  std::string v;
+  if (stbem::tune_cache_get(key, &v) && (v == "bn=128" || (v == "bn=256" && n_t > 128))) {
+    if (tile_n) *tile_n = v == "bn=128" ? 128 : 256;
+    if (from_cache) *from_cache = 1;
+    return STBEM_OK;
+  }
+  cudaStream_t s = ctx->stream;
+  CUDA_TRY(ctx, stbem::tc_error_reset(s), "tc_tune: reset error word");
+  cudaEvent_t e0, e1;
+  CUDA_TRY(ctx, cudaEventCreate(&e0), "tc_tune: event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, STBEM_ERR_CUDA, "tc_tune: event");
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  cudaError_t e = cudaSuccess;
+  for (int bn : {128, 256}) {
+    if (bn == 256 && n_t <= 128) break;    // one tile covers every step
+    float ms = 0.f;
+    e = stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, false, s, 0, bn);   // warm-up
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = stbem::apply_tc_launch(n_t, n_x, A, n_rhs, x, y, false, s, 0, bn);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      ms = r == 0 ? t : std::min(ms, t);
+    }
+    if (e != cudaSuccess) break;
+    if (best == 0 || ms < best_ms) {
+      best = bn;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tc_tune: product");
+  int flag = 0;
+  CUDA_TRY(ctx, stbem::tc_error_read(&flag, s), "tc_tune: read error word");
+  if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "tc_tune: a pipeline wait timed out");
+  if (!stbem::tune_cache_put(key, best == 128 ? "bn=128" : "bn=256"))
+    return fail(ctx, STBEM_ERR_ARG, "tc_tune: cannot write the tune cache file %s", stbem::tune_cache_path().c_str());
+  if (tile_n) *tile_n = best;
+  if (from_cache) *from_cache = 0;
   return STBEM_OK;
 }
 

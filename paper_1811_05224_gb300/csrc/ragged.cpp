@@ -5,9 +5,13 @@
 //     singular pairs) over the (problem, lag, tile) work items of every
 //     problem, largest problems first, taken from an atomic counter;
 //   * products: one persistent launch over the (problem, lag chunk, time tile,
-//     row tile) units of every problem, then one reduction; the lag-chunk
-//     length is picked by an autotuner that times the candidates on the batch
-//     itself (stbem_ragged_tune) and keeps the fastest;
+//     row tile) units of every problem, then one reduction; the tile family
+//     (FP32 register tiles or generic tiles) and the lag-chunk length are
+//     picked by an autotuner that times the candidates on the batch itself
+//     (stbem_ragged_tune), keeps the fastest and records it in the tune cache
+//     under the device and the batch's shape, so that a later batch of the
+//     same shapes (in this process, or in another one with the same cache
+//     file) skips the timing;
 //   * GMRES: all problems in lockstep, per-problem Hessenberg / Givens on the
 //     host, masks for converged problems.  The device work of one Arnoldi step
 //     (preconditioner, product, two Gram-Schmidt passes, norm, normalisation,
@@ -19,6 +23,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <string>
 #include <numeric>
 #include <vector>
 
@@ -26,6 +32,7 @@
 #include "capi_internal.h"
 #include "stbem.h"
 #include "toeplitz.h"
+#include "tune_cache.h"
 #include "vec.h"
 
 using stbem_internal::cuda_fail;
@@ -51,11 +58,14 @@ struct stbem_ragged {
   std::vector<stbem::RaggedApplyPlan> plans;
   stbem::RaggedApplyPlan* d_plans = nullptr;    // generic tiles (FP64, and FP32 when N_x % 4 != 0)
   long long* d_aprefix = nullptr;               // P + 1 (problem order)
-  bool fp32_tiles = false;                      // every N_x % 4 == 0: register-tiled FP32 kernel
+  bool fp32_tiles = false;                      // every N_x % 4 == 0: register-tiled FP32 kernel possible
+  bool use_tiles32 = true;                      // FP32 products use it (tuned)
+  bool tuned_from_cache = false;
   stbem::RaggedApplyPlan* d_plans32 = nullptr;
   long long* d_aprefix32 = nullptr;
   long long part_elems = 0;                     // max over both plan sets
-  std::vector<int> tuned_candidates;
+  std::vector<int> tuned_candidates;            // lag-chunk lengths tried
+  std::vector<int> tuned_tiles;                 // 1: register tiles, 0: generic
   std::vector<float> tuned_ms;
   // solve: pinned host buffers and captured graphs
   double* h_buf = nullptr;                      // 2 (restart + 1) P + P doubles
@@ -131,13 +141,32 @@ int set_chunk(stbem_ctx* ctx, stbem_ragged* R, int lpc) {
 
 cudaError_t rapply(stbem_ragged* R, int prec, const void* A, const double* x, double* y, double* part,
                    cudaStream_t s) {
-  const bool t32 = prec == STBEM_F32 && R->fp32_tiles;
+  const bool t32 = prec == STBEM_F32 && R->fp32_tiles && R->use_tiles32;
   return stbem::ragged_apply_launch(prec, t32, t32 ? R->d_plans32 : R->d_plans,
                                     {R->d_order, t32 ? R->d_aprefix32 : R->d_aprefix}, R->d_vprefix, R->P,
                                     R->d_counters + 2, A, x, y, part, s);
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// tune-cache key: device, precision and the (N_x, N_t) list (FNV-1a 64)
+std::string ragged_tune_key(const stbem_ragged* R, int prec) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  for (int p = 0; p < R->P; ++p) {
+    mix(R->nx[p]);
+    mix(R->nt[p]);
+  }
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "%016llx", h);
+  return stbem::tune_device_key(R->device) + "|ragged_apply|prec=" + (prec == STBEM_F64 ? "f64" : "f32") +
+         "|P=" + std::to_string(R->P) + "|shapes=" + buf;
+}
 
 }  // namespace
 
@@ -302,7 +331,7 @@ int stbem_ragged_apply(stbem_ctx* ctx, stbem_ragged* R, int prec, const void* A,
 }
 
 int stbem_ragged_tune(stbem_ctx* ctx, stbem_ragged* R, int prec, const void* A, const double* x, double* y,
-                      void* work, size_t work_bytes, int* lags_per_chunk) {
+                      void* work, size_t work_bytes, int* lags_per_chunk, int* tiles32) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!R || !A || !x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "ragged_tune: NULL argument");
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "ragged_tune: bad precision");
@@ -311,57 +340,101 @@ int stbem_ragged_tune(stbem_ctx* ctx, stbem_ragged* R, int prec, const void* A, 
   int nt_max = 0;
   for (int v : R->nt) nt_max = std::max(nt_max, v);
   R->tuned_candidates.clear();
+  R->tuned_tiles.clear();
   R->tuned_ms.clear();
+  const bool try32 = prec == STBEM_F32 && R->fp32_tiles;
+  // a recorded choice for these shapes on this device
+  const std::string key = ragged_tune_key(R, prec);
+  std::string v;
+  int c_lpc = 0, c_t32 = -1;
+  if (stbem::tune_cache_get(key, &v) && std::sscanf(v.c_str(), "tiles32=%d lpc=%d", &c_t32, &c_lpc) == 2 &&
+      (c_t32 == 0 || (c_t32 == 1 && try32)) &&
+      std::find(std::begin(kTuneCandidates), std::end(kTuneCandidates), c_lpc) != std::end(kTuneCandidates) &&
+      (size_t)part_elems_for(R, c_lpc) * sizeof(double) <= work_bytes) {
+    R->use_tiles32 = c_t32 == 1 || !try32;
+    const int rc = set_chunk(ctx, R, c_lpc);
+    if (rc != STBEM_OK) return rc;
+    R->tuned_from_cache = true;
+    if (lags_per_chunk) *lags_per_chunk = c_lpc;
+    if (tiles32) *tiles32 = c_t32;
+    return STBEM_OK;
+  }
   cudaEvent_t e0, e1;
   CUDA_TRY(ctx, cudaEventCreate(&e0), "ragged_tune: event");
-  CUDA_TRY(ctx, cudaEventCreate(&e1), "ragged_tune: event");
-  int best = 0;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, STBEM_ERR_CUDA, "ragged_tune: event");
+  }
+  int best = 0, best_t32 = 0;
   float best_ms = 0.f;
-  for (int c : kTuneCandidates) {
-    if (c > nt_max && !R->tuned_candidates.empty()) break;   // longer chunks change nothing
-    if ((size_t)part_elems_for(R, c) * sizeof(double) > work_bytes) continue;
-    int rc = set_chunk(ctx, R, c);
-    if (rc != STBEM_OK) return rc;
-    cudaError_t e = rapply(R, prec, A, x, y, static_cast<double*>(work), s);   // warm-up
-    float ms = 0.f;
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
-      e = cudaEventRecord(e0, s);
-      if (e == cudaSuccess) e = rapply(R, prec, A, x, y, static_cast<double*>(work), s);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float t = 0.f;
-      if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
-      ms = r == 0 ? t : std::min(ms, t);
-    }
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return cuda_fail(ctx, e, "ragged_tune: product");
-    }
-    R->tuned_candidates.push_back(c);
-    R->tuned_ms.push_back(ms);
-    if (best == 0 || ms < best_ms) {
-      best = c;
-      best_ms = ms;
+  // candidates: tile family (FP32 register tiles first when possible) x lag-chunk length
+  for (int t32 = try32 ? 1 : 0; t32 >= 0; --t32) {
+    R->use_tiles32 = t32 == 1;
+    int tried = 0;
+    for (int c : kTuneCandidates) {
+      if (c > nt_max && tried > 0) break;   // longer chunks change nothing
+      if ((size_t)part_elems_for(R, c) * sizeof(double) > work_bytes) continue;
+      int rc = set_chunk(ctx, R, c);
+      if (rc != STBEM_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+      cudaError_t e = rapply(R, prec, A, x, y, static_cast<double*>(work), s);   // warm-up
+      float ms = 0.f;
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = rapply(R, prec, A, x, y, static_cast<double*>(work), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        ms = r == 0 ? t : std::min(ms, t);
+      }
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(ctx, e, "ragged_tune: product");
+      }
+      ++tried;
+      R->tuned_candidates.push_back(c);
+      R->tuned_tiles.push_back(t32);
+      R->tuned_ms.push_back(ms);
+      if (best == 0 || ms < best_ms) {
+        best = c;
+        best_t32 = t32;
+        best_ms = ms;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best == 0) return fail(ctx, STBEM_ERR_NOMEM, "ragged_tune: workspace too small for any candidate");
+  R->use_tiles32 = best_t32 == 1 || !try32;
   const int rc = set_chunk(ctx, R, best);
   if (rc != STBEM_OK) return rc;
+  R->tuned_from_cache = false;
+  char val[64];
+  std::snprintf(val, sizeof(val), "tiles32=%d lpc=%d", best_t32, best);
+  if (!stbem::tune_cache_put(key, val))
+    return fail(ctx, STBEM_ERR_ARG, "ragged_tune: cannot write the tune cache file %s",
+                stbem::tune_cache_path().c_str());
   if (lags_per_chunk) *lags_per_chunk = best;
+  if (tiles32) *tiles32 = best_t32;
   return STBEM_OK;
 }
 
-int stbem_ragged_tune_report(const stbem_ragged* R, int max_n, int* candidates, float* ms, int* n_out) {
+int stbem_ragged_tune_report(const stbem_ragged* R, int max_n, int* candidates, int* tiles32, float* ms, int* n_out,
+                             int* from_cache) {
   if (!R || !n_out) return STBEM_ERR_ARG;
   const int n = (int)R->tuned_candidates.size();
   for (int i = 0; i < n && i < max_n; ++i) {
     if (candidates) candidates[i] = R->tuned_candidates[i];
+    if (tiles32) tiles32[i] = R->tuned_tiles[i];
     if (ms) ms[i] = R->tuned_ms[i];
   }
   *n_out = n;
+  if (from_cache) *from_cache = R->tuned_from_cache ? 1 : 0;
   return STBEM_OK;
 }
 

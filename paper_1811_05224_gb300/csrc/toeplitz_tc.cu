@@ -28,6 +28,7 @@
 #include "assemble.h"
 #include "device_info.h"
 #include "toeplitz_tc.h"
+#include "tune_cache.h"
 
 namespace stbem {
 
@@ -830,13 +831,30 @@ static std::atomic<long long> g_stall_cycles{0};
 
 void tc_set_stall(long long cycles) { g_stall_cycles.store(cycles > 0 ? cycles : 0); }
 
+std::string tc_plain_tune_key(int nt, int nx, int n_rhs) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return tune_device_key(dev) + "|tc_plain|nt=" + std::to_string(nt) + "|nx=" + std::to_string(nx) +
+         "|rhs=" + std::to_string(n_rhs);
+}
+
+int tc_plain_tile_n(int nt, int nx, int n_rhs) {
+  std::string v;
+  if (tune_cache_get(tc_plain_tune_key(nt, nx, n_rhs), &v)) {
+    if (v == "bn=128") return 128;
+    if (v == "bn=256" && nt > 128) return 256;
+  }
+  // untuned: products on more than 128 steps take 128 x 256 tiles (N = 256
+  // MMAs, a third less shared-memory operand traffic per flop)
+  return nt > 128 ? 256 : BN;
+}
+
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            bool accumulate, cudaStream_t s, int chunk) {
+                            bool accumulate, cudaStream_t s, int chunk, int tile_n) {
   const long long stall = g_stall_cycles.load();
   CUtensorMap mA, mX;
-  // plain products on more than 128 steps take 128 x 256 tiles (N = 256 MMAs:
-  // a third less shared-memory operand traffic per flop)
-  const int bn = (chunk <= 0 && nt > 128) ? 256 : BN;
+  int bn = BN;
+  if (chunk <= 0) bn = (tile_n == 128 || tile_n == 256) ? tile_n : tc_plain_tile_n(nt, nx, n_rhs);
   cudaError_t e = make_maps(nt, nx, A_bf16, n_rhs, X_bf16, &mA, &mX, bn);
   if (e != cudaSuccess) return e;
   const dim3 grid((nx + BM - 1) / BM, n_rhs, (nt + bn - 1) / bn);

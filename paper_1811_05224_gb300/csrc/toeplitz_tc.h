@@ -1,6 +1,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <string>
 
 #include "stbem.h"
 
@@ -8,9 +9,14 @@ namespace stbem {
 bool apply_tc_supported(int nt, int nx, int n_rhs);
 // y (FP64) = block-Toeplitz product of BF16 lag blocks A with BF16 x, on tcgen05.
 // chunk <= 0: one FP32 accumulator over the whole chain; chunk > 0: FP32 partials
-// of `chunk` 64-wide K steps each, Kahan-summed (compensated kernel).
+// of `chunk` 64-wide K steps each, Kahan-summed (compensated kernel).  The
+// plain kernel's tile width (steps per tile) is tile_n (128 or 256), else the
+// tuned value for this shape (stbem_tc_tune), else 256 for n_t > 128.
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            bool accumulate, cudaStream_t s, int chunk = 0);
+                            bool accumulate, cudaStream_t s, int chunk = 0, int tile_n = 0);
+// tune-cache key of the plain product's tile width, and the width in use
+std::string tc_plain_tune_key(int nt, int nx, int n_rhs);
+int tc_plain_tile_n(int nt, int nx, int n_rhs);
 // hi/mid/lo BF16 slices of an FP64 array (mid and lo may be NULL)
 cudaError_t bf16_split3_launch(const double* src, void* hi, void* mid, void* lo, size_t n, cudaStream_t s);
 cudaError_t tc_error_reset(cudaStream_t s);

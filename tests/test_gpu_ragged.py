@@ -84,10 +84,22 @@ def test_ragged_apply_matches_oracle_and_tuner(ctx, batch):
 
     check(R.apply(V, x))
     y = torch.empty_like(x)
+    import paper_1811_05224_gb300 as P
+    P.tune_cache_clear()
     best, report = R.tune(V, x, y)
-    assert best in report and len(report) >= 1
+    assert not best["from_cache"] and len(report) >= 1
+    assert "tiles32=%d lpc=%d" % (best["tiles32"], best["lags_per_chunk"]) in report
     assert all(ms > 0 for ms in report.values())
     check(R.apply(V, x))
+    # the same shapes again: the recorded choice, no timing
+    best2, report2 = R.tune(V, x, y)
+    assert best2["from_cache"] and report2 == {}
+    assert (best2["tiles32"], best2["lags_per_chunk"]) == (best["tiles32"], best["lags_per_chunk"])
+    check(R.apply(V, x))
+    # FP32 operators: both tile families are candidates
+    V32 = R.assemble("V", "f32")
+    best3, report3 = R.tune(V32, x, y)
+    assert {k.split()[0] for k in report3} == {"tiles32=0", "tiles32=1"}
 
 
 def test_ragged_rhs_and_mass_match_single(ctx, batch):
