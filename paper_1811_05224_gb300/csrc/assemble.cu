@@ -1080,7 +1080,16 @@ struct BlockTime {
   int d, n;
   double s[4], inv_sc;
   double sig[kMaxNodesNU], wv[kMaxNodesNU], wk[kMaxNodesNU], w3[kMaxNodesNU], w2[kMaxNodesNU];
+  // e^{-c sig} = exp_prod_fast(c, sigk) with sigk = sig 2048 / ln 2 while
+  // c sigk_max < kExpProdMax; etab: the 2048-entry table in shared memory
+  double sigk[kMaxNodesNU], sigk_max;
+  const double* etab;
 };
+
+// e^{-c sig_g} of a block's Peano node g (fast: the table form applies to every node)
+__device__ __forceinline__ double nu_exp(double c, const BlockTime& B, int g, bool fast) {
+  return fast ? exp_prod_fast(c, B.sigk[g], B.etab) : exp_neg_fast(c * B.sig[g]);
+}
 
 __device__ __forceinline__ void nu_block_index(long long p, int* m, int* n) {
   int mm = (int)floor((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
@@ -1121,6 +1130,11 @@ __device__ void build_block_time(BlockTime& B, const double* __restrict__ tn, in
     }
   }
   B.n = g;
+  B.sigk_max = 0.0;
+  for (int k = 0; k < g; ++k) {
+    B.sigk[k] = B.sig[k] * kInvLn2x2048;
+    B.sigk_max = fmax(B.sigk_max, B.sigk[k]);
+  }
 }
 
 template <int K>
@@ -1138,8 +1152,9 @@ __device__ double nu_kernel(double c, const BlockTime& B, double alpha) {
   if (B.d == 1) return z < 1.0 ? nu_lag1_series<K>(c, B.s[0], B.s[1], B.s[2], alpha) : nu_closed<K>(c, B, alpha);
   if (z > 0.5 * (double)B.d) return nu_closed<K>(c, B, alpha);
   double acc = 0.0;
+  const bool fast = c * B.sigk_max < kExpProdMax;
   for (int g = 0; g < B.n; ++g) {
-    const double e = exp_neg_fast(c * B.sig[g]);
+    const double e = nu_exp(c, B, g, fast);
     if (K == kV) acc = fma(B.wv[g], e, acc);
     else if (K == kKq) acc = fma(B.wk[g], e, acc);
     else acc = fma(e, fma(B.w3[g], c, -B.w2[g]), acc);
@@ -1151,8 +1166,9 @@ __device__ double nu_kernel(double c, const BlockTime& B, double alpha) {
 __device__ __forceinline__ void nu_kernel_D(double c, const BlockTime& B, double alpha, double* kv, double* k1v) {
   if (B.d >= 2 && !(c * B.inv_sc > 0.5 * (double)B.d)) {
     double av = 0.0, a1 = 0.0;
+    const bool fast = c * B.sigk_max < kExpProdMax;
     for (int g = 0; g < B.n; ++g) {
-      const double e = exp_neg_fast(c * B.sig[g]);
+      const double e = nu_exp(c, B, g, fast);
       av = fma(B.wv[g], e, av);
       a1 = fma(e, fma(B.w3[g], c, -B.w2[g]), a1);
     }
@@ -1247,7 +1263,8 @@ __device__ void nu_singular_moments(const Piece& A, const Piece& Bp, int cls, co
 
 template <int OP>
 constexpr size_t nu_tile_smem_bytes() {
-  return (((size_t)Tile<OP>::pairs * Tile<OP>::nm * sizeof(double) + 15) / 16) * 16 + sizeof(BlockTime);
+  return (((size_t)Tile<OP>::pairs * Tile<OP>::nm * sizeof(double) + 15) / 16) * 16 + 2048 * sizeof(double) +
+         sizeof(BlockTime);
 }
 
 // One tile of one block (m, n) = packed index p0 + blockIdx.y.
@@ -1260,7 +1277,8 @@ __global__ void __launch_bounds__(kTileThreads) k_nu_tile(DevMesh M, const doubl
   __shared__ int n_sing;
   constexpr int P = Tile<OP>::pairs, NM = Tile<OP>::nm;
   double* mom = reinterpret_cast<double*>(smem_raw);
-  BlockTime* BT = reinterpret_cast<BlockTime*>(smem_raw + ((P * NM * sizeof(double) + 15) / 16) * 16);
+  double* etab = reinterpret_cast<double*>(smem_raw + ((P * NM * sizeof(double) + 15) / 16) * 16);
+  BlockTime* BT = reinterpret_cast<BlockTime*>(etab + 2048);
   const long long p = p0 + blockIdx.y;
   int m, n;
   nu_block_index(p, &m, &n);
@@ -1276,9 +1294,16 @@ __global__ void __launch_bounds__(kTileThreads) k_nu_tile(DevMesh M, const doubl
   }
   const int r0 = rt * kT, c0 = ct * (OP == STBEM_OP_K ? kKP : kT);
   build_block_time(*BT, tn, m, n, M.alpha);
-  if (threadIdx.x == 0) n_sing = 0;
+  for (int k = threadIdx.x; k < 2048; k += kTileThreads) etab[k] = kExp2Tab2048[k];
+  if (threadIdx.x == 0) {
+    n_sing = 0;
+    BT->etab = etab;
+  }
   __syncthreads();
+  // D at d >= 2 on a diagonal tile: the half-pair block is symmetric, integrate u <= v only
+  const bool mirrored = OP == STBEM_OP_D && rt == ct && d >= 2;
   for (int q = threadIdx.x; q < P; q += kTileThreads) {
+    if (mirrored && q % kDP < q / kDP) continue;
     Piece A, B;
     int ia, ib, ring;
     double* mq = mom + (size_t)q * NM;
@@ -1307,7 +1332,7 @@ __global__ void __launch_bounds__(kTileThreads) k_nu_tile(DevMesh M, const doubl
     nu_singular_moments<OP>(A, B, pair_class(ring, ia, ib, A, B), *BT, M.alpha, mom + (size_t)q * NM, red);
   }
   __syncthreads();
-  tile_entries<OP, double>(M, rt, ct, r0, c0, mom, (size_t)p * N * N, out);
+  tile_entries<OP, double>(M, rt, ct, r0, c0, mom, (size_t)p * N * N, out, mirrored);
 }
 
 // y[m][i] = sum_{n <= m} sum_j A[p(m, n)][i][j] x[n][j]: one warp per (m, i)
