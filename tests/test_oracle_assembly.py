@@ -169,6 +169,28 @@ def bf_D(m, l, k, d, magnitude=False):
     return (tot, mag) if magnitude else tot
 
 
+def bf_D_pool(pool, m, l, k, d, magnitude=False):
+    """bf_D with its 2 x 16 piece integrals as pool tasks (same terms, same
+    summation order); returns a callable giving bf_D's result."""
+    futs = []
+    for pa, a0, a1, sa in m.dual_pieces(l):
+        for pb, b0, b1, sb in m.dual_pieces(k):
+            A0, A1, B0, B1 = m.hs0[pa], m.hs1[pa], m.hs0[pb], m.hs1[pb]
+            fa = pool.submit(piece_integral, 'V', m, A0, A1, B0, B1, m.hs_n[pb], d)
+            fb = pool.submit(piece_integral, '1', m, A0, A1, B0, B1, m.hs_n[pb], d, (a0, a1), (b0, b1))
+            futs.append((sa * sb, m.hs_n[pa] @ m.hs_n[pb], fa, fb))
+
+    def result():
+        tot, mag = 0.0, 0.0
+        for ca, cb, fa, fb in futs:
+            a = ca * fa.result()
+            b = cb * fb.result()
+            tot += a + b
+            mag += abs(a) + abs(b)
+        return (tot, mag) if magnitude else tot
+    return result
+
+
 def _meshes():
     pent = np.array([[0.0, 0.0], [1.1, 0.1], [1.3, 0.9], [0.5, 1.4], [-0.2, 0.8]])
     return {
@@ -183,14 +205,18 @@ def _check(got, ref, scale, tol=2e-11):
 
 
 @pytest.mark.parametrize("name", ['square4', 'lshape8', 'pentagon'])
-def test_V_K_entries_brute_force(name):
+def test_V_K_entries_brute_force(name, cpu_pool):
     m = _meshes()[name]
     N = m.N
     # one pair per class: identical, adjacent (both orders), near, regular
     pairs = [(0, 0), (0, 1), (N - 1, 0), (2, 0)]
     if N >= 6:
         pairs.append((0, 3))
-    for d in range(min(m.n_t, 3)):
+    lags = range(min(m.n_t, 3))
+    # the brute-force values, one task per entry, in the pool
+    fut = {(f.__name__, i, j, d): cpu_pool.submit(f, m, i, j, d)
+           for d in lags for (i, j) in pairs for f in (bf_V, bf_K)}
+    for d in lags:
         I = np.array([p[0] for p in pairs])
         J = np.array([p[1] for p in pairs])
         V = assembly.V_entries(m, d, I, J)
@@ -198,23 +224,26 @@ def test_V_K_entries_brute_force(name):
         sV = np.abs(V).max()
         sK = np.abs(K).max()
         for (i, j), v, kk in zip(pairs, V, K):
-            _check(v, bf_V(m, i, j, d), sV)
-            _check(kk, bf_K(m, i, j, d), sK)
+            _check(v, fut[("bf_V", i, j, d)].result(), sV)
+            _check(kk, fut[("bf_K", i, j, d)].result(), sK)
 
 
-def test_D_entries_brute_force():
+def test_D_entries_brute_force(cpu_pool):
     m = _meshes()['square4']
     cases = [(0, 0, 0), (0, 1, 1), (1, 3, 2)]
-    for l, k, d in cases:
+    refs = [bf_D_pool(cpu_pool, m, l, k, d) for l, k, d in cases]
+    for (l, k, d), ref in zip(cases, refs):
         got = assembly.D_entries(m, d, np.array([l]), np.array([k]))[0]
-        _check(got, bf_D(m, l, k, d), abs(got))
+        _check(got, ref(), abs(got))
 
 
-def test_D_entries_brute_force_lshape():
+def test_D_entries_brute_force_lshape(cpu_pool):
     m = _meshes()['lshape8']
-    for l, k, d in [(2, 3, 0), (1, 5, 1)]:
+    cases = [(2, 3, 0), (1, 5, 1)]
+    refs = [bf_D_pool(cpu_pool, m, l, k, d) for l, k, d in cases]
+    for (l, k, d), ref in zip(cases, refs):
         got = assembly.D_entries(m, d, np.array([l]), np.array([k]))[0]
-        _check(got, bf_D(m, l, k, d), abs(got))
+        _check(got, ref(), abs(got))
 
 
 @pytest.mark.parametrize("kind", ['V', 'K', '1'])
@@ -266,7 +295,7 @@ def _pairs_around(m, i):
 
 
 @pytest.mark.parametrize("name", ['square_h16_nt512', 'lshape1024', 'section4_L4', 'star256'])
-def test_high_lag_entries_brute_force(name):
+def test_high_lag_entries_brute_force(name, cpu_pool):
     """V, K and D entries of every pair class at lags >= 8 (the 6- and
     4-point spatial rules) against adaptive quadrature in space with the hat
     form in time, to the rule's stated bound 2e-11 (floored at 1e-6 of the
@@ -277,23 +306,27 @@ def test_high_lag_entries_brute_force(name):
     pairs = [p for i in centres for p in _pairs_around(m, i)]
     I = np.array([p[0] for p in pairs])
     J = np.array([p[1] for p in pairs])
+    c = centres[0]
+    dp = [(c, c), (c, (c + 1) % m.N), (c, (c + 3) % m.N)]
+    # the brute-force values, one task per entry, in the pool
+    fV = {(i, j, d): cpu_pool.submit(bf_V, m, min(i, j), max(i, j), d) for d in lags for (i, j) in pairs}
+    fK = {(i, j, d): cpu_pool.submit(bf_K, m, i, j, d) for d in lags for (i, j) in pairs}
+    fD = {(l, k, d): bf_D_pool(cpu_pool, m, l, k, d, True) for d in lags for (l, k) in dp}
     for d in lags:
         V = assembly.V_entries(m, d, I, J)
         K = assembly.K_entries(m, d, I, J)
         sV, sK = np.abs(V).max(), np.abs(K).max()
         for (i, j), v, kk in zip(pairs, V, K):
-            _check(v, bf_V(m, min(i, j), max(i, j), d), sV)
-            rk = bf_K(m, i, j, d)
+            _check(v, fV[(i, j, d)].result(), sV)
+            rk = fK[(i, j, d)].result()
             if rk == 0.0:       # trial support collinear with gamma_i: K = 0, the rule gives noise
                 assert abs(kk) <= 1e-12 * sK, (d, i, j, kk, sK)
             else:
                 _check(kk, rk, sK)
         # D: identical, adjacent and separated dual functions at the first centre
-        c = centres[0]
-        dp = [(c, c), (c, (c + 1) % m.N), (c, (c + 3) % m.N)]
         Dg = assembly.D_entries(m, d, np.array([p[0] for p in dp]), np.array([p[1] for p in dp]))
         for (l, k), got in zip(dp, Dg):
-            ref, mag = bf_D(m, l, k, d, magnitude=True)
+            ref, mag = fD[(l, k, d)]()
             assert abs(got - ref) <= 2e-11 * max(abs(ref), 1e-6 * np.abs(Dg).max()) + 2e-12 * mag, \
                 (d, l, k, got, ref, mag)
 

@@ -165,7 +165,7 @@ def _entry_rule(bm, dom, i, k, c, m, cls):
     return float((dG * wl[..., c]).sum())
 
 
-def test_m0_single_entries_against_bruteforce():
+def test_m0_single_entries_against_bruteforce(cpu_pool):
     n = 4
     bm = BoundaryMesh(W.unit_square(n), 1.0, n, 10.0)
     dom = I.DomainMesh(*W.square_triangulation(n, jitter=0.2, seed=3), bm)
@@ -181,9 +181,10 @@ def test_m0_single_entries_against_bruteforce():
     }
     cases = [("edge", 0, 0), ("edge", 0, 2), ("vertex", 0, 2), ("vertex", 0, 0), ("near", 0, 1),
              ("regular", 0, 0), ("edge", 1, 1), ("regular", 1, 2)]
-    for name, m, c in cases:
+    refs = [cpu_pool.submit(_entry_bruteforce, bm, dom, i, picks[name], c, m, 1e-10) for name, m, c in cases]
+    for (name, m, c), fut in zip(cases, refs):
         k = picks[name]
-        ref = _entry_bruteforce(bm, dom, i, k, c, m, tol=1e-10)
+        ref = fut.result()
         got = _entry_rule(bm, dom, i, k, c, m, cls[i, k])
         assert abs(got - ref) <= 5e-9 * abs(ref), (name, m, c, got, ref)
 

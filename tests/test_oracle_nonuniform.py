@@ -64,10 +64,11 @@ CASES = [(3, 3, 1e-4), (2, 1, 1e-4), (4, 3, 0.08), (4, 2, 2e-3), (4, 2, 0.3), (6
 
 
 @pytest.mark.parametrize("kind", ["V", "K", "1"])
-def test_time_integrals_against_nested_quadrature(kind):
-    for m, n, c in CASES:
+def test_time_integrals_against_nested_quadrature(kind, cpu_pool):
+    refs = [cpu_pool.submit(nested, kind, c, m, n) for m, n, c in CASES]
+    for (m, n, c), fut in zip(CASES, refs):
         got = float(NU.time_integral(kind, np.array([c]), T_NODES, m, n, ALPHA)[0])
-        ref = float(nested(kind, c, m, n))
+        ref = float(fut.result())
         assert abs(got - ref) <= 1e-10 * abs(ref) + 1e-300, (kind, m, n, c, got, ref)
 
 

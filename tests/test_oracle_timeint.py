@@ -75,10 +75,11 @@ MODERATE = [(0, 0.3), (0, 2.0), (1, 0.05), (1, 0.6), (1, 3.0), (2, 0.3), (2, 1.5
 
 
 @pytest.mark.parametrize("kind", ['V', 'K', '1'])
-def test_against_nested_double_integral(kind):
-    for d, zd in MODERATE:
+def test_against_nested_double_integral(kind, cpu_pool):
+    refs = [cpu_pool.submit(nested, kind, zd * max(d, 1) * HT, d) for d, zd in MODERATE]
+    for (d, zd), fut in zip(MODERATE, refs):
         c = zd * max(d, 1) * HT
-        ref = float(nested(kind, c, d))
+        ref = float(fut.result())
         got = oracle(kind, c, d)
         assert abs(got - ref) <= 5e-13 * abs(ref), (kind, d, zd, got, ref)
 
