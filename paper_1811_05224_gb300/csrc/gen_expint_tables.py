@@ -11,6 +11,12 @@ the Chebyshev points of the first kind, in 40-digit arithmetic (mpmath):
 On each interval the nearest singularity of A and B is the log branch point
 at z = 0, (1 + sqrt 2) / (sqrt 2 - 1) = 5.83 half-widths from the centre, so
 the coefficients decay like 11.66^{-k}: 18 terms reach ~1e-19.
+The device evaluates 16-term fits (Chebyshev coefficients beyond the 15th
+are below 1e-17 of c_0) in the monomial basis of t with Horner's rule: the
+Chebyshev series is converted exactly (in 40 digits) to powers of t; since
+sum |a_j| / |f| <= 1.4 on every interval, Horner's rounding stays near one
+ulp -- 15 fused multiply-adds instead of 17 Clenshaw steps of two
+operations.
 FP32: the leading 12 coefficients on the four intervals [1,2], [2,4], [4,8],
 [8,16] (26-point fits).
 
@@ -22,6 +28,7 @@ import mpmath as mp
 
 mp.mp.dps = 40
 NC = 18
+NH = 16
 NC_F32_FIT = 26
 NCF = 12
 NEIN = 18
@@ -53,6 +60,26 @@ def cheb_coeffs_map(f, s, o, n=NC):
     return out
 
 
+def cheb_to_monomial(c):
+    """Exact coefficients a_j of c_0 / 2 + sum_{k>=1} c_k T_k(t) = sum_j a_j t^j
+    (T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1})."""
+    n = len(c)
+    T = [[mp.mpf(1)], [mp.mpf(0), mp.mpf(1)]]
+    for k in range(2, n):
+        t = [mp.mpf(0)] * (k + 1)
+        for j, v in enumerate(T[k - 1]):
+            t[j + 1] += 2 * v
+        for j, v in enumerate(T[k - 2]):
+            t[j] -= v
+        T.append(t)
+    a = [mp.mpf(0)] * n
+    for k in range(n):
+        ck = c[k] / 2 if k == 0 else c[k]
+        for j, v in enumerate(T[k]):
+            a[j] += ck * v
+    return a
+
+
 def cheb_coeffs(f, a, b, n=NC_F32_FIT):
     nodes = [mp.cos(mp.pi * (j + mp.mpf(1) / 2) / n) for j in range(n)]
     vals = [f((b - a) / mp.mpf(2) * t + (a + b) / mp.mpf(2)) for t in nodes]
@@ -67,10 +94,11 @@ def main():
     A = lambda z: mp.e ** z * mp.e1(z)            # noqa: E731
     B = lambda z: mp.e ** z * mp.expint(2, z)     # noqa: E731
     iv = f64_intervals()
-    lines = ["// Generated by gen_expint_tables.py: Chebyshev coefficients of",
-             "// A(z) = e^z E1(z) and B(z) = e^z E2(z) on [1, 16): FP64 %d terms on each of" % NC,
-             "// %d intervals [a_k, a_{k+1}] (a_k = 2^{k/2}), t = fma(z, kChebS[k], kChebO[k]);" % N_INT64,
-             "// FP32 %d terms on [1,2], [2,4], [4,8], [8,16]; f = c0/2 + sum_k c_k T_k(t)." % NCF,
+    lines = ["// Generated by gen_expint_tables.py: polynomial fits of",
+             "// A(z) = e^z E1(z) and B(z) = e^z E2(z) on [1, 16): FP64 %d powers of t on each of" % NH,
+             "// %d intervals [a_k, a_{k+1}] (a_k = 2^{k/2}), t = fma(z, kChebS[k], kChebO[k]),"  % N_INT64,
+             "// f = sum_j a_j t^j (a %d-term Chebyshev fit converted exactly);" % NH,
+             "// FP32 %d Chebyshev terms on [1,2], [2,4], [4,8], [8,16]; f = c0/2 + sum_k c_k T_k(t)." % NCF,
              "#pragma once", "namespace stbem {",
              "constexpr int kChebN = %d;" % NC,
              "constexpr int kChebIntervals = %d;" % N_INT64]
@@ -78,15 +106,20 @@ def main():
     lines.append("static __constant__ const double kChebSplit[4] = {%s};" % ", ".join(r(iv[2 * e][1]) for e in range(4)))
     lines.append("static __constant__ const double kChebS[%d] = {%s};" % (N_INT64, ", ".join(r(x[2]) for x in iv)))
     lines.append("static __constant__ const double kChebO[%d] = {%s};" % (N_INT64, ", ".join(r(x[3]) for x in iv)))
-    tails = []
-    for name, f in (("kChebE1", A), ("kChebE2", B)):
-        lines.append("static __constant__ const double %s[%d][%d] = {" % (name, N_INT64, NC))
+    # the 18-term fits as powers of t, a_0 .. a_{NH-1}, for Horner's rule
+    tails, drop = [], []
+    lines.append("constexpr int kHornN = %d;" % NH)
+    for name, f in (("kHornE1", A), ("kHornE2", B)):
+        lines.append("static __constant__ const double %s[%d][%d] = {" % (name, N_INT64, NH))
         for lo, hi, sk, ok in iv:
-            c = cheb_coeffs_map(f, sk, ok)
+            c = cheb_coeffs_map(f, sk, ok)                 # 18 terms: the size of the tail
             tails.append(abs(c[-1] / c[0]))
-            lines.append("  {" + ", ".join(mp.nstr(x, 20, min_fixed=0, max_fixed=0) for x in c) + "},")
+            c16 = cheb_coeffs_map(f, sk, ok, NH)           # the fit that is converted
+            drop.append(max(abs(x) for x in c[NH:]) / abs(c[0]))
+            a = cheb_to_monomial(c16)
+            lines.append("  {" + ", ".join(mp.nstr(x, 20, min_fixed=0, max_fixed=0) for x in a) + "},")
         lines.append("};")
-    print("largest |c_last / c_0|: %.2e" % max(tails))
+    print("largest |c_17 / c_0|: %.2e; largest dropped |c_k / c_0|, k >= %d: %.2e" % (max(tails), NH, max(drop)))
     # FP32 copies: the leading 12 coefficients (the tail is below 2e-9 of c0)
     for name, f in (("kChebE1f", A), ("kChebE2f", B)):
         lines.append("static __constant__ const float %s[%d][%d] = {" % (name, len(INTERVALS), NCF))

@@ -3,10 +3,10 @@
 //  * z < 1: E1(z) = -gamma - ln z + Ein(z), Ein(z) = sum_{k>=1} (-1)^{k+1} z^k/(k k!)
 //    (Abramowitz & Stegun 5.1.11), and E2(z) = e^{-z} - z E1(z) (A&S 5.1.14);
 //    e^{-z} here and below from exp_neg_fast;
-//  * 1 <= z < 16: e^z E1 and e^z E2 from 18-term Chebyshev expansions on the
-//    eight intervals [2^{k/2}, 2^{(k+1)/2}] (coefficients in expint_cheb.inc,
-//    generated by gen_expint_tables.py in 40-digit arithmetic), Clenshaw
-//    summation;
+//  * 1 <= z < 16: e^z E1 and e^z E2 from 16-term Chebyshev fits on the
+//    eight intervals [2^{k/2}, 2^{(k+1)/2}], converted to powers of the
+//    interval variable (coefficients in expint_cheb.inc, generated by
+//    gen_expint_tables.py in 40-digit arithmetic), Horner's rule;
 //  * z >= 16: the continued fraction of A&S 5.1.22 in its even (contracted)
 //    form, E_n(z) = e^{-z} / (z + n - 1 n / (z + n + 2 - 2 (n+1) / (z + n + 4 - ...))),
 //    truncated at a fixed depth of 14 (converged to < 1e-16 there) and
@@ -180,16 +180,13 @@ STB_HD void cf_forward12(double z, double* r1, double* r2) {
   *r2 = q2 / p2;
 }
 
-// Clenshaw sum of c0/2 + sum_{k>=1} c_k T_k(t).
-STB_HD double cheb_sum(const double* c, double t) {
-  double b1 = 0.0, b2 = 0.0;
-  for (int k = kChebN - 1; k >= 1; --k) {
-    const double b0 = c[k] + 2.0 * t * b1 - b2;
-    b2 = b1;
-    b1 = b0;
-  }
-  return 0.5 * c[0] + t * b1 - b2;
+// sum_j a_j t^j, j < kHornN, by Horner's rule
+STB_HD double horner_sum(const double* a, double t) {
+  double p = a[kHornN - 1];
+  for (int j = kHornN - 2; j >= 0; --j) p = fma(p, t, a[j]);
+  return p;
 }
+
 
 // Interval of the FP64 Chebyshev tables for 1 <= z < 16: [a_k, a_{k+1}],
 // a_k = 2^{k/2} (the split inside each octave [2^e, 2^{e+1}) at sqrt 2 2^e).
@@ -208,8 +205,8 @@ STB_HD void e1e2(double z, double* e1, double* e2) {
     const int k = cheb_interval(z);
     const double t = fma(z, kChebS[k], kChebO[k]);
     const double ez = exp_neg_fast(z);
-    *e1 = cheb_sum(kChebE1[k], t) * ez;
-    *e2 = cheb_sum(kChebE2[k], t) * ez;
+    *e1 = horner_sum(kHornE1[k], t) * ez;
+    *e2 = horner_sum(kHornE2[k], t) * ez;
   } else if (z < 700.0) {
     const double ez = exp_neg_fast(z);
     double r1, r2;
@@ -230,7 +227,7 @@ STB_HD double e1_only(double z) {
   if (z < 16.0) {
     const int k = cheb_interval(z);
     const double t = fma(z, kChebS[k], kChebO[k]);
-    return cheb_sum(kChebE1[k], t) * exp_neg_fast(z);
+    return horner_sum(kHornE1[k], t) * exp_neg_fast(z);
   }
   const double ez = exp_neg_fast(z);
   if (z < 700.0) {
