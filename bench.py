@@ -53,11 +53,11 @@ def _peaks():
 # roofline divides by the FP64 FMA rate measured in the same run
 # (stbem_pipe_peaks) and reports the nominal fraction beside it.
 FP64_NOMINAL_TFLOPS = 1.25
-# DRAM bytes (read + write) of one lags >= 2 launch of the FP64 D tile kernel
-# at square256 (the launch of lags 32..95) from the ncu capture of the current
-# kernel (profiles/k_tile_D_f64_lag2.md gives the command); set to None
+# DRAM bytes (read + write) of the lags >= 2 launch of the FP64 D tile kernel
+# at square256 (one launch over lags 2..255) from the ncu capture of the
+# current kernel (profiles/k_tile_D_f64_lag2.md gives the command); set to None
 # whenever that kernel changes until it is captured again
-TRAFFIC_D2_BYTES = 219392 + 58880
+TRAFFIC_D2_BYTES = 2673664 + 80304384
 
 
 def _oracle_sample(n_entries, seed, rng_lags=None):
@@ -883,9 +883,9 @@ def run_ours(args):
     ms_apply = a0.elapsed_time(a1) / reps
     apply_flops = 2.0 * nx * nx * nt * (nt + 1) / 2
     apply_bytes = nt * nx * nx * 8 + 2 * nt * nx * 8
-    # dominant kernel: the FP64 D tile kernel at lags >= 2 (two lags per CTA,
-    # launches split at the space-order changes and every 64 lags), timed
-    # alone with CUDA events on the launching stream; launches counted
+    # dominant kernel: the FP64 D tile kernel at lags >= 2 (four lags per CTA,
+    # chunks within one space order each, one launch), timed alone with CUDA
+    # events on the launching stream; launches counted
     l2 = []
     for _ in range(2):
         c0, c1 = ev(), ev()
@@ -1095,7 +1095,9 @@ def d_lag2_flops(n_x, n_t, lags_per_group=4):
     kernel assembles them: runs of lags_per_group within the space-order
     segments [2, 8), [8, 32), [32, n_t), split every 64 lags) evaluates the
     Peano nodes of its L + 1 time intervals once per point, plus the per-lag
-    point work."""
+    point work.  (The kernel cuts each segment into chunks of lags_per_group
+    from the segment's first lag; 64 is a multiple of 4, so the 64-lag runs
+    here give the same chunks.)"""
     H = 2 * n_x
     pairs = H * (H + 1) // 2
     tot = 0.0

@@ -608,12 +608,28 @@ __global__ void __launch_bounds__(128) k_lag2_V(DevMesh M, int d_begin, T* __res
   if (i != j) out[base + (size_t)j * N + i] = (T)m[0];
 }
 
+// Lags >= 2 of one launch: up to three runs [lo, hi) of one space order each
+// (split at d = 8 and 32), cut into chunks of at most L consecutive lags;
+// chunk c of the launch (blockIdx.y) is the c-th in lag order, so the CTAs
+// of the most expensive lags (highest space and Peano orders) start first.
+struct MLSegs {
+  int lo[3], hi[3], n[3];   // n: chunks of the run
+};
+
+__device__ __forceinline__ void ml_chunk(const MLSegs& S, int L, int c, int* d0, int* d1) {
+  int sg = 0;
+  while (sg < 2 && c >= S.n[sg]) c -= S.n[sg++];
+  *d0 = S.lo[sg] + c * L;
+  *d1 = min(*d0 + L, S.hi[sg]);
+}
+
 // V, lags >= 2, L consecutive lags per block row (one table per CTA).
 template <typename R, typename T>
-__global__ void __launch_bounds__(128) k_lag2_V_ml(DevMesh M, int d_begin, int d_end, int L, T* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_lag2_V_ml(DevMesh M, MLSegs segs, int L, T* __restrict__ out) {
   __shared__ MLNodes<R> TN;
   const int N = M.N;
-  const int d0 = d_begin + blockIdx.y * L;
+  int d0, d_end;
+  ml_chunk(segs, L, blockIdx.y, &d0, &d_end);
   const int nl = min(L, d_end - d0);
   build_ml_nodes<R>(TN, d0, nl, M.ht, M.alpha);
   __syncthreads();
@@ -931,9 +947,10 @@ constexpr size_t tile_01_smem_bytes() {
 }
 
 template <int OP, typename R, typename T, int LM>
-__global__ void __launch_bounds__(kTileThreads) k_tile_ml(DevMesh M, int d_begin, int d_end, T* __restrict__ out) {
+__global__ void __launch_bounds__(kTileThreads) k_tile_ml(DevMesh M, MLSegs S, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int d0 = d_begin + blockIdx.y * LM;
+  int d0, d_end;
+  ml_chunk(S, LM, blockIdx.y, &d0, &d_end);
   tile_body_ml<OP, R, T, LM>(M, d0, min(LM, d_end - d0), blockIdx.x, out, smem_raw);
 }
 
@@ -1432,8 +1449,8 @@ static cudaError_t launch_op(const DevMesh& M, int lag_begin, int lag_end, T* ou
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // lags >= 2: L consecutive lags per CTA (one space order per launch, so
-  // launches split at the order changes d = 8 and 32), at most 64 lags each
+  // lags >= 2: L consecutive lags per CTA, each chunk within one space order
+  // (runs split at the order changes d = 8 and 32), all chunks in one launch
   constexpr int LM = lag_group_len<OP, R>();
   const size_t smem_ml = tile_ml_smem_bytes<OP, R, LM>();
   if (OP != STBEM_OP_V && LM > 1) {
@@ -1441,23 +1458,33 @@ static cudaError_t launch_op(const DevMesh& M, int lag_begin, int lag_end, T* ou
     if (e != cudaSuccess) return e;
   }
   const int seg[4] = {2, 8, 32, 1 << 30};
+  MLSegs S{};
+  int chunks = 0;
   for (int sg = 0; sg < 3; ++sg) {
-    const int lo = std::max(std::max(lag_begin, 2), seg[sg]), hi = std::min(lag_end, seg[sg + 1]);
-    for (int d0 = lo; d0 < hi; d0 += 64) {
-      const int d1 = std::min(d0 + 64, hi);
-      const int chunks = (d1 - d0 + LM - 1) / LM;
-      if (OP == STBEM_OP_V) {
-        const long long npair = (long long)N * (N + 1) / 2;
-        k_lag2_V_ml<R, T><<<dim3((unsigned)((npair + 127) / 128), chunks), 128, 0, s>>>(M, d0, d1, LM, out);
-      } else if (LM == 1) {
-        k_tile<OP, R, T, false><<<dim3(tiles, d1 - d0), kTileThreads, smem, s>>>(M, d0, M.sing, out);
-      } else {
-        k_tile_ml<OP, R, T, LM><<<dim3(tiles, chunks), kTileThreads, smem_ml, s>>>(M, d0, d1, out);
-      }
-      count_launches(1);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
+    S.lo[sg] = std::max(std::max(lag_begin, 2), seg[sg]);
+    S.hi[sg] = std::min(lag_end, seg[sg + 1]);
+    S.n[sg] = S.hi[sg] > S.lo[sg] ? (S.hi[sg] - S.lo[sg] + LM - 1) / LM : 0;
+    chunks += S.n[sg];
+  }
+  if (chunks == 0) return cudaSuccess;
+  if (chunks > 65535) return cudaErrorInvalidConfiguration;
+  if (OP == STBEM_OP_V) {
+    const long long npair = (long long)N * (N + 1) / 2;
+    k_lag2_V_ml<R, T><<<dim3((unsigned)((npair + 127) / 128), chunks), 128, 0, s>>>(M, S, LM, out);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  if (LM > 1) {
+    k_tile_ml<OP, R, T, LM><<<dim3(tiles, chunks), kTileThreads, smem_ml, s>>>(M, S, out);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  for (int sg = 0; sg < 3; ++sg) {   // one lag per CTA
+    if (S.n[sg] == 0) continue;
+    k_tile<OP, R, T, false><<<dim3(tiles, S.hi[sg] - S.lo[sg]), kTileThreads, smem, s>>>(M, S.lo[sg], M.sing, out);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
