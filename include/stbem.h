@@ -574,6 +574,20 @@ int stbem_solve_batched_exact(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const
                               double* dev_W, const stbem_solve_opts* opts, double inner_tol,
                               stbem_solve_info* infos, void* dev_work, size_t work_bytes);
 
+/* stbem_solve_mixed with the exact-slice operator V_exact (stbem_exact_slices
+ * of the FP64 V) in place of dev_V64: every outer residual f - V w is the
+ * exact-slice tensor-core product (normwise a few 1e-13 at n_slices = 7; see
+ * stbem_exact_operand) instead of the FP64 CUDA-core product.  The FP64 V
+ * itself is not needed.  Workspace: stbem_solve_mixed_exact_workspace_bytes()
+ * (the mixed solve's plus the slices of w), 256-byte aligned.  Requires
+ * n_x % 8 == 0 and n_t <= 4096.  Errors as stbem_solve_mixed, and
+ * STBEM_ERR_TIMEOUT. */
+int stbem_solve_mixed_exact_workspace_bytes(int n_t, int n_x, int restart, int n_slices, size_t* bytes);
+int stbem_solve_mixed_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* V_exact,
+                            const float* dev_V32, const float* dev_D32, const double* dev_L, const double* dev_f,
+                            double* dev_w, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info,
+                            void* dev_work, size_t work_bytes);
+
 /* ---- Ragged batches ----------------------------------------------------------
  * Many independent problems of different sizes (not in the paper, which solves
  * one problem at a time): every problem has its own polygon, N_x, N_t, T and

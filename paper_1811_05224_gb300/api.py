@@ -421,19 +421,32 @@ def round_f32(ctx: Context, A):
 
 def solve_mixed(ctx: Context, V64, V32, f, D32=None, L=None, tol: float = 1e-8, inner_tol: float = 1e-4,
                 max_iter: int = 500, restart: int = 200, work=None, out=None, raise_on_fail: bool = True):
-    """FP64 iterative refinement around preconditioned GMRES on FP32 operators."""
+    """FP64 iterative refinement around preconditioned GMRES on FP32 operators.
+    V64 gives the outer residuals: the FP64 lag blocks (an FP64 CUDA-core
+    product) or their ExactOperand (the exact-slice tensor-core product)."""
     n_t, n_x = V64.shape[0], V64.shape[1]
+    exact = isinstance(V64, ExactOperand)
     opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(D32, L))
     info = capi.SolveInfo()
     if out is None:
         out = ctx.empty((n_t, n_x))
     if work is None:
         nb = ctypes.c_size_t()
-        ctx.check(ctx.lib.stbem_solve_mixed_workspace_bytes(n_t, n_x, restart, ctypes.byref(nb)))
+        if exact:
+            ctx.check(ctx.lib.stbem_solve_mixed_exact_workspace_bytes(n_t, n_x, restart, V64.n_slices,
+                                                                      ctypes.byref(nb)))
+        else:
+            ctx.check(ctx.lib.stbem_solve_mixed_workspace_bytes(n_t, n_x, restart, ctypes.byref(nb)))
         work = torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
-    code = ctx.lib.stbem_solve_mixed(ctx.h, n_t, n_x, _ptr(V64), _ptr(V32), _ptr(D32), _ptr(L), _ptr(f),
-                                     _ptr(out), ctypes.byref(opts), float(inner_tol), ctypes.byref(info),
-                                     _ptr(work), work.numel())
+    if exact:
+        sv = V64.c_struct()
+        code = ctx.lib.stbem_solve_mixed_exact(ctx.h, n_t, n_x, ctypes.byref(sv), _ptr(V32), _ptr(D32), _ptr(L),
+                                               _ptr(f), _ptr(out), ctypes.byref(opts), float(inner_tol),
+                                               ctypes.byref(info), _ptr(work), work.numel())
+    else:
+        code = ctx.lib.stbem_solve_mixed(ctx.h, n_t, n_x, _ptr(V64), _ptr(V32), _ptr(D32), _ptr(L), _ptr(f),
+                                         _ptr(out), ctypes.byref(opts), float(inner_tol), ctypes.byref(info),
+                                         _ptr(work), work.numel())
     res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
     if code != capi.STBEM_OK and raise_on_fail:
         ctx.check(code)

@@ -47,6 +47,7 @@ EXPORTS = [
     "stbem_exact_slices", "stbem_apply_tc_exact", "stbem_apply_exact_workspace_bytes", "stbem_apply_exact",
     "stbem_solve_batched_exact_workspace_bytes", "stbem_solve_batched_exact",
     "stbem_tune_cache_path", "stbem_tune_cache_get", "stbem_tune_cache_put", "stbem_tune_cache_clear", "stbem_tc_tune",
+    "stbem_solve_mixed_exact_workspace_bytes", "stbem_solve_mixed_exact",
 ]
 
 
@@ -141,6 +142,9 @@ def load(path: str = LIB_PATH):
     L.stbem_ragged_solve_mixed.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
+    L.stbem_solve_mixed_exact_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_solve_mixed_exact.argtypes = [vp, i, i, P(ExactOperand), vp, vp, vp, vp, vp, P(SolveOpts), d,
+                                          P(SolveInfo), vp, sz]
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]
     L.stbem_to_bf16.argtypes = [vp, i, sz, vp, vp]
     L.stbem_apply_tc.argtypes = [vp, i, i, vp, i, vp, vp]

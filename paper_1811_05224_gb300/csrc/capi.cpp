@@ -1435,24 +1435,38 @@ int stbem_solve_mixed_workspace_bytes(int n_t, int n_x, int restart, size_t* byt
   return STBEM_OK;
 }
 
-int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const float* V32, const float* D32,
-                      const double* L, const double* f, double* w, const stbem_solve_opts* opts,
-                      double inner_tol, stbem_solve_info* info, void* work, size_t work_bytes) {
+namespace {
+// The mixed solve; the outer residual f - V w uses the FP64 operator V64 or,
+// when Vx is given, its exact-slice form on the tensor cores.
+int solve_mixed_impl(stbem_ctx* ctx, int nt, int nx, const double* V64, const stbem_exact_operand* Vx,
+                     const float* V32, const float* D32, const double* L, const double* f, double* w,
+                     const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info, void* work,
+                     size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
-  if (!V64 || !V32 || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: NULL pointer");
+  if ((!V64 && !Vx) || !V32 || !f || !w || !opts || !info || !work)
+    return fail(ctx, STBEM_ERR_ARG, "solve_mixed: NULL pointer");
   if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: bad sizes");
+  if (Vx) {
+    if (const int r = check_exact_operand(ctx, "solve_mixed_exact", Vx)) return r;
+    if (!stbem::apply_tc_exact_supported(nt, nx, 1, Vx->n_slices))
+      return fail(ctx, STBEM_ERR_ARG, "solve_mixed_exact: unsupported sizes for the exact product");
+    if (reinterpret_cast<uintptr_t>(work) & 255)
+      return fail(ctx, STBEM_ERR_ARG, "solve_mixed_exact: workspace not 256-byte aligned");
+  }
   const int restart = opts->restart, maxit = opts->max_iter;
   if (restart < 1 || maxit < 1 || !(opts->tol > 0) || !(inner_tol > 0) || !(inner_tol < 1))
     return fail(ctx, STBEM_ERR_ARG, "solve_mixed: bad options");
   const bool prec = opts->precondition != 0;
   if (prec && (!D32 || !L)) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: preconditioner needs D and L");
   const size_t N = (size_t)nt * nx;
-  const size_t need = solve_bytes(nt, nx, restart) + 2 * N * sizeof(double);
+  const size_t base = align256(solve_bytes(nt, nx, restart) + 2 * N * sizeof(double));
+  const size_t need = Vx ? base + exact_x_bytes(nt, nx, 1, Vx->n_slices) : solve_bytes(nt, nx, restart) + 2 * N * sizeof(double);
   if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "solve_mixed: workspace %zu < %zu bytes", work_bytes, need);
   SolveWork W;
   carve(work, solve_bytes(nt, nx, restart), nt, nx, restart, &W);
   double* r = reinterpret_cast<double*>(static_cast<char*>(work) + solve_bytes(nt, nx, restart));
   double* dw = r + N;
+  void* xwork = static_cast<char*>(work) + base;   // slices of w (exact residual)
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_mixed: set device");
   cudaStream_t s = ctx->stream;
   auto norm = [&](const double* x, double* out) -> cudaError_t {
@@ -1495,8 +1509,16 @@ int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const f
     if (st == STBEM_ERR_NAN || st == STBEM_ERR_BREAKDOWN) { status = st; break; }
     if (st != STBEM_OK && st != STBEM_ERR_NOCONV) return st;
     CUDA_TRY(ctx, stbem::axpy_launch(1.0, dw, w, N, s), "solve_mixed: w += dw");
-    // FP64 residual with the FP64 operator
-    CUDA_TRY(ctx, stbem::apply_launch(STBEM_F64, false, nt, nx, V64, 1, w, W.v, W.apply, s), "solve_mixed: V w");
+    // residual with the FP64 operator (or its exact slices)
+    if (Vx) {
+      CUDA_TRY(ctx, stbem::tc_error_reset(s), "solve_mixed: reset error word");
+      CUDA_TRY(ctx, apply_exact(nt, nx, *Vx, 1, w, W.v, xwork, s), "solve_mixed: exact V w");
+      int flag = 0;
+      CUDA_TRY(ctx, stbem::tc_error_read(&flag, s), "solve_mixed: read error word");
+      if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "solve_mixed: a tensor-core pipeline wait timed out");
+    } else {
+      CUDA_TRY(ctx, stbem::apply_launch(STBEM_F64, false, nt, nx, V64, 1, w, W.v, W.apply, s), "solve_mixed: V w");
+    }
     CUDA_TRY(ctx, stbem::sub_launch(f, W.v, r, N, s), "solve_mixed: f - V w");
     if (it == 0) { status = STBEM_ERR_NOCONV; break; }
   }
@@ -1509,6 +1531,31 @@ int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const f
                 : status == STBEM_ERR_NOCONV ? "no convergence" : "breakdown (singular operator)",
                 total, relres);
   return STBEM_OK;
+}
+}  // namespace
+
+int stbem_solve_mixed(stbem_ctx* ctx, int nt, int nx, const double* V64, const float* V32, const float* D32,
+                      const double* L, const double* f, double* w, const stbem_solve_opts* opts,
+                      double inner_tol, stbem_solve_info* info, void* work, size_t work_bytes) {
+  if (ctx && !V64) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: NULL pointer");
+  return solve_mixed_impl(ctx, nt, nx, V64, nullptr, V32, D32, L, f, w, opts, inner_tol, info, work, work_bytes);
+}
+
+int stbem_solve_mixed_exact_workspace_bytes(int n_t, int n_x, int restart, int n_slices, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || restart < 1 || n_slices < stbem::kExactMinSlices ||
+      n_slices > stbem::kExactMaxSlices)
+    return STBEM_ERR_ARG;
+  *bytes = align256(solve_bytes(n_t, n_x, restart) + 2 * (size_t)n_t * n_x * sizeof(double)) +
+           exact_x_bytes(n_t, n_x, 1, n_slices);
+  return STBEM_OK;
+}
+
+int stbem_solve_mixed_exact(stbem_ctx* ctx, int nt, int nx, const stbem_exact_operand* Vx, const float* V32,
+                            const float* D32, const double* L, const double* f, double* w,
+                            const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info, void* work,
+                            size_t work_bytes) {
+  if (ctx && !Vx) return fail(ctx, STBEM_ERR_ARG, "solve_mixed_exact: NULL operand");
+  return solve_mixed_impl(ctx, nt, nx, nullptr, Vx, V32, D32, L, f, w, opts, inner_tol, info, work, work_bytes);
 }
 
 int stbem_round_f32(stbem_ctx* ctx, size_t n, const double* src, float* dst) {

@@ -224,3 +224,31 @@ def test_batched_solve_exact_residual_against_oracle(ctx):
         assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(Fb)
         w_ref = OS.forward_substitution(Vo, Fb)
         assert np.linalg.norm(Wn - w_ref) <= 1e-7 * np.linalg.norm(w_ref)
+
+
+def test_mixed_solve_exact_residual_against_oracle(ctx):
+    """The mixed solve whose outer residuals are exact-slice products
+    (stbem_solve_mixed_exact; no FP64 V product): the FP64 residual with the
+    oracle's V below 1e-8 and w within 1e-6 of the oracle's block forward
+    substitution, as for the FP64-residual mixed solve."""
+    import paper_1811_05224_gb300 as P
+    import workloads as W
+    from oracle import assembly as OA
+    from oracle.geometry import BoundaryMesh
+    p = W.config("square32")
+    m = P.Mesh(ctx, p.vertices, p.T, p.n_t, p.alpha)
+    om = BoundaryMesh(p.vertices, p.T, p.n_t, p.alpha)
+    V = P.assemble(ctx, m, "V")
+    K = P.assemble(ctx, m, "K")
+    D32 = P.assemble(ctx, m, "D", "f32")
+    V32 = P.round_f32(ctx, V)
+    L = P.lumped_mass(ctx, m)
+    g, f = P.rhs(ctx, m, K, p.y_star)
+    wm, info = P.solve_mixed(ctx, P.exact_slices(ctx, V, 7), V32, f, D32, L, tol=1e-8, inner_tol=1e-4)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8, info
+    Vo = OA.assemble("V", om)
+    fo = f.cpu().numpy()
+    r = fo - OS.toeplitz_apply(Vo, wm.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(fo)
+    w_ref = OS.forward_substitution(Vo, fo)
+    assert np.linalg.norm(wm.cpu().numpy() - w_ref) <= 1e-6 * np.linalg.norm(w_ref)

@@ -115,3 +115,11 @@ def test_precision_workload_mixed_solve(ctx):
     assert info["status"] == 0
     r = f - P.apply(ctx, V, w)
     assert float(r.norm() / f.norm()) <= 1e-8
+    # the same solve with exact-slice outer residuals (one step tile per 128
+    # steps, 1024 x 1024 lag blocks: the full-size case of that product)
+    Vx = P.exact_slices(ctx, V, 7)
+    wx, infox = P.solve_mixed(ctx, Vx, V32, f, D32, Minv, tol=1e-8, inner_tol=1e-4, max_iter=400, restart=60)
+    assert infox["status"] == 0
+    r = f - P.apply(ctx, V, wx)
+    assert float(r.norm() / f.norm()) <= 1.01e-8
+    assert float((wx - w).norm() / w.norm()) <= 1e-6
