@@ -1131,7 +1131,7 @@ def main():
                     help="skip the L-shape N_x = N_t = 1024 mixed-versus-FP64 component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
-    ap.add_argument("--component", choices=["tc", "grad", "precision", "initial"], default=None,
+    ap.add_argument("--component", choices=["tc", "grad", "precision", "initial", "f32apply"], default=None,
                     help="run one kernel family alone on a small case (for ncu captures) and print its timing")
     ap.add_argument("--size", type=int, default=256, help="N_x = N_t of --component's case")
     ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --component tc")
@@ -1239,6 +1239,28 @@ def run_component(args):
         # --size is the level L of the Section 4 example (2^L segments per side)
         res = run_initial(ctx, dev, stream, L=n if n <= 9 else 6)
         print(json.dumps(res), flush=True)
+        return 0
+    if args.component == "f32apply":
+        # the FP32 CUDA-core product (register-tiled kernel) of a unit-square V
+        # with n_t = N_x = --size, one right-hand side
+        mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
+        V32 = P.assemble(ctx, mesh, "V", "f32")
+        g = torch.Generator(device="cpu").manual_seed(3)
+        x = torch.randn((n, n), generator=g, dtype=torch.float64).to(dev)
+        work = P.api.apply_workspace(ctx, n, n, 1, "f32")
+        y = torch.empty_like(x)
+        for _ in range(2):
+            P.apply(ctx, V32, x, work=work, out=y)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        P.apply(ctx, V32, x, work=work, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        flops = 2.0 * n * n * n * (n + 1) / 2
+        out.update({"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                    "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / P.pipe_peaks(ctx)["fp32_tflops"]})
+        print(json.dumps(out))
         return 0
     if args.component == "tc":
         mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)

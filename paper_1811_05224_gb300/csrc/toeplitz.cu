@@ -186,8 +186,16 @@ k_apply(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const TA
 // of N_x terms) is added into a compensated (hi, lo) FP32 pair per output
 // (Knuth's two-sum, 6 FP32 operations), so lags accumulate without FP32 loss
 // and without FP64 arithmetic, which runs at 1/72 of the FP32 rate here.
+// The (hi, lo) pairs live in shared memory ([k][thread], conflict-free) and
+// are touched once per lag; the 16-column stages of all lags of the chunk
+// form one software pipeline: the next stage's A and x are loaded into
+// registers while the current one is multiplied from the other half of a
+// double-buffered shared tile (one barrier per stage).
 // Requires N_x % 4 == 0 (16-byte rows).
 constexpr int TI4 = 128, TM4 = 64, TJ4 = 16;
+// dynamic shared memory of the kernels: two stages of A (16 x 128) and x
+// (16 x 64), then the (hi, lo) pairs (2 x 32 x 256 floats)
+constexpr size_t kApply32Smem = (2 * TJ4 * TI4 + 2 * TJ4 * TM4 + 2 * 32 * 256) * sizeof(float);
 
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   const float s = hi + v;
@@ -200,73 +208,100 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
 __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi,
                                              const float* __restrict__ A, const double* __restrict__ x,
                                              double* __restrict__ part, int it, int ch, int b, int mt,
-                                             float (*As)[TI4], float (*Xs)[TM4]) {
+                                             float* smem) {
   const int m0 = mt * TM4, i0 = it * TI4;
   const int mmax = min(m0 + TM4, nt) - 1;
   const int d0 = lag_lo + ch * DC;
   if (d0 > mmax || d0 >= lag_hi) return;
   const int d1 = min(min(d0 + DC, mmax + 1), lag_hi);
+  float (*As)[TJ4][TI4] = reinterpret_cast<float (*)[TJ4][TI4]>(smem);                  // [2]
+  float (*Xs)[TJ4][TM4] = reinterpret_cast<float (*)[TJ4][TM4]>(smem + 2 * TJ4 * TI4);  // [2]
+  float* H = smem + 2 * TJ4 * TI4 + 2 * TJ4 * TM4;                                        // [32][256]
+  float* Lo = H + 32 * 256;                                                               // [32][256]
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const double* xb = x + (size_t)b * nt * nx;
-  float hi[8][4], lo[8][4];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    H[k * 256 + tid] = 0.f;
+    Lo[k * 256 + tid] = 0.f;
+  }
+  const int nj = (nx + TJ4 - 1) / TJ4;
+  const int stages = (d1 - d0) * nj;
+  // this thread's loads of one stage: 2 float4 of A, 4 values of x
+  float4 ra[2];
+  float rx[4];
+  auto load = [&](int st) {
+    const int d = d0 + st / nj, j0 = (st % nj) * TJ4;
+    const float* Ad = A + (size_t)(d - lag_lo) * nx * nx;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + q * 256;
+      const int ii = e % TI4, jq = e / TI4;
+      const int gi = i0 + ii, gj = j0 + jq * 4;
+      ra[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gi < nx && gj < nx) ra[q] = *reinterpret_cast<const float4*>(Ad + (size_t)gi * nx + gj);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      const int jj = e % TJ4, mm = e / TJ4;
+      const int m = m0 + mm, gj = j0 + jj;
+      rx[q] = (m <= mmax && m - d >= 0 && gj < nx) ? (float)xb[(size_t)(m - d) * nx + gj] : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + q * 256;
+      const int ii = e % TI4, jq = e / TI4;
+      As[buf][jq * 4 + 0][ii] = ra[q].x;
+      As[buf][jq * 4 + 1][ii] = ra[q].y;
+      As[buf][jq * 4 + 2][ii] = ra[q].z;
+      As[buf][jq * 4 + 3][ii] = ra[q].w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      Xs[buf][e % TJ4][e / TJ4] = rx[q];
+    }
+  };
+  float acc[8][4];
 #pragma unroll
   for (int c = 0; c < 8; ++c)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      hi[c][a] = 0.f;
-      lo[c][a] = 0.f;
+    for (int a = 0; a < 4; ++a) acc[c][a] = 0.f;
+  load(0);
+  for (int st = 0; st < stages; ++st) {
+    const int buf = st & 1;
+    store(buf);
+    __syncthreads();
+    if (st + 1 < stages) load(st + 1);     // in flight while this stage is multiplied
+#pragma unroll
+    for (int jj = 0; jj < TJ4; ++jj) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][jj][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][jj][ty * 8 + 4]);
+      const float4 xv = *reinterpret_cast<const float4*>(&Xs[buf][jj][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[c][a] = fmaf(av[c], bv[a], acc[c][a]);
     }
-  for (int d = d0; d < d1; ++d) {
-    const float* Ad = A + (size_t)(d - lag_lo) * nx * nx;
-    float acc[8][4];
+    if (st % nj == nj - 1) {   // the lag's partial is complete: fold it, restart
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+      for (int c = 0; c < 8; ++c)
 #pragma unroll
-      for (int a = 0; a < 4; ++a) acc[c][a] = 0.f;
-    for (int j0 = 0; j0 < nx; j0 += TJ4) {
-      // A tile: 128 rows x 16 columns as float4 along j, stored transposed
-#pragma unroll
-      for (int q = 0; q < (TI4 * TJ4 / 4) / 256; ++q) {
-        const int e = tid + q * 256;
-        const int ii = e % TI4, jq = e / TI4;
-        const int gi = i0 + ii, gj = j0 + jq * 4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gi < nx && gj < nx) v = *reinterpret_cast<const float4*>(Ad + (size_t)gi * nx + gj);
-        As[jq * 4 + 0][ii] = v.x;
-        As[jq * 4 + 1][ii] = v.y;
-        As[jq * 4 + 2][ii] = v.z;
-        As[jq * 4 + 3][ii] = v.w;
-      }
-      // x tile: x[m - d][j0 + jj] for the 64 steps of the tile
-#pragma unroll
-      for (int q = 0; q < (TM4 * TJ4) / 256; ++q) {
-        const int e = tid + q * 256;
-        const int jj = e % TJ4, mm = e / TJ4;
-        const int m = m0 + mm, gj = j0 + jj;
-        float v = 0.f;
-        if (m <= mmax && m - d >= 0 && gj < nx) v = (float)xb[(size_t)(m - d) * nx + gj];
-        Xs[jj][mm] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int jj = 0; jj < TJ4; ++jj) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[jj][ty * 8]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[jj][ty * 8 + 4]);
-        const float4 xv = *reinterpret_cast<const float4*>(&Xs[jj][tx * 4]);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-#pragma unroll
-          for (int a = 0; a < 4; ++a) acc[c][a] = fmaf(av[c], bv[a], acc[c][a]);
-      }
-      __syncthreads();
+        for (int a = 0; a < 4; ++a) {
+          const int k = c * 4 + a;
+          float h = H[k * 256 + tid], l = Lo[k * 256 + tid];
+          two_sum_add(h, l, acc[c][a]);
+          H[k * 256 + tid] = h;
+          Lo[k * 256 + tid] = l;
+          acc[c][a] = 0.f;
+        }
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) two_sum_add(hi[c][a], lo[c][a], acc[c][a]);
   }
   double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TM4) * nx;
 #pragma unroll
@@ -276,7 +311,8 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int gi = i0 + ty * 8 + c;
-      if (gi < nx) pt[(size_t)mm * nx + gi] = (double)hi[c][a] + (double)lo[c][a];
+      const int k = c * 4 + a;
+      if (gi < nx) pt[(size_t)mm * nx + gi] = (double)H[k * 256 + tid] + (double)Lo[k * 256 + tid];
     }
   }
 }
@@ -284,10 +320,9 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
 __global__ void __launch_bounds__(256, 2)
 k_apply32(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const float* __restrict__ A,
           const double* __restrict__ x, double* __restrict__ part) {
-  __shared__ __align__(16) float As[TJ4][TI4];
-  __shared__ __align__(16) float Xs[TJ4][TM4];
+  extern __shared__ __align__(16) float smem32[];
   apply32_body(nt, nx, MT, CH, DC, lag_lo, lag_hi, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT,
-               blockIdx.z % MT, As, Xs);
+               blockIdx.z % MT, smem32);
 }
 
 // ---- ragged batches ------------------------------------------------------------------
@@ -335,8 +370,7 @@ __global__ void __launch_bounds__(256, 2)
 k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restrict__ order,
                  const long long* __restrict__ prefix, int P, unsigned long long* __restrict__ counter,
                  const float* __restrict__ A, const double* __restrict__ x, double* __restrict__ part) {
-  __shared__ __align__(16) float As[TJ4][TI4];
-  __shared__ __align__(16) float Xs[TJ4][TM4];
+  extern __shared__ __align__(16) float smem32[];
   __shared__ long long item_s;
   const long long total = prefix[P];
   for (;;) {
@@ -352,7 +386,7 @@ k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restric
     const long long r = u / pl.IT;
     const int mt = (int)(r % pl.MT), ch = (int)(r / pl.MT);
     apply32_body(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, 0, pl.nt, A + pl.a_off, x + pl.v_off, part + pl.part_off, it,
-                 ch, 0, mt, As, Xs);
+                 ch, 0, mt, smem32);
     __syncthreads();
   }
 }
@@ -405,8 +439,11 @@ __global__ void k_apply_reduce(int nt, int nx, int n_rhs, int MT, int CH, int DC
 static cudaError_t launch32(int nt, int nx, int lag_lo, int lag_hi, const float* A, int n_rhs, const double* x,
                             double* y, bool accumulate, double* part, cudaStream_t s) {
   const ApplyPlan p = make_plan(nt, nx, TM4, TI4, lag_hi - lag_lo);
-  k_apply32<<<dim3(p.IT, p.CH, n_rhs * p.MT), 256, 0, s>>>(nt, nx, p.MT, p.CH, p.DC, lag_lo, lag_hi, A, x, part);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(k_apply32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApply32Smem);
+  if (e != cudaSuccess) return e;
+  k_apply32<<<dim3(p.IT, p.CH, n_rhs * p.MT), 256, kApply32Smem, s>>>(nt, nx, p.MT, p.CH, p.DC, lag_lo, lag_hi,
+                                                                       A, x, part);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launches(2);
   const size_t total = (size_t)n_rhs * nt * nx;
@@ -535,10 +572,13 @@ cudaError_t ragged_apply_launch(int prec, bool fp32_tiles, const RaggedApplyPlan
     k_ragged_apply<double, double><<<sms * (occ > 0 ? occ : 1), kApplyThreads, 0, s>>>(
         plans, items.order, items.prefix, P, counter, static_cast<const double*>(A), x, part);
   } else if (fp32_tiles) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply32, 256, 0);
+    e = cudaFuncSetAttribute(k_ragged_apply32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApply32Smem);
     if (e != cudaSuccess) return e;
-    k_ragged_apply32<<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(plans, items.order, items.prefix, P, counter,
-                                                              static_cast<const float*>(A), x, part);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply32, 256, kApply32Smem);
+    if (e != cudaSuccess) return e;
+    k_ragged_apply32<<<sms * (occ > 0 ? occ : 1), 256, kApply32Smem, s>>>(plans, items.order, items.prefix, P,
+                                                                          counter, static_cast<const float*>(A), x,
+                                                                          part);
   } else {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply<float, float>, kApplyThreads, 0);
     if (e != cudaSuccess) return e;
