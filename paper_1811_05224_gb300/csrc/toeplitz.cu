@@ -24,6 +24,8 @@
 namespace stbem {
 
 constexpr int TI = 64, TM = 32, TJ = 16, kApplyThreads = 256;
+// FP32 register-tiled product: 128 rows x 128 steps per CTA, 16 columns per stage
+constexpr int TI4 = 128, TM4 = 128, TJ4 = 16;
 
 struct ApplyPlan {
   int MT, IT, CH, DC;
@@ -48,22 +50,23 @@ static ApplyPlan make_plan(int nt, int nx, int tm = TM, int ti = TI, int nlag = 
   return p;
 }
 
-// FP32 forward products use the register-tiled kernel (128 x 64 tiles) when
-// rows are 16-byte aligned and its causal tiles alone fill two waves of
-// 2 CTAs per SM; smaller products keep the 64 x 32 tiles, which need fewer
-// lag chunks (and partial sums) for the same parallelism.
+// FP32 forward products use the register-tiled kernel (128 x 128 tiles) when
+// rows are 16-byte aligned and its causal tiles alone fill one wave of one
+// CTA per SM (lag chunks multiply them further); smaller products keep the
+// 64 x 32 tiles, which need fewer lag chunks (and partial sums) for the same
+// parallelism.
 static bool use_apply32(int nx) { return nx % 4 == 0; }
 static bool use_apply32(int nt, int nx, int n_rhs) {
-  const long long it = (nx + 127) / 128, mt = (nt + 63) / 64;
-  return use_apply32(nx) && (long long)n_rhs * it * mt * (mt + 1) / 2 >= 2LL * 2 * sm_count();
+  const long long it = (nx + TI4 - 1) / TI4, mt = (nt + TM4 - 1) / TM4;
+  return use_apply32(nx) && (long long)n_rhs * it * mt * (mt + 1) / 2 >= (long long)sm_count();
 }
 
 size_t apply_range_workspace_bytes(int nt, int nx, int nlag, int n_rhs) {
   const ApplyPlan p = make_plan(nt, nx, TM, TI, nlag);
   size_t b = (size_t)n_rhs * p.MT * p.CH * TM * (size_t)nx * sizeof(double);
   if (use_apply32(nt, nx, n_rhs)) {
-    const ApplyPlan q = make_plan(nt, nx, 64, 128, nlag);
-    b = std::max(b, (size_t)n_rhs * q.MT * q.CH * 64 * (size_t)nx * sizeof(double));
+    const ApplyPlan q = make_plan(nt, nx, TM4, TI4, nlag);
+    b = std::max(b, (size_t)n_rhs * q.MT * q.CH * TM4 * (size_t)nx * sizeof(double));
   }
   return b;
 }
@@ -180,22 +183,23 @@ k_apply(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const TA
 }
 
 // ---- FP32 forward product, register-tiled ----------------------------------------------
-// A CTA owns 128 rows x 64 time steps (one right-hand side, one lag chunk);
-// thread (ty, tx) of 16 x 16 computes rows ty*8.. and steps tx*4.. from float4
-// shared-memory reads (32 FFMA per 3 loads).  Each lag's FP32 partial (a chain
-// of N_x terms) is added into a compensated (hi, lo) FP32 pair per output
-// (Knuth's two-sum, 6 FP32 operations), so lags accumulate without FP32 loss
-// and without FP64 arithmetic, which runs at 1/72 of the FP32 rate here.
-// The (hi, lo) pairs live in shared memory ([k][thread], conflict-free) and
-// are touched once per lag; the 16-column stages of all lags of the chunk
-// form one software pipeline: the next stage's A and x are loaded into
-// registers while the current one is multiplied from the other half of a
-// double-buffered shared tile (one barrier per stage).
-// Requires N_x % 4 == 0 (16-byte rows).
-constexpr int TI4 = 128, TM4 = 64, TJ4 = 16;
-// dynamic shared memory of the kernels: two stages of A (16 x 128) and x
-// (16 x 64), then the (hi, lo) pairs (2 x 32 x 256 floats)
-constexpr size_t kApply32Smem = (2 * TJ4 * TI4 + 2 * TJ4 * TM4 + 2 * 32 * 256) * sizeof(float);
+// A CTA of 16 x 16 threads owns 128 rows x 128 time steps (one right-hand
+// side, one lag chunk); thread (ty, tx) computes the rows ty*4.. and
+// 64 + ty*4.. and the steps tx*4.. and 64 + tx*4.. (split halves keep the
+// float4 shared-memory reads conflict-free): 64 FFMA per 4 float4 loads.  Each
+// lag's FP32 partial (a chain of N_x terms) is added into a compensated
+// (hi, lo) FP32 pair per output (Knuth's two-sum, 6 FP32 operations), so lags
+// accumulate without FP32 loss and without FP64 arithmetic, which runs at 1/72
+// of the FP32 rate here.  The (hi, lo) pairs live in shared memory
+// ([k][thread], conflict-free) and are touched once per lag; the 16-column
+// stages of all lags of the chunk form one software pipeline: the next
+// stage's A and x are loaded into registers while the current one is
+// multiplied from the other half of a double-buffered shared tile (one
+// barrier per stage).  Requires N_x % 4 == 0 (16-byte rows).
+constexpr int kXsLd = TM4 + 4;   // x tile row length: transposing stores 2-way at most
+// dynamic shared memory: two stages of A (16 x 128) and x (16 x 132), then
+// the (hi, lo) pairs (2 x 64 x 256 floats)
+constexpr size_t kApply32Smem = (2 * TJ4 * TI4 + 2 * TJ4 * kXsLd + 2 * 64 * 256) * sizeof(float);
 
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   const float s = hi + v;
@@ -214,23 +218,24 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
   const int d0 = lag_lo + ch * DC;
   if (d0 > mmax || d0 >= lag_hi) return;
   const int d1 = min(min(d0 + DC, mmax + 1), lag_hi);
-  float (*As)[TJ4][TI4] = reinterpret_cast<float (*)[TJ4][TI4]>(smem);                  // [2]
-  float (*Xs)[TJ4][TM4] = reinterpret_cast<float (*)[TJ4][TM4]>(smem + 2 * TJ4 * TI4);  // [2]
-  float* H = smem + 2 * TJ4 * TI4 + 2 * TJ4 * TM4;                                        // [32][256]
-  float* Lo = H + 32 * 256;                                                               // [32][256]
+  float (*As)[TJ4][TI4] = reinterpret_cast<float (*)[TJ4][TI4]>(smem);                   // [2]
+  float (*Xs)[TJ4][kXsLd] = reinterpret_cast<float (*)[TJ4][kXsLd]>(smem + 2 * TJ4 * TI4);  // [2]
+  float* H = smem + 2 * TJ4 * TI4 + 2 * TJ4 * kXsLd;                                        // [64][256]
+  float* Lo = H + 64 * 256;                                                                 // [64][256]
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const double* xb = x + (size_t)b * nt * nx;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
+  for (int k = 0; k < 64; ++k) {
     H[k * 256 + tid] = 0.f;
     Lo[k * 256 + tid] = 0.f;
   }
   const int nj = (nx + TJ4 - 1) / TJ4;
   const int stages = (d1 - d0) * nj;
-  // this thread's loads of one stage: 2 float4 of A, 4 values of x
+  // this thread's loads of one stage: 2 float4 of A, 8 values of x (kept in
+  // FP64 until the store, so that no conversion waits on a load in flight)
   float4 ra[2];
-  float rx[4];
+  double rx[8];
   auto load = [&](int st) {
     const int d = d0 + st / nj, j0 = (st % nj) * TJ4;
     const float* Ad = A + (size_t)(d - lag_lo) * nx * nx;
@@ -243,11 +248,11 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
       if (gi < nx && gj < nx) ra[q] = *reinterpret_cast<const float4*>(Ad + (size_t)gi * nx + gj);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const int e = tid + q * 256;
       const int jj = e % TJ4, mm = e / TJ4;
       const int m = m0 + mm, gj = j0 + jj;
-      rx[q] = (m <= mmax && m - d >= 0 && gj < nx) ? (float)xb[(size_t)(m - d) * nx + gj] : 0.f;
+      rx[q] = (m <= mmax && m - d >= 0 && gj < nx) ? xb[(size_t)(m - d) * nx + gj] : 0.0;
     }
   };
   auto store = [&](int buf) {
@@ -261,16 +266,16 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
       As[buf][jq * 4 + 3][ii] = ra[q].w;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const int e = tid + q * 256;
-      Xs[buf][e % TJ4][e / TJ4] = rx[q];
+      Xs[buf][e % TJ4][e / TJ4] = (float)rx[q];
     }
   };
-  float acc[8][4];
+  float acc[8][8];    // [row r: ty*4 + r (r < 4), 64 + ty*4 + r - 4][step c likewise]
 #pragma unroll
-  for (int c = 0; c < 8; ++c)
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) acc[c][a] = 0.f;
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
   load(0);
   for (int st = 0; st < stages; ++st) {
     const int buf = st & 1;
@@ -279,45 +284,46 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
     if (st + 1 < stages) load(st + 1);     // in flight while this stage is multiplied
 #pragma unroll
     for (int jj = 0; jj < TJ4; ++jj) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][jj][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][jj][ty * 8 + 4]);
-      const float4 xv = *reinterpret_cast<const float4*>(&Xs[buf][jj][tx * 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][jj][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][jj][64 + ty * 4]);
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[buf][jj][tx * 4]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[buf][jj][64 + tx * 4]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[4] = {xv.x, xv.y, xv.z, xv.w};
+      const float bv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
+      for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[c][a] = fmaf(av[c], bv[a], acc[c][a]);
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
     }
     if (st % nj == nj - 1) {   // the lag's partial is complete: fold it, restart
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
+      for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int k = c * 4 + a;
+        for (int c = 0; c < 8; ++c) {
+          const int k = r * 8 + c;
           float h = H[k * 256 + tid], l = Lo[k * 256 + tid];
-          two_sum_add(h, l, acc[c][a]);
+          two_sum_add(h, l, acc[r][c]);
           H[k * 256 + tid] = h;
           Lo[k * 256 + tid] = l;
-          acc[c][a] = 0.f;
+          acc[r][c] = 0.f;
         }
     }
   }
   double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TM4) * nx;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int mm = tx * 4 + a;
+  for (int c = 0; c < 8; ++c) {
+    const int mm = (c < 4 ? 0 : 64) + tx * 4 + (c & 3);
     if (m0 + mm > mmax) continue;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int gi = i0 + ty * 8 + c;
-      const int k = c * 4 + a;
+    for (int r = 0; r < 8; ++r) {
+      const int gi = i0 + (r < 4 ? 0 : 64) + ty * 4 + (r & 3);
+      const int k = r * 8 + c;
       if (gi < nx) pt[(size_t)mm * nx + gi] = (double)H[k * 256 + tid] + (double)Lo[k * 256 + tid];
     }
   }
 }
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 1)
 k_apply32(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const float* __restrict__ A,
           const double* __restrict__ x, double* __restrict__ part) {
   extern __shared__ __align__(16) float smem32[];
@@ -366,7 +372,7 @@ k_ragged_apply(const RaggedApplyPlan* __restrict__ plans, const int* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 1)
 k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restrict__ order,
                  const long long* __restrict__ prefix, int P, unsigned long long* __restrict__ counter,
                  const float* __restrict__ A, const double* __restrict__ x, double* __restrict__ part) {

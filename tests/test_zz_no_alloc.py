@@ -51,7 +51,7 @@ def _workspace_apply(lib, h, capi, prec, tr, A, x):
 
 
 # (n_t, n_x, right-hand sides, precision, transpose); the third case has
-# N_x % 4 == 0 and enough causal 128 x 64 tiles (35 x 36 / 2 = 630 >= 2 CTAs
+# N_x % 4 == 0 and enough causal 128 x 128 tiles (18 x 19 / 2 = 171 >= one CTA
 # per SM, two waves) for the register-tiled FP32 forward kernel, whose
 # partial sums (2.4 MB) still fit the fixed scratch
 CASES = [(256, 256, 1, "f64", 0), (37, 45, 3, "f32", 1), (2240, 4, 1, "f32", 0), (70, 64, 2, "f64", 1)]
