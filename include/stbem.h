@@ -518,8 +518,11 @@ int stbem_apply_tc_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_ope
                          const stbem_exact_operand* x, double* dev_y);
 
 /* The same product with x in FP64 ([n_rhs][n_t][n_x]), sliced inside the call
- * into dev_work (stbem_apply_exact_workspace_bytes(), 256-byte aligned).
- * Blocks the host.  Errors as stbem_apply_tc_exact, STBEM_ERR_NOMEM. */
+ * into dev_work (stbem_apply_exact_workspace_bytes(), 256-byte aligned).  When
+ * the output tiles are too few to fill the GPU (small n_rhs) the workspace
+ * also holds partial products of chunks of 64 lags per tile, summed in chunk
+ * order afterwards.  Blocks the host.  Errors as stbem_apply_tc_exact,
+ * STBEM_ERR_NOMEM. */
 int stbem_apply_exact_workspace_bytes(int n_t, int n_x, int n_rhs, int n_slices, size_t* bytes);
 int stbem_apply_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* A, int n_rhs,
                       const double* dev_x, double* dev_y, void* dev_work, size_t work_bytes);

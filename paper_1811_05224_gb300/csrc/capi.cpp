@@ -500,10 +500,11 @@ int stbem_tc_tune(stbem_ctx* ctx, int n_t, int n_x, const void* A, int n_rhs, co
 namespace {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// workspace of the x side of an exact product: S slices of n values + n / n_x exponents
+// workspace of the x side of an exact product: S slices of n values, n / n_x
+// exponents, then (few output tiles) the lag-chunk partial products
 size_t exact_x_bytes(int nt, int nx, int B, int S) {
   const size_t n = (size_t)B * nt * nx;
-  return align256((size_t)S * n * 2) + (size_t)B * nt * sizeof(int);
+  return align256(align256((size_t)S * n * 2) + (size_t)B * nt * sizeof(int)) + stbem::exact_part_bytes(nt, nx, B);
 }
 
 int check_exact_operand(stbem_ctx* ctx, const char* name, const stbem_exact_operand* A) {
@@ -522,8 +523,12 @@ cudaError_t apply_exact(int nt, int nx, const stbem_exact_operand& A, int B, con
   const size_t n = (size_t)B * nt * nx;
   void* xs = work;
   int* xe = reinterpret_cast<int*>(static_cast<char*>(work) + align256((size_t)S * n * 2));
+  double* part = stbem::exact_part_bytes(nt, nx, B) > 0
+                     ? reinterpret_cast<double*>(static_cast<char*>(work) +
+                                                 align256(align256((size_t)S * n * 2) + (size_t)B * nt * sizeof(int)))
+                     : nullptr;
   cudaError_t e = stbem::exact_slices_launch(x, (long long)B * nt, nx, S, xs, xe, s);
-  if (e == cudaSuccess) e = stbem::apply_tc_exact_launch(nt, nx, S, A.slices, A.row_exp, B, xs, xe, y, s);
+  if (e == cudaSuccess) e = stbem::apply_tc_exact_launch(nt, nx, S, A.slices, A.row_exp, B, xs, xe, y, s, part);
   return e;
 }
 }  // namespace

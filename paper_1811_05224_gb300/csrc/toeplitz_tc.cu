@@ -546,8 +546,20 @@ __device__ __forceinline__ float pow2f(int e) {
 template <int S>
 __global__ void __launch_bounds__(EX_THREADS, 1)
     k_apply_tc_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
-                     const int* __restrict__ eA, const int* __restrict__ eX, int nt, int nx,
-                     double* __restrict__ Y) {
+                     const int* __restrict__ eA, const int* __restrict__ eX, int nt, int nx, int n_chunks,
+                     int lag_chunk, double* __restrict__ Y) {
+  // grid (row tiles, right-hand sides, step tiles x lag chunks): the step
+  // tiles run in decreasing order of m0, so the longest tiles (most lags)
+  // start first and the short ones fill the tail; with n_chunks > 1 the CTA
+  // takes the lags [c lag_chunk, (c + 1) lag_chunk) of its tile and writes
+  // its partial products to Y + c n_rhs n_t n_x (summed by k_exact_reduce)
+  const int zt = blockIdx.z / n_chunks, chunk = blockIdx.z % n_chunks;
+  const int m0 = ((int)(gridDim.z / n_chunks) - 1 - zt) * BN;
+  const int dmax = min(m0 + BN - 1, nt - 1);
+  const int d_lo = n_chunks > 1 ? chunk * lag_chunk : 0;
+  if (d_lo > dmax) return;                       // a chunk past the tile's last lag: nothing to do
+  const int d_hi = n_chunks > 1 ? min(d_lo + lag_chunk, dmax + 1) : dmax + 1;
+  Y += (size_t)chunk * gridDim.y * nt * nx;
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
   unsigned char* smA = reinterpret_cast<unsigned char*>(base);
@@ -563,14 +575,10 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
   short* eXp = eXs + kExactMaxSteps;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grid (row tiles, right-hand sides, step tiles): the step tiles run in
-  // decreasing order of m0, so the longest tiles (most lags) start first and
-  // the short ones fill the tail
-  const int i0 = blockIdx.x * BM, b = blockIdx.y, m0 = (gridDim.z - 1 - blockIdx.z) * BN;
-  const int dmax = min(m0 + BN - 1, nt - 1);
+  const int i0 = blockIdx.x * BM, b = blockIdx.y;
   const int nj = (nx + BK - 1) / BK;
   const int nb = (nj + kExactJSteps - 1) / kExactJSteps;
-  const int ngroups = (dmax + 1) * S * nb;       // (d, k, jb), jb fastest
+  const int ngroups = (d_hi - d_lo) * S * nb;    // (d, k, jb), jb fastest
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < EX_STAGES; ++s) {
@@ -616,7 +624,7 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
     if (lane == 0) {
       int it = 0;
       for (int g = 0; g < ngroups && ok; ++g) {
-        const int d = g / (S * nb), k = (g / nb) % S, jb = g % nb;
+        const int d = d_lo + g / (S * nb), k = (g / nb) % S, jb = g % nb;
         const int j_lo = jb * kExactJSteps, j_hi = min(nj, j_lo + kExactJSteps);
         for (int s = 0; s <= k && ok; ++s)
           for (int jc = j_lo; jc < j_hi; ++jc, ++it) {
@@ -675,16 +683,16 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
     const int i = i0 + q * 32 + lane;
     const int mb = m0 + cq * 32;
     // reference scale of y[b][m][i]: 2^{eAmax + eXp[m]}, eAmax the row's
-    // largest over the tile's lags (rows i >= n_x and steps outside
+    // largest over the CTA's lags (rows i >= n_x and steps outside
     // 0..n_t - 1 were zero-filled by the loads, so their partials are 0: the
     // clamped indexes give them finite scales)
     const int ic = min(i, nx - 1);
     int eAmax = kZeroRowExp;
-    for (int d = 0; d <= dmax; ++d) eAmax = max(eAmax, eA[(size_t)d * nx + ic]);
+    for (int d = d_lo; d < d_hi; ++d) eAmax = max(eAmax, eA[(size_t)d * nx + ic]);
     const uint32_t tcol = tmem + lane_base + static_cast<uint32_t>(cq * 32);
     int er = 0;
     for (int g = 0; g < ngroups; ++g) {
-      const int buf = g & 1, d = g / (S * nb), k = (g / nb) % S;
+      const int buf = g & 1, d = d_lo + g / (S * nb), k = (g / nb) % S;
       if (g % (S * nb) == 0) er = eA[(size_t)d * nx + ic] - eAmax;
       // after a failed wait the remaining groups are skipped without waiting
       const bool got = __all_sync(0xffffffffu, ok && mbar_wait(&acc_full[buf], (g >> 1) & 1));
@@ -899,17 +907,45 @@ cudaError_t exact_slices_launch(const double* src, long long rows, int cols, int
 namespace {
 template <int S>
 cudaError_t launch_exact_s(const CUtensorMap& mA, const CUtensorMap& mX, dim3 grid, const int* eA, const int* eX,
-                           int nt, int nx, double* Y, cudaStream_t s) {
+                           int nt, int nx, int n_chunks, int lag_chunk, double* Y, cudaStream_t s) {
   cudaError_t e =
       cudaFuncSetAttribute(k_apply_tc_exact<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EX_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  k_apply_tc_exact<S><<<grid, EX_THREADS, EX_SMEM_BYTES, s>>>(mA, mX, eA, eX, nt, nx, Y);
+  k_apply_tc_exact<S><<<grid, EX_THREADS, EX_SMEM_BYTES, s>>>(mA, mX, eA, eX, nt, nx, n_chunks, lag_chunk, Y);
   return cudaSuccess;
+}
+
+// y = the sum, in chunk order, of the lag-chunk partials written for y's step
+// tile (chunk c exists for the tile when c lag_chunk <= its last lag)
+__global__ void k_exact_reduce(int nt, int nx, int n_rhs, int n_chunks, int lag_chunk,
+                               const double* __restrict__ part, double* __restrict__ Y) {
+  const size_t total = (size_t)n_rhs * nt * nx;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)((e / nx) % nt);
+    const int dmax = min((m / BN) * BN + BN - 1, nt - 1);
+    const int nc = min(n_chunks, dmax / lag_chunk + 1);
+    double acc = 0.0;
+    for (int c = 0; c < nc; ++c) acc += part[(size_t)c * total + e];
+    Y[e] = acc;
+  }
 }
 }  // namespace
 
+int exact_lag_chunks(int nt, int nx, int n_rhs) {
+  // products whose output tiles leave the GPU short of two CTAs per SM split
+  // each tile's lags into chunks of kExactLagChunk
+  const long long tiles = (long long)((nx + BM - 1) / BM) * n_rhs * ((nt + BN - 1) / BN);
+  if (tiles >= 2LL * sm_count()) return 1;
+  return (nt + kExactLagChunk - 1) / kExactLagChunk;
+}
+
+size_t exact_part_bytes(int nt, int nx, int n_rhs) {
+  const int c = exact_lag_chunks(nt, nx, n_rhs);
+  return c > 1 ? (size_t)c * n_rhs * nt * nx * sizeof(double) : 0;
+}
+
 cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_slices, const int* A_exp, int n_rhs,
-                                  const void* X_slices, const int* X_exp, double* Y, cudaStream_t s) {
+                                  const void* X_slices, const int* X_exp, double* Y, cudaStream_t s, double* part) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   // A slices [S][nt][nx][nx] and x slices [S][n_rhs][nt][nx], BF16, as 4-D maps
@@ -927,17 +963,25 @@ cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_sl
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const dim3 grid((nx + BM - 1) / BM, n_rhs, (nt + BN - 1) / BN);
+  const int nch = part ? exact_lag_chunks(nt, nx, n_rhs) : 1;
+  const int lc = nch > 1 ? kExactLagChunk : 0;
+  double* out = nch > 1 ? part : Y;
+  const dim3 grid((nx + BM - 1) / BM, n_rhs, ((nt + BN - 1) / BN) * nch);
   cudaError_t e = cudaErrorInvalidValue;
   switch (n_slices) {
-    case 4: e = launch_exact_s<4>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
-    case 5: e = launch_exact_s<5>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
-    case 6: e = launch_exact_s<6>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
-    case 7: e = launch_exact_s<7>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
-    case 8: e = launch_exact_s<8>(mA, mX, grid, A_exp, X_exp, nt, nx, Y, s); break;
+    case 4: e = launch_exact_s<4>(mA, mX, grid, A_exp, X_exp, nt, nx, nch, lc, out, s); break;
+    case 5: e = launch_exact_s<5>(mA, mX, grid, A_exp, X_exp, nt, nx, nch, lc, out, s); break;
+    case 6: e = launch_exact_s<6>(mA, mX, grid, A_exp, X_exp, nt, nx, nch, lc, out, s); break;
+    case 7: e = launch_exact_s<7>(mA, mX, grid, A_exp, X_exp, nt, nx, nch, lc, out, s); break;
+    case 8: e = launch_exact_s<8>(mA, mX, grid, A_exp, X_exp, nt, nx, nch, lc, out, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  count_launches(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || nch == 1) return e;
+  const size_t total = (size_t)n_rhs * nt * nx;
+  k_exact_reduce<<<stride_grid(total, 256, 16), 256, 0, s>>>(nt, nx, n_rhs, nch, kExactLagChunk, part, Y);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -33,7 +33,13 @@ bool apply_tc_exact_supported(int nt, int nx, int n_rhs, int n_slices);
 // slices [n_slices][rows][cols] BF16, row_exp [rows]
 cudaError_t exact_slices_launch(const double* src, long long rows, int cols, int n_slices, void* slices,
                                 int* row_exp, cudaStream_t s);
+// part: scratch of exact_part_bytes() for products that split each output
+// tile's lags into chunks (few output tiles: small n_rhs); NULL: no split
 cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_slices, const int* A_exp, int n_rhs,
-                                  const void* X_slices, const int* X_exp, double* Y, cudaStream_t s);
+                                  const void* X_slices, const int* X_exp, double* Y, cudaStream_t s,
+                                  double* part = nullptr);
+constexpr int kExactLagChunk = 64;
+int exact_lag_chunks(int nt, int nx, int n_rhs);
+size_t exact_part_bytes(int nt, int nx, int n_rhs);
 cudaError_t to_bf16_launch(int src_prec, const void* src, void* dst, size_t n, cudaStream_t s);
 }  // namespace stbem

@@ -85,11 +85,13 @@ def test_apply_exact_matches_oracle(ctx, nt, nx, B, S):
     Ad, xd = torch.as_tensor(A).cuda(), torch.as_tensor(x).cuda()
     Ax = P.exact_slices(ctx, Ad, S)
     y = P.apply_exact(ctx, Ax, xd).cpu().numpy()
+    # pre-sliced x: one launch over whole tiles (the FP64-x call may split the
+    # lags of few tiles into chunks, summed afterwards); both within the bound
     y2 = P.apply_exact(ctx, Ax, P.exact_slices(ctx, xd, S)).cpu().numpy()
-    assert np.array_equal(y, y2)              # pre-sliced x: the same launch
     ref, mag, M = _ref(A, x)
     err = np.abs(y - ref)
     assert np.all(err <= _bound(S, M, mag, nt, nx)), float((err / M).max())
+    assert np.all(np.abs(y2 - ref) <= _bound(S, M, mag, nt, nx))
     # and elementwise against |A| |x| (4 2^-6S in a CPU emulation of the scheme)
     assert np.all(err <= 16 * 2.0 ** (-6 * S) * mag + 2 * nt * nx * U64 * mag + 1e-300), \
         float((err / (mag + 1e-300)).max())
