@@ -434,7 +434,9 @@ int stbem_bf16_split3(stbem_ctx* ctx, size_t n, const double* dev_src, void* dev
  * stbem_apply_tc_comp (partials of 4 K steps for hi x hi, 16 for the rest),
  * summed in FP64: a few 1e-7 relative to |A| |x|, against ~4e-3 for one BF16
  * product and ~4e-4 for the uncompensated split product over 512 lags.  Workspace: stbem_apply_tc3_workspace_bytes() (the three
- * slices of x).  Blocks the host.  Errors as stbem_apply_tc, STBEM_ERR_NOMEM. */
+ * slices of x and, with few output tiles, the partial products of chunks of
+ * 64 lags per tile), 256-byte aligned.  Blocks the host.  Errors as
+ * stbem_apply_tc, STBEM_ERR_NOMEM. */
 int stbem_apply_tc3_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes);
 int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* dev_A_hi, const void* dev_A_mid,
                     const void* dev_A_lo, int n_rhs, const double* dev_x, double* dev_y, void* dev_work,
@@ -590,6 +592,23 @@ int stbem_solve_mixed_exact(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_
                             const float* dev_V32, const float* dev_D32, const double* dev_L, const double* dev_f,
                             double* dev_w, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info,
                             void* dev_work, size_t work_bytes);
+
+/* stbem_solve_mixed_exact with the inner GMRES on the BF16 tensor cores: V and
+ * D given by their three BF16 slices (stbem_bf16_split3 of the FP64 V and D;
+ * dev_*_mid / dev_*_lo may be NULL), every inner product the compensated
+ * three-slice product of stbem_apply_tc3 (a few 1e-7 of |A| |x|, the accuracy
+ * of an FP32 product), the outer residuals exact-slice products of V_exact.
+ * With few output tiles the products split each tile's lags into chunks.
+ * Preconditioner as stbem_solve_mixed (opts->precondition 1: lumped, 2: the
+ * consistent mixed mass inverse).  Workspace:
+ * stbem_solve_mixed_tc_workspace_bytes(), 256-byte aligned.  Requires
+ * n_x % 8 == 0, n_t <= 4096.  Errors as stbem_solve_mixed_exact. */
+int stbem_solve_mixed_tc_workspace_bytes(int n_t, int n_x, int restart, int n_slices, size_t* bytes);
+int stbem_solve_mixed_tc(stbem_ctx* ctx, int n_t, int n_x, const stbem_exact_operand* V_exact,
+                         const void* dev_V_hi, const void* dev_V_mid, const void* dev_V_lo, const void* dev_D_hi,
+                         const void* dev_D_mid, const void* dev_D_lo, const double* dev_L, const double* dev_f,
+                         double* dev_w, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info,
+                         void* dev_work, size_t work_bytes);
 
 /* ---- Ragged batches ----------------------------------------------------------
  * Many independent problems of different sizes (not in the paper, which solves

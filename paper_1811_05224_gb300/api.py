@@ -423,9 +423,35 @@ def solve_mixed(ctx: Context, V64, V32, f, D32=None, L=None, tol: float = 1e-8, 
                 max_iter: int = 500, restart: int = 200, work=None, out=None, raise_on_fail: bool = True):
     """FP64 iterative refinement around preconditioned GMRES on FP32 operators.
     V64 gives the outer residuals: the FP64 lag blocks (an FP64 CUDA-core
-    product) or their ExactOperand (the exact-slice tensor-core product)."""
+    product) or their ExactOperand (the exact-slice tensor-core product).
+    With V32 and D32 given as the three BF16 slices of V and D
+    (bf16_split3) and V64 an ExactOperand, the inner GMRES runs on the
+    tensor cores (three-slice products, FP32-grade accuracy)."""
     n_t, n_x = V64.shape[0], V64.shape[1]
     exact = isinstance(V64, ExactOperand)
+    if isinstance(V32, (tuple, list)):
+        if not exact:
+            raise ValueError("solve_mixed: tensor-core inner operators need an ExactOperand V64")
+        Vs = list(V32) + [None] * (3 - len(V32))
+        Ds = list(D32) + [None] * (3 - len(D32)) if D32 is not None else [None] * 3
+        opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(D32, L))
+        info = capi.SolveInfo()
+        if out is None:
+            out = ctx.empty((n_t, n_x))
+        if work is None:
+            nb = ctypes.c_size_t()
+            ctx.check(ctx.lib.stbem_solve_mixed_tc_workspace_bytes(n_t, n_x, restart, V64.n_slices,
+                                                                   ctypes.byref(nb)))
+            work = torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+        sv = V64.c_struct()
+        code = ctx.lib.stbem_solve_mixed_tc(ctx.h, n_t, n_x, ctypes.byref(sv), _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]),
+                                            _ptr(Ds[0]), _ptr(Ds[1]), _ptr(Ds[2]), _ptr(L), _ptr(f), _ptr(out),
+                                            ctypes.byref(opts), float(inner_tol), ctypes.byref(info), _ptr(work),
+                                            work.numel())
+        res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
+        if code != capi.STBEM_OK and raise_on_fail:
+            ctx.check(code)
+        return out, res
     opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(D32, L))
     info = capi.SolveInfo()
     if out is None:

@@ -48,6 +48,7 @@ EXPORTS = [
     "stbem_solve_batched_exact_workspace_bytes", "stbem_solve_batched_exact",
     "stbem_tune_cache_path", "stbem_tune_cache_get", "stbem_tune_cache_put", "stbem_tune_cache_clear", "stbem_tc_tune",
     "stbem_solve_mixed_exact_workspace_bytes", "stbem_solve_mixed_exact",
+    "stbem_solve_mixed_tc_workspace_bytes", "stbem_solve_mixed_tc",
 ]
 
 
@@ -143,6 +144,9 @@ def load(path: str = LIB_PATH):
     L.stbem_solve_mixed_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_mixed.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_solve_mixed_exact_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_solve_mixed_tc_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_solve_mixed_tc.argtypes = [vp, i, i, P(ExactOperand), vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       P(SolveOpts), d, P(SolveInfo), vp, sz]
     L.stbem_solve_mixed_exact.argtypes = [vp, i, i, P(ExactOperand), vp, vp, vp, vp, vp, P(SolveOpts), d,
                                           P(SolveInfo), vp, sz]
     L.stbem_round_f32.argtypes = [vp, sz, vp, vp]

@@ -371,8 +371,11 @@ constexpr int kTc3ChunkLo = 16;
 // y = sum over slice pairs (s, t), s + t <= 2, of A_s x_t on the tensor cores,
 // with x split into three BF16 slices in `xs` (3 n_rhs n_t n_x BF16), each
 // product Kahan-accumulated over FP32 partials.
+// part (optional, stbem::exact_part_bytes()): with few output tiles the
+// products split each tile's lags into chunks, accumulated there and summed
+// into y at the end.
 cudaError_t apply_tc3(int nt, int nx, const void* const A[3], int B, const double* x, double* y, void* xs,
-                      cudaStream_t s) {
+                      cudaStream_t s, double* part = nullptr) {
   const size_t n = (size_t)B * nt * nx;
   char* base = static_cast<char*>(xs);
   void* X[3] = {base, base + n * 2, base + 2 * n * 2};
@@ -383,17 +386,27 @@ cudaError_t apply_tc3(int nt, int nx, const void* const A[3], int B, const doubl
     for (int sx = 0; sx + sa < 3; ++sx) {
       if (!A[sa]) continue;
       e = stbem::apply_tc_launch(nt, nx, A[sa], B, X[sx], y, !first, s,
-                                 sa + sx == 0 ? kTc3ChunkHi : kTc3ChunkLo);
+                                 sa + sx == 0 ? kTc3ChunkHi : kTc3ChunkLo, 0, part);
       if (e != cudaSuccess) return e;
       first = false;
     }
-  return cudaSuccess;
+  return part ? stbem::tc_chunk_reduce_launch(nt, nx, B, part, y, s) : cudaSuccess;
+}
+
+// workspace of apply_tc3 with lag chunks: three slices of x, then the partials
+size_t tc3_bytes(int nt, int nx, int B) {
+  const size_t x3 = ((3 * (size_t)B * nt * nx * 2 + 255) & ~(size_t)255);
+  return x3 + stbem::exact_part_bytes(nt, nx, B);
+}
+double* tc3_part(void* work, int nt, int nx, int B) {
+  if (stbem::exact_part_bytes(nt, nx, B) == 0) return nullptr;
+  return reinterpret_cast<double*>(static_cast<char*>(work) + ((3 * (size_t)B * nt * nx * 2 + 255) & ~(size_t)255));
 }
 }  // namespace
 
 int stbem_apply_tc3_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes) {
   if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1) return STBEM_ERR_ARG;
-  *bytes = 3 * (size_t)n_rhs * n_t * n_x * 2;
+  *bytes = tc3_bytes(n_t, n_x, n_rhs);
   return STBEM_OK;
 }
 
@@ -402,11 +415,12 @@ int stbem_apply_tc3(stbem_ctx* ctx, int n_t, int n_x, const void* A_hi, const vo
   if (!ctx) return STBEM_ERR_ARG;
   if (!A_hi || !x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "apply_tc3: NULL pointer");
   if (!stbem::apply_tc_supported(n_t, n_x, n_rhs)) return fail(ctx, STBEM_ERR_ARG, "apply_tc3: unsupported sizes");
-  if (work_bytes < 3 * (size_t)n_rhs * n_t * n_x * 2) return fail(ctx, STBEM_ERR_NOMEM, "apply_tc3: workspace too small");
+  if (work_bytes < tc3_bytes(n_t, n_x, n_rhs)) return fail(ctx, STBEM_ERR_NOMEM, "apply_tc3: workspace too small");
+  if (reinterpret_cast<uintptr_t>(work) & 255) return fail(ctx, STBEM_ERR_ARG, "apply_tc3: workspace not 256-byte aligned");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_tc3: set device");
   CUDA_TRY(ctx, stbem::tc_error_reset(ctx->stream), "apply_tc3: reset error word");
   const void* A[3] = {A_hi, A_mid, A_lo};
-  CUDA_TRY(ctx, apply_tc3(n_t, n_x, A, n_rhs, x, y, work, ctx->stream), "apply_tc3");
+  CUDA_TRY(ctx, apply_tc3(n_t, n_x, A, n_rhs, x, y, work, ctx->stream, tc3_part(work, n_t, n_x, n_rhs)), "apply_tc3");
   int flag = 0;
   CUDA_TRY(ctx, stbem::tc_error_read(&flag, ctx->stream), "apply_tc3: read error word");
   if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "apply_tc3: a pipeline wait timed out");
@@ -974,6 +988,13 @@ struct GmresOp {
   // non-uniform time grid: V and D are packed blocks (forward products only)
   // and L holds the lumped mass of every step (n_t x n_x)
   bool packed = false;
+  // three-slice BF16 operators on the tensor cores (forward products of one
+  // right-hand side): V3 / D3 the slices, V = V3[0] and D = D3[0] name them;
+  // tcx the slices of x, tcpart the lag-chunk partial sums (may be NULL)
+  const void* const* V3 = nullptr;
+  const void* const* D3 = nullptr;
+  void* tcx = nullptr;
+  double* tcpart = nullptr;
 };
 
 // y = A x with A one of op's operators (full, or this rank's lag ranges then
@@ -981,6 +1002,7 @@ struct GmresOp {
 cudaError_t op_product(const GmresOp& op, const void* A, const double* x, double* y, void* work, cudaStream_t s,
                        int* reduce_rc) {
   if (op.packed) return stbem::nu_apply_launch(op.nt, op.nx, static_cast<const double*>(A), x, y, s);
+  if (op.V3) return apply_tc3(op.nt, op.nx, A == op.V ? op.V3 : op.D3, 1, x, y, op.tcx, s, op.tcpart);
   if (op.n_ranges < 0) return stbem::apply_launch(op.prec, op.transpose, op.nt, op.nx, A, 1, x, y, work, s);
   const size_t N = (size_t)op.nt * op.nx;
   const size_t elt = op.prec == STBEM_F64 ? sizeof(double) : sizeof(float);
@@ -1446,10 +1468,12 @@ namespace {
 int solve_mixed_impl(stbem_ctx* ctx, int nt, int nx, const double* V64, const stbem_exact_operand* Vx,
                      const float* V32, const float* D32, const double* L, const double* f, double* w,
                      const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* info, void* work,
-                     size_t work_bytes) {
+                     size_t work_bytes, const void* const* V3 = nullptr, const void* const* D3 = nullptr) {
   if (!ctx) return STBEM_ERR_ARG;
-  if ((!V64 && !Vx) || !V32 || !f || !w || !opts || !info || !work)
+  if ((!V64 && !Vx) || (!V32 && !(V3 && V3[0])) || !f || !w || !opts || !info || !work)
     return fail(ctx, STBEM_ERR_ARG, "solve_mixed: NULL pointer");
+  if (V3 && !stbem::apply_tc_supported(nt, nx, 1))
+    return fail(ctx, STBEM_ERR_ARG, "solve_mixed_tc: unsupported sizes (need n_x %% 8 == 0)");
   if (nt < 1 || nx < 1) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: bad sizes");
   if (Vx) {
     if (const int r = check_exact_operand(ctx, "solve_mixed_exact", Vx)) return r;
@@ -1462,10 +1486,13 @@ int solve_mixed_impl(stbem_ctx* ctx, int nt, int nx, const double* V64, const st
   if (restart < 1 || maxit < 1 || !(opts->tol > 0) || !(inner_tol > 0) || !(inner_tol < 1))
     return fail(ctx, STBEM_ERR_ARG, "solve_mixed: bad options");
   const bool prec = opts->precondition != 0;
-  if (prec && (!D32 || !L)) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: preconditioner needs D and L");
+  const bool have_d = V3 ? (D3 && D3[0]) : D32 != nullptr;
+  if (prec && (!have_d || !L)) return fail(ctx, STBEM_ERR_ARG, "solve_mixed: preconditioner needs D and L");
   const size_t N = (size_t)nt * nx;
   const size_t base = align256(solve_bytes(nt, nx, restart) + 2 * N * sizeof(double));
-  const size_t need = Vx ? base + exact_x_bytes(nt, nx, 1, Vx->n_slices) : solve_bytes(nt, nx, restart) + 2 * N * sizeof(double);
+  const size_t xbytes = Vx ? align256(exact_x_bytes(nt, nx, 1, Vx->n_slices)) : 0;
+  const size_t need = (Vx || V3) ? base + xbytes + (V3 ? tc3_bytes(nt, nx, 1) : 0)
+                                 : solve_bytes(nt, nx, restart) + 2 * N * sizeof(double);
   if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "solve_mixed: workspace %zu < %zu bytes", work_bytes, need);
   SolveWork W;
   carve(work, solve_bytes(nt, nx, restart), nt, nx, restart, &W);
@@ -1496,6 +1523,16 @@ int solve_mixed_impl(stbem_ctx* ctx, int nt, int nx, const double* V64, const st
   if (nf == 0.0) return STBEM_OK;
   GmresOp op{nt, nx, STBEM_F32, V32, prec ? (const void*)D32 : nullptr, L};
   op.mass = opts->precondition == 2 ? 2 : 1;
+  if (V3) {   // the inner products: three-slice BF16 operators on the tensor cores
+    op.V = V3[0];
+    op.D = prec ? D3[0] : nullptr;
+    op.V3 = V3;
+    op.D3 = D3;
+    op.tcx = static_cast<char*>(work) + base + xbytes;
+    op.tcpart = tc3_part(op.tcx, nt, nx, 1);
+  }
+  // tensor-core pipeline time-outs of the inner products and the residuals
+  if (V3 || Vx) CUDA_TRY(ctx, stbem::tc_error_reset(s), "solve_mixed: reset error word");
   CUDA_TRY(ctx, cudaMemcpyAsync(r, f, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "solve_mixed: r");
   int total = 0, status = STBEM_OK;
   double relres = 1.0;
@@ -1515,14 +1552,12 @@ int solve_mixed_impl(stbem_ctx* ctx, int nt, int nx, const double* V64, const st
     if (st != STBEM_OK && st != STBEM_ERR_NOCONV) return st;
     CUDA_TRY(ctx, stbem::axpy_launch(1.0, dw, w, N, s), "solve_mixed: w += dw");
     // residual with the FP64 operator (or its exact slices)
-    if (Vx) {
-      CUDA_TRY(ctx, stbem::tc_error_reset(s), "solve_mixed: reset error word");
-      CUDA_TRY(ctx, apply_exact(nt, nx, *Vx, 1, w, W.v, xwork, s), "solve_mixed: exact V w");
+    if (Vx) CUDA_TRY(ctx, apply_exact(nt, nx, *Vx, 1, w, W.v, xwork, s), "solve_mixed: exact V w");
+    else CUDA_TRY(ctx, stbem::apply_launch(STBEM_F64, false, nt, nx, V64, 1, w, W.v, W.apply, s), "solve_mixed: V w");
+    if (V3 || Vx) {
       int flag = 0;
       CUDA_TRY(ctx, stbem::tc_error_read(&flag, s), "solve_mixed: read error word");
       if (flag) return fail(ctx, STBEM_ERR_TIMEOUT, "solve_mixed: a tensor-core pipeline wait timed out");
-    } else {
-      CUDA_TRY(ctx, stbem::apply_launch(STBEM_F64, false, nt, nx, V64, 1, w, W.v, W.apply, s), "solve_mixed: V w");
     }
     CUDA_TRY(ctx, stbem::sub_launch(f, W.v, r, N, s), "solve_mixed: f - V w");
     if (it == 0) { status = STBEM_ERR_NOCONV; break; }
@@ -1561,6 +1596,27 @@ int stbem_solve_mixed_exact(stbem_ctx* ctx, int nt, int nx, const stbem_exact_op
                             size_t work_bytes) {
   if (ctx && !Vx) return fail(ctx, STBEM_ERR_ARG, "solve_mixed_exact: NULL operand");
   return solve_mixed_impl(ctx, nt, nx, nullptr, Vx, V32, D32, L, f, w, opts, inner_tol, info, work, work_bytes);
+}
+
+int stbem_solve_mixed_tc_workspace_bytes(int n_t, int n_x, int restart, int n_slices, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || restart < 1 || n_slices < stbem::kExactMinSlices ||
+      n_slices > stbem::kExactMaxSlices)
+    return STBEM_ERR_ARG;
+  *bytes = align256(solve_bytes(n_t, n_x, restart) + 2 * (size_t)n_t * n_x * sizeof(double)) +
+           align256(exact_x_bytes(n_t, n_x, 1, n_slices)) + tc3_bytes(n_t, n_x, 1);
+  return STBEM_OK;
+}
+
+int stbem_solve_mixed_tc(stbem_ctx* ctx, int nt, int nx, const stbem_exact_operand* Vx, const void* V_hi,
+                         const void* V_mid, const void* V_lo, const void* D_hi, const void* D_mid, const void* D_lo,
+                         const double* L, const double* f, double* w, const stbem_solve_opts* opts, double inner_tol,
+                         stbem_solve_info* info, void* work, size_t work_bytes) {
+  if (ctx && (!Vx || !V_hi)) return fail(ctx, STBEM_ERR_ARG, "solve_mixed_tc: NULL operand");
+  if (ctx && opts && opts->precondition && !D_hi) return fail(ctx, STBEM_ERR_ARG, "solve_mixed_tc: NULL D");
+  const void* V3[3] = {V_hi, V_mid, V_lo};
+  const void* D3[3] = {D_hi, D_mid, D_lo};
+  return solve_mixed_impl(ctx, nt, nx, nullptr, Vx, nullptr, nullptr, L, f, w, opts, inner_tol, info, work,
+                          work_bytes, V3, D3);
 }
 
 int stbem_round_f32(stbem_ctx* ctx, size_t n, const double* src, float* dst) {

@@ -339,7 +339,18 @@ constexpr size_t COMP_SMEM_BYTES = 1024 + STAGES * (size_t)STAGE_BYTES + 512;
 
 __global__ void __launch_bounds__(COMP_THREADS, 1)
     k_apply_tc_comp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int nt, int nx,
-                    int chunk, int accumulate, double* __restrict__ Y) {
+                    int chunk, int accumulate, int n_lchunks, int lag_chunk, double* __restrict__ Y) {
+  // grid (row tiles, right-hand sides, step tiles x lag chunks), step tiles
+  // longest first; with n_lchunks > 1 the CTA takes the lags
+  // [c lag_chunk, (c + 1) lag_chunk) of its tile and writes (or adds) its
+  // partial product to Y + c n_rhs n_t n_x (summed by k_exact_reduce)
+  const int zt = blockIdx.z / n_lchunks, lchunk = blockIdx.z % n_lchunks;
+  const int m0 = ((int)(gridDim.z / n_lchunks) - 1 - zt) * BN;
+  const int dmax = min(m0 + BN - 1, nt - 1);
+  const int d_lo = n_lchunks > 1 ? lchunk * lag_chunk : 0;
+  if (d_lo > dmax) return;                       // a chunk past the tile's last lag: nothing to do
+  const int d_hi = n_lchunks > 1 ? min(d_lo + lag_chunk, dmax + 1) : dmax + 1;
+  Y += (size_t)lchunk * gridDim.y * nt * nx;
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023);
   unsigned char* smA = reinterpret_cast<unsigned char*>(base);
@@ -352,11 +363,9 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grid (row tiles, right-hand sides, step tiles), step tiles longest first
-  const int i0 = blockIdx.x * BM, b = blockIdx.y, m0 = (gridDim.z - 1 - blockIdx.z) * BN;
-  const int dmax = min(m0 + BN - 1, nt - 1);
+  const int i0 = blockIdx.x * BM, b = blockIdx.y;
   const int nj = (nx + BK - 1) / BK;
-  const int iters = (dmax + 1) * nj;
+  const int iters = (d_hi - d_lo) * nj;
   const int nchunks = (iters + chunk - 1) / chunk;
 
   if (threadIdx.x == 0) {
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(COMP_THREADS, 1)
           ok = false;
           break;
         }
-        const int d = it / nj, j0 = (it % nj) * BK;
+        const int d = d_lo + it / nj, j0 = (it % nj) * BK;
         mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load_3d(&tmA, &full[s], smA + s * A_BYTES, j0, i0, d);
         tma_load_3d(&tmX, &full[s], smB + s * B_BYTES, j0, m0 - d, b);
@@ -858,7 +867,7 @@ int tc_plain_tile_n(int nt, int nx, int n_rhs) {
 }
 
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            bool accumulate, cudaStream_t s, int chunk, int tile_n) {
+                            bool accumulate, cudaStream_t s, int chunk, int tile_n, double* part) {
   const long long stall = g_stall_cycles.load();
   CUtensorMap mA, mX;
   int bn = BN;
@@ -881,7 +890,11 @@ cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const
   } else {
     e = cudaFuncSetAttribute(k_apply_tc_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COMP_SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k_apply_tc_comp<<<grid, COMP_THREADS, COMP_SMEM_BYTES, s>>>(mA, mX, nt, nx, chunk, accumulate ? 1 : 0, Y);
+    // few output tiles and a partial-sum buffer: lag chunks (tc_chunk_reduce_launch sums them)
+    const int nch = part ? exact_lag_chunks(nt, nx, n_rhs) : 1;
+    const dim3 gridc(grid.x, grid.y, grid.z * nch);
+    k_apply_tc_comp<<<gridc, COMP_THREADS, COMP_SMEM_BYTES, s>>>(mA, mX, nt, nx, chunk, accumulate ? 1 : 0, nch,
+                                                                 kExactLagChunk, nch > 1 ? part : Y);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -980,6 +993,15 @@ cudaError_t apply_tc_exact_launch(int nt, int nx, int n_slices, const void* A_sl
   count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess || nch == 1) return e;
+  const size_t total = (size_t)n_rhs * nt * nx;
+  k_exact_reduce<<<stride_grid(total, 256, 16), 256, 0, s>>>(nt, nx, n_rhs, nch, kExactLagChunk, part, Y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_chunk_reduce_launch(int nt, int nx, int n_rhs, const double* part, double* Y, cudaStream_t s) {
+  const int nch = exact_lag_chunks(nt, nx, n_rhs);
+  if (nch == 1) return cudaSuccess;
   const size_t total = (size_t)n_rhs * nt * nx;
   k_exact_reduce<<<stride_grid(total, 256, 16), 256, 0, s>>>(nt, nx, n_rhs, nch, kExactLagChunk, part, Y);
   count_launches(1);

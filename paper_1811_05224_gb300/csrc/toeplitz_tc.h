@@ -12,8 +12,14 @@ bool apply_tc_supported(int nt, int nx, int n_rhs);
 // of `chunk` 64-wide K steps each, Kahan-summed (compensated kernel).  The
 // plain kernel's tile width (steps per tile) is tile_n (128 or 256), else the
 // tuned value for this shape (stbem_tc_tune), else 256 for n_t > 128.
+// With chunk > 0 and a partial-sum buffer `part` (exact_part_bytes()), products
+// with few output tiles split each tile's lags into chunks and write (or add)
+// the chunks' partial products to `part` instead of Y; tc_chunk_reduce_launch
+// then sets Y to their sum (a no-op when the product does not split).
 cudaError_t apply_tc_launch(int nt, int nx, const void* A_bf16, int n_rhs, const void* X_bf16, double* Y,
-                            bool accumulate, cudaStream_t s, int chunk = 0, int tile_n = 0);
+                            bool accumulate, cudaStream_t s, int chunk = 0, int tile_n = 0,
+                            double* part = nullptr);
+cudaError_t tc_chunk_reduce_launch(int nt, int nx, int n_rhs, const double* part, double* Y, cudaStream_t s);
 // tune-cache key of the plain product's tile width, and the width in use
 std::string tc_plain_tune_key(int nt, int nx, int n_rhs);
 int tc_plain_tile_n(int nt, int nx, int n_rhs);

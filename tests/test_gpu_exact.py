@@ -254,3 +254,31 @@ def test_mixed_solve_exact_residual_against_oracle(ctx):
     assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(fo)
     w_ref = OS.forward_substitution(Vo, fo)
     assert np.linalg.norm(wm.cpu().numpy() - w_ref) <= 1e-6 * np.linalg.norm(w_ref)
+
+
+def test_mixed_solve_tensor_core_inner_against_oracle(ctx):
+    """The mixed solve with the inner GMRES on the tensor cores (three-slice
+    BF16 V and D, stbem_solve_mixed_tc) and exact-slice outer residuals: the
+    FP64 residual with the oracle's V below 1e-8 and w within 1e-6 of the
+    oracle's block forward substitution; lumped and consistent mass."""
+    import paper_1811_05224_gb300 as P
+    import workloads as W
+    from oracle import assembly as OA
+    from oracle.geometry import BoundaryMesh
+    X, T, nt, al = W.l_shape(48, seed=3), 1.0, 24, 0.5
+    m = P.Mesh(ctx, X, T, nt, al)
+    om = BoundaryMesh(X, T, nt, al)
+    V = P.assemble(ctx, m, "V")
+    K = P.assemble(ctx, m, "K")
+    D = P.assemble(ctx, m, "D")
+    g, f = P.rhs(ctx, m, K, (1.5, 1.5))
+    V3, D3, Vx = P.bf16_split3(ctx, V), P.bf16_split3(ctx, D), P.exact_slices(ctx, V, 7)
+    Vo = OA.assemble("V", om)
+    fo = f.cpu().numpy()
+    w_ref = OS.forward_substitution(Vo, fo)
+    for Lm in (P.lumped_mass(ctx, m), P.mixed_mass_inverse(ctx, m)):
+        wm, info = P.solve_mixed(ctx, Vx, V3, f, D3, Lm, tol=1e-8, inner_tol=1e-4)
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-8, info
+        r = fo - OS.toeplitz_apply(Vo, wm.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(fo)
+        assert np.linalg.norm(wm.cpu().numpy() - w_ref) <= 1e-6 * np.linalg.norm(w_ref)

@@ -123,3 +123,11 @@ def test_precision_workload_mixed_solve(ctx):
     r = f - P.apply(ctx, V, wx)
     assert float(r.norm() / f.norm()) <= 1.01e-8
     assert float((wx - w).norm() / w.norm()) <= 1e-6
+    # and with the inner GMRES on the tensor cores (three-slice V and D; the
+    # D slices from the FP32 D: only the preconditioner)
+    V3, D3 = P.bf16_split3(ctx, V), P.bf16_split3(ctx, D32.double())
+    wt, infot = P.solve_mixed(ctx, Vx, V3, f, D3, Minv, tol=1e-8, inner_tol=1e-4, max_iter=400, restart=60)
+    assert infot["status"] == 0
+    r = f - P.apply(ctx, V, wt)
+    assert float(r.norm() / f.norm()) <= 1.01e-8
+    assert float((wt - w).norm() / w.norm()) <= 1e-6
