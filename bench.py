@@ -1195,6 +1195,8 @@ def run_precision(ctx, dev, stream):
     t[2].record(stream)
     del Vx, V3, D3
     torch.cuda.empty_cache()
+    f0 = ev()
+    f0.record(stream)         # the FP64 path starts here
     D = P.assemble(ctx, m, "D")
     e[6].record(stream)
     w, i64 = P.solve(ctx, V, f, D, Minv, tol=1e-8, max_iter=400, restart=60)
@@ -1204,12 +1206,12 @@ def run_precision(ctx, dev, stream):
     out = {
         "workload": "lshape1024: N_x = N_t = 1024, alpha = 0.5, seeded lengths (seed 3)",
         "assembly_ms": {"V_f64": e[0].elapsed_time(e[1]), "K_f64": e[1].elapsed_time(e[2]),
-                        "D_f32_and_V_round": e[3].elapsed_time(e[4]), "D_f64": e[5].elapsed_time(e[6])},
+                        "D_f32_and_V_round": e[3].elapsed_time(e[4]), "D_f64": f0.elapsed_time(e[6])},
         "mixed_solve_ms": e[4].elapsed_time(e[5]), "mixed_inner_iterations": im["iterations"],
         "fp64_solve_ms": e[6].elapsed_time(e[7]), "fp64_iterations": i64["iterations"],
         "mixed_fp64_rel_residual": float(r.norm() / f.norm()),
         "w_rel_diff_mixed_vs_fp64": float((wm - w).norm() / w.norm()),
-        "mixed_path_ms": e[3].elapsed_time(e[5]), "fp64_path_ms": e[5].elapsed_time(e[7]),
+        "mixed_path_ms": e[3].elapsed_time(e[5]), "fp64_path_ms": f0.elapsed_time(e[7]),
     }
     r2 = f - P.apply(ctx, V, w)
     out["fp64_rel_residual"] = float(r2.norm() / f.norm())
