@@ -24,8 +24,9 @@
 namespace stbem {
 
 constexpr int TI = 64, TM = 32, TJ = 16, kApplyThreads = 256;
-// FP32 register-tiled product: 128 rows x 128 steps per CTA, 16 columns per stage
-constexpr int TI4 = 128, TM4 = 128, TJ4 = 16;
+// FP32 register-tiled product: 128 rows x 128 steps per CTA (single
+// problems), 128 x 64 (ragged batches of smaller problems), 16 columns per stage
+constexpr int TI4 = 128, TM4 = 128, TM4R = 64, TJ4 = 16;
 
 struct ApplyPlan {
   int MT, IT, CH, DC;
@@ -196,10 +197,15 @@ k_apply(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const TA
 // stage's A and x are loaded into registers while the current one is
 // multiplied from the other half of a double-buffered shared tile (one
 // barrier per stage).  Requires N_x % 4 == 0 (16-byte rows).
-constexpr int kXsLd = TM4 + 4;   // x tile row length: transposing stores 2-way at most
-// dynamic shared memory: two stages of A (16 x 128) and x (16 x 132), then
-// the (hi, lo) pairs (2 x 64 x 256 floats)
-constexpr size_t kApply32Smem = (2 * TJ4 * TI4 + 2 * TJ4 * kXsLd + 2 * 64 * 256) * sizeof(float);
+// dynamic shared memory of a TMV-step tile: two stages of A (16 x 128) and x
+// (16 x (TMV + 4): transposing stores 2-way at most), then the (hi, lo) pairs
+// (2 x 8 TMV / 16 x 256 floats)
+template <int TMV>
+constexpr size_t apply32_smem() {
+  return (2 * TJ4 * TI4 + 2 * TJ4 * (TMV + 4) + 2 * (8 * TMV / 16) * 256) * sizeof(float);
+}
+constexpr size_t kApply32Smem = apply32_smem<TM4>();
+constexpr size_t kApply32SmemR = apply32_smem<TM4R>();
 
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   const float s = hi + v;
@@ -209,33 +215,36 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   lo += err;
 }
 
+template <int TMV>
 __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi,
                                              const float* __restrict__ A, const double* __restrict__ x,
                                              double* __restrict__ part, int it, int ch, int b, int mt,
                                              float* smem) {
-  const int m0 = mt * TM4, i0 = it * TI4;
-  const int mmax = min(m0 + TM4, nt) - 1;
+  constexpr int NC = TMV / 16;            // steps per thread: tx*4.. (and 64 + tx*4.. for 128)
+  constexpr int kXsLd = TMV + 4;
+  const int m0 = mt * TMV, i0 = it * TI4;
+  const int mmax = min(m0 + TMV, nt) - 1;
   const int d0 = lag_lo + ch * DC;
   if (d0 > mmax || d0 >= lag_hi) return;
   const int d1 = min(min(d0 + DC, mmax + 1), lag_hi);
   float (*As)[TJ4][TI4] = reinterpret_cast<float (*)[TJ4][TI4]>(smem);                   // [2]
   float (*Xs)[TJ4][kXsLd] = reinterpret_cast<float (*)[TJ4][kXsLd]>(smem + 2 * TJ4 * TI4);  // [2]
-  float* H = smem + 2 * TJ4 * TI4 + 2 * TJ4 * kXsLd;                                        // [64][256]
-  float* Lo = H + 64 * 256;                                                                 // [64][256]
+  float* H = smem + 2 * TJ4 * TI4 + 2 * TJ4 * kXsLd;                                        // [8 NC][256]
+  float* Lo = H + 8 * NC * 256;                                                             // [8 NC][256]
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const double* xb = x + (size_t)b * nt * nx;
 #pragma unroll
-  for (int k = 0; k < 64; ++k) {
+  for (int k = 0; k < 8 * NC; ++k) {
     H[k * 256 + tid] = 0.f;
     Lo[k * 256 + tid] = 0.f;
   }
   const int nj = (nx + TJ4 - 1) / TJ4;
   const int stages = (d1 - d0) * nj;
-  // this thread's loads of one stage: 2 float4 of A, 8 values of x (kept in
+  // this thread's loads of one stage: 2 float4 of A, NC values of x (kept in
   // FP64 until the store, so that no conversion waits on a load in flight)
   float4 ra[2];
-  double rx[8];
+  double rx[NC];
   auto load = [&](int st) {
     const int d = d0 + st / nj, j0 = (st % nj) * TJ4;
     const float* Ad = A + (size_t)(d - lag_lo) * nx * nx;
@@ -248,7 +257,7 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
       if (gi < nx && gj < nx) ra[q] = *reinterpret_cast<const float4*>(Ad + (size_t)gi * nx + gj);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < NC; ++q) {
       const int e = tid + q * 256;
       const int jj = e % TJ4, mm = e / TJ4;
       const int m = m0 + mm, gj = j0 + jj;
@@ -266,16 +275,16 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
       As[buf][jq * 4 + 3][ii] = ra[q].w;
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < NC; ++q) {
       const int e = tid + q * 256;
       Xs[buf][e % TJ4][e / TJ4] = (float)rx[q];
     }
   };
-  float acc[8][8];    // [row r: ty*4 + r (r < 4), 64 + ty*4 + r - 4][step c likewise]
+  float acc[8][NC];   // [row r: ty*4 + r (r < 4), 64 + ty*4 + r - 4][step c likewise]
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    for (int c = 0; c < NC; ++c) acc[r][c] = 0.f;
   load(0);
   for (int st = 0; st < stages; ++st) {
     const int buf = st & 1;
@@ -287,20 +296,30 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
       const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][jj][ty * 4]);
       const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][jj][64 + ty * 4]);
       const float4 x0 = *reinterpret_cast<const float4*>(&Xs[buf][jj][tx * 4]);
-      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[buf][jj][64 + tx * 4]);
+      float bv[NC];
+      bv[0] = x0.x;
+      bv[1] = x0.y;
+      bv[2] = x0.z;
+      bv[3] = x0.w;
+      if constexpr (NC == 8) {
+        const float4 x1 = *reinterpret_cast<const float4*>(&Xs[buf][jj][64 + tx * 4]);
+        bv[4] = x1.x;
+        bv[5] = x1.y;
+        bv[6] = x1.z;
+        bv[7] = x1.w;
+      }
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        for (int c = 0; c < NC; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
     }
     if (st % nj == nj - 1) {   // the lag's partial is complete: fold it, restart
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int k = r * 8 + c;
+        for (int c = 0; c < NC; ++c) {
+          const int k = r * NC + c;
           float h = H[k * 256 + tid], l = Lo[k * 256 + tid];
           two_sum_add(h, l, acc[r][c]);
           H[k * 256 + tid] = h;
@@ -309,15 +328,15 @@ __device__ __forceinline__ void apply32_body(int nt, int nx, int MT, int CH, int
         }
     }
   }
-  double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TM4) * nx;
+  double* pt = part + ((((size_t)b * MT + mt) * CH + ch) * TMV) * nx;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < NC; ++c) {
     const int mm = (c < 4 ? 0 : 64) + tx * 4 + (c & 3);
     if (m0 + mm > mmax) continue;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int gi = i0 + (r < 4 ? 0 : 64) + ty * 4 + (r & 3);
-      const int k = r * 8 + c;
+      const int k = r * NC + c;
       if (gi < nx) pt[(size_t)mm * nx + gi] = (double)H[k * 256 + tid] + (double)Lo[k * 256 + tid];
     }
   }
@@ -327,8 +346,8 @@ __global__ void __launch_bounds__(256, 1)
 k_apply32(int nt, int nx, int MT, int CH, int DC, int lag_lo, int lag_hi, const float* __restrict__ A,
           const double* __restrict__ x, double* __restrict__ part) {
   extern __shared__ __align__(16) float smem32[];
-  apply32_body(nt, nx, MT, CH, DC, lag_lo, lag_hi, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT,
-               blockIdx.z % MT, smem32);
+  apply32_body<TM4>(nt, nx, MT, CH, DC, lag_lo, lag_hi, A, x, part, blockIdx.x, blockIdx.y, blockIdx.z / MT,
+                    blockIdx.z % MT, smem32);
 }
 
 // ---- ragged batches ------------------------------------------------------------------
@@ -372,7 +391,7 @@ k_ragged_apply(const RaggedApplyPlan* __restrict__ plans, const int* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restrict__ order,
                  const long long* __restrict__ prefix, int P, unsigned long long* __restrict__ counter,
                  const float* __restrict__ A, const double* __restrict__ x, double* __restrict__ part) {
@@ -391,8 +410,8 @@ k_ragged_apply32(const RaggedApplyPlan* __restrict__ plans, const int* __restric
     const int it = (int)(u % pl.IT);
     const long long r = u / pl.IT;
     const int mt = (int)(r % pl.MT), ch = (int)(r / pl.MT);
-    apply32_body(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, 0, pl.nt, A + pl.a_off, x + pl.v_off, part + pl.part_off, it,
-                 ch, 0, mt, smem32);
+    apply32_body<TM4R>(pl.nt, pl.nx, pl.MT, pl.CH, pl.DC, 0, pl.nt, A + pl.a_off, x + pl.v_off, part + pl.part_off,
+                       it, ch, 0, mt, smem32);
     __syncthreads();
   }
 }
@@ -551,7 +570,7 @@ bool apply_grid_fits(int nt, int nx, int n_rhs) {
 }
 
 void ragged_apply_plan(int nt, int nx, int lags_per_chunk, bool fp32_tiles, RaggedApplyPlan* p) {
-  const int tm = fp32_tiles ? TM4 : TM, ti = fp32_tiles ? TI4 : TI;
+  const int tm = fp32_tiles ? TM4R : TM, ti = fp32_tiles ? TI4 : TI;
   p->nt = nt;
   p->nx = nx;
   p->MT = (nt + tm - 1) / tm;
@@ -578,11 +597,11 @@ cudaError_t ragged_apply_launch(int prec, bool fp32_tiles, const RaggedApplyPlan
     k_ragged_apply<double, double><<<sms * (occ > 0 ? occ : 1), kApplyThreads, 0, s>>>(
         plans, items.order, items.prefix, P, counter, static_cast<const double*>(A), x, part);
   } else if (fp32_tiles) {
-    e = cudaFuncSetAttribute(k_ragged_apply32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApply32Smem);
+    e = cudaFuncSetAttribute(k_ragged_apply32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApply32SmemR);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply32, 256, kApply32Smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ragged_apply32, 256, kApply32SmemR);
     if (e != cudaSuccess) return e;
-    k_ragged_apply32<<<sms * (occ > 0 ? occ : 1), 256, kApply32Smem, s>>>(plans, items.order, items.prefix, P,
+    k_ragged_apply32<<<sms * (occ > 0 ? occ : 1), 256, kApply32SmemR, s>>>(plans, items.order, items.prefix, P,
                                                                           counter, static_cast<const float*>(A), x,
                                                                           part);
   } else {
@@ -594,7 +613,7 @@ cudaError_t ragged_apply_launch(int prec, bool fp32_tiles, const RaggedApplyPlan
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (prec != STBEM_F64 && fp32_tiles)
-    k_ragged_reduce<TM4><<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
+    k_ragged_reduce<TM4R><<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
   else
     k_ragged_reduce<TM><<<sms * 8, 256, 0, s>>>(plans, vprefix, P, part, y);
   count_launches(2);
