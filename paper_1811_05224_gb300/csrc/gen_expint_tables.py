@@ -147,12 +147,6 @@ def main():
     lines.append("constexpr double kLn2by256Lo = %s;" % mp.nstr(lo, 20, min_fixed=0, max_fixed=0))
     lines.append("static __constant__ const double kExp2Tab[256] = {%s};" % ", ".join(
         mp.nstr(t, 20, min_fixed=0, max_fixed=0) for t in tab))
-    # e^{-r l} for the pre-scaled argument y = x 256/ln2 = n + r, |r| <= 1/2:
-    # Taylor coefficients (-l)^k / k!, k = 1..4, l = ln2/256 (remainder
-    # (|r| l)^5 / 120 < 4e-17)
-    sc = [(-l) ** k / mp.factorial(k) for k in range(1, 5)]
-    for k, c in enumerate(sc):
-        lines.append("constexpr double kExpScaledC%d = %s;" % (k + 1, mp.nstr(c, 21, min_fixed=0, max_fixed=0)))
     # e^{-c k} with k = sigma 2048/ln2 for the hot loops: c k = n + r by a fused
     # multiply-add rounding, table 2^{-j/2048}, j = 0..2047, and Taylor
     # coefficients (-l)^k / k!, k = 1..3, l = ln2/2048 (remainder
