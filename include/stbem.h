@@ -111,6 +111,19 @@ int stbem_op_bytes(const stbem_mesh* mesh, int op, int prec, size_t* bytes);
 int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* mesh, int op, int prec,
                    void* dev_out);
 
+/* The three operators of the boundary integral system (Section 2, eq. (7)):
+ * stbem_assemble of V, K and D at once, each into its own n_t x n_x x n_x
+ * array of its own precision prec_V / prec_K / prec_D (STBEM_F64 or
+ * STBEM_F32, checked for all three; a NULL output is skipped and at least one
+ * is given).  D runs on the context's stream and K, V on two side streams the
+ * context owns (created on the first call), which wait for the context
+ * stream's earlier work and are joined back into it: work enqueued on the
+ * context stream afterwards sees all three.  Each operator uses its own slice
+ * of the mesh's singular-pair scratch, so the result equals three
+ * stbem_assemble calls bit for bit.  Errors as stbem_assemble. */
+int stbem_assemble_ops(stbem_ctx* ctx, const stbem_mesh* mesh, int prec_V, int prec_K,
+                       int prec_D, void* dev_V, void* dev_K, void* dev_D);
+
 /* As stbem_assemble, restricted to the lag blocks d in [lag_begin, lag_end)
  * (0 <= lag_begin <= lag_end <= n_t); dev_out is still the full
  * n_t x n_x x n_x array and only those blocks are written.  Lag ranges are

@@ -260,6 +260,26 @@ def assemble(ctx: Context, mesh: Mesh, op: str, prec: str = "f64", out=None):
     return out
 
 
+def assemble_ops(ctx: Context, mesh: Mesh, prec="f64", ops: str = "VKD", out=None):
+    """The lag blocks of each operator in ops, assembled concurrently on the
+    context's stream and two side streams; returns {op: array}.  prec is one
+    precision for all, or a dict {op: precision}; out may map an operator to a
+    preallocated array."""
+    precs = {op: PRECS[prec[op] if isinstance(prec, dict) else prec] for op in "VKD" if op in ops}
+    out = dict(out or {})
+    for op in ops:
+        if op not in out:
+            out[op] = ctx.empty((mesh.n_t, mesh.n_x, mesh.n_x), DTYPES[precs[op]])
+        elif out[op].dtype != DTYPES[precs[op]] or tuple(out[op].shape) != (mesh.n_t, mesh.n_x, mesh.n_x) \
+                or not out[op].is_contiguous():
+            raise ValueError("assemble_ops: out[%r] must be a contiguous %s array of shape %s"
+                             % (op, DTYPES[precs[op]], (mesh.n_t, mesh.n_x, mesh.n_x)))
+    ptrs = [_ptr(out[op]) if op in ops else None for op in "VKD"]
+    pv = [precs.get(op, capi.F64) for op in "VKD"]
+    ctx.check(ctx.lib.stbem_assemble_ops(ctx.h, mesh.h, *pv, *ptrs))
+    return {op: out[op] for op in ops}
+
+
 def assemble_lags(ctx: Context, mesh: Mesh, op: str, lag_begin: int, lag_end: int, prec: str = "f64", out=None):
     """Write only the lag blocks [lag_begin, lag_end) of op into out."""
     p = PRECS[prec]

@@ -145,7 +145,7 @@ int stbem_mesh_create(stbem_ctx* ctx, const double* xy, int n_x, double T, int n
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&m->dbuf, host.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&m->ibuf, dp.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&m->sbuf, (size_t)2 * 3 * (2 * N) * 5 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->sbuf, 3 * stbem_internal::sing_slice(N) * sizeof(double));
   std::vector<double> tn(n_t + 1);
   for (int k = 0; k <= n_t; ++k) tn[k] = k == n_t ? T : (double)k * m->ht;
   if (e == cudaSuccess) e = cudaMalloc(&m->tbuf, tn.size() * sizeof(double));
@@ -233,7 +233,41 @@ int stbem_assemble(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, void* 
   if (op < 0 || op > 2) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown operator %d", op);
   if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "assemble: unknown precision %d", prec);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble: set device");
-  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, 0, m->n_t, out, ctx->stream), "assemble: launch");
+  CUDA_TRY(ctx, stbem::assemble_launch(stbem_internal::op_dev(m, op), op, prec, 0, m->n_t, out, ctx->stream),
+           "assemble: launch");
+  return STBEM_OK;
+}
+
+int stbem_assemble_ops(stbem_ctx* ctx, const stbem_mesh* m, int prec_V, int prec_K, int prec_D, void* V, void* K,
+                       void* D) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (const int rg = reject_graded(ctx, m, "assemble_ops")) return rg;
+  if (!m || (!V && !K && !D)) return fail(ctx, STBEM_ERR_ARG, "assemble_ops: NULL mesh or no output");
+  const int precs[3] = {prec_V, prec_K, prec_D};
+  for (int op = 0; op < 3; ++op)
+    if (precs[op] != STBEM_F64 && precs[op] != STBEM_F32)
+      return fail(ctx, STBEM_ERR_ARG, "assemble_ops: unknown precision %d", precs[op]);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble_ops: set device");
+  for (int k = 0; k < 2; ++k)
+    if (!ctx->side[k]) CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking), "assemble_ops: stream");
+  for (int k = 0; k < 3; ++k)
+    if (!ctx->ev[k]) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev[k], cudaEventDisableTiming), "assemble_ops: event");
+  // D (the largest) on the caller's stream, K and V on the side streams, which
+  // first wait for the caller's earlier work and are joined back at the end
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream), "assemble_ops: fork");
+  void* outs[3] = {V, K, D};
+  const cudaStream_t streams[3] = {ctx->side[1], ctx->side[0], ctx->stream};
+  for (int op = 2; op >= 0; --op) {
+    if (!outs[op]) continue;
+    if (streams[op] != ctx->stream) CUDA_TRY(ctx, cudaStreamWaitEvent(streams[op], ctx->ev[0], 0), "assemble_ops: wait");
+    CUDA_TRY(ctx, stbem::assemble_launch(stbem_internal::op_dev(m, op), op, precs[op], 0, m->n_t, outs[op], streams[op]),
+             "assemble_ops: launch");
+  }
+  for (int op = 0; op < 2; ++op) {
+    if (!outs[op]) continue;
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1 + op], streams[op]), "assemble_ops: join");
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev[1 + op], 0), "assemble_ops: join");
+  }
   return STBEM_OK;
 }
 
@@ -247,7 +281,8 @@ int stbem_assemble_lags(stbem_ctx* ctx, const stbem_mesh* m, int op, int prec, i
   if (lag_begin < 0 || lag_end > m->n_t || lag_begin > lag_end)
     return fail(ctx, STBEM_ERR_ARG, "assemble_lags: lag range [%d, %d) outside [0, %d)", lag_begin, lag_end, m->n_t);
   CUDA_TRY(ctx, cudaSetDevice(ctx->device), "assemble_lags: set device");
-  CUDA_TRY(ctx, stbem::assemble_launch(m->dev, op, prec, lag_begin, lag_end, out, ctx->stream), "assemble_lags");
+  CUDA_TRY(ctx, stbem::assemble_launch(stbem_internal::op_dev(m, op), op, prec, lag_begin, lag_end, out, ctx->stream),
+           "assemble_lags");
   return STBEM_OK;
 }
 

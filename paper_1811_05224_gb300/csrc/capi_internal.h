@@ -14,6 +14,15 @@ struct stbem_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   std::string err;
+  // stbem_assemble_ops: two side streams and three events, created on first use
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  ~stbem_ctx() {
+    for (auto& st : side)
+      if (st) cudaStreamDestroy(st);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 struct stbem_mesh {
@@ -24,7 +33,7 @@ struct stbem_mesh {
   std::vector<double> xy;    // vertices (host copy, 2 N)
   double* dbuf = nullptr;    // device geometry
   int* ibuf = nullptr;
-  double* sbuf = nullptr;    // lag-0/1 singular-pair moments (2 lags x 3 x 2N x 5)
+  double* sbuf = nullptr;    // lag-0/1 singular-pair moments, one slice per operator (V, K, D: 2 lags x 3 x 2N x 5)
   double* tbuf = nullptr;    // the n_t + 1 time nodes (uniform k T / n_t unless graded)
   std::vector<double> tnodes;  // host copy of a graded mesh's nodes
   bool graded = false;       // non-uniform time grid: only the stbem_nu_* calls apply
@@ -32,6 +41,18 @@ struct stbem_mesh {
 };
 
 namespace stbem_internal {
+
+// doubles of one operator's slice of the singular-pair scratch
+inline size_t sing_slice(int N) { return (size_t)2 * 3 * (2 * N) * 5; }
+
+// the mesh's device view for assembling operator op: its own slice of the
+// singular-pair scratch, so that the three operators may be assembled
+// concurrently
+inline stbem::DevMesh op_dev(const stbem_mesh* m, int op) {
+  stbem::DevMesh d = m->dev;
+  d.sing = m->sbuf + (size_t)op * sing_slice(m->N);
+  return d;
+}
 
 inline int fail(stbem_ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) {

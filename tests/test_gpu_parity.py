@@ -249,6 +249,32 @@ def test_assemble_lags_pieces_equal_full(ctx):
         P.assemble_lags(ctx, m, "V", 3, nt + 1)
 
 
+@pytest.mark.parametrize("nx,nt", [(24, 16), (256, 48)])
+def test_assemble_ops_equals_separate(ctx, nx, nt):
+    """V, K and D assembled concurrently (side streams, one singular-pair
+    scratch slice per operator) equal three separate assemblies bit for bit,
+    for one precision and for mixed per-operator precisions, and work queued
+    on the context's stream afterwards sees every output."""
+    import paper_1811_05224_gb300 as P
+    m = P.Mesh(ctx, W.l_shape(nx, seed=3), 1.0, nt, 0.5)
+    for prec in ("f64", "f32", {"V": "f64", "K": "f64", "D": "f32"}):
+        ref = {op: P.assemble(ctx, m, op, prec[op] if isinstance(prec, dict) else prec) for op in "VKD"}
+        for rep in range(2):
+            got = P.assemble_ops(ctx, m, prec)
+            for op in "VKD":
+                assert torch.equal(ref[op], got[op]), (prec, op, rep)
+    # a subset, into preallocated outputs (NaN-filled: every entry is written)
+    out = {op: torch.full((nt, m.n_x, m.n_x), float("nan"), dtype=torch.float64, device="cuda") for op in "KD"}
+    got = P.assemble_ops(ctx, m, "f64", ops="KD", out=out)
+    assert set(got) == {"K", "D"}
+    assert torch.equal(got["K"], P.assemble(ctx, m, "K")) and torch.equal(got["D"], P.assemble(ctx, m, "D"))
+    with pytest.raises(ValueError):
+        P.assemble_ops(ctx, m, "f32", ops="V", out={"V": torch.empty((nt, m.n_x, m.n_x), dtype=torch.float64,
+                                                                      device="cuda")})
+    with pytest.raises(Exception):
+        ctx.check(ctx.lib.stbem_assemble_ops(ctx.h, m.h, 0, 0, 0, None, None, None))
+
+
 def test_consistent_mixed_mass_preconditioner(ctx):
     """stbem_mixed_mass_inverse against the inverse of the oracle's consistent
     mixed mass, and the solves preconditioned with M_h^{-1} D_h M_h^{-T}
