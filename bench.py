@@ -7,7 +7,10 @@ g = U*(x - y*, t) with y* = (1.5, 1.5), u_0 = 0 (synthetic, seeded geometry).
 One step = the whole hot path on one GPU, inputs (the mesh) resident:
   assembly of V_h, K_h, D_h (FP64, 3 x 256 x 256 x 256 Toeplitz entries),
   right-hand side f = 1/2 M_h g + K_h g, lumped mass,
-  right-preconditioned GMRES to a relative residual of 1e-8.
+  right-preconditioned GMRES to a relative residual of 1e-8 (FP64), its
+  products of V_h and D_h taken through the frequency blocks of the lag
+  blocks (time FFTs, transformed inside the step) unless --solve direct; the
+  step with the other product is timed beside it.
 value = distinct Toeplitz entries assembled per second of whole-step time.
 Component figures (assembly entries/s, Toeplitz-apply GB/s and GFLOP/s, GMRES
 time) are reported beside it.  Between timed steps a 256 MB buffer is written
@@ -94,9 +97,10 @@ def W_config():
     return W.config(WORKLOAD)
 
 
-def _config(p, l2):
+def _config(p, l2, solve="fft"):
     return {"workload": WORKLOAD, "n_x": p.n_x, "n_t": p.n_t, "alpha": p.alpha, "T": p.T,
-            "y_star": list(p.y_star), "precision": "fp64 assembly + fp64 GMRES", "l2": l2}
+            "y_star": list(p.y_star), "precision": "fp64 assembly + fp64 GMRES", "l2": l2,
+            "gmres_products": "time FFTs of the lag blocks (fp64)" if solve == "fft" else "direct block sums"}
 
 
 def _oracle_worker(args):
@@ -795,6 +799,12 @@ def run_ours(args):
     awork = P.api.apply_workspace(ctx, nt, nx, 1)
     swork = P.api.solve_workspace(ctx, nt, nx, 200)
     w = ctx.empty((nt, nx))
+    # frequency blocks of V and D for the products through time FFTs
+    nf, nfb = ctypes.c_int(), ctypes.c_size_t()
+    ctx.check(lib.stbem_fft_operator_bytes(nt, nx, ctypes.byref(nf), ctypes.byref(nfb)))
+    Vh, Dh = (P.FFTOperator(torch.empty((nf.value, nx, nx), dtype=torch.complex128, device=dev), nt, nx)
+              for _ in range(2))
+    fswork = P.api.solve_fft_workspace(ctx, nt, nx, 200)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)       # noqa: E731
     infos = []
@@ -807,7 +817,7 @@ def run_ours(args):
         ranges = P.shard.lag_ranges(nt, world, rank, 16)
         Vs, Ks, Ds = (P.shard.ShardedOperator(ctx, mesh, o, ranges) for o in "VKD")
 
-    def step(m, events=None):
+    def step(m, events=None, solve_mode=args.solve, infos_out=infos):
         e = [ev() for _ in range(5)] if events is None else events
         e[0].record(stream)
         if sharded:
@@ -824,9 +834,14 @@ def run_ours(args):
             g, f = P.rhs(ctx, m, K, p.y_star, work=awork)
             L = P.lumped_mass(ctx, m)
             e[2].record(stream)
-            _, info = P.solve(ctx, V, f, D, L, tol=1e-8, max_iter=500, restart=200, work=swork, out=w)
+            if solve_mode == "fft":
+                P.fft_operator(ctx, V, out=Vh.data)
+                P.fft_operator(ctx, D, out=Dh.data)
+                _, info = P.solve_fft(ctx, Vh, f, Dh, L, tol=1e-8, max_iter=500, restart=200, work=fswork, out=w)
+            else:
+                _, info = P.solve(ctx, V, f, D, L, tol=1e-8, max_iter=500, restart=200, work=swork, out=w)
         e[3].record(stream)
-        infos.append(info)
+        infos_out.append(info)
         return e
 
     def barrier():
@@ -859,6 +874,28 @@ def run_ours(args):
     # replicas: every rank its own (weak)
     value = strong_value(entries, ms_step) if sharded else weak_value(entries, world, ms_step)
     asm_rate = entries / (statistics.mean(ms_asm) * 1e-3)
+    # the same step with the other product (direct block sums or time FFTs),
+    # timed the same way, and the distance between the two solutions
+    step_alt = None
+    if not sharded:
+        alt_mode = "direct" if args.solve == "fft" else "fft"
+        w_main = w.clone()
+        alt_infos = []
+        for _ in range(max(args.warmup, 1)):
+            step(mesh, solve_mode=alt_mode, infos_out=alt_infos)
+        torch.cuda.synchronize(dev)
+        alt_events = []
+        for _ in range(args.steps):
+            flush.zero_()
+            alt_events.append(step(mesh, solve_mode=alt_mode, infos_out=alt_infos))
+        torch.cuda.synchronize(dev)
+        step_alt = {"solve": alt_mode,
+                    "ms_per_step": statistics.mean(e[0].elapsed_time(e[3]) for e in alt_events),
+                    "gmres_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in alt_events),
+                    "gmres_iterations": alt_infos[-1]["iterations"],
+                    "gmres_rel_residual": alt_infos[-1]["rel_residual"],
+                    "w_rel_diff": float((w - w_main).norm() / w_main.norm())}
+        w.copy_(w_main)
     if sharded:
         # the per-kernel components below use full operators on every rank
         for op, buf in (("V", V), ("K", K), ("D", D)):
@@ -881,6 +918,39 @@ def run_ours(args):
     ms_apply = a0.elapsed_time(a1) / reps
     apply_flops = 2.0 * nx * nx * nt * (nt + 1) / 2
     apply_bytes = nt * nx * nx * 8 + 2 * nt * nx * 8
+    # the same product through the frequency blocks (three launches: the
+    # transform of x, one complex matrix-vector product per frequency, the
+    # inverse transform); algorithmic bytes: the frequency blocks once, x and
+    # y, and the two transforms written and read once each
+    P.fft_operator(ctx, V, out=Vh.data)
+    fawork = P.api.apply_fft_workspace(ctx, nt, nx, 1)
+    yf = torch.empty_like(x)
+    for _ in range(3):
+        P.apply_fft(ctx, Vh, x, work=fawork, out=yf)
+    f0, f1 = ev(), ev()
+    flush.zero_()
+    f0.record(stream)
+    for _ in range(reps):
+        P.apply_fft(ctx, Vh, x, work=fawork, out=yf)
+    f1.record(stream)
+    o0, o1 = ev(), ev()
+    flush.zero_()
+    o0.record(stream)
+    for _ in range(reps):
+        P.fft_operator(ctx, V, out=Vh.data)
+    o1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_apply_fft = f0.elapsed_time(f1) / reps
+    ms_fft_op = o0.elapsed_time(o1) / reps
+    fft_apply_bytes = nf.value * nx * nx * 16 + 2 * nt * nx * 8 + 4 * nf.value * nx * 16
+    fft_op_bytes = nt * nx * nx * 8 + nf.value * nx * nx * 16
+    # flops: 8 per complex multiply-add of the frequency products, and
+    # 5 L log2 L per complex transform of length L (two real columns each)
+    Lf = 2 * (nf.value - 1)
+    fft_len_flops = 5.0 * Lf * np.log2(Lf)
+    fft_apply_flops = 8.0 * nf.value * nx * nx + 2 * (nx / 2) * fft_len_flops
+    fft_op_flops = (nx * nx / 2) * fft_len_flops
+    apply_fft_rel = float((yf - y).norm() / y.norm())
     # dominant kernel: the FP64 D tile kernel at lags >= 2 (four lags per CTA,
     # chunks within one space order each, one launch), timed alone with CUDA
     # events on the launching stream; launches counted
@@ -968,6 +1038,12 @@ def run_ours(args):
     it_last = infos[-1]["iterations"]
     t_apply = max(apply_bytes / (hbm_gbs * 1e9), apply_flops / (fp64_peak * 1e12))
     t_gs = sum(4.0 * (k + 1) * nt * nx * 8 / (hbm_gbs * 1e9) for k in range(it_last))
+    if args.solve == "fft" and not sharded:
+        # products through the frequency blocks, plus the two operator
+        # transforms inside the timed solve interval, each at
+        # max(bytes / HBM, flops / measured FP64)
+        t_apply = max(fft_apply_bytes / (hbm_gbs * 1e9), fft_apply_flops / (fp64_peak * 1e12))
+        t_gs += 2 * max(fft_op_bytes / (hbm_gbs * 1e9), fft_op_flops / (fp64_peak * 1e12))
     gmres_roof_ms = 1e3 * ((2 * it_last + 1) * t_apply + t_gs)
 
     # end to end through the public API with host buffers: vertices in, w out
@@ -1008,7 +1084,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(_config(p, "256 MB buffer written between steps"),
+        "config": dict(_config(p, "256 MB buffer written between steps", args.solve),
                        parallelism=("lag-sharded over %d GPUs (chunks of 16 lags, snake order), NCCL all-reduce "
                                     "per product" % world) if sharded else
                        ("%d independent replicas" % world if world > 1 else "1 GPU")),
@@ -1025,9 +1101,27 @@ def run_ours(args):
             "gmres_rel_residual": last["rel_residual"],
             "gmres_roofline_ms": gmres_roof_ms,
             "gmres_roofline_frac": gmres_roof_ms / statistics.mean(ms_solve),
-            "gmres_roofline_note": "iterations x (V apply + D apply at max(bytes / HBM, flops / measured FP64)) "
-                                   "+ Gram-Schmidt traffic + final residual apply, over the GMRES time "
-                                   "(right-hand side excluded)",
+            "gmres_roofline_note": "iterations x (V apply + D apply at their roofline: direct products at "
+                                   "max(bytes / HBM, flops / measured FP64), products through the frequency "
+                                   "blocks at bytes / HBM plus the two operator transforms) + Gram-Schmidt "
+                                   "traffic + final residual apply, over the GMRES time (right-hand side "
+                                   "excluded)",
+            "solve": args.solve,
+            "step_other_product": step_alt,
+            "apply_fft": {
+                "ms": ms_apply_fft, "gbs": fft_apply_bytes / (ms_apply_fft * 1e-3) / 1e9,
+                "tflops": fft_apply_flops / (ms_apply_fft * 1e-3) / 1e12,
+                "bound": "alu", "frac_of_fp64": fft_apply_flops / (ms_apply_fft * 1e-3) / 1e12 / fp64_peak,
+                "frac_of_hbm": fft_apply_bytes / (ms_apply_fft * 1e-3) / 1e9 / hbm_gbs,
+                "bytes": fft_apply_bytes, "flops": fft_apply_flops, "rel_diff_vs_direct": apply_fft_rel,
+                "note": "three launches (transform of x, frequency products, inverse transform); 8 flops "
+                        "per complex multiply-add and 16 bytes per frequency-block entry: 0.5 flop/byte, "
+                        "above the FP64/HBM balance, so FP64-bound"},
+            "fft_operator": {
+                "ms": ms_fft_op, "gbs": fft_op_bytes / (ms_fft_op * 1e-3) / 1e9,
+                "tflops": fft_op_flops / (ms_fft_op * 1e-3) / 1e12,
+                "bound": "alu", "frac_of_fp64": fft_op_flops / (ms_fft_op * 1e-3) / 1e12 / fp64_peak,
+                "bytes": fft_op_bytes, "flops": fft_op_flops},
             "peaks": dict(peaks, hbm_gbs=hbm_gbs, note="fp64/fp32/ex2 measured in this run by stbem_pipe_peaks; "
                                                        "hbm from MEASURED_PEAKS.json"),
             "precision": precision,
@@ -1118,6 +1212,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve", choices=["fft", "direct"], default="fft",
+                    help="products inside the step's GMRES: through time FFTs of the lag blocks (default) or the "
+                         "direct block sums; the other is timed beside it")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-right-hand-side square512 component")
     ap.add_argument("--batched-fp64-residual", action="store_true",
                     help="also time the batched solve on FP64 CUDA-core residuals (about a minute)")
@@ -1130,7 +1227,8 @@ def main():
                     help="skip the L-shape N_x = N_t = 1024 mixed-versus-FP64 component")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default square256; smaller ones are for profiling)")
-    ap.add_argument("--component", choices=["tc", "grad", "precision", "initial", "f32apply"], default=None,
+    ap.add_argument("--component", choices=["tc", "grad", "precision", "initial", "f32apply", "fftapply"],
+                    default=None,
                     help="run one kernel family alone on a small case (for ncu captures) and print its timing")
     ap.add_argument("--size", type=int, default=256, help="N_x = N_t of --component's case")
     ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --component tc")
@@ -1194,13 +1292,31 @@ def run_precision(ctx, dev, stream):
     t[2].record(stream)
     del Vx, V3, D3
     torch.cuda.empty_cache()
+    # FP64 GMRES with the products through time FFTs: frequency blocks of the
+    # FP64 V and of the FP32 D (the preconditioner), no FP32 product anywhere
+    q = [ev() for _ in range(3)]
+    q[0].record(stream)
+    Vh = P.fft_operator(ctx, V)
+    Dh = P.fft_operator(ctx, D32)
+    q[1].record(stream)
+    wf, i_f = P.solve_fft(ctx, Vh, f, Dh, Minv, tol=1e-8, max_iter=400, restart=60)
+    q[2].record(stream)
     f0 = ev()
     f0.record(stream)         # the FP64 path starts here
     D = P.assemble(ctx, m, "D")
     e[6].record(stream)
     w, i64 = P.solve(ctx, V, f, D, Minv, tol=1e-8, max_iter=400, restart=60)
     e[7].record(stream)
+    # the FP64 path's GMRES with the products through time FFTs
+    h = [ev() for _ in range(3)]
+    h[0].record(stream)
+    P.fft_operator(ctx, D, out=Dh.data)
+    h[1].record(stream)
+    wf64, i_f64 = P.solve_fft(ctx, Vh, f, Dh, Minv, tol=1e-8, max_iter=400, restart=60)
+    h[2].record(stream)
     torch.cuda.synchronize(dev)
+    del Vh, Dh
+    torch.cuda.empty_cache()
     r = f - P.apply(ctx, V, wm)
     out = {
         "workload": "lshape1024: N_x = N_t = 1024, alpha = 0.5, seeded lengths (seed 3)",
@@ -1224,6 +1340,25 @@ def run_precision(ctx, dev, stream):
         "note": "FP32 D and V inner GMRES; outer residuals from the exact-slice V product (7 slices) "
                 "on the tensor cores instead of the FP64 CUDA-core product; path = D32 + V32 + mass + "
                 "slicing V + solve"}
+    r5 = f - P.apply(ctx, V, wf)
+    out["mixed_fft"] = {
+        "transforms_ms": q[0].elapsed_time(q[1]), "solve_ms": q[1].elapsed_time(q[2]),
+        "iterations": i_f["iterations"],
+        "path_ms": e[3].elapsed_time(e[4]) + q[0].elapsed_time(q[2]),
+        "fp64_rel_residual": float(r5.norm() / f.norm()),
+        "w_rel_diff_vs_fp64": float((wf - w).norm() / w.norm()),
+        "note": "FP64 GMRES, every product through the frequency blocks (time FFTs) of the FP64 V and of "
+                "the FP32 D; path = D32 + V32 + mass + both transforms + solve"}
+    r6 = f - P.apply(ctx, V, wf64)
+    out["fp64_fft"] = {
+        "transform_D_ms": h[0].elapsed_time(h[1]), "transform_V_ms": q[0].elapsed_time(q[1]) - h[0].elapsed_time(h[1]),
+        "solve_ms": h[1].elapsed_time(h[2]), "iterations": i_f64["iterations"],
+        "path_ms": f0.elapsed_time(e[6]) + q[0].elapsed_time(q[1]) + h[1].elapsed_time(h[2]),
+        "fp64_rel_residual": float(r6.norm() / f.norm()),
+        "w_rel_diff_vs_fp64": float((wf64 - w).norm() / w.norm()),
+        "note": "the FP64 path with its GMRES products through the frequency blocks of V and D (FP64); "
+                "path = D FP64 assembly + both transforms + solve (transform_V_ms: the two transforms of "
+                "the mixed_fft entry less that of D)"}
     r4 = f - P.apply(ctx, V, wt)
     out["mixed_tc"] = {
         "slices_ms": t[0].elapsed_time(t[1]), "solve_ms": t[1].elapsed_time(t[2]),
@@ -1234,7 +1369,7 @@ def run_precision(ctx, dev, stream):
         "note": "inner GMRES on the BF16 tensor cores (three-slice V and D, compensated products, "
                 "lag chunks for one right-hand side), exact-slice outer residuals; path = D32 + mass + "
                 "exact slices of V + BF16 slices of V and D + solve"}
-    del V, D, D32, wm, w, wx, wt, f, g, L, Minv, r, r2, r3, r4
+    del V, D, D32, wm, w, wx, wt, wf, wf64, f, g, L, Minv, r, r2, r3, r4, r5, r6
     torch.cuda.empty_cache()
     return out
 
@@ -1281,6 +1416,46 @@ def run_component(args):
         flops = 2.0 * n * n * n * (n + 1) / 2
         out.update({"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
                     "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / P.pipe_peaks(ctx)["fp32_tflops"]})
+        print(json.dumps(out))
+        return 0
+    if args.component == "fftapply":
+        # the product through the frequency blocks of a unit-square V with
+        # n_t = N_x = --size, one right-hand side: the operator transform
+        # (first launch of k_rfft_cols), then forward and transposed products
+        mesh = P.Mesh(ctx, W.unit_square(n // 4), 1.0, n, 1.0)
+        V = P.assemble(ctx, mesh, "V")
+        Vh = P.fft_operator(ctx, V)
+        g = torch.Generator(device="cpu").manual_seed(3)
+        x = torch.randn((n, n), generator=g, dtype=torch.float64).to(dev)
+        work = P.api.apply_fft_workspace(ctx, n, n, 1)
+        y = torch.empty_like(x)
+        nf = Vh.data.shape[0]
+        res = {}
+        for name, call, reps in (("apply_fft", lambda: P.apply_fft(ctx, Vh, x, work=work, out=y), 20),
+                                 ("apply_fft_t", lambda: P.apply_fft(ctx, Vh, x, True, work=work, out=y), 20),
+                                 ("fft_operator", lambda: P.fft_operator(ctx, V, out=Vh.data), 5)):
+            for _ in range(3):
+                call()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(reps):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            res[name] = e0.elapsed_time(e1) / reps
+        prod_bytes = nf * n * n * 16 + 2 * n * n * 8 + 4 * nf * n * 16
+        op_bytes = n * n * n * 8 + nf * n * n * 16
+        Lf = 2 * (nf - 1)
+        tflops = 5.0 * Lf * np.log2(Lf)
+        prod_flops = 8.0 * nf * n * n + n * tflops
+        op_flops = (n * n / 2) * tflops
+        fp64 = P.pipe_peaks(ctx)["fp64_tflops"]
+        out.update({"ms": res, "apply_fft_gbs": prod_bytes / (res["apply_fft"] * 1e-3) / 1e9,
+                    "apply_fft_frac_of_fp64": prod_flops / (res["apply_fft"] * 1e-3) / 1e12 / fp64,
+                    "fft_operator_frac_of_fp64": op_flops / (res["fft_operator"] * 1e-3) / 1e12 / fp64,
+                    "fp64_tflops_measured": fp64,
+                    "bytes": {"apply_fft": prod_bytes, "fft_operator": op_bytes},
+                    "flops": {"apply_fft": prod_flops, "fft_operator": op_flops}})
         print(json.dumps(out))
         return 0
     if args.component == "tc":

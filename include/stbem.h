@@ -287,6 +287,65 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void*
                         double* dev_lambda, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* dev_work, size_t work_bytes);
 
+/* ---- Products through time FFTs (Section 2: the block-Toeplitz structure) --
+ * The product y_n = sum_{d=0}^{n} A_d x_{n-d} with the lag blocks of
+ * V_h, K_h or D_h is a convolution in the time index.  With L the smallest
+ * power of two >= 2 n_t and w = e^{-2 pi i / L} the frequency blocks are
+ *     Ahat_k = sum_{d=0}^{n_t - 1} A_d w^{d k},  k = 0 .. L/2
+ * (complex N_x x N_x, stored Ahat[k][i][j] as interleaved (re, im) doubles;
+ * the remaining frequencies are their complex conjugates).  A product is a
+ * real FFT of x along time, Yhat_k = Ahat_k Xhat_k per frequency, and the
+ * inverse real FFT: the same matrix-vector product as stbem_apply up to
+ * rounding, with (L/2 + 1) N_x^2 complex multiply-adds in place of
+ * n_t (n_t + 1) N_x^2 / 2 real ones and the frequency blocks read once.
+ * Rounding: per output row i and right-hand side,
+ *     ||y_i - (A x)_i||_2 <= c_L sum_j ||a_ij||_1 ||x_j||_2,
+ * a_ij = (A_d[i][j])_d, x_j = (x_n[j])_n, c_L of order log2(L) sqrt(n_t) u
+ * (u = 2^-53): a normwise bound, unlike the entrywise one of stbem_apply.
+ * Limits: 1 <= n_t <= 4096, 1 <= n_x <= 8192. */
+
+/* Size of the frequency blocks of an n_t x n_x x n_x operator: *n_freq =
+ * L/2 + 1 (may be NULL), *bytes = n_freq * n_x * n_x * 16.  Errors:
+ * STBEM_ERR_ARG (sizes outside the limits, NULL bytes). */
+int stbem_fft_operator_bytes(int n_t, int n_x, int* n_freq, size_t* bytes);
+
+/* dev_Ahat (16-byte aligned, stbem_fft_operator_bytes) from the lag blocks
+ * dev_A (n_t x n_x x n_x, FP64 or FP32 by prec; an FP32 operator is widened
+ * exactly, which suits a preconditioner such as the mixed D_h).  Errors:
+ * STBEM_ERR_ARG (sizes, NULL, alignment, precision), STBEM_ERR_CUDA. */
+int stbem_fft_operator(stbem_ctx* ctx, int n_t, int n_x, int prec, const void* dev_A,
+                       void* dev_Ahat);
+
+/* Scratch of stbem_apply_fft: the transforms of x and y,
+ * 2 n_rhs (L/2 + 1) n_x complex doubles. */
+int stbem_apply_fft_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes);
+
+/* dev_y = A dev_x (transpose != 0: A^T x, y_n = sum_d A_d^T x_{n+d}) for
+ * n_rhs right-hand sides x[r][n][j] (FP64, n_rhs x n_t x n_x) through the
+ * frequency blocks dev_Ahat.  x is read completely before y is written, so
+ * dev_y may equal dev_x.  dev_work: 16-byte aligned, at least
+ * stbem_apply_fft_workspace_bytes.  Errors: STBEM_ERR_ARG (sizes, NULL,
+ * alignment, n_rhs outside [1, 65535]), STBEM_ERR_NOMEM (workspace too
+ * small), STBEM_ERR_CUDA. */
+int stbem_apply_fft(stbem_ctx* ctx, int transpose, int n_t, int n_x, int n_rhs,
+                    const void* dev_Ahat, const double* dev_x, double* dev_y, void* dev_work,
+                    size_t work_bytes);
+
+/* Workspace of stbem_solve_fft: that of stbem_solve plus one product's
+ * scratch. */
+int stbem_solve_fft_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes);
+
+/* stbem_solve (transpose = 0) or stbem_solve_adjoint (transpose != 0) with
+ * every product of V_h and D_h taken through their frequency blocks dev_Vhat
+ * and dev_Dhat (stbem_fft_operator; dev_Dhat may come from an FP32 D_h: the
+ * preconditioner changes the iterations, not the solution).  The GMRES, its
+ * options, the FP64 residual test and the errors are those of stbem_solve;
+ * dev_work 16-byte aligned, at least stbem_solve_fft_workspace_bytes. */
+int stbem_solve_fft(stbem_ctx* ctx, int transpose, int n_t, int n_x, const void* dev_Vhat,
+                    const void* dev_Dhat, const double* dev_L, const double* dev_f,
+                    double* dev_w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                    void* dev_work, size_t work_bytes);
+
 /* ---- Non-uniform time grids (Section 1: any decomposition of (0, T)) ------
  * With time nodes 0 = t_0 < .. < t_{n_t} = T the block of test step m and
  * trial step n <= m depends on (m, n), not on m - n alone: the matrices stay

@@ -406,6 +406,76 @@ def solve_adjoint(ctx: Context, V, b, D=None, L=None, tol: float = 1e-8, max_ite
     return out, res
 
 
+class FFTOperator:
+    """Frequency blocks Ahat_k = sum_d A_d w^{d k}, k = 0 .. L/2, of an
+    n_t x n_x x n_x lag-block operator (stbem_fft_operator): `data` is a
+    complex128 array (L/2 + 1) x n_x x n_x."""
+
+    def __init__(self, data, n_t: int, n_x: int):
+        self.data, self.n_t, self.n_x = data, n_t, n_x
+
+
+def fft_operator(ctx: Context, A, out=None) -> FFTOperator:
+    """The frequency blocks of the lag blocks A (FP64 or FP32, n_t x n_x x n_x)."""
+    n_t, n_x = A.shape[0], A.shape[1]
+    prec = capi.F64 if A.dtype == torch.float64 else capi.F32
+    nf, nb = ctypes.c_int(), ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_fft_operator_bytes(n_t, n_x, ctypes.byref(nf), ctypes.byref(nb)))
+    if out is None:
+        out = torch.empty((nf.value, n_x, n_x), dtype=torch.complex128, device=ctx.device)
+    elif out.dtype != torch.complex128 or tuple(out.shape) != (nf.value, n_x, n_x) or not out.is_contiguous():
+        raise ValueError("fft_operator: out must be a contiguous complex128 array of shape %s"
+                         % ((nf.value, n_x, n_x),))
+    ctx.check(ctx.lib.stbem_fft_operator(ctx.h, n_t, n_x, prec, _ptr(A.contiguous()), _ptr(out)))
+    return FFTOperator(out, n_t, n_x)
+
+
+def apply_fft_workspace(ctx: Context, n_t: int, n_x: int, n_rhs: int = 1):
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_apply_fft_workspace_bytes(n_t, n_x, n_rhs, ctypes.byref(nb)))
+    return torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+
+
+def apply_fft(ctx: Context, Ah: FFTOperator, x, transpose: bool = False, work=None, out=None):
+    """y = A x (or A^T x) through the frequency blocks (x: [n_rhs,] n_t x n_x, FP64)."""
+    xb = x if x.dim() == 3 else x.unsqueeze(0)
+    n_rhs = xb.shape[0]
+    if out is None:
+        out = torch.empty_like(x)
+    if work is None:
+        work = apply_fft_workspace(ctx, Ah.n_t, Ah.n_x, n_rhs)
+    ctx.check(ctx.lib.stbem_apply_fft(ctx.h, int(transpose), Ah.n_t, Ah.n_x, n_rhs, _ptr(Ah.data), _ptr(x),
+                                      _ptr(out), _ptr(work), work.numel()))
+    return out
+
+
+def solve_fft_workspace(ctx: Context, n_t: int, n_x: int, restart: int):
+    nb = ctypes.c_size_t()
+    ctx.check(ctx.lib.stbem_solve_fft_workspace_bytes(n_t, n_x, restart, ctypes.byref(nb)))
+    return torch.empty(nb.value, dtype=torch.uint8, device=ctx.device)
+
+
+def solve_fft(ctx: Context, Vh: FFTOperator, f, Dh: FFTOperator = None, L=None, tol: float = 1e-8,
+              max_iter: int = 500, restart: int = 200, transpose: bool = False, work=None, out=None,
+              raise_on_fail: bool = True):
+    """solve (or solve_adjoint with transpose) with the products of V_h and
+    D_h through their frequency blocks; returns (w, info dict)."""
+    n_t, n_x = Vh.n_t, Vh.n_x
+    opts = capi.SolveOpts(tol, max_iter, restart, _prec_mode(Dh, L))
+    info = capi.SolveInfo()
+    if out is None:
+        out = ctx.empty((n_t, n_x))
+    if work is None:
+        work = solve_fft_workspace(ctx, n_t, n_x, restart)
+    code = ctx.lib.stbem_solve_fft(ctx.h, int(transpose), n_t, n_x, _ptr(Vh.data),
+                                   _ptr(Dh.data) if Dh is not None else None, _ptr(L), _ptr(f), _ptr(out),
+                                   ctypes.byref(opts), ctypes.byref(info), _ptr(work), work.numel())
+    res = {"iterations": info.iterations, "status": info.status, "rel_residual": info.rel_residual}
+    if code != capi.STBEM_OK and raise_on_fail:
+        ctx.check(code)
+    return out, res
+
+
 def grad_workspace(ctx: Context, n_t: int, n_x: int):
     nb = ctypes.c_size_t()
     ctx.check(ctx.lib.stbem_grad_workspace_bytes(n_t, n_x, ctypes.byref(nb)))

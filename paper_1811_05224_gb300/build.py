@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libstbem.so")
-SOURCES = ["assemble.cu", "grad.cu", "initial.cu", "toeplitz.cu", "toeplitz_tc.cu", "vec.cu", "peaks.cu", "capi.cpp",
+SOURCES = ["assemble.cu", "grad.cu", "initial.cu", "toeplitz.cu", "toeplitz_fft.cu", "toeplitz_tc.cu", "vec.cu", "peaks.cu", "capi.cpp",
            "initial_capi.cpp", "ragged.cpp", "rules_host.cpp", "tune_cache.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

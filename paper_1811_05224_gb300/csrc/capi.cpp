@@ -19,6 +19,7 @@
 #include "grad.h"
 #include "initial.h"
 #include "mass_host.h"
+#include "toeplitz_fft.h"
 #include "toeplitz_tc.h"
 #include "tune_cache.h"
 #include "vec.h"
@@ -1030,6 +1031,10 @@ struct GmresOp {
   const void* const* D3 = nullptr;
   void* tcx = nullptr;
   double* tcpart = nullptr;
+  // frequency blocks (stbem_fft_operator): V and D name them; fftwork is the
+  // product's scratch (stbem::fft_apply_bytes for one right-hand side)
+  bool fft = false;
+  void* fftwork = nullptr;
 };
 
 // y = A x with A one of op's operators (full, or this rank's lag ranges then
@@ -1037,6 +1042,8 @@ struct GmresOp {
 cudaError_t op_product(const GmresOp& op, const void* A, const double* x, double* y, void* work, cudaStream_t s,
                        int* reduce_rc) {
   if (op.packed) return stbem::nu_apply_launch(op.nt, op.nx, static_cast<const double*>(A), x, y, s);
+  if (op.fft)
+    return stbem::fft_apply_launch(op.transpose, op.nt, op.nx, 1, static_cast<const double2*>(A), x, y, op.fftwork, s);
   if (op.V3) return apply_tc3(op.nt, op.nx, A == op.V ? op.V3 : op.D3, 1, x, y, op.tcx, s, op.tcpart);
   if (op.n_ranges < 0) return stbem::apply_launch(op.prec, op.transpose, op.nt, op.nx, A, 1, x, y, work, s);
   const size_t N = (size_t)op.nt * op.nx;
@@ -1249,6 +1256,111 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int nt, int nx, int vprec, const void* V
                         const double* b, double* lam, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* work, size_t work_bytes) {
   return solve_impl(ctx, true, nt, nx, vprec, V, D, L, b, lam, opts, info, work, work_bytes);
+}
+
+// ------------------------------------------ products through time FFTs ------
+
+namespace {
+size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+int fft_sizes_ok(stbem_ctx* ctx, int nt, int nx, const char* where) {
+  if (nt < 1 || nx < 1 || nt > stbem::kFftMaxSteps || nx > stbem::kFftMaxSpace)
+    return fail(ctx, STBEM_ERR_ARG, "%s: sizes n_t = %d, n_x = %d outside [1, %d] x [1, %d]", where, nt, nx,
+                stbem::kFftMaxSteps, stbem::kFftMaxSpace);
+  return STBEM_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+size_t solve_fft_bytes(int nt, int nx, int restart) {
+  return align16(solve_bytes(nt, nx, restart)) + stbem::fft_apply_bytes(nt, nx, 1);
+}
+}  // namespace
+
+int stbem_fft_operator_bytes(int n_t, int n_x, int* n_freq, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_t > stbem::kFftMaxSteps || n_x > stbem::kFftMaxSpace) return STBEM_ERR_ARG;
+  if (n_freq) *n_freq = stbem::fft_freqs(n_t);
+  *bytes = stbem::fft_operator_bytes(n_t, n_x);
+  return STBEM_OK;
+}
+
+int stbem_fft_operator(stbem_ctx* ctx, int n_t, int n_x, int prec, const void* A, void* Ahat) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (const int rc = fft_sizes_ok(ctx, n_t, n_x, "fft_operator")) return rc;
+  if (!A || !Ahat) return fail(ctx, STBEM_ERR_ARG, "fft_operator: NULL pointer");
+  if (prec != STBEM_F64 && prec != STBEM_F32) return fail(ctx, STBEM_ERR_ARG, "fft_operator: bad precision %d", prec);
+  if (!aligned16(Ahat)) return fail(ctx, STBEM_ERR_ARG, "fft_operator: frequency blocks not 16-byte aligned");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "fft_operator: set device");
+  CUDA_TRY(ctx, stbem::fft_operator_launch(prec, n_t, n_x, A, static_cast<double2*>(Ahat), ctx->stream),
+           "fft_operator");
+  return STBEM_OK;
+}
+
+int stbem_apply_fft_workspace_bytes(int n_t, int n_x, int n_rhs, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || n_t > stbem::kFftMaxSteps || n_x > stbem::kFftMaxSpace)
+    return STBEM_ERR_ARG;
+  *bytes = stbem::fft_apply_bytes(n_t, n_x, n_rhs);
+  return STBEM_OK;
+}
+
+int stbem_apply_fft(stbem_ctx* ctx, int transpose, int n_t, int n_x, int n_rhs, const void* Ahat, const double* x,
+                    double* y, void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (const int rc = fft_sizes_ok(ctx, n_t, n_x, "apply_fft")) return rc;
+  if (n_rhs < 1 || n_rhs > 65535) return fail(ctx, STBEM_ERR_ARG, "apply_fft: n_rhs = %d outside [1, 65535]", n_rhs);
+  if (!Ahat || !x || !y || !work) return fail(ctx, STBEM_ERR_ARG, "apply_fft: NULL pointer");
+  if (!aligned16(Ahat) || !aligned16(work))
+    return fail(ctx, STBEM_ERR_ARG, "apply_fft: frequency blocks or workspace not 16-byte aligned");
+  const size_t need = stbem::fft_apply_bytes(n_t, n_x, n_rhs);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "apply_fft: workspace %zu < %zu bytes", work_bytes, need);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "apply_fft: set device");
+  CUDA_TRY(ctx, stbem::fft_apply_launch(transpose != 0, n_t, n_x, n_rhs, static_cast<const double2*>(Ahat), x, y,
+                                        work, ctx->stream),
+           "apply_fft");
+  return STBEM_OK;
+}
+
+int stbem_solve_fft_workspace_bytes(int n_t, int n_x, int restart, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || restart < 1 || n_t > stbem::kFftMaxSteps || n_x > stbem::kFftMaxSpace)
+    return STBEM_ERR_ARG;
+  *bytes = solve_fft_bytes(n_t, n_x, restart);
+  return STBEM_OK;
+}
+
+int stbem_solve_fft(stbem_ctx* ctx, int transpose, int nt, int nx, const void* Vhat, const void* Dhat,
+                    const double* L, const double* f, double* w, const stbem_solve_opts* opts, stbem_solve_info* info,
+                    void* work, size_t work_bytes) {
+  if (!ctx) return STBEM_ERR_ARG;
+  if (const int rc = fft_sizes_ok(ctx, nt, nx, "solve_fft")) return rc;
+  if (!Vhat || !f || !w || !opts || !info || !work) return fail(ctx, STBEM_ERR_ARG, "solve_fft: NULL pointer");
+  const int restart = opts->restart, maxit = opts->max_iter;
+  if (restart < 1 || maxit < 1 || !(opts->tol > 0)) return fail(ctx, STBEM_ERR_ARG, "solve_fft: bad options");
+  const bool prec = opts->precondition != 0;
+  if (prec && (!Dhat || !L)) return fail(ctx, STBEM_ERR_ARG, "solve_fft: preconditioner needs D and L");
+  if (!aligned16(Vhat) || (prec && !aligned16(Dhat)) || !aligned16(work))
+    return fail(ctx, STBEM_ERR_ARG, "solve_fft: frequency blocks or workspace not 16-byte aligned");
+  const size_t need = solve_fft_bytes(nt, nx, restart);
+  if (work_bytes < need) return fail(ctx, STBEM_ERR_NOMEM, "solve_fft: workspace %zu < %zu bytes", work_bytes, need);
+  SolveWork W;
+  carve(work, work_bytes, nt, nx, restart, &W);
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device), "solve_fft: set device");
+  GmresOp op{nt, nx, STBEM_F64, Vhat, prec ? Dhat : nullptr, L};
+  op.transpose = transpose != 0;
+  op.mass = opts->precondition == 2 ? 2 : 1;
+  op.fft = true;
+  op.fftwork = static_cast<char*>(work) + align16(solve_bytes(nt, nx, restart));
+  int iters = 0;
+  double relres = 0.0;
+  const int status = gmres_core(ctx, op, f, w, opts->tol, maxit, restart, W, &iters, &relres);
+  info->iterations = iters;
+  info->rel_residual = relres;
+  info->status = status;
+  if (status == STBEM_ERR_NAN || status == STBEM_ERR_NOCONV || status == STBEM_ERR_BREAKDOWN)
+    return fail(ctx, status, "solve_fft: %s after %d iterations (relres %.3e)",
+                status == STBEM_ERR_NAN ? "NaN"
+                : status == STBEM_ERR_NOCONV ? "no convergence" : "breakdown (singular operator)",
+                iters, relres);
+  return status;
 }
 
 // ------------------------------------------------- non-uniform time grids ------
