@@ -674,9 +674,10 @@ def rhs_batched(ctx: Context, mesh: Mesh, K, y_stars):
     """(G, F) for many sources: G[k] vertex time averages of U*(x - y_k, t),
     F = 1/2 M_h G + K_h G.  K is the FP64 operator (an FP64 CUDA-core product
     of all right-hand sides: F to FP64 accuracy), its ExactOperand (the
-    exact-slice tensor-core product, normwise a few 1e-13 at 7 slices) or a
-    tuple of its three BF16 slices (the compensated tensor-core product, a few
-    1e-7 of |K||G|)."""
+    exact-slice tensor-core product, normwise a few 1e-13 at 7 slices), its
+    FFTOperator (the product through time FFTs, FP64, normwise) or a tuple of
+    its three BF16 slices (the compensated tensor-core product, a few 1e-7 of
+    |K||G|)."""
     ys = np.ascontiguousarray(np.asarray(y_stars, dtype=np.float64).reshape(-1))
     B = ys.size // 2
     G = ctx.empty((B, mesh.n_t, mesh.n_x))
@@ -684,6 +685,8 @@ def rhs_batched(ctx: Context, mesh: Mesh, K, y_stars):
                                           _ptr(G)))
     if isinstance(K, ExactOperand):
         F = apply_exact(ctx, K, G)
+    elif isinstance(K, FFTOperator):
+        F = apply_fft(ctx, K, G)
     elif isinstance(K, (tuple, list)):
         F = apply_tc3(ctx, K, G)
     else:

@@ -33,18 +33,24 @@ __device__ __forceinline__ void twiddles(double2* tw, int L, double sign) {
   }
 }
 
-// In-place radix-2 butterflies of Q bit-reversed sequences z[q][0..L)
-__device__ __forceinline__ void fft_stages(double2* z, const double2* tw, int Q, int L, int logL) {
+// In-place radix-2 butterflies of Q bit-reversed sequences z[q][0..L), from
+// stage s0 on (stage s combines pairs 2^s apart).  The twiddles of stage 1
+// are 1 and w^{L/4} = -i (sign -1) or +i (sign +1): no multiplication.
+__device__ __forceinline__ void fft_stages(double2* z, const double2* tw, int Q, int L, int logL, int s0,
+                                           double sign) {
   const int H = L / 2;
-  for (int s = 0; s < logL; ++s) {
+  for (int s = s0; s < logL; ++s) {
     const int half = 1 << s;
     for (int idx = threadIdx.x; idx < Q * H; idx += blockDim.x) {
       const int q = idx / H, b = idx - q * H;
       const int pos = b & (half - 1);
       const int i0 = ((b >> s) << (s + 1)) + pos;
       double2* zq = z + (size_t)q * L;
-      const double2 u = zq[i0];
-      const double2 t = cmul(tw[pos << (logL - 1 - s)], zq[i0 + half]);
+      const double2 u = zq[i0], v = zq[i0 + half];
+      double2 t;
+      if (s == 0 || (s == 1 && pos == 0)) t = v;
+      else if (s == 1) t = sign < 0 ? make_double2(v.y, -v.x) : make_double2(-v.y, v.x);
+      else t = cmul(tw[pos << (logL - 1 - s)], v);
       zq[i0] = make_double2(u.x + t.x, u.y + t.y);
       zq[i0 + half] = make_double2(u.x - t.x, u.y - t.y);
     }
@@ -69,27 +75,33 @@ __global__ void __launch_bounds__(kFftThreads) k_rfft_cols(const T* __restrict__
   const long long c0 = (long long)blockIdx.x * 2 * Q;
   twiddles(tw, L, -1.0);
   const int G = 2 * Q;
-  // eight loads in flight per thread before their shared-memory stores
+  // The second half of every sequence is zero padding (n_t <= L/2), so the
+  // first stage maps the pair (x_d, x_{d + L/2} = 0), d < L/2, at bit-reversed
+  // positions p, p + 1 to (x_d, x_d): it is done here, on load.  Eight loads
+  // in flight per thread before their shared-memory stores.
   constexpr int U = 8;
-  for (int base = 0; base < L * G; base += U * kFftThreads) {
+  const int HG = (L / 2) * G;
+  for (int base = 0; base < HG; base += U * kFftThreads) {
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int idx = base + u * kFftThreads + threadIdx.x;
       const int d = idx / G, cc = idx - d * G;
       const long long c = c0 + cc;
-      v[u] = (idx < L * G && d < nt && c < ncols) ? (double)in[(long long)d * ld + c] : 0.0;
+      v[u] = (idx < HG && d < nt && c < ncols) ? (double)in[(long long)d * ld + c] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int idx = base + u * kFftThreads + threadIdx.x;
-      if (idx >= L * G) break;
+      if (idx >= HG) break;
       const int d = idx / G, cc = idx - d * G;
-      reinterpret_cast<double*>(z + (size_t)(cc >> 1) * L + bitrev(d, logL))[cc & 1] = v[u];
+      double* p = reinterpret_cast<double*>(z + (size_t)(cc >> 1) * L + bitrev(d, logL));
+      p[cc & 1] = v[u];
+      p[2 + (cc & 1)] = v[u];
     }
   }
   __syncthreads();
-  fft_stages(z, tw, Q, L, logL);
+  fft_stages(z, tw, Q, L, logL, 1, -1.0);
   const int K = L / 2 + 1;
   for (int idx = threadIdx.x; idx < K * G; idx += blockDim.x) {
     const int k = idx / G, cc = idx - k * G;
@@ -131,7 +143,7 @@ __global__ void __launch_bounds__(kFftThreads) k_irfft_cols(const double2* __res
     if (k > 0 && k < H) zq[bitrev(L - k, logL)] = make_double2(ya.x + yb.y, yb.x - ya.y);
   }
   __syncthreads();
-  fft_stages(z, tw, Q, L, logL);
+  fft_stages(z, tw, Q, L, logL, 0, 1.0);
   const int G = 2 * Q;
   const double inv = 1.0 / (double)L;
   for (int idx = threadIdx.x; idx < nt * G; idx += blockDim.x) {

@@ -155,6 +155,14 @@ def test_solve_fft_matches_oracle(ctx):
     fo = f.cpu().numpy()
     w_ref = OS.forward_substitution(Vo, fo)
     Vh, Dh, Dh32 = P.fft_operator(ctx, V), P.fft_operator(ctx, D), P.fft_operator(ctx, D32)
+    # the right-hand side with K g through the frequency blocks of K
+    Gb, Fb = P.rhs_batched(ctx, m, P.fft_operator(ctx, K), [p.y_star])
+    assert torch.equal(Gb[0], g)          # the same datum kernel
+    Ko = OA.assemble("K", om)
+    gn = g.cpu().numpy()
+    Kg_ref = OS.toeplitz_apply(Ko, gn)
+    Kg = Fb[0].cpu().numpy() - (f.cpu().numpy() - P.apply(ctx, K, g).cpu().numpy())
+    check_product(Kg, Kg_ref, Ko, gn, False, p.n_t, p.n_x)
     for Dx, Lx in ((Dh, L), (Dh, Mi), (Dh32, L), (None, None)):
         w, info = P.solve_fft(ctx, Vh, f, Dx, Lx, tol=1e-10)
         assert info["status"] == 0 and info["rel_residual"] <= 1e-10
