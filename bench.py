@@ -423,6 +423,25 @@ def run_grad(ctx, dev, stream):
     P.grad(ctx, mesh, K, ys, g, w, lam, work=gwork)
     k1.record(stream)
     torch.cuda.synchronize(dev)
+    # the forward and adjoint solves with the products through time FFTs
+    fwork = P.api.solve_fft_workspace(ctx, nt, mesh.n_x, 100)
+    q = [ev() for _ in range(5)]
+    q[0].record(stream)
+    Vh, Dh = P.fft_operator(ctx, V), P.fft_operator(ctx, D)
+    q[1].record(stream)
+    w_f, finfo_f = P.solve_fft(ctx, Vh, f_fwd, Dh, L, tol=1e-12, restart=100, max_iter=2000, work=fwork)
+    q[2].record(stream)
+    q[3].record(stream)
+    lam_f, ainfo_f = P.solve_fft(ctx, Vh, rhs_adj, Dh, L, tol=1e-12, restart=100, max_iter=2000, transpose=True,
+                                 work=fwork)
+    q[4].record(stream)
+    torch.cuda.synchronize(dev)
+    fft_out = {"transforms_ms": q[0].elapsed_time(q[1]),
+               "forward_solve_ms": q[1].elapsed_time(q[2]), "forward_iterations": finfo_f["iterations"],
+               "adjoint_solve_ms": q[3].elapsed_time(q[4]), "adjoint_iterations": ainfo_f["iterations"],
+               "w_rel_diff": float((w_f - w).norm() / w.norm()),
+               "lambda_rel_diff": float((lam_f - lam).norm() / lam.norm())}
+    del Vh, Dh, w_f, lam_f, fwork
     gC = S.T @ dxy.cpu().numpy()
     ga = float(dal)
     v, va, h = rng.standard_normal(C0.shape), float(rng.standard_normal()), 1e-6
@@ -441,6 +460,7 @@ def run_grad(ctx, dev, stream):
         "backward_ms": e[2].elapsed_time(e[3]) + e[4].elapsed_time(e[5]),
         "fd_check": {"directional_derivative": an, "central_difference": fd,
                      "rel_diff": abs(fd - an) / abs(an), "h": h},
+        "fft_products": fft_out,
     }
     del V, K, D, g, w, lam, gwork, awork
     torch.cuda.empty_cache()

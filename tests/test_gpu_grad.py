@@ -90,9 +90,11 @@ def test_adjoint_solve_matches_backward_substitution(ctx):
     assert float(np.abs(lam2.cpu().numpy() - ref).max() / np.abs(ref).max()) < 1e-10
 
 
-def test_autograd_loss_gradient_matches_oracle(ctx):
+@pytest.mark.parametrize("products", ["direct", "fft"])
+def test_autograd_loss_gradient_matches_oracle(ctx, products):
     """dL/d(vertices, alpha) of L = ||w_h - w_target||^2 through
-    neumann_solve's backward against the oracle's adjoint gradient."""
+    neumann_solve's backward against the oracle's adjoint gradient, with the
+    GMRES products as block sums and through time FFTs."""
     import paper_1811_05224_gb300 as P
     X = W.star(8, 2, seed=5)
     T, nt, al, ys = 1.0, 6, 0.9, (1.5, 1.5)
@@ -101,7 +103,7 @@ def test_autograd_loss_gradient_matches_oracle(ctx):
     Lref, gref, aref = OG.loss_grad(X, T, nt, al, ys, wt)
     Xt = torch.tensor(X, dtype=torch.float64, requires_grad=True)
     at = torch.tensor(al, dtype=torch.float64, requires_grad=True)
-    w = P.neumann_solve(ctx, Xt, at, ys, T, nt, tol=1e-13)
+    w = P.neumann_solve(ctx, Xt, at, ys, T, nt, tol=1e-13, products=products)
     loss = ((w - torch.as_tensor(wt).cuda()) ** 2).sum()
     loss.backward()
     assert float(loss.detach()) == pytest.approx(Lref, rel=1e-9)
@@ -110,7 +112,8 @@ def test_autograd_loss_gradient_matches_oracle(ctx):
     assert abs(float(at.grad) - aref) <= 1e-8 * max(abs(aref), scale)
 
 
-def test_star256_gradient_against_central_differences(ctx):
+@pytest.mark.parametrize("products", ["direct", "fft"])
+def test_star256_gradient_against_central_differences(ctx, products):
     """The differentiation workload: 16-vertex star (seeded radii), N_x = 256,
     N_t = 256, alpha = 1; w_target from seeded perturbed corners; gradient with
     respect to the 32 corner coordinates and alpha against FP64 central
@@ -125,7 +128,7 @@ def test_star256_gradient_against_central_differences(ctx):
         wt = P.neumann_solve(ctx, S @ Ct, torch.tensor(1.0, dtype=torch.float64), ys, T, nt, tol=1e-13)
 
     def loss_of(C, a):
-        w = P.neumann_solve(ctx, S @ C, a, ys, T, nt, tol=1e-13)
+        w = P.neumann_solve(ctx, S @ C, a, ys, T, nt, tol=1e-13, products=products)
         return ((w - wt) ** 2).sum()
 
     C = torch.tensor(C0, requires_grad=True)
