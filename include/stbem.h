@@ -651,6 +651,21 @@ int stbem_solve_batched_exact(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const
                               double* dev_W, const stbem_solve_opts* opts, double inner_tol,
                               stbem_solve_info* infos, void* dev_work, size_t work_bytes);
 
+/* stbem_solve_batched with the frequency blocks dev_Vhat of the FP64 V
+ * (stbem_fft_operator) in place of dev_V64: once every relative residual is
+ * below 2e-6, refinement continues on F - V W from the product through time
+ * FFTs of all right-hand sides (FP64, normwise; see stbem_apply_fft).
+ * Workspace: stbem_solve_batched_fft_workspace_bytes() (the base workspace
+ * plus the transforms of W and of V W), 256-byte aligned; dev_Vhat 16-byte
+ * aligned.  Requires, besides the sizes of stbem_solve_batched, the limits
+ * of stbem_apply_fft.  Errors as stbem_solve_batched. */
+int stbem_solve_batched_fft_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, size_t* bytes);
+int stbem_solve_batched_fft(stbem_ctx* ctx, int n_t, int n_x, int n_rhs, const void* dev_V_hi,
+                            const void* dev_V_mid, const void* dev_V_lo, const void* dev_D_bf16,
+                            const double* dev_L, const void* dev_Vhat, const double* dev_F,
+                            double* dev_W, const stbem_solve_opts* opts, double inner_tol,
+                            stbem_solve_info* infos, void* dev_work, size_t work_bytes);
+
 /* stbem_solve_mixed with the exact-slice operator V_exact (stbem_exact_slices
  * of the FP64 V) in place of dev_V64: every outer residual f - V w is the
  * exact-slice tensor-core product (normwise a few 1e-13 at n_slices = 7; see

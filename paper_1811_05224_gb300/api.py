@@ -700,18 +700,22 @@ def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1
                   V64=None):
     """Many-right-hand-side solve on the tensor cores; returns (W, infos).
     With V64 the refinement finishes on residuals of that operator: the FP64
-    lag blocks (an FP64 CUDA-core product) or their ExactOperand (the
-    exact-slice tensor-core product); either gives FP64-solve accuracy for tol
-    down to 1e-8 and below."""
+    lag blocks (an FP64 CUDA-core product), their ExactOperand (the
+    exact-slice tensor-core product) or their FFTOperator (the FP64 product
+    through time FFTs); each gives FP64-solve accuracy for tol down to 1e-8
+    and below."""
     B, n_t, n_x = F.shape
     opts = capi.SolveOpts(tol, max_iter, restart, int(D_bf16 is not None))
     infos = (capi.SolveInfo * B)()
     if out is None:
         out = torch.empty_like(F)
     exact = isinstance(V64, ExactOperand)
+    fft = isinstance(V64, FFTOperator)
     if work is None:
         nb = ctypes.c_size_t()
-        if exact:
+        if fft:
+            ctx.check(ctx.lib.stbem_solve_batched_fft_workspace_bytes(n_t, n_x, B, restart, ctypes.byref(nb)))
+        elif exact:
             ctx.check(ctx.lib.stbem_solve_batched_exact_workspace_bytes(n_t, n_x, B, restart, V64.n_slices,
                                                                         ctypes.byref(nb)))
         else:
@@ -719,7 +723,11 @@ def solve_batched(ctx: Context, V_slices, F, D_bf16=None, L=None, tol: float = 1
                                                                   ctypes.byref(nb)))
         work = torch.empty(nb.value, dtype=torch.uint8, device=F.device)
     Vs = list(V_slices) + [None] * (3 - len(V_slices))
-    if exact:
+    if fft:
+        code = ctx.lib.stbem_solve_batched_fft(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]),
+                                               _ptr(D_bf16), _ptr(L), _ptr(V64.data), _ptr(F), _ptr(out),
+                                               ctypes.byref(opts), float(inner_tol), infos, _ptr(work), work.numel())
+    elif exact:
         sv = V64.c_struct()
         code = ctx.lib.stbem_solve_batched_exact(ctx.h, n_t, n_x, B, _ptr(Vs[0]), _ptr(Vs[1]), _ptr(Vs[2]),
                                                  _ptr(D_bf16), _ptr(L), ctypes.byref(sv), _ptr(F), _ptr(out),

@@ -28,7 +28,7 @@ ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOMEM", -4: "ERR_N
 
 EXPORTS = [
     "stbem_version", "stbem_launch_count", "stbem_create", "stbem_destroy", "stbem_last_error", "stbem_mesh_create",
-    "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_assemble_ops", "stbem_assemble_lags", "stbem_fft_operator_bytes", "stbem_fft_operator", "stbem_apply_fft_workspace_bytes", "stbem_apply_fft", "stbem_solve_fft_workspace_bytes", "stbem_solve_fft", "stbem_apply_workspace_bytes",
+    "stbem_mesh_destroy", "stbem_op_bytes", "stbem_assemble", "stbem_assemble_ops", "stbem_assemble_lags", "stbem_fft_operator_bytes", "stbem_fft_operator", "stbem_apply_fft_workspace_bytes", "stbem_apply_fft", "stbem_solve_fft_workspace_bytes", "stbem_solve_fft", "stbem_solve_batched_fft_workspace_bytes", "stbem_solve_batched_fft", "stbem_apply_workspace_bytes",
     "stbem_apply", "stbem_apply_noalloc", "stbem_rhs", "stbem_lumped_mass", "stbem_solve_workspace_bytes", "stbem_solve",
     "stbem_solve_mixed_workspace_bytes", "stbem_solve_mixed", "stbem_round_f32",
     "stbem_to_bf16", "stbem_apply_tc", "stbem_apply_tc_comp", "stbem_debug_tc_stall", "stbem_pipe_peaks", "stbem_bf16_split3", "stbem_apply_tc3_workspace_bytes",
@@ -123,6 +123,9 @@ def load(path: str = LIB_PATH):
     L.stbem_apply_fft.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, sz]
     L.stbem_solve_fft_workspace_bytes.argtypes = [i, i, i, P(sz)]
     L.stbem_solve_fft.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo), vp, sz]
+    L.stbem_solve_batched_fft_workspace_bytes.argtypes = [i, i, i, i, P(sz)]
+    L.stbem_solve_batched_fft.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, P(SolveOpts), d,
+                                          P(SolveInfo), vp, sz]
     L.stbem_grad_workspace_bytes.argtypes = [i, i, P(sz)]
     L.stbem_mixed_mass_inverse.argtypes = [vp, vp, vp]
     L.stbem_grad.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp, sz]

@@ -674,11 +674,13 @@ size_t batch_base_bytes(int nt, int nx, int B, int m) {
   return ((size_t)(m + 1) * n + 4 * n + (size_t)(m + 4) * B) * sizeof(double) + 3 * n * 2 + 256;
 }
 // with an FP64 residual operator: + the FP64 product's lag-chunk partial sums;
-// with an exact-slice one (exact_slices > 0): + the slices of W
-size_t batch_bytes(int nt, int nx, int B, int m, bool fp64_residual, int exact_slices = 0) {
+// with an exact-slice one (exact_slices > 0): + the slices of W; with
+// frequency blocks (fft): + the transforms of W and of the product
+size_t batch_bytes(int nt, int nx, int B, int m, bool fp64_residual, int exact_slices = 0, bool fft = false) {
   size_t b = batch_base_bytes(nt, nx, B, m);
   if (fp64_residual) b = ((b + 255) & ~(size_t)255) + stbem::apply_workspace_bytes(nt, nx, B);
   else if (exact_slices > 0) b = ((b + 255) & ~(size_t)255) + exact_x_bytes(nt, nx, B, exact_slices);
+  else if (fft) b = ((b + 255) & ~(size_t)255) + stbem::fft_apply_bytes(nt, nx, B);
   return b;
 }
 
@@ -703,12 +705,21 @@ int stbem_solve_batched_exact_workspace_bytes(int n_t, int n_x, int n_rhs, int r
   return STBEM_OK;
 }
 
+int stbem_solve_batched_fft_workspace_bytes(int n_t, int n_x, int n_rhs, int restart, size_t* bytes) {
+  if (!bytes || n_t < 1 || n_x < 1 || n_rhs < 1 || restart < 1 || n_t > stbem::kFftMaxSteps ||
+      n_x > stbem::kFftMaxSpace)
+    return STBEM_ERR_ARG;
+  *bytes = batch_bytes(n_t, n_x, n_rhs, restart, false, 0, true);
+  return STBEM_OK;
+}
+
 namespace {
 // The batched solve; the refinement's final residual phase uses the FP64
-// operator V64, the exact-slice operator Vx, or neither.
+// operator V64, the exact-slice operator Vx, the frequency blocks Vf, or
+// none of them.
 int solve_batched_impl(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid, const void* V_lo,
                        const void* D_bf16, const double* Lm, const double* V64, const stbem_exact_operand* Vx,
-                       const double* F, double* W, const stbem_solve_opts* opts, double inner_tol,
+                       const void* Vf, const double* F, double* W, const stbem_solve_opts* opts, double inner_tol,
                        stbem_solve_info* infos, void* work, size_t work_bytes) {
   if (!ctx) return STBEM_ERR_ARG;
   if (!V_hi || !F || !W || !opts || !infos || !work) return fail(ctx, STBEM_ERR_ARG, "solve_batched: NULL pointer");
@@ -729,7 +740,13 @@ int solve_batched_impl(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, 
     if (reinterpret_cast<uintptr_t>(work) & 255)
       return fail(ctx, STBEM_ERR_ARG, "solve_batched_exact: workspace not 256-byte aligned");
   }
-  if (work_bytes < batch_bytes(nt, nx, B, m, V64 != nullptr, Vx ? Vx->n_slices : 0))
+  if (Vf) {
+    if (nt > stbem::kFftMaxSteps || nx > stbem::kFftMaxSpace || B > 65535)
+      return fail(ctx, STBEM_ERR_ARG, "solve_batched_fft: sizes beyond the FFT product's limits");
+    if ((reinterpret_cast<uintptr_t>(Vf) & 15) || (reinterpret_cast<uintptr_t>(work) & 255))
+      return fail(ctx, STBEM_ERR_ARG, "solve_batched_fft: frequency blocks or workspace misaligned");
+  }
+  if (work_bytes < batch_bytes(nt, nx, B, m, V64 != nullptr, Vx ? Vx->n_slices : 0, Vf != nullptr))
     return fail(ctx, STBEM_ERR_NOMEM, "solve_batched: workspace too small");
   const size_t N = (size_t)nt * nx, n = (size_t)B * N;
   BatchWork Wk;
@@ -781,11 +798,13 @@ int solve_batched_impl(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, 
   // first, then (with V64 or Vx) the FP64 or exact-slice product once that
   // one reaches its floor
   bool fp64_phase = false;
-  const bool final_phase = V64 || Vx;
+  const bool final_phase = V64 || Vx || Vf;
   const double tol_tc = final_phase ? std::max(opts->tol, kTc3ResidualFloor) : opts->tol;
   auto residual = [&]() -> cudaError_t {
     cudaError_t e = !fp64_phase ? apply_tc3(nt, nx, Vs, B, W, Wk.U, Wk.xb, s)
                     : Vx        ? apply_exact(nt, nx, *Vx, B, W, Wk.U, part64, s)
+                    : Vf        ? stbem::fft_apply_launch(false, nt, nx, B, static_cast<const double2*>(Vf), W, Wk.U,
+                                                          part64, s)
                                 : stbem::apply_launch(STBEM_F64, false, nt, nx, V64, B, W, Wk.U, part64, s);
     if (e == cudaSuccess) e = stbem::sub_launch(F, Wk.U, Wk.R, n, s);
     return e;
@@ -930,8 +949,17 @@ int stbem_solve_batched(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi,
                         const void* V_lo, const void* D_bf16, const double* Lm, const double* V64, const double* F,
                         double* W, const stbem_solve_opts* opts, double inner_tol, stbem_solve_info* infos,
                         void* work, size_t work_bytes) {
-  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, V64, nullptr, F, W, opts, inner_tol,
-                            infos, work, work_bytes);
+  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, V64, nullptr, nullptr, F, W, opts,
+                            inner_tol, infos, work, work_bytes);
+}
+
+int stbem_solve_batched_fft(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
+                            const void* V_lo, const void* D_bf16, const double* Lm, const void* Vhat,
+                            const double* F, double* W, const stbem_solve_opts* opts, double inner_tol,
+                            stbem_solve_info* infos, void* work, size_t work_bytes) {
+  if (ctx && !Vhat) return fail(ctx, STBEM_ERR_ARG, "solve_batched_fft: NULL frequency blocks");
+  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, nullptr, nullptr, Vhat, F, W, opts,
+                            inner_tol, infos, work, work_bytes);
 }
 
 int stbem_solve_batched_exact(stbem_ctx* ctx, int nt, int nx, int B, const void* V_hi, const void* V_mid,
@@ -939,8 +967,8 @@ int stbem_solve_batched_exact(stbem_ctx* ctx, int nt, int nx, int B, const void*
                               const double* F, double* W, const stbem_solve_opts* opts, double inner_tol,
                               stbem_solve_info* infos, void* work, size_t work_bytes) {
   if (ctx && !Vx) return fail(ctx, STBEM_ERR_ARG, "solve_batched_exact: NULL operand");
-  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, nullptr, Vx, F, W, opts, inner_tol,
-                            infos, work, work_bytes);
+  return solve_batched_impl(ctx, nt, nx, B, V_hi, V_mid, V_lo, D_bf16, Lm, nullptr, Vx, nullptr, F, W, opts,
+                            inner_tol, infos, work, work_bytes);
 }
 
 int stbem_rhs(stbem_ctx* ctx, const stbem_mesh* m, const double* K, double ysx, double ysy, double* g,

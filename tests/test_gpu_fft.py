@@ -208,3 +208,33 @@ def test_fft_errors(ctx):
     y = P.apply_fft(ctx, Ah, x)
     ref = OS.toeplitz_apply(A.cpu().numpy(), x.cpu().numpy())
     check_product(y.cpu().numpy(), ref, A.cpu().numpy(), x.cpu().numpy(), False, 6, 5)
+
+
+def test_batched_solve_fft_residual_against_oracle(ctx):
+    """The batched solve whose refinement finishes on residuals through the
+    frequency blocks of V (stbem_solve_batched_fft), with F from the
+    frequency blocks of K: the FP64 residual with the oracle's V below 1e-8,
+    w within 1e-7 of the oracle's forward substitution, F within 1e-12 of the
+    oracle's (1/2 M_h + K_h) g."""
+    import paper_1811_05224_gb300 as P
+    from oracle import rhs as OR
+    X = W.l_shape(48, seed=3)
+    nt = 40
+    m = P.Mesh(ctx, X, 1.0, nt, 1.0)
+    om = BoundaryMesh(X, 1.0, nt, 1.0)
+    V, K, D = (P.assemble(ctx, m, o) for o in "VKD")
+    L = P.lumped_mass(ctx, m)
+    ys = W.annulus_sources(4, seed=4)
+    G, F = P.rhs_batched(ctx, m, P.fft_operator(ctx, K), ys)
+    Wb, infos = P.solve_batched(ctx, P.bf16_split3(ctx, V), F, P.to_bf16(ctx, D), L, tol=1e-8,
+                                V64=P.fft_operator(ctx, V))
+    assert all(i["status"] == 0 and i["rel_residual"] <= 1e-8 for i in infos), infos
+    Vo, Ko = OA.assemble("V", om), OA.assemble("K", om)
+    for b in range(len(ys)):
+        f_ref = OR.f_vec(om, Ko, OR.g_vec(om, ys[b]))
+        Fb, Wn = F[b].cpu().numpy(), Wb[b].cpu().numpy()
+        assert np.linalg.norm(Fb - f_ref) <= 1e-12 * np.linalg.norm(f_ref)
+        r = Fb - OS.toeplitz_apply(Vo, Wn)
+        assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(Fb)
+        w_ref = OS.forward_substitution(Vo, Fb)
+        assert np.linalg.norm(Wn - w_ref) <= 1e-7 * np.linalg.norm(w_ref)
