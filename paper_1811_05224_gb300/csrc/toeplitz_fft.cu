@@ -155,8 +155,21 @@ __global__ void __launch_bounds__(kFftThreads) k_irfft_cols(const double2* __res
   }
 }
 
-constexpr int kMvRowsPerWarp = 4;
-constexpr int kMvRows = (kFftThreads / 32) * kMvRowsPerWarp;
+// Forward frequency products: a group of 8 lanes per row, each lane a
+// stride-8 eighth of the row (16-byte loads, 128 contiguous bytes per row and
+// step), two rows per group, four steps of both rows in flight; the group's
+// sums are combined in 3 shuffle steps, so the reduction's FP64 adds stay a
+// few percent of the multiply-adds (a warp per row spends 5 steps, a quarter
+// of the work at N_x = 256).
+constexpr int kMvGroup = 8;
+constexpr int kMvGroups = kFftThreads / kMvGroup;
+constexpr int kMvRowsPerGroup = 2;
+constexpr int kMvRows = kMvGroups * kMvRowsPerGroup;
+
+__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 x) {
+  acc.x = fma(a.x, x.x, fma(-a.y, x.y, acc.x));
+  acc.y = fma(a.x, x.y, fma(a.y, x.x, acc.y));
+}
 
 // Yh[r][k][i] = sum_j Ahat[k][i][j] Xh[r][k][j]; grid (row blocks, K, n_rhs)
 __global__ void __launch_bounds__(kFftThreads) k_fft_matvec(const double2* __restrict__ Ahat, int nx, int K,
@@ -166,56 +179,51 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_matvec(const double2* __res
   const double2* xk = Xh + ((long long)r * K + k) * nx;
   for (int j = threadIdx.x; j < nx; j += blockDim.x) xs[j] = xk[j];
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * kMvRows + warp;
+  const int g = threadIdx.x / kMvGroup, l = threadIdx.x % kMvGroup;
+  const int i0 = blockIdx.x * kMvRows + g;
   const double2* Ak = Ahat + (long long)k * nx * nx;
-  double2 acc[kMvRowsPerWarp];
-  const double2* row[kMvRowsPerWarp];
+  double2 acc[kMvRowsPerGroup];
+  const double2* row[kMvRowsPerGroup];
 #pragma unroll
-  for (int t = 0; t < kMvRowsPerWarp; ++t) {
+  for (int t = 0; t < kMvRowsPerGroup; ++t) {
     acc[t] = make_double2(0.0, 0.0);
-    const int i = i0 + t * (kFftThreads / 32);
+    const int i = i0 + t * kMvGroups;
     row[t] = i < nx ? Ak + (long long)i * nx : nullptr;
   }
-  int j = lane;
-  for (; j + 32 < nx; j += 64) {
-    double2 a0[kMvRowsPerWarp], a1[kMvRowsPerWarp];
+  constexpr int S = 4;     // steps of 8 columns in flight
+  int j = l;
+  for (; j + (S - 1) * kMvGroup < nx; j += S * kMvGroup) {
+    double2 a[kMvRowsPerGroup][S];
 #pragma unroll
-    for (int t = 0; t < kMvRowsPerWarp; ++t) {
-      a0[t] = row[t] ? __ldg(row[t] + j) : make_double2(0.0, 0.0);
-      a1[t] = row[t] ? __ldg(row[t] + j + 32) : make_double2(0.0, 0.0);
-    }
-    const double2 x0 = xs[j], x1 = xs[j + 32];
+    for (int t = 0; t < kMvRowsPerGroup; ++t)
 #pragma unroll
-    for (int t = 0; t < kMvRowsPerWarp; ++t) {
-      acc[t].x = fma(a0[t].x, x0.x, fma(-a0[t].y, x0.y, acc[t].x));
-      acc[t].y = fma(a0[t].x, x0.y, fma(a0[t].y, x0.x, acc[t].y));
-      acc[t].x = fma(a1[t].x, x1.x, fma(-a1[t].y, x1.y, acc[t].x));
-      acc[t].y = fma(a1[t].x, x1.y, fma(a1[t].y, x1.x, acc[t].y));
+      for (int u = 0; u < S; ++u) a[t][u] = row[t] ? __ldg(row[t] + j + u * kMvGroup) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      const double2 x = xs[j + u * kMvGroup];
+#pragma unroll
+      for (int t = 0; t < kMvRowsPerGroup; ++t) cmac(acc[t], a[t][u], x);
     }
   }
-  if (j < nx) {
-    const double2 x0 = xs[j];
+  for (; j < nx; j += kMvGroup) {
+    const double2 x = xs[j];
 #pragma unroll
-    for (int t = 0; t < kMvRowsPerWarp; ++t) {
-      const double2 a = row[t] ? __ldg(row[t] + j) : make_double2(0.0, 0.0);
-      acc[t].x = fma(a.x, x0.x, fma(-a.y, x0.y, acc[t].x));
-      acc[t].y = fma(a.x, x0.y, fma(a.y, x0.x, acc[t].y));
-    }
+    for (int t = 0; t < kMvRowsPerGroup; ++t)
+      cmac(acc[t], row[t] ? __ldg(row[t] + j) : make_double2(0.0, 0.0), x);
   }
 #pragma unroll
-  for (int t = 0; t < kMvRowsPerWarp; ++t) {
+  for (int t = 0; t < kMvRowsPerGroup; ++t) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = kMvGroup / 2; o > 0; o >>= 1) {
       acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
       acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
     }
   }
-  if (lane == 0) {
+  if (l == 0) {
     double2* yk = Yh + ((long long)r * K + k) * nx;
 #pragma unroll
-    for (int t = 0; t < kMvRowsPerWarp; ++t)
-      if (row[t]) yk[i0 + t * (kFftThreads / 32)] = acc[t];
+    for (int t = 0; t < kMvRowsPerGroup; ++t)
+      if (row[t]) yk[i0 + t * kMvGroups] = acc[t];
   }
 }
 
