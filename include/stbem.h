@@ -287,9 +287,10 @@ int stbem_solve_adjoint(stbem_ctx* ctx, int n_t, int n_x, int vprec, const void*
                         double* dev_lambda, const stbem_solve_opts* opts, stbem_solve_info* info,
                         void* dev_work, size_t work_bytes);
 
-/* ---- Products through time FFTs (Section 2: the block-Toeplitz structure) --
+/* ---- Products through time FFTs (Section 3: block lower triangular) -------
  * The product y_n = sum_{d=0}^{n} A_d x_{n-d} with the lag blocks of
- * V_h, K_h or D_h is a convolution in the time index.  With L the smallest
+ * V_h, K_h or D_h (Toeplitz in time on a uniform grid: the integrals of
+ * eq. (4) depend on t - s only) is a convolution in the time index.  With L the smallest
  * power of two >= 2 n_t and w = e^{-2 pi i / L} the frequency blocks are
  *     Ahat_k = sum_{d=0}^{n_t - 1} A_d w^{d k},  k = 0 .. L/2
  * (complex N_x x N_x, stored Ahat[k][i][j] as interleaved (re, im) doubles;

@@ -3,9 +3,10 @@
 #include <cstddef>
 
 namespace stbem {
-// The block-Toeplitz product y_n = sum_{d<=n} A_d x_{n-d} (Section 2: the
-// lower block-triangular Toeplitz structure of V_h, K_h, D_h) is a linear
-// convolution in the time index.  With L the smallest power of two >= 2 n_t
+// The block-Toeplitz product y_n = sum_{d<=n} A_d x_{n-d} (V_h, K_h, D_h are
+// block lower triangular, Section 3, and on a uniform grid Toeplitz in time,
+// the integrals of eq. (4) depending on t - s only) is a linear convolution
+// in the time index.  With L the smallest power of two >= 2 n_t
 // the zero-padded circular convolution of length L equals it on n < n_t, so
 // with w = e^{-2 pi i / L} and the frequency blocks
 //     Ahat_k = sum_{d < n_t} A_d w^{d k},   k = 0 .. L/2

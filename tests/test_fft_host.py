@@ -2,9 +2,10 @@
 length L (smallest power of two >= 2 n_t), the number of frequency blocks
 L/2 + 1, the byte counts of the frequency blocks and of the workspaces, the
 size limits; and the fact the length rests on, that the zero-padded circular
-convolution of length L equals the linear one on the first n_t steps (Section 2:
-the block-Toeplitz product is a convolution in time), for the product and
-for its transpose (a correlation)."""
+convolution of length L equals the linear one on the first n_t steps (the
+block lower-triangular product of Section 3, Toeplitz in time on a uniform
+grid, is a convolution in time), for the product and for its transpose (a
+correlation)."""
 import ctypes
 
 import numpy as np
